@@ -1,0 +1,307 @@
+"""numpy front end of the C oracle (argument marshalling only).
+
+TEST INFRASTRUCTURE ONLY.  Every function builds the oracle library on first
+use (plain gcc) and calls it through ctypes.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "levels", "decompose", "recompose", "recompose_adjoint", "decompose_adjoint",
+    "correction_norms", "bins", "quantize", "dequantize", "histogram",
+    "code_lengths", "canonical_codes", "encode", "decode", "compress",
+    "decompress", "inspect", "compress_bound", "crc32", "level_sizes",
+    "parse_header", "DTYPE_F32", "DTYPE_F64", "LINF", "L2", "ABS", "REL",
+]
+
+DTYPE_F32, DTYPE_F64 = 0, 1
+LINF, L2 = 0, 1
+ABS, REL = 0, 1
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(_build.build())
+        sz = C.POINTER(C.c_size_t)
+        dp = C.POINTER(C.c_double)
+        u8 = C.POINTER(C.c_uint8)
+        u16 = C.POINTER(C.c_uint16)
+        u32 = C.POINTER(C.c_uint32)
+        u64 = C.POINTER(C.c_uint64)
+        i64 = C.POINTER(C.c_int64)
+        sig = {
+            "oracle_levels": [C.c_int, sz, C.POINTER(C.c_int), sz],
+            "oracle_decompose": [C.c_int, sz, dp, dp],
+            "oracle_recompose": [C.c_int, sz, dp, dp],
+            "oracle_recompose_adjoint": [C.c_int, sz, dp, dp],
+            "oracle_decompose_adjoint": [C.c_int, sz, dp, dp],
+            "oracle_correction_norms": [C.c_int, sz, dp],
+            "oracle_bins": [C.c_int, sz, C.c_double, C.c_double, C.c_double, dp],
+            "oracle_quantize": [C.c_int, sz, dp, dp, C.c_int, C.c_uint32, u16, u64, u64, i64,
+                                C.c_uint64],
+            "oracle_dequantize": [C.c_int, sz, u16, dp, C.c_uint32, C.c_uint64, u64, i64, dp],
+            "oracle_histogram": [u16, C.c_uint64, C.c_uint32, u64],
+            "oracle_code_lengths": [u64, C.c_uint32, u8],
+            "oracle_canonical_codes": [u8, C.c_uint32, u64],
+            "oracle_encode": [u16, C.c_uint64, u8, u64, C.c_uint32, u32, C.c_uint64, u64, u64],
+            "oracle_decode": [u32, C.c_uint64, u64, C.c_uint64, C.c_uint32, u8, C.c_uint32, u16],
+            "oracle_compress": [C.c_int, sz, dp, C.c_int, C.c_double, C.c_int, C.c_int,
+                                C.c_uint32, C.c_uint32, u8, C.c_uint64, u64],
+            "oracle_decompress": [u8, C.c_uint64, dp, C.c_uint64],
+            "oracle_inspect": [u8, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_int), u64],
+        }
+        for name, args in sig.items():
+            f = getattr(_lib, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        _lib.oracle_compress_bound.argtypes = [C.c_int, sz, C.c_uint32, C.c_uint32]
+        _lib.oracle_compress_bound.restype = C.c_uint64
+        _lib.oracle_crc32.argtypes = [u8, C.c_uint64]
+        _lib.oracle_crc32.restype = C.c_uint32
+    return _lib
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def _dims(shape):
+    d = len(shape)
+    if not 1 <= d <= 3 or any(int(s) < 2 for s in shape):
+        raise ValueError("dims must be 1..3 sizes, each >= 2: %r" % (shape,))
+    return d, (C.c_size_t * 3)(*[int(s) for s in shape] + [1] * (3 - d))
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError("%s failed with status %d" % (what, rc))
+
+
+def levels(shape):
+    """Return (L, m) with m[k][l] the node count of dim k on level l."""
+    d, dims = _dims(shape)
+    L = C.c_int()
+    _check(_L().oracle_levels(d, dims, C.byref(L), None), "levels")
+    m = np.zeros(3 * (L.value + 1), dtype=np.uint64)
+    _check(_L().oracle_levels(d, dims, C.byref(L), m.ctypes.data_as(C.POINTER(C.c_size_t))),
+           "levels")
+    return L.value, m.reshape(3, L.value + 1)[:d].astype(np.int64)
+
+
+def level_sizes(shape):
+    """Node count N_l of every level l = 0..L (N_L = number of elements)."""
+    L, m = levels(shape)
+    return [int(np.prod(m[:, l])) for l in range(L + 1)]
+
+
+def _field_op(fn, x, shape, what):
+    d, dims = _dims(shape)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+    if x.size != int(np.prod(shape)):
+        raise ValueError("size mismatch")
+    out = np.empty_like(x)
+    _check(fn(d, dims, _p(x, C.c_double), _p(out, C.c_double)), what)
+    return out
+
+
+def decompose(u):
+    """Level-major coefficient stream (FP64) of the field u (Alg. 1)."""
+    u = np.asarray(u)
+    return _field_op(_L().oracle_decompose, u, u.shape, "decompose")
+
+
+def recompose(coef, shape):
+    return _field_op(_L().oracle_recompose, coef, shape, "recompose").reshape(shape)
+
+
+def recompose_adjoint(g_u):
+    g_u = np.asarray(g_u)
+    return _field_op(_L().oracle_recompose_adjoint, g_u, g_u.shape, "recompose_adjoint")
+
+
+def decompose_adjoint(g_coef, shape):
+    return _field_op(_L().oracle_decompose_adjoint, g_coef, shape,
+                     "decompose_adjoint").reshape(shape)
+
+
+def correction_norms(shape):
+    d, dims = _dims(shape)
+    L, _ = levels(shape)
+    c = np.zeros(L + 1)
+    _check(_L().oracle_correction_norms(d, dims, _p(c, C.c_double)), "correction_norms")
+    return c
+
+
+def bins(shape, tau_abs, norm_inf, eps):
+    d, dims = _dims(shape)
+    L, _ = levels(shape)
+    q = np.zeros(L + 1)
+    _check(_L().oracle_bins(d, dims, float(tau_abs), float(norm_inf), float(eps),
+                            _p(q, C.c_double)), "bins")
+    return q
+
+
+def quantize(coef, shape, q, D=8192, precision=64):
+    """Symbols (uint16) and outliers (stream index, code) of a coefficient stream."""
+    d, dims = _dims(shape)
+    coef = np.ascontiguousarray(coef, dtype=np.float64).reshape(-1)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    sym = np.empty(coef.size, dtype=np.uint16)
+    nout = C.c_uint64()
+    _check(_L().oracle_quantize(d, dims, _p(coef, C.c_double), _p(q, C.c_double), precision, D,
+                                _p(sym, C.c_uint16), C.byref(nout), None, None, 0), "quantize")
+    idx = np.zeros(max(nout.value, 1), dtype=np.uint64)
+    k = np.zeros(max(nout.value, 1), dtype=np.int64)
+    _check(_L().oracle_quantize(d, dims, _p(coef, C.c_double), _p(q, C.c_double), precision, D,
+                                _p(sym, C.c_uint16), C.byref(nout), _p(idx, C.c_uint64),
+                                _p(k, C.c_int64), nout.value), "quantize")
+    return sym, idx[:nout.value], k[:nout.value]
+
+
+def dequantize(sym, shape, q, D, out_idx, out_k):
+    d, dims = _dims(shape)
+    sym = np.ascontiguousarray(sym, dtype=np.uint16)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    out_idx = np.ascontiguousarray(out_idx, dtype=np.uint64)
+    out_k = np.ascontiguousarray(out_k, dtype=np.int64)
+    coef = np.empty(sym.size)
+    _check(_L().oracle_dequantize(d, dims, _p(sym, C.c_uint16), _p(q, C.c_double), D,
+                                  out_idx.size, _p(out_idx, C.c_uint64), _p(out_k, C.c_int64),
+                                  _p(coef, C.c_double)), "dequantize")
+    return coef
+
+
+def histogram(sym, D):
+    sym = np.ascontiguousarray(sym, dtype=np.uint16)
+    h = np.zeros(D, dtype=np.uint64)
+    _check(_L().oracle_histogram(_p(sym, C.c_uint16), sym.size, D, _p(h, C.c_uint64)), "histogram")
+    return h
+
+
+def code_lengths(hist):
+    hist = np.ascontiguousarray(hist, dtype=np.uint64)
+    ln = np.zeros(hist.size, dtype=np.uint8)
+    _check(_L().oracle_code_lengths(_p(hist, C.c_uint64), hist.size, _p(ln, C.c_uint8)),
+           "code_lengths")
+    return ln
+
+
+def canonical_codes(lengths):
+    lengths = np.ascontiguousarray(lengths, dtype=np.uint8)
+    code = np.zeros(lengths.size, dtype=np.uint64)
+    _check(_L().oracle_canonical_codes(_p(lengths, C.c_uint8), lengths.size,
+                                       _p(code, C.c_uint64)), "canonical_codes")
+    return code
+
+
+def encode(sym, lengths, K=1024):
+    """Huffman-encode symbols: returns (words uint32, chunk table uint64, total bits)."""
+    sym = np.ascontiguousarray(sym, dtype=np.uint16)
+    lengths = np.ascontiguousarray(lengths, dtype=np.uint8)
+    code = canonical_codes(lengths)
+    bits = int(lengths[sym].astype(np.uint64).sum())
+    nw = (bits + 31) // 32
+    words = np.zeros(max(nw, 1), dtype=np.uint32)
+    nch = (sym.size + K - 1) // K
+    chunk = np.zeros(max(nch, 1), dtype=np.uint64)
+    tb = C.c_uint64()
+    _check(_L().oracle_encode(_p(sym, C.c_uint16), sym.size, _p(lengths, C.c_uint8),
+                              _p(code, C.c_uint64), K, _p(words, C.c_uint32), words.size,
+                              _p(chunk, C.c_uint64), C.byref(tb)), "encode")
+    return words[:nw], chunk[:nch], tb.value
+
+
+def decode(words, chunk, N, K, lengths):
+    words = np.ascontiguousarray(words, dtype=np.uint32)
+    chunk = np.ascontiguousarray(chunk, dtype=np.uint64)
+    lengths = np.ascontiguousarray(lengths, dtype=np.uint8)
+    sym = np.zeros(N, dtype=np.uint16)
+    w = words if words.size else np.zeros(1, dtype=np.uint32)
+    _check(_L().oracle_decode(_p(w, C.c_uint32), words.size, _p(chunk, C.c_uint64), N, K,
+                              _p(lengths, C.c_uint8), lengths.size, _p(sym, C.c_uint16)), "decode")
+    return sym
+
+
+def compress_bound(shape, D=8192, K=1024):
+    d, dims = _dims(shape)
+    return int(_L().oracle_compress_bound(d, dims, D, K))
+
+
+def compress(u, tol, tol_kind=REL, mode=LINF, D=8192, K=1024, dtype=None):
+    """Container bytes of the field u (dtype defaults to u's own: f32 or f64)."""
+    u = np.asarray(u)
+    if dtype is None:
+        dtype = DTYPE_F32 if u.dtype == np.float32 else DTYPE_F64
+    d, dims = _dims(u.shape)
+    x = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+    cap = compress_bound(u.shape, D, K)
+    out = np.zeros(cap, dtype=np.uint8)
+    nb = C.c_uint64()
+    _check(_L().oracle_compress(d, dims, _p(x, C.c_double), dtype, float(tol), tol_kind, mode, D,
+                                K, _p(out, C.c_uint8), cap, C.byref(nb)), "compress")
+    return out[:nb.value].copy()
+
+
+def inspect(buf):
+    buf = np.ascontiguousarray(np.frombuffer(bytes(buf), dtype=np.uint8))
+    dt, d = C.c_int(), C.c_int()
+    dims = np.zeros(3, dtype=np.uint64)
+    _check(_L().oracle_inspect(_p(buf, C.c_uint8), buf.size, C.byref(dt), C.byref(d),
+                               _p(dims, C.c_uint64)), "inspect")
+    return dt.value, tuple(int(x) for x in dims[:d.value])
+
+
+def decompress(buf):
+    """FP64 reconstruction of a container (shape from the header)."""
+    buf = np.ascontiguousarray(np.frombuffer(bytes(buf), dtype=np.uint8))
+    _, shape = inspect(buf)
+    n = int(np.prod(shape))
+    u = np.empty(n)
+    _check(_L().oracle_decompress(_p(buf, C.c_uint8), buf.size, _p(u, C.c_double), n),
+           "decompress")
+    return u.reshape(shape)
+
+
+def crc32(data):
+    b = np.ascontiguousarray(np.frombuffer(bytes(data), dtype=np.uint8))
+    return int(_L().oracle_crc32(_p(b, C.c_uint8), b.size))
+
+
+def parse_header(buf):
+    """Header fields and section views of a v1 container (plain byte reads)."""
+    b = bytes(buf)
+    u32 = lambda o: int.from_bytes(b[o:o + 4], "little")  # noqa: E731
+    u64 = lambda o: int.from_bytes(b[o:o + 8], "little")  # noqa: E731
+    f64 = lambda o: float(np.frombuffer(b[o:o + 8], dtype="<f8")[0])  # noqa: E731
+    h = dict(magic=b[:4], version=u32(4), dtype=u32(8), ndim=u32(12),
+             dims=tuple(u64(16 + 8 * k) for k in range(u32(12))), L=u32(40), mode=u32(44),
+             tol_kind=u32(48), D=u32(52), K=u32(56), s_lo=u32(60), tol=f64(64),
+             tau_abs=f64(72), norm_inf=f64(80), norm_rms=f64(88), N=u64(96),
+             n_outliers=u64(104), total_bits=u64(112), s_hi=u32(120), crc=u32(124))
+    a16 = lambda x: (x + 15) & ~15  # noqa: E731
+    L = h["L"]
+    off_q = 128
+    off_len = a16(off_q + 8 * (L + 1))
+    off_chunk = a16(off_len + h["s_hi"] - h["s_lo"] + 1)
+    nch = (h["N"] + h["K"] - 1) // h["K"]
+    off_out = a16(off_chunk + 8 * nch)
+    off_bits = a16(off_out + 16 * h["n_outliers"])
+    nw = (h["total_bits"] + 31) // 32
+    arr = np.frombuffer(b, dtype=np.uint8)
+    h["q"] = arr[off_q:off_q + 8 * (L + 1)].view("<f8").copy()
+    ln = np.zeros(h["D"], dtype=np.uint8)
+    ln[h["s_lo"]:h["s_hi"] + 1] = arr[off_len:off_len + h["s_hi"] - h["s_lo"] + 1]
+    h["lengths"] = ln
+    h["chunk"] = arr[off_chunk:off_chunk + 8 * nch].view("<u8").copy()
+    no = h["n_outliers"]
+    h["out_idx"] = arr[off_out:off_out + 8 * no].view("<u8").copy()
+    h["out_k"] = arr[off_out + 8 * no:off_out + 16 * no].view("<i8").copy()
+    h["words"] = arr[off_bits:off_bits + 4 * nw].view("<u4").copy()
+    h["total_bytes"] = off_bits + 4 * nw
+    return h

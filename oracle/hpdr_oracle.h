@@ -1,0 +1,83 @@
+/*
+ * hpdr_oracle.h -- plain, slow FP64 CPU oracle for the MGARD-style reduction
+ * path (multilevel decomposition, level-scaled quantization, canonical
+ * Huffman coding) described in Sec. IV-A (Alg. 1) and Sec. IV-B (Alg. 2) of
+ * "HPDR: High-Performance Portable Scientific Data Reduction Framework".
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or constant with the GPU library; the container format is
+ * implemented here independently from its written definition.
+ *
+ * Conventions
+ *   - arrays are row-major, last dimension contiguous, d = 1..3 dimensions,
+ *     every n_k >= 2;
+ *   - coefficient streams are level-major: level 0 (all coarsest nodes), then
+ *     the nodes that are new on level 1, ..., level L; inside a level, nodes
+ *     follow the row-major order of their level-grid index;
+ *   - every function returns 0 on success and a negative value on a bad
+ *     argument or a malformed buffer.
+ */
+#ifndef HPDR_ORACLE_H
+#define HPDR_ORACLE_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Hierarchy: number of levels L and the node count of every dim per level. */
+int oracle_levels(int d, const size_t *n, int *L, size_t *m_out /* [3*(L+1)], m_out[k*(L+1)+l] */);
+
+/* Multilevel decomposition / recomposition and their transposes (FP64). */
+int oracle_decompose(int d, const size_t *n, const double *u, double *coef);
+int oracle_recompose(int d, const size_t *n, const double *coef, double *u);
+int oracle_recompose_adjoint(int d, const size_t *n, const double *g_u, double *g_coef);
+int oracle_decompose_adjoint(int d, const size_t *n, const double *g_coef, double *g_u);
+
+/* Per-level correction operator norms c_l (l = 1..L; c[0] = 0). */
+int oracle_correction_norms(int d, const size_t *n, double *c /* [L+1] */);
+
+/* Level-scaled quantization bins q[0..L] for an absolute bound tau_abs.
+ * eps = unit roundoff of the data type (2^-24 or 2^-53). */
+int oracle_bins(int d, const size_t *n, double tau_abs, double norm_inf, double eps, double *q);
+
+/* Quantization of a level-major coefficient stream.
+ * precision: 32 = decision in binary32, 64 = decision in binary64.
+ * Writes symbols[N]; returns the number of outliers through *n_out and
+ * their (stream index, integer code) pairs into out_idx/out_k when those
+ * pointers are non-NULL (capacity out_cap). */
+int oracle_quantize(int d, const size_t *n, const double *coef, const double *q, int precision,
+                    uint32_t D, uint16_t *symbols, uint64_t *n_out,
+                    uint64_t *out_idx, int64_t *out_k, uint64_t out_cap);
+int oracle_dequantize(int d, const size_t *n, const uint16_t *symbols, const double *q, uint32_t D,
+                      uint64_t n_out, const uint64_t *out_idx, const int64_t *out_k, double *coef);
+
+/* Huffman stage (Alg. 2). */
+int oracle_histogram(const uint16_t *symbols, uint64_t N, uint32_t D, uint64_t *hist);
+int oracle_code_lengths(const uint64_t *hist, uint32_t D, uint8_t *len);
+int oracle_canonical_codes(const uint8_t *len, uint32_t D, uint64_t *code);
+/* Encode: writes the bitstream (uint32 words, MSB first) and the chunk table
+ * (bit offset of every K-th symbol).  words must hold ceil(bits/32) words. */
+int oracle_encode(const uint16_t *symbols, uint64_t N, const uint8_t *len, const uint64_t *code,
+                  uint32_t K, uint32_t *words, uint64_t nwords_cap, uint64_t *chunk_bits,
+                  uint64_t *total_bits);
+int oracle_decode(const uint32_t *words, uint64_t nwords, const uint64_t *chunk_bits, uint64_t N,
+                  uint32_t K, const uint8_t *len, uint32_t D, uint16_t *symbols);
+
+/* Full container (format v1).  dtype: 0 = binary32 data, 1 = binary64 data
+ * (u is always passed as FP64 values).  mode: 0 = L-infinity, 1 = L2 (RMS).
+ * tol_kind: 0 = absolute, 1 = relative. */
+int oracle_compress(int d, const size_t *n, const double *u, int dtype, double tol, int tol_kind,
+                    int mode, uint32_t D, uint32_t K, uint8_t *out, uint64_t cap,
+                    uint64_t *out_bytes);
+int oracle_decompress(const uint8_t *in, uint64_t in_bytes, double *u, uint64_t cap_elems);
+int oracle_inspect(const uint8_t *in, uint64_t in_bytes, int *dtype, int *d, uint64_t *dims);
+uint64_t oracle_compress_bound(int d, const size_t *n, uint32_t D, uint32_t K);
+uint32_t oracle_crc32(const uint8_t *p, uint64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
