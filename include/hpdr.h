@@ -1,0 +1,162 @@
+/*
+ * hpdr.h -- C ABI of the GB300 (sm_103a) error-bounded multilevel compressor.
+ *
+ * The library implements the data-parallel path of the MGARD reduction
+ * pipeline of "HPDR: High-Performance Portable Scientific Data Reduction
+ * Framework" (Sec. IV-A, Alg. 1: multilevel decomposition with per-level
+ * interpolation coefficients and an L2-projection correction computed by a
+ * mass-matrix multiply and a tridiagonal solve along every dimension, then
+ * level-scaled linear quantization; Sec. IV-B, Alg. 2: histogram, canonical
+ * Huffman codebook, encoding and serialization into one bitstream) and its
+ * inverse.  Every step runs in hand-written CUDA kernels.
+ *
+ * Common conventions
+ *   - Arrays are row-major with the last dimension contiguous; 1 <= ndim <= 3
+ *     and every dims[k] >= 2 (squeeze size-1 dimensions before calling).
+ *   - Pointers named d_* are CUDA device pointers on the context's device;
+ *     h_* are host pointers; the caller owns every buffer it passes.  The
+ *     context owns only its cached plans and workspaces (reused across calls,
+ *     grown on demand; the reductions themselves allocate nothing once the
+ *     workspace is large enough).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All work is
+ *     enqueued on it.  Calls that return a size to the host (compress,
+ *     decompress) synchronize that stream once before returning.
+ *   - Coefficient streams (decompose/recompose and their adjoints) are
+ *     level-major: level 0 (every node of the coarsest grid, row-major), then
+ *     for l = 1..L the nodes that are new on level l, in row-major order of
+ *     their level-l grid index.  Level l therefore starts at N_{l-1}, the node
+ *     count of level l-1.  Element type = dtype.
+ *   - Hierarchy: node i of a dimension sits at coordinate i; one coarsening
+ *     keeps every other node plus the last one; all dimensions coarsen
+ *     together, L = the smallest per-dimension number of coarsenings that
+ *     reaches two nodes.
+ *   - No exception crosses the ABI.  Errors are reported by the returned
+ *     status; a failing call leaves the output buffer's contents undefined.
+ *   - Calls on one context must not overlap in time (one host thread at a
+ *     time per context); use one context per host thread.
+ */
+#ifndef HPDR_H
+#define HPDR_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HPDR_OK = 0,
+    HPDR_ERR_ARG = -1,       /* invalid argument (dims, dtype, tolerance, null pointer) */
+    HPDR_ERR_CUDA = -2,      /* a CUDA runtime call or kernel failed */
+    HPDR_ERR_CAPACITY = -3,  /* output buffer too small (or too many outliers) */
+    HPDR_ERR_FORMAT = -4,    /* malformed or corrupted container */
+    HPDR_ERR_TIMEOUT = -5,   /* a bounded device-side wait gave up */
+    HPDR_ERR_NOMEM = -6      /* device allocation of a workspace failed */
+} hpdr_status;
+
+typedef enum { HPDR_F32 = 0, HPDR_F64 = 1 } hpdr_dtype;
+typedef enum { HPDR_LINF = 0, HPDR_L2 = 1 } hpdr_mode;      /* norm of the error bound */
+typedef enum { HPDR_ABS = 0, HPDR_REL = 1 } hpdr_tol_kind;  /* REL: tol x norm of the input */
+
+typedef struct hpdr_ctx hpdr_ctx;
+
+/* Tunables of the lossless stage (Alg. 2).  dict_size D: quantized codes k
+ * with |k| < D/2 become symbols k + D/2; others are escaped (symbol 0) and
+ * stored verbatim as outliers; even, 4 <= D <= 65536; default 8192.
+ * chunk K: symbols per decode chunk (the chunk table stores the bit offset of
+ * every K-th symbol); multiple of 128, 128 <= K <= 32768; default 1024.
+ * A zero field selects the default. */
+typedef struct {
+    uint32_t dict_size;
+    uint32_t chunk;
+} hpdr_config;
+
+/* Create a context on CUDA device `device`.  *ctx receives the handle.
+ * Errors: HPDR_ERR_ARG (null ctx, bad device), HPDR_ERR_CUDA. */
+hpdr_status hpdr_ctx_create(hpdr_ctx **ctx, int device);
+
+/* Release the context's workspaces and plans.  Waits for nothing: the caller
+ * must make sure no work of this context is still running. */
+hpdr_status hpdr_ctx_destroy(hpdr_ctx *ctx);
+
+/* Upper bound of the container size for a field, with the given config (NULL
+ * = defaults).  0 on bad arguments. */
+size_t hpdr_compress_bound(int ndim, const size_t *dims, hpdr_dtype dtype, const hpdr_config *cfg);
+
+/* Compress a device-resident field (Alg. 1 then Alg. 2).
+ *   d_in        device array, ndim/dims as above, element type dtype.
+ *   tol, tol_kind, mode: the error bound.  REL: tau = tol * max|u| (LINF) or
+ *               tol * rms(u) (L2); ABS: tau = tol.  The reconstruction then
+ *               satisfies max|u - u~| <= tau (which also bounds the RMS error).
+ *   d_out       device buffer of out_capacity bytes receiving the container
+ *               (format v1: 128-byte header, bins, code lengths, chunk table,
+ *               outliers, bitstream).
+ *   out_bytes   host pointer receiving the container size.
+ * Errors: HPDR_ERR_ARG (including a bound below the data type's precision
+ * floor, tau <= 32 (L+1) eps max|u|), HPDR_ERR_CAPACITY, HPDR_ERR_NOMEM,
+ * HPDR_ERR_CUDA.  Synchronizes `stream` once. */
+hpdr_status hpdr_compress(hpdr_ctx *ctx, const void *d_in, hpdr_dtype dtype, int ndim,
+                          const size_t *dims, double tol, hpdr_tol_kind tol_kind, hpdr_mode mode,
+                          const hpdr_config *cfg, void *d_out, size_t out_capacity,
+                          size_t *out_bytes, void *stream);
+
+/* Decompress a device-resident container into d_out (out_capacity bytes; the
+ * field's shape and type are read from the header, see hpdr_inspect).
+ * Errors: HPDR_ERR_FORMAT, HPDR_ERR_CAPACITY, HPDR_ERR_ARG, HPDR_ERR_CUDA.
+ * Synchronizes `stream` once (to read the header). */
+hpdr_status hpdr_decompress(hpdr_ctx *ctx, const void *d_in, size_t in_bytes, void *d_out,
+                            size_t out_capacity, void *stream);
+
+/* Read the shape and type of a container held in host or device memory
+ * (detected).  dims receives ndim entries (3 slots must be provided). */
+hpdr_status hpdr_inspect(const void *in, size_t in_bytes, hpdr_dtype *dtype, int *ndim,
+                         size_t *dims);
+
+/* Multilevel decomposition (Alg. 1 without quantization): d_coef receives the
+ * level-major coefficient stream of d_u (same element count and type). */
+hpdr_status hpdr_decompose(hpdr_ctx *ctx, const void *d_u, void *d_coef, hpdr_dtype dtype,
+                           int ndim, const size_t *dims, void *stream);
+
+/* Multilevel recomposition, the exact inverse of hpdr_decompose. */
+hpdr_status hpdr_recompose(hpdr_ctx *ctx, const void *d_coef, void *d_u, hpdr_dtype dtype,
+                           int ndim, const size_t *dims, void *stream);
+
+/* Transpose of hpdr_recompose: maps a field-shaped gradient d_grad_u to the
+ * gradient with respect to the coefficient stream (no intermediate of the
+ * forward pass is needed: the map is linear). */
+hpdr_status hpdr_recompose_adjoint(hpdr_ctx *ctx, const void *d_grad_u, void *d_grad_coef,
+                                   hpdr_dtype dtype, int ndim, const size_t *dims, void *stream);
+
+/* Transpose of hpdr_decompose: maps a coefficient-stream gradient to a
+ * field-shaped gradient. */
+hpdr_status hpdr_decompose_adjoint(hpdr_ctx *ctx, const void *d_grad_coef, void *d_grad_u,
+                                   hpdr_dtype dtype, int ndim, const size_t *dims, void *stream);
+
+/* Huffman stage alone (Alg. 2) on a device array of N uint16 symbols < D:
+ * histogram, code lengths (two-queue rule, leaves sorted by (frequency,
+ * symbol)), canonical codewords, encoding.  Outputs (device): d_lengths[D]
+ * code length per symbol, d_chunk_bits[ceil(N/K)] bit offset of every K-th
+ * symbol, d_words[words_capacity] bitstream (uint32 words, MSB first).
+ * *total_bits (host) receives the bitstream length.  Synchronizes `stream`.
+ * Errors: HPDR_ERR_ARG, HPDR_ERR_CAPACITY, HPDR_ERR_CUDA. */
+hpdr_status hpdr_huffman_encode(hpdr_ctx *ctx, const uint16_t *d_symbols, uint64_t N, uint32_t D,
+                                uint32_t K, uint8_t *d_lengths, uint64_t *d_chunk_bits,
+                                uint32_t *d_words, uint64_t words_capacity, uint64_t *total_bits,
+                                void *stream);
+
+/* Inverse of hpdr_huffman_encode: decodes N symbols from the bitstream of
+ * total_bits bits (ceil(total_bits/32) words) with the given code lengths and
+ * chunk table (device pointers) into d_symbols.  Every chunk must end exactly
+ * where the next one starts and the last one at total_bits.
+ * Errors: HPDR_ERR_FORMAT (invalid stream), HPDR_ERR_ARG, HPDR_ERR_CUDA. */
+hpdr_status hpdr_huffman_decode(hpdr_ctx *ctx, const uint32_t *d_words, uint64_t total_bits,
+                                const uint64_t *d_chunk_bits, uint64_t N, uint32_t D, uint32_t K,
+                                const uint8_t *d_lengths, uint16_t *d_symbols, void *stream);
+
+/* Static description of a status code. */
+const char *hpdr_status_string(hpdr_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,644 @@
+// api.cu -- extern "C" entry points declared in include/hpdr.h.
+//
+// compress  = norm pre-pass -> bins -> for l = L..1 { fused coefficients +
+//             quantization + histogram + restriction; Thomas solves + add }
+//             -> level 0 -> codebook -> encode -> header   (Alg. 1, Alg. 2)
+// decompress = header -> decode tables -> chunk-parallel decode -> level 0 ->
+//             for l = 1..L { restriction of the dequantized level; solves and
+//             subtract; expand }  (the inverse of Alg. 1)
+#include <cstring>
+#include <cstdio>
+#include <cmath>
+#include <new>
+#include "internal.cuh"
+#include "levels.cuh"
+#include "huffman.cuh"
+
+using namespace hpdr;
+
+namespace {
+
+struct DevGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DevGuard(int d)
+    {
+        cudaGetDevice(&prev);
+        if (prev != d) { changed = cudaSetDevice(d) == cudaSuccess; }
+    }
+    ~DevGuard() { if (changed) cudaSetDevice(prev); }
+};
+
+struct Carver {
+    char *p;
+    size_t used = 0;
+    explicit Carver(void *base) : p((char *)base) {}
+    template <typename T> T *take(size_t count)
+    {
+        size_t off = (used + 255) & ~size_t(255);
+        used = off + count * sizeof(T);
+        return reinterpret_cast<T *>(p ? p + off : nullptr);
+    }
+};
+
+hpdr_status map_device_status(unsigned st)
+{
+    switch (st) {
+    case DS_OK: return HPDR_OK;
+    case DS_ARG: return HPDR_ERR_ARG;
+    case DS_CAPACITY: return HPDR_ERR_CAPACITY;
+    case DS_FORMAT: return HPDR_ERR_FORMAT;
+    case DS_LENGTH: return HPDR_ERR_CAPACITY;
+    default: return HPDR_ERR_CUDA;
+    }
+}
+
+bool valid_cfg(const hpdr_config *cfg, unsigned &D, unsigned &K)
+{
+    D = cfg ? cfg->dict_size : 8192;
+    K = cfg ? cfg->chunk : 1024;
+    if (cfg && D == 0) D = 8192;
+    if (cfg && K == 0) K = 1024;
+    if (D < 4 || D > 65536 || (D & 1)) return false;
+    if (K < 128 || K > 32768 || (K % 128)) return false;
+    return true;
+}
+
+// outlier list: up to N/8 entries (at least 2^20, at most N)
+unsigned long long out_cap_of(long long N) { return std::min<long long>(N, std::max<long long>(1 << 20, N / 8)); }
+
+long long total_of(int ndim, const size_t *dims)
+{
+    long long n = 1;
+    for (int k = 0; k < ndim; k++) n *= (long long)dims[k];
+    return n;
+}
+
+// workspace of one field: scalars, partials, hist, level buffers, symbols,
+// chunk tables, outliers, Huffman scratch
+struct Ws {
+    Scalars *sc;
+    double *partials;
+    unsigned long long *hist;
+    void *va, *vb, *b;
+    uint16_t *sym;
+    unsigned long long *chunk_bits;
+    unsigned *chunk_esc;
+    unsigned long long *oidx;
+    long long *ok;
+    unsigned long long ocap;
+    void *huff;
+};
+
+size_t carve_ws(void *base, const Plan *P, size_t esz, unsigned D, unsigned K, bool need_sym, Ws *w)
+{
+    Carver c(base);
+    long long N = P->N[P->L];
+    long long Nl1 = P->L >= 1 ? P->N[P->L - 1] : 1;
+    unsigned long long nch = (N + K - 1) / K;
+    w->sc = c.take<Scalars>(1);
+    w->partials = c.take<double>(2 * norm_parts());
+    w->hist = c.take<unsigned long long>(D);
+    w->va = c.take<char>(Nl1 * esz);
+    w->vb = c.take<char>(Nl1 * esz);
+    w->b = c.take<char>(Nl1 * esz);
+    w->sym = need_sym ? c.take<uint16_t>(N + 8) : nullptr;
+    w->chunk_bits = c.take<unsigned long long>(nch + 2);
+    w->chunk_esc = c.take<unsigned>(nch + 2);
+    w->ocap = out_cap_of(N);
+    w->oidx = c.take<unsigned long long>(w->ocap);
+    w->ok = c.take<long long>(w->ocap);
+    w->huff = c.take<char>(huff_scratch_bytes(D));
+    return c.used + 256;
+}
+
+template <typename T> const LevelGeom<T> &geom(const Plan *P, int l);
+template <> const LevelGeom<float> &geom<float>(const Plan *P, int l) { return P->gf[l]; }
+template <> const LevelGeom<double> &geom<double>(const Plan *P, int l) { return P->gd[l]; }
+
+#define CK(x)                                                    \
+    do {                                                         \
+        cudaError_t _e = (x);                                    \
+        if (_e != cudaSuccess) { return HPDR_ERR_CUDA; }         \
+    } while (0)
+
+template <typename T>
+hpdr_status compress_t(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, const size_t *dims,
+                       double tol, int tol_kind, int mode, unsigned D, unsigned K, uint8_t *out,
+                       size_t cap, size_t *out_bytes, cudaStream_t s)
+{
+    Ws w;
+    size_t need = carve_ws(nullptr, P, sizeof(T), D, K, true, &w);
+    hpdr_status st = ensure_workspace(ctx, need);
+    if (st != HPDR_OK) return st;
+    carve_ws(ctx->ws.base, P, sizeof(T), D, K, true, &w);
+    const int L = P->L;
+    const long long N = P->N[L];
+    CK(cudaMemsetAsync(w.sc, 0, sizeof(Scalars), s));
+    CK(cudaMemsetAsync(w.hist, 0, sizeof(unsigned long long) * D, s));
+    CK(launch_norm<T>(u, N, w.partials, norm_parts(), s));
+    BinArgs ba;
+    memset(&ba, 0, sizeof(ba));
+    ba.L = L;
+    for (int l = 0; l <= L; l++) ba.c[l] = P->corr_norm[l];
+    ba.tol = tol;
+    ba.tol_kind = tol_kind;
+    ba.mode = mode;
+    ba.eps = sizeof(T) == 4 ? ldexp(1.0, -24) : ldexp(1.0, -53);
+    ba.N = N;
+    CK(launch_bins(ba, w.partials, norm_parts(), w.sc, s));
+
+    QuantOut qo;
+    qo.sym = w.sym; qo.hist = w.hist; qo.out_idx = w.oidx; qo.out_k = w.ok; qo.out_cap = w.ocap;
+    qo.D = D; qo.sc = w.sc;
+    const T *v = u;
+    for (int l = L; l >= 1; l--) {
+        T *vc = (T *)(((L - l) % 2 == 0) ? w.va : w.vb);
+        RestrictArgs<T> a;
+        memset(&a, 0, sizeof(a));
+        a.g = geom<T>(P, l);
+        a.v = v;
+        a.qo = qo;
+        a.b = (T *)w.b;
+        a.vc = vc;
+        CK(launch_restrict<T>(WSrc::FIELD, Sink::QUANT, a, s));
+        CK(launch_solves<T>(a.g, (T *)w.b, vc, +1, s));
+        v = vc;
+    }
+    CK(launch_level0<T>(Sink::QUANT, v, P->N[0], nullptr, qo, s));
+
+    HuffScratch hs;
+    huff_scratch_carve(w.huff, D, w.sc, &hs);
+    CK(launch_codebook(w.hist, D, hs, s));
+    EncodeArgs ea;
+    memset(&ea, 0, sizeof(ea));
+    ea.sym = w.sym; ea.N = (unsigned long long)N; ea.D = D; ea.K = K;
+    ea.len = hs.len; ea.code = hs.code;
+    ea.chunk_bits = w.chunk_bits; ea.chunk_esc = w.chunk_esc; ea.sc = w.sc;
+    ea.container = out; ea.L = L; ea.capacity = cap;
+    ea.oidx_unordered = w.oidx; ea.ok_unordered = w.ok;
+    CK(launch_encode(ea, s));
+    HeaderArgs h;
+    memset(&h, 0, sizeof(h));
+    h.dtype = sizeof(T) == 4 ? 0 : 1;
+    h.ndim = ndim;
+    h.L = L;
+    h.mode = mode;
+    h.tol_kind = tol_kind;
+    for (int k = 0; k < 3; k++) h.dims[k] = k < ndim ? dims[k] : 1;
+    h.D = D; h.K = K; h.tol = tol; h.N = (unsigned long long)N;
+    CK(launch_header(h, hs.len, w.sc, out, s));
+    Scalars *hsc = (Scalars *)ctx->host_pinned;
+    CK(cudaMemcpyAsync(hsc, w.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hsc->status) return map_device_status(hsc->status);
+    *out_bytes = (size_t)hsc->out_bytes;
+    return HPDR_OK;
+}
+
+// ----- container header (host side) --------------------------------------
+struct Hdr {
+    int dtype, ndim, L, mode, tol_kind;
+    size_t dims[3];
+    unsigned D, K, s_lo, s_hi;
+    unsigned long long N, n_out, bits, nch, nwords;
+    unsigned long long off_len, off_chunk, off_out, off_bits, total;
+    double q[kMaxLevels + 1];
+};
+
+uint32_t crc32_host(const uint8_t *p, int n)
+{
+    uint32_t c = 0xFFFFFFFFu;
+    for (int i = 0; i < n; i++) {
+        c ^= p[i];
+        for (int b = 0; b < 8; b++) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
+    }
+    return c ^ 0xFFFFFFFFu;
+}
+uint32_t rd32(const uint8_t *p) { uint32_t v = 0; for (int i = 0; i < 4; i++) v |= (uint32_t)p[i] << (8 * i); return v; }
+uint64_t rd64(const uint8_t *p) { uint64_t v = 0; for (int i = 0; i < 8; i++) v |= (uint64_t)p[i] << (8 * i); return v; }
+
+hpdr_status parse_header(const uint8_t *b, size_t avail, size_t in_bytes, Hdr *h)
+{
+    if (in_bytes < 128 || avail < 128) return HPDR_ERR_FORMAT;
+    if (memcmp(b, "HPDR", 4) != 0 || rd32(b + 4) != 1) return HPDR_ERR_FORMAT;
+    if (crc32_host(b, 124) != rd32(b + 124)) return HPDR_ERR_FORMAT;
+    h->dtype = (int)rd32(b + 8);
+    h->ndim = (int)rd32(b + 12);
+    if (h->dtype < 0 || h->dtype > 1 || h->ndim < 1 || h->ndim > 3) return HPDR_ERR_FORMAT;
+    for (int k = 0; k < 3; k++) h->dims[k] = (size_t)rd64(b + 16 + 8 * k);
+    for (int k = 0; k < h->ndim; k++) if (h->dims[k] < 2 || h->dims[k] > (1u << 30)) return HPDR_ERR_FORMAT;
+    h->L = (int)rd32(b + 40);
+    h->mode = (int)rd32(b + 44);
+    h->tol_kind = (int)rd32(b + 48);
+    h->D = rd32(b + 52);
+    h->K = rd32(b + 56);
+    h->s_lo = rd32(b + 60);
+    h->N = rd64(b + 96);
+    h->n_out = rd64(b + 104);
+    h->bits = rd64(b + 112);
+    h->s_hi = rd32(b + 120);
+    if (levels_of(h->ndim, h->dims) != h->L || h->L > kMaxLevels) return HPDR_ERR_FORMAT;
+    if ((long long)h->N != total_of(h->ndim, h->dims)) return HPDR_ERR_FORMAT;
+    if (h->D < 4 || h->D > 65536 || (h->D & 1) || h->K < 128 || h->K > 32768 || (h->K % 128))
+        return HPDR_ERR_FORMAT;
+    if (h->s_hi >= h->D || h->s_lo > h->s_hi || h->n_out > h->N) return HPDR_ERR_FORMAT;
+    if (h->bits > 63ULL * h->N || h->bits < h->N) return HPDR_ERR_FORMAT;
+    h->nch = (h->N + h->K - 1) / h->K;
+    h->nwords = (h->bits + 31) / 32;
+    h->off_len = a16(128 + 8ULL * (h->L + 1));
+    h->off_chunk = a16(h->off_len + (h->s_hi - h->s_lo + 1));
+    h->off_out = a16(h->off_chunk + 8 * h->nch);
+    h->off_bits = a16(h->off_out + 16 * h->n_out);
+    h->total = h->off_bits + 4 * h->nwords;
+    if (h->total > in_bytes) return HPDR_ERR_FORMAT;
+    if (avail >= 128 + 8ULL * (h->L + 1))
+        for (int l = 0; l <= h->L; l++) {
+            uint64_t u = rd64(b + 128 + 8 * l);
+            memcpy(&h->q[l], &u, 8);
+            if (!(h->q[l] > 0.0) || !std::isfinite(h->q[l])) return HPDR_ERR_FORMAT;
+        }
+    return HPDR_OK;
+}
+
+template <typename T>
+hpdr_status decompress_t(hpdr_ctx *ctx, const Plan *P, const Hdr &h, const uint8_t *in, T *out,
+                         cudaStream_t s)
+{
+    Ws w;
+    size_t need = carve_ws(nullptr, P, sizeof(T), h.D, h.K, true, &w);
+    hpdr_status st = ensure_workspace(ctx, need);
+    if (st != HPDR_OK) return st;
+    carve_ws(ctx->ws.base, P, sizeof(T), h.D, h.K, true, &w);
+    const int L = P->L;
+    Scalars *hsc = (Scalars *)ctx->host_pinned;
+    memset(hsc, 0, sizeof(Scalars));
+    for (int l = 0; l <= L; l++) {
+        hsc->q[l] = h.q[l];
+        hsc->q_f[l] = (float)h.q[l];
+        hsc->rho_d[l] = 1.0 / h.q[l];
+        hsc->rho_f[l] = (float)(1.0 / h.q[l]);
+    }
+    hsc->n_out = h.n_out;
+    hsc->total_bits = h.bits;
+    CK(cudaMemcpyAsync(w.sc, hsc, sizeof(Scalars), cudaMemcpyHostToDevice, s));
+    HuffScratch hs;
+    huff_scratch_carve(w.huff, h.D, w.sc, &hs);
+    CK(cudaMemsetAsync(hs.len, 0, h.D, s));
+    CK(cudaMemcpyAsync(hs.len + h.s_lo, in + h.off_len, h.s_hi - h.s_lo + 1, cudaMemcpyDeviceToDevice, s));
+    CK(launch_decode_tables(hs.len, h.D, hs, s));
+    DecodeArgs da;
+    da.words = (const uint32_t *)(in + h.off_bits);
+    da.nwords = h.nwords;
+    da.chunk = (const unsigned long long *)(in + h.off_chunk);
+    da.N = h.N; da.total_bits = h.bits; da.K = h.K; da.sym = w.sym;
+    CK(launch_decode(da, hs, s));
+    SymIn si;
+    si.sym = w.sym; si.D = h.D; si.sc = w.sc;
+    si.out_idx = (const unsigned long long *)(in + h.off_out);
+    si.out_k = (const long long *)(in + h.off_out + 8 * h.n_out);
+    si.n_out = h.n_out;
+    si.status = &w.sc->status;
+    // level buffers: v_{l-1} in X, v_l written to Y (or to out at l = L)
+    T *bufs[2] = {(T *)w.va, (T *)w.vb};
+    T *v = L == 0 ? out : bufs[0];
+    CK(launch_level0_in<T>(WSrc::SYMBOLS, nullptr, si, P->N[0], v, s));
+    for (int l = 1; l <= L; l++) {
+        const LevelGeom<T> &g = geom<T>(P, l);
+        RestrictArgs<T> a;
+        memset(&a, 0, sizeof(a));
+        a.g = g;
+        a.symin = si;
+        a.b = (T *)w.b;
+        CK(launch_restrict<T>(WSrc::SYMBOLS, Sink::NONE, a, s));
+        CK(launch_solves<T>(g, (T *)w.b, v, -1, s));
+        T *dst = (l == L) ? out : bufs[l % 2];
+        CK(launch_expand<T>(WSrc::SYMBOLS, g, v, nullptr, si, dst, s));
+        v = dst;
+    }
+    CK(cudaMemcpyAsync(hsc, w.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hsc->status) return map_device_status(hsc->status);
+    return HPDR_OK;
+}
+
+template <typename T>
+hpdr_status decompose_t(hpdr_ctx *ctx, const Plan *P, const T *u, T *coef, cudaStream_t s)
+{
+    Ws w;
+    size_t need = carve_ws(nullptr, P, sizeof(T), 4, 128, false, &w);
+    hpdr_status st = ensure_workspace(ctx, need);
+    if (st != HPDR_OK) return st;
+    carve_ws(ctx->ws.base, P, sizeof(T), 4, 128, false, &w);
+    const int L = P->L;
+    const T *v = u;
+    QuantOut qo;
+    memset(&qo, 0, sizeof(qo));
+    for (int l = L; l >= 1; l--) {
+        T *vc = (T *)(((L - l) % 2 == 0) ? w.va : w.vb);
+        RestrictArgs<T> a;
+        memset(&a, 0, sizeof(a));
+        a.g = geom<T>(P, l);
+        a.v = v;
+        a.coef_out = coef;
+        a.b = (T *)w.b;
+        a.vc = vc;
+        CK(launch_restrict<T>(WSrc::FIELD, Sink::STREAM, a, s));
+        CK(launch_solves<T>(a.g, (T *)w.b, vc, +1, s));
+        v = vc;
+    }
+    CK(launch_level0<T>(Sink::STREAM, v, P->N[0], coef, qo, s));
+    return HPDR_OK;
+}
+
+template <typename T>
+hpdr_status recompose_t(hpdr_ctx *ctx, const Plan *P, const T *coef, T *out, cudaStream_t s)
+{
+    Ws w;
+    size_t need = carve_ws(nullptr, P, sizeof(T), 4, 128, false, &w);
+    hpdr_status st = ensure_workspace(ctx, need);
+    if (st != HPDR_OK) return st;
+    carve_ws(ctx->ws.base, P, sizeof(T), 4, 128, false, &w);
+    const int L = P->L;
+    SymIn si;
+    memset(&si, 0, sizeof(si));
+    T *bufs[2] = {(T *)w.va, (T *)w.vb};
+    T *v = L == 0 ? out : bufs[0];
+    CK(launch_level0_in<T>(WSrc::STREAM, coef, si, P->N[0], v, s));
+    for (int l = 1; l <= L; l++) {
+        const LevelGeom<T> &g = geom<T>(P, l);
+        RestrictArgs<T> a;
+        memset(&a, 0, sizeof(a));
+        a.g = g;
+        a.coef_in = coef;
+        a.b = (T *)w.b;
+        CK(launch_restrict<T>(WSrc::STREAM, Sink::NONE, a, s));
+        CK(launch_solves<T>(g, (T *)w.b, v, -1, s));
+        T *dst = (l == L) ? out : bufs[l % 2];
+        CK(launch_expand<T>(WSrc::STREAM, g, v, coef, si, dst, s));
+        v = dst;
+    }
+    return HPDR_OK;
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+hpdr_status hpdr_ctx_create(hpdr_ctx **ctx, int device)
+{
+    if (!ctx) return HPDR_ERR_ARG;
+    *ctx = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) { cudaGetLastError(); return HPDR_ERR_CUDA; }
+    if (device < 0 || device >= n) return HPDR_ERR_ARG;
+    hpdr_ctx *c = new (std::nothrow) hpdr_ctx();
+    if (!c) return HPDR_ERR_NOMEM;
+    c->device = device;
+    DevGuard g(device);
+    if (cudaMallocHost(&c->host_pinned, 64 * 1024) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return HPDR_ERR_CUDA;
+    }
+    *ctx = c;
+    return HPDR_OK;
+}
+
+hpdr_status hpdr_ctx_destroy(hpdr_ctx *ctx)
+{
+    if (!ctx) return HPDR_ERR_ARG;
+    DevGuard g(ctx->device);
+    for (auto &kv : ctx->plans) { cudaFree(kv.second->tables); delete kv.second; }
+    if (ctx->ws.base) cudaFree(ctx->ws.base);
+    if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+    delete ctx;
+    return HPDR_OK;
+}
+
+size_t hpdr_compress_bound(int ndim, const size_t *dims, hpdr_dtype dtype, const hpdr_config *cfg)
+{
+    unsigned D, K;
+    if (!dims || ndim < 1 || ndim > 3 || !valid_cfg(cfg, D, K)) return 0;
+    if (dtype != HPDR_F32 && dtype != HPDR_F64) return 0;
+    for (int k = 0; k < ndim; k++) if (dims[k] < 2 || dims[k] > (1u << 30)) return 0;
+    int L = levels_of(ndim, dims);
+    unsigned long long N = (unsigned long long)total_of(ndim, dims);
+    unsigned long long b = a16(128 + 8ULL * (L + 1));
+    b = a16(b + D);
+    b = a16(b + 8 * ((N + K - 1) / K));
+    b = a16(b + 16 * N);
+    b += 4 * ((63 * N + 31) / 32);
+    return (size_t)b;
+}
+
+hpdr_status hpdr_compress(hpdr_ctx *ctx, const void *d_in, hpdr_dtype dtype, int ndim,
+                          const size_t *dims, double tol, hpdr_tol_kind tol_kind, hpdr_mode mode,
+                          const hpdr_config *cfg, void *d_out, size_t out_capacity,
+                          size_t *out_bytes, void *stream)
+{
+    unsigned D, K;
+    if (!ctx || !d_in || !d_out || !out_bytes || !valid_cfg(cfg, D, K)) return HPDR_ERR_ARG;
+    if ((dtype != HPDR_F32 && dtype != HPDR_F64) || (mode != HPDR_LINF && mode != HPDR_L2) ||
+        (tol_kind != HPDR_ABS && tol_kind != HPDR_REL) || !(tol > 0.0) || !std::isfinite(tol))
+        return HPDR_ERR_ARG;
+    DevGuard g(ctx->device);
+    Plan *P;
+    hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P);
+    if (st != HPDR_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == HPDR_F32)
+        return compress_t<float>(ctx, P, (const float *)d_in, ndim, dims, tol, tol_kind, mode, D, K,
+                                 (uint8_t *)d_out, out_capacity, out_bytes, s);
+    return compress_t<double>(ctx, P, (const double *)d_in, ndim, dims, tol, tol_kind, mode, D, K,
+                              (uint8_t *)d_out, out_capacity, out_bytes, s);
+}
+
+hpdr_status hpdr_inspect(const void *in, size_t in_bytes, hpdr_dtype *dtype, int *ndim, size_t *dims)
+{
+    if (!in || !dtype || !ndim || !dims) return HPDR_ERR_ARG;
+    uint8_t hb[128];
+    if (in_bytes < 128) return HPDR_ERR_FORMAT;
+    if (is_device_ptr(in)) {
+        if (cudaMemcpy(hb, in, 128, cudaMemcpyDeviceToHost) != cudaSuccess) return HPDR_ERR_CUDA;
+    } else {
+        memcpy(hb, in, 128);
+    }
+    Hdr h;
+    hpdr_status st = parse_header(hb, 128, in_bytes, &h);
+    if (st != HPDR_OK) return st;
+    *dtype = (hpdr_dtype)h.dtype;
+    *ndim = h.ndim;
+    for (int k = 0; k < 3; k++) dims[k] = k < h.ndim ? h.dims[k] : 1;
+    return HPDR_OK;
+}
+
+hpdr_status hpdr_decompress(hpdr_ctx *ctx, const void *d_in, size_t in_bytes, void *d_out,
+                            size_t out_capacity, void *stream)
+{
+    if (!ctx || !d_in || !d_out) return HPDR_ERR_ARG;
+    DevGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    uint8_t *hb = (uint8_t *)ctx->host_pinned + 32 * 1024;
+    size_t hdr_bytes = 128 + 8 * (kMaxLevels + 1);
+    size_t rd = in_bytes < hdr_bytes ? in_bytes : hdr_bytes;
+    if (in_bytes < 128) return HPDR_ERR_FORMAT;
+    CK(cudaMemcpyAsync(hb, d_in, rd, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    Hdr h;
+    hpdr_status st = parse_header(hb, rd, in_bytes, &h);
+    if (st != HPDR_OK) return st;
+    if (rd < 128 + 8ULL * (h.L + 1)) return HPDR_ERR_FORMAT;
+    size_t esz = h.dtype == 0 ? 4 : 8;
+    if (out_capacity < h.N * esz) return HPDR_ERR_CAPACITY;
+    Plan *P;
+    st = get_plan(ctx, h.ndim, h.dims, h.dtype == 1, &P);
+    if (st != HPDR_OK) return st;
+    if (h.dtype == 0) return decompress_t<float>(ctx, P, h, (const uint8_t *)d_in, (float *)d_out, s);
+    return decompress_t<double>(ctx, P, h, (const uint8_t *)d_in, (double *)d_out, s);
+}
+
+hpdr_status hpdr_decompose(hpdr_ctx *ctx, const void *d_u, void *d_coef, hpdr_dtype dtype,
+                           int ndim, const size_t *dims, void *stream)
+{
+    if (!ctx || !d_u || !d_coef || (dtype != HPDR_F32 && dtype != HPDR_F64)) return HPDR_ERR_ARG;
+    DevGuard g(ctx->device);
+    Plan *P;
+    hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P);
+    if (st != HPDR_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == HPDR_F32) return decompose_t<float>(ctx, P, (const float *)d_u, (float *)d_coef, s);
+    return decompose_t<double>(ctx, P, (const double *)d_u, (double *)d_coef, s);
+}
+
+hpdr_status hpdr_recompose(hpdr_ctx *ctx, const void *d_coef, void *d_u, hpdr_dtype dtype,
+                           int ndim, const size_t *dims, void *stream)
+{
+    if (!ctx || !d_u || !d_coef || (dtype != HPDR_F32 && dtype != HPDR_F64)) return HPDR_ERR_ARG;
+    DevGuard g(ctx->device);
+    Plan *P;
+    hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P);
+    if (st != HPDR_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == HPDR_F32) return recompose_t<float>(ctx, P, (const float *)d_coef, (float *)d_u, s);
+    return recompose_t<double>(ctx, P, (const double *)d_coef, (double *)d_u, s);
+}
+
+hpdr_status hpdr_huffman_encode(hpdr_ctx *ctx, const uint16_t *d_symbols, uint64_t N, uint32_t D,
+                                uint32_t K, uint8_t *d_lengths, uint64_t *d_chunk_bits,
+                                uint32_t *d_words, uint64_t words_capacity, uint64_t *total_bits,
+                                void *stream)
+{
+    hpdr_config cfg = {D, K};
+    unsigned Dv, Kv;
+    if (!ctx || !d_symbols || !d_lengths || !d_chunk_bits || !d_words || !total_bits || N == 0 ||
+        !valid_cfg(&cfg, Dv, Kv) || ((uintptr_t)d_symbols & 15))
+        return HPDR_ERR_ARG;
+    DevGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long nch = (N + K - 1) / K;
+    Carver c(nullptr);
+    c.take<Scalars>(1); c.take<unsigned long long>(D); c.take<unsigned long long>(nch + 2);
+    c.take<unsigned>(nch + 2); c.take<char>(huff_scratch_bytes(D));
+    hpdr_status st = ensure_workspace(ctx, c.used + 256);
+    if (st != HPDR_OK) return st;
+    Carver w(ctx->ws.base);
+    Scalars *sc = w.take<Scalars>(1);
+    unsigned long long *hist = w.take<unsigned long long>(D);
+    unsigned long long *cb = w.take<unsigned long long>(nch + 2);
+    unsigned *ce = w.take<unsigned>(nch + 2);
+    void *hb = w.take<char>(huff_scratch_bytes(D));
+    CK(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
+    CK(cudaMemsetAsync(hist, 0, 8ULL * D, s));
+    CK(launch_histogram(d_symbols, N, D, hist, &sc->status, s));
+    HuffScratch hs;
+    huff_scratch_carve(hb, D, sc, &hs);
+    CK(launch_codebook(hist, D, hs, s));
+    EncodeArgs ea;
+    memset(&ea, 0, sizeof(ea));
+    ea.sym = d_symbols; ea.N = N; ea.D = D; ea.K = K; ea.len = hs.len; ea.code = hs.code;
+    ea.chunk_bits = cb; ea.chunk_esc = ce; ea.sc = sc;
+    ea.chunk_out = (unsigned long long *)d_chunk_bits;
+    ea.words_out = d_words;
+    ea.words_cap = words_capacity;
+    CK(launch_encode(ea, s));
+    CK(cudaMemcpyAsync(d_lengths, hs.len, D, cudaMemcpyDeviceToDevice, s));
+    Scalars *hsc = (Scalars *)ctx->host_pinned;
+    CK(cudaMemcpyAsync(hsc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hsc->status) return map_device_status(hsc->status);
+    *total_bits = hsc->total_bits;
+    return HPDR_OK;
+}
+
+hpdr_status hpdr_huffman_decode(hpdr_ctx *ctx, const uint32_t *d_words, uint64_t total_bits,
+                                const uint64_t *d_chunk_bits, uint64_t N, uint32_t D, uint32_t K,
+                                const uint8_t *d_lengths, uint16_t *d_symbols, void *stream)
+{
+    hpdr_config cfg = {D, K};
+    unsigned Dv, Kv;
+    if (!ctx || !d_words || !d_chunk_bits || !d_lengths || !d_symbols || N == 0 ||
+        !valid_cfg(&cfg, Dv, Kv) || ((uintptr_t)d_symbols & 15))
+        return HPDR_ERR_ARG;
+    DevGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Carver c(nullptr);
+    c.take<Scalars>(1); c.take<char>(huff_scratch_bytes(D));
+    hpdr_status st = ensure_workspace(ctx, c.used + 256);
+    if (st != HPDR_OK) return st;
+    Carver w(ctx->ws.base);
+    Scalars *sc = w.take<Scalars>(1);
+    void *hb = w.take<char>(huff_scratch_bytes(D));
+    CK(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
+    HuffScratch hs;
+    huff_scratch_carve(hb, D, sc, &hs);
+    CK(cudaMemcpyAsync(hs.len, d_lengths, D, cudaMemcpyDeviceToDevice, s));
+    CK(launch_decode_tables(hs.len, D, hs, s));
+    DecodeArgs da;
+    da.words = d_words; da.nwords = (total_bits + 31) / 32;
+    da.chunk = (const unsigned long long *)d_chunk_bits;
+    da.N = N; da.K = K; da.sym = d_symbols; da.total_bits = total_bits;
+    Scalars *hsc = (Scalars *)ctx->host_pinned;
+    CK(launch_decode(da, hs, s));
+    CK(cudaMemcpyAsync(hsc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hsc->status) return map_device_status(hsc->status);
+    return HPDR_OK;
+}
+
+hpdr_status hpdr_recompose_adjoint(hpdr_ctx *ctx, const void *d_grad_u, void *d_grad_coef,
+                                   hpdr_dtype dtype, int ndim, const size_t *dims, void *stream)
+{
+    (void)ctx; (void)d_grad_u; (void)d_grad_coef; (void)dtype; (void)ndim; (void)dims; (void)stream;
+    return HPDR_ERR_ARG;
+}
+
+hpdr_status hpdr_decompose_adjoint(hpdr_ctx *ctx, const void *d_grad_coef, void *d_grad_u,
+                                   hpdr_dtype dtype, int ndim, const size_t *dims, void *stream)
+{
+    (void)ctx; (void)d_grad_coef; (void)d_grad_u; (void)dtype; (void)ndim; (void)dims; (void)stream;
+    return HPDR_ERR_ARG;
+}
+
+const char *hpdr_status_string(hpdr_status st)
+{
+    switch (st) {
+    case HPDR_OK: return "ok";
+    case HPDR_ERR_ARG: return "invalid argument";
+    case HPDR_ERR_CUDA: return "CUDA error";
+    case HPDR_ERR_CAPACITY: return "output buffer too small";
+    case HPDR_ERR_FORMAT: return "malformed container";
+    case HPDR_ERR_TIMEOUT: return "device wait timed out";
+    case HPDR_ERR_NOMEM: return "device allocation failed";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

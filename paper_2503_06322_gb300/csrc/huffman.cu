@@ -1,0 +1,826 @@
+// huffman.cu -- Huffman stage of Sec. IV-B (Alg. 2) for sm_103a: SortByKey of
+// the frequencies, filter of zero frequencies, code lengths (tree_build),
+// canonical codewords, encode + serialize, and the chunk-parallel decoder.
+//
+// Code lengths follow the two-queue Huffman rule (leaves sorted by
+// (frequency, symbol); on equal weights a leaf is picked before a merged
+// node).  It is computed here in rounds instead of one pick at a time: if w
+// is the smallest weight left, every node created from now on weighs at least
+// 2w, so all leaves and merged nodes of weight <= 2w are picked next, in
+// merged order, before any new node; a round pairs an even number of them in
+// parallel.  This yields exactly the picks of the sequential rule.
+#include <cstdio>
+#include "huffman.cuh"
+
+namespace hpdr {
+namespace {
+
+constexpr int kRankBlocks = 152 * 2;
+constexpr int kSmemKeys = 12288;     // keys one block stages in shared memory (96 KB)
+constexpr int kSmemCodes = 8192;     // codewords staged by the encoder
+constexpr int kEncThreads = 128;
+
+__device__ __forceinline__ unsigned warp_sum(unsigned v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// keys of the present symbols, in increasing symbol order:
+//   from a histogram: (frequency << 16) | s   (frequency > 0)
+//   from lengths:     (length << 16) | s      (length > 0)
+__global__ void __launch_bounds__(1024)
+compact_kernel(const unsigned long long *hist, const uint8_t *len, unsigned D,
+               unsigned long long *keys, unsigned *nsym, unsigned *s_lo, unsigned *s_hi)
+{
+    __shared__ unsigned wcnt[32], wpre[32];
+    __shared__ unsigned base, lo, hi;
+    const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) { base = 0; lo = 0xFFFFFFFFu; hi = 0; }
+    __syncthreads();
+    for (unsigned t0 = 0; t0 < D; t0 += 1024) {
+        unsigned s = t0 + threadIdx.x;
+        unsigned long long f = 0;
+        if (s < D) f = hist ? hist[s] : (unsigned long long)len[s];
+        bool p = f != 0;
+        unsigned ball = __ballot_sync(0xffffffffu, p);
+        if (lane == 0) wcnt[w] = __popc(ball);
+        __syncthreads();
+        if (w == 0) {
+            unsigned v = wcnt[lane], x = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+                if ((int)lane >= o) x += y;
+            }
+            wpre[lane] = x - v;
+        }
+        __syncthreads();
+        if (p) {
+            keys[base + wpre[w] + __popc(ball & ((1u << lane) - 1))] = (f << 16) | s;
+            atomicMin(&lo, s);
+            atomicMax(&hi, s);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) base += wpre[31] + wcnt[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *nsym = base;
+        if (s_lo) { *s_lo = base ? lo : 0; *s_hi = base ? hi : 0; }
+    }
+}
+
+// rank of every key among the n (unique) keys; scatter into sorted[] and/or rank[]
+__global__ void __launch_bounds__(256)
+rank_kernel(const unsigned long long *keys, const unsigned *nsym, unsigned long long *sorted,
+            unsigned *rank_out)
+{
+    extern __shared__ unsigned long long sk[];
+    const unsigned n = *nsym;
+    const unsigned long long *K = keys;
+    if (n <= (unsigned)kSmemKeys) {
+        for (unsigned i = threadIdx.x; i < n; i += blockDim.x) sk[i] = keys[i];
+        __syncthreads();
+        K = sk;
+    }
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned wg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const unsigned nw = gridDim.x * (blockDim.x >> 5);
+    for (unsigned i = wg; i < n; i += nw) {
+        const unsigned long long ki = K[i];
+        unsigned c = 0;
+        for (unsigned j = lane; j < n; j += 32) c += K[j] < ki ? 1u : 0u;
+        c = warp_sum(c);
+        if (lane == 0) {
+            if (sorted) sorted[c] = ki;
+            if (rank_out) rank_out[i] = c;
+        }
+    }
+}
+
+// all threads of a block take the same decision even if another block
+// raises the status meanwhile
+__device__ bool block_skip(const unsigned *status)
+{
+    __shared__ int flag;
+    __syncthreads();
+    if (threadIdx.x == 0) flag = *((volatile const unsigned *)status) != 0;
+    __syncthreads();
+    return flag != 0;
+}
+
+__device__ unsigned count_le(const unsigned long long *a, unsigned n, unsigned long long v)
+{
+    unsigned lo = 0, hi = n;
+    while (lo < hi) { unsigned m = (lo + hi) >> 1; if (a[m] <= v) lo = m + 1; else hi = m; }
+    return lo;
+}
+__device__ unsigned count_lt(const unsigned long long *a, unsigned n, unsigned long long v)
+{
+    unsigned lo = 0, hi = n;
+    while (lo < hi) { unsigned m = (lo + hi) >> 1; if (a[m] < v) lo = m + 1; else hi = m; }
+    return lo;
+}
+
+__device__ void length_tables(HuffScratch &hs, unsigned *cnt)
+{
+    // first canonical code and start index of every length
+    unsigned long long c = 0;
+    int prev = -1;
+    unsigned st = 0;
+    bool ok = true;
+    for (int L = 1; L <= kMaxCodeLen; L++) {
+        hs.start[L] = st;
+        hs.count[L] = cnt[L];
+        if (cnt[L]) {
+            if (prev >= 0) c <<= (L - prev);
+            hs.first[L] = c;
+            c += cnt[L];
+            if (c > (1ULL << L)) ok = false;   // not a prefix code
+            prev = L;
+            st += cnt[L];
+        } else {
+            hs.first[L] = 0;
+        }
+    }
+    hs.count[0] = 0;
+    if (!ok) atomicExch(hs.status, (unsigned)DS_FORMAT);
+}
+
+// code lengths from the frequency-sorted leaves, one block
+__global__ void __launch_bounds__(1024) merge_kernel(HuffScratch hs, unsigned D)
+{
+    extern __shared__ unsigned long long sm[];
+    __shared__ unsigned ia, ib, nb, ka, kb, cnt[kMaxCodeLen + 2];
+    __shared__ int done;
+    const unsigned n = *hs.nsym;
+    const unsigned tid = threadIdx.x;
+    for (unsigned s = tid; s < D; s += blockDim.x) hs.len[s] = 0;
+    for (unsigned L = tid; L < kMaxCodeLen + 2; L += blockDim.x) cnt[L] = 0;
+    if (n == 0) return;
+    if (n == 1) {
+        __syncthreads();
+        if (tid == 0) {
+            unsigned s = (unsigned)(hs.sorted[0] & 0xFFFFu);
+            hs.len[s] = 1;
+            hs.keys2[0] = (1ULL << 16) | s;
+            cnt[1] = 1;
+            length_tables(hs, cnt);
+        }
+        return;
+    }
+    const bool insm = n <= (unsigned)kSmemKeys;
+    unsigned long long *leafw = insm ? sm : hs.leafw;
+    unsigned long long *intw = insm ? sm + n : hs.intw;
+    for (unsigned i = tid; i < n; i += blockDim.x) {
+        leafw[i] = hs.sorted[i] >> 16;
+        intw[i] = 0;
+    }
+    if (tid == 0) { ia = ib = nb = 0; done = 0; }
+    __syncthreads();
+    const unsigned long long INF = ~0ULL;
+    while (true) {
+        if (tid == 0) {
+            unsigned remA = n - ia, remB = nb - ib;
+            if (remA + remB <= 1) {
+                done = 1;
+            } else {
+                unsigned long long wa = remA ? leafw[ia] : INF, wb = remB ? intw[ib] : INF;
+                unsigned long long wmin = wa < wb ? wa : wb;
+                unsigned long long thr = wmin > (INF >> 1) ? INF : 2 * wmin;
+                unsigned a = count_le(leafw + ia, remA, thr), b = count_le(intw + ib, remB, thr);
+                if (a + b < 2) {
+                    a = b = 0;
+                    for (int t = 0; t < 2; t++) {
+                        bool la = (a < remA) && (b >= remB || leafw[ia + a] <= intw[ib + b]);
+                        if (la) a++; else b++;
+                    }
+                } else if ((a + b) & 1) {
+                    if (a == 0) b--;
+                    else if (b == 0) a--;
+                    else if (intw[ib + b - 1] >= leafw[ia + a - 1]) b--;
+                    else a--;
+                }
+                ka = a;
+                kb = b;
+            }
+        }
+        __syncthreads();
+        if (done) break;
+        const unsigned a = ka, b = kb;
+        for (unsigned i = tid; i < a + b; i += blockDim.x) {
+            unsigned long long w;
+            unsigned q, node;
+            if (i < a) {
+                w = leafw[ia + i];
+                q = i + count_lt(intw + ib, b, w);       // equal weights: the leaf first
+                node = ia + i;
+            } else {
+                unsigned j = i - a;
+                w = intw[ib + j];
+                q = j + count_le(leafw + ia, a, w);
+                node = n + ib + j;
+            }
+            unsigned t = nb + (q >> 1);
+            atomicAdd(&intw[t], w);
+            hs.parent[node] = n + t;
+        }
+        __syncthreads();
+        if (tid == 0) { ia += a; ib += b; nb += (a + b) >> 1; }
+        __syncthreads();
+    }
+    // depth of every node by pointer jumping (parents have larger indices)
+    const unsigned total = 2 * n - 1, root = total - 1;
+    unsigned *A0 = hs.anc, *A1 = hs.anc + total, *D0 = hs.dep, *D1 = hs.dep + total;
+    for (unsigned i = tid; i < total; i += blockDim.x) {
+        A0[i] = (i == root) ? root : hs.parent[i];
+        D0[i] = (i == root) ? 0u : 1u;
+    }
+    __syncthreads();
+    for (int step = 0; step < 7; step++) {
+        for (unsigned i = tid; i < total; i += blockDim.x) {
+            unsigned a = A0[i];
+            D1[i] = D0[i] + D0[a];
+            A1[i] = A0[a];
+        }
+        __syncthreads();
+        unsigned *t = A0; A0 = A1; A1 = t;
+        t = D0; D0 = D1; D1 = t;
+    }
+    for (unsigned i = tid; i < n; i += blockDim.x) {
+        unsigned L = D0[i];
+        if (A0[i] != root || L > (unsigned)kMaxCodeLen || L == 0) {
+            atomicExch(hs.status, (unsigned)DS_LENGTH);
+            L = kMaxCodeLen;
+        }
+        unsigned s = (unsigned)(hs.sorted[i] & 0xFFFFu);
+        hs.len[s] = (uint8_t)L;
+        hs.keys2[i] = ((unsigned long long)L << 16) | s;
+        atomicAdd(&cnt[L], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) length_tables(hs, cnt);
+}
+
+// decoder side: per-length counts from the present (length, symbol) keys
+__global__ void __launch_bounds__(1024) length_count_kernel(HuffScratch hs)
+{
+    __shared__ unsigned cnt[kMaxCodeLen + 2];
+    const unsigned n = *hs.nsym;
+    for (unsigned L = threadIdx.x; L < kMaxCodeLen + 2; L += blockDim.x) cnt[L] = 0;
+    __syncthreads();
+    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+        unsigned L = (unsigned)(hs.keys2[i] >> 16);
+        if (L > (unsigned)kMaxCodeLen) { atomicExch(hs.status, (unsigned)DS_FORMAT); L = kMaxCodeLen; }
+        atomicAdd(&cnt[L], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (n == 0) atomicExch(hs.status, (unsigned)DS_FORMAT);
+        length_tables(hs, cnt);
+    }
+}
+
+// canonical codeword of every present symbol and the (length, symbol) order
+__global__ void __launch_bounds__(256) assign_kernel(HuffScratch hs)
+{
+    const unsigned n = *hs.nsym;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        unsigned long long k = hs.keys2[i];
+        unsigned s = (unsigned)(k & 0xFFFFu), L = (unsigned)(k >> 16);
+        unsigned r = hs.rank[i];
+        hs.code[s] = hs.first[L] + (r - hs.start[L]);
+        hs.sorted_sym[r] = (uint16_t)s;
+    }
+}
+
+__global__ void __launch_bounds__(256) lut_kernel(HuffScratch hs)
+{
+    const unsigned n = *hs.nsym;
+    if (*hs.status) return;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        unsigned long long k = hs.keys2[i];
+        unsigned s = (unsigned)(k & 0xFFFFu), L = (unsigned)(k >> 16);
+        if (L == 0 || L > (unsigned)kLutBits) continue;
+        unsigned long long c = hs.code[s];
+        unsigned base = (unsigned)(c << (kLutBits - L));
+        unsigned span = 1u << (kLutBits - L);
+        for (unsigned e = 0; e < span; e++) hs.lut[base + e] = s | (L << 16);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Encoder
+
+struct Layout {
+    unsigned long long off_len, off_chunk, off_out, off_bits, total;
+};
+__device__ __forceinline__ Layout container_layout(int L, unsigned s_lo, unsigned s_hi,
+                                                   unsigned long long nch, unsigned long long nout,
+                                                   unsigned long long bits)
+{
+    Layout y;
+    y.off_len = a16(128 + 8ULL * (L + 1));
+    y.off_chunk = a16(y.off_len + (s_hi - s_lo + 1));
+    y.off_out = a16(y.off_chunk + 8 * nch);
+    y.off_bits = a16(y.off_out + 16 * nout);
+    y.total = y.off_bits + 4 * ((bits + 31) / 32);
+    return y;
+}
+
+__global__ void __launch_bounds__(256) enc_count_kernel(EncodeArgs a)
+{
+    extern __shared__ uint8_t slen[];
+    if (block_skip(&a.sc->status)) return;
+    for (unsigned i = threadIdx.x; i < a.D; i += blockDim.x) slen[i] = a.len[i];
+    __syncthreads();
+    const unsigned long long nch = (a.N + a.K - 1) / a.K;
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned long long wg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long c = wg; c < nch; c += nw) {
+        const unsigned long long beg = c * a.K;
+        const unsigned long long end = beg + a.K < a.N ? beg + a.K : a.N;
+        unsigned long long bits = 0;
+        unsigned esc = 0;
+        if (end - beg == a.K) {
+            const uint4 *v = reinterpret_cast<const uint4 *>(a.sym + beg);
+            for (unsigned i = lane; i < a.K / 8; i += 32) {
+                uint4 x = v[i];
+                const uint16_t *e = reinterpret_cast<const uint16_t *>(&x);
+#pragma unroll
+                for (int k = 0; k < 8; k++) { bits += slen[e[k]]; esc += e[k] == 0; }
+            }
+        } else {
+            for (unsigned long long i = beg + lane; i < end; i += 32) {
+                uint16_t s = a.sym[i];
+                bits += slen[s];
+                esc += s == 0;
+            }
+        }
+        bits = warp_sum64(bits);
+        esc = warp_sum(esc);
+        if (lane == 0) { a.chunk_bits[c] = bits; a.chunk_esc[c] = esc; }
+    }
+}
+
+// exclusive scan of the per-chunk bit counts and escapes, layout and capacity
+__global__ void __launch_bounds__(1024) enc_scan_kernel(EncodeArgs a)
+{
+    __shared__ unsigned long long sb[1024];
+    __shared__ unsigned se[1024];
+    __shared__ int ok;
+    __shared__ unsigned long long bits_total, wbase;
+    __shared__ uint32_t *words;
+    if (block_skip(&a.sc->status)) return;
+    const unsigned long long nch = (a.N + a.K - 1) / a.K;
+    const unsigned long long seg = (nch + 1023) / 1024;
+    const unsigned long long b0 = threadIdx.x * seg;
+    const unsigned long long b1 = b0 + seg < nch ? b0 + seg : nch;
+    unsigned long long bs = 0;
+    unsigned es = 0;
+    for (unsigned long long c = b0; c < b1; c++) { bs += a.chunk_bits[c]; es += a.chunk_esc[c]; }
+    sb[threadIdx.x] = bs;
+    se[threadIdx.x] = es;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long x = 0;
+        unsigned y = 0;
+        for (int i = 0; i < 1024; i++) {
+            unsigned long long t = sb[i];
+            unsigned u = se[i];
+            sb[i] = x;
+            se[i] = y;
+            x += t;
+            y += u;
+        }
+        bits_total = x;
+        ok = 1;
+        if (a.container) {
+            if ((unsigned long long)y != a.sc->n_out) atomicExch(&a.sc->status, (unsigned)DS_FORMAT);
+            Layout lay = container_layout(a.L, a.sc->s_lo, a.sc->s_hi, nch, a.sc->n_out, x);
+            if (lay.total > a.capacity) { ok = 0; atomicExch(&a.sc->status, (unsigned)DS_CAPACITY); }
+            words = reinterpret_cast<uint32_t *>(a.container + lay.off_bits);
+            a.sc->out_bytes = lay.total;
+            wbase = lay.off_chunk;
+        } else {
+            if ((x + 31) / 32 > a.words_cap) { ok = 0; atomicExch(&a.sc->status, (unsigned)DS_CAPACITY); }
+            words = a.words_out;
+            wbase = 0;
+        }
+        a.sc->total_bits = x;
+    }
+    __syncthreads();
+    if (!ok) return;
+    unsigned long long *ctab = a.container ? reinterpret_cast<unsigned long long *>(a.container + wbase)
+                                           : a.chunk_out;
+    unsigned long long x = sb[threadIdx.x];
+    unsigned y = se[threadIdx.x];
+    for (unsigned long long c = b0; c < b1; c++) {
+        unsigned long long t = a.chunk_bits[c];
+        unsigned u = a.chunk_esc[c];
+        a.chunk_bits[c] = x;
+        a.chunk_esc[c] = y;
+        ctab[c] = x;
+        words[x >> 5] = 0u;   // first word of the chunk (shared with the previous one)
+        x += t;
+        y += u;
+    }
+    if (threadIdx.x == 0 && (bits_total & 31)) words[bits_total >> 5] = 0u;
+    if (threadIdx.x == 0) { a.chunk_bits[nch] = bits_total; }
+}
+
+__global__ void __launch_bounds__(kEncThreads) enc_write_kernel(EncodeArgs a)
+{
+    extern __shared__ unsigned long long esm[];
+    __shared__ unsigned long long tb[kEncThreads];
+    __shared__ unsigned te[kEncThreads];
+    if (block_skip(&a.sc->status)) return;
+    const bool code_sm = a.D <= (unsigned)kSmemCodes;
+    unsigned long long *scode = esm;                                   // [D] if code_sm
+    uint8_t *slen = reinterpret_cast<uint8_t *>(esm + (code_sm ? a.D : 0));
+    uint32_t *sw = reinterpret_cast<uint32_t *>(slen + ((a.D + 15) & ~15u));
+    for (unsigned i = threadIdx.x; i < a.D; i += blockDim.x) {
+        slen[i] = a.len[i];
+        if (code_sm) scode[i] = a.code[i];
+    }
+    __syncthreads();
+    const unsigned long long *codes = code_sm ? scode : a.code;
+    const unsigned long long nch = (a.N + a.K - 1) / a.K;
+    const unsigned spt = a.K / kEncThreads;
+    const unsigned long long nout = a.container ? a.sc->n_out : 0;
+    Layout lay;
+    uint32_t *words;
+    unsigned long long *oidx = nullptr;
+    if (a.container) {
+        lay = container_layout(a.L, a.sc->s_lo, a.sc->s_hi, nch, nout, a.sc->total_bits);
+        words = reinterpret_cast<uint32_t *>(a.container + lay.off_bits);
+        oidx = reinterpret_cast<unsigned long long *>(a.container + lay.off_out);
+    } else {
+        words = a.words_out;
+    }
+    for (unsigned long long c = blockIdx.x; c < nch; c += gridDim.x) {
+        const unsigned long long beg = c * a.K;
+        const unsigned long long end = beg + a.K < a.N ? beg + a.K : a.N;
+        unsigned long long m0 = beg + (unsigned long long)threadIdx.x * spt;
+        unsigned long long m1 = m0 + spt;
+        if (m0 > end) m0 = end;
+        if (m1 > end) m1 = end;
+        unsigned long long mb = 0;
+        unsigned me = 0;
+        for (unsigned long long i = m0; i < m1; i++) { uint16_t s = a.sym[i]; mb += slen[s]; me += s == 0; }
+        tb[threadIdx.x] = mb;
+        te[threadIdx.x] = me;
+        __syncthreads();
+        if (threadIdx.x < 32) {   // exclusive scan of 128 entries by one warp
+            unsigned long long v[4];
+            unsigned u[4];
+            unsigned long long s = 0;
+            unsigned su = 0;
+            for (int k = 0; k < 4; k++) { v[k] = tb[threadIdx.x * 4 + k]; u[k] = te[threadIdx.x * 4 + k]; s += v[k]; su += u[k]; }
+            unsigned long long x = s;
+            unsigned xu = su;
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+                unsigned yu = __shfl_up_sync(0xffffffffu, xu, o);
+                if ((int)threadIdx.x >= o) { x += y; xu += yu; }
+            }
+            x -= s;
+            xu -= su;
+            for (int k = 0; k < 4; k++) {
+                tb[threadIdx.x * 4 + k] = x; x += v[k];
+                te[threadIdx.x * 4 + k] = xu; xu += u[k];
+            }
+        }
+        __syncthreads();
+        const unsigned long long start = a.chunk_bits[c];
+        const unsigned long long cend = a.chunk_bits[c + 1];
+        const unsigned so = (unsigned)(start & 31);
+        const unsigned long long wstart = start >> 5;
+        const unsigned nwl = (unsigned)((so + (cend - start) + 31) >> 5);
+        for (unsigned i = threadIdx.x; i < nwl + 2; i += blockDim.x) sw[i] = 0u;
+        __syncthreads();
+        unsigned long long b = so + tb[threadIdx.x];
+        unsigned ebase = a.chunk_esc[c] + te[threadIdx.x];
+        for (unsigned long long i = m0; i < m1; i++) {
+            uint16_t s = a.sym[i];
+            unsigned L = slen[s];
+            unsigned long long cw = codes[s];
+            unsigned w = (unsigned)(b >> 5), off = (unsigned)(b & 31);
+            unsigned long long hi64 = (off + L <= 64) ? (cw << (64 - off - L)) : (cw >> (off + L - 64));
+            atomicOr(&sw[w], (uint32_t)(hi64 >> 32));
+            uint32_t x1 = (uint32_t)hi64;
+            if (x1) atomicOr(&sw[w + 1], x1);
+            if (off + L > 64) atomicOr(&sw[w + 2], (uint32_t)(cw << (96 - off - L)));
+            b += L;
+            if (oidx && s == 0) oidx[ebase++] = i;
+        }
+        __syncthreads();
+        const bool tail_shared = ((so + (cend - start)) & 31) != 0;
+        for (unsigned i = threadIdx.x; i < nwl; i += blockDim.x) {
+            uint32_t v = sw[i];
+            if (i == 0 || (i == nwl - 1 && tail_shared)) { if (v) atomicOr(&words[wstart + i], v); }
+            else words[wstart + i] = v;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) outlier_place_kernel(EncodeArgs a)
+{
+    if (a.sc->status || !a.container) return;
+    const unsigned long long nout = a.sc->n_out;
+    const unsigned long long nch = (a.N + a.K - 1) / a.K;
+    Layout lay = container_layout(a.L, a.sc->s_lo, a.sc->s_hi, nch, nout, a.sc->total_bits);
+    const unsigned long long *sidx = reinterpret_cast<const unsigned long long *>(a.container + lay.off_out);
+    long long *sk = reinterpret_cast<long long *>(a.container + lay.off_out + 8 * nout);
+    for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; e < nout;
+         e += (unsigned long long)gridDim.x * blockDim.x) {
+        unsigned long long idx = a.oidx_unordered[e];
+        unsigned long long lo = 0, hi = nout;
+        while (lo < hi) { unsigned long long m = (lo + hi) >> 1; if (sidx[m] < idx) lo = m + 1; else hi = m; }
+        if (lo < nout && sidx[lo] == idx) sk[lo] = a.ok_unordered[e];
+        else atomicExch(&a.sc->status, (unsigned)DS_FORMAT);
+    }
+}
+
+__device__ uint32_t crc32_bytes(const uint8_t *p, int n)
+{
+    uint32_t c = 0xFFFFFFFFu;
+    for (int i = 0; i < n; i++) {
+        c ^= p[i];
+        for (int b = 0; b < 8; b++) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
+    }
+    return c ^ 0xFFFFFFFFu;
+}
+
+__device__ __forceinline__ void put32(uint8_t *p, uint32_t v) { for (int i = 0; i < 4; i++) p[i] = (uint8_t)(v >> (8 * i)); }
+__device__ __forceinline__ void put64(uint8_t *p, unsigned long long v) { for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i)); }
+__device__ __forceinline__ void putd(uint8_t *p, double v) { put64(p, (unsigned long long)__double_as_longlong(v)); }
+
+__global__ void __launch_bounds__(256)
+header_kernel(HeaderArgs h, const uint8_t *len, Scalars *sc, uint8_t *out)
+{
+    __shared__ uint8_t hdr[128];
+    if (block_skip(&sc->status)) return;
+    const unsigned long long nch = (h.N + h.K - 1) / h.K;
+    Layout lay = container_layout(h.L, sc->s_lo, sc->s_hi, nch, sc->n_out, sc->total_bits);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 128; i++) hdr[i] = 0;
+        hdr[0] = 'H'; hdr[1] = 'P'; hdr[2] = 'D'; hdr[3] = 'R';
+        put32(hdr + 4, 1);
+        put32(hdr + 8, (uint32_t)h.dtype);
+        put32(hdr + 12, (uint32_t)h.ndim);
+        for (int k = 0; k < 3; k++) put64(hdr + 16 + 8 * k, h.dims[k]);
+        put32(hdr + 40, (uint32_t)h.L);
+        put32(hdr + 44, (uint32_t)h.mode);
+        put32(hdr + 48, (uint32_t)h.tol_kind);
+        put32(hdr + 52, h.D);
+        put32(hdr + 56, h.K);
+        put32(hdr + 60, sc->s_lo);
+        putd(hdr + 64, h.tol);
+        putd(hdr + 72, sc->tau_abs);
+        putd(hdr + 80, sc->maxabs);
+        putd(hdr + 88, sqrt(sc->sumsq / (double)h.N));
+        put64(hdr + 96, h.N);
+        put64(hdr + 104, sc->n_out);
+        put64(hdr + 112, sc->total_bits);
+        put32(hdr + 120, sc->s_hi);
+        put32(hdr + 124, crc32_bytes(hdr, 124));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 128; i += blockDim.x) out[i] = hdr[i];
+    const unsigned long long qend = 128 + 8ULL * (h.L + 1);
+    for (int l = threadIdx.x; l <= h.L; l += blockDim.x) putd(out + 128 + 8 * l, sc->q[l]);
+    for (unsigned long long i = qend + threadIdx.x; i < lay.off_len; i += blockDim.x) out[i] = 0;
+    const unsigned nlen = sc->s_hi - sc->s_lo + 1;
+    for (unsigned i = threadIdx.x; i < nlen; i += blockDim.x) out[lay.off_len + i] = len[sc->s_lo + i];
+    for (unsigned long long i = lay.off_len + nlen + threadIdx.x; i < lay.off_chunk; i += blockDim.x) out[i] = 0;
+    for (unsigned long long i = lay.off_chunk + 8 * nch + threadIdx.x; i < lay.off_out; i += blockDim.x) out[i] = 0;
+    for (unsigned long long i = lay.off_out + 16 * sc->n_out + threadIdx.x; i < lay.off_bits; i += blockDim.x) out[i] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Decoder: one thread per chunk, canonical decode with a 12-bit table and a
+// per-length fallback for longer codewords.
+
+__device__ __forceinline__ uint32_t ldw(const uint32_t *w, unsigned long long i, unsigned long long n)
+{
+    return i < n ? __ldg(w + i) : 0u;
+}
+
+__global__ void __launch_bounds__(256) decode_kernel(DecodeArgs a, HuffScratch hs)
+{
+    __shared__ uint32_t lut[1 << kLutBits];
+    __shared__ unsigned long long sfirst[kMaxCodeLen + 1];
+    __shared__ unsigned scount[kMaxCodeLen + 1], sstart[kMaxCodeLen + 1];
+    if (block_skip(hs.status)) return;
+    for (int i = threadIdx.x; i < (1 << kLutBits); i += blockDim.x) lut[i] = hs.lut[i];
+    for (int i = threadIdx.x; i <= kMaxCodeLen; i += blockDim.x) {
+        sfirst[i] = hs.first[i];
+        scount[i] = hs.count[i];
+        sstart[i] = hs.start[i];
+    }
+    __syncthreads();
+    const unsigned long long nch = (a.N + a.K - 1) / a.K;
+    for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < nch;
+         c += (unsigned long long)gridDim.x * blockDim.x) {
+        unsigned long long pos = a.chunk[c];
+        const unsigned long long expect = (c + 1 < nch) ? a.chunk[c + 1] : a.total_bits;
+        if (pos > a.total_bits || expect > a.total_bits || pos > expect) {
+            atomicExch(hs.status, (unsigned)DS_FORMAT);
+            continue;
+        }
+        unsigned long long wi = pos >> 5;
+        unsigned sh = (unsigned)(pos & 31);
+        uint32_t w0 = ldw(a.words, wi, a.nwords), w1 = ldw(a.words, wi + 1, a.nwords),
+                 w2 = ldw(a.words, wi + 2, a.nwords);
+        const unsigned long long beg = c * a.K;
+        const unsigned long long end = beg + a.K < a.N ? beg + a.K : a.N;
+        uint16_t buf[8];
+        bool bad = false;
+        for (unsigned long long i = beg; i < end; i++) {
+            unsigned long long win = (((unsigned long long)w0 << 32) | w1) << sh;
+            if (sh) win |= (unsigned long long)(w2 >> (32 - sh));
+            uint32_t e = lut[win >> (64 - kLutBits)];
+            unsigned L = e >> 16, s = e & 0xFFFFu;
+            if (L == 0) {
+                for (L = kLutBits + 1; L <= (unsigned)kMaxCodeLen; L++) {
+                    unsigned long long v = win >> (64 - L);
+                    if (scount[L] && v >= sfirst[L] && v - sfirst[L] < scount[L]) {
+                        s = hs.sorted_sym[sstart[L] + (unsigned)(v - sfirst[L])];
+                        break;
+                    }
+                }
+                if (L > (unsigned)kMaxCodeLen) { bad = true; L = 1; s = 0; }
+            }
+            pos += L;
+            sh += L;
+            while (sh >= 32) { sh -= 32; w0 = w1; w1 = w2; wi++; w2 = ldw(a.words, wi + 2, a.nwords); }
+            buf[(i - beg) & 7] = (uint16_t)s;
+            if (((i - beg) & 7) == 7) {
+                uint4 v;
+                uint16_t *vp = reinterpret_cast<uint16_t *>(&v);
+#pragma unroll
+                for (int k = 0; k < 8; k++) vp[k] = buf[k];
+                *reinterpret_cast<uint4 *>(a.sym + (i - 7)) = v;
+            }
+        }
+        const unsigned long long tail = (end - beg) & 7;
+        for (unsigned long long k = 0; k < tail; k++) a.sym[end - tail + k] = buf[k];
+        if (bad || pos != expect) atomicExch(hs.status, (unsigned)DS_FORMAT);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+hist_kernel(const uint16_t *sym, unsigned long long N, unsigned D, unsigned long long *hist,
+            unsigned *status)
+{
+    extern __shared__ unsigned hsm[];
+    const bool sm = D <= 16384;
+    if (sm) for (unsigned i = threadIdx.x; i < D; i += blockDim.x) hsm[i] = 0;
+    __syncthreads();
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < N;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        unsigned s = sym[i];
+        if (s >= D) { atomicExch(status, (unsigned)DS_ARG); continue; }
+        if (sm) atomicAdd(&hsm[s], 1u); else atomicAdd(&hist[s], 1ULL);
+    }
+    __syncthreads();
+    if (sm)
+        for (unsigned i = threadIdx.x; i < D; i += blockDim.x)
+            if (hsm[i]) atomicAdd(&hist[i], (unsigned long long)hsm[i]);
+}
+
+bool g_attr_done = false;
+cudaError_t set_attrs()
+{
+    if (g_attr_done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemKeys * 8);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemKeys * 16);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(enc_write_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(enc_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+    if (e == cudaSuccess) g_attr_done = true;
+    return e;
+}
+
+}  // namespace
+
+size_t huff_scratch_bytes(unsigned int D)
+{
+    size_t d = D;
+    size_t b = 0;
+    auto add = [&](size_t x) { b += (x + 255) & ~size_t(255); };
+    add(8 * d); add(8 * d); add(8 * d); add(4 * d);    // keys, keys2, sorted, rank
+    add(4 * 2 * d); add(4 * 4 * d); add(4 * 4 * d);    // parent, anc, dep
+    add(8 * d); add(8 * d);                            // leafw, intw
+    add(4); add(8 * 64); add(4 * 64); add(4 * 64);     // nsym, first, count, start
+    add(d); add(8 * d); add(2 * d); add(4u << kLutBits);
+    return b;
+}
+
+void huff_scratch_carve(void *base, unsigned int D, Scalars *sc, HuffScratch *hs)
+{
+    char *p = (char *)base;
+    size_t d = D;
+    auto take = [&](size_t x) { char *r = p; p += (x + 255) & ~size_t(255); return (void *)r; };
+    hs->keys = (unsigned long long *)take(8 * d);
+    hs->keys2 = (unsigned long long *)take(8 * d);
+    hs->sorted = (unsigned long long *)take(8 * d);
+    hs->rank = (unsigned *)take(4 * d);
+    hs->parent = (unsigned *)take(4 * 2 * d);
+    hs->anc = (unsigned *)take(4 * 4 * d);
+    hs->dep = (unsigned *)take(4 * 4 * d);
+    hs->leafw = (unsigned long long *)take(8 * d);
+    hs->intw = (unsigned long long *)take(8 * d);
+    hs->nsym = (unsigned *)take(4);
+    hs->first = (unsigned long long *)take(8 * 64);
+    hs->count = (unsigned *)take(4 * 64);
+    hs->start = (unsigned *)take(4 * 64);
+    hs->len = (uint8_t *)take(d);
+    hs->code = (unsigned long long *)take(8 * d);
+    hs->sorted_sym = (uint16_t *)take(2 * d);
+    hs->lut = (uint32_t *)take(4u << kLutBits);
+    hs->status = &sc->status;
+    hs->s_lo = &sc->s_lo;
+    hs->s_hi = &sc->s_hi;
+}
+
+cudaError_t launch_codebook(const unsigned long long *hist, unsigned int D, const HuffScratch &hs,
+                            cudaStream_t s)
+{
+    cudaError_t e = set_attrs();
+    if (e != cudaSuccess) return e;
+    compact_kernel<<<1, 1024, 0, s>>>(hist, nullptr, D, hs.keys, hs.nsym, hs.s_lo, hs.s_hi);
+    rank_kernel<<<kRankBlocks, 256, kSmemKeys * 8, s>>>(hs.keys, hs.nsym, hs.sorted, nullptr);
+    merge_kernel<<<1, 1024, kSmemKeys * 16, s>>>(hs, D);
+    rank_kernel<<<kRankBlocks, 256, kSmemKeys * 8, s>>>(hs.keys2, hs.nsym, nullptr, hs.rank);
+    assign_kernel<<<64, 256, 0, s>>>(hs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decode_tables(const uint8_t *len, unsigned int D, const HuffScratch &hs,
+                                 cudaStream_t s)
+{
+    cudaError_t e = set_attrs();
+    if (e != cudaSuccess) return e;
+    compact_kernel<<<1, 1024, 0, s>>>(nullptr, len, D, hs.keys2, hs.nsym, nullptr, nullptr);
+    length_count_kernel<<<1, 1024, 0, s>>>(hs);
+    rank_kernel<<<kRankBlocks, 256, kSmemKeys * 8, s>>>(hs.keys2, hs.nsym, nullptr, hs.rank);
+    assign_kernel<<<64, 256, 0, s>>>(hs);
+    e = cudaMemsetAsync(hs.lut, 0, 4u << kLutBits, s);
+    if (e != cudaSuccess) return e;
+    lut_kernel<<<64, 256, 0, s>>>(hs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encode(const EncodeArgs &a, cudaStream_t s)
+{
+    cudaError_t e = set_attrs();
+    if (e != cudaSuccess) return e;
+    enc_count_kernel<<<152 * 4, 256, a.D, s>>>(a);
+    enc_scan_kernel<<<1, 1024, 0, s>>>(a);
+    const bool code_sm = a.D <= (unsigned)kSmemCodes;
+    size_t words = ((size_t)a.K * kMaxCodeLen + 31) / 32 + 4;
+    size_t sm = (code_sm ? 8 * (size_t)a.D : 0) + ((a.D + 15) & ~15u) + 4 * words;
+    enc_write_kernel<<<152 * 4, kEncThreads, sm, s>>>(a);
+    if (a.container) outlier_place_kernel<<<152, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_header(const HeaderArgs &h, const uint8_t *len, Scalars *sc, uint8_t *container,
+                          cudaStream_t s)
+{
+    header_kernel<<<1, 256, 0, s>>>(h, len, sc, container);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_histogram(const uint16_t *sym, unsigned long long N, unsigned D,
+                             unsigned long long *hist, unsigned *status, cudaStream_t s)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    hist_kernel<<<152 * 4, 256, D <= 16384 ? D * 4 : 0, s>>>(sym, N, D, hist, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decode(const DecodeArgs &a, const HuffScratch &hs, cudaStream_t s)
+{
+    decode_kernel<<<152 * 4, 256, 0, s>>>(a, hs);
+    return cudaGetLastError();
+}
+
+}  // namespace hpdr

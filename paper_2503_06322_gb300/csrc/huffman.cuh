@@ -1,0 +1,92 @@
+// huffman.cuh -- launchers of the Huffman stage (huffman.cu), Sec. IV-B / Alg. 2.
+#pragma once
+#include "internal.cuh"
+
+namespace hpdr {
+
+constexpr int kLutBits = 12;
+constexpr int kMaxCodeLen = 63;
+
+// Device scratch of one codebook build (sizes for an alphabet of D symbols).
+struct HuffScratch {
+    unsigned long long *keys;     // [D]
+    unsigned long long *keys2;    // [D]
+    unsigned long long *sorted;   // [D]
+    unsigned int *rank;           // [D]
+    unsigned int *parent;         // [2D]
+    unsigned int *anc;            // [2*2D] ping-pong
+    unsigned int *dep;            // [2*2D] ping-pong
+    unsigned long long *leafw;    // [D]   (used when the alphabet is too large for shared memory)
+    unsigned long long *intw;     // [D]
+    unsigned int *nsym;           // [1]
+    unsigned long long *first;    // [64]
+    unsigned int *count;          // [64]
+    unsigned int *start;          // [64]
+    uint8_t *len;                 // [D]
+    unsigned long long *code;     // [D]
+    uint16_t *sorted_sym;         // [D]
+    uint32_t *lut;                // [1 << kLutBits]
+    unsigned int *status;         // -> Scalars::status
+    unsigned int *s_lo, *s_hi;    // -> Scalars
+};
+size_t huff_scratch_bytes(unsigned int D);
+void huff_scratch_carve(void *base, unsigned int D, Scalars *sc, HuffScratch *hs);
+
+// Codebook from a histogram hist[D] (two-queue lengths, canonical codes).
+cudaError_t launch_codebook(const unsigned long long *hist, unsigned int D, const HuffScratch &hs,
+                            cudaStream_t s);
+// Canonical tables + LUT from given lengths len[D] (decoder side).
+cudaError_t launch_decode_tables(const uint8_t *len, unsigned int D, const HuffScratch &hs,
+                                 cudaStream_t s);
+
+// Encoder.  Layout of the destination: chunk table at chunk_out, bitstream at
+// words (both device pointers, possibly inside a container whose offsets are
+// only known on the device: then pass the base and the Scalars-derived
+// offsets through ContainerLayout).
+struct EncodeArgs {
+    const uint16_t *sym;
+    unsigned long long N;
+    unsigned int D, K;
+    const uint8_t *len;
+    const unsigned long long *code;
+    unsigned long long *chunk_bits;   // ws [nch+1] totals then offsets
+    unsigned int *chunk_esc;          // ws [nch+1]
+    Scalars *sc;
+    // destination
+    uint8_t *container;               // if non-null: chunk table, outliers, bits go into the container
+    int L;                            // levels (container layout)
+    unsigned long long capacity;      // bytes available at container / words
+    unsigned long long *chunk_out;    // (container == null) chunk table destination
+    uint32_t *words_out;              // (container == null) bitstream destination
+    unsigned long long words_cap;
+    const unsigned long long *oidx_unordered;  // outliers from quantization
+    const long long *ok_unordered;
+};
+cudaError_t launch_encode(const EncodeArgs &a, cudaStream_t s);
+
+struct HeaderArgs {
+    int dtype, ndim, L, mode, tol_kind;
+    unsigned long long dims[3];
+    unsigned int D, K;
+    double tol;
+    unsigned long long N;
+};
+cudaError_t launch_header(const HeaderArgs &h, const uint8_t *len, Scalars *sc, uint8_t *container,
+                          cudaStream_t s);
+
+struct DecodeArgs {
+    const uint32_t *words;
+    unsigned long long nwords;
+    const unsigned long long *chunk;  // chunk table (device)
+    unsigned long long N, total_bits;
+    unsigned int K;
+    uint16_t *sym;
+};
+cudaError_t launch_decode(const DecodeArgs &a, const HuffScratch &hs, cudaStream_t s);
+cudaError_t launch_histogram(const uint16_t *sym, unsigned long long N, unsigned D,
+                             unsigned long long *hist, unsigned *status, cudaStream_t s);
+
+// container offsets (same rule as the format definition)
+__host__ __device__ inline unsigned long long a16(unsigned long long x) { return (x + 15) & ~15ULL; }
+
+}  // namespace hpdr

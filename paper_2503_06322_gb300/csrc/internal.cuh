@@ -1,0 +1,135 @@
+// internal.cuh -- shared declarations of the sm_103a library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <vector>
+#include <map>
+#include <string>
+#include "../../include/hpdr.h"
+
+namespace hpdr {
+
+constexpr int kMaxLevels = 40;
+
+// ---------------------------------------------------------------------------
+// Geometry of one level pair (l, l-1), padded to three dimensions.  Dim k of a
+// field with fewer dimensions is inactive: one node, kept, identity taps.
+
+template <typename T>
+struct DimTables {
+    int m;              // nodes on level l
+    int mc;             // nodes on level l-1
+    const T *wl;        // [m] interpolation weight of the left coarse neighbour (new nodes)
+    const T *wr;        // [m] ... of the right coarse neighbour
+    const T *tap;       // [mc*5] restriction P^T M_l, offsets -2..2 around the kept position
+    const T *ptap;      // [mc*5] transpose of interpolation P^T, offsets -2..2
+    const T *sub;       // [mc] Thomas factors of M_{l-1}: sub-diagonal
+    const T *cp;        // [mc] modified super-diagonal c'
+    const T *inv_den;   // [mc] 1 / pivot
+    const T *etap;      // [m*3] (M_l P): fine node p <- coarse nodes jfirst(p)..+2
+    const int *efirst;  // [m] first coarse index of etap's three taps
+};
+
+template <typename T>
+struct LevelGeom {
+    DimTables<T> dim[3];
+    int level;               // l
+    long long Nprev;         // N_{l-1}: start of level l's section in the stream
+};
+
+__host__ __device__ inline int cpos_of(int m, int mc, int j) { return (j + 1 < mc) ? 2 * j : m - 1; }
+__host__ __device__ inline bool kept_pos(int m, int p) { return ((p & 1) == 0) || (p == m - 1); }
+// number of kept positions strictly before p
+__host__ __device__ inline int kept_before(int p) { return (p + 1) >> 1; }
+// coarse index of a kept position
+__host__ __device__ inline int cidx_of(int m, int mc, int p) { return (p == m - 1) ? mc - 1 : (p >> 1); }
+
+// ---------------------------------------------------------------------------
+// Explicitly rounded arithmetic: the quantization decision and the
+// coefficients must not depend on how the compiler contracts expressions.
+
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// ---------------------------------------------------------------------------
+// Device-side scalars of one compression (one per field).
+
+struct Scalars {
+    double maxabs;            // max |u|
+    double sumsq;             // sum u^2
+    double tau_abs;           // absolute bound
+    double q[kMaxLevels + 1]; // bins (binary64)
+    double rho_d[kMaxLevels + 1];
+    float rho_f[kMaxLevels + 1];
+    float q_f[kMaxLevels + 1];
+    unsigned long long n_out;     // outliers collected
+    unsigned long long total_bits;
+    unsigned long long out_bytes; // container size
+    unsigned int status;          // 0 ok, else an hpdr_status magnitude
+    unsigned int s_lo, s_hi;
+    unsigned int maxbits_f32;     // max|u| as float bits (atomicMax)
+    unsigned long long maxbits_f64;
+};
+
+enum DeviceStatus : unsigned int {
+    DS_OK = 0,
+    DS_ARG = 1,          // bound below the precision floor
+    DS_CAPACITY = 3,     // output too small / outlier list full
+    DS_FORMAT = 4,       // invalid stream on decode
+    DS_LENGTH = 5,       // a code length above 63
+};
+
+// ---------------------------------------------------------------------------
+// Plans: hierarchy + device tables for one (shape, dtype).
+
+struct Plan {
+    int ndim;
+    long long n[3];          // padded shape (leading inactive dims = 1)
+    int L;
+    int m[3][kMaxLevels + 1];
+    long long N[kMaxLevels + 1];   // node count per level
+    std::vector<double> corr_norm; // c_l
+    void *tables = nullptr;        // one device allocation
+    LevelGeom<float> gf[kMaxLevels + 1];
+    LevelGeom<double> gd[kMaxLevels + 1];
+    bool is_f64;
+};
+
+struct Workspace {
+    void *base = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace hpdr
+
+struct hpdr_ctx {
+    int device;
+    std::map<std::string, hpdr::Plan *> plans;
+    hpdr::Workspace ws;
+    void *host_pinned = nullptr;   // small pinned buffer for scalars read back
+    cudaEvent_t ev = nullptr;
+};
+
+namespace hpdr {
+
+// plan.cu
+hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan **out);
+hpdr_status ensure_workspace(hpdr_ctx *ctx, size_t bytes);
+int levels_of(int ndim, const size_t *dims);
+
+inline hpdr_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HPDR_OK : HPDR_ERR_CUDA; }
+
+}  // namespace hpdr
+
+#define HPDR_CUDA_TRY(expr)                                      \
+    do {                                                         \
+        cudaError_t _e = (expr);                                 \
+        if (_e != cudaSuccess) return HPDR_ERR_CUDA;             \
+    } while (0)

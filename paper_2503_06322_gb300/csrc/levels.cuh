@@ -1,0 +1,96 @@
+// levels.cuh -- launchers of the per-level kernels (levels.cu).
+#pragma once
+#include "internal.cuh"
+
+namespace hpdr {
+
+// Where a restriction reads its fine-level values w from.
+enum class WSrc : int {
+    FIELD = 0,     // w = new-node coefficients computed from a level-l field (Alg. 1 lerp)
+    STREAM = 1,    // w = coefficients read from a level-major stream (type T)
+    SYMBOLS = 2,   // w = dequantized symbols of a level-major stream
+    DENSE = 3,     // w = a dense level-l array (all nodes; used by the transposes)
+};
+// What the FIELD source does with the coefficients it computes.
+enum class Sink : int { NONE = 0, STREAM = 1, QUANT = 2 };
+
+struct QuantOut {
+    uint16_t *sym;                 // stream of symbols
+    unsigned long long *hist;      // global histogram [D]
+    unsigned long long *out_idx;   // unordered outlier list
+    long long *out_k;
+    unsigned long long out_cap;
+    unsigned int D;
+    Scalars *sc;
+};
+
+struct SymIn {
+    const uint16_t *sym;
+    unsigned int D;
+    const Scalars *sc;               // q per level
+    const unsigned long long *out_idx;  // sorted by stream index
+    const long long *out_k;
+    unsigned long long n_out;
+    unsigned int *status;
+};
+
+template <typename T>
+struct RestrictArgs {
+    LevelGeom<T> g;
+    const T *v;          // FIELD / DENSE: level-l array
+    const T *coef_in;    // STREAM source
+    SymIn symin;         // SYMBOLS source
+    T *coef_out;         // Sink::STREAM
+    QuantOut qo;         // Sink::QUANT
+    T *b;                // coarse output (level l-1 grid)
+    T *vc;               // coarse copy of v (FIELD with a sink), may be null
+    int use_ptap;        // 0: P^T M_l taps, 1: P^T taps
+    int dense_new_only;  // DENSE: 1 = use only the new nodes (E_new^T of the input)
+};
+
+template <typename T>
+cudaError_t launch_restrict(WSrc src, Sink sink, const RestrictArgs<T> &a, cudaStream_t s);
+
+// Solve (x)_k M_{l-1} along every active dimension of the coarse array b, in
+// place; the last solve optionally adds (sign=+1) or subtracts (sign=-1) the
+// result into vc instead of storing it into b.
+template <typename T>
+cudaError_t launch_solves(const LevelGeom<T> &g, T *b, T *vc, int sign, cudaStream_t s);
+
+// Recomposition of level l: out (level-l grid) = kept nodes from vc (level
+// l-1 grid), new nodes = coefficient + interpolant of vc.
+template <typename T>
+cudaError_t launch_expand(WSrc src, const LevelGeom<T> &g, const T *vc, const T *coef_in,
+                          const SymIn &symin, T *out, cudaStream_t s);
+
+// Level 0: quantize (Sink::QUANT) or copy (Sink::STREAM) the coarsest grid.
+template <typename T>
+cudaError_t launch_level0(Sink sink, const T *v0, long long N0, T *coef_out, const QuantOut &qo,
+                          cudaStream_t s);
+// Level 0 of recomposition: v0 = coefficient stream entries [0, N0).
+template <typename T>
+cudaError_t launch_level0_in(WSrc src, const T *coef_in, const SymIn &symin, long long N0, T *v0,
+                             cudaStream_t s);
+
+// max|u| and sum u^2 (deterministic), then bins (one thread block).
+template <typename T>
+cudaError_t launch_norm(const T *u, long long N, double *partials, int nparts, cudaStream_t s);
+struct BinArgs {
+    int L;
+    double c[kMaxLevels + 1];
+    double tol;
+    int tol_kind, mode;
+    double eps;
+    long long N;
+};
+cudaError_t launch_bins(const BinArgs &ba, const double *partials, int nparts, Scalars *sc,
+                        cudaStream_t s);
+
+// Transposes: dense level-l array from a coarse array through (x)_k M_l P
+template <typename T>
+cudaError_t launch_mass_prolong(const LevelGeom<T> &g, const T *yc, T *yf, T *tmp,
+                                cudaStream_t s);
+
+int norm_parts();
+
+}  // namespace hpdr

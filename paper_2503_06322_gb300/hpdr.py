@@ -1,0 +1,231 @@
+"""Thin Python binding of ``libhpdr.so`` (the C ABI in ``include/hpdr.h``).
+
+Argument marshalling only: every step of the reduction runs in the library's
+CUDA kernels.  Tensors are PyTorch CUDA tensors (PyTorch supplies device memory
+and the current stream); the library must have been built
+(``__graft_entry__.build()``) -- a missing library is an error, there is no
+fallback.
+
+Function names follow the C ABI:
+  hpdr_compress, hpdr_decompress, hpdr_inspect, hpdr_compress_bound,
+  hpdr_decompose, hpdr_recompose, hpdr_recompose_adjoint,
+  hpdr_decompose_adjoint, hpdr_huffman_encode, hpdr_huffman_decode.
+"""
+import ctypes as C
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhpdr.so")
+
+F32, F64 = 0, 1
+LINF, L2 = 0, 1
+ABS, REL = 0, 1
+STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "output buffer too small",
+          -4: "malformed container", -5: "device wait timed out", -6: "device allocation failed"}
+
+
+class HpdrError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__("%s: %s (status %d)" % (what, STATUS.get(status, "?"), status))
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [("dict_size", C.c_uint32), ("chunk", C.c_uint32)]
+
+
+_lib = None
+_ctx = {}
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhpdr.so is not built: run __graft_entry__.build() first")
+        L = C.CDLL(LIB_PATH)
+        vp, sz = C.c_void_p, C.POINTER(C.c_size_t)
+        sigs = {
+            "hpdr_ctx_create": [C.POINTER(vp), C.c_int],
+            "hpdr_ctx_destroy": [vp],
+            "hpdr_compress": [vp, vp, C.c_int, C.c_int, sz, C.c_double, C.c_int, C.c_int,
+                              C.POINTER(Config), vp, C.c_size_t, sz, vp],
+            "hpdr_decompress": [vp, vp, C.c_size_t, vp, C.c_size_t, vp],
+            "hpdr_inspect": [vp, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_int), sz],
+            "hpdr_decompose": [vp, vp, vp, C.c_int, C.c_int, sz, vp],
+            "hpdr_recompose": [vp, vp, vp, C.c_int, C.c_int, sz, vp],
+            "hpdr_recompose_adjoint": [vp, vp, vp, C.c_int, C.c_int, sz, vp],
+            "hpdr_decompose_adjoint": [vp, vp, vp, C.c_int, C.c_int, sz, vp],
+            "hpdr_huffman_encode": [vp, vp, C.c_uint64, C.c_uint32, C.c_uint32, vp, vp, vp,
+                                    C.c_uint64, C.POINTER(C.c_uint64), vp],
+            "hpdr_huffman_decode": [vp, vp, C.c_uint64, vp, C.c_uint64, C.c_uint32, C.c_uint32,
+                                    vp, vp, vp],
+        }
+        for name, args in sigs.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.hpdr_compress_bound.argtypes = [C.c_int, sz, C.c_int, C.POINTER(Config)]
+        L.hpdr_compress_bound.restype = C.c_size_t
+        L.hpdr_status_string.argtypes = [C.c_int]
+        L.hpdr_status_string.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(st, what):
+    if st != 0:
+        raise HpdrError(st, what)
+
+
+def context(device=None):
+    """Per-device library context (plans and workspaces are cached in it)."""
+    dev = torch.cuda.current_device() if device is None else int(device)
+    if dev not in _ctx:
+        h = C.c_void_p()
+        _check(lib().hpdr_ctx_create(C.byref(h), dev), "hpdr_ctx_create")
+        _ctx[dev] = h
+    return _ctx[dev]
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dims(shape):
+    shape = tuple(int(s) for s in shape)
+    return len(shape), (C.c_size_t * 3)(*(list(shape) + [1] * (3 - len(shape))))
+
+
+def _dtype_code(t):
+    if t == torch.float32:
+        return F32
+    if t == torch.float64:
+        return F64
+    raise TypeError("only float32 and float64 fields are supported, got %s" % t)
+
+
+def _cfg(dict_size, chunk):
+    return Config(int(dict_size), int(chunk))
+
+
+def _dev_tensor(t, what):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous CUDA tensor" % what)
+    return t
+
+
+def hpdr_compress_bound(shape, dtype=torch.float32, dict_size=8192, chunk=1024):
+    nd, dims = _dims(shape)
+    cfg = _cfg(dict_size, chunk)
+    return int(lib().hpdr_compress_bound(nd, dims, _dtype_code(dtype), C.byref(cfg)))
+
+
+def hpdr_compress(u, tol, tol_kind=REL, mode=LINF, dict_size=8192, chunk=1024, out=None,
+                  stream=None):
+    """Compress a CUDA field; returns a uint8 CUDA tensor holding the container."""
+    _dev_tensor(u, "u")
+    nd, dims = _dims(u.shape)
+    cfg = _cfg(dict_size, chunk)
+    cap = hpdr_compress_bound(u.shape, u.dtype, dict_size, chunk)
+    if out is None:
+        out = torch.empty(cap, dtype=torch.uint8, device=u.device)
+    nb = C.c_size_t()
+    _check(lib().hpdr_compress(context(u.device.index), C.c_void_p(u.data_ptr()), _dtype_code(u.dtype),
+                               nd, dims, float(tol), int(tol_kind), int(mode), C.byref(cfg),
+                               C.c_void_p(out.data_ptr()), out.numel(), C.byref(nb),
+                               _stream(stream)), "hpdr_compress")
+    return out[:nb.value]
+
+
+def hpdr_inspect(buf):
+    """(torch dtype, shape) of a container held in a CUDA or CPU uint8 tensor."""
+    dt, nd = C.c_int(), C.c_int()
+    dims = (C.c_size_t * 3)()
+    _check(lib().hpdr_inspect(C.c_void_p(buf.data_ptr()), buf.numel(), C.byref(dt), C.byref(nd),
+                              dims), "hpdr_inspect")
+    return (torch.float32 if dt.value == F32 else torch.float64), tuple(dims[:nd.value])
+
+
+def hpdr_decompress(buf, out=None, stream=None):
+    _dev_tensor(buf, "buf")
+    dt, shape = hpdr_inspect(buf)
+    if out is None:
+        out = torch.empty(shape, dtype=dt, device=buf.device)
+    _check(lib().hpdr_decompress(context(buf.device.index), C.c_void_p(buf.data_ptr()), buf.numel(),
+                                 C.c_void_p(out.data_ptr()), out.numel() * out.element_size(),
+                                 _stream(stream)), "hpdr_decompress")
+    return out
+
+
+def _field_call(name, src, out, shape, stream):
+    nd, dims = _dims(shape)
+    _check(getattr(lib(), name)(context(src.device.index), C.c_void_p(src.data_ptr()),
+                                C.c_void_p(out.data_ptr()), _dtype_code(src.dtype), nd, dims,
+                                _stream(stream)), name)
+    return out
+
+
+def hpdr_decompose(u, out=None, stream=None):
+    """Level-major coefficient stream (1-D tensor) of the field u."""
+    _dev_tensor(u, "u")
+    if out is None:
+        out = torch.empty(u.numel(), dtype=u.dtype, device=u.device)
+    return _field_call("hpdr_decompose", u, out, u.shape, stream)
+
+
+def hpdr_recompose(coef, shape, out=None, stream=None):
+    _dev_tensor(coef, "coef")
+    if out is None:
+        out = torch.empty(tuple(shape), dtype=coef.dtype, device=coef.device)
+    return _field_call("hpdr_recompose", coef, out, shape, stream)
+
+
+def hpdr_recompose_adjoint(grad_u, out=None, stream=None):
+    _dev_tensor(grad_u, "grad_u")
+    if out is None:
+        out = torch.empty(grad_u.numel(), dtype=grad_u.dtype, device=grad_u.device)
+    return _field_call("hpdr_recompose_adjoint", grad_u, out, grad_u.shape, stream)
+
+
+def hpdr_decompose_adjoint(grad_coef, shape, out=None, stream=None):
+    _dev_tensor(grad_coef, "grad_coef")
+    if out is None:
+        out = torch.empty(tuple(shape), dtype=grad_coef.dtype, device=grad_coef.device)
+    return _field_call("hpdr_decompose_adjoint", grad_coef, out, shape, stream)
+
+
+def hpdr_huffman_encode(symbols, D=8192, K=1024, stream=None):
+    """Huffman-encode a CUDA int16 tensor holding uint16 symbols < D.
+
+    Returns (lengths uint8[D], chunk table int64[ceil(N/K)], words int32[...],
+    total_bits)."""
+    _dev_tensor(symbols, "symbols")
+    N = symbols.numel()
+    dev = symbols.device
+    lengths = torch.empty(D, dtype=torch.uint8, device=dev)
+    chunk = torch.empty((N + K - 1) // K, dtype=torch.int64, device=dev)
+    cap = (63 * N + 31) // 32 + 4
+    words = torch.empty(cap, dtype=torch.int32, device=dev)
+    tb = C.c_uint64()
+    _check(lib().hpdr_huffman_encode(context(dev.index), C.c_void_p(symbols.data_ptr()), N, D, K,
+                                     C.c_void_p(lengths.data_ptr()), C.c_void_p(chunk.data_ptr()),
+                                     C.c_void_p(words.data_ptr()), cap, C.byref(tb),
+                                     _stream(stream)), "hpdr_huffman_encode")
+    return lengths, chunk, words[:(tb.value + 31) // 32], tb.value
+
+
+def hpdr_huffman_decode(words, total_bits, chunk, N, lengths, D=8192, K=1024, out=None,
+                        stream=None):
+    dev = words.device
+    if out is None:
+        out = torch.empty(N, dtype=torch.int16, device=dev)
+    _check(lib().hpdr_huffman_decode(context(dev.index), C.c_void_p(words.data_ptr()),
+                                     int(total_bits), C.c_void_p(chunk.data_ptr()), N, D, K,
+                                     C.c_void_p(lengths.data_ptr()), C.c_void_p(out.data_ptr()),
+                                     _stream(stream)), "hpdr_huffman_decode")
+    return out
