@@ -1,0 +1,421 @@
+#!/usr/bin/env python3
+"""Throughput of the GPU reduction path: compress + decompress of a 513^3 FP32
+Gaussian random field (power spectrum ~|k|^-11/3, unit variance; stands in for
+the paper's NYX 512^3 FP32 fields, which are not available) at a relative
+L-infinity bound of 1e-3, on one GB300.
+
+One step = hpdr_compress (device field -> device container) followed by
+hpdr_decompress (container -> device field).  value = 2 x field bytes per
+step / step time (each direction moves the field's original bytes once; the
+paper's throughput unit is original bytes per second).
+
+Run:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch with torchrun: every rank compresses its own field (replicas,
+no data exchange); value = bytes of all ranks / max time over ranks.
+"""
+import argparse
+import ctypes as C
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "compress/decompress GB/s on 1 GB300 at rel L∞ 1e-3; % of HBM roofline"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--shape", default="513,513,513")
+    ap.add_argument("--tol", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-to-host leg")
+    ap.add_argument("--cpu-planes", type=int, default=65,
+                    help="planes of the field in the CPU-baseline sample")
+    return ap.parse_args()
+
+
+def workload_name(shape, tol):
+    return "%s FP32 power-law field (|k|^-11/3), rel Linf %g, compress+decompress" % (
+        "x".join(str(s) for s in shape), tol)
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows),
+                "window": "warmup+timed region (200 ms sampling)"}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("levels.cu", "huffman.cu", "levels.cuh", "internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2503_06322_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_group):
+    """DRAM bytes per launch of a kernel group from the committed ncu summary,
+    only if it was captured from the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    cur = source_hash()
+    for ln in lines:
+        parts = [p.strip() for p in ln.strip().strip("|").split("|")]
+        if len(parts) >= 4 and parts[0] == kernel_group and parts[1] == cur:
+            try:
+                return float(parts[3])
+            except ValueError:
+                return None
+    return None
+
+
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(group, S, NL, NL1, bits, nch):
+    """Bytes each kernel must move, per launch (roofline)."""
+    new = NL - NL1
+    if group == "c_restrict_quant_L":      # read v_L, write symbols, b and coarse copy
+        return S * NL + 2 * new + 2 * S * NL1
+    if group == "d_expand_L":              # read symbols and corrected coarse grid, write field
+        return 2 * new + S * NL1 + S * NL
+    if group == "d_restrict_sym_L":        # read symbols, write b
+        return 2 * new + S * NL1
+    if group == "d_decode":                # read bitstream + chunk table, write symbols
+        return bits / 8.0 + 8 * nch + 2 * NL
+    if group == "norm":
+        return S * NL
+    return None
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2503_06322_gb300 import fields, hpdr
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    shape = tuple(int(x) for x in args.shape.split(","))
+    u = fields.powerlaw_field_torch(shape, seed=args.seed + rank, device=dev)
+    nbytes = u.numel() * u.element_size()
+    L = hpdr.lib()
+    ctx = hpdr.context(local)
+    stream = torch.cuda.current_stream()
+    cap = hpdr.hpdr_compress_bound(shape, u.dtype)
+    cbuf = torch.empty(cap, dtype=torch.uint8, device=dev)
+    rec = torch.empty_like(u)
+
+    def step():
+        b = hpdr.hpdr_compress(u, args.tol, out=cbuf)
+        hpdr.hpdr_decompress(b, out=rec)
+        return b
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    # ---- per-direction throughput (separate, untimed for `value`) ----
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    nsep = min(20, args.steps)
+    tc = td = 0.0
+    for _ in range(nsep):
+        e0.record(stream)
+        b = hpdr.hpdr_compress(u, args.tol, out=cbuf)
+        e1.record(stream)
+        hpdr.hpdr_decompress(b, out=rec)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        tc += e0.elapsed_time(e1)
+        td += e1.elapsed_time(e2)
+    comp_bytes = b.numel()
+
+    # ---- timed region ----
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.6)
+    L.hpdr_profile_enable.argtypes = [C.c_void_p, C.c_int]
+    L.hpdr_profile_enable(ctx, 1)
+    nprof_read = (C.c_char_p * 64)()
+    ms_arr = (C.c_double * 64)()
+    cnt_arr = (C.c_longlong * 64)()
+    L.hpdr_profile_read.argtypes = [C.c_void_p, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_longlong), C.c_int]
+    L.hpdr_launch_count.restype = C.c_ulonglong
+    L.hpdr_profile_read(ctx, nprof_read, ms_arr, cnt_arr, 64)   # clear
+    barrier()
+    launches0 = L.hpdr_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_stop = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        if i == 500:   # the diagnostics' event pool covers the first 500 steps
+            L.hpdr_profile_enable(ctx, 0)
+        step()
+    t_stop.record(stream)
+    barrier()
+    launches = L.hpdr_launch_count() - launches0
+    L.hpdr_profile_enable(ctx, 0)
+    ng = L.hpdr_profile_read(ctx, nprof_read, ms_arr, cnt_arr, 64)
+    groups = {nprof_read[i].decode(): (ms_arr[i], cnt_arr[i]) for i in range(ng)}
+    ms_total = t_start.elapsed_time(t_stop)
+    clk = clocks.stop()
+    ms_local = ms_total
+    if world > 1:
+        t = torch.tensor([ms_local], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * 2.0 * nbytes / (ms_step * 1e-3) / 1e9
+
+    # ---- correctness of the timed output ----
+    tau = args.tol * u.abs().max().item()
+    err = (rec - u).abs().max().item()
+
+    # ---- roofline of the dominant single kernel ----
+    NL = u.numel()
+    NL1 = level_nodes(shape, 1)
+    bits = _parse_bits(b)
+    nch = (NL + 1023) // 1024
+    single = ["c_restrict_quant_L", "d_expand_L", "d_restrict_sym_L", "d_decode", "norm"]
+    best = max((g for g in single if g in groups), key=lambda g: groups[g][0])
+    ms_b, cnt_b = groups[best]
+    avg_s = ms_b / cnt_b * 1e-3
+    alg = algorithmic_bytes(best, 4, NL, NL1, bits, nch)
+    peak, peak_kind = measured_peak()
+    achieved = alg / avg_s / 1e9
+    traffic = ncu_traffic(best)
+    prof_steps = max(1, groups.get("norm", (0, 1))[1])
+    breakdown = {g: round(v[0] / prof_steps, 4) for g, v in sorted(groups.items(), key=lambda x: -x[1][0])}
+    roofline = {"bound": "hbm", "kernel": best, "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": peak_kind, "algorithmic_bytes_per_launch": int(alg),
+                "avg_launch_ms": round(avg_s * 1e3, 4)}
+
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded power-law Gaussian random field generated on the device)",
+        "config": {"workload": workload_name(shape, args.tol), "shape": list(shape),
+                   "tol": args.tol, "tol_kind": "rel", "mode": "Linf", "dict_size": 8192,
+                   "chunk": 1024, "l2": "inputs larger than L2 (540 MB field, 129 MB L2)",
+                   "parallelism": "replicas x%d" % world},
+        "compress_gbs": round(nbytes / (tc / nsep * 1e-3) / 1e9, 2),
+        "decompress_gbs": round(nbytes / (td / nsep * 1e-3) / 1e9, 2),
+        "compression_ratio": round(nbytes / comp_bytes, 4),
+        "max_err_over_tau": round(err / tau, 4),
+        "roofline": roofline, "breakdown_ms_per_step": breakdown,
+        "gpu_launches": int(launches), "clocks": clk,
+    }
+    return out, u, cbuf, comp_bytes
+
+
+def level_nodes(shape, down):
+    """Node count of the level `down` coarsenings below the finest grid."""
+    n = 1
+    for s in shape:
+        for _ in range(down):
+            s = (s + 1) // 2 if s % 2 else s // 2 + 1
+        n *= s
+    return n
+
+
+def _parse_bits(buf):
+    h = buf[:128].cpu().numpy().tobytes()
+    return int.from_bytes(h[112:120], "little")
+
+
+def run_e2e(args, u, out):
+    """Host-to-host: pinned field -> H2D -> compress -> D2H container -> H2D
+    container -> decompress -> D2H field, all inside the timed region."""
+    import torch
+    from paper_2503_06322_gb300 import hpdr
+    dev = u.device
+    stream = torch.cuda.current_stream()
+    h_in = torch.empty(u.shape, dtype=u.dtype, pin_memory=True)
+    h_in.copy_(u.cpu())
+    h_out = torch.empty_like(h_in).pin_memory()
+    d_in = torch.empty_like(u)
+    d_rec = torch.empty_like(u)
+    cap = hpdr.hpdr_compress_bound(u.shape, u.dtype)
+    cbuf = torch.empty(cap, dtype=torch.uint8, device=dev)
+    h_c = torch.empty(cap, dtype=torch.uint8, pin_memory=True)
+    d_c2 = torch.empty(cap, dtype=torch.uint8, device=dev)
+
+    def step():
+        d_in.copy_(h_in, non_blocking=True)
+        b = hpdr.hpdr_compress(d_in, args.tol, out=cbuf)
+        n = b.numel()
+        h_c[:n].copy_(b, non_blocking=True)
+        d_c2[:n].copy_(h_c[:n], non_blocking=True)
+        hpdr.hpdr_decompress(d_c2[:n], out=d_rec)
+        h_out.copy_(d_rec, non_blocking=True)
+        return n
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    k = max(3, min(args.steps, 20))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    nb = 0
+    for _ in range(k):
+        nb = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / k
+    fb = u.numel() * u.element_size()
+    return {"value": round(2.0 * fb / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+            "h2d_bytes_per_step": fb + nb, "d2h_bytes_per_step": nb + fb,
+            "ms_per_step": round(ms, 3), "steps": k,
+            "path": "pinned host field -> H2D -> hpdr_compress -> D2H -> H2D -> hpdr_decompress -> D2H"}
+
+
+def cpu_sample(args, u_host_planes, steps=1):
+    """The oracle (single-threaded C, FP64) on the first planes of the field."""
+    import numpy as np
+    import oracle
+    x = np.ascontiguousarray(u_host_planes)
+    t = 0.0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        b = oracle.compress(x, args.tol)
+        oracle.decompress(b)
+        t += time.perf_counter() - t0
+    gbs = 2.0 * x.nbytes * steps / t / 1e9
+    return gbs, t / steps, x.shape
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    shape = tuple(int(x) for x in args.shape.split(","))
+
+    if args.impl == "reference":
+        # the reference arm is the CPU oracle, timed as it stands on the host cores
+        if rank != 0:
+            return 0
+        from paper_2503_06322_gb300 import fields
+        import numpy as np
+        planes = min(shape[0], 17)
+        sample = fields.powerlaw_field((planes,) + shape[1:], seed=args.seed)
+        for _ in range(args.warmup):
+            cpu_sample(args, sample)
+        gbs, sec, shp = cpu_sample(args, sample, steps=args.steps)
+        desc = "oracle compress+decompress of a %s slab of the %s workload per step" % (
+            "x".join(map(str, shp)), "x".join(map(str, shape)))
+        out = {"impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s",
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": round(sec * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": workload_name(shape, args.tol), "shape": list(shape)},
+               "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1,
+                                "kind": "oracle", "sample": desc},
+               "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return 0
+
+    import torch
+    if world > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    out, u, cbuf, nb = run_ours(args, rank, world, local)
+    if not args.no_e2e:
+        e2e = run_e2e(args, u, out)
+        if world > 1:
+            t = torch.tensor([e2e["ms_per_step"]], device=u.device, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            fb = u.numel() * u.element_size()
+            e2e["value"] = round(world * 2.0 * fb / (float(t.item()) * 1e-3) / 1e9, 2)
+        out["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu:
+        planes = min(args.cpu_planes, shape[0])
+        host = u[:planes].cpu().numpy()
+        gbs, sec, shp = cpu_sample(args, host)
+        out["cpu_baseline"] = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                               "sample": "oracle compress+decompress of the first %d planes (%s) of "
+                                         "the timed field, %.1f s" % (planes, "x".join(map(str, shp)), sec)}
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

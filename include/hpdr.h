@@ -153,6 +153,18 @@ hpdr_status hpdr_huffman_decode(hpdr_ctx *ctx, const uint32_t *d_words, uint64_t
                                 const uint64_t *d_chunk_bits, uint64_t N, uint32_t D, uint32_t K,
                                 const uint8_t *d_lengths, uint16_t *d_symbols, void *stream);
 
+/* Diagnostics (not part of the reduction; off by default).
+ * hpdr_profile_enable: when on, every call of this context records CUDA
+ * events around each of its kernel groups on the call's stream.
+ * hpdr_profile_read: waits for the recorded events, adds their elapsed times
+ * per group name, returns the number of groups (at most cap are written:
+ * names[i] static strings owned by the context, ms[i] total milliseconds,
+ * count[i] number of recorded intervals) and clears the records.
+ * hpdr_launch_count: kernels launched by the library since it was loaded. */
+hpdr_status hpdr_profile_enable(hpdr_ctx *ctx, int on);
+int hpdr_profile_read(hpdr_ctx *ctx, const char **names, double *ms, long long *count, int cap);
+unsigned long long hpdr_launch_count(void);
+
 /* Static description of a status code. */
 const char *hpdr_status_string(hpdr_status status);
 

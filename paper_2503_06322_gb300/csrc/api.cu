@@ -136,7 +136,10 @@ hpdr_status compress_t(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, const
     const long long N = P->N[L];
     CK(cudaMemsetAsync(w.sc, 0, sizeof(Scalars), s));
     CK(cudaMemsetAsync(w.hist, 0, sizeof(unsigned long long) * D, s));
+    {
+    ProfScope ps(ctx, "norm", s);
     CK(launch_norm<T>(u, N, w.partials, norm_parts(), s));
+    }
     BinArgs ba;
     memset(&ba, 0, sizeof(ba));
     ba.L = L;
@@ -161,15 +164,24 @@ hpdr_status compress_t(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, const
         a.qo = qo;
         a.b = (T *)w.b;
         a.vc = vc;
+        {
+        ProfScope ps(ctx, l == L ? "c_restrict_quant_L" : "c_restrict_quant_coarse", s);
         CK(launch_restrict<T>(WSrc::FIELD, Sink::QUANT, a, s));
+        }
+        {
+        ProfScope ps(ctx, l == L ? "c_solves_L" : "c_solves_coarse", s);
         CK(launch_solves<T>(a.g, (T *)w.b, vc, +1, s));
+        }
         v = vc;
     }
     CK(launch_level0<T>(Sink::QUANT, v, P->N[0], nullptr, qo, s));
 
     HuffScratch hs;
     huff_scratch_carve(w.huff, D, w.sc, &hs);
+    {
+    ProfScope ps(ctx, "c_codebook", s);
     CK(launch_codebook(w.hist, D, hs, s));
+    }
     EncodeArgs ea;
     memset(&ea, 0, sizeof(ea));
     ea.sym = w.sym; ea.N = (unsigned long long)N; ea.D = D; ea.K = K;
@@ -177,7 +189,10 @@ hpdr_status compress_t(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, const
     ea.chunk_bits = w.chunk_bits; ea.chunk_esc = w.chunk_esc; ea.sc = w.sc;
     ea.container = out; ea.L = L; ea.capacity = cap;
     ea.oidx_unordered = w.oidx; ea.ok_unordered = w.ok;
+    {
+    ProfScope ps(ctx, "c_encode", s);
     CK(launch_encode(ea, s));
+    }
     HeaderArgs h;
     memset(&h, 0, sizeof(h));
     h.dtype = sizeof(T) == 4 ? 0 : 1;
@@ -286,13 +301,19 @@ hpdr_status decompress_t(hpdr_ctx *ctx, const Plan *P, const Hdr &h, const uint8
     huff_scratch_carve(w.huff, h.D, w.sc, &hs);
     CK(cudaMemsetAsync(hs.len, 0, h.D, s));
     CK(cudaMemcpyAsync(hs.len + h.s_lo, in + h.off_len, h.s_hi - h.s_lo + 1, cudaMemcpyDeviceToDevice, s));
+    {
+    ProfScope ps(ctx, "d_tables", s);
     CK(launch_decode_tables(hs.len, h.D, hs, s));
+    }
     DecodeArgs da;
     da.words = (const uint32_t *)(in + h.off_bits);
     da.nwords = h.nwords;
     da.chunk = (const unsigned long long *)(in + h.off_chunk);
     da.N = h.N; da.total_bits = h.bits; da.K = h.K; da.sym = w.sym;
+    {
+    ProfScope ps(ctx, "d_decode", s);
     CK(launch_decode(da, hs, s));
+    }
     SymIn si;
     si.sym = w.sym; si.D = h.D; si.sc = w.sc;
     si.out_idx = (const unsigned long long *)(in + h.off_out);
@@ -310,10 +331,19 @@ hpdr_status decompress_t(hpdr_ctx *ctx, const Plan *P, const Hdr &h, const uint8
         a.g = g;
         a.symin = si;
         a.b = (T *)w.b;
+        {
+        ProfScope ps(ctx, l == L ? "d_restrict_sym_L" : "d_restrict_sym_coarse", s);
         CK(launch_restrict<T>(WSrc::SYMBOLS, Sink::NONE, a, s));
+        }
+        {
+        ProfScope ps(ctx, l == L ? "d_solves_L" : "d_solves_coarse", s);
         CK(launch_solves<T>(g, (T *)w.b, v, -1, s));
+        }
         T *dst = (l == L) ? out : bufs[l % 2];
+        {
+        ProfScope ps(ctx, l == L ? "d_expand_L" : "d_expand_coarse", s);
         CK(launch_expand<T>(WSrc::SYMBOLS, g, v, nullptr, si, dst, s));
+        }
         v = dst;
     }
     CK(cudaMemcpyAsync(hsc, w.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
@@ -626,6 +656,46 @@ hpdr_status hpdr_decompose_adjoint(hpdr_ctx *ctx, const void *d_grad_coef, void 
     (void)ctx; (void)d_grad_coef; (void)d_grad_u; (void)dtype; (void)ndim; (void)dims; (void)stream;
     return HPDR_ERR_ARG;
 }
+
+hpdr_status hpdr_profile_enable(hpdr_ctx *ctx, int on)
+{
+    if (!ctx) return HPDR_ERR_ARG;
+    DevGuard g(ctx->device);
+    if (on && ctx->prof_pool.empty()) {
+        ctx->prof_pool.resize(65536);
+        for (auto &e : ctx->prof_pool)
+            if (cudaEventCreate(&e) != cudaSuccess) return HPDR_ERR_CUDA;
+    }
+    ctx->prof_on = on != 0;
+    return HPDR_OK;
+}
+
+int hpdr_profile_read(hpdr_ctx *ctx, const char **names, double *ms, long long *count, int cap)
+{
+    if (!ctx) return -1;
+    DevGuard g(ctx->device);
+    for (auto &r : ctx->prof_recs) {
+        float t = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+            ctx->prof_ms[r.id] += t;
+            ctx->prof_cnt[r.id] += 1;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    ctx->prof_recs.clear();
+    ctx->prof_used = 0;
+    int n = (int)ctx->prof_names.size();
+    for (int i = 0; i < n && i < cap; i++) {
+        if (names) names[i] = ctx->prof_names[i].c_str();
+        if (ms) ms[i] = ctx->prof_ms[i];
+        if (count) count[i] = ctx->prof_cnt[i];
+    }
+    for (int i = 0; i < n; i++) { ctx->prof_ms[i] = 0.0; ctx->prof_cnt[i] = 0; }
+    return n;
+}
+
+unsigned long long hpdr_launch_count(void) { return g_launches; }
 
 const char *hpdr_status_string(hpdr_status st)
 {

@@ -765,6 +765,7 @@ cudaError_t launch_codebook(const unsigned long long *hist, unsigned int D, cons
     merge_kernel<<<1, 1024, kSmemKeys * 16, s>>>(hs, D);
     rank_kernel<<<kRankBlocks, 256, kSmemKeys * 8, s>>>(hs.keys2, hs.nsym, nullptr, hs.rank);
     assign_kernel<<<64, 256, 0, s>>>(hs);
+    count_launch(5);
     return cudaGetLastError();
 }
 
@@ -780,6 +781,7 @@ cudaError_t launch_decode_tables(const uint8_t *len, unsigned int D, const HuffS
     e = cudaMemsetAsync(hs.lut, 0, 4u << kLutBits, s);
     if (e != cudaSuccess) return e;
     lut_kernel<<<64, 256, 0, s>>>(hs);
+    count_launch(5);
     return cudaGetLastError();
 }
 
@@ -794,6 +796,7 @@ cudaError_t launch_encode(const EncodeArgs &a, cudaStream_t s)
     size_t sm = (code_sm ? 8 * (size_t)a.D : 0) + ((a.D + 15) & ~15u) + 4 * words;
     enc_write_kernel<<<152 * 4, kEncThreads, sm, s>>>(a);
     if (a.container) outlier_place_kernel<<<152, 256, 0, s>>>(a);
+    count_launch(a.container ? 4 : 3);
     return cudaGetLastError();
 }
 
@@ -801,6 +804,7 @@ cudaError_t launch_header(const HeaderArgs &h, const uint8_t *len, Scalars *sc, 
                           cudaStream_t s)
 {
     header_kernel<<<1, 256, 0, s>>>(h, len, sc, container);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -814,12 +818,14 @@ cudaError_t launch_histogram(const uint16_t *sym, unsigned long long N, unsigned
         attr = true;
     }
     hist_kernel<<<152 * 4, 256, D <= 16384 ? D * 4 : 0, s>>>(sym, N, D, hist, status);
+    count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_decode(const DecodeArgs &a, const HuffScratch &hs, cudaStream_t s)
 {
     decode_kernel<<<152 * 4, 256, 0, s>>>(a, hs);
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -109,15 +109,40 @@ struct Workspace {
 
 }  // namespace hpdr
 
+struct hpdr_prof_rec {
+    int id;
+    cudaEvent_t a, b;
+};
+
 struct hpdr_ctx {
     int device;
     std::map<std::string, hpdr::Plan *> plans;
     hpdr::Workspace ws;
     void *host_pinned = nullptr;   // small pinned buffer for scalars read back
-    cudaEvent_t ev = nullptr;
+    // diagnostics: CUDA-event time per kernel group (off by default)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_pool;
+    size_t prof_used = 0;
+    std::vector<hpdr_prof_rec> prof_recs;
+    std::vector<std::string> prof_names;
+    std::vector<double> prof_ms;
+    std::vector<long long> prof_cnt;
 };
 
 namespace hpdr {
+
+// number of kernels launched by this library since it was loaded
+extern unsigned long long g_launches;
+inline void count_launch(int n = 1) { g_launches += (unsigned long long)n; }
+
+// diagnostics scope: records CUDA events around a group of launches
+struct ProfScope {
+    hpdr_ctx *ctx;
+    int slot = -1;
+    cudaStream_t s;
+    ProfScope(hpdr_ctx *c, const char *name, cudaStream_t st);
+    ~ProfScope();
+};
 
 // plan.cu
 hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan **out);

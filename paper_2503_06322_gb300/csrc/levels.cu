@@ -554,6 +554,7 @@ cudaError_t launch_restrict_t(const RestrictArgs<T> &a, cudaStream_t s)
         attr_set = true;
     }
     restrict_kernel<T, SRC, SINK><<<dim3(gx, gy, gz), RTHREADS, sm, s>>>(a, seg);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -607,6 +608,7 @@ cudaError_t launch_solves(const LevelGeom<T> &g, T *b, T *vc, int sign, cudaStre
                     b, n, nlines, rows, pitch, d.sub, d.cp, d.inv_den, vc, sg);
             }
         }
+        count_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -620,6 +622,7 @@ cudaError_t launch_expand(WSrc src, const LevelGeom<T> &g, const T *vc, const T 
     long long rows = (long long)g.dim[0].m * g.dim[1].m;
     if (src == WSrc::STREAM) expand_kernel<T, 1><<<(unsigned)rows, 128, 0, s>>>(g, vc, coef_in, symin, out);
     else expand_kernel<T, 2><<<(unsigned)rows, 128, 0, s>>>(g, vc, coef_in, symin, out);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -630,6 +633,7 @@ cudaError_t launch_level0(Sink sink, const T *v0, long long N0, T *coef_out, con
     unsigned blocks = (unsigned)((N0 + 255) / 256);
     if (sink == Sink::STREAM) level0_kernel<T, 1><<<blocks, 256, 0, s>>>(v0, N0, coef_out, qo);
     else level0_kernel<T, 2><<<blocks, 256, 0, s>>>(v0, N0, coef_out, qo);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -640,6 +644,7 @@ cudaError_t launch_level0_in(WSrc src, const T *coef_in, const SymIn &symin, lon
     unsigned blocks = (unsigned)((N0 + 255) / 256);
     if (src == WSrc::STREAM) level0_in_kernel<T, 1><<<blocks, 256, 0, s>>>(coef_in, symin, N0, v0);
     else level0_in_kernel<T, 2><<<blocks, 256, 0, s>>>(coef_in, symin, N0, v0);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -647,6 +652,7 @@ template <typename T>
 cudaError_t launch_norm(const T *u, long long N, double *partials, int nparts, cudaStream_t s)
 {
     norm_kernel<T><<<nparts, 256, 0, s>>>(u, N, partials);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -654,6 +660,7 @@ cudaError_t launch_bins(const BinArgs &ba, const double *partials, int nparts, S
                         cudaStream_t s)
 {
     bins_kernel<<<1, 256, 0, s>>>(ba, partials, nparts, sc);
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -275,6 +275,35 @@ hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan
     return HPDR_OK;
 }
 
+unsigned long long g_launches = 0;
+
+ProfScope::ProfScope(hpdr_ctx *c, const char *name, cudaStream_t st) : ctx(c), s(st)
+{
+    if (!ctx || !ctx->prof_on) return;
+    if (ctx->prof_used + 2 > ctx->prof_pool.size()) return;
+    int id = -1;
+    for (size_t i = 0; i < ctx->prof_names.size(); i++)
+        if (ctx->prof_names[i] == name) { id = (int)i; break; }
+    if (id < 0) {
+        id = (int)ctx->prof_names.size();
+        ctx->prof_names.push_back(name);
+        ctx->prof_ms.push_back(0.0);
+        ctx->prof_cnt.push_back(0);
+    }
+    hpdr_prof_rec r;
+    r.id = id;
+    r.a = ctx->prof_pool[ctx->prof_used++];
+    r.b = ctx->prof_pool[ctx->prof_used++];
+    cudaEventRecord(r.a, s);
+    slot = (int)ctx->prof_recs.size();
+    ctx->prof_recs.push_back(r);
+}
+
+ProfScope::~ProfScope()
+{
+    if (slot >= 0) cudaEventRecord(ctx->prof_recs[slot].b, s);
+}
+
 hpdr_status ensure_workspace(hpdr_ctx *ctx, size_t bytes)
 {
     if (ctx->ws.bytes >= bytes) return HPDR_OK;
