@@ -49,6 +49,7 @@ hpdr_status map_device_status(unsigned st)
     case DS_CAPACITY: return HPDR_ERR_CAPACITY;
     case DS_FORMAT: return HPDR_ERR_FORMAT;
     case DS_LENGTH: return HPDR_ERR_CAPACITY;
+    case DS_TIMEOUT: return HPDR_ERR_TIMEOUT;
     default: return HPDR_ERR_CUDA;
     }
 }
@@ -84,6 +85,8 @@ struct Ws {
     uint16_t *sym;
     unsigned long long *chunk_bits;
     unsigned *chunk_esc;
+    unsigned long long *bsum;
+    unsigned *besc;
     unsigned long long *oidx;
     long long *ok;
     unsigned long long ocap;
@@ -105,12 +108,24 @@ size_t carve_ws(void *base, const Plan *P, size_t esz, unsigned D, unsigned K, b
     w->sym = need_sym ? c.take<uint16_t>(N + 8) : nullptr;
     w->chunk_bits = c.take<unsigned long long>(nch + 2);
     w->chunk_esc = c.take<unsigned>(nch + 2);
+    w->bsum = c.take<unsigned long long>(1024);
+    w->besc = c.take<unsigned>(1024);
     w->ocap = out_cap_of(N);
     w->oidx = c.take<unsigned long long>(w->ocap);
     w->ok = c.take<long long>(w->ocap);
     w->huff = c.take<char>(huff_scratch_bytes(D));
     return c.used + 256;
 }
+
+// diagnostics group names of the levels below the finest
+#define LN(p) {p "_l0", p "_l1", p "_l2", p "_l3", p "_l4", p "_l5", p "_l6", p "_l7", p "_l8", p "_l9", \
+               p "_l10", p "_l11", p "_l12", p "_l13", p "_l14", p "_l15", p "_l16", p "_l17", p "_l18", \
+               p "_l19", p "_l20", p "_l21", p "_l22", p "_l23", p "_l24", p "_l25", p "_l26", p "_l27", \
+               p "_l28", p "_l29", p "_l30", p "_l31", p "_l32", p "_l33", p "_l34", p "_l35", p "_l36", \
+               p "_l37", p "_l38", p "_l39", p "_l40"}
+const char *const kLevelName[5][kMaxLevels + 1] = {LN("c_restrict_quant"), LN("c_solves"), LN("d_restrict_sym"),
+                                                   LN("d_solves"), LN("d_expand")};
+#undef LN
 
 template <typename T> const LevelGeom<T> &geom(const Plan *P, int l);
 template <> const LevelGeom<float> &geom<float>(const Plan *P, int l) { return P->gf[l]; }
@@ -161,15 +176,17 @@ hpdr_status compress_t(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, const
         memset(&a, 0, sizeof(a));
         a.g = geom<T>(P, l);
         a.v = v;
+        a.src_end = v + P->N[l];
+        a.status = &w.sc->status;
         a.qo = qo;
         a.b = (T *)w.b;
         a.vc = vc;
         {
-        ProfScope ps(ctx, l == L ? "c_restrict_quant_L" : "c_restrict_quant_coarse", s);
+        ProfScope ps(ctx, l == L ? "c_restrict_quant_L" : kLevelName[0][l], s);
         CK(launch_restrict<T>(WSrc::FIELD, Sink::QUANT, a, s));
         }
         {
-        ProfScope ps(ctx, l == L ? "c_solves_L" : "c_solves_coarse", s);
+        ProfScope ps(ctx, l == L ? "c_solves_L" : kLevelName[1][l], s);
         CK(launch_solves<T>(a.g, (T *)w.b, vc, +1, s));
         }
         v = vc;
@@ -187,6 +204,7 @@ hpdr_status compress_t(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, const
     ea.sym = w.sym; ea.N = (unsigned long long)N; ea.D = D; ea.K = K;
     ea.len = hs.len; ea.code = hs.code;
     ea.chunk_bits = w.chunk_bits; ea.chunk_esc = w.chunk_esc; ea.sc = w.sc;
+    ea.bsum = w.bsum; ea.besc = w.besc;
     ea.container = out; ea.L = L; ea.capacity = cap;
     ea.oidx_unordered = w.oidx; ea.ok_unordered = w.ok;
     {
@@ -320,6 +338,9 @@ hpdr_status decompress_t(hpdr_ctx *ctx, const Plan *P, const Hdr &h, const uint8
     si.out_k = (const long long *)(in + h.off_out + 8 * h.n_out);
     si.n_out = h.n_out;
     si.status = &w.sc->status;
+    si.K = h.K;
+    si.ochunk = w.chunk_bits;
+    CK(launch_outlier_chunks(si.out_idx, h.n_out, h.K, h.nch, w.chunk_bits, s));
     // level buffers: v_{l-1} in X, v_l written to Y (or to out at l = L)
     T *bufs[2] = {(T *)w.va, (T *)w.vb};
     T *v = L == 0 ? out : bufs[0];
@@ -330,18 +351,20 @@ hpdr_status decompress_t(hpdr_ctx *ctx, const Plan *P, const Hdr &h, const uint8
         memset(&a, 0, sizeof(a));
         a.g = g;
         a.symin = si;
+        a.src_end = w.sym + h.N + 8;
+        a.status = &w.sc->status;
         a.b = (T *)w.b;
         {
-        ProfScope ps(ctx, l == L ? "d_restrict_sym_L" : "d_restrict_sym_coarse", s);
+        ProfScope ps(ctx, l == L ? "d_restrict_sym_L" : kLevelName[2][l], s);
         CK(launch_restrict<T>(WSrc::SYMBOLS, Sink::NONE, a, s));
         }
         {
-        ProfScope ps(ctx, l == L ? "d_solves_L" : "d_solves_coarse", s);
+        ProfScope ps(ctx, l == L ? "d_solves_L" : kLevelName[3][l], s);
         CK(launch_solves<T>(g, (T *)w.b, v, -1, s));
         }
         T *dst = (l == L) ? out : bufs[l % 2];
         {
-        ProfScope ps(ctx, l == L ? "d_expand_L" : "d_expand_coarse", s);
+        ProfScope ps(ctx, l == L ? "d_expand_L" : kLevelName[4][l], s);
         CK(launch_expand<T>(WSrc::SYMBOLS, g, v, nullptr, si, dst, s));
         }
         v = dst;
@@ -362,6 +385,7 @@ hpdr_status decompose_t(hpdr_ctx *ctx, const Plan *P, const T *u, T *coef, cudaS
     carve_ws(ctx->ws.base, P, sizeof(T), 4, 128, false, &w);
     const int L = P->L;
     const T *v = u;
+    CK(cudaMemsetAsync(w.sc, 0, sizeof(Scalars), s));
     QuantOut qo;
     memset(&qo, 0, sizeof(qo));
     for (int l = L; l >= 1; l--) {
@@ -370,6 +394,8 @@ hpdr_status decompose_t(hpdr_ctx *ctx, const Plan *P, const T *u, T *coef, cudaS
         memset(&a, 0, sizeof(a));
         a.g = geom<T>(P, l);
         a.v = v;
+        a.src_end = v + P->N[l];
+        a.status = &w.sc->status;
         a.coef_out = coef;
         a.b = (T *)w.b;
         a.vc = vc;
@@ -479,6 +505,7 @@ hpdr_status hpdr_compress(hpdr_ctx *ctx, const void *d_in, hpdr_dtype dtype, int
     if ((dtype != HPDR_F32 && dtype != HPDR_F64) || (mode != HPDR_LINF && mode != HPDR_L2) ||
         (tol_kind != HPDR_ABS && tol_kind != HPDR_REL) || !(tol > 0.0) || !std::isfinite(tol))
         return HPDR_ERR_ARG;
+    if (((uintptr_t)d_in & 15) || ((uintptr_t)d_out & 15)) return HPDR_ERR_ARG;
     DevGuard g(ctx->device);
     Plan *P;
     hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P);
@@ -539,6 +566,7 @@ hpdr_status hpdr_decompose(hpdr_ctx *ctx, const void *d_u, void *d_coef, hpdr_dt
                            int ndim, const size_t *dims, void *stream)
 {
     if (!ctx || !d_u || !d_coef || (dtype != HPDR_F32 && dtype != HPDR_F64)) return HPDR_ERR_ARG;
+    if ((uintptr_t)d_u & 15) return HPDR_ERR_ARG;
     DevGuard g(ctx->device);
     Plan *P;
     hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P);
@@ -576,7 +604,8 @@ hpdr_status hpdr_huffman_encode(hpdr_ctx *ctx, const uint16_t *d_symbols, uint64
     unsigned long long nch = (N + K - 1) / K;
     Carver c(nullptr);
     c.take<Scalars>(1); c.take<unsigned long long>(D); c.take<unsigned long long>(nch + 2);
-    c.take<unsigned>(nch + 2); c.take<char>(huff_scratch_bytes(D));
+    c.take<unsigned>(nch + 2); c.take<unsigned long long>(1024); c.take<unsigned>(1024);
+    c.take<char>(huff_scratch_bytes(D));
     hpdr_status st = ensure_workspace(ctx, c.used + 256);
     if (st != HPDR_OK) return st;
     Carver w(ctx->ws.base);
@@ -584,6 +613,8 @@ hpdr_status hpdr_huffman_encode(hpdr_ctx *ctx, const uint16_t *d_symbols, uint64
     unsigned long long *hist = w.take<unsigned long long>(D);
     unsigned long long *cb = w.take<unsigned long long>(nch + 2);
     unsigned *ce = w.take<unsigned>(nch + 2);
+    unsigned long long *bs = w.take<unsigned long long>(1024);
+    unsigned *be = w.take<unsigned>(1024);
     void *hb = w.take<char>(huff_scratch_bytes(D));
     CK(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
     CK(cudaMemsetAsync(hist, 0, 8ULL * D, s));
@@ -594,7 +625,7 @@ hpdr_status hpdr_huffman_encode(hpdr_ctx *ctx, const uint16_t *d_symbols, uint64
     EncodeArgs ea;
     memset(&ea, 0, sizeof(ea));
     ea.sym = d_symbols; ea.N = N; ea.D = D; ea.K = K; ea.len = hs.len; ea.code = hs.code;
-    ea.chunk_bits = cb; ea.chunk_esc = ce; ea.sc = sc;
+    ea.chunk_bits = cb; ea.chunk_esc = ce; ea.sc = sc; ea.bsum = bs; ea.besc = be;
     ea.chunk_out = (unsigned long long *)d_chunk_bits;
     ea.words_out = d_words;
     ea.words_cap = words_capacity;

@@ -150,6 +150,18 @@ __device__ void length_tables(HuffScratch &hs, unsigned *cnt)
     }
     hs.count[0] = 0;
     if (!ok) atomicExch(hs.status, (unsigned)DS_FORMAT);
+    // left-justified limit of the codes of length <= L: (first_L + count_L) << (64 - L),
+    // with first_L from the canonical recurrence for every L
+    unsigned long long f = 0;
+    bool started = false;
+    for (int L = 1; L <= kMaxCodeLen; L++) {
+        if (started) f <<= 1;
+        if (cnt[L] && !started) { started = true; f = 0; }
+        const unsigned long long nxt = f + cnt[L];
+        hs.lim[L] = (nxt >= (1ULL << L)) ? ~0ULL : (nxt << (64 - L));
+        f = nxt;
+    }
+    hs.lim[0] = 0;
 }
 
 // code lengths from the frequency-sorted leaves, one block
@@ -314,6 +326,20 @@ __global__ void __launch_bounds__(256) lut_kernel(HuffScratch hs)
     }
 }
 
+__global__ void __launch_bounds__(256) len16_kernel(HuffScratch hs)
+{
+    const unsigned n = *hs.nsym;
+    if (*hs.status) return;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned long long k = hs.keys2[i];
+        const unsigned s = (unsigned)(k & 0xFFFFu), L = (unsigned)(k >> 16);
+        if (L == 0 || L > (unsigned)kLenBits) continue;
+        const unsigned base = (unsigned)(hs.code[s] << (kLenBits - L));
+        const unsigned span = 1u << (kLenBits - L);
+        for (unsigned e = 0; e < span; e++) hs.len16[base + e] = (uint8_t)L;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Encoder
 
@@ -333,17 +359,25 @@ __device__ __forceinline__ Layout container_layout(int L, unsigned s_lo, unsigne
     return y;
 }
 
+constexpr int kEncBlocks = 152 * 4;
+
+// bits and escapes of every chunk; block b owns the contiguous chunk range
+// [b*cpb, (b+1)*cpb) and also leaves the sums of its range in bsum/besc
 __global__ void __launch_bounds__(256) enc_count_kernel(EncodeArgs a)
 {
     extern __shared__ uint8_t slen[];
+    __shared__ unsigned long long wb[8];
+    __shared__ unsigned we[8];
     if (block_skip(&a.sc->status)) return;
     for (unsigned i = threadIdx.x; i < a.D; i += blockDim.x) slen[i] = a.len[i];
     __syncthreads();
     const unsigned long long nch = (a.N + a.K - 1) / a.K;
-    const unsigned lane = threadIdx.x & 31;
-    const unsigned long long wg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
-    for (unsigned long long c = wg; c < nch; c += nw) {
+    const unsigned long long cpb = (nch + gridDim.x - 1) / gridDim.x;
+    const unsigned long long c0 = blockIdx.x * cpb, c1 = c0 + cpb < nch ? c0 + cpb : nch;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long tb = 0;
+    unsigned te = 0;
+    for (unsigned long long c = c0 + warp; c < c1; c += blockDim.x >> 5) {
         const unsigned long long beg = c * a.K;
         const unsigned long long end = beg + a.K < a.N ? beg + a.K : a.N;
         unsigned long long bits = 0;
@@ -365,86 +399,134 @@ __global__ void __launch_bounds__(256) enc_count_kernel(EncodeArgs a)
         }
         bits = warp_sum64(bits);
         esc = warp_sum(esc);
-        if (lane == 0) { a.chunk_bits[c] = bits; a.chunk_esc[c] = esc; }
+        if (lane == 0) { a.chunk_bits[c] = bits; a.chunk_esc[c] = esc; tb += bits; te += esc; }
     }
-}
-
-// exclusive scan of the per-chunk bit counts and escapes, layout and capacity
-__global__ void __launch_bounds__(1024) enc_scan_kernel(EncodeArgs a)
-{
-    __shared__ unsigned long long sb[1024];
-    __shared__ unsigned se[1024];
-    __shared__ int ok;
-    __shared__ unsigned long long bits_total, wbase;
-    __shared__ uint32_t *words;
-    if (block_skip(&a.sc->status)) return;
-    const unsigned long long nch = (a.N + a.K - 1) / a.K;
-    const unsigned long long seg = (nch + 1023) / 1024;
-    const unsigned long long b0 = threadIdx.x * seg;
-    const unsigned long long b1 = b0 + seg < nch ? b0 + seg : nch;
-    unsigned long long bs = 0;
-    unsigned es = 0;
-    for (unsigned long long c = b0; c < b1; c++) { bs += a.chunk_bits[c]; es += a.chunk_esc[c]; }
-    sb[threadIdx.x] = bs;
-    se[threadIdx.x] = es;
+    if (lane == 0) { wb[warp] = tb; we[warp] = te; }
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long x = 0;
         unsigned y = 0;
-        for (int i = 0; i < 1024; i++) {
-            unsigned long long t = sb[i];
-            unsigned u = se[i];
-            sb[i] = x;
-            se[i] = y;
-            x += t;
-            y += u;
-        }
-        bits_total = x;
-        ok = 1;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) { x += wb[w]; y += we[w]; }
+        a.bsum[blockIdx.x] = x;
+        a.besc[blockIdx.x] = y;
+    }
+}
+
+// exclusive scan of the block sums (one block), container layout and capacity
+__global__ void __launch_bounds__(1024) enc_scan1_kernel(EncodeArgs a, int nb)
+{
+    __shared__ unsigned long long sb[1024];
+    __shared__ unsigned se[1024];
+    if (block_skip(&a.sc->status)) return;
+    const int t = threadIdx.x;
+    sb[t] = t < nb ? a.bsum[t] : 0;
+    se[t] = t < nb ? a.besc[t] : 0;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        unsigned long long x = t >= o ? sb[t - o] : 0;
+        unsigned y = t >= o ? se[t - o] : 0;
+        __syncthreads();
+        sb[t] += x;
+        se[t] += y;
+        __syncthreads();
+    }
+    // inclusive -> exclusive
+    if (t < nb) {
+        a.bsum[t] = t ? sb[t - 1] : 0;
+        a.besc[t] = t ? se[t - 1] : 0;
+    }
+    if (t == 0) {
+        const unsigned long long nch = (a.N + a.K - 1) / a.K;
+        const unsigned long long x = sb[1023];
+        const unsigned y = se[1023];
         if (a.container) {
             if ((unsigned long long)y != a.sc->n_out) atomicExch(&a.sc->status, (unsigned)DS_FORMAT);
             Layout lay = container_layout(a.L, a.sc->s_lo, a.sc->s_hi, nch, a.sc->n_out, x);
-            if (lay.total > a.capacity) { ok = 0; atomicExch(&a.sc->status, (unsigned)DS_CAPACITY); }
-            words = reinterpret_cast<uint32_t *>(a.container + lay.off_bits);
+            if (lay.total > a.capacity) atomicExch(&a.sc->status, (unsigned)DS_CAPACITY);
             a.sc->out_bytes = lay.total;
-            wbase = lay.off_chunk;
         } else {
-            if ((x + 31) / 32 > a.words_cap) { ok = 0; atomicExch(&a.sc->status, (unsigned)DS_CAPACITY); }
-            words = a.words_out;
-            wbase = 0;
+            if ((x + 31) / 32 > a.words_cap) atomicExch(&a.sc->status, (unsigned)DS_CAPACITY);
         }
         a.sc->total_bits = x;
     }
-    __syncthreads();
-    if (!ok) return;
-    unsigned long long *ctab = a.container ? reinterpret_cast<unsigned long long *>(a.container + wbase)
-                                           : a.chunk_out;
-    unsigned long long x = sb[threadIdx.x];
-    unsigned y = se[threadIdx.x];
-    for (unsigned long long c = b0; c < b1; c++) {
-        unsigned long long t = a.chunk_bits[c];
-        unsigned u = a.chunk_esc[c];
-        a.chunk_bits[c] = x;
-        a.chunk_esc[c] = y;
-        ctab[c] = x;
-        words[x >> 5] = 0u;   // first word of the chunk (shared with the previous one)
-        x += t;
-        y += u;
-    }
-    if (threadIdx.x == 0 && (bits_total & 31)) words[bits_total >> 5] = 0u;
-    if (threadIdx.x == 0) { a.chunk_bits[nch] = bits_total; }
 }
 
-__global__ void __launch_bounds__(kEncThreads) enc_write_kernel(EncodeArgs a)
+__device__ __forceinline__ uint32_t *enc_words(const EncodeArgs &a, unsigned long long nch)
+{
+    if (!a.container) return a.words_out;
+    Layout lay = container_layout(a.L, a.sc->s_lo, a.sc->s_hi, nch, a.sc->n_out, a.sc->total_bits);
+    return reinterpret_cast<uint32_t *>(a.container + lay.off_bits);
+}
+
+// chunk offsets within each block's range (plus the block's offset), chunk
+// table, and zeroed words where more than one writer will meet
+__global__ void __launch_bounds__(256) enc_scan2_kernel(EncodeArgs a)
+{
+    __shared__ unsigned long long sb[256];
+    __shared__ unsigned se[256];
+    if (block_skip(&a.sc->status)) return;
+    const unsigned long long nch = (a.N + a.K - 1) / a.K;
+    const unsigned long long cpb = (nch + gridDim.x - 1) / gridDim.x;
+    const unsigned long long c0 = blockIdx.x * cpb, c1 = c0 + cpb < nch ? c0 + cpb : nch;
+    uint32_t *words = enc_words(a, nch);
+    unsigned long long *ctab = a.chunk_out;
+    if (a.container) {
+        Layout lay = container_layout(a.L, a.sc->s_lo, a.sc->s_hi, nch, a.sc->n_out, a.sc->total_bits);
+        ctab = reinterpret_cast<unsigned long long *>(a.container + lay.off_chunk);
+    }
+    const unsigned long long total = a.sc->total_bits;
+    unsigned long long carry = a.bsum[blockIdx.x];
+    unsigned ecarry = a.besc[blockIdx.x];
+    const int t = threadIdx.x;
+    for (unsigned long long base = c0; base < c1; base += 256) {
+        const unsigned long long c = base + t;
+        unsigned long long v = c < c1 ? a.chunk_bits[c] : 0;
+        unsigned e = c < c1 ? a.chunk_esc[c] : 0;
+        sb[t] = v;
+        se[t] = e;
+        __syncthreads();
+        for (int o = 1; o < 256; o <<= 1) {
+            unsigned long long x = t >= o ? sb[t - o] : 0;
+            unsigned y = t >= o ? se[t - o] : 0;
+            __syncthreads();
+            sb[t] += x;
+            se[t] += y;
+            __syncthreads();
+        }
+        if (c < c1) {
+            const unsigned long long off = carry + sb[t] - v;
+            a.chunk_bits[c] = off;
+            a.chunk_esc[c] = ecarry + se[t] - e;
+            ctab[c] = off;
+            const unsigned long long cend = off + v;
+            // full chunks of K >= 1024 symbols share only their first word with the previous
+            // chunk; other chunks are written word by word with atomics: zero them
+            const bool full = (c + 1) * (unsigned long long)a.K <= a.N && a.K >= 1024;
+            if (full) {
+                words[off >> 5] = 0u;
+            } else {
+                for (unsigned long long w = off >> 5; w <= ((cend ? cend - 1 : 0) >> 5); w++) words[w] = 0u;
+            }
+            if (c + 1 == nch && (total & 31)) words[total >> 5] = 0u;
+        }
+        __syncthreads();
+        carry += sb[255];
+        ecarry += se[255];
+        __syncthreads();
+    }
+    if (blockIdx.x == 0 && t == 0) a.chunk_bits[nch] = total;
+}
+
+// one warp per chunk: every lane encodes K/32 consecutive symbols, assembling
+// its bits in a 64-bit register and storing whole words; the partial words
+// at lane boundaries are merged through shuffles (full chunks) or atomics
+__global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
 {
     extern __shared__ unsigned long long esm[];
-    __shared__ unsigned long long tb[kEncThreads];
-    __shared__ unsigned te[kEncThreads];
     if (block_skip(&a.sc->status)) return;
     const bool code_sm = a.D <= (unsigned)kSmemCodes;
-    unsigned long long *scode = esm;                                   // [D] if code_sm
+    unsigned long long *scode = esm;
     uint8_t *slen = reinterpret_cast<uint8_t *>(esm + (code_sm ? a.D : 0));
-    uint32_t *sw = reinterpret_cast<uint32_t *>(slen + ((a.D + 15) & ~15u));
     for (unsigned i = threadIdx.x; i < a.D; i += blockDim.x) {
         slen[i] = a.len[i];
         if (code_sm) scode[i] = a.code[i];
@@ -452,82 +534,104 @@ __global__ void __launch_bounds__(kEncThreads) enc_write_kernel(EncodeArgs a)
     __syncthreads();
     const unsigned long long *codes = code_sm ? scode : a.code;
     const unsigned long long nch = (a.N + a.K - 1) / a.K;
-    const unsigned spt = a.K / kEncThreads;
-    const unsigned long long nout = a.container ? a.sc->n_out : 0;
-    Layout lay;
-    uint32_t *words;
+    uint32_t *words = enc_words(a, nch);
     unsigned long long *oidx = nullptr;
     if (a.container) {
-        lay = container_layout(a.L, a.sc->s_lo, a.sc->s_hi, nch, nout, a.sc->total_bits);
-        words = reinterpret_cast<uint32_t *>(a.container + lay.off_bits);
+        Layout lay = container_layout(a.L, a.sc->s_lo, a.sc->s_hi, nch, a.sc->n_out, a.sc->total_bits);
         oidx = reinterpret_cast<unsigned long long *>(a.container + lay.off_out);
-    } else {
-        words = a.words_out;
     }
-    for (unsigned long long c = blockIdx.x; c < nch; c += gridDim.x) {
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned spl = a.K >> 5;
+    const unsigned long long wg = blockIdx.x * (unsigned long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long c = wg; c < nch; c += nw) {
         const unsigned long long beg = c * a.K;
         const unsigned long long end = beg + a.K < a.N ? beg + a.K : a.N;
-        unsigned long long m0 = beg + (unsigned long long)threadIdx.x * spt;
-        unsigned long long m1 = m0 + spt;
+        unsigned long long m0 = beg + (unsigned long long)lane * spl, m1 = m0 + spl;
         if (m0 > end) m0 = end;
         if (m1 > end) m1 = end;
         unsigned long long mb = 0;
         unsigned me = 0;
-        for (unsigned long long i = m0; i < m1; i++) { uint16_t s = a.sym[i]; mb += slen[s]; me += s == 0; }
-        tb[threadIdx.x] = mb;
-        te[threadIdx.x] = me;
-        __syncthreads();
-        if (threadIdx.x < 32) {   // exclusive scan of 128 entries by one warp
-            unsigned long long v[4];
-            unsigned u[4];
-            unsigned long long s = 0;
-            unsigned su = 0;
-            for (int k = 0; k < 4; k++) { v[k] = tb[threadIdx.x * 4 + k]; u[k] = te[threadIdx.x * 4 + k]; s += v[k]; su += u[k]; }
-            unsigned long long x = s;
-            unsigned xu = su;
-            for (int o = 1; o < 32; o <<= 1) {
-                unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-                unsigned yu = __shfl_up_sync(0xffffffffu, xu, o);
-                if ((int)threadIdx.x >= o) { x += y; xu += yu; }
+        // full lanes of 32 symbols keep them in registers (four 16-byte loads)
+        uint32_t rs[16];
+        const bool regs = (m1 - m0 == 32) && spl == 32;
+        if (regs) {
+            const uint4 *v = reinterpret_cast<const uint4 *>(a.sym + m0);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const uint4 x = v[q];
+                rs[4 * q] = x.x; rs[4 * q + 1] = x.y; rs[4 * q + 2] = x.z; rs[4 * q + 3] = x.w;
             }
-            x -= s;
-            xu -= su;
-            for (int k = 0; k < 4; k++) {
-                tb[threadIdx.x * 4 + k] = x; x += v[k];
-                te[threadIdx.x * 4 + k] = xu; xu += u[k];
+#pragma unroll
+            for (int q = 0; q < 32; q++) {
+                const unsigned sv = (rs[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+                mb += slen[sv];
+                me += sv == 0;
             }
+        } else {
+            for (unsigned long long i = m0; i < m1; i++) { const uint16_t s = a.sym[i]; mb += slen[s]; me += s == 0; }
         }
-        __syncthreads();
-        const unsigned long long start = a.chunk_bits[c];
-        const unsigned long long cend = a.chunk_bits[c + 1];
-        const unsigned so = (unsigned)(start & 31);
-        const unsigned long long wstart = start >> 5;
-        const unsigned nwl = (unsigned)((so + (cend - start) + 31) >> 5);
-        for (unsigned i = threadIdx.x; i < nwl + 2; i += blockDim.x) sw[i] = 0u;
-        __syncthreads();
-        unsigned long long b = so + tb[threadIdx.x];
-        unsigned ebase = a.chunk_esc[c] + te[threadIdx.x];
-        for (unsigned long long i = m0; i < m1; i++) {
-            uint16_t s = a.sym[i];
-            unsigned L = slen[s];
-            unsigned long long cw = codes[s];
-            unsigned w = (unsigned)(b >> 5), off = (unsigned)(b & 31);
-            unsigned long long hi64 = (off + L <= 64) ? (cw << (64 - off - L)) : (cw >> (off + L - 64));
-            atomicOr(&sw[w], (uint32_t)(hi64 >> 32));
-            uint32_t x1 = (uint32_t)hi64;
-            if (x1) atomicOr(&sw[w + 1], x1);
-            if (off + L > 64) atomicOr(&sw[w + 2], (uint32_t)(cw << (96 - off - L)));
-            b += L;
+        unsigned long long xb = mb;
+        unsigned xe = me;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long yb = __shfl_up_sync(0xffffffffu, xb, o);
+            const unsigned ye = __shfl_up_sync(0xffffffffu, xe, o);
+            if ((int)lane >= o) { xb += yb; xe += ye; }
+        }
+        const unsigned long long start = a.chunk_bits[c] + xb - mb;
+        unsigned ebase = a.chunk_esc[c] + xe - me;
+        unsigned long long acc = 0;
+        unsigned nacc = (unsigned)(start & 31);
+        unsigned long long widx = start >> 5;
+        const unsigned long long fidx = widx;
+        uint32_t firstw = 0;
+        bool have_first = false;
+        auto put = [&](uint16_t s, unsigned long long i) {
+            int L = slen[s];
+            const unsigned long long cw = codes[s];
             if (oidx && s == 0) oidx[ebase++] = i;
+            while (L > 0) {
+                const int take = L > 32 ? 32 : L;
+                const unsigned long long part = (cw >> (L - take)) & ((1ULL << take) - 1);
+                L -= take;
+                acc |= part << (64 - nacc - take);
+                nacc += take;
+                if (nacc >= 32) {
+                    const uint32_t wv = (uint32_t)(acc >> 32);
+                    if (!have_first) { firstw = wv; have_first = true; }
+                    else words[widx] = wv;
+                    widx++;
+                    acc <<= 32;
+                    nacc -= 32;
+                }
+            }
+        };
+        if (regs) {
+#pragma unroll
+            for (int q = 0; q < 32; q++) put((uint16_t)((rs[q >> 1] >> (16 * (q & 1))) & 0xFFFFu), m0 + q);
+        } else {
+            for (unsigned long long i = m0; i < m1; i++) put(a.sym[i], i);
         }
-        __syncthreads();
-        const bool tail_shared = ((so + (cend - start)) & 31) != 0;
-        for (unsigned i = threadIdx.x; i < nwl; i += blockDim.x) {
-            uint32_t v = sw[i];
-            if (i == 0 || (i == nwl - 1 && tail_shared)) { if (v) atomicOr(&words[wstart + i], v); }
-            else words[wstart + i] = v;
+        const uint32_t lastw = (uint32_t)(acc >> 32);
+        const bool has_last = nacc > 0;
+        const bool full = (end - beg == a.K) && spl >= 32;
+        if (full) {
+            // every lane holds >= 32 bits: lane i's last partial word is lane i+1's first word
+            const uint32_t prev = __shfl_up_sync(0xffffffffu, lastw, 1);
+            const bool sh = (start & 31) != 0;
+            if (lane > 0 && sh) firstw |= prev;
+            if (have_first) {
+                if (lane == 0 && sh) atomicOr(&words[fidx], firstw);
+                else words[fidx] = firstw;
+            }
+            if (lane == 31 && has_last) atomicOr(&words[widx], lastw);
+        } else {
+            if (have_first) {
+                if (start & 31) atomicOr(&words[fidx], firstw);
+                else words[fidx] = firstw;
+            }
+            if (has_last) atomicOr(&words[widx], lastw);
         }
-        __syncthreads();
     }
 }
 
@@ -614,19 +718,51 @@ __device__ __forceinline__ uint32_t ldw(const uint32_t *w, unsigned long long i,
     return i < n ? __ldg(w + i) : 0u;
 }
 
-__global__ void __launch_bounds__(256) decode_kernel(DecodeArgs a, HuffScratch hs)
+// four words from an aligned block index (words past n read as zero)
+__device__ __forceinline__ uint4 ld4(const uint32_t *w, unsigned long long i, unsigned long long n)
 {
-    __shared__ uint32_t lut[1 << kLutBits];
-    __shared__ unsigned long long sfirst[kMaxCodeLen + 1];
-    __shared__ unsigned scount[kMaxCodeLen + 1], sstart[kMaxCodeLen + 1];
+    if (i + 4 <= n && ((reinterpret_cast<uintptr_t>(w) & 15) == 0))
+        return __ldg(reinterpret_cast<const uint4 *>(w + i));
+    uint4 v;
+    v.x = ldw(w, i, n); v.y = ldw(w, i + 1, n); v.z = ldw(w, i + 2, n); v.w = ldw(w, i + 3, n);
+    return v;
+}
+
+// Decoder: one thread per chunk.  A table of 2^16 bytes gives the code length
+// of every 16-bit prefix (canonical codes make the length a function of the
+// prefix); longer codes count the limits they exceed, without branches.  The
+// symbol is then sorted_sym[start[L] + code - first[L]].
+constexpr int kDecSymSmem = 8192;
+
+__global__ void __launch_bounds__(256, 4) decode_kernel(DecodeArgs a, HuffScratch hs)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    uint8_t *len16 = dsm;                                                     // [1 << kLenBits]
+    unsigned long long *sfirst = reinterpret_cast<unsigned long long *>(dsm + (1 << kLenBits));  // [64]
+    unsigned long long *slim = sfirst + 64;                                   // [64]
+    unsigned *sstart = reinterpret_cast<unsigned *>(slim + 64);               // [64]
+    unsigned *scount = sstart + 64;                                           // [64]
+    uint16_t *ssym = reinterpret_cast<uint16_t *>(scount + 64);               // [kDecSymSmem]
     if (block_skip(hs.status)) return;
-    for (int i = threadIdx.x; i < (1 << kLutBits); i += blockDim.x) lut[i] = hs.lut[i];
-    for (int i = threadIdx.x; i <= kMaxCodeLen; i += blockDim.x) {
-        sfirst[i] = hs.first[i];
-        scount[i] = hs.count[i];
-        sstart[i] = hs.start[i];
+    const unsigned nsym = *hs.nsym;
+    const bool sym_sm = nsym <= (unsigned)kDecSymSmem;
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(hs.len16);
+        uint4 *dst = reinterpret_cast<uint4 *>(len16);
+        for (int i = threadIdx.x; i < (1 << kLenBits) / 16; i += blockDim.x) dst[i] = src[i];
     }
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+        sfirst[i] = hs.first[i];
+        slim[i] = hs.lim[i];
+        sstart[i] = hs.start[i];
+        scount[i] = hs.count[i];
+    }
+    if (sym_sm)
+        for (unsigned i = threadIdx.x; i < nsym; i += blockDim.x) ssym[i] = hs.sorted_sym[i];
     __syncthreads();
+    const uint16_t *symtab = sym_sm ? ssym : hs.sorted_sym;
+    int maxL = 0;
+    for (int L = kMaxCodeLen; L >= 1; L--) if (scount[L]) { maxL = L; break; }
     const unsigned long long nch = (a.N + a.K - 1) / a.K;
     for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < nch;
          c += (unsigned long long)gridDim.x * blockDim.x) {
@@ -636,43 +772,53 @@ __global__ void __launch_bounds__(256) decode_kernel(DecodeArgs a, HuffScratch h
             atomicExch(hs.status, (unsigned)DS_FORMAT);
             continue;
         }
-        unsigned long long wi = pos >> 5;
+        // words arrive 16 bytes at a time, one aligned block ahead of use:
+        // w0..w2 hold the window, pa the rest of the current block, pb the next
+        const unsigned long long wb0 = (pos >> 5) & ~3ULL;   // aligned block of the first word
+        uint4 pa = ld4(a.words, wb0, a.nwords), pb = ld4(a.words, wb0 + 4, a.nwords);
+        unsigned k = (unsigned)((pos >> 5) & 3);             // next word of pa to shift in
+        unsigned long long nxt = wb0 + 8;                    // next block to fetch
+        auto take = [&]() -> uint32_t {
+            const uint32_t v = k == 0 ? pa.x : k == 1 ? pa.y : k == 2 ? pa.z : pa.w;
+            if (++k == 4) { k = 0; pa = pb; pb = ld4(a.words, nxt, a.nwords); nxt += 4; }
+            return v;
+        };
+        uint32_t w0 = take(), w1 = take(), w2 = take();
         unsigned sh = (unsigned)(pos & 31);
-        uint32_t w0 = ldw(a.words, wi, a.nwords), w1 = ldw(a.words, wi + 1, a.nwords),
-                 w2 = ldw(a.words, wi + 2, a.nwords);
         const unsigned long long beg = c * a.K;
         const unsigned long long end = beg + a.K < a.N ? beg + a.K : a.N;
-        uint16_t buf[8];
         bool bad = false;
-        for (unsigned long long i = beg; i < end; i++) {
+        auto step = [&]() -> uint16_t {
             unsigned long long win = (((unsigned long long)w0 << 32) | w1) << sh;
             if (sh) win |= (unsigned long long)(w2 >> (32 - sh));
-            uint32_t e = lut[win >> (64 - kLutBits)];
-            unsigned L = e >> 16, s = e & 0xFFFFu;
+            unsigned L = len16[win >> (64 - kLenBits)];
             if (L == 0) {
-                for (L = kLutBits + 1; L <= (unsigned)kMaxCodeLen; L++) {
-                    unsigned long long v = win >> (64 - L);
-                    if (scount[L] && v >= sfirst[L] && v - sfirst[L] < scount[L]) {
-                        s = hs.sorted_sym[sstart[L] + (unsigned)(v - sfirst[L])];
-                        break;
-                    }
-                }
-                if (L > (unsigned)kMaxCodeLen) { bad = true; L = 1; s = 0; }
+                L = kLenBits + 1;
+                for (int l = kLenBits + 1; l < maxL; l++) L += (win >= slim[l]) ? 1u : 0u;
             }
+            const unsigned long long code = win >> (64 - L);
+            const unsigned long long off = code - sfirst[L];
+            if (off >= scount[L]) bad = true;
+            const unsigned idx = sstart[L] + (unsigned)(off < scount[L] ? off : 0);
+            const uint16_t sv = symtab[idx < nsym ? idx : 0];
             pos += L;
             sh += L;
-            while (sh >= 32) { sh -= 32; w0 = w1; w1 = w2; wi++; w2 = ldw(a.words, wi + 2, a.nwords); }
-            buf[(i - beg) & 7] = (uint16_t)s;
-            if (((i - beg) & 7) == 7) {
-                uint4 v;
-                uint16_t *vp = reinterpret_cast<uint16_t *>(&v);
-#pragma unroll
-                for (int k = 0; k < 8; k++) vp[k] = buf[k];
-                *reinterpret_cast<uint4 *>(a.sym + (i - 7)) = v;
+            if (sh >= 32) {
+                sh -= 32; w0 = w1; w1 = w2; w2 = take();
+                if (sh >= 32) { sh -= 32; w0 = w1; w1 = w2; w2 = take(); }
             }
+            return sv;
+        };
+        unsigned long long i = beg;
+        for (; i + 8 <= end; i += 8) {
+            uint4 v;
+            v.x = step(); v.x |= (unsigned)step() << 16;
+            v.y = step(); v.y |= (unsigned)step() << 16;
+            v.z = step(); v.z |= (unsigned)step() << 16;
+            v.w = step(); v.w |= (unsigned)step() << 16;
+            *reinterpret_cast<uint4 *>(a.sym + i) = v;
         }
-        const unsigned long long tail = (end - beg) & 7;
-        for (unsigned long long k = 0; k < tail; k++) a.sym[end - tail + k] = buf[k];
+        for (; i < end; i++) a.sym[i] = step();
         if (bad || pos != expect) atomicExch(hs.status, (unsigned)DS_FORMAT);
     }
 }
@@ -709,6 +855,8 @@ cudaError_t set_attrs()
         e = cudaFuncSetAttribute(enc_write_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(enc_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
     if (e == cudaSuccess) g_attr_done = true;
     return e;
 }
@@ -725,6 +873,7 @@ size_t huff_scratch_bytes(unsigned int D)
     add(8 * d); add(8 * d);                            // leafw, intw
     add(4); add(8 * 64); add(4 * 64); add(4 * 64);     // nsym, first, count, start
     add(d); add(8 * d); add(2 * d); add(4u << kLutBits);
+    add(1u << kLenBits); add(8 * 64);
     return b;
 }
 
@@ -750,6 +899,8 @@ void huff_scratch_carve(void *base, unsigned int D, Scalars *sc, HuffScratch *hs
     hs->code = (unsigned long long *)take(8 * d);
     hs->sorted_sym = (uint16_t *)take(2 * d);
     hs->lut = (uint32_t *)take(4u << kLutBits);
+    hs->len16 = (uint8_t *)take(1u << kLenBits);
+    hs->lim = (unsigned long long *)take(8 * 64);
     hs->status = &sc->status;
     hs->s_lo = &sc->s_lo;
     hs->s_hi = &sc->s_hi;
@@ -778,9 +929,9 @@ cudaError_t launch_decode_tables(const uint8_t *len, unsigned int D, const HuffS
     length_count_kernel<<<1, 1024, 0, s>>>(hs);
     rank_kernel<<<kRankBlocks, 256, kSmemKeys * 8, s>>>(hs.keys2, hs.nsym, nullptr, hs.rank);
     assign_kernel<<<64, 256, 0, s>>>(hs);
-    e = cudaMemsetAsync(hs.lut, 0, 4u << kLutBits, s);
+    e = cudaMemsetAsync(hs.len16, 0, 1u << kLenBits, s);
     if (e != cudaSuccess) return e;
-    lut_kernel<<<64, 256, 0, s>>>(hs);
+    len16_kernel<<<64, 256, 0, s>>>(hs);
     count_launch(5);
     return cudaGetLastError();
 }
@@ -789,14 +940,14 @@ cudaError_t launch_encode(const EncodeArgs &a, cudaStream_t s)
 {
     cudaError_t e = set_attrs();
     if (e != cudaSuccess) return e;
-    enc_count_kernel<<<152 * 4, 256, a.D, s>>>(a);
-    enc_scan_kernel<<<1, 1024, 0, s>>>(a);
+    enc_count_kernel<<<kEncBlocks, 256, a.D, s>>>(a);
+    enc_scan1_kernel<<<1, 1024, 0, s>>>(a, kEncBlocks);
+    enc_scan2_kernel<<<kEncBlocks, 256, 0, s>>>(a);
     const bool code_sm = a.D <= (unsigned)kSmemCodes;
-    size_t words = ((size_t)a.K * kMaxCodeLen + 31) / 32 + 4;
-    size_t sm = (code_sm ? 8 * (size_t)a.D : 0) + ((a.D + 15) & ~15u) + 4 * words;
-    enc_write_kernel<<<152 * 4, kEncThreads, sm, s>>>(a);
+    size_t sm = (code_sm ? 8 * (size_t)a.D : 0) + ((a.D + 15) & ~15u);
+    enc_write_kernel<<<152 * 3, 256, sm, s>>>(a);
     if (a.container) outlier_place_kernel<<<152, 256, 0, s>>>(a);
-    count_launch(a.container ? 4 : 3);
+    count_launch(a.container ? 5 : 4);
     return cudaGetLastError();
 }
 
@@ -824,7 +975,10 @@ cudaError_t launch_histogram(const uint16_t *sym, unsigned long long N, unsigned
 
 cudaError_t launch_decode(const DecodeArgs &a, const HuffScratch &hs, cudaStream_t s)
 {
-    decode_kernel<<<152 * 4, 256, 0, s>>>(a, hs);
+    cudaError_t e = set_attrs();
+    if (e != cudaSuccess) return e;
+    const size_t sm = (1u << kLenBits) + 64 * 8 * 2 + 64 * 4 * 2 + kDecSymSmem * 2;
+    decode_kernel<<<152 * 4, 256, sm, s>>>(a, hs);
     count_launch();
     return cudaGetLastError();
 }

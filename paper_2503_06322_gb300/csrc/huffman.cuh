@@ -5,6 +5,7 @@
 namespace hpdr {
 
 constexpr int kLutBits = 12;
+constexpr int kLenBits = 15;    // decoder: code length of every 15-bit prefix
 constexpr int kMaxCodeLen = 63;
 
 // Device scratch of one codebook build (sizes for an alphabet of D symbols).
@@ -26,6 +27,8 @@ struct HuffScratch {
     unsigned long long *code;     // [D]
     uint16_t *sorted_sym;         // [D]
     uint32_t *lut;                // [1 << kLutBits]
+    uint8_t *len16;               // [1 << kLenBits] code length of a 16-bit prefix (0: longer)
+    unsigned long long *lim;      // [64] left-justified upper limit of the codes of each length
     unsigned int *status;         // -> Scalars::status
     unsigned int *s_lo, *s_hi;    // -> Scalars
 };
@@ -51,6 +54,8 @@ struct EncodeArgs {
     const unsigned long long *code;
     unsigned long long *chunk_bits;   // ws [nch+1] totals then offsets
     unsigned int *chunk_esc;          // ws [nch+1]
+    unsigned long long *bsum;         // ws [kEncBlocks] per-block sums, then offsets
+    unsigned int *besc;               // ws [kEncBlocks]
     Scalars *sc;
     // destination
     uint8_t *container;               // if non-null: chunk table, outliers, bits go into the container

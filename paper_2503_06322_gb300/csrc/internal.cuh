@@ -29,6 +29,7 @@ struct DimTables {
     const T *inv_den;   // [mc] 1 / pivot
     const T *etap;      // [m*3] (M_l P): fine node p <- coarse nodes jfirst(p)..+2
     const int *efirst;  // [m] first coarse index of etap's three taps
+    const T *mtap;      // [mc*3] rows of M_{l-1}: (sub, diag, super) of coarse node j
 };
 
 template <typename T>
@@ -84,7 +85,58 @@ enum DeviceStatus : unsigned int {
     DS_CAPACITY = 3,     // output too small / outlier list full
     DS_FORMAT = 4,       // invalid stream on decode
     DS_LENGTH = 5,       // a code length above 63
+    DS_TIMEOUT = 6,      // a bounded device-side wait gave up
 };
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (global -> shared) completed on an mbarrier.
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the phase with the given parity; gives up after `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t parity, int limit)
+{
+    for (int i = 0; i < limit; i++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// 16-byte aligned source, destination and size.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+constexpr int kWaitPolls = 1 << 20;
 
 // ---------------------------------------------------------------------------
 // Plans: hierarchy + device tables for one (shape, dtype).

@@ -16,6 +16,7 @@
 // The result does not depend on the tiling: every coarse value sums its taps
 // in a fixed order.
 #include <cfloat>
+#include <type_traits>
 #include "levels.cuh"
 
 namespace hpdr {
@@ -30,10 +31,11 @@ constexpr int kNormBlocks = 152 * 8;
 template <typename T>
 __device__ __forceinline__ long long quant_code(T x, T rho)
 {
+    // k = sign(x) floor(|x| rho + 1/2), every operation rounded in T
     T ax = x < (T)0 ? -x : x;
     T y = mul_rn(ax, rho);
     T t = add_rn(y, (T)0.5);
-    long long k = (long long)floor(t);
+    long long k = (t < (T)1073741824) ? (long long)(int)floor(t) : (long long)floor(t);
     return x < (T)0 ? -k : k;
 }
 
@@ -56,6 +58,24 @@ __device__ __forceinline__ long long stream_rank(const LevelGeom<T> &g, int p0, 
         if (kept_pos((int)m1, p1)) cr += kept_before(p2);
     }
     return g.Nprev + flat - cr;
+}
+
+// Stream index of the new nodes of row (p0, p1) of level l:
+//   every node new (p0 or p1 new):        base + p2
+//   p0 and p1 kept (only odd p2 new):     base + (p2 - 1) / 2
+template <typename T>
+__device__ __forceinline__ long long row_base(const LevelGeom<T> &g, long long plane_base, bool k0,
+                                              int p1)
+{
+    const long long m2 = g.dim[2].m, mc2 = g.dim[2].mc;
+    return plane_base + (long long)p1 * m2 - (k0 ? (long long)kept_before(p1) * mc2 : 0LL);
+}
+template <typename T>
+__device__ __forceinline__ long long plane_base_of(const LevelGeom<T> &g, int p0)
+{
+    const long long m1 = g.dim[1].m, m2 = g.dim[2].m;
+    const long long mc1 = g.dim[1].mc, mc2 = g.dim[2].mc;
+    return g.Nprev + (long long)p0 * m1 * m2 - (long long)kept_before(p0) * mc1 * mc2;
 }
 
 // quantize one coefficient into the symbol stream (+ block histogram / outliers)
@@ -83,28 +103,38 @@ __device__ __forceinline__ void quant_emit(const QuantOut &qo, unsigned int *hs,
     else atomicAdd(&qo.hist[sym], 1ULL);
 }
 
+// k of an escaped symbol: outliers are sorted by stream index; ochunk[c] is
+// the first outlier of chunk c (stream indices [c*K, (c+1)*K)).
+__device__ __noinline__ long long outlier_code(const unsigned long long *out_idx, const long long *out_k,
+                                               unsigned long long n_out, const unsigned long long *ochunk,
+                                               unsigned K, unsigned *status, long long idx)
+{
+    unsigned long long lo = 0, hi = n_out;
+    if (ochunk) {
+        unsigned long long c = (unsigned long long)idx / K;
+        lo = ochunk[c];
+        hi = ochunk[c + 1];
+    }
+    while (lo < hi) {
+        unsigned long long mid = (lo + hi) >> 1;
+        if (out_idx[mid] < (unsigned long long)idx) lo = mid + 1; else hi = mid;
+    }
+    if (lo < n_out && out_idx[lo] == (unsigned long long)idx) return out_k[lo];
+    atomicExch(status, (unsigned int)DS_FORMAT);
+    return 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T dequant_sym(const SymIn &si_, unsigned s, long long idx, T q)
+{
+    if (s != 0) return mul_rn((T)((int)s - (int)(si_.D / 2)), q);
+    return mul_rn((T)outlier_code(si_.out_idx, si_.out_k, si_.n_out, si_.ochunk, si_.K, si_.status, idx), q);
+}
+
 template <typename T>
 __device__ __forceinline__ T dequant(const SymIn &si_, long long idx, int level)
 {
-    unsigned int s = si_.sym[idx];
-    long long k;
-    if (s != 0) {
-        k = (long long)s - (long long)(si_.D / 2);
-    } else {
-        // outliers are sorted by stream index
-        unsigned long long lo = 0, hi = si_.n_out;
-        while (lo < hi) {
-            unsigned long long mid = (lo + hi) >> 1;
-            if (si_.out_idx[mid] < (unsigned long long)idx) lo = mid + 1; else hi = mid;
-        }
-        if (lo < si_.n_out && si_.out_idx[lo] == (unsigned long long)idx) {
-            k = si_.out_k[lo];
-        } else {
-            atomicExch(si_.status, (unsigned int)DS_FORMAT);
-            k = 0;
-        }
-    }
-    return mul_rn((T)k, q_of<T>(si_.sc, level));
+    return dequant_sym<T>(si_, si_.sym[idx], idx, q_of<T>(si_.sc, level));
 }
 
 template <typename T>
@@ -115,10 +145,37 @@ __device__ __forceinline__ int first_coarse_at_or_after(const DimTables<T> &d, i
     return j < d.mc ? j : d.mc - 1;
 }
 
+constexpr int NST = 4;   // planes in flight per CTA
+
+template <typename E>
+__host__ __device__ constexpr int row_pitch_bytes() { return ((RR2 * (int)sizeof(E) + 32) + 15) & ~15; }
+
+// Per-plane dim-0 restriction info: the first coarse index whose five-tap
+// window contains the plane, and the taps of the three candidates.
+template <typename T>
+struct PlaneTaps {
+    int jlo;
+    T t[3];
+};
+
+// The planes the restriction streams through come from global memory by
+// bulk asynchronous row copies (one per region row, 16-byte aligned around
+// the row), completed on one mbarrier per stage.  E = element type of the
+// staged rows (T for FIELD, uint16_t for SYMBOLS).
+//
+// FIELD source: the multilinear interpolant is applied separably.  For every
+// kept plane the CTA forms J = I_1 I_2 v (interpolation along dims 2 and 1 of
+// that plane) once; the new-node coefficients are then
+//     kept plane:  w = v - J(p0)                       (new nodes only)
+//     new plane:   w = v - (wl0 J(p0-1) + wr0 J(p0+1)).
 template <typename T, int SRC, int SINK>
-__global__ void __launch_bounds__(RTHREADS)
+__global__ void __launch_bounds__(RTHREADS, 3)
 restrict_kernel(RestrictArgs<T> a, int seg_len)
 {
+    typedef typename std::conditional<SRC == (int)WSrc::SYMBOLS, uint16_t, T>::type E;
+    constexpr bool STAGED = (SRC == (int)WSrc::FIELD || SRC == (int)WSrc::SYMBOLS);
+    constexpr bool FIELD = (SRC == (int)WSrc::FIELD);
+    constexpr int PB = row_pitch_bytes<E>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int m0 = a.g.dim[0].m, m1 = a.g.dim[1].m, m2 = a.g.dim[2].m;
     const int mc0 = a.g.dim[0].mc, mc1 = a.g.dim[1].mc, mc2 = a.g.dim[2].mc;
@@ -138,13 +195,17 @@ restrict_kernel(RestrictArgs<T> a, int seg_len)
     const int o1a = cpos_of(m1, mc1, J1), o1b = (J1 + n1 < mc1) ? cpos_of(m1, mc1, J1 + n1) : m1;
     const int o0a = cpos_of(m0, mc0, J0a), o0b = (J0b < mc0) ? cpos_of(m0, mc0, J0b) : m0;
 
-    T *V = reinterpret_cast<T *>(smem_raw);                 // [3][RR1][RR2] (FIELD)
-    T *W = V + (SRC == (int)WSrc::FIELD ? 3 * RR1 * RR2 : 0);  // [RR1][RR2]
-    T *R2s = W + RR1 * RR2;                                // [RR1][TT2]
-    T *tap2s = R2s + RR1 * TT2;                            // [TT2*5]
-    T *tap1s = tap2s + TT2 * 5;                            // [TT1*5]
-    T *wl2s = tap1s + TT1 * 5, *wr2s = wl2s + RR2;         // [RR2]
-    T *wl1s = wr2s + RR2, *wr1s = wl1s + RR1;              // [RR1]
+    // shared memory layout
+    unsigned char *stage_base = smem_raw;
+    int *rowoff = reinterpret_cast<int *>(smem_raw + (STAGED ? NST * RR1 * PB : 0));
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(
+        (reinterpret_cast<uintptr_t>(rowoff + (STAGED ? NST * RR1 : 0)) + 15) & ~uintptr_t(15));
+    PlaneTaps<T> *ptaps = reinterpret_cast<PlaneTaps<T> *>(mbar + (STAGED ? NST : 0));  // [NST]
+    T *W = reinterpret_cast<T *>(ptaps + NST);                       // [RR1][RR2]
+    T *Jb = W + RR1 * RR2;                                           // [2][RR1][RR2] (FIELD)
+    T *R2s = Jb + (FIELD ? 2 * RR1 * RR2 : 0);                       // [RR1][TT2]
+    T *wl2s = R2s + RR1 * TT2, *wr2s = wl2s + RR2;                   // [RR2]
+    T *wl1s = wr2s + RR2, *wr1s = wl1s + RR1;                        // [RR1]
     unsigned int *hs = reinterpret_cast<unsigned int *>(wr1s + RR1);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -152,95 +213,214 @@ restrict_kernel(RestrictArgs<T> a, int seg_len)
     const T *tap2src = a.use_ptap ? a.g.dim[2].ptap : a.g.dim[2].tap;
     const T *tap1src = a.use_ptap ? a.g.dim[1].ptap : a.g.dim[1].tap;
     const T *tap0src = a.use_ptap ? a.g.dim[0].ptap : a.g.dim[0].tap;
-    for (int i = tid; i < n2 * 5; i += RTHREADS) tap2s[i] = tap2src[J2 * 5 + i];
-    for (int i = tid; i < n1 * 5; i += RTHREADS) tap1s[i] = tap1src[J1 * 5 + i];
     for (int i = tid; i < r2n; i += RTHREADS) { wl2s[i] = a.g.dim[2].wl[lo2 + i]; wr2s[i] = a.g.dim[2].wr[lo2 + i]; }
     for (int i = tid; i < r1n; i += RTHREADS) { wl1s[i] = a.g.dim[1].wl[lo1 + i]; wr1s[i] = a.g.dim[1].wr[lo1 + i]; }
     if (smem_hist)
         for (int i = tid; i < (int)a.qo.D; i += RTHREADS) hs[i] = 0u;
+    if (STAGED && tid == 0) {
+        for (int i = 0; i < NST; i++) mbar_init(&mbar[i], 1);
+        mbar_fence_init();
+    }
+    // restriction taps of this thread's dim-2 column (phase C) and output (phase D)
+    const int jl = lane;                    // dim-2 coarse column in the tile
+    T t2[5], t1[5];
+    const int c2col = jl < n2 ? cpos_of(m2, mc2, J2 + jl) - lo2 : 0;
+#pragma unroll
+    for (int o = 0; o < 5; o++) t2[o] = jl < n2 ? tap2src[(J2 + jl) * 5 + o] : (T)0;
+    const int j1l = warp;
+    const bool outp = j1l < n1 && lane < n2;
+    const int c1r = outp ? cpos_of(m1, mc1, J1 + j1l) - lo1 : 0;
+#pragma unroll
+    for (int o = 0; o < 5; o++) t1[o] = outp ? tap1src[(J1 + j1l) * 5 + o] : (T)0;
+    __syncthreads();
 
     T rho = (T)0;
     if (SINK == (int)Sink::QUANT) rho = rho_of<T>(a.qo.sc, a.g.level);
+    T qlev = (T)0;
+    if (SRC == (int)WSrc::SYMBOLS) qlev = q_of<T>(a.symin.sc, a.g.level);
+    const float inv_r2n = 1.0f / (float)r2n;
 
-    auto load_plane = [&](int p) {
-        T *dst = V + (p % 3) * RR1 * RR2;
-        const T *src = a.v + ((long long)p * m1 + lo1) * m2 + lo2;
-        for (int i1 = warp; i1 < r1n; i1 += RTHREADS / 32) {
-            const T *row = src + (long long)i1 * m2;
-            for (int i2 = lane; i2 < r2n; i2 += 32) dst[i1 * RR2 + i2] = row[i2];
-        }
-    };
-    if (SRC == (int)WSrc::FIELD) load_plane(lo0);
-
-    // per-thread output (j1l, j2l) and its dim-0 accumulators
-    const int j1l = tid >> 5, j2l = tid & 31;
-    const bool outp = j1l < n1 && j2l < n2;
-    const int c1r = outp ? cpos_of(m1, mc1, J1 + j1l) - lo1 : 0;
-    const int c2r = outp ? cpos_of(m2, mc2, J2 + j2l) - lo2 : 0;
-    T acc0 = 0, acc1 = 0, acc2 = 0;
-    int jb = J0a;
-    const long long out_col = (long long)(J1 + j1l) * mc2 + (J2 + j2l);
-
-    for (int p0 = lo0; p0 <= hi0; p0++) {
-        if (SRC == (int)WSrc::FIELD && p0 + 1 <= hi0) load_plane(p0 + 1);
-        __syncthreads();
-        // ---- B: w on the region --------------------------------------------
-        const bool f0 = !kept_pos(m0, p0);
-        const bool own0 = p0 >= o0a && p0 < o0b;
-        const int s0 = p0 % 3, sm = (p0 + 2) % 3, sp = (p0 + 1) % 3;
-        T wl0 = (T)0, wr0 = (T)0;
-        if (SRC == (int)WSrc::FIELD && f0) { wl0 = a.g.dim[0].wl[p0]; wr0 = a.g.dim[0].wr[p0]; }
-        for (int i1 = warp; i1 < r1n; i1 += RTHREADS / 32) {
-            const int p1 = lo1 + i1;
-            const bool f1 = !kept_pos(m1, p1);
-            const bool own01 = own0 && p1 >= o1a && p1 < o1b;
-            for (int i2 = lane; i2 < r2n; i2 += 32) {
-                const int p2 = lo2 + i2;
-                const bool f2 = !kept_pos(m2, p2);
-                const bool isnew = f0 || f1 || f2;
-                T w = (T)0;
-                if (SRC == (int)WSrc::FIELD) {
-                    const T *P0 = V + s0 * RR1 * RR2;
-                    if (isnew) {
-                        auto val = [&](int s, int r) -> T {
-                            const T *row = V + (s * RR1 + r) * RR2;
-                            if (f2) return fma_rn(wr2s[i2], row[i2 + 1], mul_rn(wl2s[i2], row[i2 - 1]));
-                            return row[i2];
-                        };
-                        auto pl = [&](int s) -> T {
-                            if (f1) return fma_rn(wr1s[i1], val(s, i1 + 1), mul_rn(wl1s[i1], val(s, i1 - 1)));
-                            return val(s, i1);
-                        };
-                        T lerp = f0 ? fma_rn(wr0, pl(sp), mul_rn(wl0, pl(sm))) : pl(s0);
-                        w = sub_rn(P0[i1 * RR2 + i2], lerp);
-                        if (SINK != (int)Sink::NONE && own01 && p2 >= o2a && p2 < o2b) {
-                            long long si = stream_rank(a.g, p0, p1, p2);
-                            if (SINK == (int)Sink::STREAM) a.coef_out[si] = w;
-                            else quant_emit(a.qo, hs, smem_hist, si, w, rho);
-                        }
-                    }
-                } else if (SRC == (int)WSrc::STREAM) {
-                    if (isnew) w = a.coef_in[stream_rank(a.g, p0, p1, p2)];
-                } else if (SRC == (int)WSrc::SYMBOLS) {
-                    if (isnew) w = dequant<T>(a.symin, stream_rank(a.g, p0, p1, p2), a.g.level);
-                } else {  // DENSE
-                    if (isnew || !a.dense_new_only) w = a.v[((long long)p0 * m1 + p1) * m2 + p2];
-                }
-                W[i1 * RR2 + i2] = w;
+    // ---- producer: warp 0 issues the row copies of plane p ------------------
+    auto issue = [&](int p) {
+        const int slot = (p - lo0) % NST;
+        unsigned char *dst0 = stage_base + slot * RR1 * PB;
+        const bool k0 = kept_pos(m0, p);
+        const long long pb = (SRC == (int)WSrc::SYMBOLS) ? plane_base_of(a.g, p) : 0;
+        uint32_t bytes = 0;
+        const unsigned char *src = nullptr;
+        if (lane < r1n) {
+            const int p1 = lo1 + lane;
+            uintptr_t g0, g1;   // byte range [g0, g1) of the row's data
+            if (FIELD) {
+                const T *row = a.v + ((long long)p * m1 + p1) * m2 + lo2;
+                g0 = reinterpret_cast<uintptr_t>(row);
+                g1 = g0 + (uintptr_t)r2n * sizeof(T);
+            } else {
+                const bool rownew = !k0 || !kept_pos(m1, p1);
+                const long long rb = row_base(a.g, pb, k0, p1);
+                const long long first = rownew ? rb + lo2 : rb + (lo2 >> 1);
+                const int cnt = rownew ? r2n : ((hi2 - lo2) >> 1);
+                g0 = reinterpret_cast<uintptr_t>(a.symin.sym + first);
+                g1 = g0 + (uintptr_t)cnt * 2;
+            }
+            const uintptr_t s0 = g0 & ~uintptr_t(15);
+            uintptr_t s1 = (g1 + 15) & ~uintptr_t(15);
+            const uintptr_t lim = reinterpret_cast<uintptr_t>(a.src_end) & ~uintptr_t(15);
+            uint32_t tail = 0;
+            if (s1 > lim) { tail = 1; s1 = lim; }
+            if (g1 <= g0) { s1 = s0; tail = 0; }
+            bytes = s1 > s0 ? (uint32_t)(s1 - s0) : 0u;
+            src = reinterpret_cast<const unsigned char *>(s0);
+            rowoff[slot * RR1 + lane] = (int)((g0 - s0) / sizeof(E));
+            // the last bytes of the buffer (past its last 16-byte boundary) are read with plain loads
+            if (tail) {
+                const uintptr_t t0 = s1 > g0 ? s1 : g0;
+                for (uintptr_t b = t0; b < g1; b += sizeof(E))
+                    *reinterpret_cast<E *>(dst0 + lane * PB + (b - s0)) = *reinterpret_cast<const E *>(b);
             }
         }
+        if (lane == 0) {
+            // dim-0 restriction taps of plane p (zero where p is outside a window or the segment)
+            PlaneTaps<T> pt;
+            int jlo = first_coarse_at_or_after(a.g.dim[0], p - 2);
+            if (jlo < J0a) jlo = J0a;
+            pt.jlo = jlo;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                const int j = jlo + i;
+                const int o = p - cpos_of(m0, mc0, j);
+                pt.t[i] = (j < J0b && o >= -2 && o <= 2) ? tap0src[j * 5 + o + 2] : (T)0;
+            }
+            ptaps[slot] = pt;
+        }
+        uint32_t tot = bytes;
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        if (lane == 0) mbar_arrive_expect_tx(&mbar[slot], tot);
+        __syncwarp();
+        if (lane < r1n && bytes) bulk_g2s(dst0 + lane * PB, src, bytes, &mbar[slot]);
+    };
+    auto wait_plane = [&](int p) -> bool {
+        const int r = p - lo0;
+        return mbar_wait_bounded(&mbar[r % NST], (uint32_t)((r / NST) & 1), kWaitPolls);
+    };
+    auto Vrow = [&](int slot, int i1) -> const E * {
+        return reinterpret_cast<const E *>(stage_base + (slot * RR1 + i1) * PB) + rowoff[slot * RR1 + i1];
+    };
+
+    if (STAGED && warp == 0)
+        for (int p = lo0; p <= hi0 && p < lo0 + NST - 1; p++) issue(p);
+    int waited = lo0 - 1;   // planes up to here are complete
+    int jdone = lo0 - 1;    // last plane whose J is formed
+
+    T acc0 = 0, acc1 = 0, acc2 = 0;
+    int jb = J0a;
+    const long long out_col = (long long)(J1 + j1l) * mc2 + (J2 + lane);
+    const long long cstride = (long long)mc1 * mc2;
+    const int nreg = r1n * r2n;
+
+    // J = I_1 I_2 v on the region of kept plane p (slot of its coarse index parity)
+    auto form_J = [&](int p) {
+      if constexpr (FIELD) {
+        const int vs = (p - lo0) % NST;
+        T *J = Jb + (cidx_of(m0, mc0, p) & 1) * RR1 * RR2;
+        for (int idx = tid; idx < nreg; idx += RTHREADS) {
+            const int i1 = __float2int_rz(((float)idx + 0.5f) * inv_r2n);
+            const int i2 = idx - i1 * r2n;
+            const bool f1 = !kept_pos(m1, lo1 + i1), f2 = !kept_pos(m2, lo2 + i2);
+            auto I2 = [&](int r) -> T {
+                const T *row = Vrow(vs, r);
+                return f2 ? fma_rn(wr2s[i2], row[i2 + 1], mul_rn(wl2s[i2], row[i2 - 1])) : row[i2];
+            };
+            J[i1 * RR2 + i2] = f1 ? fma_rn(wr1s[i1], I2(i1 + 1), mul_rn(wl1s[i1], I2(i1 - 1))) : I2(i1);
+        }
+      }
+    };
+
+    for (int p0 = lo0; p0 <= hi0; p0++) {
+        const int s0 = (p0 - lo0) % NST;
+        bool ok = true;
+        if (STAGED) {
+            const int need = min(p0 + 1, hi0);
+            while (waited < need) { waited++; ok = ok && wait_plane(waited); }
+        }
+        if (__syncthreads_or(!ok)) {
+            // give up: wait (bounded) for the copies still in flight, then leave
+            if (tid == 0) atomicExch(a.status, (unsigned)DS_TIMEOUT);
+            for (int p = waited + 1; p <= hi0 && p < p0 + NST; p++) wait_plane(p);
+            return;
+        }
+        const bool f0 = !kept_pos(m0, p0);
+        if constexpr (FIELD) {
+            const int pj = f0 ? p0 + 1 : p0;     // kept plane whose J this plane needs next
+            if (jdone < pj) {
+                form_J(pj);
+                jdone = pj;
+                __syncthreads();
+            }
+        }
+        // ---- B: w on the region ---------------------------------------------
+        const bool own0 = p0 >= o0a && p0 < o0b;
+        const long long pbase = plane_base_of(a.g, p0);
+        T wl0 = (T)0, wr0 = (T)0;
+        const T *Jm = Jb, *Jp = Jb;
+        if constexpr (FIELD) {
+            if (f0) {
+                wl0 = a.g.dim[0].wl[p0];
+                wr0 = a.g.dim[0].wr[p0];
+                Jm = Jb + (cidx_of(m0, mc0, p0 - 1) & 1) * RR1 * RR2;
+                Jp = Jb + (cidx_of(m0, mc0, p0 + 1) & 1) * RR1 * RR2;
+            } else {
+                Jm = Jb + (cidx_of(m0, mc0, p0) & 1) * RR1 * RR2;
+            }
+        }
+        for (int idx = tid; idx < nreg; idx += RTHREADS) {
+            const int i1 = __float2int_rz(((float)idx + 0.5f) * inv_r2n);
+            const int i2 = idx - i1 * r2n;
+            const int p1 = lo1 + i1, p2 = lo2 + i2;
+            const bool f1 = !kept_pos(m1, p1);
+            const bool f2 = !kept_pos(m2, p2);
+            const bool isnew = f0 || f1 || f2;
+            T w = (T)0;
+            if constexpr (FIELD) {
+                if (isnew) {
+                    const int q = i1 * RR2 + i2;
+                    const T lerp = f0 ? fma_rn(wr0, Jp[q], mul_rn(wl0, Jm[q])) : Jm[q];
+                    w = sub_rn(Vrow(s0, i1)[i2], lerp);
+                    if (SINK != (int)Sink::NONE && own0 && p1 >= o1a && p1 < o1b && p2 >= o2a && p2 < o2b) {
+                        const bool rownew = f0 || f1;
+                        const long long si = row_base(a.g, pbase, !f0, p1) + (rownew ? p2 : (p2 - 1) >> 1);
+                        if (SINK == (int)Sink::STREAM) a.coef_out[si] = w;
+                        else quant_emit(a.qo, hs, smem_hist, si, w, rho);
+                    }
+                }
+            } else if constexpr (SRC == (int)WSrc::SYMBOLS) {
+                if (isnew) {
+                    const bool rownew = f0 || f1;
+                    const unsigned sv = Vrow(s0, i1)[rownew ? i2 : (i2 - 1) >> 1];
+                    const long long si = row_base(a.g, pbase, !f0, p1) + (rownew ? p2 : (p2 - 1) >> 1);
+                    w = dequant_sym<T>(a.symin, sv, si, qlev);
+                }
+            } else if constexpr (SRC == (int)WSrc::STREAM) {
+                if (isnew) w = a.coef_in[stream_rank(a.g, p0, p1, p2)];
+            } else {  // DENSE
+                if (isnew || !a.dense_new_only) w = a.v[((long long)p0 * m1 + p1) * m2 + p2];
+            }
+            W[i1 * RR2 + i2] = w;
+        }
         __syncthreads();
-        // ---- C: restriction along dim 2 ---------------------------------------
-        for (int i1 = warp; i1 < r1n; i1 += RTHREADS / 32) {
-            if (lane < n2) {
-                const int c = cpos_of(m2, mc2, J2 + lane) - lo2;
-                T s = (T)0;
+        // the stage of plane p0 - 1 is free: refill it with plane p0 + NST - 1
+        if (STAGED && warp == 0 && p0 + NST - 1 <= hi0) issue(p0 + NST - 1);
+        // ---- C: restriction along dim 2 (taps of column jl in registers) -------
+        if (jl < n2) {
+            for (int i1 = warp; i1 < r1n; i1 += RTHREADS / 32) {
+                const T *wr = W + i1 * RR2 + c2col;
+                T sacc = (T)0;
 #pragma unroll
                 for (int o = -2; o <= 2; o++) {
-                    const int idx = c + o;
-                    if (idx >= 0 && idx < r2n) s = fma_rn(tap2s[lane * 5 + o + 2], W[i1 * RR2 + idx], s);
+                    const int q = c2col + o;
+                    if (q >= 0 && q < r2n) sacc = fma_rn(t2[o + 2], wr[o], sacc);
                 }
-                R2s[i1 * TT2 + lane] = s;
+                R2s[i1 * TT2 + jl] = sacc;
             }
         }
         __syncthreads();
@@ -249,34 +429,43 @@ restrict_kernel(RestrictArgs<T> a, int seg_len)
             T r = (T)0;
 #pragma unroll
             for (int o = -2; o <= 2; o++) {
-                const int idx = c1r + o;
-                if (idx >= 0 && idx < r1n) r = fma_rn(tap1s[j1l * 5 + o + 2], R2s[idx * TT2 + j2l], r);
+                const int q = c1r + o;
+                if (q >= 0 && q < r1n) r = fma_rn(t1[o + 2], R2s[q * TT2 + lane], r);
             }
-            int jlo = first_coarse_at_or_after(a.g.dim[0], p0 - 2);
-            if (jlo < J0a) jlo = J0a;
-            while (jb < jlo && jb < J0b) {
-                a.b[(long long)jb * mc1 * mc2 + out_col] = acc0;
+            PlaneTaps<T> pt;
+            if (STAGED) {
+                pt = ptaps[s0];
+            } else {
+                int jlo = first_coarse_at_or_after(a.g.dim[0], p0 - 2);
+                if (jlo < J0a) jlo = J0a;
+                pt.jlo = jlo;
+#pragma unroll
+                for (int i = 0; i < 3; i++) {
+                    const int j = jlo + i;
+                    const int o = p0 - cpos_of(m0, mc0, j);
+                    pt.t[i] = (j < J0b && o >= -2 && o <= 2) ? tap0src[j * 5 + o + 2] : (T)0;
+                }
+            }
+            while (jb < pt.jlo && jb < J0b) {
+                a.b[(long long)jb * cstride + out_col] = acc0;
                 acc0 = acc1; acc1 = acc2; acc2 = (T)0;
                 jb++;
             }
-            {
-                int j = jb, o = p0 - cpos_of(m0, mc0, j);
-                if (j < J0b && o >= -2 && o <= 2) acc0 = fma_rn(tap0src[j * 5 + o + 2], r, acc0);
-                j = jb + 1;
-                if (j < J0b) { o = p0 - cpos_of(m0, mc0, j); if (o >= -2 && o <= 2) acc1 = fma_rn(tap0src[j * 5 + o + 2], r, acc1); }
-                j = jb + 2;
-                if (j < J0b) { o = p0 - cpos_of(m0, mc0, j); if (o >= -2 && o <= 2) acc2 = fma_rn(tap0src[j * 5 + o + 2], r, acc2); }
-            }
-            if (SRC == (int)WSrc::FIELD && SINK != (int)Sink::NONE && a.vc && kept_pos(m0, p0)) {
-                const int j0 = cidx_of(m0, mc0, p0);
-                if (j0 >= J0a && j0 < J0b)
-                    a.vc[(long long)j0 * mc1 * mc2 + out_col] = V[(s0 * RR1 + c1r) * RR2 + c2r];
+            acc0 = fma_rn(pt.t[0], r, acc0);
+            acc1 = fma_rn(pt.t[1], r, acc1);
+            acc2 = fma_rn(pt.t[2], r, acc2);
+            if constexpr (FIELD && SINK != (int)Sink::NONE) {
+                if (a.vc && !f0) {
+                    const int j0 = cidx_of(m0, mc0, p0);
+                    if (j0 >= J0a && j0 < J0b)
+                        a.vc[(long long)j0 * cstride + out_col] = Vrow(s0, c1r)[c2col];
+                }
             }
         }
     }
     if (outp) {
         while (jb < J0b) {
-            a.b[(long long)jb * mc1 * mc2 + out_col] = acc0;
+            a.b[(long long)jb * cstride + out_col] = acc0;
             acc0 = acc1; acc1 = acc2; acc2 = (T)0;
             jb++;
         }
@@ -288,12 +477,369 @@ restrict_kernel(RestrictArgs<T> a, int seg_len)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Decomposition of one level from a level-l field (Alg. 1: lerp, quantization
+// of the new-node coefficients, mass_trans).  The coarse right-hand side uses
+// the Galerkin identity P^T M_l P = M_{l-1} of nested piecewise-linear spaces:
+//     b = P^T M_l (v - P v_c) = ((x)_k P^T M_l) v - ((x)_k M_{l-1}) v_c,
+// so the restriction reads the staged level-l values directly and the
+// coefficients w = v - lerp(v) are formed only on the nodes the CTA owns
+// (each thread: four consecutive nodes of one row).
+
+constexpr int OWN1 = 2 * TT1, OWN2 = 2 * TT2;   // owned fine region of a tile
+constexpr int JPITCH = OWN2 + 4;
+constexpr int kHistWin = 2048;                  // shared-memory histogram: D/2 +- kHistWin
+
+template <typename T>
+struct PlaneTaps2 {
+    int jlo;
+    T tr[3];   // restriction taps of plane p for coarse jlo..jlo+2
+    T tm[3];   // coarse mass-matrix taps (kept planes only)
+};
+
+template <typename T>
+__device__ __forceinline__ void quant_emit_w(const QuantOut &qo, unsigned int *hs, int hlo, int hn,
+                                             long long si, T w, T rho)
+{
+    long long k = quant_code(w, rho);
+    long long s = k + (long long)(qo.D / 2);
+    unsigned int sym;
+    if (s >= 1 && s <= (long long)qo.D - 1) {
+        sym = (unsigned int)s;
+    } else {
+        sym = 0;
+        unsigned long long pos = atomicAdd(&qo.sc->n_out, 1ULL);
+        if (pos < qo.out_cap) {
+            qo.out_idx[pos] = (unsigned long long)si;
+            qo.out_k[pos] = k;
+        } else {
+            atomicExch(&qo.sc->status, (unsigned int)DS_CAPACITY);
+        }
+    }
+    qo.sym[si] = (uint16_t)sym;
+    const unsigned rel = sym - (unsigned)hlo;
+    if (rel < (unsigned)hn) atomicAdd(&hs[rel], 1u);
+    else atomicAdd(&qo.hist[sym], 1ULL);
+}
+
+template <typename T, int SINK>
+__global__ void __launch_bounds__(RTHREADS, 3)
+decomp_level_kernel(RestrictArgs<T> a, int seg_len)
+{
+    constexpr int PB = row_pitch_bytes<T>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int m0 = a.g.dim[0].m, m1 = a.g.dim[1].m, m2 = a.g.dim[2].m;
+    const int mc0 = a.g.dim[0].mc, mc1 = a.g.dim[1].mc, mc2 = a.g.dim[2].mc;
+    const int J2 = blockIdx.x * TT2, J1 = blockIdx.y * TT1;
+    const int J0a = blockIdx.z * seg_len;
+    const int J0b = min(J0a + seg_len, mc0);
+    if (J0a >= J0b) return;
+    const int n2 = min(TT2, mc2 - J2), n1 = min(TT1, mc1 - J1);
+    const int lo2 = max(0, cpos_of(m2, mc2, J2) - 2) & ~1;
+    const int hi2 = min(m2 - 1, cpos_of(m2, mc2, J2 + n2 - 1) + 2);
+    const int lo1 = max(0, cpos_of(m1, mc1, J1) - 2) & ~1;
+    const int hi1 = min(m1 - 1, cpos_of(m1, mc1, J1 + n1 - 1) + 2);
+    const int lo0 = max(0, cpos_of(m0, mc0, J0a) - 2) & ~1;
+    const int hi0 = min(m0 - 1, cpos_of(m0, mc0, J0b - 1) + 2);
+    const int r1n = hi1 - lo1 + 1, r2n = hi2 - lo2 + 1;
+    const int o2a = cpos_of(m2, mc2, J2), o2b = (J2 + n2 < mc2) ? cpos_of(m2, mc2, J2 + n2) : m2;
+    const int o1a = cpos_of(m1, mc1, J1), o1b = (J1 + n1 < mc1) ? cpos_of(m1, mc1, J1 + n1) : m1;
+    const int o0a = cpos_of(m0, mc0, J0a), o0b = (J0b < mc0) ? cpos_of(m0, mc0, J0b) : m0;
+
+    unsigned char *stage_base = smem_raw;
+    int *rowoff = reinterpret_cast<int *>(smem_raw + NST * RR1 * PB);
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(
+        (reinterpret_cast<uintptr_t>(rowoff + NST * RR1) + 15) & ~uintptr_t(15));
+    PlaneTaps2<T> *ptaps = reinterpret_cast<PlaneTaps2<T> *>(mbar + NST);
+    T *Jb = reinterpret_cast<T *>(ptaps + NST);          // [2][OWN1][JPITCH]
+    T *Rrow = Jb + 2 * OWN1 * JPITCH;                    // [RR1][TT2]
+    T *Mrow = Rrow + RR1 * TT2;                          // [RR1][TT2]
+    T *wl2s = Mrow + RR1 * TT2, *wr2s = wl2s + RR2;      // [RR2]
+    T *wl1s = wr2s + RR2, *wr1s = wl1s + RR1;            // [RR1]
+    unsigned int *hs = reinterpret_cast<unsigned int *>(wr1s + RR1);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int hhalf = SINK == (int)Sink::QUANT ? min((int)a.qo.D / 2, kHistWin) : 0;
+    const int hlo = (int)(a.qo.D / 2) - hhalf, hn = 2 * hhalf;
+    for (int i = tid; i < r2n; i += RTHREADS) { wl2s[i] = a.g.dim[2].wl[lo2 + i]; wr2s[i] = a.g.dim[2].wr[lo2 + i]; }
+    for (int i = tid; i < r1n; i += RTHREADS) { wl1s[i] = a.g.dim[1].wl[lo1 + i]; wr1s[i] = a.g.dim[1].wr[lo1 + i]; }
+    for (int i = tid; i < hn; i += RTHREADS) hs[i] = 0u;
+    if (tid == 0) {
+        for (int i = 0; i < NST; i++) mbar_init(&mbar[i], 1);
+        mbar_fence_init();
+    }
+    // taps of this thread's dim-2 column (restriction and coarse mass matrix)
+    const int jl = lane;
+    const bool colv = jl < n2;
+    T t2[5], mt2[3];
+    int mc2col[3];
+    const int c2col = colv ? cpos_of(m2, mc2, J2 + jl) - lo2 : 0;
+#pragma unroll
+    for (int o = 0; o < 5; o++) t2[o] = colv ? a.g.dim[2].tap[(J2 + jl) * 5 + o] : (T)0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const int j = J2 + jl + d - 1;
+        const bool ok = colv && j >= 0 && j < mc2;
+        mt2[d] = ok ? a.g.dim[2].mtap[(J2 + jl) * 3 + d] : (T)0;
+        mc2col[d] = ok ? cpos_of(m2, mc2, j) - lo2 : 0;
+    }
+    // taps of this thread's output row (phase D)
+    const int j1l = warp;
+    const bool outp = j1l < n1 && colv;
+    T t1[5], mt1[3];
+    int mr1[3];
+    const int c1r = outp ? cpos_of(m1, mc1, J1 + j1l) - lo1 : 0;
+#pragma unroll
+    for (int o = 0; o < 5; o++) t1[o] = outp ? a.g.dim[1].tap[(J1 + j1l) * 5 + o] : (T)0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const int j = J1 + j1l + d - 1;
+        const bool ok = outp && j >= 0 && j < mc1;
+        mt1[d] = ok ? a.g.dim[1].mtap[(J1 + j1l) * 3 + d] : (T)0;
+        mr1[d] = ok ? cpos_of(m1, mc1, j) - lo1 : 0;
+    }
+    // this thread's owned nodes: row rr, four consecutive nodes from column 4q
+    const int rr = tid >> 4, q4 = (tid & 15) * 4;
+    const int p1 = o1a + rr;
+    const bool rowv = p1 < o1b;
+    const int i1 = p1 - lo1;
+    const bool f1 = rowv && !kept_pos(m1, p1);
+    T rho = (T)0;
+    if (SINK == (int)Sink::QUANT) rho = rho_of<T>(a.qo.sc, a.g.level);
+    __syncthreads();
+
+    auto issue = [&](int p) {
+        const int slot = (p - lo0) % NST;
+        unsigned char *dst0 = stage_base + slot * RR1 * PB;
+        uint32_t bytes = 0;
+        const unsigned char *src = nullptr;
+        if (lane < r1n) {
+            const T *row = a.v + ((long long)p * m1 + lo1 + lane) * m2 + lo2;
+            const uintptr_t g0 = reinterpret_cast<uintptr_t>(row);
+            const uintptr_t g1 = g0 + (uintptr_t)r2n * sizeof(T);
+            const uintptr_t s0 = g0 & ~uintptr_t(15);
+            uintptr_t s1 = (g1 + 15) & ~uintptr_t(15);
+            const uintptr_t lim = reinterpret_cast<uintptr_t>(a.src_end) & ~uintptr_t(15);
+            bool tail = false;
+            if (s1 > lim) { tail = true; s1 = lim; }
+            bytes = s1 > s0 ? (uint32_t)(s1 - s0) : 0u;
+            src = reinterpret_cast<const unsigned char *>(s0);
+            rowoff[slot * RR1 + lane] = (int)((g0 - s0) / sizeof(T));
+            if (tail) {
+                const uintptr_t t0 = s1 > g0 ? s1 : g0;
+                for (uintptr_t b = t0; b < g1; b += sizeof(T))
+                    *reinterpret_cast<T *>(dst0 + lane * PB + (b - s0)) = *reinterpret_cast<const T *>(b);
+            }
+        }
+        if (lane == 0) {
+            PlaneTaps2<T> pt;
+            int jlo = first_coarse_at_or_after(a.g.dim[0], p - 2);
+            if (jlo < J0a) jlo = J0a;
+            pt.jlo = jlo;
+            const bool k0 = kept_pos(m0, p);
+            const int jc = k0 ? cidx_of(m0, mc0, p) : -10;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                const int j = jlo + i;
+                const int o = p - cpos_of(m0, mc0, j);
+                const bool inj = j < J0b;
+                pt.tr[i] = (inj && o >= -2 && o <= 2) ? a.g.dim[0].tap[j * 5 + o + 2] : (T)0;
+                const int d = jc - j;
+                pt.tm[i] = (inj && d >= -1 && d <= 1) ? a.g.dim[0].mtap[j * 3 + d + 1] : (T)0;
+            }
+            ptaps[slot] = pt;
+        }
+        uint32_t tot = bytes;
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        if (lane == 0) mbar_arrive_expect_tx(&mbar[slot], tot);
+        __syncwarp();
+        if (lane < r1n && bytes) bulk_g2s(dst0 + lane * PB, src, bytes, &mbar[slot]);
+    };
+    auto wait_plane = [&](int p) -> bool {
+        const int r = p - lo0;
+        return mbar_wait_bounded(&mbar[r % NST], (uint32_t)((r / NST) & 1), kWaitPolls);
+    };
+    auto Vrow = [&](int slot, int r) -> const T * {
+        return reinterpret_cast<const T *>(stage_base + (slot * RR1 + r) * PB) + rowoff[slot * RR1 + r];
+    };
+    // J = I_1 I_2 v of kept plane p on the owned region
+    auto form_J = [&](int p) {
+        if (!rowv) return;
+        const int vs = (p - lo0) % NST;
+        T *J = Jb + (cidx_of(m0, mc0, p) & 1) * OWN1 * JPITCH + rr * JPITCH + q4;
+        const T *r0 = Vrow(vs, i1);
+        const T *rm = f1 ? Vrow(vs, i1 - 1) : r0;
+        const T *rp = f1 ? Vrow(vs, i1 + 1) : r0;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const int p2 = o2a + q4 + e;
+            if (p2 >= o2b) break;
+            const int i2 = p2 - lo2;
+            const bool f2 = !kept_pos(m2, p2);
+            auto I2 = [&](const T *row) -> T {
+                return f2 ? fma_rn(wr2s[i2], row[i2 + 1], mul_rn(wl2s[i2], row[i2 - 1])) : row[i2];
+            };
+            J[e] = f1 ? fma_rn(wr1s[i1], I2(rp), mul_rn(wl1s[i1], I2(rm))) : I2(r0);
+        }
+    };
+
+    if (warp == 0)
+        for (int p = lo0; p <= hi0 && p < lo0 + NST - 1; p++) issue(p);
+    int waited = lo0 - 1, jdone = lo0 - 1;
+    T acc0 = 0, acc1 = 0, acc2 = 0;
+    int jb = J0a;
+    const long long cstride = (long long)mc1 * mc2;
+    const long long out_col = (long long)(J1 + j1l) * mc2 + (J2 + jl);
+
+    for (int p0 = lo0; p0 <= hi0; p0++) {
+        const int s0 = (p0 - lo0) % NST;
+        bool ok = true;
+        const int need = min(p0 + 1, hi0);
+        while (waited < need) { waited++; ok = ok && wait_plane(waited); }
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(a.status, (unsigned)DS_TIMEOUT);
+            for (int p = waited + 1; p <= hi0 && p < p0 + NST; p++) wait_plane(p);
+            return;
+        }
+        const bool f0 = !kept_pos(m0, p0);
+        const int pj = f0 ? p0 + 1 : p0;
+        if (jdone < pj) {
+            form_J(pj);
+            jdone = pj;
+            __syncthreads();
+        }
+        // ---- B: coefficients of the owned nodes -----------------------------
+        if (rowv && p0 >= o0a && p0 < o0b) {
+            const T *Jm = Jb + (cidx_of(m0, mc0, f0 ? p0 - 1 : p0) & 1) * OWN1 * JPITCH + rr * JPITCH + q4;
+            const T *Jp = Jb + (cidx_of(m0, mc0, f0 ? p0 + 1 : p0) & 1) * OWN1 * JPITCH + rr * JPITCH + q4;
+            const T wl0 = f0 ? a.g.dim[0].wl[p0] : (T)0, wr0 = f0 ? a.g.dim[0].wr[p0] : (T)0;
+            const T *vr = Vrow(s0, i1);
+            const bool rownew = f0 || f1;
+            const long long rb = row_base(a.g, plane_base_of(a.g, p0), !f0, p1);
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int p2 = o2a + q4 + e;
+                if (p2 >= o2b) break;
+                const int i2 = p2 - lo2;
+                const bool f2 = !kept_pos(m2, p2);
+                if (rownew || f2) {
+                    const T lerp = f0 ? fma_rn(wr0, Jp[e], mul_rn(wl0, Jm[e])) : Jm[e];
+                    const T w = sub_rn(vr[i2], lerp);
+                    if (SINK != (int)Sink::NONE) {
+                        const long long si = rb + (rownew ? p2 : (p2 - 1) >> 1);
+                        if (SINK == (int)Sink::STREAM) a.coef_out[si] = w;
+                        else quant_emit_w(a.qo, hs, hlo, hn, si, w, rho);
+                    }
+                } else if (a.vc) {
+                    a.vc[(long long)cidx_of(m0, mc0, p0) * cstride +
+                         (long long)cidx_of(m1, mc1, p1) * mc2 + cidx_of(m2, mc2, p2)] = vr[i2];
+                }
+            }
+        }
+        // ---- C: restriction of the staged rows along dim 2 ---------------------
+        if (colv) {
+            for (int r = warp; r < r1n; r += RTHREADS / 32) {
+                const T *vr = Vrow(s0, r);
+                T sacc = (T)0;
+#pragma unroll
+                for (int o = -2; o <= 2; o++) {
+                    const int qq = c2col + o;
+                    if (qq >= 0 && qq < r2n) sacc = fma_rn(t2[o + 2], vr[qq], sacc);
+                }
+                Rrow[r * TT2 + jl] = sacc;
+                if (!f0) {
+                    T macc = (T)0;
+#pragma unroll
+                    for (int d = 0; d < 3; d++) macc = fma_rn(mt2[d], vr[mc2col[d]], macc);
+                    Mrow[r * TT2 + jl] = macc;
+                }
+            }
+        }
+        __syncthreads();
+        if (warp == 0 && p0 + NST - 1 <= hi0) issue(p0 + NST - 1);
+        // ---- D: dim 1, then the dim-0 taps into registers ---------------------
+        if (outp) {
+            T r = (T)0;
+#pragma unroll
+            for (int o = -2; o <= 2; o++) {
+                const int qq = c1r + o;
+                if (qq >= 0 && qq < r1n) r = fma_rn(t1[o + 2], Rrow[qq * TT2 + jl], r);
+            }
+            T rc = (T)0;
+            if (!f0) {
+#pragma unroll
+                for (int d = 0; d < 3; d++) rc = fma_rn(mt1[d], Mrow[mr1[d] * TT2 + jl], rc);
+            }
+            const PlaneTaps2<T> pt = ptaps[s0];
+            while (jb < pt.jlo && jb < J0b) {
+                a.b[(long long)jb * cstride + out_col] = acc0;
+                acc0 = acc1; acc1 = acc2; acc2 = (T)0;
+                jb++;
+            }
+            acc0 = fma_rn(-pt.tm[0], rc, fma_rn(pt.tr[0], r, acc0));
+            acc1 = fma_rn(-pt.tm[1], rc, fma_rn(pt.tr[1], r, acc1));
+            acc2 = fma_rn(-pt.tm[2], rc, fma_rn(pt.tr[2], r, acc2));
+        }
+    }
+    if (outp) {
+        while (jb < J0b) {
+            a.b[(long long)jb * cstride + out_col] = acc0;
+            acc0 = acc1; acc1 = acc2; acc2 = (T)0;
+            jb++;
+        }
+    }
+    if (hn) {
+        __syncthreads();
+        for (int i = tid; i < hn; i += RTHREADS)
+            if (hs[i]) atomicAdd(&a.qo.hist[hlo + i], (unsigned long long)hs[i]);
+    }
+}
+
+template <typename T>
+size_t decomp_smem(Sink sink, unsigned int D)
+{
+    size_t b = (size_t)NST * RR1 * row_pitch_bytes<T>() + NST * RR1 * 4 + 16 + NST * 8;
+    b += NST * sizeof(PlaneTaps2<T>);
+    b = (b + 15) & ~size_t(15);
+    b += (2 * OWN1 * JPITCH + 2 * RR1 * TT2 + 2 * (RR1 + RR2)) * sizeof(T) + 16;
+    if (sink == Sink::QUANT) b += (size_t)2 * std::min<unsigned>(D / 2, kHistWin) * sizeof(unsigned int);
+    return b;
+}
+
+template <typename T, int SINK>
+cudaError_t launch_decomp_t(const RestrictArgs<T> &a, cudaStream_t s)
+{
+    const int mc0 = a.g.dim[0].mc, mc1 = a.g.dim[1].mc, mc2 = a.g.dim[2].mc;
+    const int gx = (mc2 + TT2 - 1) / TT2, gy = (mc1 + TT1 - 1) / TT1;
+    const long long target = 152LL * 6;
+    long long tiles = (long long)gx * gy;
+    int seg = (int)std::max<long long>(2, (mc0 * tiles + target - 1) / target);
+    if (seg > 64) seg = 64;
+    if (seg > mc0) seg = mc0;
+    const int gz = (mc0 + seg - 1) / seg;
+    size_t sm = decomp_smem<T>((Sink)SINK, SINK == (int)Sink::QUANT ? a.qo.D : 0);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(decomp_level_kernel<T, SINK>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    decomp_level_kernel<T, SINK><<<dim3(gx, gy, gz), RTHREADS, sm, s>>>(a, seg);
+    count_launch();
+    return cudaGetLastError();
+}
+
 template <typename T>
 size_t restrict_smem(WSrc src, Sink sink, unsigned int D)
 {
-    size_t n = (src == WSrc::FIELD ? 3 : 0) * RR1 * RR2 + RR1 * RR2 + RR1 * TT2 + (TT2 + TT1) * 5 +
-               2 * (RR1 + RR2);
-    size_t b = n * sizeof(T);
+    size_t b = 0;
+    if (src == WSrc::FIELD) b += (size_t)NST * RR1 * row_pitch_bytes<T>() + NST * RR1 * 4 + 16 + NST * 8;
+    else if (src == WSrc::SYMBOLS) b += (size_t)NST * RR1 * row_pitch_bytes<uint16_t>() + NST * RR1 * 4 + 16 + NST * 8;
+    b += NST * sizeof(PlaneTaps<T>);
+    b = (b + 15) & ~size_t(15);
+    size_t n = RR1 * RR2 * (src == WSrc::FIELD ? 3 : 1) + RR1 * TT2 + 2 * (RR1 + RR2);
+    b += n * sizeof(T) + 16;
     if (sink == Sink::QUANT && D <= (unsigned)kHistSmemMax) b += (size_t)D * sizeof(unsigned int);
     return b;
 }
@@ -330,26 +876,79 @@ solve_strided_kernel(T *b, int n, long long stride, long long nlines, const T *_
 }
 
 template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst_smem, const T *src)
+{
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// 32 lines per CTA, staged in shared memory as [n][32]: line i's element t at
+// base + t*st + i (the 32 lines are contiguous), so every load and store of a
+// step t is one coalesced 128-byte row; one warp then runs the 32 sweeps.
+template <typename T>
+__global__ void __launch_bounds__(128)
+solve_tile_kernel(T *b, int n, long long st, long long ostride, int ninner,
+                  const T *__restrict__ sub, const T *__restrict__ cp, const T *__restrict__ inv_den)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *S = reinterpret_cast<T *>(smem_raw);
+    T *csub = S + n * 32, *ccp = csub + n, *cinv = ccp + n;   // Thomas factors, staged
+    for (int t = threadIdx.x; t < n; t += blockDim.x) { csub[t] = sub[t]; ccp[t] = cp[t]; cinv[t] = inv_den[t]; }
+    const int nblk = (ninner + 31) >> 5;
+    const long long o = blockIdx.x / nblk;
+    const int jb = (int)(blockIdx.x - o * nblk);
+    const int nl = min(32, ninner - jb * 32);
+    T *base = b + o * ostride + (long long)jb * 32;
+    for (int idx = threadIdx.x; idx < n * 32; idx += blockDim.x) {
+        const int t = idx >> 5, i = idx & 31;
+        if (i < nl) cp_async_elem(&S[idx], base + (long long)t * st + i);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if ((int)threadIdx.x < nl) {
+        T *p = S + threadIdx.x;
+        T y = (T)0;
+        for (int t = 0; t < n; t++) { y = mul_rn(fma_rn(-csub[t], y, p[t * 32]), cinv[t]); p[t * 32] = y; }
+        T x = (T)0;
+        for (int t = n - 1; t >= 0; t--) { x = fma_rn(-ccp[t], x, p[t * 32]); p[t * 32] = x; }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n * 32; idx += blockDim.x) {
+        const int t = idx >> 5, i = idx & 31;
+        if (i < nl) base[(long long)t * st + i] = S[idx];
+    }
+}
+
+template <typename T>
 __global__ void __launch_bounds__(256)
 solve_contig_kernel(T *b, int n, long long nlines, int rows, int pitch, const T *__restrict__ sub,
                     const T *__restrict__ cp, const T *__restrict__ inv_den, T *vc, int sign)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *S = reinterpret_cast<T *>(smem_raw);
+    T *csub = S + (size_t)rows * pitch, *ccp = csub + n, *cinv = ccp + n;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) { csub[t] = sub[t]; ccp[t] = cp[t]; cinv[t] = inv_den[t]; }
     long long row0 = blockIdx.x * (long long)rows;
     int nr = (int)min((long long)rows, nlines - row0);
     const T *src = b + row0 * n;
     for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
         int r = idx / n, t = idx - r * n;
-        S[r * pitch + t] = src[idx];
+        cp_async_elem(&S[r * pitch + t], src + idx);
     }
+    cp_async_wait_all();
     __syncthreads();
     if ((int)threadIdx.x < nr) {
         T *p = S + threadIdx.x * pitch;
         T y = (T)0;
-        for (int t = 0; t < n; t++) { y = mul_rn(fma_rn(-sub[t], y, p[t]), inv_den[t]); p[t] = y; }
+        for (int t = 0; t < n; t++) { y = mul_rn(fma_rn(-csub[t], y, p[t]), cinv[t]); p[t] = y; }
         T x = (T)0;
-        for (int t = n - 1; t >= 0; t--) { x = fma_rn(-cp[t], x, p[t]); p[t] = x; }
+        for (int t = n - 1; t >= 0; t--) { x = fma_rn(-ccp[t], x, p[t]); p[t] = x; }
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
@@ -370,6 +969,10 @@ template <typename T, int SRC>
 __global__ void __launch_bounds__(128)
 expand_kernel(LevelGeom<T> g, const T *__restrict__ vc, const T *coef_in, SymIn symin, T *out)
 {
+    // One block per output row (p0, p1).  Thread t owns coarse column t: it
+    // interpolates the corrected coarse grid along dims 0 and 1 at column t
+    // (V_t), writes the kept position of that column and the new position
+    // after it, which interpolates V_t and V_{t+1} (from the next lane).
     const int m0 = g.dim[0].m, m1 = g.dim[1].m, m2 = g.dim[2].m;
     const int mc0 = g.dim[0].mc, mc1 = g.dim[1].mc, mc2 = g.dim[2].mc;
     const long long row = blockIdx.x;
@@ -381,30 +984,43 @@ expand_kernel(LevelGeom<T> g, const T *__restrict__ vc, const T *coef_in, SymIn 
     else { a0 = b0 = cidx_of(m0, mc0, p0); }
     if (f1) { a1 = cidx_of(m1, mc1, p1 - 1); b1 = cidx_of(m1, mc1, p1 + 1); wl1 = g.dim[1].wl[p1]; wr1 = g.dim[1].wr[p1]; }
     else { a1 = b1 = cidx_of(m1, mc1, p1); }
-    const T *wl2 = g.dim[2].wl, *wr2 = g.dim[2].wr;
+    const T *raa = vc + ((long long)a0 * mc1 + a1) * mc2;
+    const T *rab = vc + ((long long)a0 * mc1 + b1) * mc2;
+    const T *rba = vc + ((long long)b0 * mc1 + a1) * mc2;
+    const T *rbb = vc + ((long long)b0 * mc1 + b1) * mc2;
+    const bool rownew = f0 || f1;
+    const long long rb = row_base(g, plane_base_of(g, p0), !f0, p1);
+    const T q = (SRC == (int)WSrc::SYMBOLS) ? q_of<T>(symin.sc, g.level) : (T)0;
+    auto V = [&](int t) -> T {
+        T va = raa[t];
+        if (f1) va = fma_rn(wr1, rab[t], mul_rn(wl1, va));
+        if (!f0) return va;
+        T vb = rba[t];
+        if (f1) vb = fma_rn(wr1, rbb[t], mul_rn(wl1, vb));
+        return fma_rn(wr0, vb, mul_rn(wl0, va));
+    };
+    auto coef = [&](long long si) -> T {
+        if (SRC == (int)WSrc::STREAM) return coef_in[si];
+        return dequant_sym<T>(symin, symin.sym[si], si, q);
+    };
     T *orow = out + row * m2;
-    for (int p2 = threadIdx.x; p2 < m2; p2 += blockDim.x) {
-        const bool f2 = !kept_pos(m2, p2);
-        if (!(f0 || f1 || f2)) {
-            orow[p2] = vc[((long long)a0 * mc1 + a1) * mc2 + cidx_of(m2, mc2, p2)];
-            continue;
+    const int lane = threadIdx.x & 31;
+    for (int t0 = 0; t0 < mc2; t0 += blockDim.x) {
+        const int t = t0 + threadIdx.x;
+        const bool act = t < mc2;
+        const T vt = act ? V(t) : (T)0;
+        T vn = __shfl_down_sync(0xffffffffu, vt, 1);
+        if (act) {
+            const int pk = cpos_of(m2, mc2, t);              // kept position of column t
+            orow[pk] = rownew ? add_rn(coef(rb + pk), vt) : vt;
+            const int pf = pk + 1;                           // new position after it, if any
+            if (pf < m2 && !kept_pos(m2, pf)) {
+                if (lane == 31 || t + 1 >= t0 + (int)blockDim.x) vn = V(t + 1);
+                const T lerp = fma_rn(g.dim[2].wr[pf], vn, mul_rn(g.dim[2].wl[pf], vt));
+                const long long si = rb + (rownew ? pf : (pf - 1) >> 1);
+                orow[pf] = add_rn(coef(si), lerp);
+            }
         }
-        const int a2 = f2 ? cidx_of(m2, mc2, p2 - 1) : cidx_of(m2, mc2, p2);
-        const int b2 = f2 ? cidx_of(m2, mc2, p2 + 1) : a2;
-        const T w2l = f2 ? wl2[p2] : (T)0, w2r = f2 ? wr2[p2] : (T)0;
-        auto val = [&](int c0, int c1) -> T {
-            const T *r = vc + ((long long)c0 * mc1 + c1) * mc2;
-            if (f2) return fma_rn(w2r, r[b2], mul_rn(w2l, r[a2]));
-            return r[a2];
-        };
-        auto pl = [&](int c0) -> T {
-            if (f1) return fma_rn(wr1, val(c0, b1), mul_rn(wl1, val(c0, a1)));
-            return val(c0, a1);
-        };
-        T lerp = f0 ? fma_rn(wr0, pl(b0), mul_rn(wl0, pl(a0))) : pl(a0);
-        long long si = stream_rank(g, p0, p1, p2);
-        T c = (SRC == (int)WSrc::STREAM) ? coef_in[si] : dequant<T>(symin, si, g.level);
-        orow[p2] = add_rn(c, lerp);
     }
 }
 
@@ -440,6 +1056,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) norm_kernel(const T *__restrict__ u, long long N, double *partials)
 {
     T mx = (T)0;
+    T ssT = (T)0;   // per-thread partial sum in T (binary64 arithmetic is slow on this part)
     double ss = 0.0;
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long nth = (long long)gridDim.x * blockDim.x;
@@ -456,7 +1073,7 @@ __global__ void __launch_bounds__(256) norm_kernel(const T *__restrict__ u, long
             for (int k = 0; k < V; k++) {
                 T ax = e[k] < (T)0 ? -e[k] : e[k];
                 nan_max(mx, ax);
-                ss += (double)e[k] * (double)e[k];
+                ssT = fma_rn(e[k], e[k], ssT);
             }
         }
     }
@@ -464,8 +1081,9 @@ __global__ void __launch_bounds__(256) norm_kernel(const T *__restrict__ u, long
         T x = u[i];
         T ax = x < (T)0 ? -x : x;
         nan_max(mx, ax);
-        ss += (double)x * (double)x;
+        ssT = fma_rn(x, x, ssT);
     }
+    ss = (double)ssT;
     for (int o = 16; o > 0; o >>= 1) {
         T om = __shfl_down_sync(0xffffffffu, mx, o);
         double os = __shfl_down_sync(0xffffffffu, ss, o);
@@ -540,9 +1158,12 @@ cudaError_t launch_restrict_t(const RestrictArgs<T> &a, cudaStream_t s)
 {
     const int mc0 = a.g.dim[0].mc, mc1 = a.g.dim[1].mc, mc2 = a.g.dim[2].mc;
     const int gx = (mc2 + TT2 - 1) / TT2, gy = (mc1 + TT1 - 1) / TT1;
-    const long long target = 152LL * 9;
+    // enough CTAs for every SM to hold three; segments of at least two coarse
+    // planes keep the dim-0 halo (two planes each side) small
+    const long long target = 152LL * 6;
     long long tiles = (long long)gx * gy;
-    int seg = (int)std::max<long long>(8, (mc0 * tiles + target - 1) / target);
+    int seg = (int)std::max<long long>(2, (mc0 * tiles + target - 1) / target);
+    if (seg > 64) seg = 64;
     if (seg > mc0) seg = mc0;
     const int gz = (mc0 + seg - 1) / seg;
     size_t sm = restrict_smem<T>((WSrc)SRC, (Sink)SINK, SINK == (int)Sink::QUANT ? a.qo.D : 0);
@@ -558,16 +1179,41 @@ cudaError_t launch_restrict_t(const RestrictArgs<T> &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+__global__ void outlier_chunks_kernel(const unsigned long long *out_idx, unsigned long long n_out,
+                                      unsigned K, unsigned long long nch, unsigned long long *ochunk)
+{
+    for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c <= nch;
+         c += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long key = c * K;
+        unsigned long long lo = 0, hi = n_out;
+        while (lo < hi) {
+            unsigned long long mid = (lo + hi) >> 1;
+            if (out_idx[mid] < key) lo = mid + 1; else hi = mid;
+        }
+        ochunk[c] = lo;
+    }
+}
+
 }  // namespace
 
 int norm_parts() { return kNormBlocks; }
 
+cudaError_t launch_outlier_chunks(const unsigned long long *out_idx, unsigned long long n_out,
+                                  unsigned K, unsigned long long nch, unsigned long long *ochunk,
+                                  cudaStream_t s)
+{
+    outlier_chunks_kernel<<<(unsigned)std::min<unsigned long long>(1024, (nch + 256) / 256), 256, 0, s>>>(
+        out_idx, n_out, K, nch, ochunk);
+    count_launch();
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_restrict(WSrc src, Sink sink, const RestrictArgs<T> &a, cudaStream_t s)
 {
-    if (src == WSrc::FIELD && sink == Sink::QUANT) return launch_restrict_t<T, 0, 2>(a, s);
-    if (src == WSrc::FIELD && sink == Sink::STREAM) return launch_restrict_t<T, 0, 1>(a, s);
-    if (src == WSrc::FIELD) return launch_restrict_t<T, 0, 0>(a, s);
+    if (src == WSrc::FIELD && sink == Sink::QUANT) return launch_decomp_t<T, 2>(a, s);
+    if (src == WSrc::FIELD && sink == Sink::STREAM) return launch_decomp_t<T, 1>(a, s);
+    if (src == WSrc::FIELD) return launch_decomp_t<T, 0>(a, s);
     if (src == WSrc::STREAM) return launch_restrict_t<T, 1, 0>(a, s);
     if (src == WSrc::SYMBOLS) return launch_restrict_t<T, 2, 0>(a, s);
     return launch_restrict_t<T, 3, 0>(a, s);
@@ -583,7 +1229,21 @@ cudaError_t launch_solves(const LevelGeom<T> &g, T *b, T *vc, int sign, cudaStre
         const DimTables<T> &d = g.dim[k];
         if (!(d.m > 1)) continue;
         int sg = (k == last) ? sign : 0;
-        if (k < 2) {
+        if (k < 2 && sg == 0 && (size_t)d.mc * 35 * sizeof(T) <= 160 * 1024) {
+            // dim 0: lines (j1, j2), step c1*c2; dim 1: lines (j0, j2), step c2
+            const long long st = (k == 0) ? c1 * c2 : c2;
+            const long long outer = (k == 0) ? c1 : c0;
+            const long long ostride = (k == 0) ? c2 : c1 * c2;
+            const int ninner = (int)c2;
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(solve_tile_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 164 * 1024);
+                attr = true;
+            }
+            const long long grid = outer * ((ninner + 31) / 32);
+            solve_tile_kernel<T><<<(unsigned)grid, 128, (size_t)d.mc * 35 * sizeof(T), s>>>(
+                b, d.mc, st, ostride, ninner, d.sub, d.cp, d.inv_den);
+        } else if (k < 2) {
             long long stride = (k == 0) ? c1 * c2 : c2;
             long long nlines = (k == 0) ? c1 * c2 : c0 * c2;
             int n = d.mc;
@@ -594,7 +1254,7 @@ cudaError_t launch_solves(const LevelGeom<T> &g, T *b, T *vc, int sign, cudaStre
             long long nlines = c0 * c1;
             int pitch = n | 1;
             size_t rowbytes = (size_t)pitch * sizeof(T);
-            int rows = (int)std::min<size_t>(64, (96 * 1024) / rowbytes);
+            int rows = (int)std::min<size_t>(64, (90 * 1024) / rowbytes);
             if (rows < 1) {
                 solve_strided_kernel<T><<<(unsigned)((nlines + 255) / 256), 256, 0, s>>>(
                     b, n, 1, nlines, d.sub, d.cp, d.inv_den, vc, sg);
@@ -604,7 +1264,8 @@ cudaError_t launch_solves(const LevelGeom<T> &g, T *b, T *vc, int sign, cudaStre
                     cudaFuncSetAttribute(solve_contig_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
                     attr = true;
                 }
-                solve_contig_kernel<T><<<(unsigned)((nlines + rows - 1) / rows), 256, rows * rowbytes, s>>>(
+                solve_contig_kernel<T><<<(unsigned)((nlines + rows - 1) / rows), 256,
+                                         rows * rowbytes + 3 * (size_t)n * sizeof(T), s>>>(
                     b, n, nlines, rows, pitch, d.sub, d.cp, d.inv_den, vc, sg);
             }
         }

@@ -32,6 +32,8 @@ struct SymIn {
     const long long *out_k;
     unsigned long long n_out;
     unsigned int *status;
+    const unsigned long long *ochunk;   // first outlier of every chunk of K stream entries, or null
+    unsigned int K;
 };
 
 template <typename T>
@@ -46,6 +48,8 @@ struct RestrictArgs {
     T *vc;               // coarse copy of v (FIELD with a sink), may be null
     int use_ptap;        // 0: P^T M_l taps, 1: P^T taps
     int dense_new_only;  // DENSE: 1 = use only the new nodes (E_new^T of the input)
+    const void *src_end; // one past the last byte of the staged source (FIELD: v, SYMBOLS: sym)
+    unsigned int *status;  // device status word (timeouts)
 };
 
 template <typename T>
@@ -92,5 +96,9 @@ cudaError_t launch_mass_prolong(const LevelGeom<T> &g, const T *yc, T *yf, T *tm
                                 cudaStream_t s);
 
 int norm_parts();
+// ochunk[c] = first outlier with stream index >= c*K, c = 0..nch
+cudaError_t launch_outlier_chunks(const unsigned long long *out_idx, unsigned long long n_out,
+                                  unsigned K, unsigned long long nch, unsigned long long *ochunk,
+                                  cudaStream_t s);
 
 }  // namespace hpdr

@@ -41,7 +41,7 @@ struct Dim1 {
 // host tables of one (level, dim), binary64
 struct HostTab {
     int m, mc;
-    std::vector<double> wl, wr, tap, ptap, sub, cp, inv_den, etap;
+    std::vector<double> wl, wr, tap, ptap, sub, cp, inv_den, etap, mtap;
     std::vector<int> efirst;
 };
 
@@ -64,8 +64,9 @@ HostTab build_tab(const std::vector<double> &xf, const std::vector<double> &xc, 
     t.tap.assign(mc * 5, 0.0); t.ptap.assign(mc * 5, 0.0);
     t.sub.assign(mc, 0.0); t.cp.assign(mc, 0.0); t.inv_den.assign(mc, 1.0);
     t.etap.assign(m * 3, 0.0); t.efirst.assign(m, 0);
+    t.mtap.assign(mc * 3, 0.0);
     if (!active) {
-        t.tap[2] = 1.0; t.ptap[2] = 1.0; t.etap[0] = 1.0;
+        t.tap[2] = 1.0; t.ptap[2] = 1.0; t.etap[0] = 1.0; t.mtap[1] = 1.0;
         return t;
     }
     for (int p = 0; p < m; p++) {
@@ -116,10 +117,13 @@ HostTab build_tab(const std::vector<double> &xf, const std::vector<double> &xc, 
             t.etap[p * 3 + i] = s;
         }
     }
-    // Thomas factors of M_{l-1}
+    // Thomas factors of M_{l-1}, and its rows
     for (int i = 0; i < mc; i++) {
         double d, lo, hi;
         mass_entries(xc, i, d, lo, hi);
+        t.mtap[i * 3 + 0] = lo;
+        t.mtap[i * 3 + 1] = d;
+        t.mtap[i * 3 + 2] = hi;
         double den = (i == 0) ? d : d - lo * t.cp[i - 1];
         t.sub[i] = (i == 0) ? 0.0 : lo;
         t.inv_den[i] = 1.0 / den;
@@ -207,7 +211,7 @@ hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan
     Packer<float> pf;
     Packer<double> pd;
     // build both precisions into one buffer: float tables first, then double
-    struct Off { size_t wl, wr, tap, ptap, sub, cp, inv_den, etap, efirst; };
+    struct Off { size_t wl, wr, tap, ptap, sub, cp, inv_den, etap, efirst, mtap; };
     std::vector<Off> offF((L + 1) * 3), offD((L + 1) * 3);
     std::vector<unsigned char> all;
     auto append = [&](const void *p, size_t bytes) {
@@ -230,6 +234,7 @@ hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan
                 };
                 o.wl = put(t.wl); o.wr = put(t.wr); o.tap = put(t.tap); o.ptap = put(t.ptap);
                 o.sub = put(t.sub); o.cp = put(t.cp); o.inv_den = put(t.inv_den); o.etap = put(t.etap);
+                o.mtap = put(t.mtap);
                 o.efirst = append(t.efirst.data(), t.efirst.size() * sizeof(int));
             }
         }
@@ -252,8 +257,8 @@ hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan
             a.m = b.m = P->m[k][l];
             a.mc = b.mc = l > 0 ? P->m[k][l - 1] : P->m[k][l];
             if (l == 0) {
-                a.wl = a.wr = a.tap = a.ptap = a.sub = a.cp = a.inv_den = a.etap = nullptr; a.efirst = nullptr;
-                b.wl = b.wr = b.tap = b.ptap = b.sub = b.cp = b.inv_den = b.etap = nullptr; b.efirst = nullptr;
+                a.wl = a.wr = a.tap = a.ptap = a.sub = a.cp = a.inv_den = a.etap = a.mtap = nullptr; a.efirst = nullptr;
+                b.wl = b.wr = b.tap = b.ptap = b.sub = b.cp = b.inv_den = b.etap = b.mtap = nullptr; b.efirst = nullptr;
                 continue;
             }
             const Off &o = offF[l * 3 + k], &q = offD[l * 3 + k];
@@ -262,11 +267,13 @@ hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan
             a.sub = (const float *)(base + o.sub); a.cp = (const float *)(base + o.cp);
             a.inv_den = (const float *)(base + o.inv_den); a.etap = (const float *)(base + o.etap);
             a.efirst = (const int *)(base + o.efirst);
+            a.mtap = (const float *)(base + o.mtap);
             b.wl = (const double *)(base + q.wl); b.wr = (const double *)(base + q.wr);
             b.tap = (const double *)(base + q.tap); b.ptap = (const double *)(base + q.ptap);
             b.sub = (const double *)(base + q.sub); b.cp = (const double *)(base + q.cp);
             b.inv_den = (const double *)(base + q.inv_den); b.etap = (const double *)(base + q.etap);
             b.efirst = (const int *)(base + q.efirst);
+            b.mtap = (const double *)(base + q.mtap);
         }
     }
     (void)pf; (void)pd;
