@@ -197,6 +197,17 @@ struct ProfScope {
 };
 
 // plan.cu
+struct TableOff {
+    size_t wl = 0, wr = 0, tap = 0, ptap = 0, sub = 0, cp = 0, inv_den = 0, etap = 0, efirst = 0, mtap = 0;
+};
+struct PlanImage {
+    std::vector<unsigned char> bytes;   // host image of the device tables
+    std::vector<TableOff> offF, offD;   // offsets of every (level, dim) table, binary32 / binary64
+};
+// hierarchy and host image of the tables of one (shape, type)
+hpdr_status plan_image(int ndim, const size_t *dims, bool f64, Plan *P, PlanImage *img);
+// point the plan's tables at a device copy of img.bytes
+void bind_plan(Plan *P, const PlanImage &img, void *tables);
 hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan **out);
 hpdr_status ensure_workspace(hpdr_ctx *ctx, size_t bytes);
 int levels_of(int ndim, const size_t *dims);

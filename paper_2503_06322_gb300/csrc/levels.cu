@@ -373,6 +373,35 @@ restrict_kernel(RestrictArgs<T> a, int seg_len)
                 Jm = Jb + (cidx_of(m0, mc0, p0) & 1) * RR1 * RR2;
             }
         }
+        if constexpr (SRC == (int)WSrc::SYMBOLS) {
+            // four consecutive nodes of one region row per thread, one vector store
+            constexpr int NQ = RR2 / 4;
+            for (int u = tid; u < r1n * NQ; u += RTHREADS) {
+                const int i1 = u / NQ, i2b = (u - i1 * NQ) * 4;
+                const int p1 = lo1 + i1;
+                const bool f1 = !kept_pos(m1, p1);
+                const bool rownew = f0 || f1;
+                const E *sr = Vrow(s0, i1);
+                const long long rb = row_base(a.g, pbase, !f0, p1);
+                T wv[4];
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const int i2 = i2b + e, p2 = lo2 + i2;
+                    wv[e] = (T)0;
+                    if (i2 < r2n && (rownew || !kept_pos(m2, p2))) {
+                        const int si2 = rownew ? i2 : (i2 - 1) >> 1;
+                        wv[e] = dequant_sym<T>(a.symin, sr[si2], rb + (rownew ? p2 : (p2 - 1) >> 1), qlev);
+                    }
+                }
+                T *wd = W + i1 * RR2 + i2b;
+                if constexpr (sizeof(T) == 4) {
+                    *reinterpret_cast<float4 *>(wd) = make_float4(wv[0], wv[1], wv[2], wv[3]);
+                } else {
+                    reinterpret_cast<double2 *>(wd)[0] = make_double2(wv[0], wv[1]);
+                    reinterpret_cast<double2 *>(wd)[1] = make_double2(wv[2], wv[3]);
+                }
+            }
+        } else
         for (int idx = tid; idx < nreg; idx += RTHREADS) {
             const int i1 = __float2int_rz(((float)idx + 0.5f) * inv_r2n);
             const int i2 = idx - i1 * r2n;

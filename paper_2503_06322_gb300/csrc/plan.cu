@@ -152,40 +152,18 @@ double corr_norm_dim(const HostTab &t)
     return mx;
 }
 
-template <typename T>
-struct Packer {
-    std::vector<unsigned char> buf;
-    size_t add(const void *p, size_t bytes)
-    {
-        size_t off = (buf.size() + 255) & ~size_t(255);
-        buf.resize(off + bytes);
-        std::memcpy(buf.data() + off, p, bytes);
-        return off;
-    }
-    size_t addv(const std::vector<double> &v)
-    {
-        std::vector<T> c(v.begin(), v.end());
-        return add(c.data(), c.size() * sizeof(T));
-    }
-};
 
 }  // namespace
 
-hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan **out)
+hpdr_status plan_image(int ndim, const size_t *dims, bool f64, Plan *P, PlanImage *img)
 {
     if (ndim < 1 || ndim > 3 || !dims) return HPDR_ERR_ARG;
     for (int k = 0; k < ndim; k++)
         if (dims[k] < 2 || dims[k] > (size_t)(1u << 30)) return HPDR_ERR_ARG;
-    std::string key = std::to_string(ndim) + (f64 ? "d" : "f");
-    for (int k = 0; k < ndim; k++) key += ":" + std::to_string(dims[k]);
-    auto it = ctx->plans.find(key);
-    if (it != ctx->plans.end()) { *out = it->second; return HPDR_OK; }
-
-    Plan *P = new Plan();
     P->ndim = ndim;
     P->is_f64 = f64;
     int L = levels_of(ndim, dims);
-    if (L > kMaxLevels) { delete P; return HPDR_ERR_ARG; }
+    if (L > kMaxLevels) return HPDR_ERR_ARG;
     P->L = L;
     int pad = 3 - ndim;
     bool active[3];
@@ -208,12 +186,10 @@ hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan
     }
     for (int l = 0; l <= L; l++) P->N[l] = (long long)P->m[0][l] * P->m[1][l] * P->m[2][l];
 
-    Packer<float> pf;
-    Packer<double> pd;
-    // build both precisions into one buffer: float tables first, then double
-    struct Off { size_t wl, wr, tap, ptap, sub, cp, inv_den, etap, efirst, mtap; };
-    std::vector<Off> offF((L + 1) * 3), offD((L + 1) * 3);
-    std::vector<unsigned char> all;
+    img->offF.assign((L + 1) * 3, TableOff());
+    img->offD.assign((L + 1) * 3, TableOff());
+    std::vector<unsigned char> &all = img->bytes;
+    all.clear();
     auto append = [&](const void *p, size_t bytes) {
         size_t off = (all.size() + 255) & ~size_t(255);
         all.resize(off + bytes);
@@ -227,7 +203,7 @@ hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan
             HostTab t = build_tab(xs[k][l], xs[k][l - 1], active[k]);
             prod *= corr_norm_dim(t);
             for (int pass = 0; pass < 2; pass++) {
-                Off &o = pass == 0 ? offF[l * 3 + k] : offD[l * 3 + k];
+                TableOff &o = pass == 0 ? img->offF[l * 3 + k] : img->offD[l * 3 + k];
                 auto put = [&](const std::vector<double> &v) {
                     if (pass == 0) { std::vector<float> c(v.begin(), v.end()); return append(c.data(), c.size() * 4); }
                     return append(v.data(), v.size() * 8);
@@ -240,14 +216,15 @@ hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan
         }
         P->corr_norm[l] = prod;
     }
-    int dev_prev = -1;
-    cudaGetDevice(&dev_prev);
-    if (dev_prev != ctx->device) cudaSetDevice(ctx->device);
-    cudaError_t e = cudaMalloc(&P->tables, all.size() ? all.size() : 256);
-    if (e == cudaSuccess && all.size()) e = cudaMemcpy(P->tables, all.data(), all.size(), cudaMemcpyHostToDevice);
-    if (dev_prev != ctx->device) cudaSetDevice(dev_prev);
-    if (e != cudaSuccess) { cudaFree(P->tables); delete P; return e == cudaErrorMemoryAllocation ? HPDR_ERR_NOMEM : HPDR_ERR_CUDA; }
-    char *base = (char *)P->tables;
+    if (all.empty()) all.resize(256);
+    return HPDR_OK;
+}
+
+void bind_plan(Plan *P, const PlanImage &img, void *tables)
+{
+    P->tables = tables;
+    char *base = (char *)tables;
+    const int L = P->L;
     for (int l = 0; l <= L; l++) {
         P->gf[l].level = P->gd[l].level = l;
         P->gf[l].Nprev = P->gd[l].Nprev = l > 0 ? P->N[l - 1] : 0;
@@ -261,7 +238,7 @@ hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan
                 b.wl = b.wr = b.tap = b.ptap = b.sub = b.cp = b.inv_den = b.etap = b.mtap = nullptr; b.efirst = nullptr;
                 continue;
             }
-            const Off &o = offF[l * 3 + k], &q = offD[l * 3 + k];
+            const TableOff &o = img.offF[l * 3 + k], &q = img.offD[l * 3 + k];
             a.wl = (const float *)(base + o.wl); a.wr = (const float *)(base + o.wr);
             a.tap = (const float *)(base + o.tap); a.ptap = (const float *)(base + o.ptap);
             a.sub = (const float *)(base + o.sub); a.cp = (const float *)(base + o.cp);
@@ -276,7 +253,35 @@ hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan
             b.mtap = (const double *)(base + q.mtap);
         }
     }
-    (void)pf; (void)pd;
+}
+
+hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan **out)
+{
+    if (ndim < 1 || ndim > 3 || !dims) return HPDR_ERR_ARG;
+    for (int k = 0; k < ndim; k++)
+        if (dims[k] < 2 || dims[k] > (size_t)(1u << 30)) return HPDR_ERR_ARG;
+    std::string key = std::to_string(ndim) + (f64 ? "d" : "f");
+    for (int k = 0; k < ndim; k++) key += ":" + std::to_string(dims[k]);
+    auto it = ctx->plans.find(key);
+    if (it != ctx->plans.end()) { *out = it->second; return HPDR_OK; }
+    Plan *P = new Plan();
+    PlanImage img;
+    hpdr_status st = plan_image(ndim, dims, f64, P, &img);
+    if (st != HPDR_OK) { delete P; return st; }
+    int dev_prev = -1;
+    cudaGetDevice(&dev_prev);
+    if (dev_prev != ctx->device) cudaSetDevice(ctx->device);
+    void *tables = nullptr;
+    cudaError_t e = cudaMalloc(&tables, img.bytes.size());
+    if (e == cudaSuccess) e = cudaMemcpy(tables, img.bytes.data(), img.bytes.size(), cudaMemcpyHostToDevice);
+    if (dev_prev != ctx->device) cudaSetDevice(dev_prev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(tables);
+        delete P;
+        return e == cudaErrorMemoryAllocation ? HPDR_ERR_NOMEM : HPDR_ERR_CUDA;
+    }
+    bind_plan(P, img, tables);
     ctx->plans[key] = P;
     *out = P;
     return HPDR_OK;
