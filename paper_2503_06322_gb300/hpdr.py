@@ -9,7 +9,8 @@ fallback.
 Function names follow the C ABI:
   hpdr_compress, hpdr_decompress, hpdr_inspect, hpdr_compress_bound,
   hpdr_decompose, hpdr_recompose, hpdr_recompose_adjoint,
-  hpdr_decompose_adjoint, hpdr_huffman_encode, hpdr_huffman_decode.
+  hpdr_decompose_adjoint, hpdr_huffman_encode, hpdr_huffman_decode,
+  hpdr_decompose_noalloc.
 """
 import ctypes as C
 import os
@@ -63,6 +64,7 @@ def lib():
                                     C.c_uint64, C.POINTER(C.c_uint64), vp],
             "hpdr_huffman_decode": [vp, vp, C.c_uint64, vp, C.c_uint64, C.c_uint32, C.c_uint32,
                                     vp, vp, vp],
+            "hpdr_decompose_noalloc": [vp, vp, C.c_int, C.c_int, sz, vp],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -176,6 +178,20 @@ def hpdr_decompose(u, out=None, stream=None):
     if out is None:
         out = torch.empty(u.numel(), dtype=u.dtype, device=u.device)
     return _field_call("hpdr_decompose", u, out, u.shape, stream)
+
+
+def hpdr_decompose_noalloc(u, out=None, stream=None):
+    """hpdr_decompose without device allocation inside the library: the
+    scratch lives in a fixed device array of the library (see include/hpdr.h)."""
+    _dev_tensor(u, "u")
+    if out is None:
+        out = torch.empty(u.numel(), dtype=u.dtype, device=u.device)
+    nd, dims = _dims(u.shape)
+    with torch.cuda.device(u.device):
+        _check(lib().hpdr_decompose_noalloc(C.c_void_p(u.data_ptr()), C.c_void_p(out.data_ptr()),
+                                            _dtype_code(u.dtype), nd, dims, _stream(stream)),
+               "hpdr_decompose_noalloc")
+    return out
 
 
 def hpdr_recompose(coef, shape, out=None, stream=None):
