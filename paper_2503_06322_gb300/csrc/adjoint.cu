@@ -1,0 +1,201 @@
+// adjoint.cu -- transposes of recomposition and decomposition (the maps are
+// linear, so backward passes need no saved forward state).
+//
+// One level of recomposition is  v_l = P (v_{l-1} - S c_l) + E_new c_l  with
+// S = (x)M_{l-1}^{-1} (x)P^T M_l E_new; its transpose, from the level-l
+// gradient g_l, is
+//     g_{l-1} = P^T g_l,      g_{c_l} = g_l|new - E_new^T ((x)M_l P) (x)M_{l-1}^{-1} P^T g_l.
+// One level of decomposition is  c_l = (v - P v|kept)|new,
+// v_{l-1} = v|kept + S c_l; its transpose, from g_{c_l} and g_{v_{l-1}}, is
+//     h = g_{c_l} + E_new^T ((x)M_l P) (x)M_{l-1}^{-1} g_{v_{l-1}},
+//     g_{v_l} = E_new h + E_kept (g_{v_{l-1}} - P^T E_new h).
+// P^T is the restriction kernel with the interpolation taps, M_{l-1}^{-1} the
+// Thomas solves, and (x)M_l P is applied one dimension at a time below.
+#include <cstring>
+#include "internal.cuh"
+#include "levels.cuh"
+
+namespace hpdr {
+namespace {
+
+enum { MP_PLAIN = 0, MP_RT_FINAL = 1, MP_DT_FINAL = 2 };
+
+// out (dims s0 x s1 x s2) = (M_l P) along dim k of in (dim k of size mc_k).
+// Final modes (k = 0, output on the level-l grid):
+//   MP_RT_FINAL: stream[rank(p)] = gsrc[p] - value   at the new nodes
+//   MP_DT_FINAL: out[p] = coef[rank(p)] + value       at the new nodes
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256)
+mass_prolong_kernel(const T *__restrict__ in, T *out, long long s0, long long s1, long long s2, int k,
+                    int mck, const T *__restrict__ etap, const int *__restrict__ efirst, LevelGeom<T> g,
+                    const T *gsrc, T *stream, const T *coef)
+{
+    const long long n = s0 * s1 * s2;
+    const long long in1 = (k == 1) ? mck : s1, in2 = (k == 2) ? mck : s2;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long i2 = idx % s2, t = idx / s2;
+        const long long i1 = t % s1, i0 = t / s1;
+        const long long p = (k == 0) ? i0 : (k == 1) ? i1 : i2;
+        const int j0 = efirst[p];
+        T v = (T)0;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            const int j = j0 + i;
+            if (j < mck) {
+                const long long a0 = (k == 0) ? j : i0, a1 = (k == 1) ? j : i1, a2 = (k == 2) ? j : i2;
+                v = fma_rn(etap[p * 3 + i], in[(a0 * in1 + a1) * in2 + a2], v);
+            }
+        }
+        if (MODE == MP_PLAIN) {
+            out[idx] = v;
+        } else {
+            const int p0 = (int)i0, p1 = (int)i1, p2 = (int)i2;
+            const bool isnew = !kept_pos(g.dim[0].m, p0) || !kept_pos(g.dim[1].m, p1) || !kept_pos(g.dim[2].m, p2);
+            if (!isnew) continue;
+            long long cr = (long long)kept_before(p0) * g.dim[1].mc * g.dim[2].mc;
+            if (kept_pos(g.dim[0].m, p0)) {
+                cr += (long long)kept_before(p1) * g.dim[2].mc;
+                if (kept_pos(g.dim[1].m, p1)) cr += kept_before(p2);
+            }
+            const long long si = g.Nprev + idx - cr;
+            if (MODE == MP_RT_FINAL) stream[si] = sub_rn(gsrc[idx], v);
+            else out[idx] = add_rn(coef[si], v);
+        }
+    }
+}
+
+// decompose transpose: G(kept node of coarse q) = gv[q] - R[q]
+template <typename T>
+__global__ void set_kept_kernel(T *G, const T *gv, const T *R, LevelGeom<T> g)
+{
+    const long long c1 = g.dim[1].mc, c2 = g.dim[2].mc;
+    const long long n = (long long)g.dim[0].mc * c1 * c2;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const long long q2 = q % c2, t = q / c2;
+        const long long q1 = t % c1, q0 = t / c1;
+        const long long p0 = cpos_of(g.dim[0].m, g.dim[0].mc, (int)q0);
+        const long long p1 = cpos_of(g.dim[1].m, g.dim[1].mc, (int)q1);
+        const long long p2 = cpos_of(g.dim[2].m, g.dim[2].mc, (int)q2);
+        G[(p0 * g.dim[1].m + p1) * g.dim[2].m + p2] = sub_rn(gv[q], R[q]);
+    }
+}
+
+template <typename T>
+__global__ void copy_kernel(T *dst, const T *src, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+unsigned grid_for(long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16); }
+
+// y_f = (x)_k M_l P_k y, the last dimension-0 pass in a final mode
+template <typename T, int MODE>
+cudaError_t mass_prolong_all(const LevelGeom<T> &g, const T *y, T *t1, T *t2, T *out, const T *gsrc,
+                             T *stream, const T *coef, cudaStream_t s)
+{
+    const long long m0 = g.dim[0].m, m1 = g.dim[1].m, m2 = g.dim[2].m;
+    const long long c0 = g.dim[0].mc, c1 = g.dim[1].mc;
+    // dim 2: c0 x c1 x c2 -> c0 x c1 x m2
+    long long n = c0 * c1 * m2;
+    mass_prolong_kernel<T, MP_PLAIN><<<grid_for(n), 256, 0, s>>>(y, t1, c0, c1, m2, 2, g.dim[2].mc, g.dim[2].etap,
+                                                                g.dim[2].efirst, g, nullptr, nullptr, nullptr);
+    // dim 1: -> c0 x m1 x m2
+    n = c0 * m1 * m2;
+    mass_prolong_kernel<T, MP_PLAIN><<<grid_for(n), 256, 0, s>>>(t1, t2, c0, m1, m2, 1, g.dim[1].mc, g.dim[1].etap,
+                                                                g.dim[1].efirst, g, nullptr, nullptr, nullptr);
+    // dim 0: -> m0 x m1 x m2, final
+    n = m0 * m1 * m2;
+    mass_prolong_kernel<T, MODE><<<grid_for(n), 256, 0, s>>>(t2, out, m0, m1, m2, 0, g.dim[0].mc, g.dim[0].etap,
+                                                            g.dim[0].efirst, g, gsrc, stream, coef);
+    count_launch(3);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t recompose_adjoint_run(const Plan &P, const LevelGeom<T> *geo, const T *gu, T *gcoef, T *ga, T *gb,
+                                  T *y, T *t1, T *t2, unsigned *status, cudaStream_t s)
+{
+    const int L = P.L;
+    const T *gl = gu;
+    for (int l = L; l >= 1; l--) {
+        const LevelGeom<T> &g = geo[l];
+        T *gc = ((L - l) % 2 == 0) ? ga : gb;   // g_{l-1} = P^T g_l
+        RestrictArgs<T> a;
+        memset(&a, 0, sizeof(a));
+        a.g = g;
+        a.v = gl;
+        a.use_ptap = 1;
+        a.dense_new_only = 0;
+        a.b = gc;
+        a.status = status;
+        cudaError_t e = launch_restrict<T>(WSrc::DENSE, Sink::NONE, a, s);
+        if (e != cudaSuccess) return e;
+        const long long nc = P.N[l - 1];
+        copy_kernel<T><<<grid_for(nc), 256, 0, s>>>(y, gc, nc);
+        count_launch();
+        e = launch_solves<T>(g, y, nullptr, 0, s);
+        if (e != cudaSuccess) return e;
+        e = mass_prolong_all<T, MP_RT_FINAL>(g, y, t1, t2, nullptr, gl, gcoef, nullptr, s);
+        if (e != cudaSuccess) return e;
+        gl = gc;
+    }
+    copy_kernel<T><<<grid_for(P.N[0]), 256, 0, s>>>(gcoef, gl, P.N[0]);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t decompose_adjoint_run(const Plan &P, const LevelGeom<T> *geo, const T *gcoef, T *gu, T *ga, T *gb,
+                                  T *y, T *t1, T *t2, T *R, unsigned *status, cudaStream_t s)
+{
+    const int L = P.L;
+    T *gv = (L == 0) ? gu : ((L % 2 == 1) ? ga : gb);
+    copy_kernel<T><<<grid_for(P.N[0]), 256, 0, s>>>(gv, gcoef, P.N[0]);
+    count_launch();
+    for (int l = 1; l <= L; l++) {
+        const LevelGeom<T> &g = geo[l];
+        T *G = (l == L) ? gu : (((L - l) % 2 == 1) ? ga : gb);
+        const long long nc = P.N[l - 1];
+        copy_kernel<T><<<grid_for(nc), 256, 0, s>>>(y, gv, nc);
+        count_launch();
+        cudaError_t e = launch_solves<T>(g, y, nullptr, 0, s);
+        if (e != cudaSuccess) return e;
+        // new nodes: G = h = g_c + ((x)M_l P) y
+        e = mass_prolong_all<T, MP_DT_FINAL>(g, y, t1, t2, G, nullptr, nullptr, gcoef, s);
+        if (e != cudaSuccess) return e;
+        // kept nodes: G = gv - P^T E_new h
+        RestrictArgs<T> a;
+        memset(&a, 0, sizeof(a));
+        a.g = g;
+        a.v = G;
+        a.use_ptap = 1;
+        a.dense_new_only = 1;
+        a.b = R;
+        a.status = status;
+        e = launch_restrict<T>(WSrc::DENSE, Sink::NONE, a, s);
+        if (e != cudaSuccess) return e;
+        set_kept_kernel<T><<<grid_for(nc), 256, 0, s>>>(G, gv, R, g);
+        count_launch();
+        gv = G;
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t recompose_adjoint_run<float>(const Plan &, const LevelGeom<float> *, const float *, float *,
+                                                  float *, float *, float *, float *, float *, unsigned *,
+                                                  cudaStream_t);
+template cudaError_t recompose_adjoint_run<double>(const Plan &, const LevelGeom<double> *, const double *,
+                                                   double *, double *, double *, double *, double *, double *,
+                                                   unsigned *, cudaStream_t);
+template cudaError_t decompose_adjoint_run<float>(const Plan &, const LevelGeom<float> *, const float *, float *,
+                                                  float *, float *, float *, float *, float *, float *,
+                                                  unsigned *, cudaStream_t);
+template cudaError_t decompose_adjoint_run<double>(const Plan &, const LevelGeom<double> *, const double *,
+                                                   double *, double *, double *, double *, double *, double *,
+                                                   double *, unsigned *, cudaStream_t);
+
+}  // namespace hpdr

@@ -437,6 +437,42 @@ hpdr_status recompose_t(hpdr_ctx *ctx, const Plan *P, const T *coef, T *out, cud
     return HPDR_OK;
 }
 
+template <typename T> const LevelGeom<T> *geos(const Plan *P);
+template <> const LevelGeom<float> *geos<float>(const Plan *P) { return P->gf; }
+template <> const LevelGeom<double> *geos<double>(const Plan *P) { return P->gd; }
+
+template <typename T>
+hpdr_status adjoint_t(hpdr_ctx *ctx, const Plan *P, const T *in, T *out, bool recompose, cudaStream_t s)
+{
+    const int L = P->L;
+    size_t n1 = L >= 1 ? (size_t)P->N[L - 1] : 1, t1n = 1, t2n = 1;
+    for (int l = 1; l <= L; l++) {
+        const size_t c0 = P->m[0][l - 1], c1 = P->m[1][l - 1], m1 = P->m[1][l], m2 = P->m[2][l];
+        t1n = std::max(t1n, c0 * c1 * m2);
+        t2n = std::max(t2n, c0 * m1 * m2);
+    }
+    Carver c(nullptr);
+    c.take<Scalars>(1);
+    for (int i = 0; i < 4; i++) c.take<T>(n1);
+    c.take<T>(t1n);
+    c.take<T>(t2n);
+    hpdr_status st = ensure_workspace(ctx, c.used + 256);
+    if (st != HPDR_OK) return st;
+    Carver w(ctx->ws.base);
+    Scalars *sc = w.take<Scalars>(1);
+    T *ga = w.take<T>(n1), *gb = w.take<T>(n1), *y = w.take<T>(n1), *R = w.take<T>(n1);
+    T *t1 = w.take<T>(t1n), *t2 = w.take<T>(t2n);
+    CK(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
+    if (recompose) {
+        ProfScope ps(ctx, "adj_recompose", s);
+        CK(recompose_adjoint_run<T>(*P, geos<T>(P), in, out, ga, gb, y, t1, t2, &sc->status, s));
+    } else {
+        ProfScope ps(ctx, "adj_decompose", s);
+        CK(decompose_adjoint_run<T>(*P, geos<T>(P), in, out, ga, gb, y, t1, t2, R, &sc->status, s));
+    }
+    return HPDR_OK;
+}
+
 bool is_device_ptr(const void *p)
 {
     cudaPointerAttributes at;
@@ -677,15 +713,29 @@ hpdr_status hpdr_huffman_decode(hpdr_ctx *ctx, const uint32_t *d_words, uint64_t
 hpdr_status hpdr_recompose_adjoint(hpdr_ctx *ctx, const void *d_grad_u, void *d_grad_coef,
                                    hpdr_dtype dtype, int ndim, const size_t *dims, void *stream)
 {
-    (void)ctx; (void)d_grad_u; (void)d_grad_coef; (void)dtype; (void)ndim; (void)dims; (void)stream;
-    return HPDR_ERR_ARG;
+    if (!ctx || !d_grad_u || !d_grad_coef || (dtype != HPDR_F32 && dtype != HPDR_F64)) return HPDR_ERR_ARG;
+    DevGuard g(ctx->device);
+    Plan *P;
+    hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P);
+    if (st != HPDR_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == HPDR_F32)
+        return adjoint_t<float>(ctx, P, (const float *)d_grad_u, (float *)d_grad_coef, true, s);
+    return adjoint_t<double>(ctx, P, (const double *)d_grad_u, (double *)d_grad_coef, true, s);
 }
 
 hpdr_status hpdr_decompose_adjoint(hpdr_ctx *ctx, const void *d_grad_coef, void *d_grad_u,
                                    hpdr_dtype dtype, int ndim, const size_t *dims, void *stream)
 {
-    (void)ctx; (void)d_grad_coef; (void)d_grad_u; (void)dtype; (void)ndim; (void)dims; (void)stream;
-    return HPDR_ERR_ARG;
+    if (!ctx || !d_grad_u || !d_grad_coef || (dtype != HPDR_F32 && dtype != HPDR_F64)) return HPDR_ERR_ARG;
+    DevGuard g(ctx->device);
+    Plan *P;
+    hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P);
+    if (st != HPDR_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == HPDR_F32)
+        return adjoint_t<float>(ctx, P, (const float *)d_grad_coef, (float *)d_grad_u, false, s);
+    return adjoint_t<double>(ctx, P, (const double *)d_grad_coef, (double *)d_grad_u, false, s);
 }
 
 hpdr_status hpdr_profile_enable(hpdr_ctx *ctx, int on)

@@ -96,6 +96,16 @@ cudaError_t launch_mass_prolong(const LevelGeom<T> &g, const T *yc, T *yf, T *tm
                                 cudaStream_t s);
 
 int norm_parts();
+
+// adjoint.cu: transposes of recomposition / decomposition over all levels.
+// ga, gb, y, R hold N_{L-1} elements; t1, t2 the partial prolongations
+// (max over levels of c0*c1*m2 and c0*m1*m2 elements).
+template <typename T>
+cudaError_t recompose_adjoint_run(const Plan &P, const LevelGeom<T> *geo, const T *gu, T *gcoef, T *ga, T *gb,
+                                  T *y, T *t1, T *t2, unsigned *status, cudaStream_t s);
+template <typename T>
+cudaError_t decompose_adjoint_run(const Plan &P, const LevelGeom<T> *geo, const T *gcoef, T *gu, T *ga, T *gb,
+                                  T *y, T *t1, T *t2, T *R, unsigned *status, cudaStream_t s);
 // ochunk[c] = first outlier with stream index >= c*K, c = 0..nch
 cudaError_t launch_outlier_chunks(const unsigned long long *out_idx, unsigned long long n_out,
                                   unsigned K, unsigned long long nch, unsigned long long *ochunk,
