@@ -153,6 +153,32 @@ hpdr_status hpdr_huffman_decode(hpdr_ctx *ctx, const uint32_t *d_words, uint64_t
                                 const uint64_t *d_chunk_bits, uint64_t N, uint32_t D, uint32_t K,
                                 const uint8_t *d_lengths, uint16_t *d_symbols, void *stream);
 
+/* Compression of a host-resident field in slabs along its first dimension
+ * (the host-device pipeline of Sec. V: Fig. 7 and Alg. 4 with a fixed slab
+ * size).  Host-to-device copies, compression and device-to-host copies run on
+ * three streams owned by the context, with two input and two output device
+ * buffers; slab i+1 is copied in while slab i is compressed and slab i-1 is
+ * copied out.  Every slab is compressed on its own with the given bound
+ * (relative bounds use the slab's own norm, never larger than the field's,
+ * so the field's bound holds).
+ *   h_in        host array (pinned memory gives overlapped copies).
+ *   slab_bytes  target slab size (0: 256 MiB); at least two planes per slab.
+ *   h_out       host buffer of out_capacity bytes receiving the streamed
+ *               container: "HPDS" directory (64 bytes + 32 per slab: first
+ *               plane, planes, byte offset, bytes) followed by the slab
+ *               containers (format v1) at 16-byte boundaries.
+ *   out_bytes   receives the size.
+ * Synchronous.  Errors as hpdr_compress. */
+hpdr_status hpdr_compress_host_streamed(hpdr_ctx *ctx, const void *h_in, hpdr_dtype dtype, int ndim,
+                                        const size_t *dims, double tol, hpdr_tol_kind tol_kind,
+                                        hpdr_mode mode, const hpdr_config *cfg, size_t slab_bytes,
+                                        void *h_out, size_t out_capacity, size_t *out_bytes);
+
+/* Inverse of hpdr_compress_host_streamed with the same three-stream
+ * pipeline: h_out (host, out_capacity bytes) receives the field. */
+hpdr_status hpdr_decompress_host_streamed(hpdr_ctx *ctx, const void *h_in, size_t in_bytes, void *h_out,
+                                          size_t out_capacity);
+
 /* Decomposition for callers that cannot allocate device memory on their call
  * path -- for example code running while a stream is captured into a CUDA
  * graph (allocation calls are not permitted in a global-mode capture), or a

@@ -508,6 +508,7 @@ hpdr_status hpdr_ctx_destroy(hpdr_ctx *ctx)
 {
     if (!ctx) return HPDR_ERR_ARG;
     DevGuard g(ctx->device);
+    destroy_stream_res(ctx);
     for (auto &kv : ctx->plans) { cudaFree(kv.second->tables); delete kv.second; }
     if (ctx->ws.base) cudaFree(ctx->ws.base);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);

@@ -179,6 +179,7 @@ struct hpdr_ctx {
     std::vector<std::string> prof_names;
     std::vector<double> prof_ms;
     std::vector<long long> prof_cnt;
+    void *stream_res = nullptr;    // streams, events and slab buffers of the host-streamed pipeline
 };
 
 namespace hpdr {
@@ -211,6 +212,9 @@ void bind_plan(Plan *P, const PlanImage &img, void *tables);
 hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan **out);
 hpdr_status ensure_workspace(hpdr_ctx *ctx, size_t bytes);
 int levels_of(int ndim, const size_t *dims);
+
+// streamed.cu
+void destroy_stream_res(hpdr_ctx *ctx);
 
 inline hpdr_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HPDR_OK : HPDR_ERR_CUDA; }
 

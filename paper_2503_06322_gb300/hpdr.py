@@ -65,6 +65,9 @@ def lib():
             "hpdr_huffman_decode": [vp, vp, C.c_uint64, vp, C.c_uint64, C.c_uint32, C.c_uint32,
                                     vp, vp, vp],
             "hpdr_decompose_noalloc": [vp, vp, C.c_int, C.c_int, sz, vp],
+            "hpdr_compress_host_streamed": [vp, vp, C.c_int, C.c_int, sz, C.c_double, C.c_int, C.c_int,
+                                            C.POINTER(Config), C.c_size_t, vp, C.c_size_t, sz],
+            "hpdr_decompress_host_streamed": [vp, vp, C.c_size_t, vp, C.c_size_t],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -191,6 +194,53 @@ def hpdr_decompose_noalloc(u, out=None, stream=None):
         _check(lib().hpdr_decompose_noalloc(C.c_void_p(u.data_ptr()), C.c_void_p(out.data_ptr()),
                                             _dtype_code(u.dtype), nd, dims, _stream(stream)),
                "hpdr_decompose_noalloc")
+    return out
+
+
+def streamed_bound(shape, dtype=torch.float32, slab_bytes=256 << 20, dict_size=8192, chunk=1024):
+    """Capacity that always holds the streamed container of a field."""
+    esz = 4 if dtype == torch.float32 else 8
+    plane = esz
+    for s in shape[1:]:
+        plane *= int(s)
+    per = max(2, slab_bytes // plane) if len(shape) > 1 else int(shape[0])
+    nslab = max(1, -(-int(shape[0]) // per))
+    slab = (min(per + 1, int(shape[0])),) + tuple(shape[1:])
+    return 64 + 32 * nslab + 16 + nslab * (hpdr_compress_bound(slab, dtype, dict_size, chunk) + 16)
+
+
+def hpdr_compress_host_streamed(u, tol, tol_kind=REL, mode=LINF, slab_bytes=256 << 20, dict_size=8192,
+                                chunk=1024, out=None, device=None):
+    """Compress a CPU tensor (pinned for overlapped copies) in slabs; returns a
+    CPU uint8 tensor holding the streamed container."""
+    if u.is_cuda or not u.is_contiguous():
+        raise TypeError("u must be a contiguous CPU tensor")
+    nd, dims = _dims(u.shape)
+    cfg = _cfg(dict_size, chunk)
+    if out is None:
+        out = torch.empty(streamed_bound(u.shape, u.dtype, slab_bytes, dict_size, chunk), dtype=torch.uint8,
+                          pin_memory=True)
+    nb = C.c_size_t()
+    _check(lib().hpdr_compress_host_streamed(context(device), C.c_void_p(u.data_ptr()), _dtype_code(u.dtype),
+                                             nd, dims, float(tol), int(tol_kind), int(mode), C.byref(cfg),
+                                             int(slab_bytes), C.c_void_p(out.data_ptr()), out.numel(),
+                                             C.byref(nb)), "hpdr_compress_host_streamed")
+    return out[:nb.value]
+
+
+def hpdr_decompress_host_streamed(buf, out=None, device=None):
+    """Inverse of hpdr_compress_host_streamed (CPU tensors in and out)."""
+    b = bytes(buf[:64].numpy().tobytes())
+    ns = int.from_bytes(b[8:12], "little")
+    dt = torch.float32 if int.from_bytes(b[12:16], "little") == 0 else torch.float64
+    nd = int.from_bytes(b[40:44], "little")
+    shape = tuple(int.from_bytes(b[16 + 8 * k:24 + 8 * k], "little") for k in range(nd))
+    if out is None:
+        out = torch.empty(shape, dtype=dt, pin_memory=True)
+    _check(lib().hpdr_decompress_host_streamed(context(device), C.c_void_p(buf.data_ptr()), buf.numel(),
+                                               C.c_void_p(out.data_ptr()), out.numel() * out.element_size()),
+           "hpdr_decompress_host_streamed")
+    del ns
     return out
 
 
