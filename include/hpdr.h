@@ -153,6 +153,39 @@ hpdr_status hpdr_huffman_decode(hpdr_ctx *ctx, const uint32_t *d_words, uint64_t
                                 const uint64_t *d_chunk_bits, uint64_t N, uint32_t D, uint32_t K,
                                 const uint8_t *d_lengths, uint16_t *d_symbols, void *stream);
 
+/* One field of a batch. */
+typedef struct {
+    const void *d_in;        /* device array, 16-byte aligned */
+    hpdr_dtype dtype;
+    int ndim;
+    size_t dims[3];
+    double tol;
+    hpdr_tol_kind tol_kind;
+    hpdr_mode mode;
+} hpdr_field;
+
+/* Compress many fields of uneven shapes (each with its own bound) in one
+ * replay of a CUDA graph.  The first call with a given batch (fields,
+ * pointers, config) captures every field's whole compression into one graph,
+ * forked over K worker streams (fields assigned largest first to the least-
+ * loaded stream); an autotuner captures K = 1, 2, 4, 8, 16, times one replay
+ * of each and keeps the fastest.  Later calls with the same batch only
+ * replay it (one graph launch, one wait).  Each field's container is
+ * byte-identical to hpdr_compress on that field.
+ *   d_out          device buffer of out_capacity bytes;
+ *   out_offsets    host [nfields+1]: field i's container starts at
+ *                  d_out + out_offsets[i] (256-byte aligned slots of
+ *                  hpdr_compress_bound bytes); out_offsets[nfields] = bytes used;
+ *   out_sizes      host [nfields]: container sizes.
+ * The context keeps one workspace per field of a cached batch.  Synchronous
+ * (waits for the replay).  Errors as hpdr_compress. */
+hpdr_status hpdr_compress_batched(hpdr_ctx *ctx, int nfields, const hpdr_field *fields, const hpdr_config *cfg,
+                                  void *d_out, size_t out_capacity, size_t *out_offsets, size_t *out_sizes,
+                                  void *stream);
+
+/* Stream count the autotuner chose for the last cached batch (0: none). */
+int hpdr_batched_streams(hpdr_ctx *ctx);
+
 /* Compression of a host-resident field in slabs along its first dimension
  * (the host-device pipeline of Sec. V: Fig. 7 and Alg. 4 with a fixed slab
  * size).  Host-to-device copies, compression and device-to-host copies run on

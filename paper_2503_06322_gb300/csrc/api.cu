@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cmath>
 #include <new>
+#include <algorithm>
 #include "internal.cuh"
 #include "levels.cuh"
 #include "huffman.cuh"
@@ -137,16 +138,13 @@ template <> const LevelGeom<double> &geom<double>(const Plan *P, int l) { return
         if (_e != cudaSuccess) { return HPDR_ERR_CUDA; }         \
     } while (0)
 
+// the whole compression of one field, enqueued on s without any host wait;
+// the container size and status stay in w.sc (device)
 template <typename T>
-hpdr_status compress_t(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, const size_t *dims,
-                       double tol, int tol_kind, int mode, unsigned D, unsigned K, uint8_t *out,
-                       size_t cap, size_t *out_bytes, cudaStream_t s)
+hpdr_status compress_core(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, const size_t *dims, double tol,
+                          int tol_kind, int mode, unsigned D, unsigned K, uint8_t *out, size_t cap, const Ws &w,
+                          cudaStream_t s)
 {
-    Ws w;
-    size_t need = carve_ws(nullptr, P, sizeof(T), D, K, true, &w);
-    hpdr_status st = ensure_workspace(ctx, need);
-    if (st != HPDR_OK) return st;
-    carve_ws(ctx->ws.base, P, sizeof(T), D, K, true, &w);
     const int L = P->L;
     const long long N = P->N[L];
     CK(cudaMemsetAsync(w.sc, 0, sizeof(Scalars), s));
@@ -221,6 +219,21 @@ hpdr_status compress_t(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, const
     for (int k = 0; k < 3; k++) h.dims[k] = k < ndim ? dims[k] : 1;
     h.D = D; h.K = K; h.tol = tol; h.N = (unsigned long long)N;
     CK(launch_header(h, hs.len, w.sc, out, s));
+    return HPDR_OK;
+}
+
+template <typename T>
+hpdr_status compress_t(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, const size_t *dims,
+                       double tol, int tol_kind, int mode, unsigned D, unsigned K, uint8_t *out,
+                       size_t cap, size_t *out_bytes, cudaStream_t s)
+{
+    Ws w;
+    size_t need = carve_ws(nullptr, P, sizeof(T), D, K, true, &w);
+    hpdr_status st = ensure_workspace(ctx, need);
+    if (st != HPDR_OK) return st;
+    carve_ws(ctx->ws.base, P, sizeof(T), D, K, true, &w);
+    st = compress_core<T>(ctx, P, u, ndim, dims, tol, tol_kind, mode, D, K, out, cap, w, s);
+    if (st != HPDR_OK) return st;
     Scalars *hsc = (Scalars *)ctx->host_pinned;
     CK(cudaMemcpyAsync(hsc, w.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -473,6 +486,119 @@ hpdr_status adjoint_t(hpdr_ctx *ctx, const Plan *P, const T *in, T *out, bool re
     return HPDR_OK;
 }
 
+// ---- batched compression ------------------------------------------------
+__global__ void store_size_kernel(const Scalars *sc, unsigned long long *dst)
+{
+    dst[0] = sc->out_bytes;
+    dst[1] = sc->status;
+}
+
+struct BatchPlan {
+    int nfields = 0;
+    std::vector<Plan *> plans;
+    std::vector<size_t> ws_off, out_off, bound;
+    size_t ws_total = 0;
+    void *ws = nullptr;
+    unsigned long long *sizes = nullptr;   // device [nfields][2]: container bytes, status
+    cudaGraphExec_t exec = nullptr;
+    int streams = 0;
+    double tuned_ms = 0.0;
+};
+
+struct BatchRes {
+    cudaStream_t origin = nullptr;
+    std::vector<cudaStream_t> workers;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    std::map<std::string, BatchPlan *> plans;
+};
+
+hpdr_status batch_res(hpdr_ctx *ctx, BatchRes *&r, int nworkers)
+{
+    if (!ctx->batch_res) {
+        r = new BatchRes();
+        if (cudaStreamCreateWithFlags(&r->origin, cudaStreamNonBlocking) != cudaSuccess) return HPDR_ERR_CUDA;
+        if (cudaEventCreateWithFlags(&r->fork, cudaEventDisableTiming) != cudaSuccess) return HPDR_ERR_CUDA;
+        ctx->batch_res = r;
+    }
+    r = (BatchRes *)ctx->batch_res;
+    while ((int)r->workers.size() < nworkers) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return HPDR_ERR_CUDA;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return HPDR_ERR_CUDA;
+        r->workers.push_back(st);
+        r->join.push_back(ev);
+    }
+    return HPDR_OK;
+}
+
+// fields assigned largest first to the least-loaded of K streams
+std::vector<std::vector<int>> schedule(const hpdr_field *f, int n, int K)
+{
+    std::vector<int> order(n);
+    for (int i = 0; i < n; i++) order[i] = i;
+    auto work = [&](int i) {
+        double w = f[i].dtype == HPDR_F64 ? 8.0 : 4.0;
+        for (int k = 0; k < f[i].ndim; k++) w *= (double)f[i].dims[k];
+        return w;
+    };
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+    std::vector<std::vector<int>> q(K);
+    std::vector<double> load(K, 0.0);
+    for (int i : order) {
+        int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        q[k].push_back(i);
+        load[k] += work(i);
+    }
+    return q;
+}
+
+hpdr_status enqueue_batch(hpdr_ctx *ctx, BatchRes *r, BatchPlan *bp, const hpdr_field *f, unsigned D, unsigned K,
+                          uint8_t *d_out, int nstreams)
+{
+    if (cudaEventRecord(r->fork, r->origin) != cudaSuccess) return HPDR_ERR_CUDA;
+    std::vector<std::vector<int>> q = schedule(f, bp->nfields, nstreams);
+    for (int k = 0; k < nstreams; k++) {
+        cudaStream_t st = r->workers[k];
+        if (cudaStreamWaitEvent(st, r->fork, 0) != cudaSuccess) return HPDR_ERR_CUDA;
+        for (int i : q[k]) {
+            const Plan *P = bp->plans[i];
+            const bool f64 = f[i].dtype == HPDR_F64;
+            Ws w;
+            carve_ws((char *)bp->ws + bp->ws_off[i], P, f64 ? 8 : 4, D, K, true, &w);
+            hpdr_status stt;
+            if (f64)
+                stt = compress_core<double>(ctx, P, (const double *)f[i].d_in, f[i].ndim, f[i].dims, f[i].tol,
+                                            f[i].tol_kind, f[i].mode, D, K, d_out + bp->out_off[i], bp->bound[i], w, st);
+            else
+                stt = compress_core<float>(ctx, P, (const float *)f[i].d_in, f[i].ndim, f[i].dims, f[i].tol,
+                                           f[i].tol_kind, f[i].mode, D, K, d_out + bp->out_off[i], bp->bound[i], w, st);
+            if (stt != HPDR_OK) return stt;
+            store_size_kernel<<<1, 1, 0, st>>>(w.sc, bp->sizes + 2 * i);
+            count_launch();
+        }
+        if (cudaEventRecord(r->join[k], st) != cudaSuccess) return HPDR_ERR_CUDA;
+        if (cudaStreamWaitEvent(r->origin, r->join[k], 0) != cudaSuccess) return HPDR_ERR_CUDA;
+    }
+    return HPDR_OK;
+}
+
+hpdr_status capture_batch(hpdr_ctx *ctx, BatchRes *r, BatchPlan *bp, const hpdr_field *f, unsigned D, unsigned K,
+                          uint8_t *d_out, int nstreams, cudaGraphExec_t *exec)
+{
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(r->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HPDR_ERR_CUDA;
+    hpdr_status st = enqueue_batch(ctx, r, bp, f, D, K, d_out, nstreams);
+    cudaError_t e = cudaStreamEndCapture(r->origin, &g);
+    if (st != HPDR_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) { cudaGetLastError(); return HPDR_ERR_CUDA; }
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { cudaGetLastError(); return HPDR_ERR_CUDA; }
+    return HPDR_OK;
+}
+
 bool is_device_ptr(const void *p)
 {
     cudaPointerAttributes at;
@@ -509,6 +635,20 @@ hpdr_status hpdr_ctx_destroy(hpdr_ctx *ctx)
     if (!ctx) return HPDR_ERR_ARG;
     DevGuard g(ctx->device);
     destroy_stream_res(ctx);
+    if (ctx->batch_res) {
+        BatchRes *r = (BatchRes *)ctx->batch_res;
+        for (auto &kv : r->plans) {
+            if (kv.second->exec) cudaGraphExecDestroy(kv.second->exec);
+            cudaFree(kv.second->ws);
+            cudaFree(kv.second->sizes);
+            delete kv.second;
+        }
+        for (auto st : r->workers) cudaStreamDestroy(st);
+        for (auto ev : r->join) cudaEventDestroy(ev);
+        if (r->fork) cudaEventDestroy(r->fork);
+        if (r->origin) cudaStreamDestroy(r->origin);
+        delete r;
+    }
     for (auto &kv : ctx->plans) { cudaFree(kv.second->tables); delete kv.second; }
     if (ctx->ws.base) cudaFree(ctx->ws.base);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
@@ -524,11 +664,15 @@ size_t hpdr_compress_bound(int ndim, const size_t *dims, hpdr_dtype dtype, const
     for (int k = 0; k < ndim; k++) if (dims[k] < 2 || dims[k] > (1u << 30)) return 0;
     int L = levels_of(ndim, dims);
     unsigned long long N = (unsigned long long)total_of(ndim, dims);
+    // a Huffman code is never longer in total than the fixed-length code of
+    // ceil(log2 D) bits per symbol; the outlier list holds at most out_cap_of(N)
+    unsigned bpsym = 1;
+    while ((1ULL << bpsym) < D) bpsym++;
     unsigned long long b = a16(128 + 8ULL * (L + 1));
     b = a16(b + D);
     b = a16(b + 8 * ((N + K - 1) / K));
-    b = a16(b + 16 * N);
-    b += 4 * ((63 * N + 31) / 32);
+    b = a16(b + 16 * out_cap_of((long long)N));
+    b += 4 * ((bpsym * N + 31) / 32);
     return (size_t)b;
 }
 
@@ -778,6 +922,144 @@ int hpdr_profile_read(hpdr_ctx *ctx, const char **names, double *ms, long long *
 }
 
 unsigned long long hpdr_launch_count(void) { return g_launches; }
+
+hpdr_status hpdr_compress_batched(hpdr_ctx *ctx, int nfields, const hpdr_field *fields, const hpdr_config *cfg,
+                                  void *d_out, size_t out_capacity, size_t *out_offsets, size_t *out_sizes,
+                                  void *stream)
+{
+    unsigned D, K;
+    if (!ctx || nfields < 1 || !fields || !d_out || !out_offsets || !out_sizes || !valid_cfg(cfg, D, K))
+        return HPDR_ERR_ARG;
+    if ((uintptr_t)d_out & 15) return HPDR_ERR_ARG;
+    DevGuard g(ctx->device);
+    // key: everything the captured graph depends on
+    std::string key = std::to_string(nfields) + "|" + std::to_string(D) + "|" + std::to_string(K) + "|" +
+                      std::to_string((uintptr_t)d_out);
+    size_t off = 0;
+    for (int i = 0; i < nfields; i++) {
+        const hpdr_field &f = fields[i];
+        if (!f.d_in || ((uintptr_t)f.d_in & 15) || (f.dtype != HPDR_F32 && f.dtype != HPDR_F64) ||
+            (f.mode != HPDR_LINF && f.mode != HPDR_L2) || (f.tol_kind != HPDR_ABS && f.tol_kind != HPDR_REL) ||
+            !(f.tol > 0.0) || !std::isfinite(f.tol))
+            return HPDR_ERR_ARG;
+        const size_t b = hpdr_compress_bound(f.ndim, f.dims, f.dtype, cfg);
+        if (!b) return HPDR_ERR_ARG;
+        out_offsets[i] = off;
+        off = (off + b + 255) & ~size_t(255);
+        char buf[160];
+        snprintf(buf, sizeof(buf), "|%p,%d,%d,%zu,%zu,%zu,%.17g,%d,%d", f.d_in, (int)f.dtype, f.ndim, f.dims[0],
+                 f.ndim > 1 ? f.dims[1] : 1, f.ndim > 2 ? f.dims[2] : 1, f.tol, (int)f.tol_kind, (int)f.mode);
+        key += buf;
+    }
+    out_offsets[nfields] = off;
+    if (off > out_capacity) return HPDR_ERR_CAPACITY;
+    BatchRes *r = nullptr;
+    hpdr_status st = batch_res(ctx, r, 16);
+    if (st != HPDR_OK) return st;
+    cudaStream_t user = (cudaStream_t)stream;
+    BatchPlan *bp;
+    auto it = r->plans.find(key);
+    if (it != r->plans.end()) {
+        bp = it->second;
+    } else {
+        bp = new BatchPlan();
+        bp->nfields = nfields;
+        bp->plans.resize(nfields);
+        bp->ws_off.resize(nfields);
+        bp->out_off.resize(nfields);
+        bp->bound.resize(nfields);
+        size_t wsz = 0;
+        for (int i = 0; i < nfields; i++) {
+            const hpdr_field &f = fields[i];
+            st = get_plan(ctx, f.ndim, f.dims, f.dtype == HPDR_F64, &bp->plans[i]);
+            if (st != HPDR_OK) { delete bp; return st; }
+            Ws w;
+            const size_t need = carve_ws(nullptr, bp->plans[i], f.dtype == HPDR_F64 ? 8 : 4, D, K, true, &w);
+            bp->ws_off[i] = wsz;
+            wsz = (wsz + need + 255) & ~size_t(255);
+            bp->out_off[i] = out_offsets[i];
+            bp->bound[i] = out_offsets[i + 1 <= nfields ? i + 1 : i] - out_offsets[i];
+        }
+        bp->ws_total = wsz;
+        if (cudaMalloc(&bp->ws, wsz) != cudaSuccess || cudaMalloc(&bp->sizes, 16ull * nfields) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(bp->ws);
+            delete bp;
+            return HPDR_ERR_NOMEM;
+        }
+        // one eager run (sets kernel attributes, warms the plans), then the
+        // autotuner: capture the batch for every stream count and keep the fastest replay
+        const bool prof = ctx->prof_on;
+        ctx->prof_on = false;
+        st = enqueue_batch(ctx, r, bp, fields, D, K, (uint8_t *)d_out, 1);
+        if (st == HPDR_OK && cudaStreamSynchronize(r->origin) != cudaSuccess) st = HPDR_ERR_CUDA;
+        cudaEvent_t t0, t1;
+        cudaEventCreate(&t0);
+        cudaEventCreate(&t1);
+        const int cand[5] = {1, 2, 4, 8, 16};
+        for (int ci = 0; ci < 5 && st == HPDR_OK; ci++) {
+            const int ns = cand[ci];
+            if (ns > nfields && ns > 1) break;
+            cudaGraphExec_t ex = nullptr;
+            st = capture_batch(ctx, r, bp, fields, D, K, (uint8_t *)d_out, ns, &ex);
+            if (st != HPDR_OK) break;
+            cudaGraphLaunch(ex, r->origin);
+            cudaEventRecord(t0, r->origin);
+            cudaGraphLaunch(ex, r->origin);
+            cudaEventRecord(t1, r->origin);
+            if (cudaEventSynchronize(t1) != cudaSuccess) { st = HPDR_ERR_CUDA; cudaGraphExecDestroy(ex); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, t0, t1);
+            if (!bp->exec || ms < bp->tuned_ms) {
+                if (bp->exec) cudaGraphExecDestroy(bp->exec);
+                bp->exec = ex;
+                bp->streams = ns;
+                bp->tuned_ms = ms;
+            } else {
+                cudaGraphExecDestroy(ex);
+            }
+        }
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        ctx->prof_on = prof;
+        if (st != HPDR_OK) {
+            if (bp->exec) cudaGraphExecDestroy(bp->exec);
+            cudaFree(bp->ws);
+            cudaFree(bp->sizes);
+            delete bp;
+            return st;
+        }
+        r->plans[key] = bp;
+    }
+    // replay: the caller's stream orders the graph before and after
+    cudaEvent_t ev = r->fork;
+    CK(cudaEventRecord(ev, user));
+    CK(cudaStreamWaitEvent(r->origin, ev, 0));
+    {
+        ProfScope ps(ctx, "batched_graph", r->origin);
+        CK(cudaGraphLaunch(bp->exec, r->origin));
+    }
+    count_launch();
+    unsigned long long *hs = (unsigned long long *)ctx->host_pinned;
+    std::vector<unsigned long long> sizes(2 * (size_t)nfields);
+    CK(cudaMemcpyAsync(sizes.data(), bp->sizes, 16ull * nfields, cudaMemcpyDeviceToHost, r->origin));
+    CK(cudaStreamSynchronize(r->origin));
+    (void)hs;
+    for (int i = 0; i < nfields; i++) {
+        if (sizes[2 * i + 1]) return map_device_status((unsigned)sizes[2 * i + 1]);
+        out_sizes[i] = (size_t)sizes[2 * i];
+    }
+    return HPDR_OK;
+}
+
+int hpdr_batched_streams(hpdr_ctx *ctx)
+{
+    if (!ctx || !ctx->batch_res) return 0;
+    BatchRes *r = (BatchRes *)ctx->batch_res;
+    int s = 0;
+    for (auto &kv : r->plans) s = kv.second->streams;
+    return s;
+}
 
 const char *hpdr_status_string(hpdr_status st)
 {

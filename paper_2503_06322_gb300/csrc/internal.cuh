@@ -180,6 +180,7 @@ struct hpdr_ctx {
     std::vector<double> prof_ms;
     std::vector<long long> prof_cnt;
     void *stream_res = nullptr;    // streams, events and slab buffers of the host-streamed pipeline
+    void *batch_res = nullptr;     // worker streams and captured graphs of batched compression
 };
 
 namespace hpdr {

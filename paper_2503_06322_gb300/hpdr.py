@@ -37,6 +37,11 @@ class Config(C.Structure):
     _fields_ = [("dict_size", C.c_uint32), ("chunk", C.c_uint32)]
 
 
+class Field(C.Structure):
+    _fields_ = [("d_in", C.c_void_p), ("dtype", C.c_int), ("ndim", C.c_int), ("dims", C.c_size_t * 3),
+                ("tol", C.c_double), ("tol_kind", C.c_int), ("mode", C.c_int)]
+
+
 _lib = None
 _ctx = {}
 
@@ -68,6 +73,9 @@ def lib():
             "hpdr_compress_host_streamed": [vp, vp, C.c_int, C.c_int, sz, C.c_double, C.c_int, C.c_int,
                                             C.POINTER(Config), C.c_size_t, vp, C.c_size_t, sz],
             "hpdr_decompress_host_streamed": [vp, vp, C.c_size_t, vp, C.c_size_t],
+            "hpdr_compress_batched": [vp, C.c_int, C.POINTER(Field), C.POINTER(Config), vp, C.c_size_t,
+                                      sz, sz, vp],
+            "hpdr_batched_streams": [vp],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -242,6 +250,37 @@ def hpdr_decompress_host_streamed(buf, out=None, device=None):
            "hpdr_decompress_host_streamed")
     del ns
     return out
+
+
+def batched_capacity(shapes_dtypes, dict_size=8192, chunk=1024):
+    """Output bytes hpdr_compress_batched needs for these (shape, dtype) fields."""
+    total = 0
+    for shape, dt in shapes_dtypes:
+        total = (total + hpdr_compress_bound(shape, dt, dict_size, chunk) + 255) & ~255
+    return total
+
+
+def hpdr_compress_batched(fields, tols, tol_kind=REL, mode=LINF, dict_size=8192, chunk=1024, out=None,
+                          stream=None):
+    """Compress a list of CUDA fields (one graph replay; see include/hpdr.h).
+    Returns (out uint8 tensor, offsets list, sizes list)."""
+    n = len(fields)
+    arr = (Field * n)()
+    for i, (u, tol) in enumerate(zip(fields, tols)):
+        _dev_tensor(u, "field")
+        nd, dims = _dims(u.shape)
+        arr[i] = Field(C.c_void_p(u.data_ptr()), _dtype_code(u.dtype), nd, dims, float(tol), int(tol_kind),
+                       int(mode))
+    if out is None:
+        out = torch.empty(batched_capacity([(u.shape, u.dtype) for u in fields], dict_size, chunk),
+                          dtype=torch.uint8, device=fields[0].device)
+    cfg = _cfg(dict_size, chunk)
+    offs = (C.c_size_t * (n + 1))()
+    sizes = (C.c_size_t * n)()
+    _check(lib().hpdr_compress_batched(context(fields[0].device.index), n, arr, C.byref(cfg),
+                                       C.c_void_p(out.data_ptr()), out.numel(), offs, sizes, _stream(stream)),
+           "hpdr_compress_batched")
+    return out, list(offs), list(sizes)
 
 
 def hpdr_recompose(coef, shape, out=None, stream=None):

@@ -1,0 +1,34 @@
+"""Batched compression (one graph replay): every field's container is
+byte-identical to the plain API on that field, and replays repeat it."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+def test_batched_matches_plain_and_replays(oracle):
+    from paper_2503_06322_gb300 import fields, hpdr
+    shapes = fields.batch_shapes(count=24, seed=11, lo=17, hi=90)
+    us, tols = [], []
+    for i, (shape, tol) in enumerate(shapes):
+        us.append(torch.from_numpy(fields.powerlaw_field(shape, seed=100 + i)).cuda())
+        tols.append(tol)
+    us.append(torch.from_numpy(fields.powerlaw_field((40, 30, 20), seed=99, dtype=np.float64)).cuda())
+    tols.append(1e-3)
+    out, offs, sizes = hpdr.hpdr_compress_batched(us, tols)
+    for i, (u, tol) in enumerate(zip(us, tols)):
+        plain = hpdr.hpdr_compress(u, tol)
+        got = out[offs[i]:offs[i] + sizes[i]]
+        assert sizes[i] == plain.numel()
+        assert torch.equal(got, plain)
+        rec = hpdr.hpdr_decompress(got.clone())
+        un = u.double()
+        assert (rec.double() - un).abs().max().item() <= tol * un.abs().max().item()
+    out2, offs2, sizes2 = hpdr.hpdr_compress_batched(us, tols, out=out)
+    assert offs2 == offs and sizes2 == sizes
+    assert hpdr.lib().hpdr_batched_streams(hpdr.context()) in (1, 2, 4, 8, 16)
+    # one container through the oracle
+    h = out[offs[3]:offs[3] + sizes[3]].cpu().numpy()
+    u3 = us[3].cpu().numpy().astype(np.float64)
+    assert np.abs(oracle.decompress(h) - u3).max() <= tols[3] * np.abs(u3).max()
