@@ -42,6 +42,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-to-host leg")
     ap.add_argument("--cpu-planes", type=int, default=65,
                     help="planes of the field in the CPU-baseline sample")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the 257^3 adjoint leg")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-field batched leg")
+    ap.add_argument("--no-stream", action="store_true", help="skip the 1025^3 host-streamed leg")
     return ap.parse_args()
 
 
@@ -296,50 +299,158 @@ def _parse_bits(buf):
 
 
 def run_e2e(args, u, out):
-    """Host-to-host: pinned field -> H2D -> compress -> D2H container -> H2D
-    container -> decompress -> D2H field, all inside the timed region."""
+    """Host to host through the public streamed API: a pinned host field is
+    compressed (slabs copied in, compressed, containers copied out, overlapped
+    on three streams) and the container decompressed back to host memory."""
     import torch
     from paper_2503_06322_gb300 import hpdr
-    dev = u.device
-    stream = torch.cuda.current_stream()
     h_in = torch.empty(u.shape, dtype=u.dtype, pin_memory=True)
     h_in.copy_(u.cpu())
     h_out = torch.empty_like(h_in).pin_memory()
-    d_in = torch.empty_like(u)
-    d_rec = torch.empty_like(u)
-    cap = hpdr.hpdr_compress_bound(u.shape, u.dtype)
-    cbuf = torch.empty(cap, dtype=torch.uint8, device=dev)
+    cap = hpdr.streamed_bound(u.shape, u.dtype)
     h_c = torch.empty(cap, dtype=torch.uint8, pin_memory=True)
-    d_c2 = torch.empty(cap, dtype=torch.uint8, device=dev)
 
     def step():
-        d_in.copy_(h_in, non_blocking=True)
-        b = hpdr.hpdr_compress(d_in, args.tol, out=cbuf)
-        n = b.numel()
-        h_c[:n].copy_(b, non_blocking=True)
-        d_c2[:n].copy_(h_c[:n], non_blocking=True)
-        hpdr.hpdr_decompress(d_c2[:n], out=d_rec)
-        h_out.copy_(d_rec, non_blocking=True)
-        return n
+        b = hpdr.hpdr_compress_host_streamed(h_in, args.tol, out=h_c)
+        hpdr.hpdr_decompress_host_streamed(b, out=h_out)
+        return b.numel()
 
     for _ in range(2):
         step()
-    torch.cuda.synchronize()
-    k = max(3, min(args.steps, 20))
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    k = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
     nb = 0
     for _ in range(k):
         nb = step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / k
+    ms = (time.perf_counter() - t0) * 1e3 / k
     fb = u.numel() * u.element_size()
+    err = (h_out.double() - h_in.double()).abs().max().item() / (args.tol * h_in.abs().max().item())
     return {"value": round(2.0 * fb / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": fb + nb, "d2h_bytes_per_step": nb + fb,
-            "ms_per_step": round(ms, 3), "steps": k,
-            "path": "pinned host field -> H2D -> hpdr_compress -> D2H -> H2D -> hpdr_decompress -> D2H"}
+            "ms_per_step": round(ms, 3), "steps": k, "max_err_over_tau": round(err, 4),
+            "path": "pinned host field -> hpdr_compress_host_streamed (256 MiB slabs) -> "
+                    "hpdr_decompress_host_streamed -> pinned host field (wall clock)"}
+
+
+def run_adjoint(args, dev):
+    """257^3 FP32 coefficient set; loss = mean((R(c) - t)^2) through the
+    autograd wrapper (forward hpdr_recompose, backward hpdr_recompose_adjoint)."""
+    import torch
+    from paper_2503_06322_gb300 import autograd, fields, hpdr
+    shape = (257, 257, 257)
+    u0 = fields.powerlaw_field_torch(shape, seed=4, device=dev)
+    t = fields.powerlaw_field_torch(shape, seed=5, device=dev)
+    c0 = hpdr.hpdr_decompose(u0)
+
+    def step():
+        c = c0.detach().requires_grad_(True)
+        loss = ((autograd.recompose(c, shape) - t) ** 2).mean()
+        loss.backward()
+        return c.grad
+
+    for _ in range(3):
+        step()
+    k = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(k):
+        g = step()
+    e1.record()
+    torch.cuda.synchronize()
+    fwd_bwd = e0.elapsed_time(e1) / k
+    e0.record()
+    for _ in range(k):
+        hpdr.hpdr_recompose(c0, shape)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd = e0.elapsed_time(e1) / k
+    return {"workload": "257^3 FP32 coefficients, loss = mean((recompose(c) - t)^2)",
+            "fwd_bwd_ms_per_step": round(fwd_bwd, 3), "recompose_ms": round(fwd, 3),
+            "grad_norm": round(float(g.norm().item()), 6)}
+
+
+def run_batched(args, dev):
+    """256 FP32 fields, 2-D or 3-D, dims log-uniform in [17, 513], own bounds in
+    {1e-2, 1e-3, 1e-4}: one graph replay vs one hpdr_compress call per field."""
+    import torch
+    from paper_2503_06322_gb300 import fields, hpdr
+    shapes = fields.batch_shapes(count=256, seed=3)
+    us = [fields.powerlaw_field_torch(sh, seed=1000 + i, device=dev) for i, (sh, _) in enumerate(shapes)]
+    tols = [t for _, t in shapes]
+    total = sum(u.numel() * u.element_size() for u in us)
+    out, offs, sizes = hpdr.hpdr_compress_batched(us, tols, dict_size=65536)   # captures + tunes
+    for _ in range(2):
+        hpdr.hpdr_compress_batched(us, tols, out=out, dict_size=65536)
+    torch.cuda.synchronize()
+    k = 5
+    t0 = time.perf_counter()
+    for _ in range(k):
+        hpdr.hpdr_compress_batched(us, tols, out=out, dict_size=65536)
+    bt = (time.perf_counter() - t0) / k
+    bufs = [torch.empty(hpdr.hpdr_compress_bound(u.shape, u.dtype, 65536), dtype=torch.uint8, device=dev)
+            for u in us]
+    for u, t, b in zip(us, tols, bufs):
+        hpdr.hpdr_compress(u, t, out=b, dict_size=65536)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k):
+        for u, t, b in zip(us, tols, bufs):
+            hpdr.hpdr_compress(u, t, out=b, dict_size=65536)
+    st = (time.perf_counter() - t0) / k
+    return {"workload": "256 FP32 fields (2-D/3-D, dims log-uniform in [17,513]), rel Linf bound each "
+                        "from {1e-2,1e-3,1e-4}, D = 65536",
+            "total_bytes": total, "graph_gbs": round(total / bt / 1e9, 2),
+            "sequential_gbs": round(total / st / 1e9, 2), "speedup": round(st / bt, 3),
+            "streams_chosen": int(hpdr.lib().hpdr_batched_streams(hpdr.context())),
+            "compression_ratio": round(total / sum(sizes), 4)}
+
+
+def run_stream(args, dev):
+    """1025^3 FP32 (4.3 GB) power-law field plus a tanh front, in pinned host
+    memory, compressed in 256 MiB slabs at rel Linf 1e-3 (and decompressed back)."""
+    import ctypes as C
+    import torch
+    from paper_2503_06322_gb300 import fields, hpdr
+    shape = (1025, 1025, 1025)
+    ud = fields.front_field_torch(shape, seed=7, device=dev)
+    h = torch.empty(shape, dtype=torch.float32, pin_memory=True)
+    h.copy_(ud)
+    del ud
+    torch.cuda.empty_cache()
+    cap = hpdr.streamed_bound(shape, torch.float32)
+    hc = torch.empty(cap, dtype=torch.uint8, pin_memory=True)
+    L = hpdr.lib()
+    ctx = hpdr.context(dev.index)
+    b = hpdr.hpdr_compress_host_streamed(h, args.tol, out=hc)          # warm
+    names = (C.c_char_p * 64)()
+    ms = (C.c_double * 64)()
+    cnt = (C.c_longlong * 64)()
+    L.hpdr_profile_read(ctx, names, ms, cnt, 64)
+    L.hpdr_profile_enable(ctx, 1)
+    t0 = time.perf_counter()
+    b = hpdr.hpdr_compress_host_streamed(h, args.tol, out=hc)
+    tc = time.perf_counter() - t0
+    L.hpdr_profile_enable(ctx, 0)
+    n = L.hpdr_profile_read(ctx, names, ms, cnt, 64)
+    g = {names[i].decode(): ms[i] for i in range(n)}
+    comp = g.get("s_compute", 0.0)
+    xfer = g.get("s_h2d", 0.0) + g.get("s_d2h", 0.0)
+    exposed = max(0.0, tc * 1e3 - comp) / xfer if xfer > 0 else None
+    out = torch.empty_like(h).pin_memory()
+    t0 = time.perf_counter()
+    hpdr.hpdr_decompress_host_streamed(b, out=out)
+    td = time.perf_counter() - t0
+    fb = h.numel() * 4
+    err = (out - h).abs().max().item() / (args.tol * h.abs().max().item())
+    whole = hpdr.hpdr_compress(h.cuda(), args.tol).numel()
+    return {"workload": "1025^3 FP32 power-law field + tanh front, pinned host, 256 MiB slabs, rel Linf 1e-3",
+            "compress_host_to_host_gbs": round(fb / tc / 1e9, 2),
+            "decompress_host_to_host_gbs": round(fb / td / 1e9, 2),
+            "exposed_transfer_fraction": None if exposed is None else round(min(1.0, exposed), 4),
+            "compute_ms": round(comp, 2), "transfer_ms": round(xfer, 2), "wall_ms": round(tc * 1e3, 2),
+            "compression_ratio": round(fb / b.numel(), 4), "whole_field_ratio": round(fb / whole, 4),
+            "max_err_over_tau": round(err, 4)}
 
 
 def cpu_sample(args, u_host_planes, steps=1):
@@ -402,6 +513,13 @@ def main():
             fb = u.numel() * u.element_size()
             e2e["value"] = round(world * 2.0 * fb / (float(t.item()) * 1e-3) / 1e9, 2)
         out["e2e"] = e2e
+    del cbuf
+    if rank == 0 and not args.no_adjoint:
+        out["adjoint"] = run_adjoint(args, u.device)
+    if rank == 0 and not args.no_batched:
+        out["batched"] = run_batched(args, u.device)
+    if rank == 0 and not args.no_stream:
+        out["host_streamed"] = run_stream(args, u.device)
     if rank == 0 and world == 1 and not args.no_cpu:
         planes = min(args.cpu_planes, shape[0])
         host = u[:planes].cpu().numpy()

@@ -30,18 +30,20 @@ struct StreamRes {
     size_t bytes[4] = {0, 0, 0, 0};
 };
 
-// slab split along dim 0: planes per slab from the byte budget (at least 2
-// planes); a remainder of one plane joins the last slab
+// slab split along dim 0: as few slabs as the byte budget allows, of equal
+// size (differing by at most one plane), each of at least two planes
 void split_slabs(size_t n0, size_t plane_bytes, size_t slab_bytes, std::vector<size_t> &first,
                  std::vector<size_t> &count)
 {
     size_t p = plane_bytes ? slab_bytes / plane_bytes : n0;
     if (p < 2) p = 2;
     if (p > n0) p = n0;
+    size_t ns = (n0 + p - 1) / p;
+    while (ns > 1 && n0 / ns < 2) ns--;
+    const size_t base = n0 / ns, extra = n0 % ns;
     size_t at = 0;
-    while (at < n0) {
-        size_t c = std::min(p, n0 - at);
-        if (n0 - at - c == 1) c += 1;   // never leave a single plane
+    for (size_t i = 0; i < ns; i++) {
+        const size_t c = base + (i < extra ? 1 : 0);
         first.push_back(at);
         count.push_back(c);
         at += c;

@@ -213,7 +213,7 @@ def streamed_bound(shape, dtype=torch.float32, slab_bytes=256 << 20, dict_size=8
         plane *= int(s)
     per = max(2, slab_bytes // plane) if len(shape) > 1 else int(shape[0])
     nslab = max(1, -(-int(shape[0]) // per))
-    slab = (min(per + 1, int(shape[0])),) + tuple(shape[1:])
+    slab = (min(-(-int(shape[0]) // nslab), int(shape[0])),) + tuple(shape[1:])
     return 64 + 32 * nslab + 16 + nslab * (hpdr_compress_bound(slab, dtype, dict_size, chunk) + 16)
 
 
