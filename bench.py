@@ -144,7 +144,7 @@ def ncu_traffic(kernel_group):
 
 # ---------------------------------------------------------------------------
 def algorithmic_bytes(group, S, NL, NL1, bits, nch):
-    """Bytes each kernel must move, per launch (roofline)."""
+    """Bytes each kernel group must move per launch (the roofline numerator)."""
     new = NL - NL1
     if group == "c_restrict_quant_L":      # read v_L, write symbols, b and coarse copy
         return S * NL + 2 * new + 2 * S * NL1
@@ -232,13 +232,9 @@ def run_ours(args, rank, world, local):
     groups = {nprof_read[i].decode(): (ms_arr[i], cnt_arr[i]) for i in range(ng)}
     ms_total = t_start.elapsed_time(t_stop)
     clk = clocks.stop()
-    ms_local = ms_total
-    if world > 1:
-        t = torch.tensor([ms_local], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, dev)
     ms_step = ms_total / args.steps
-    value = world * 2.0 * nbytes / (ms_step * 1e-3) / 1e9
+    value = job_gbs(world, 2.0 * nbytes, ms_step)
 
     # ---- correctness of the timed output ----
     tau = args.tol * u.abs().max().item()
@@ -281,6 +277,23 @@ def run_ours(args, rank, world, local):
         "gpu_launches": int(launches), "clocks": clk,
     }
     return out, u, cbuf, comp_bytes
+
+
+def max_over_ranks(x, device):
+    """The largest per-rank value over the process group (the slowest rank's
+    time); the value itself when there is no group or a single rank."""
+    import torch
+    dist = torch.distributed
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbs(world, bytes_per_rank_step, ms_per_step):
+    """Whole-job throughput: bytes all ranks moved per step / the step time."""
+    return world * bytes_per_rank_step / (ms_per_step * 1e-3) / 1e9
 
 
 def level_nodes(shape, down):
@@ -508,10 +521,8 @@ def main():
     if not args.no_e2e:
         e2e = run_e2e(args, u, out)
         if world > 1:
-            t = torch.tensor([e2e["ms_per_step"]], device=u.device, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            fb = u.numel() * u.element_size()
-            e2e["value"] = round(world * 2.0 * fb / (float(t.item()) * 1e-3) / 1e9, 2)
+            ms = max_over_ranks(e2e["ms_per_step"], u.device)
+            e2e["value"] = round(job_gbs(world, 2.0 * u.numel() * u.element_size(), ms), 2)
         out["e2e"] = e2e
     del cbuf
     if rank == 0 and not args.no_adjoint:
