@@ -48,7 +48,7 @@ typedef enum {
     HPDR_OK = 0,
     HPDR_ERR_ARG = -1,       /* invalid argument (dims, dtype, tolerance, null pointer) */
     HPDR_ERR_CUDA = -2,      /* a CUDA runtime call or kernel failed */
-    HPDR_ERR_CAPACITY = -3,  /* output buffer too small (or too many outliers) */
+    HPDR_ERR_CAPACITY = -3,  /* output buffer too small */
     HPDR_ERR_FORMAT = -4,    /* malformed or corrupted container */
     HPDR_ERR_TIMEOUT = -5,   /* a bounded device-side wait gave up */
     HPDR_ERR_NOMEM = -6      /* device allocation of a workspace failed */
@@ -61,8 +61,8 @@ typedef enum { HPDR_ABS = 0, HPDR_REL = 1 } hpdr_tol_kind;  /* REL: tol x norm o
 typedef struct hpdr_ctx hpdr_ctx;
 
 /* Tunables of the lossless stage (Alg. 2).  dict_size D: quantized codes k
- * with |k| < D/2 become symbols k + D/2; others are escaped (symbol 0) and
- * stored verbatim as outliers; even, 4 <= D <= 65536; default 8192.
+ * with |k| < D/2 become symbols k + D/2; others are escaped (symbol 0, with
+ * k written after its codeword); even, 4 <= D <= 65536; default 8192.
  * chunk K: symbols per decode chunk (the chunk table stores the bit offset of
  * every K-th symbol); multiple of 128, 128 <= K <= 32768; default 1024.
  * A zero field selects the default. */
@@ -80,7 +80,12 @@ hpdr_status hpdr_ctx_create(hpdr_ctx **ctx, int device);
 hpdr_status hpdr_ctx_destroy(hpdr_ctx *ctx);
 
 /* Upper bound of the container size for a field, with the given config (NULL
- * = defaults).  0 on bad arguments. */
+ * = defaults): header, bins, code lengths, chunk table and ceil(log2 D) + 38
+ * bits per value (a Huffman code never exceeds the fixed-length code of
+ * ceil(log2 D) bits in total; an escape payload takes at most 38 bits while
+ * |k| < 2^31).  Only tolerances so small that many codes reach |k| >= 2^31
+ * can exceed it; hpdr_compress then returns HPDR_ERR_CAPACITY.  0 on bad
+ * arguments. */
 size_t hpdr_compress_bound(int ndim, const size_t *dims, hpdr_dtype dtype, const hpdr_config *cfg);
 
 /* Compress a device-resident field (Alg. 1 then Alg. 2).
@@ -89,11 +94,15 @@ size_t hpdr_compress_bound(int ndim, const size_t *dims, hpdr_dtype dtype, const
  *               tol * rms(u) (L2); ABS: tau = tol.  The reconstruction then
  *               satisfies max|u - u~| <= tau (which also bounds the RMS error).
  *   d_out       device buffer of out_capacity bytes receiving the container
- *               (format v1: 128-byte header, bins, code lengths, chunk table,
- *               outliers, bitstream).
+ *               (format v2: 128-byte header, bins, code lengths, chunk table,
+ *               bitstream; every section 16-byte aligned).  A code k whose
+ *               symbol k + D/2 falls outside [1, D-1] is escaped: symbol 0,
+ *               followed in the bitstream by 6 bits holding n - 1 and the n
+ *               bits of zigzag(k) (n = its bit length).
  *   out_bytes   host pointer receiving the container size.
  * Errors: HPDR_ERR_ARG (including a bound below the data type's precision
- * floor, tau <= 32 (L+1) eps max|u|), HPDR_ERR_CAPACITY, HPDR_ERR_NOMEM,
+ * floor, tau <= 32 (L+1) eps max|u|, or a code with |k| >= 2^62),
+ * HPDR_ERR_CAPACITY, HPDR_ERR_NOMEM,
  * HPDR_ERR_CUDA.  Synchronizes `stream` once. */
 hpdr_status hpdr_compress(hpdr_ctx *ctx, const void *d_in, hpdr_dtype dtype, int ndim,
                           const size_t *dims, double tol, hpdr_tol_kind tol_kind, hpdr_mode mode,
@@ -199,7 +208,7 @@ int hpdr_batched_streams(hpdr_ctx *ctx);
  *   h_out       host buffer of out_capacity bytes receiving the streamed
  *               container: "HPDS" directory (64 bytes + 32 per slab: first
  *               plane, planes, byte offset, bytes) followed by the slab
- *               containers (format v1) at 16-byte boundaries.
+ *               containers (format v2) at 16-byte boundaries.
  *   out_bytes   receives the size.
  * Synchronous.  Errors as hpdr_compress. */
 hpdr_status hpdr_compress_host_streamed(hpdr_ctx *ctx, const void *h_in, hpdr_dtype dtype, int ndim,

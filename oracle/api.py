@@ -49,8 +49,10 @@ def _L():
             "oracle_histogram": [u16, C.c_uint64, C.c_uint32, u64],
             "oracle_code_lengths": [u64, C.c_uint32, u8],
             "oracle_canonical_codes": [u8, C.c_uint32, u64],
-            "oracle_encode": [u16, C.c_uint64, u8, u64, C.c_uint32, u32, C.c_uint64, u64, u64],
-            "oracle_decode": [u32, C.c_uint64, u64, C.c_uint64, C.c_uint32, u8, C.c_uint32, u16],
+            "oracle_encode": [u16, C.c_uint64, u8, u64, C.c_uint32, i64, u32, C.c_uint64, u64, u64],
+            "oracle_decode": [u32, C.c_uint64, u64, C.c_uint64, C.c_uint32, u8, C.c_uint32, u16,
+                              C.c_int, i64, C.c_uint64, u64],
+            "oracle_escape_bits": [C.c_int64],
             "oracle_compress": [C.c_int, sz, dp, C.c_int, C.c_double, C.c_int, C.c_int,
                                 C.c_uint32, C.c_uint32, u8, C.c_uint64, u64],
             "oracle_decompress": [u8, C.c_uint64, dp, C.c_uint64],
@@ -200,31 +202,59 @@ def canonical_codes(lengths):
     return code
 
 
-def encode(sym, lengths, K=1024):
-    """Huffman-encode symbols: returns (words uint32, chunk table uint64, total bits)."""
+def encode(sym, lengths, K=1024, esc_k=None):
+    """Huffman-encode symbols: returns (words uint32, chunk table uint64, total bits).
+    esc_k: None for plain symbols; else the integer codes of the escapes (symbol 0)
+    in stream order, written as payloads after their codewords."""
     sym = np.ascontiguousarray(sym, dtype=np.uint16)
     lengths = np.ascontiguousarray(lengths, dtype=np.uint8)
     code = canonical_codes(lengths)
     bits = int(lengths[sym].astype(np.uint64).sum())
+    ek = None
+    if esc_k is not None:
+        ek = np.ascontiguousarray(esc_k, dtype=np.int64)
+        bits += int(_escape_bits_np(ek).sum())
+        if ek.size == 0:
+            ek = np.zeros(1, dtype=np.int64)
     nw = (bits + 31) // 32
     words = np.zeros(max(nw, 1), dtype=np.uint32)
     nch = (sym.size + K - 1) // K
     chunk = np.zeros(max(nch, 1), dtype=np.uint64)
     tb = C.c_uint64()
     _check(_L().oracle_encode(_p(sym, C.c_uint16), sym.size, _p(lengths, C.c_uint8),
-                              _p(code, C.c_uint64), K, _p(words, C.c_uint32), words.size,
-                              _p(chunk, C.c_uint64), C.byref(tb)), "encode")
+                              _p(code, C.c_uint64), K, _p(ek, C.c_int64) if ek is not None else None,
+                              _p(words, C.c_uint32), words.size, _p(chunk, C.c_uint64),
+                              C.byref(tb)), "encode")
     return words[:nw], chunk[:nch], tb.value
 
 
-def decode(words, chunk, N, K, lengths):
+def _escape_bits_np(k):
+    """6 + bit length of zigzag(k), vectorised (|k| < 2^62)."""
+    k = k.astype(np.int64)
+    z = np.where(k >= 0, 2 * k.astype(np.uint64), 2 * (-(k + 1)).astype(np.uint64) + 1)
+    n = np.zeros(z.shape, dtype=np.int64)
+    while np.any(z):
+        n += (z != 0)
+        z = z >> np.uint64(1)
+    return 6 + n
+
+
+def decode(words, chunk, N, K, lengths, escapes=False):
+    """Decode N symbols; with escapes=True also returns the escapes' codes
+    (stream order)."""
     words = np.ascontiguousarray(words, dtype=np.uint32)
     chunk = np.ascontiguousarray(chunk, dtype=np.uint64)
     lengths = np.ascontiguousarray(lengths, dtype=np.uint8)
     sym = np.zeros(N, dtype=np.uint16)
+    ek = np.zeros(max(N, 1), dtype=np.int64)
+    ne = C.c_uint64()
     w = words if words.size else np.zeros(1, dtype=np.uint32)
     _check(_L().oracle_decode(_p(w, C.c_uint32), words.size, _p(chunk, C.c_uint64), N, K,
-                              _p(lengths, C.c_uint8), lengths.size, _p(sym, C.c_uint16)), "decode")
+                              _p(lengths, C.c_uint8), lengths.size, _p(sym, C.c_uint16),
+                              1 if escapes else 0, _p(ek, C.c_int64), ek.size, C.byref(ne)),
+           "decode")
+    if escapes:
+        return sym, ek[:ne.value].copy()
     return sym
 
 
@@ -283,15 +313,14 @@ def parse_header(buf):
              dims=tuple(u64(16 + 8 * k) for k in range(u32(12))), L=u32(40), mode=u32(44),
              tol_kind=u32(48), D=u32(52), K=u32(56), s_lo=u32(60), tol=f64(64),
              tau_abs=f64(72), norm_inf=f64(80), norm_rms=f64(88), N=u64(96),
-             n_outliers=u64(104), total_bits=u64(112), s_hi=u32(120), crc=u32(124))
+             n_escapes=u64(104), total_bits=u64(112), s_hi=u32(120), crc=u32(124))
     a16 = lambda x: (x + 15) & ~15  # noqa: E731
     L = h["L"]
     off_q = 128
     off_len = a16(off_q + 8 * (L + 1))
     off_chunk = a16(off_len + h["s_hi"] - h["s_lo"] + 1)
     nch = (h["N"] + h["K"] - 1) // h["K"]
-    off_out = a16(off_chunk + 8 * nch)
-    off_bits = a16(off_out + 16 * h["n_outliers"])
+    off_bits = a16(off_chunk + 8 * nch)
     nw = (h["total_bits"] + 31) // 32
     arr = np.frombuffer(b, dtype=np.uint8)
     h["q"] = arr[off_q:off_q + 8 * (L + 1)].view("<f8").copy()
@@ -299,9 +328,6 @@ def parse_header(buf):
     ln[h["s_lo"]:h["s_hi"] + 1] = arr[off_len:off_len + h["s_hi"] - h["s_lo"] + 1]
     h["lengths"] = ln
     h["chunk"] = arr[off_chunk:off_chunk + 8 * nch].view("<u8").copy()
-    no = h["n_outliers"]
-    h["out_idx"] = arr[off_out:off_out + 8 * no].view("<u8").copy()
-    h["out_k"] = arr[off_out + 8 * no:off_out + 16 * no].view("<i8").copy()
     h["words"] = arr[off_bits:off_bits + 4 * nw].view("<u4").copy()
     h["total_bytes"] = off_bits + 4 * nw
     return h

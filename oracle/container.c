@@ -1,23 +1,27 @@
 /*
  * container.c -- oracle of the whole reduction path (Alg. 1 followed by
  * Alg. 2) and of its inverse, written into / read from the self-describing
- * container, format version 1.  TEST INFRASTRUCTURE ONLY (see
+ * container, format version 2.  TEST INFRASTRUCTURE ONLY (see
  * hpdr_oracle.h).
  *
- * Container v1 (little endian; every section starts on a 16-byte boundary;
+ * Container v2 (little endian; every section starts on a 16-byte boundary;
  * padding bytes are zero):
- *   0   "HPDR"            4  u32 version (1)     8  u32 dtype (0 f32, 1 f64)
+ *   0   "HPDR"            4  u32 version (2)     8  u32 dtype (0 f32, 1 f64)
  *   12  u32 ndim          16 u64 dims[3] (unused dims hold 1)
  *   40  u32 L             44 u32 mode (0 Linf, 1 L2)   48 u32 tol kind (0 abs, 1 rel)
  *   52  u32 D             56 u32 K               60 u32 s_lo
  *   64  f64 tol           72 f64 tau_abs         80 f64 max|u|    88 f64 rms(u)
- *   96  u64 N             104 u64 outliers       112 u64 bitstream bits
+ *   96  u64 N             104 u64 escapes        112 u64 bitstream bits
  *   120 u32 s_hi          124 u32 CRC-32 of bytes [0,124)
  *   128 f64 q[L+1]
  *   code lengths  u8[s_hi - s_lo + 1]  (symbols s_lo..s_hi)
  *   chunk table   u64[ceil(N/K)]       (bit offset of symbol j*K)
- *   outliers      u64 index[n], then i64 code[n]   (stream order)
  *   bitstream     u32[ceil(bits/32)]
+ *
+ * Symbol s = k + D/2 carries the quantized code k when 1 <= s <= D-1; every
+ * other code is escaped: symbol 0, whose codeword is followed in the
+ * bitstream by 6 bits holding n - 1 and the n bits of zigzag(k) (see
+ * oracle_encode).
  *
  * Tolerance: REL means tol times max|u| (Linf mode) or times rms(u) (L2
  * mode); ABS means tol itself.  L2 mode uses the same bins, which bound the
@@ -58,8 +62,11 @@ uint64_t oracle_compress_bound(int d, const size_t *n, uint32_t D, uint32_t K)
     uint64_t b = align16(HDR + 8 * (uint64_t)(L + 1));
     b = align16(b + D);
     b = align16(b + 8 * ((N + K - 1) / K));
-    b = align16(b + 16 * N);
-    b += 4 * ((63 * N + 31) / 32);
+    /* Huffman bits <= N ceil(log2 D) (a fixed-length code is a prefix code);
+     * escape payloads <= 38 bits each while |k| < 2^31 */
+    uint64_t lg = 0;
+    while ((1ULL << lg) < D) lg++;
+    b += 4 * ((N * (lg + 38) + 31) / 32);
     return b;
 }
 
@@ -108,10 +115,14 @@ int oracle_compress(int d, const size_t *n, const double *u, int dtype, double t
     uint64_t off_q = HDR;
     uint64_t off_len = align16(off_q + 8 * (uint64_t)(L + 1));
     uint64_t off_chunk = align16(off_len + (shi - slo + 1));
-    uint64_t off_out = align16(off_chunk + 8 * nch);
-    uint64_t off_bits = align16(off_out + 16 * nout);
+    uint64_t off_bits = align16(off_chunk + 8 * nch);
     uint64_t bits = 0;
     for (uint64_t i = 0; i < N && rc == 0; i++) bits += len[sym[i]];
+    for (uint64_t j = 0; j < nout && rc == 0; j++) {
+        int eb = oracle_escape_bits(ok[j]);
+        if (eb < 0) rc = -1;
+        else bits += (uint64_t)eb;
+    }
     uint64_t nwords = (bits + 31) / 32;
     uint64_t total = off_bits + 4 * nwords;
     if (rc == 0 && total > cap) rc = -3;
@@ -120,9 +131,10 @@ int oracle_compress(int d, const size_t *n, const double *u, int dtype, double t
         uint64_t *chunk = (uint64_t *)malloc(nch * sizeof(uint64_t));
         uint32_t *words = (uint32_t *)malloc((nwords + 1) * sizeof(uint32_t));
         uint64_t tb = 0;
-        rc = oracle_encode(sym, N, len, code, K, words, nwords + 1, chunk, &tb);
+        rc = oracle_encode(sym, N, len, code, K, ok, words, nwords + 1, chunk, &tb);
+        if (rc == 0 && tb != bits) rc = -1;
         memcpy(out, "HPDR", 4);
-        put32(out + 4, 1);
+        put32(out + 4, 2);
         put32(out + 8, (uint32_t)dtype);
         put32(out + 12, (uint32_t)d);
         for (int k = 0; k < 3; k++) put64(out + 16 + 8 * k, (k < d) ? (uint64_t)n[k] : 1);
@@ -144,10 +156,6 @@ int oracle_compress(int d, const size_t *n, const double *u, int dtype, double t
         for (int l = 0; l <= L; l++) putf64(out + off_q + 8 * l, q[l]);
         for (uint32_t s = slo; s <= shi; s++) out[off_len + (s - slo)] = len[s];
         for (uint64_t j = 0; j < nch; j++) put64(out + off_chunk + 8 * j, chunk[j]);
-        for (uint64_t j = 0; j < nout; j++) {
-            put64(out + off_out + 8 * j, oidx[j]);
-            put64(out + off_out + 8 * nout + 8 * j, (uint64_t)ok[j]);
-        }
         for (uint64_t w = 0; w < nwords; w++) put32(out + off_bits + 4 * w, words[w]);
         *out_bytes = total;
         free(chunk); free(words);
@@ -161,12 +169,12 @@ typedef struct {
     size_t n[3];
     uint32_t D, K, slo, shi;
     uint64_t N, nout, bits, nch, nwords;
-    uint64_t off_q, off_len, off_chunk, off_out, off_bits, total;
+    uint64_t off_q, off_len, off_chunk, off_bits, total;
 } hdr_t;
 
 static int parse(const uint8_t *in, uint64_t in_bytes, hdr_t *h)
 {
-    if (in_bytes < HDR || memcmp(in, "HPDR", 4) != 0 || get32(in + 4) != 1) return -4;
+    if (in_bytes < HDR || memcmp(in, "HPDR", 4) != 0 || get32(in + 4) != 2) return -4;
     if (oracle_crc32(in, 124) != get32(in + 124)) return -4;
     h->dtype = (int)get32(in + 8);
     h->d = (int)get32(in + 12);
@@ -194,8 +202,7 @@ static int parse(const uint8_t *in, uint64_t in_bytes, hdr_t *h)
     h->off_q = HDR;
     h->off_len = align16(h->off_q + 8 * (uint64_t)(L + 1));
     h->off_chunk = align16(h->off_len + (h->shi - h->slo + 1));
-    h->off_out = align16(h->off_chunk + 8 * h->nch);
-    h->off_bits = align16(h->off_out + 16 * h->nout);
+    h->off_bits = align16(h->off_chunk + 8 * h->nch);
     h->total = h->off_bits + 4 * h->nwords;
     if (h->total > in_bytes) return -4;
     return 0;
@@ -226,15 +233,15 @@ int oracle_decompress(const uint8_t *in, uint64_t in_bytes, double *u, uint64_t 
     for (uint64_t j = 0; j < h.nch; j++) chunk[j] = get64(in + h.off_chunk + 8 * j);
     uint64_t *oidx = (uint64_t *)malloc((h.nout + 1) * sizeof(uint64_t));
     int64_t *ok = (int64_t *)malloc((h.nout + 1) * sizeof(int64_t));
-    for (uint64_t j = 0; j < h.nout; j++) {
-        oidx[j] = get64(in + h.off_out + 8 * j);
-        ok[j] = (int64_t)get64(in + h.off_out + 8 * h.nout + 8 * j);
-    }
     uint32_t *words = (uint32_t *)malloc((h.nwords + 1) * sizeof(uint32_t));
     for (uint64_t w = 0; w < h.nwords; w++) words[w] = get32(in + h.off_bits + 4 * w);
     uint16_t *sym = (uint16_t *)malloc(h.N * sizeof(uint16_t));
     double *coef = (double *)malloc(h.N * sizeof(double));
-    rc = oracle_decode(words, h.nwords, chunk, h.N, h.K, len, h.D, sym);
+    uint64_t ne = 0;
+    rc = oracle_decode(words, h.nwords, chunk, h.N, h.K, len, h.D, sym, 1, ok, h.nout, &ne);
+    if (rc == 0 && ne != h.nout) rc = -4;
+    for (uint64_t i = 0, j = 0; rc == 0 && i < h.N; i++)
+        if (sym[i] == 0) oidx[j++] = i;
     if (rc == 0) rc = oracle_dequantize(h.d, h.n, sym, q, h.D, h.nout, oidx, ok, coef);
     if (rc == 0) rc = oracle_recompose(h.d, h.n, coef, u);
     free(q); free(len); free(chunk); free(oidx); free(ok); free(words); free(sym); free(coef);

@@ -97,36 +97,75 @@ int oracle_canonical_codes(const uint8_t *len, uint32_t D, uint64_t *code)
     return 0;
 }
 
+/* zigzag map of an escaped code: k >= 0 -> 2k, k < 0 -> -2k - 1 */
+static uint64_t zigzag(int64_t k) { return k >= 0 ? 2 * (uint64_t)k : 2 * (uint64_t)(-(k + 1)) + 1; }
+static int64_t unzigzag(uint64_t z) { return (z & 1) ? -(int64_t)(z >> 1) - 1 : (int64_t)(z >> 1); }
+static int bitlen(uint64_t z) { int n = 0; while (z) { n++; z >>= 1; } return n; }
+
+int oracle_escape_bits(int64_t k)
+{
+    if (k == 0 || k >= ((int64_t)1 << 62) || k <= -((int64_t)1 << 62)) return -1;
+    return 6 + bitlen(zigzag(k));
+}
+
+static void put_bits(uint32_t *words, uint64_t *pos, uint64_t v, int nbits)
+{
+    for (int b = nbits - 1; b >= 0; b--) {
+        if ((v >> b) & 1u) words[*pos / 32] |= 1u << (31 - (*pos % 32));
+        (*pos)++;
+    }
+}
+
 int oracle_encode(const uint16_t *symbols, uint64_t N, const uint8_t *len, const uint64_t *code,
-                  uint32_t K, uint32_t *words, uint64_t nwords_cap, uint64_t *chunk_bits,
-                  uint64_t *total_bits)
+                  uint32_t K, const int64_t *esc_k, uint32_t *words, uint64_t nwords_cap,
+                  uint64_t *chunk_bits, uint64_t *total_bits)
 {
     if (K == 0) return -1;
-    uint64_t bits = 0;
+    uint64_t bits = 0, e = 0;
     for (uint64_t i = 0; i < N; i++) {
         if (len[symbols[i]] == 0) return -1;
         bits += len[symbols[i]];
+        if (esc_k && symbols[i] == 0) {
+            int eb = oracle_escape_bits(esc_k[e++]);
+            if (eb < 0) return -1;
+            bits += (uint64_t)eb;
+        }
     }
     uint64_t nwords = (bits + 31) / 32;
     *total_bits = bits;
     if (nwords > nwords_cap) return -3;
     memset(words, 0, nwords * sizeof(uint32_t));
     uint64_t pos = 0;
+    e = 0;
     for (uint64_t i = 0; i < N; i++) {
         if (i % K == 0) chunk_bits[i / K] = pos;
-        uint64_t c = code[symbols[i]];
-        int l = len[symbols[i]];
-        for (int b = l - 1; b >= 0; b--) {
-            if ((c >> b) & 1u) words[pos / 32] |= 1u << (31 - (pos % 32));
-            pos++;
+        put_bits(words, &pos, code[symbols[i]], len[symbols[i]]);
+        if (esc_k && symbols[i] == 0) {
+            uint64_t z = zigzag(esc_k[e++]);
+            int nb = bitlen(z);
+            put_bits(words, &pos, (uint64_t)(nb - 1), 6);
+            put_bits(words, &pos, z, nb);
         }
     }
     return 0;
 }
 
-int oracle_decode(const uint32_t *words, uint64_t nwords, const uint64_t *chunk_bits, uint64_t N,
-                  uint32_t K, const uint8_t *len, uint32_t D, uint16_t *symbols)
+static int get_bits(const uint32_t *words, uint64_t nwords, uint64_t *pos, int nbits, uint64_t *v)
 {
+    *v = 0;
+    for (int b = 0; b < nbits; b++) {
+        if (*pos / 32 >= nwords) return -4;
+        *v = (*v << 1) | ((words[*pos / 32] >> (31 - (*pos % 32))) & 1u);
+        (*pos)++;
+    }
+    return 0;
+}
+
+int oracle_decode(const uint32_t *words, uint64_t nwords, const uint64_t *chunk_bits, uint64_t N,
+                  uint32_t K, const uint8_t *len, uint32_t D, uint16_t *symbols, int escapes,
+                  int64_t *esc_k, uint64_t esc_cap, uint64_t *n_esc)
+{
+    uint64_t ne = 0;
     uint64_t count[OMAXLEN + 2] = {0}, first[OMAXLEN + 2] = {0}, findex[OMAXLEN + 2] = {0};
     uint32_t *sorted = (uint32_t *)malloc((size_t)D * sizeof(uint32_t));
     uint32_t ns = 0;
@@ -165,8 +204,18 @@ int oracle_decode(const uint32_t *words, uint64_t nwords, const uint64_t *chunk_
                     found = 1;
                 }
             }
+            if (escapes && symbols[i] == 0) {
+                uint64_t nb, z;
+                if (get_bits(words, nwords, &pos, 6, &nb) ||
+                    get_bits(words, nwords, &pos, (int)nb + 1, &z) || ne >= esc_cap) {
+                    free(sorted);
+                    return -4;
+                }
+                esc_k[ne++] = unzigzag(z);
+            }
         }
     }
+    if (n_esc) *n_esc = ne;
     free(sorted);
     return 0;
 }

@@ -66,9 +66,6 @@ bool valid_cfg(const hpdr_config *cfg, unsigned &D, unsigned &K)
     return true;
 }
 
-// outlier list: up to N/8 entries (at least 2^20, at most N)
-unsigned long long out_cap_of(long long N) { return std::min<long long>(N, std::max<long long>(1 << 20, N / 8)); }
-
 long long total_of(int ndim, const size_t *dims)
 {
     long long n = 1;
@@ -77,20 +74,16 @@ long long total_of(int ndim, const size_t *dims)
 }
 
 // workspace of one field: scalars, partials, hist, level buffers, symbols,
-// chunk tables, outliers, Huffman scratch
+// escaped codes, chunk tables, Huffman scratch
 struct Ws {
     Scalars *sc;
     double *partials;
     unsigned long long *hist;
     void *va, *vb, *b;
     uint16_t *sym;
+    long long *esc;
     unsigned long long *chunk_bits;
-    unsigned *chunk_esc;
     unsigned long long *bsum;
-    unsigned *besc;
-    unsigned long long *oidx;
-    long long *ok;
-    unsigned long long ocap;
     void *huff;
 };
 
@@ -107,13 +100,9 @@ size_t carve_ws(void *base, const Plan *P, size_t esz, unsigned D, unsigned K, b
     w->vb = c.take<char>(Nl1 * esz);
     w->b = c.take<char>(Nl1 * esz);
     w->sym = need_sym ? c.take<uint16_t>(N + 8) : nullptr;
+    w->esc = need_sym ? c.take<long long>(N) : nullptr;
     w->chunk_bits = c.take<unsigned long long>(nch + 2);
-    w->chunk_esc = c.take<unsigned>(nch + 2);
     w->bsum = c.take<unsigned long long>(1024);
-    w->besc = c.take<unsigned>(1024);
-    w->ocap = out_cap_of(N);
-    w->oidx = c.take<unsigned long long>(w->ocap);
-    w->ok = c.take<long long>(w->ocap);
     w->huff = c.take<char>(huff_scratch_bytes(D));
     return c.used + 256;
 }
@@ -165,7 +154,7 @@ hpdr_status compress_core(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, co
     CK(launch_bins(ba, w.partials, norm_parts(), w.sc, s));
 
     QuantOut qo;
-    qo.sym = w.sym; qo.hist = w.hist; qo.out_idx = w.oidx; qo.out_k = w.ok; qo.out_cap = w.ocap;
+    qo.sym = w.sym; qo.hist = w.hist; qo.esc = w.esc;
     qo.D = D; qo.sc = w.sc;
     const T *v = u;
     for (int l = L; l >= 1; l--) {
@@ -201,10 +190,10 @@ hpdr_status compress_core(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, co
     memset(&ea, 0, sizeof(ea));
     ea.sym = w.sym; ea.N = (unsigned long long)N; ea.D = D; ea.K = K;
     ea.len = hs.len; ea.code = hs.code;
-    ea.chunk_bits = w.chunk_bits; ea.chunk_esc = w.chunk_esc; ea.sc = w.sc;
-    ea.bsum = w.bsum; ea.besc = w.besc;
+    ea.esc = w.esc;
+    ea.chunk_bits = w.chunk_bits; ea.sc = w.sc;
+    ea.bsum = w.bsum;
     ea.container = out; ea.L = L; ea.capacity = cap;
-    ea.oidx_unordered = w.oidx; ea.ok_unordered = w.ok;
     {
     ProfScope ps(ctx, "c_encode", s);
     CK(launch_encode(ea, s));
@@ -217,7 +206,7 @@ hpdr_status compress_core(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, co
     h.mode = mode;
     h.tol_kind = tol_kind;
     for (int k = 0; k < 3; k++) h.dims[k] = k < ndim ? dims[k] : 1;
-    h.D = D; h.K = K; h.tol = tol; h.N = (unsigned long long)N;
+    h.D = D; h.K = K; h.tol = tol; h.N = (unsigned long long)N; h.hist = w.hist;
     CK(launch_header(h, hs.len, w.sc, out, s));
     return HPDR_OK;
 }
@@ -247,8 +236,8 @@ struct Hdr {
     int dtype, ndim, L, mode, tol_kind;
     size_t dims[3];
     unsigned D, K, s_lo, s_hi;
-    unsigned long long N, n_out, bits, nch, nwords;
-    unsigned long long off_len, off_chunk, off_out, off_bits, total;
+    unsigned long long N, n_esc, bits, nch, nwords;
+    unsigned long long off_len, off_chunk, off_bits, total;
     double q[kMaxLevels + 1];
 };
 
@@ -267,7 +256,7 @@ uint64_t rd64(const uint8_t *p) { uint64_t v = 0; for (int i = 0; i < 8; i++) v 
 hpdr_status parse_header(const uint8_t *b, size_t avail, size_t in_bytes, Hdr *h)
 {
     if (in_bytes < 128 || avail < 128) return HPDR_ERR_FORMAT;
-    if (memcmp(b, "HPDR", 4) != 0 || rd32(b + 4) != 1) return HPDR_ERR_FORMAT;
+    if (memcmp(b, "HPDR", 4) != 0 || rd32(b + 4) != 2) return HPDR_ERR_FORMAT;
     if (crc32_host(b, 124) != rd32(b + 124)) return HPDR_ERR_FORMAT;
     h->dtype = (int)rd32(b + 8);
     h->ndim = (int)rd32(b + 12);
@@ -281,21 +270,21 @@ hpdr_status parse_header(const uint8_t *b, size_t avail, size_t in_bytes, Hdr *h
     h->K = rd32(b + 56);
     h->s_lo = rd32(b + 60);
     h->N = rd64(b + 96);
-    h->n_out = rd64(b + 104);
+    h->n_esc = rd64(b + 104);
     h->bits = rd64(b + 112);
     h->s_hi = rd32(b + 120);
     if (levels_of(h->ndim, h->dims) != h->L || h->L > kMaxLevels) return HPDR_ERR_FORMAT;
     if ((long long)h->N != total_of(h->ndim, h->dims)) return HPDR_ERR_FORMAT;
     if (h->D < 4 || h->D > 65536 || (h->D & 1) || h->K < 128 || h->K > 32768 || (h->K % 128))
         return HPDR_ERR_FORMAT;
-    if (h->s_hi >= h->D || h->s_lo > h->s_hi || h->n_out > h->N) return HPDR_ERR_FORMAT;
-    if (h->bits > 63ULL * h->N || h->bits < h->N) return HPDR_ERR_FORMAT;
+    if (h->s_hi >= h->D || h->s_lo > h->s_hi || h->n_esc > h->N) return HPDR_ERR_FORMAT;
+    // at most 63 code bits per symbol plus 69 payload bits per escape
+    if (h->bits > 63ULL * h->N + 69ULL * h->n_esc || h->bits < h->N) return HPDR_ERR_FORMAT;
     h->nch = (h->N + h->K - 1) / h->K;
     h->nwords = (h->bits + 31) / 32;
     h->off_len = a16(128 + 8ULL * (h->L + 1));
     h->off_chunk = a16(h->off_len + (h->s_hi - h->s_lo + 1));
-    h->off_out = a16(h->off_chunk + 8 * h->nch);
-    h->off_bits = a16(h->off_out + 16 * h->n_out);
+    h->off_bits = a16(h->off_chunk + 8 * h->nch);
     h->total = h->off_bits + 4 * h->nwords;
     if (h->total > in_bytes) return HPDR_ERR_FORMAT;
     if (avail >= 128 + 8ULL * (h->L + 1))
@@ -325,7 +314,7 @@ hpdr_status decompress_t(hpdr_ctx *ctx, const Plan *P, const Hdr &h, const uint8
         hsc->rho_d[l] = 1.0 / h.q[l];
         hsc->rho_f[l] = (float)(1.0 / h.q[l]);
     }
-    hsc->n_out = h.n_out;
+    hsc->n_esc = h.n_esc;
     hsc->total_bits = h.bits;
     CK(cudaMemcpyAsync(w.sc, hsc, sizeof(Scalars), cudaMemcpyHostToDevice, s));
     HuffScratch hs;
@@ -340,20 +329,14 @@ hpdr_status decompress_t(hpdr_ctx *ctx, const Plan *P, const Hdr &h, const uint8
     da.words = (const uint32_t *)(in + h.off_bits);
     da.nwords = h.nwords;
     da.chunk = (const unsigned long long *)(in + h.off_chunk);
-    da.N = h.N; da.total_bits = h.bits; da.K = h.K; da.sym = w.sym;
+    da.N = h.N; da.total_bits = h.bits; da.K = h.K; da.sym = w.sym; da.esc = w.esc;
     {
     ProfScope ps(ctx, "d_decode", s);
     CK(launch_decode(da, hs, s));
     }
     SymIn si;
-    si.sym = w.sym; si.D = h.D; si.sc = w.sc;
-    si.out_idx = (const unsigned long long *)(in + h.off_out);
-    si.out_k = (const long long *)(in + h.off_out + 8 * h.n_out);
-    si.n_out = h.n_out;
+    si.sym = w.sym; si.D = h.D; si.sc = w.sc; si.esc = w.esc;
     si.status = &w.sc->status;
-    si.K = h.K;
-    si.ochunk = w.chunk_bits;
-    CK(launch_outlier_chunks(si.out_idx, h.n_out, h.K, h.nch, w.chunk_bits, s));
     // level buffers: v_{l-1} in X, v_l written to Y (or to out at l = L)
     T *bufs[2] = {(T *)w.va, (T *)w.vb};
     T *v = L == 0 ? out : bufs[0];
@@ -665,14 +648,14 @@ size_t hpdr_compress_bound(int ndim, const size_t *dims, hpdr_dtype dtype, const
     int L = levels_of(ndim, dims);
     unsigned long long N = (unsigned long long)total_of(ndim, dims);
     // a Huffman code is never longer in total than the fixed-length code of
-    // ceil(log2 D) bits per symbol; the outlier list holds at most out_cap_of(N)
+    // ceil(log2 D) bits per symbol; an escape payload takes at most 38 bits
+    // while |k| < 2^31
     unsigned bpsym = 1;
     while ((1ULL << bpsym) < D) bpsym++;
     unsigned long long b = a16(128 + 8ULL * (L + 1));
     b = a16(b + D);
     b = a16(b + 8 * ((N + K - 1) / K));
-    b = a16(b + 16 * out_cap_of((long long)N));
-    b += 4 * ((bpsym * N + 31) / 32);
+    b += 4 * (((bpsym + 38ULL) * N + 31) / 32);
     return (size_t)b;
 }
 
@@ -785,7 +768,7 @@ hpdr_status hpdr_huffman_encode(hpdr_ctx *ctx, const uint16_t *d_symbols, uint64
     unsigned long long nch = (N + K - 1) / K;
     Carver c(nullptr);
     c.take<Scalars>(1); c.take<unsigned long long>(D); c.take<unsigned long long>(nch + 2);
-    c.take<unsigned>(nch + 2); c.take<unsigned long long>(1024); c.take<unsigned>(1024);
+    c.take<unsigned long long>(1024);
     c.take<char>(huff_scratch_bytes(D));
     hpdr_status st = ensure_workspace(ctx, c.used + 256);
     if (st != HPDR_OK) return st;
@@ -793,9 +776,7 @@ hpdr_status hpdr_huffman_encode(hpdr_ctx *ctx, const uint16_t *d_symbols, uint64
     Scalars *sc = w.take<Scalars>(1);
     unsigned long long *hist = w.take<unsigned long long>(D);
     unsigned long long *cb = w.take<unsigned long long>(nch + 2);
-    unsigned *ce = w.take<unsigned>(nch + 2);
     unsigned long long *bs = w.take<unsigned long long>(1024);
-    unsigned *be = w.take<unsigned>(1024);
     void *hb = w.take<char>(huff_scratch_bytes(D));
     CK(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
     CK(cudaMemsetAsync(hist, 0, 8ULL * D, s));
@@ -806,7 +787,7 @@ hpdr_status hpdr_huffman_encode(hpdr_ctx *ctx, const uint16_t *d_symbols, uint64
     EncodeArgs ea;
     memset(&ea, 0, sizeof(ea));
     ea.sym = d_symbols; ea.N = N; ea.D = D; ea.K = K; ea.len = hs.len; ea.code = hs.code;
-    ea.chunk_bits = cb; ea.chunk_esc = ce; ea.sc = sc; ea.bsum = bs; ea.besc = be;
+    ea.chunk_bits = cb; ea.sc = sc; ea.bsum = bs;
     ea.chunk_out = (unsigned long long *)d_chunk_bits;
     ea.words_out = d_words;
     ea.words_cap = words_capacity;
@@ -846,7 +827,7 @@ hpdr_status hpdr_huffman_decode(hpdr_ctx *ctx, const uint32_t *d_words, uint64_t
     DecodeArgs da;
     da.words = d_words; da.nwords = (total_bits + 31) / 32;
     da.chunk = (const unsigned long long *)d_chunk_bits;
-    da.N = N; da.K = K; da.sym = d_symbols; da.total_bits = total_bits;
+    da.N = N; da.K = K; da.sym = d_symbols; da.total_bits = total_bits; da.esc = nullptr;
     Scalars *hsc = (Scalars *)ctx->host_pinned;
     CK(launch_decode(da, hs, s));
     CK(cudaMemcpyAsync(hsc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));

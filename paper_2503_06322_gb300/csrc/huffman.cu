@@ -17,7 +17,7 @@ namespace {
 
 constexpr int kRankBlocks = 152 * 2;
 constexpr int kSmemKeys = 12288;     // keys one block stages in shared memory (96 KB)
-constexpr int kSmemCodes = 8192;     // codewords staged by the encoder
+constexpr int kSmemCodes = 16384;    // codewords staged by the encoder
 constexpr int kEncThreads = 128;
 
 __device__ __forceinline__ unsigned warp_sum(unsigned v)
@@ -311,21 +311,6 @@ __global__ void __launch_bounds__(256) assign_kernel(HuffScratch hs)
     }
 }
 
-__global__ void __launch_bounds__(256) lut_kernel(HuffScratch hs)
-{
-    const unsigned n = *hs.nsym;
-    if (*hs.status) return;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        unsigned long long k = hs.keys2[i];
-        unsigned s = (unsigned)(k & 0xFFFFu), L = (unsigned)(k >> 16);
-        if (L == 0 || L > (unsigned)kLutBits) continue;
-        unsigned long long c = hs.code[s];
-        unsigned base = (unsigned)(c << (kLutBits - L));
-        unsigned span = 1u << (kLutBits - L);
-        for (unsigned e = 0; e < span; e++) hs.lut[base + e] = s | (L << 16);
-    }
-}
-
 __global__ void __launch_bounds__(256) len16_kernel(HuffScratch hs)
 {
     const unsigned n = *hs.nsym;
@@ -340,34 +325,75 @@ __global__ void __launch_bounds__(256) len16_kernel(HuffScratch hs)
     }
 }
 
+// Decoder table entry of every 15-bit prefix t:
+//   codeword of at most 15 bits:  symbol | L << 16                       (1 <= L <= 15)
+//   longer codewords:             kLongFlag | Lmin << 16 | (Lmax - Lmin) << 24,
+//                                 the lengths of the smallest and largest codeword
+//                                 under t (canonical codes grow in length with value)
+//   no codeword (incomplete code): 0
+constexpr uint32_t kLongFlag = 0x80000000u;
+
+__device__ __forceinline__ unsigned code_len_at(const HuffScratch &hs, unsigned long long win, int maxL)
+{
+    // length of the canonical codeword at the top of the left-aligned window:
+    // one more than the number of shorter lengths whose limit win reaches
+    unsigned L = 1;
+    for (int l = 1; l < maxL; l++) L += (win >= hs.lim[l]) ? 1u : 0u;
+    return L;
+}
+
+__global__ void __launch_bounds__(256) lut15_kernel(HuffScratch hs)
+{
+    const unsigned n = *hs.nsym;
+    const bool ok = *hs.status == 0;
+    int maxL = 0;
+    for (int l = kMaxCodeLen; l >= 1; l--) if (hs.count[l]) { maxL = l; break; }
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < (1u << kLenBits); t += gridDim.x * blockDim.x) {
+        uint32_t e = 0;
+        const unsigned L = ok ? hs.len16[t] : 0u;
+        if (L) {
+            const unsigned long long off = (unsigned long long)(t >> (kLenBits - L)) - hs.first[L];
+            if (off < hs.count[L]) {
+                const unsigned idx = hs.start[L] + (unsigned)off;
+                if (idx < n) e = (uint32_t)hs.sorted_sym[idx] | (L << 16);
+            }
+        } else if (ok) {
+            const unsigned long long w0 = (unsigned long long)t << (64 - kLenBits);
+            const unsigned long long w1 = w0 | ((1ULL << (64 - kLenBits)) - 1);
+            const unsigned lmin = code_len_at(hs, w0, maxL);
+            const unsigned lmax = code_len_at(hs, w1, maxL);
+            if (lmin > (unsigned)kLenBits && lmin <= lmax)
+                e = kLongFlag | (lmin << 16) | ((lmax - lmin) << 24);
+        }
+        hs.lut15[t] = e;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Encoder
 
 struct Layout {
-    unsigned long long off_len, off_chunk, off_out, off_bits, total;
+    unsigned long long off_len, off_chunk, off_bits, total;
 };
 __device__ __forceinline__ Layout container_layout(int L, unsigned s_lo, unsigned s_hi,
-                                                   unsigned long long nch, unsigned long long nout,
-                                                   unsigned long long bits)
+                                                   unsigned long long nch, unsigned long long bits)
 {
     Layout y;
     y.off_len = a16(128 + 8ULL * (L + 1));
     y.off_chunk = a16(y.off_len + (s_hi - s_lo + 1));
-    y.off_out = a16(y.off_chunk + 8 * nch);
-    y.off_bits = a16(y.off_out + 16 * nout);
+    y.off_bits = a16(y.off_chunk + 8 * nch);
     y.total = y.off_bits + 4 * ((bits + 31) / 32);
     return y;
 }
 
 constexpr int kEncBlocks = 152 * 4;
 
-// bits and escapes of every chunk; block b owns the contiguous chunk range
-// [b*cpb, (b+1)*cpb) and also leaves the sums of its range in bsum/besc
+// bits of every chunk (codewords + escape payloads); block b owns the
+// contiguous chunk range [b*cpb, (b+1)*cpb) and leaves its sum in bsum
 __global__ void __launch_bounds__(256) enc_count_kernel(EncodeArgs a)
 {
     extern __shared__ uint8_t slen[];
     __shared__ unsigned long long wb[8];
-    __shared__ unsigned we[8];
     if (block_skip(&a.sc->status)) return;
     for (unsigned i = threadIdx.x; i < a.D; i += blockDim.x) slen[i] = a.len[i];
     __syncthreads();
@@ -376,39 +402,37 @@ __global__ void __launch_bounds__(256) enc_count_kernel(EncodeArgs a)
     const unsigned long long c0 = blockIdx.x * cpb, c1 = c0 + cpb < nch ? c0 + cpb : nch;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long tb = 0;
-    unsigned te = 0;
     for (unsigned long long c = c0 + warp; c < c1; c += blockDim.x >> 5) {
         const unsigned long long beg = c * a.K;
         const unsigned long long end = beg + a.K < a.N ? beg + a.K : a.N;
         unsigned long long bits = 0;
-        unsigned esc = 0;
         if (end - beg == a.K) {
             const uint4 *v = reinterpret_cast<const uint4 *>(a.sym + beg);
             for (unsigned i = lane; i < a.K / 8; i += 32) {
                 uint4 x = v[i];
                 const uint16_t *e = reinterpret_cast<const uint16_t *>(&x);
 #pragma unroll
-                for (int k = 0; k < 8; k++) { bits += slen[e[k]]; esc += e[k] == 0; }
+                for (int k = 0; k < 8; k++) {
+                    bits += slen[e[k]];
+                    if (a.esc && e[k] == 0) bits += esc_bits(a.esc[beg + 8ULL * i + k]);
+                }
             }
         } else {
             for (unsigned long long i = beg + lane; i < end; i += 32) {
                 uint16_t s = a.sym[i];
                 bits += slen[s];
-                esc += s == 0;
+                if (a.esc && s == 0) bits += esc_bits(a.esc[i]);
             }
         }
         bits = warp_sum64(bits);
-        esc = warp_sum(esc);
-        if (lane == 0) { a.chunk_bits[c] = bits; a.chunk_esc[c] = esc; tb += bits; te += esc; }
+        if (lane == 0) { a.chunk_bits[c] = bits; tb += bits; }
     }
-    if (lane == 0) { wb[warp] = tb; we[warp] = te; }
+    if (lane == 0) wb[warp] = tb;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long x = 0;
-        unsigned y = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) { x += wb[w]; y += we[w]; }
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) x += wb[w];
         a.bsum[blockIdx.x] = x;
-        a.besc[blockIdx.x] = y;
     }
 }
 
@@ -416,32 +440,23 @@ __global__ void __launch_bounds__(256) enc_count_kernel(EncodeArgs a)
 __global__ void __launch_bounds__(1024) enc_scan1_kernel(EncodeArgs a, int nb)
 {
     __shared__ unsigned long long sb[1024];
-    __shared__ unsigned se[1024];
     if (block_skip(&a.sc->status)) return;
     const int t = threadIdx.x;
     sb[t] = t < nb ? a.bsum[t] : 0;
-    se[t] = t < nb ? a.besc[t] : 0;
     __syncthreads();
     for (int o = 1; o < 1024; o <<= 1) {
         unsigned long long x = t >= o ? sb[t - o] : 0;
-        unsigned y = t >= o ? se[t - o] : 0;
         __syncthreads();
         sb[t] += x;
-        se[t] += y;
         __syncthreads();
     }
     // inclusive -> exclusive
-    if (t < nb) {
-        a.bsum[t] = t ? sb[t - 1] : 0;
-        a.besc[t] = t ? se[t - 1] : 0;
-    }
+    if (t < nb) a.bsum[t] = t ? sb[t - 1] : 0;
     if (t == 0) {
         const unsigned long long nch = (a.N + a.K - 1) / a.K;
         const unsigned long long x = sb[1023];
-        const unsigned y = se[1023];
         if (a.container) {
-            if ((unsigned long long)y != a.sc->n_out) atomicExch(&a.sc->status, (unsigned)DS_FORMAT);
-            Layout lay = container_layout(a.L, a.sc->s_lo, a.sc->s_hi, nch, a.sc->n_out, x);
+            Layout lay = container_layout(a.L, a.sc->s_lo, a.sc->s_hi, nch, x);
             if (lay.total > a.capacity) atomicExch(&a.sc->status, (unsigned)DS_CAPACITY);
             a.sc->out_bytes = lay.total;
         } else {
@@ -454,7 +469,7 @@ __global__ void __launch_bounds__(1024) enc_scan1_kernel(EncodeArgs a, int nb)
 __device__ __forceinline__ uint32_t *enc_words(const EncodeArgs &a, unsigned long long nch)
 {
     if (!a.container) return a.words_out;
-    Layout lay = container_layout(a.L, a.sc->s_lo, a.sc->s_hi, nch, a.sc->n_out, a.sc->total_bits);
+    Layout lay = container_layout(a.L, a.sc->s_lo, a.sc->s_hi, nch, a.sc->total_bits);
     return reinterpret_cast<uint32_t *>(a.container + lay.off_bits);
 }
 
@@ -463,7 +478,6 @@ __device__ __forceinline__ uint32_t *enc_words(const EncodeArgs &a, unsigned lon
 __global__ void __launch_bounds__(256) enc_scan2_kernel(EncodeArgs a)
 {
     __shared__ unsigned long long sb[256];
-    __shared__ unsigned se[256];
     if (block_skip(&a.sc->status)) return;
     const unsigned long long nch = (a.N + a.K - 1) / a.K;
     const unsigned long long cpb = (nch + gridDim.x - 1) / gridDim.x;
@@ -471,32 +485,26 @@ __global__ void __launch_bounds__(256) enc_scan2_kernel(EncodeArgs a)
     uint32_t *words = enc_words(a, nch);
     unsigned long long *ctab = a.chunk_out;
     if (a.container) {
-        Layout lay = container_layout(a.L, a.sc->s_lo, a.sc->s_hi, nch, a.sc->n_out, a.sc->total_bits);
+        Layout lay = container_layout(a.L, a.sc->s_lo, a.sc->s_hi, nch, a.sc->total_bits);
         ctab = reinterpret_cast<unsigned long long *>(a.container + lay.off_chunk);
     }
     const unsigned long long total = a.sc->total_bits;
     unsigned long long carry = a.bsum[blockIdx.x];
-    unsigned ecarry = a.besc[blockIdx.x];
     const int t = threadIdx.x;
     for (unsigned long long base = c0; base < c1; base += 256) {
         const unsigned long long c = base + t;
         unsigned long long v = c < c1 ? a.chunk_bits[c] : 0;
-        unsigned e = c < c1 ? a.chunk_esc[c] : 0;
         sb[t] = v;
-        se[t] = e;
         __syncthreads();
         for (int o = 1; o < 256; o <<= 1) {
             unsigned long long x = t >= o ? sb[t - o] : 0;
-            unsigned y = t >= o ? se[t - o] : 0;
             __syncthreads();
             sb[t] += x;
-            se[t] += y;
             __syncthreads();
         }
         if (c < c1) {
             const unsigned long long off = carry + sb[t] - v;
             a.chunk_bits[c] = off;
-            a.chunk_esc[c] = ecarry + se[t] - e;
             ctab[c] = off;
             const unsigned long long cend = off + v;
             // full chunks of K >= 1024 symbols share only their first word with the previous
@@ -511,7 +519,6 @@ __global__ void __launch_bounds__(256) enc_scan2_kernel(EncodeArgs a)
         }
         __syncthreads();
         carry += sb[255];
-        ecarry += se[255];
         __syncthreads();
     }
     if (blockIdx.x == 0 && t == 0) a.chunk_bits[nch] = total;
@@ -535,11 +542,7 @@ __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
     const unsigned long long *codes = code_sm ? scode : a.code;
     const unsigned long long nch = (a.N + a.K - 1) / a.K;
     uint32_t *words = enc_words(a, nch);
-    unsigned long long *oidx = nullptr;
-    if (a.container) {
-        Layout lay = container_layout(a.L, a.sc->s_lo, a.sc->s_hi, nch, a.sc->n_out, a.sc->total_bits);
-        oidx = reinterpret_cast<unsigned long long *>(a.container + lay.off_out);
-    }
+    const long long *esc = a.esc;
     const unsigned lane = threadIdx.x & 31;
     const unsigned spl = a.K >> 5;
     const unsigned long long wg = blockIdx.x * (unsigned long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -551,7 +554,6 @@ __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
         if (m0 > end) m0 = end;
         if (m1 > end) m1 = end;
         unsigned long long mb = 0;
-        unsigned me = 0;
         // full lanes of 32 symbols keep them in registers (four 16-byte loads)
         uint32_t rs[16];
         const bool regs = (m1 - m0 == 32) && spl == 32;
@@ -566,30 +568,29 @@ __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
             for (int q = 0; q < 32; q++) {
                 const unsigned sv = (rs[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
                 mb += slen[sv];
-                me += sv == 0;
+                if (esc && sv == 0) mb += esc_bits(esc[m0 + q]);
             }
         } else {
-            for (unsigned long long i = m0; i < m1; i++) { const uint16_t s = a.sym[i]; mb += slen[s]; me += s == 0; }
+            for (unsigned long long i = m0; i < m1; i++) {
+                const uint16_t s = a.sym[i];
+                mb += slen[s];
+                if (esc && s == 0) mb += esc_bits(esc[i]);
+            }
         }
         unsigned long long xb = mb;
-        unsigned xe = me;
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long yb = __shfl_up_sync(0xffffffffu, xb, o);
-            const unsigned ye = __shfl_up_sync(0xffffffffu, xe, o);
-            if ((int)lane >= o) { xb += yb; xe += ye; }
+            if ((int)lane >= o) xb += yb;
         }
         const unsigned long long start = a.chunk_bits[c] + xb - mb;
-        unsigned ebase = a.chunk_esc[c] + xe - me;
         unsigned long long acc = 0;
         unsigned nacc = (unsigned)(start & 31);
         unsigned long long widx = start >> 5;
         const unsigned long long fidx = widx;
         uint32_t firstw = 0;
         bool have_first = false;
-        auto put = [&](uint16_t s, unsigned long long i) {
-            int L = slen[s];
-            const unsigned long long cw = codes[s];
-            if (oidx && s == 0) oidx[ebase++] = i;
+        // append the low L bits of cw (L <= 64), most significant first
+        auto emit = [&](unsigned long long cw, int L) {
             while (L > 0) {
                 const int take = L > 32 ? 32 : L;
                 const unsigned long long part = (cw >> (L - take)) & ((1ULL << take) - 1);
@@ -605,6 +606,27 @@ __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
                     nacc -= 32;
                 }
             }
+        };
+        auto put = [&](uint16_t s, unsigned long long i) {
+            unsigned long long cw = codes[s];
+            int L = slen[s];
+            if (esc && s == 0) {
+                // codeword, 6 bits n - 1 and the n bits of zigzag(k), in one
+                // emission when they fit 64 bits
+                const unsigned long long z = zigzag(esc[i]);
+                const int n = 64 - __clzll((long long)z);
+                const unsigned long long pay = ((unsigned long long)(n - 1) << n) | z;
+                if (L + 6 + n <= 64) {
+                    cw = (cw << (6 + n)) | pay;
+                    L += 6 + n;
+                } else {
+                    emit(cw, L);
+                    emit((unsigned long long)(n - 1), 6);
+                    cw = z;
+                    L = n;
+                }
+            }
+            emit(cw, L);
         };
         if (regs) {
 #pragma unroll
@@ -635,23 +657,6 @@ __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
     }
 }
 
-__global__ void __launch_bounds__(256) outlier_place_kernel(EncodeArgs a)
-{
-    if (a.sc->status || !a.container) return;
-    const unsigned long long nout = a.sc->n_out;
-    const unsigned long long nch = (a.N + a.K - 1) / a.K;
-    Layout lay = container_layout(a.L, a.sc->s_lo, a.sc->s_hi, nch, nout, a.sc->total_bits);
-    const unsigned long long *sidx = reinterpret_cast<const unsigned long long *>(a.container + lay.off_out);
-    long long *sk = reinterpret_cast<long long *>(a.container + lay.off_out + 8 * nout);
-    for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; e < nout;
-         e += (unsigned long long)gridDim.x * blockDim.x) {
-        unsigned long long idx = a.oidx_unordered[e];
-        unsigned long long lo = 0, hi = nout;
-        while (lo < hi) { unsigned long long m = (lo + hi) >> 1; if (sidx[m] < idx) lo = m + 1; else hi = m; }
-        if (lo < nout && sidx[lo] == idx) sk[lo] = a.ok_unordered[e];
-        else atomicExch(&a.sc->status, (unsigned)DS_FORMAT);
-    }
-}
 
 __device__ uint32_t crc32_bytes(const uint8_t *p, int n)
 {
@@ -673,11 +678,12 @@ header_kernel(HeaderArgs h, const uint8_t *len, Scalars *sc, uint8_t *out)
     __shared__ uint8_t hdr[128];
     if (block_skip(&sc->status)) return;
     const unsigned long long nch = (h.N + h.K - 1) / h.K;
-    Layout lay = container_layout(h.L, sc->s_lo, sc->s_hi, nch, sc->n_out, sc->total_bits);
+    Layout lay = container_layout(h.L, sc->s_lo, sc->s_hi, nch, sc->total_bits);
+    const unsigned long long n_esc = h.hist ? h.hist[0] : 0ULL;
     if (threadIdx.x == 0) {
         for (int i = 0; i < 128; i++) hdr[i] = 0;
         hdr[0] = 'H'; hdr[1] = 'P'; hdr[2] = 'D'; hdr[3] = 'R';
-        put32(hdr + 4, 1);
+        put32(hdr + 4, 2);
         put32(hdr + 8, (uint32_t)h.dtype);
         put32(hdr + 12, (uint32_t)h.ndim);
         for (int k = 0; k < 3; k++) put64(hdr + 16 + 8 * k, h.dims[k]);
@@ -692,7 +698,8 @@ header_kernel(HeaderArgs h, const uint8_t *len, Scalars *sc, uint8_t *out)
         putd(hdr + 80, sc->maxabs);
         putd(hdr + 88, sqrt(sc->sumsq / (double)h.N));
         put64(hdr + 96, h.N);
-        put64(hdr + 104, sc->n_out);
+        put64(hdr + 104, n_esc);
+        sc->n_esc = n_esc;
         put64(hdr + 112, sc->total_bits);
         put32(hdr + 120, sc->s_hi);
         put32(hdr + 124, crc32_bytes(hdr, 124));
@@ -705,8 +712,7 @@ header_kernel(HeaderArgs h, const uint8_t *len, Scalars *sc, uint8_t *out)
     const unsigned nlen = sc->s_hi - sc->s_lo + 1;
     for (unsigned i = threadIdx.x; i < nlen; i += blockDim.x) out[lay.off_len + i] = len[sc->s_lo + i];
     for (unsigned long long i = lay.off_len + nlen + threadIdx.x; i < lay.off_chunk; i += blockDim.x) out[i] = 0;
-    for (unsigned long long i = lay.off_chunk + 8 * nch + threadIdx.x; i < lay.off_out; i += blockDim.x) out[i] = 0;
-    for (unsigned long long i = lay.off_out + 16 * sc->n_out + threadIdx.x; i < lay.off_bits; i += blockDim.x) out[i] = 0;
+    for (unsigned long long i = lay.off_chunk + 8 * nch + threadIdx.x; i < lay.off_bits; i += blockDim.x) out[i] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -728,28 +734,74 @@ __device__ __forceinline__ uint4 ld4(const uint32_t *w, unsigned long long i, un
     return v;
 }
 
-// Decoder: one thread per chunk.  A table of 2^16 bytes gives the code length
-// of every 16-bit prefix (canonical codes make the length a function of the
-// prefix); longer codes count the limits they exceed, without branches.  The
-// symbol is then sorted_sym[start[L] + code - first[L]].
-constexpr int kDecSymSmem = 8192;
+// Decoder: one thread per chunk of K symbols.  The thread keeps the next bits
+// of its chunk MSB-aligned in two 32-bit registers hi:lo (nb valid bits, at
+// least 32 before every read) and refills them a word at a time from a queue
+// of two prefetched 16-byte blocks.  The 2^15-entry table of every 15-bit
+// prefix gives symbol and length of a codeword of at most 15 bits in one
+// shared-memory load; for longer codewords it gives the range of lengths
+// under the prefix, and the length is the lower end plus the number of
+// length limits the window reaches in that range (canonical codes); the
+// symbol is then sorted_sym[start[L] + code - first[L]].  A codeword longer
+// than the buffered bits (only possible above 32 bits) re-reads its window
+// from global memory.  Escape payloads (container streams) follow symbol 0.
+constexpr int kDecSymSmem = 16384;
+constexpr int kDecThreads = 1024;
 
-__global__ void __launch_bounds__(256, 4) decode_kernel(DecodeArgs a, HuffScratch hs)
+struct BitQueue {
+    const uint32_t *w;
+    unsigned long long n;     // words in the stream
+    uint4 pa, pb;             // current and next aligned block
+    unsigned k;               // next word of pa
+    unsigned long long nxt;   // next block to fetch
+    __device__ __forceinline__ uint32_t next()
+    {
+        const uint32_t v = k == 0 ? pa.x : k == 1 ? pa.y : k == 2 ? pa.z : pa.w;
+        if (++k == 4) { k = 0; pa = pb; pb = ld4(w, nxt, n); nxt += 4; }
+        return v;
+    }
+    // position the queue at bit pos and load the first 64 bits from there
+    __device__ __forceinline__ void prime(unsigned long long pos, uint32_t &hi, uint32_t &lo, int &nb)
+    {
+        const unsigned long long wb0 = (pos >> 5) & ~3ULL;
+        pa = ld4(w, wb0, n);
+        pb = ld4(w, wb0 + 4, n);
+        nxt = wb0 + 8;
+        k = (unsigned)((pos >> 5) & 3);
+        const uint32_t w0 = next(), w1 = next();
+        const unsigned sh = (unsigned)(pos & 31);
+        hi = __funnelshift_l(w1, w0, sh);
+        lo = w1 << sh;
+        nb = 64 - (int)sh;
+    }
+};
+
+// 64 bits of the stream from bit pos (words past the end read as zero)
+__device__ __forceinline__ unsigned long long window64(const uint32_t *w, unsigned long long n,
+                                                       unsigned long long pos)
+{
+    const unsigned long long i = pos >> 5;
+    const unsigned sh = (unsigned)(pos & 31);
+    const unsigned long long hi = (((unsigned long long)ldw(w, i, n)) << 32) | ldw(w, i + 1, n);
+    return sh ? (hi << sh) | (ldw(w, i + 2, n) >> (32 - sh)) : hi;
+}
+
+__global__ void __launch_bounds__(kDecThreads, 1) decode_kernel(DecodeArgs a, HuffScratch hs)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
-    uint8_t *len16 = dsm;                                                     // [1 << kLenBits]
-    unsigned long long *sfirst = reinterpret_cast<unsigned long long *>(dsm + (1 << kLenBits));  // [64]
-    unsigned long long *slim = sfirst + 64;                                   // [64]
-    unsigned *sstart = reinterpret_cast<unsigned *>(slim + 64);               // [64]
-    unsigned *scount = sstart + 64;                                           // [64]
-    uint16_t *ssym = reinterpret_cast<uint16_t *>(scount + 64);               // [kDecSymSmem]
+    uint32_t *lut = reinterpret_cast<uint32_t *>(dsm);                                      // [1 << kLenBits]
+    unsigned long long *sfirst = reinterpret_cast<unsigned long long *>(dsm + (4u << kLenBits));  // [64]
+    unsigned long long *slim = sfirst + 64;                                                  // [64]
+    unsigned *sstart = reinterpret_cast<unsigned *>(slim + 64);                              // [64]
+    unsigned *scount = sstart + 64;                                                          // [64]
+    uint16_t *ssym = reinterpret_cast<uint16_t *>(scount + 64);                              // [kDecSymSmem]
     if (block_skip(hs.status)) return;
     const unsigned nsym = *hs.nsym;
     const bool sym_sm = nsym <= (unsigned)kDecSymSmem;
     {
-        const uint4 *src = reinterpret_cast<const uint4 *>(hs.len16);
-        uint4 *dst = reinterpret_cast<uint4 *>(len16);
-        for (int i = threadIdx.x; i < (1 << kLenBits) / 16; i += blockDim.x) dst[i] = src[i];
+        const uint4 *src = reinterpret_cast<const uint4 *>(hs.lut15);
+        uint4 *dst = reinterpret_cast<uint4 *>(lut);
+        for (int i = threadIdx.x; i < (4 << kLenBits) / 16; i += blockDim.x) dst[i] = src[i];
     }
     for (int i = threadIdx.x; i < 64; i += blockDim.x) {
         sfirst[i] = hs.first[i];
@@ -761,65 +813,102 @@ __global__ void __launch_bounds__(256, 4) decode_kernel(DecodeArgs a, HuffScratc
         for (unsigned i = threadIdx.x; i < nsym; i += blockDim.x) ssym[i] = hs.sorted_sym[i];
     __syncthreads();
     const uint16_t *symtab = sym_sm ? ssym : hs.sorted_sym;
-    int maxL = 0;
-    for (int L = kMaxCodeLen; L >= 1; L--) if (scount[L]) { maxL = L; break; }
+    long long *const esc = a.esc;
     const unsigned long long nch = (a.N + a.K - 1) / a.K;
     for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < nch;
          c += (unsigned long long)gridDim.x * blockDim.x) {
-        unsigned long long pos = a.chunk[c];
+        const unsigned long long pos0 = a.chunk[c];
         const unsigned long long expect = (c + 1 < nch) ? a.chunk[c + 1] : a.total_bits;
-        if (pos > a.total_bits || expect > a.total_bits || pos > expect) {
+        if (pos0 > a.total_bits || expect > a.total_bits || pos0 > expect) {
             atomicExch(hs.status, (unsigned)DS_FORMAT);
             continue;
         }
-        // words arrive 16 bytes at a time, one aligned block ahead of use:
-        // w0..w2 hold the window, pa the rest of the current block, pb the next
-        const unsigned long long wb0 = (pos >> 5) & ~3ULL;   // aligned block of the first word
-        uint4 pa = ld4(a.words, wb0, a.nwords), pb = ld4(a.words, wb0 + 4, a.nwords);
-        unsigned k = (unsigned)((pos >> 5) & 3);             // next word of pa to shift in
-        unsigned long long nxt = wb0 + 8;                    // next block to fetch
-        auto take = [&]() -> uint32_t {
-            const uint32_t v = k == 0 ? pa.x : k == 1 ? pa.y : k == 2 ? pa.z : pa.w;
-            if (++k == 4) { k = 0; pa = pb; pb = ld4(a.words, nxt, a.nwords); nxt += 4; }
+        BitQueue q;
+        q.w = a.words;
+        q.n = a.nwords;
+        uint32_t hi, lo;
+        int nb;
+        q.prime(pos0, hi, lo, nb);
+        unsigned used = 0;
+        bool bad = false;
+        // drop n <= 32 bits, then refill to at least 32 valid bits
+        auto drop = [&](unsigned n) {
+            if (n < 32) { hi = __funnelshift_l(lo, hi, n); lo <<= n; }
+            else { hi = lo; lo = 0; }
+            nb -= (int)n;
+            used += n;
+            if (nb < 32) {
+                const uint32_t wv = q.next();
+                hi |= wv >> nb;
+                lo = __funnelshift_rc(0u, wv, (unsigned)nb);
+                nb += 32;
+            }
+        };
+        auto take = [&](unsigned n) -> uint32_t {   // 1 <= n <= 32
+            const uint32_t v = hi >> (32 - n);
+            drop(n);
             return v;
         };
-        uint32_t w0 = take(), w1 = take(), w2 = take();
-        unsigned sh = (unsigned)(pos & 31);
-        const unsigned long long beg = c * a.K;
-        const unsigned long long end = beg + a.K < a.N ? beg + a.K : a.N;
-        bool bad = false;
-        auto step = [&]() -> uint16_t {
-            unsigned long long win = (((unsigned long long)w0 << 32) | w1) << sh;
-            if (sh) win |= (unsigned long long)(w2 >> (32 - sh));
-            unsigned L = len16[win >> (64 - kLenBits)];
-            if (L == 0) {
-                L = kLenBits + 1;
-                for (int l = kLenBits + 1; l < maxL; l++) L += (win >= slim[l]) ? 1u : 0u;
+        auto step = [&](unsigned long long i) -> uint16_t {
+            const uint32_t e = lut[hi >> (32 - kLenBits)];
+            uint16_t sv = (uint16_t)(e & 0xFFFFu);
+            unsigned L = (e >> 16) & 0x3Fu;
+            if (e >= kLongFlag || e == 0) {
+                // codeword longer than 15 bits (or no codeword: a corrupt stream)
+                if (e == 0) {
+                    bad = true;
+                    L = 1;
+                } else {
+                    const unsigned long long win = ((unsigned long long)hi << 32) | lo;
+                    const unsigned lmin = L, lmax = L + ((e >> 24) & 0x3Fu);
+                    for (unsigned l = lmin; l < lmax; l++) L += (win >= slim[l]) ? 1u : 0u;
+                    unsigned long long wl = win;
+                    if ((int)L > nb) {
+                        // the codeword extends past the buffered bits: exact window
+                        wl = window64(a.words, a.nwords, pos0 + used);
+                        L = lmin;
+                        for (unsigned l = lmin; l < lmax; l++) L += (wl >= slim[l]) ? 1u : 0u;
+                    }
+                    const unsigned long long off = (wl >> (64 - L)) - sfirst[L];
+                    if (off >= scount[L]) bad = true;
+                    const unsigned idx = sstart[L] + (unsigned)(off < scount[L] ? off : 0);
+                    sv = symtab[idx < nsym ? idx : 0];
+                    if ((int)L > nb) {
+                        used += L;
+                        q.prime(pos0 + used, hi, lo, nb);
+                        L = 0;
+                    } else if (L > 32) {
+                        drop(32);
+                        L -= 32;
+                    }
+                }
             }
-            const unsigned long long code = win >> (64 - L);
-            const unsigned long long off = code - sfirst[L];
-            if (off >= scount[L]) bad = true;
-            const unsigned idx = sstart[L] + (unsigned)(off < scount[L] ? off : 0);
-            const uint16_t sv = symtab[idx < nsym ? idx : 0];
-            pos += L;
-            sh += L;
-            if (sh >= 32) {
-                sh -= 32; w0 = w1; w1 = w2; w2 = take();
-                if (sh >= 32) { sh -= 32; w0 = w1; w1 = w2; w2 = take(); }
+            if (L) drop(L);
+            if (esc && sv == 0) {
+                // escape payload: 6 bits n - 1, then the n bits of zigzag(k)
+                const unsigned n = take(6) + 1;
+                unsigned long long z;
+                if (n > 32) {
+                    const unsigned long long zh = take(n - 32);
+                    z = (zh << 32) | take(32);
+                } else {
+                    z = take(n);
+                }
+                if (n == 64) bad = true;
+                esc[i] = unzigzag(z);
             }
             return sv;
         };
+        const unsigned long long beg = c * a.K;
+        const unsigned long long end = beg + a.K < a.N ? beg + a.K : a.N;
         unsigned long long i = beg;
-        for (; i + 8 <= end; i += 8) {
-            uint4 v;
-            v.x = step(); v.x |= (unsigned)step() << 16;
-            v.y = step(); v.y |= (unsigned)step() << 16;
-            v.z = step(); v.z |= (unsigned)step() << 16;
-            v.w = step(); v.w |= (unsigned)step() << 16;
-            *reinterpret_cast<uint4 *>(a.sym + i) = v;
+        for (; i + 2 <= end; i += 2) {
+            const uint32_t v0 = step(i);
+            const uint32_t v1 = step(i + 1);
+            *reinterpret_cast<uint32_t *>(a.sym + i) = v0 | (v1 << 16);
         }
-        for (; i < end; i++) a.sym[i] = step();
-        if (bad || pos != expect) atomicExch(hs.status, (unsigned)DS_FORMAT);
+        if (i < end) a.sym[i] = step(i);
+        if (bad || pos0 + used != expect) atomicExch(hs.status, (unsigned)DS_FORMAT);
     }
 }
 
@@ -856,7 +945,7 @@ cudaError_t set_attrs()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(enc_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        e = cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e == cudaSuccess) g_attr_done = true;
     return e;
 }
@@ -872,7 +961,7 @@ size_t huff_scratch_bytes(unsigned int D)
     add(4 * 2 * d); add(4 * 4 * d); add(4 * 4 * d);    // parent, anc, dep
     add(8 * d); add(8 * d);                            // leafw, intw
     add(4); add(8 * 64); add(4 * 64); add(4 * 64);     // nsym, first, count, start
-    add(d); add(8 * d); add(2 * d); add(4u << kLutBits);
+    add(d); add(8 * d); add(2 * d); add(4u << kLenBits);
     add(1u << kLenBits); add(8 * 64);
     return b;
 }
@@ -898,7 +987,7 @@ void huff_scratch_carve(void *base, unsigned int D, Scalars *sc, HuffScratch *hs
     hs->len = (uint8_t *)take(d);
     hs->code = (unsigned long long *)take(8 * d);
     hs->sorted_sym = (uint16_t *)take(2 * d);
-    hs->lut = (uint32_t *)take(4u << kLutBits);
+    hs->lut15 = (uint32_t *)take(4u << kLenBits);
     hs->len16 = (uint8_t *)take(1u << kLenBits);
     hs->lim = (unsigned long long *)take(8 * 64);
     hs->status = &sc->status;
@@ -932,7 +1021,8 @@ cudaError_t launch_decode_tables(const uint8_t *len, unsigned int D, const HuffS
     e = cudaMemsetAsync(hs.len16, 0, 1u << kLenBits, s);
     if (e != cudaSuccess) return e;
     len16_kernel<<<64, 256, 0, s>>>(hs);
-    count_launch(5);
+    lut15_kernel<<<(1u << kLenBits) / 256, 256, 0, s>>>(hs);
+    count_launch(6);
     return cudaGetLastError();
 }
 
@@ -946,8 +1036,7 @@ cudaError_t launch_encode(const EncodeArgs &a, cudaStream_t s)
     const bool code_sm = a.D <= (unsigned)kSmemCodes;
     size_t sm = (code_sm ? 8 * (size_t)a.D : 0) + ((a.D + 15) & ~15u);
     enc_write_kernel<<<152 * 3, 256, sm, s>>>(a);
-    if (a.container) outlier_place_kernel<<<152, 256, 0, s>>>(a);
-    count_launch(a.container ? 5 : 4);
+    count_launch(4);
     return cudaGetLastError();
 }
 
@@ -977,8 +1066,8 @@ cudaError_t launch_decode(const DecodeArgs &a, const HuffScratch &hs, cudaStream
 {
     cudaError_t e = set_attrs();
     if (e != cudaSuccess) return e;
-    const size_t sm = (1u << kLenBits) + 64 * 8 * 2 + 64 * 4 * 2 + kDecSymSmem * 2;
-    decode_kernel<<<152 * 4, 256, sm, s>>>(a, hs);
+    const size_t sm = (4u << kLenBits) + 64 * 8 * 2 + 64 * 4 * 2 + kDecSymSmem * 2;
+    decode_kernel<<<152, kDecThreads, sm, s>>>(a, hs);
     count_launch();
     return cudaGetLastError();
 }

@@ -4,9 +4,22 @@
 
 namespace hpdr {
 
-constexpr int kLutBits = 12;
-constexpr int kLenBits = 15;    // decoder: code length of every 15-bit prefix
+constexpr int kLenBits = 15;    // decoder: code length / symbol of every 15-bit prefix
 constexpr int kMaxCodeLen = 63;
+
+// Escape payload (container format v2): after the codeword of symbol 0, 6
+// bits holding n - 1 and the n bits of zigzag(k), n = bit length (1..63).
+__host__ __device__ inline unsigned long long zigzag(long long k)
+{
+    return k >= 0 ? 2ULL * (unsigned long long)k : 2ULL * (unsigned long long)(-(k + 1)) + 1ULL;
+}
+__host__ __device__ inline long long unzigzag(unsigned long long z)
+{
+    return (z & 1ULL) ? -(long long)(z >> 1) - 1 : (long long)(z >> 1);
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned esc_bits(long long k) { return 6u + 64u - (unsigned)__clzll((long long)zigzag(k)); }
+#endif
 
 // Device scratch of one codebook build (sizes for an alphabet of D symbols).
 struct HuffScratch {
@@ -26,8 +39,8 @@ struct HuffScratch {
     uint8_t *len;                 // [D]
     unsigned long long *code;     // [D]
     uint16_t *sorted_sym;         // [D]
-    uint32_t *lut;                // [1 << kLutBits]
-    uint8_t *len16;               // [1 << kLenBits] code length of a 16-bit prefix (0: longer)
+    uint32_t *lut15;              // [1 << kLenBits] symbol | length << 16 of a 15-bit prefix (0: longer)
+    uint8_t *len16;               // [1 << kLenBits] code length of a 15-bit prefix (0: longer)
     unsigned long long *lim;      // [64] left-justified upper limit of the codes of each length
     unsigned int *status;         // -> Scalars::status
     unsigned int *s_lo, *s_hi;    // -> Scalars
@@ -52,20 +65,18 @@ struct EncodeArgs {
     unsigned int D, K;
     const uint8_t *len;
     const unsigned long long *code;
+    const long long *esc;             // null: plain symbols; else symbol 0 is the quantizer's
+                                      // escape and esc[i] its code k (payload after the codeword)
     unsigned long long *chunk_bits;   // ws [nch+1] totals then offsets
-    unsigned int *chunk_esc;          // ws [nch+1]
     unsigned long long *bsum;         // ws [kEncBlocks] per-block sums, then offsets
-    unsigned int *besc;               // ws [kEncBlocks]
     Scalars *sc;
     // destination
-    uint8_t *container;               // if non-null: chunk table, outliers, bits go into the container
+    uint8_t *container;               // if non-null: chunk table and bits go into the container
     int L;                            // levels (container layout)
     unsigned long long capacity;      // bytes available at container / words
     unsigned long long *chunk_out;    // (container == null) chunk table destination
     uint32_t *words_out;              // (container == null) bitstream destination
     unsigned long long words_cap;
-    const unsigned long long *oidx_unordered;  // outliers from quantization
-    const long long *ok_unordered;
 };
 cudaError_t launch_encode(const EncodeArgs &a, cudaStream_t s);
 
@@ -75,6 +86,7 @@ struct HeaderArgs {
     unsigned int D, K;
     double tol;
     unsigned long long N;
+    const unsigned long long *hist;   // histogram: hist[0] = escapes recorded in the header
 };
 cudaError_t launch_header(const HeaderArgs &h, const uint8_t *len, Scalars *sc, uint8_t *container,
                           cudaStream_t s);
@@ -86,6 +98,7 @@ struct DecodeArgs {
     unsigned long long N, total_bits;
     unsigned int K;
     uint16_t *sym;
+    long long *esc;                   // null: plain symbols; else receives k of every escape
 };
 cudaError_t launch_decode(const DecodeArgs &a, const HuffScratch &hs, cudaStream_t s);
 cudaError_t launch_histogram(const uint16_t *sym, unsigned long long N, unsigned D,

@@ -70,7 +70,7 @@ struct Scalars {
     double rho_d[kMaxLevels + 1];
     float rho_f[kMaxLevels + 1];
     float q_f[kMaxLevels + 1];
-    unsigned long long n_out;     // outliers collected
+    unsigned long long n_esc;     // escaped codes (occurrences of symbol 0)
     unsigned long long total_bits;
     unsigned long long out_bytes; // container size
     unsigned int status;          // 0 ok, else an hpdr_status magnitude
@@ -79,10 +79,13 @@ struct Scalars {
     unsigned long long maxbits_f64;
 };
 
+// escaped codes must satisfy |k| < 2^62 (payload of at most 63 bits)
+constexpr long long kEscMax = 1LL << 62;
+
 enum DeviceStatus : unsigned int {
     DS_OK = 0,
-    DS_ARG = 1,          // bound below the precision floor
-    DS_CAPACITY = 3,     // output too small / outlier list full
+    DS_ARG = 1,          // bound below the precision floor, or a code beyond +-2^62
+    DS_CAPACITY = 3,     // output too small
     DS_FORMAT = 4,       // invalid stream on decode
     DS_LENGTH = 5,       // a code length above 63
     DS_TIMEOUT = 6,      // a bounded device-side wait gave up

@@ -78,7 +78,15 @@ __device__ __forceinline__ long long plane_base_of(const LevelGeom<T> &g, int p0
     return g.Nprev + (long long)p0 * m1 * m2 - (long long)kept_before(p0) * mc1 * mc2;
 }
 
-// quantize one coefficient into the symbol stream (+ block histogram / outliers)
+// an escaped code (symbol 0) keeps its k at its stream position; the encoder
+// writes it into the bitstream after the escape's codeword
+__device__ __forceinline__ void escape_store(const QuantOut &qo, long long si, long long k)
+{
+    if (k >= kEscMax || k <= -kEscMax) atomicExch(&qo.sc->status, (unsigned int)DS_ARG);
+    qo.esc[si] = k;
+}
+
+// quantize one coefficient into the symbol stream (+ block histogram / escapes)
 template <typename T>
 __device__ __forceinline__ void quant_emit(const QuantOut &qo, unsigned int *hs, bool smem_hist,
                                            long long si, T w, T rho)
@@ -90,45 +98,18 @@ __device__ __forceinline__ void quant_emit(const QuantOut &qo, unsigned int *hs,
         sym = (unsigned int)s;
     } else {
         sym = 0;
-        unsigned long long pos = atomicAdd(&qo.sc->n_out, 1ULL);
-        if (pos < qo.out_cap) {
-            qo.out_idx[pos] = (unsigned long long)si;
-            qo.out_k[pos] = k;
-        } else {
-            atomicExch(&qo.sc->status, (unsigned int)DS_CAPACITY);
-        }
+        escape_store(qo, si, k);
     }
     qo.sym[si] = (uint16_t)sym;
     if (smem_hist) atomicAdd(&hs[sym], 1u);
     else atomicAdd(&qo.hist[sym], 1ULL);
 }
 
-// k of an escaped symbol: outliers are sorted by stream index; ochunk[c] is
-// the first outlier of chunk c (stream indices [c*K, (c+1)*K)).
-__device__ __noinline__ long long outlier_code(const unsigned long long *out_idx, const long long *out_k,
-                                               unsigned long long n_out, const unsigned long long *ochunk,
-                                               unsigned K, unsigned *status, long long idx)
-{
-    unsigned long long lo = 0, hi = n_out;
-    if (ochunk) {
-        unsigned long long c = (unsigned long long)idx / K;
-        lo = ochunk[c];
-        hi = ochunk[c + 1];
-    }
-    while (lo < hi) {
-        unsigned long long mid = (lo + hi) >> 1;
-        if (out_idx[mid] < (unsigned long long)idx) lo = mid + 1; else hi = mid;
-    }
-    if (lo < n_out && out_idx[lo] == (unsigned long long)idx) return out_k[lo];
-    atomicExch(status, (unsigned int)DS_FORMAT);
-    return 0;
-}
-
 template <typename T>
 __device__ __forceinline__ T dequant_sym(const SymIn &si_, unsigned s, long long idx, T q)
 {
     if (s != 0) return mul_rn((T)((int)s - (int)(si_.D / 2)), q);
-    return mul_rn((T)outlier_code(si_.out_idx, si_.out_k, si_.n_out, si_.ochunk, si_.K, si_.status, idx), q);
+    return mul_rn((T)si_.esc[idx], q);
 }
 
 template <typename T>
@@ -517,7 +498,8 @@ restrict_kernel(RestrictArgs<T> a, int seg_len)
 
 constexpr int OWN1 = 2 * TT1, OWN2 = 2 * TT2;   // owned fine region of a tile
 constexpr int JPITCH = OWN2 + 4;
-constexpr int kHistWin = 2048;                  // shared-memory histogram: D/2 +- kHistWin
+constexpr int kHistWin = 4096;                  // shared-memory histogram: D/2 +- kHistWin,
+                                                // plus one slot for the escape symbol 0
 
 template <typename T>
 struct PlaneTaps2 {
@@ -537,17 +519,12 @@ __device__ __forceinline__ void quant_emit_w(const QuantOut &qo, unsigned int *h
         sym = (unsigned int)s;
     } else {
         sym = 0;
-        unsigned long long pos = atomicAdd(&qo.sc->n_out, 1ULL);
-        if (pos < qo.out_cap) {
-            qo.out_idx[pos] = (unsigned long long)si;
-            qo.out_k[pos] = k;
-        } else {
-            atomicExch(&qo.sc->status, (unsigned int)DS_CAPACITY);
-        }
+        escape_store(qo, si, k);
     }
     qo.sym[si] = (uint16_t)sym;
     const unsigned rel = sym - (unsigned)hlo;
     if (rel < (unsigned)hn) atomicAdd(&hs[rel], 1u);
+    else if (sym == 0) atomicAdd(&hs[hn], 1u);
     else atomicAdd(&qo.hist[sym], 1ULL);
 }
 
@@ -592,7 +569,7 @@ decomp_level_kernel(RestrictArgs<T> a, int seg_len)
     const int hlo = (int)(a.qo.D / 2) - hhalf, hn = 2 * hhalf;
     for (int i = tid; i < r2n; i += RTHREADS) { wl2s[i] = a.g.dim[2].wl[lo2 + i]; wr2s[i] = a.g.dim[2].wr[lo2 + i]; }
     for (int i = tid; i < r1n; i += RTHREADS) { wl1s[i] = a.g.dim[1].wl[lo1 + i]; wr1s[i] = a.g.dim[1].wr[lo1 + i]; }
-    for (int i = tid; i < hn; i += RTHREADS) hs[i] = 0u;
+    if (hn) for (int i = tid; i <= hn; i += RTHREADS) hs[i] = 0u;
     if (tid == 0) {
         for (int i = 0; i < NST; i++) mbar_init(&mbar[i], 1);
         mbar_fence_init();
@@ -633,8 +610,17 @@ decomp_level_kernel(RestrictArgs<T> a, int seg_len)
     const bool rowv = p1 < o1b;
     const int i1 = p1 - lo1;
     const bool f1 = rowv && !kept_pos(m1, p1);
+    // the four owned columns: valid ones and new ones (bit e = column p2b + e)
+    const int p2b = o2a + q4, i2b = p2b - lo2;
+    unsigned vmask = 0, nmask = 0;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        if (p2b + e < o2b) vmask |= 1u << e;
+        if (!kept_pos(m2, p2b + e)) nmask |= 1u << e;
+    }
     T rho = (T)0;
     if (SINK == (int)Sink::QUANT) rho = rho_of<T>(a.qo.sc, a.g.level);
+    const T halfD = (T)(a.qo.D / 2);
     __syncthreads();
 
     auto issue = [&](int p) {
@@ -742,26 +728,41 @@ decomp_level_kernel(RestrictArgs<T> a, int seg_len)
             const T *Jm = Jb + (cidx_of(m0, mc0, f0 ? p0 - 1 : p0) & 1) * OWN1 * JPITCH + rr * JPITCH + q4;
             const T *Jp = Jb + (cidx_of(m0, mc0, f0 ? p0 + 1 : p0) & 1) * OWN1 * JPITCH + rr * JPITCH + q4;
             const T wl0 = f0 ? a.g.dim[0].wl[p0] : (T)0, wr0 = f0 ? a.g.dim[0].wr[p0] : (T)0;
-            const T *vr = Vrow(s0, i1);
+            const T *vr = Vrow(s0, i1) + i2b;
             const bool rownew = f0 || f1;
+            const unsigned emask = vmask & (rownew ? 0xFu : nmask);   // nodes with a coefficient
             const long long rb = row_base(a.g, plane_base_of(a.g, p0), !f0, p1);
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-                const int p2 = o2a + q4 + e;
-                if (p2 >= o2b) break;
-                const int i2 = p2 - lo2;
-                const bool f2 = !kept_pos(m2, p2);
-                if (rownew || f2) {
+                if (!((vmask >> e) & 1u)) continue;
+                const T v = vr[e];
+                if ((emask >> e) & 1u) {
                     const T lerp = f0 ? fma_rn(wr0, Jp[e], mul_rn(wl0, Jm[e])) : Jm[e];
-                    const T w = sub_rn(vr[i2], lerp);
+                    const T w = sub_rn(v, lerp);
                     if (SINK != (int)Sink::NONE) {
+                        const int p2 = p2b + e;
                         const long long si = rb + (rownew ? p2 : (p2 - 1) >> 1);
-                        if (SINK == (int)Sink::STREAM) a.coef_out[si] = w;
-                        else quant_emit_w(a.qo, hs, hlo, hn, si, w, rho);
+                        if (SINK == (int)Sink::STREAM) {
+                            a.coef_out[si] = w;
+                        } else {
+                            // k = sign(w) floor(|w| rho + 1/2), every operation rounded in T;
+                            // symbols D/2 + k for |k| < D/2, escapes otherwise
+                            const T kf = floor(add_rn(mul_rn(w < (T)0 ? -w : w, rho), (T)0.5));
+                            if (kf < halfD) {
+                                const int ki = (int)kf;
+                                const unsigned sym = (unsigned)((int)(a.qo.D / 2) + (w < (T)0 ? -ki : ki));
+                                a.qo.sym[si] = (uint16_t)sym;
+                                const unsigned rel = sym - (unsigned)hlo;
+                                if (rel < (unsigned)hn) atomicAdd(&hs[rel], 1u);
+                                else atomicAdd(&a.qo.hist[sym], 1ULL);
+                            } else {
+                                quant_emit_w(a.qo, hs, hlo, hn, si, w, rho);
+                            }
+                        }
                     }
                 } else if (a.vc) {
                     a.vc[(long long)cidx_of(m0, mc0, p0) * cstride +
-                         (long long)cidx_of(m1, mc1, p1) * mc2 + cidx_of(m2, mc2, p2)] = vr[i2];
+                         (long long)cidx_of(m1, mc1, p1) * mc2 + cidx_of(m2, mc2, p2b + e)] = v;
                 }
             }
         }
@@ -821,6 +822,7 @@ decomp_level_kernel(RestrictArgs<T> a, int seg_len)
         __syncthreads();
         for (int i = tid; i < hn; i += RTHREADS)
             if (hs[i]) atomicAdd(&a.qo.hist[hlo + i], (unsigned long long)hs[i]);
+        if (tid == 0 && hs[hn]) atomicAdd(&a.qo.hist[0], (unsigned long long)hs[hn]);
     }
 }
 
@@ -831,7 +833,7 @@ size_t decomp_smem(Sink sink, unsigned int D)
     b += NST * sizeof(PlaneTaps2<T>);
     b = (b + 15) & ~size_t(15);
     b += (2 * OWN1 * JPITCH + 2 * RR1 * TT2 + 2 * (RR1 + RR2)) * sizeof(T) + 16;
-    if (sink == Sink::QUANT) b += (size_t)2 * std::min<unsigned>(D / 2, kHistWin) * sizeof(unsigned int);
+    if (sink == Sink::QUANT) b += ((size_t)2 * std::min<unsigned>(D / 2, kHistWin) + 1) * sizeof(unsigned int);
     return b;
 }
 
@@ -1182,6 +1184,10 @@ __global__ void bins_kernel(BinArgs ba, const double *partials, int nparts, Scal
     if (!ok) atomicExch(&sc->status, (unsigned int)DS_ARG);
 }
 
+}  // namespace
+
+int norm_parts() { return kNormBlocks; }
+
 template <typename T, int SRC, int SINK>
 cudaError_t launch_restrict_t(const RestrictArgs<T> &a, cudaStream_t s)
 {
@@ -1208,34 +1214,6 @@ cudaError_t launch_restrict_t(const RestrictArgs<T> &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-__global__ void outlier_chunks_kernel(const unsigned long long *out_idx, unsigned long long n_out,
-                                      unsigned K, unsigned long long nch, unsigned long long *ochunk)
-{
-    for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c <= nch;
-         c += (unsigned long long)gridDim.x * blockDim.x) {
-        const unsigned long long key = c * K;
-        unsigned long long lo = 0, hi = n_out;
-        while (lo < hi) {
-            unsigned long long mid = (lo + hi) >> 1;
-            if (out_idx[mid] < key) lo = mid + 1; else hi = mid;
-        }
-        ochunk[c] = lo;
-    }
-}
-
-}  // namespace
-
-int norm_parts() { return kNormBlocks; }
-
-cudaError_t launch_outlier_chunks(const unsigned long long *out_idx, unsigned long long n_out,
-                                  unsigned K, unsigned long long nch, unsigned long long *ochunk,
-                                  cudaStream_t s)
-{
-    outlier_chunks_kernel<<<(unsigned)std::min<unsigned long long>(1024, (nch + 256) / 256), 256, 0, s>>>(
-        out_idx, n_out, K, nch, ochunk);
-    count_launch();
-    return cudaGetLastError();
-}
 
 template <typename T>
 cudaError_t launch_restrict(WSrc src, Sink sink, const RestrictArgs<T> &a, cudaStream_t s)

@@ -17,9 +17,7 @@ enum class Sink : int { NONE = 0, STREAM = 1, QUANT = 2 };
 struct QuantOut {
     uint16_t *sym;                 // stream of symbols
     unsigned long long *hist;      // global histogram [D]
-    unsigned long long *out_idx;   // unordered outlier list
-    long long *out_k;
-    unsigned long long out_cap;
+    long long *esc;                // [N] code k at every escaped stream position (symbol 0)
     unsigned int D;
     Scalars *sc;
 };
@@ -28,12 +26,8 @@ struct SymIn {
     const uint16_t *sym;
     unsigned int D;
     const Scalars *sc;               // q per level
-    const unsigned long long *out_idx;  // sorted by stream index
-    const long long *out_k;
-    unsigned long long n_out;
+    const long long *esc;            // [N] code k at every escaped stream position
     unsigned int *status;
-    const unsigned long long *ochunk;   // first outlier of every chunk of K stream entries, or null
-    unsigned int K;
 };
 
 template <typename T>
@@ -106,9 +100,5 @@ cudaError_t recompose_adjoint_run(const Plan &P, const LevelGeom<T> *geo, const 
 template <typename T>
 cudaError_t decompose_adjoint_run(const Plan &P, const LevelGeom<T> *geo, const T *gcoef, T *gu, T *ga, T *gb,
                                   T *y, T *t1, T *t2, T *R, unsigned *status, cudaStream_t s);
-// ochunk[c] = first outlier with stream index >= c*K, c = 0..nch
-cudaError_t launch_outlier_chunks(const unsigned long long *out_idx, unsigned long long n_out,
-                                  unsigned K, unsigned long long nch, unsigned long long *ochunk,
-                                  cudaStream_t s);
 
 }  // namespace hpdr

@@ -79,13 +79,13 @@ def test_513_codes_and_huffman_bit_exact(oracle, H, big):
     u, ud = big
     buf = H.hpdr_compress(u, 1e-3).cpu().numpy()
     h = _parse(oracle, buf)
-    sym = oracle.decode(h["words"], h["chunk"], h["N"], h["K"], h["lengths"])
+    sym, esc = oracle.decode(h["words"], h["chunk"], h["N"], h["K"], h["lengths"], escapes=True)
     coef = H.hpdr_decompose(u).cpu().numpy().astype(np.float64)
     ref_sym, ref_idx, ref_k = oracle.quantize(coef, BIG, h["q"], D=h["D"], precision=32)
     assert np.array_equal(sym, ref_sym)
-    assert np.array_equal(h["out_idx"], ref_idx) and np.array_equal(h["out_k"], ref_k)
+    assert np.array_equal(np.flatnonzero(sym == 0), ref_idx) and np.array_equal(esc, ref_k)
     ln = oracle.code_lengths(oracle.histogram(ref_sym, h["D"]))
-    words, chunk, bits = oracle.encode(ref_sym, ln, K=h["K"])
+    words, chunk, bits = oracle.encode(ref_sym, ln, K=h["K"], esc_k=ref_k)
     assert np.array_equal(h["lengths"], ln)
     assert h["total_bits"] == bits and np.array_equal(h["chunk"], chunk)
     assert np.array_equal(h["words"], words)

@@ -65,8 +65,8 @@ def test_recompose_parity_and_identity(oracle, H, dev, shape, dtype):
 
 def _decode_container_symbols(oracle, buf):
     h = oracle.parse_header(buf)
-    sym = oracle.decode(h["words"], h["chunk"], h["N"], h["K"], h["lengths"])
-    return h, sym
+    sym, esc = oracle.decode(h["words"], h["chunk"], h["N"], h["K"], h["lengths"], escapes=True)
+    return h, sym, esc
 
 
 @pytest.mark.parametrize("shape,tol,D", [((129, 129), 1e-3, 8192), ((33, 17, 9), 1e-2, 8192),
@@ -78,13 +78,13 @@ def test_codes_bit_exact_on_identical_inputs(oracle, H, dev, shape, tol, D, dtyp
     u = _field(shape, 3, dtype)
     ut = torch.from_numpy(u).to(dev)
     buf = H.hpdr_compress(ut, tol, dict_size=D).cpu().numpy()
-    h, sym = _decode_container_symbols(oracle, buf)
+    h, sym, esc = _decode_container_symbols(oracle, buf)
     coef = H.hpdr_decompose(ut).cpu().numpy().astype(np.float64)
     prec = 32 if dtype == np.float32 else 64
     ref_sym, ref_idx, ref_k = oracle.quantize(coef, shape, h["q"], D=D, precision=prec)
     assert np.array_equal(sym, ref_sym)
-    assert np.array_equal(h["out_idx"], ref_idx)
-    assert np.array_equal(h["out_k"], ref_k)
+    assert np.array_equal(np.flatnonzero(sym == 0), ref_idx)
+    assert np.array_equal(esc, ref_k) and h["n_escapes"] == ref_k.size
     # bins: same definition computed independently (correction norms differ only by rounding)
     eps = 2.0 ** -24 if dtype == np.float32 else 2.0 ** -53
     q_ref = oracle.bins(shape, tol * np.abs(u.astype(np.float64)).max(),
@@ -92,7 +92,7 @@ def test_codes_bit_exact_on_identical_inputs(oracle, H, dev, shape, tol, D, dtyp
     assert np.allclose(h["q"], q_ref, rtol=1e-12, atol=0)
     # the whole Huffman part of the container equals the oracle's encoding of these codes
     ln = oracle.code_lengths(oracle.histogram(ref_sym, D))
-    words, chunk, bits = oracle.encode(ref_sym, ln, K=h["K"])
+    words, chunk, bits = oracle.encode(ref_sym, ln, K=h["K"], esc_k=ref_k)
     assert np.array_equal(h["lengths"], ln)
     assert np.array_equal(h["chunk"], chunk) and h["total_bits"] == bits
     assert np.array_equal(h["words"], words)
@@ -113,6 +113,31 @@ def test_huffman_bit_exact(oracle, H, dev, n, D, K, spread):
     assert np.array_equal(chunk.cpu().numpy().view(np.uint64), chunk_ref)
     assert np.array_equal(words.cpu().numpy().view(np.uint32), words_ref)
     # GPU decodes the oracle's stream
+    wt = torch.from_numpy(words_ref.view(np.int32).copy()).to(dev)
+    ct = torch.from_numpy(chunk_ref.view(np.int64).copy()).to(dev)
+    lt = torch.from_numpy(ln_ref).to(dev)
+    dec = H.hpdr_huffman_decode(wt, bits_ref, ct, n, lt, D=D, K=K)
+    assert np.array_equal(dec.cpu().numpy().view(np.uint16), sym)
+
+
+@pytest.mark.parametrize("nsym,K", [(20, 1024), (35, 2048)])
+def test_huffman_long_codewords(oracle, H, dev, nsym, K):
+    """Fibonacci frequencies give codewords up to nsym - 1 bits: past the
+    decoder's 15-bit table and, for 35 symbols, past 32 bits."""
+    fib = [1, 1]
+    while len(fib) < nsym:
+        fib.append(fib[-1] + fib[-2])
+    D = 64
+    sym = np.repeat(np.arange(1, nsym + 1, dtype=np.uint16), fib)
+    sym = sym[np.random.default_rng(nsym).permutation(sym.size)]
+    n = sym.size
+    ln_ref = oracle.code_lengths(oracle.histogram(sym, D))
+    assert ln_ref.max() == nsym - 1
+    words_ref, chunk_ref, bits_ref = oracle.encode(sym, ln_ref, K=K)
+    st = torch.from_numpy(sym.view(np.int16)).to(dev)
+    ln, chunk, words, bits = H.hpdr_huffman_encode(st, D=D, K=K)
+    assert np.array_equal(ln.cpu().numpy(), ln_ref) and bits == bits_ref
+    assert np.array_equal(words.cpu().numpy().view(np.uint32), words_ref)
     wt = torch.from_numpy(words_ref.view(np.int32).copy()).to(dev)
     ct = torch.from_numpy(chunk_ref.view(np.int64).copy()).to(dev)
     lt = torch.from_numpy(ln_ref).to(dev)
