@@ -80,9 +80,9 @@ hpdr_status hpdr_ctx_create(hpdr_ctx **ctx, int device);
 hpdr_status hpdr_ctx_destroy(hpdr_ctx *ctx);
 
 /* Upper bound of the container size for a field, with the given config (NULL
- * = defaults): header, bins, code lengths, chunk table and ceil(log2 D) + 38
+ * = defaults): header, bins, code lengths, chunk table and ceil(log2 D) + 32
  * bits per value (a Huffman code never exceeds the fixed-length code of
- * ceil(log2 D) bits in total; an escape payload takes at most 38 bits while
+ * ceil(log2 D) bits in total; an escape payload takes at most 32 bits while
  * |k| < 2^31).  Only tolerances so small that many codes reach |k| >= 2^31
  * can exceed it; hpdr_compress then returns HPDR_ERR_CAPACITY.  0 on bad
  * arguments. */
@@ -94,11 +94,11 @@ size_t hpdr_compress_bound(int ndim, const size_t *dims, hpdr_dtype dtype, const
  *               tol * rms(u) (L2); ABS: tau = tol.  The reconstruction then
  *               satisfies max|u - u~| <= tau (which also bounds the RMS error).
  *   d_out       device buffer of out_capacity bytes receiving the container
- *               (format v2: 128-byte header, bins, code lengths, chunk table,
+ *               (format v3: 128-byte header, bins, code lengths, chunk table,
  *               bitstream; every section 16-byte aligned).  A code k whose
  *               symbol k + D/2 falls outside [1, D-1] is escaped: symbol 0,
- *               followed in the bitstream by 6 bits holding n - 1 and the n
- *               bits of zigzag(k) (n = its bit length).
+ *               followed in the bitstream by zigzag(k) in W bits, W the
+ *               largest bit length among the container's escapes (header).
  *   out_bytes   host pointer receiving the container size.
  * Errors: HPDR_ERR_ARG (including a bound below the data type's precision
  * floor, tau <= 32 (L+1) eps max|u|, or a code with |k| >= 2^62),
@@ -208,7 +208,7 @@ int hpdr_batched_streams(hpdr_ctx *ctx);
  *   h_out       host buffer of out_capacity bytes receiving the streamed
  *               container: "HPDS" directory (64 bytes + 32 per slab: first
  *               plane, planes, byte offset, bytes) followed by the slab
- *               containers (format v2) at 16-byte boundaries.
+ *               containers (format v3) at 16-byte boundaries.
  *   out_bytes   receives the size.
  * Synchronous.  Errors as hpdr_compress. */
 hpdr_status hpdr_compress_host_streamed(hpdr_ctx *ctx, const void *h_in, hpdr_dtype dtype, int ndim,

@@ -12,7 +12,7 @@ from . import build as _build
 __all__ = [
     "levels", "decompose", "recompose", "recompose_adjoint", "decompose_adjoint",
     "correction_norms", "bins", "quantize", "dequantize", "histogram",
-    "code_lengths", "canonical_codes", "encode", "decode", "compress",
+    "code_lengths", "canonical_codes", "encode", "decode", "escape_width", "compress",
     "decompress", "inspect", "compress_bound", "crc32", "level_sizes",
     "parse_header", "DTYPE_F32", "DTYPE_F64", "LINF", "L2", "ABS", "REL",
 ]
@@ -49,7 +49,8 @@ def _L():
             "oracle_histogram": [u16, C.c_uint64, C.c_uint32, u64],
             "oracle_code_lengths": [u64, C.c_uint32, u8],
             "oracle_canonical_codes": [u8, C.c_uint32, u64],
-            "oracle_encode": [u16, C.c_uint64, u8, u64, C.c_uint32, i64, u32, C.c_uint64, u64, u64],
+            "oracle_encode": [u16, C.c_uint64, u8, u64, C.c_uint32, i64, C.c_int, u32, C.c_uint64, u64,
+                              u64],
             "oracle_decode": [u32, C.c_uint64, u64, C.c_uint64, C.c_uint32, u8, C.c_uint32, u16,
                               C.c_int, i64, C.c_uint64, u64],
             "oracle_escape_bits": [C.c_int64],
@@ -202,18 +203,20 @@ def canonical_codes(lengths):
     return code
 
 
-def encode(sym, lengths, K=1024, esc_k=None):
+def encode(sym, lengths, K=1024, esc_k=None, esc_width=None):
     """Huffman-encode symbols: returns (words uint32, chunk table uint64, total bits).
     esc_k: None for plain symbols; else the integer codes of the escapes (symbol 0)
-    in stream order, written as payloads after their codewords."""
+    in stream order, each written after its codeword as zigzag(k) in esc_width
+    bits (default: the largest bit length among them)."""
     sym = np.ascontiguousarray(sym, dtype=np.uint16)
     lengths = np.ascontiguousarray(lengths, dtype=np.uint8)
     code = canonical_codes(lengths)
     bits = int(lengths[sym].astype(np.uint64).sum())
-    ek = None
+    ek, ew = None, 0
     if esc_k is not None:
         ek = np.ascontiguousarray(esc_k, dtype=np.int64)
-        bits += int(_escape_bits_np(ek).sum())
+        ew = escape_width(ek) if esc_width is None else int(esc_width)
+        bits += int(ek.size) * ew
         if ek.size == 0:
             ek = np.zeros(1, dtype=np.int64)
     nw = (bits + 31) // 32
@@ -223,25 +226,24 @@ def encode(sym, lengths, K=1024, esc_k=None):
     tb = C.c_uint64()
     _check(_L().oracle_encode(_p(sym, C.c_uint16), sym.size, _p(lengths, C.c_uint8),
                               _p(code, C.c_uint64), K, _p(ek, C.c_int64) if ek is not None else None,
-                              _p(words, C.c_uint32), words.size, _p(chunk, C.c_uint64),
+                              ew, _p(words, C.c_uint32), words.size, _p(chunk, C.c_uint64),
                               C.byref(tb)), "encode")
     return words[:nw], chunk[:nch], tb.value
 
 
-def _escape_bits_np(k):
-    """6 + bit length of zigzag(k), vectorised (|k| < 2^62)."""
-    k = k.astype(np.int64)
+def escape_width(esc_k):
+    """Largest bit length of zigzag(k) over the escapes (|k| < 2^62); 0 if none."""
+    k = np.asarray(esc_k, dtype=np.int64)
+    if k.size == 0:
+        return 0
     z = np.where(k >= 0, 2 * k.astype(np.uint64), 2 * (-(k + 1)).astype(np.uint64) + 1)
-    n = np.zeros(z.shape, dtype=np.int64)
-    while np.any(z):
-        n += (z != 0)
-        z = z >> np.uint64(1)
-    return 6 + n
+    return int(max(int(x).bit_length() for x in (z.max(),)))
 
 
-def decode(words, chunk, N, K, lengths, escapes=False):
-    """Decode N symbols; with escapes=True also returns the escapes' codes
-    (stream order)."""
+def decode(words, chunk, N, K, lengths, esc_width=None):
+    """Decode N symbols.  With esc_width given (a container stream, symbol 0
+    the quantizer's escape) also returns the escapes' codes in stream order,
+    each read as zigzag(k) in esc_width bits (0: the stream has no escapes)."""
     words = np.ascontiguousarray(words, dtype=np.uint32)
     chunk = np.ascontiguousarray(chunk, dtype=np.uint64)
     lengths = np.ascontiguousarray(lengths, dtype=np.uint8)
@@ -251,9 +253,9 @@ def decode(words, chunk, N, K, lengths, escapes=False):
     w = words if words.size else np.zeros(1, dtype=np.uint32)
     _check(_L().oracle_decode(_p(w, C.c_uint32), words.size, _p(chunk, C.c_uint64), N, K,
                               _p(lengths, C.c_uint8), lengths.size, _p(sym, C.c_uint16),
-                              1 if escapes else 0, _p(ek, C.c_int64), ek.size, C.byref(ne)),
+                              int(esc_width or 0), _p(ek, C.c_int64), ek.size, C.byref(ne)),
            "decode")
-    if escapes:
+    if esc_width is not None:
         return sym, ek[:ne.value].copy()
     return sym
 
@@ -313,7 +315,8 @@ def parse_header(buf):
              dims=tuple(u64(16 + 8 * k) for k in range(u32(12))), L=u32(40), mode=u32(44),
              tol_kind=u32(48), D=u32(52), K=u32(56), s_lo=u32(60), tol=f64(64),
              tau_abs=f64(72), norm_inf=f64(80), norm_rms=f64(88), N=u64(96),
-             n_escapes=u64(104), total_bits=u64(112), s_hi=u32(120), crc=u32(124))
+             n_escapes=u64(104), total_bits=u64(112), s_hi=u32(120) & 0xFFFF,
+             esc_width=(u32(120) >> 16) & 0xFF, crc=u32(124))
     a16 = lambda x: (x + 15) & ~15  # noqa: E731
     L = h["L"]
     off_q = 128

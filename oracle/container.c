@@ -1,18 +1,19 @@
 /*
  * container.c -- oracle of the whole reduction path (Alg. 1 followed by
  * Alg. 2) and of its inverse, written into / read from the self-describing
- * container, format version 2.  TEST INFRASTRUCTURE ONLY (see
+ * container, format version 3.  TEST INFRASTRUCTURE ONLY (see
  * hpdr_oracle.h).
  *
- * Container v2 (little endian; every section starts on a 16-byte boundary;
+ * Container v3 (little endian; every section starts on a 16-byte boundary;
  * padding bytes are zero):
- *   0   "HPDR"            4  u32 version (2)     8  u32 dtype (0 f32, 1 f64)
+ *   0   "HPDR"            4  u32 version (3)     8  u32 dtype (0 f32, 1 f64)
  *   12  u32 ndim          16 u64 dims[3] (unused dims hold 1)
  *   40  u32 L             44 u32 mode (0 Linf, 1 L2)   48 u32 tol kind (0 abs, 1 rel)
  *   52  u32 D             56 u32 K               60 u32 s_lo
  *   64  f64 tol           72 f64 tau_abs         80 f64 max|u|    88 f64 rms(u)
  *   96  u64 N             104 u64 escapes        112 u64 bitstream bits
- *   120 u32 s_hi          124 u32 CRC-32 of bytes [0,124)
+ *   120 u16 s_hi          122 u8 escape width W   123 u8 0
+ *   124 u32 CRC-32 of bytes [0,124)
  *   128 f64 q[L+1]
  *   code lengths  u8[s_hi - s_lo + 1]  (symbols s_lo..s_hi)
  *   chunk table   u64[ceil(N/K)]       (bit offset of symbol j*K)
@@ -20,8 +21,8 @@
  *
  * Symbol s = k + D/2 carries the quantized code k when 1 <= s <= D-1; every
  * other code is escaped: symbol 0, whose codeword is followed in the
- * bitstream by 6 bits holding n - 1 and the n bits of zigzag(k) (see
- * oracle_encode).
+ * bitstream by zigzag(k) in W bits, W the largest bit length of the
+ * container's escapes (0 without escapes; see oracle_encode).
  *
  * Tolerance: REL means tol times max|u| (Linf mode) or times rms(u) (L2
  * mode); ABS means tol itself.  L2 mode uses the same bins, which bound the
@@ -63,10 +64,10 @@ uint64_t oracle_compress_bound(int d, const size_t *n, uint32_t D, uint32_t K)
     b = align16(b + D);
     b = align16(b + 8 * ((N + K - 1) / K));
     /* Huffman bits <= N ceil(log2 D) (a fixed-length code is a prefix code);
-     * escape payloads <= 38 bits each while |k| < 2^31 */
+     * escape payloads <= 32 bits each while |k| < 2^31 */
     uint64_t lg = 0;
     while ((1ULL << lg) < D) lg++;
-    b += 4 * ((N * (lg + 38) + 31) / 32);
+    b += 4 * ((N * (lg + 32) + 31) / 32);
     return b;
 }
 
@@ -118,11 +119,13 @@ int oracle_compress(int d, const size_t *n, const double *u, int dtype, double t
     uint64_t off_bits = align16(off_chunk + 8 * nch);
     uint64_t bits = 0;
     for (uint64_t i = 0; i < N && rc == 0; i++) bits += len[sym[i]];
+    int ew = 0;
     for (uint64_t j = 0; j < nout && rc == 0; j++) {
         int eb = oracle_escape_bits(ok[j]);
         if (eb < 0) rc = -1;
-        else bits += (uint64_t)eb;
+        else if (eb > ew) ew = eb;
     }
+    bits += nout * (uint64_t)ew;
     uint64_t nwords = (bits + 31) / 32;
     uint64_t total = off_bits + 4 * nwords;
     if (rc == 0 && total > cap) rc = -3;
@@ -131,10 +134,10 @@ int oracle_compress(int d, const size_t *n, const double *u, int dtype, double t
         uint64_t *chunk = (uint64_t *)malloc(nch * sizeof(uint64_t));
         uint32_t *words = (uint32_t *)malloc((nwords + 1) * sizeof(uint32_t));
         uint64_t tb = 0;
-        rc = oracle_encode(sym, N, len, code, K, ok, words, nwords + 1, chunk, &tb);
+        rc = oracle_encode(sym, N, len, code, K, nout ? ok : NULL, ew, words, nwords + 1, chunk, &tb);
         if (rc == 0 && tb != bits) rc = -1;
         memcpy(out, "HPDR", 4);
-        put32(out + 4, 2);
+        put32(out + 4, 3);
         put32(out + 8, (uint32_t)dtype);
         put32(out + 12, (uint32_t)d);
         for (int k = 0; k < 3; k++) put64(out + 16 + 8 * k, (k < d) ? (uint64_t)n[k] : 1);
@@ -151,7 +154,7 @@ int oracle_compress(int d, const size_t *n, const double *u, int dtype, double t
         put64(out + 96, N);
         put64(out + 104, nout);
         put64(out + 112, bits);
-        put32(out + 120, shi);
+        put32(out + 120, shi | ((uint32_t)ew << 16));
         put32(out + 124, oracle_crc32(out, 124));
         for (int l = 0; l <= L; l++) putf64(out + off_q + 8 * l, q[l]);
         for (uint32_t s = slo; s <= shi; s++) out[off_len + (s - slo)] = len[s];
@@ -167,14 +170,14 @@ int oracle_compress(int d, const size_t *n, const double *u, int dtype, double t
 typedef struct {
     int dtype, d, L, mode, tol_kind;
     size_t n[3];
-    uint32_t D, K, slo, shi;
+    uint32_t D, K, slo, shi, ew;
     uint64_t N, nout, bits, nch, nwords;
     uint64_t off_q, off_len, off_chunk, off_bits, total;
 } hdr_t;
 
 static int parse(const uint8_t *in, uint64_t in_bytes, hdr_t *h)
 {
-    if (in_bytes < HDR || memcmp(in, "HPDR", 4) != 0 || get32(in + 4) != 2) return -4;
+    if (in_bytes < HDR || memcmp(in, "HPDR", 4) != 0 || get32(in + 4) != 3) return -4;
     if (oracle_crc32(in, 124) != get32(in + 124)) return -4;
     h->dtype = (int)get32(in + 8);
     h->d = (int)get32(in + 12);
@@ -189,14 +192,16 @@ static int parse(const uint8_t *in, uint64_t in_bytes, hdr_t *h)
     h->N = get64(in + 96);
     h->nout = get64(in + 104);
     h->bits = get64(in + 112);
-    h->shi = get32(in + 120);
+    h->shi = get32(in + 120) & 0xFFFFu;
+    h->ew = (get32(in + 120) >> 16) & 0xFFu;
+    if (get32(in + 120) >> 24) return -4;
     int L;
     if (oracle_levels(h->d, h->n, &L, NULL) || L != h->L) return -4;
     uint64_t N = 1;
     for (int k = 0; k < h->d; k++) N *= h->n[k];
     if (N != h->N || h->K == 0 || h->D < 4 || h->D > 65536 || h->shi >= h->D || h->slo > h->shi)
         return -4;
-    if (h->nout > N) return -4;
+    if (h->nout > N || h->ew > 63 || (h->nout && h->ew == 0)) return -4;
     h->nch = (N + h->K - 1) / h->K;
     h->nwords = (h->bits + 31) / 32;
     h->off_q = HDR;
@@ -238,7 +243,7 @@ int oracle_decompress(const uint8_t *in, uint64_t in_bytes, double *u, uint64_t 
     uint16_t *sym = (uint16_t *)malloc(h.N * sizeof(uint16_t));
     double *coef = (double *)malloc(h.N * sizeof(double));
     uint64_t ne = 0;
-    rc = oracle_decode(words, h.nwords, chunk, h.N, h.K, len, h.D, sym, 1, ok, h.nout, &ne);
+    rc = oracle_decode(words, h.nwords, chunk, h.N, h.K, len, h.D, sym, (int)h.ew, ok, h.nout, &ne);
     if (rc == 0 && ne != h.nout) rc = -4;
     for (uint64_t i = 0, j = 0; rc == 0 && i < h.N; i++)
         if (sym[i] == 0) oidx[j++] = i;

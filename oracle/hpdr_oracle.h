@@ -62,20 +62,23 @@ int oracle_canonical_codes(const uint8_t *len, uint32_t D, uint64_t *code);
  * (bit offset of every K-th symbol).  words must hold ceil(bits/32) words.
  * esc_k: NULL for plain symbols; otherwise symbol 0 is the escape of the
  * quantizer and esc_k holds, in stream order, the integer code of every
- * escape.  Each escape's codeword is followed by its payload: 6 bits holding
- * n - 1, then the n bits of zigzag(k) (n = bit length, 1..63; |k| < 2^62). */
+ * escape.  Each escape's codeword is followed by its payload: zigzag(k)
+ * (k >= 0 -> 2k, k < 0 -> -2k - 1) in esc_width bits (0..63; 0 only for a
+ * stream without escapes), which must hold the bit length of every escape's
+ * zigzag(k) (|k| < 2^62). */
 int oracle_encode(const uint16_t *symbols, uint64_t N, const uint8_t *len, const uint64_t *code,
-                  uint32_t K, const int64_t *esc_k, uint32_t *words, uint64_t nwords_cap,
+                  uint32_t K, const int64_t *esc_k, int esc_width, uint32_t *words, uint64_t nwords_cap,
                   uint64_t *chunk_bits, uint64_t *total_bits);
-/* Payload bits of one escape (6 + n), or -1 when k = 0 or |k| >= 2^62. */
+/* Bit length of zigzag(k) of one escape, or -1 when k = 0 or |k| >= 2^62. */
 int oracle_escape_bits(int64_t k);
-/* Decode; with escapes != 0 the payload of every escape is read and its code
- * stored into esc_k (stream order, capacity esc_cap), their count in *n_esc. */
+/* Decode; with esc_width > 0 every escape's payload of esc_width bits is read
+ * and its code stored into esc_k (stream order, capacity esc_cap), their
+ * count in *n_esc. */
 int oracle_decode(const uint32_t *words, uint64_t nwords, const uint64_t *chunk_bits, uint64_t N,
-                  uint32_t K, const uint8_t *len, uint32_t D, uint16_t *symbols, int escapes,
+                  uint32_t K, const uint8_t *len, uint32_t D, uint16_t *symbols, int esc_width,
                   int64_t *esc_k, uint64_t esc_cap, uint64_t *n_esc);
 
-/* Full container (format v2).  dtype: 0 = binary32 data, 1 = binary64 data
+/* Full container (format v3).  dtype: 0 = binary32 data, 1 = binary64 data
  * (u is always passed as FP64 values).  mode: 0 = L-infinity, 1 = L2 (RMS).
  * tol_kind: 0 = absolute, 1 = relative. */
 int oracle_compress(int d, const size_t *n, const double *u, int dtype, double tol, int tol_kind,

@@ -105,7 +105,7 @@ static int bitlen(uint64_t z) { int n = 0; while (z) { n++; z >>= 1; } return n;
 int oracle_escape_bits(int64_t k)
 {
     if (k == 0 || k >= ((int64_t)1 << 62) || k <= -((int64_t)1 << 62)) return -1;
-    return 6 + bitlen(zigzag(k));
+    return bitlen(zigzag(k));
 }
 
 static void put_bits(uint32_t *words, uint64_t *pos, uint64_t v, int nbits)
@@ -117,18 +117,18 @@ static void put_bits(uint32_t *words, uint64_t *pos, uint64_t v, int nbits)
 }
 
 int oracle_encode(const uint16_t *symbols, uint64_t N, const uint8_t *len, const uint64_t *code,
-                  uint32_t K, const int64_t *esc_k, uint32_t *words, uint64_t nwords_cap,
+                  uint32_t K, const int64_t *esc_k, int esc_width, uint32_t *words, uint64_t nwords_cap,
                   uint64_t *chunk_bits, uint64_t *total_bits)
 {
-    if (K == 0) return -1;
+    if (K == 0 || esc_width < 0 || esc_width > 63) return -1;
     uint64_t bits = 0, e = 0;
     for (uint64_t i = 0; i < N; i++) {
         if (len[symbols[i]] == 0) return -1;
         bits += len[symbols[i]];
         if (esc_k && symbols[i] == 0) {
             int eb = oracle_escape_bits(esc_k[e++]);
-            if (eb < 0) return -1;
-            bits += (uint64_t)eb;
+            if (eb < 0 || eb > esc_width) return -1;
+            bits += (uint64_t)esc_width;
         }
     }
     uint64_t nwords = (bits + 31) / 32;
@@ -140,12 +140,7 @@ int oracle_encode(const uint16_t *symbols, uint64_t N, const uint8_t *len, const
     for (uint64_t i = 0; i < N; i++) {
         if (i % K == 0) chunk_bits[i / K] = pos;
         put_bits(words, &pos, code[symbols[i]], len[symbols[i]]);
-        if (esc_k && symbols[i] == 0) {
-            uint64_t z = zigzag(esc_k[e++]);
-            int nb = bitlen(z);
-            put_bits(words, &pos, (uint64_t)(nb - 1), 6);
-            put_bits(words, &pos, z, nb);
-        }
+        if (esc_k && symbols[i] == 0) put_bits(words, &pos, zigzag(esc_k[e++]), esc_width);
     }
     return 0;
 }
@@ -162,9 +157,10 @@ static int get_bits(const uint32_t *words, uint64_t nwords, uint64_t *pos, int n
 }
 
 int oracle_decode(const uint32_t *words, uint64_t nwords, const uint64_t *chunk_bits, uint64_t N,
-                  uint32_t K, const uint8_t *len, uint32_t D, uint16_t *symbols, int escapes,
+                  uint32_t K, const uint8_t *len, uint32_t D, uint16_t *symbols, int esc_width,
                   int64_t *esc_k, uint64_t esc_cap, uint64_t *n_esc)
 {
+    if (esc_width < 0 || esc_width > 63) return -4;
     uint64_t ne = 0;
     uint64_t count[OMAXLEN + 2] = {0}, first[OMAXLEN + 2] = {0}, findex[OMAXLEN + 2] = {0};
     uint32_t *sorted = (uint32_t *)malloc((size_t)D * sizeof(uint32_t));
@@ -204,10 +200,9 @@ int oracle_decode(const uint32_t *words, uint64_t nwords, const uint64_t *chunk_
                     found = 1;
                 }
             }
-            if (escapes && symbols[i] == 0) {
-                uint64_t nb, z;
-                if (get_bits(words, nwords, &pos, 6, &nb) ||
-                    get_bits(words, nwords, &pos, (int)nb + 1, &z) || ne >= esc_cap) {
+            if (esc_width && symbols[i] == 0) {
+                uint64_t z;
+                if (get_bits(words, nwords, &pos, esc_width, &z) || ne >= esc_cap) {
                     free(sorted);
                     return -4;
                 }

@@ -235,7 +235,7 @@ hpdr_status compress_t(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, const
 struct Hdr {
     int dtype, ndim, L, mode, tol_kind;
     size_t dims[3];
-    unsigned D, K, s_lo, s_hi;
+    unsigned D, K, s_lo, s_hi, esc_w;
     unsigned long long N, n_esc, bits, nch, nwords;
     unsigned long long off_len, off_chunk, off_bits, total;
     double q[kMaxLevels + 1];
@@ -256,7 +256,7 @@ uint64_t rd64(const uint8_t *p) { uint64_t v = 0; for (int i = 0; i < 8; i++) v 
 hpdr_status parse_header(const uint8_t *b, size_t avail, size_t in_bytes, Hdr *h)
 {
     if (in_bytes < 128 || avail < 128) return HPDR_ERR_FORMAT;
-    if (memcmp(b, "HPDR", 4) != 0 || rd32(b + 4) != 2) return HPDR_ERR_FORMAT;
+    if (memcmp(b, "HPDR", 4) != 0 || rd32(b + 4) != 3) return HPDR_ERR_FORMAT;
     if (crc32_host(b, 124) != rd32(b + 124)) return HPDR_ERR_FORMAT;
     h->dtype = (int)rd32(b + 8);
     h->ndim = (int)rd32(b + 12);
@@ -272,14 +272,18 @@ hpdr_status parse_header(const uint8_t *b, size_t avail, size_t in_bytes, Hdr *h
     h->N = rd64(b + 96);
     h->n_esc = rd64(b + 104);
     h->bits = rd64(b + 112);
-    h->s_hi = rd32(b + 120);
+    h->s_hi = rd32(b + 120) & 0xFFFFu;
+    h->esc_w = (rd32(b + 120) >> 16) & 0xFFu;
+    if (rd32(b + 120) >> 24) return HPDR_ERR_FORMAT;
     if (levels_of(h->ndim, h->dims) != h->L || h->L > kMaxLevels) return HPDR_ERR_FORMAT;
     if ((long long)h->N != total_of(h->ndim, h->dims)) return HPDR_ERR_FORMAT;
     if (h->D < 4 || h->D > 65536 || (h->D & 1) || h->K < 128 || h->K > 32768 || (h->K % 128))
         return HPDR_ERR_FORMAT;
     if (h->s_hi >= h->D || h->s_lo > h->s_hi || h->n_esc > h->N) return HPDR_ERR_FORMAT;
-    // at most 63 code bits per symbol plus 69 payload bits per escape
-    if (h->bits > 63ULL * h->N + 69ULL * h->n_esc || h->bits < h->N) return HPDR_ERR_FORMAT;
+    if (h->esc_w > 63 || (h->n_esc > 0) != (h->esc_w > 0)) return HPDR_ERR_FORMAT;
+    // at most 63 code bits per symbol plus the payload of every escape
+    if (h->bits > 63ULL * h->N + (unsigned long long)h->esc_w * h->n_esc || h->bits < h->N)
+        return HPDR_ERR_FORMAT;
     h->nch = (h->N + h->K - 1) / h->K;
     h->nwords = (h->bits + 31) / 32;
     h->off_len = a16(128 + 8ULL * (h->L + 1));
@@ -329,7 +333,8 @@ hpdr_status decompress_t(hpdr_ctx *ctx, const Plan *P, const Hdr &h, const uint8
     da.words = (const uint32_t *)(in + h.off_bits);
     da.nwords = h.nwords;
     da.chunk = (const unsigned long long *)(in + h.off_chunk);
-    da.N = h.N; da.total_bits = h.bits; da.K = h.K; da.sym = w.sym; da.esc = w.esc;
+    da.N = h.N; da.total_bits = h.bits; da.K = h.K; da.sym = w.sym;
+    da.esc = h.esc_w ? w.esc : nullptr; da.esc_w = h.esc_w;
     {
     ProfScope ps(ctx, "d_decode", s);
     CK(launch_decode(da, hs, s));
@@ -648,14 +653,14 @@ size_t hpdr_compress_bound(int ndim, const size_t *dims, hpdr_dtype dtype, const
     int L = levels_of(ndim, dims);
     unsigned long long N = (unsigned long long)total_of(ndim, dims);
     // a Huffman code is never longer in total than the fixed-length code of
-    // ceil(log2 D) bits per symbol; an escape payload takes at most 38 bits
+    // ceil(log2 D) bits per symbol; an escape payload takes at most 32 bits
     // while |k| < 2^31
     unsigned bpsym = 1;
     while ((1ULL << bpsym) < D) bpsym++;
     unsigned long long b = a16(128 + 8ULL * (L + 1));
     b = a16(b + D);
     b = a16(b + 8 * ((N + K - 1) / K));
-    b += 4 * (((bpsym + 38ULL) * N + 31) / 32);
+    b += 4 * (((bpsym + 32ULL) * N + 31) / 32);
     return (size_t)b;
 }
 
@@ -827,7 +832,7 @@ hpdr_status hpdr_huffman_decode(hpdr_ctx *ctx, const uint32_t *d_words, uint64_t
     DecodeArgs da;
     da.words = d_words; da.nwords = (total_bits + 31) / 32;
     da.chunk = (const unsigned long long *)d_chunk_bits;
-    da.N = N; da.K = K; da.sym = d_symbols; da.total_bits = total_bits; da.esc = nullptr;
+    da.N = N; da.K = K; da.sym = d_symbols; da.total_bits = total_bits; da.esc = nullptr; da.esc_w = 0;
     Scalars *hsc = (Scalars *)ctx->host_pinned;
     CK(launch_decode(da, hs, s));
     CK(cudaMemcpyAsync(hsc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));

@@ -18,7 +18,6 @@ namespace {
 constexpr int kRankBlocks = 152 * 2;
 constexpr int kSmemKeys = 12288;     // keys one block stages in shared memory (96 KB)
 constexpr int kSmemCodes = 16384;    // codewords staged by the encoder
-constexpr int kEncThreads = 128;
 
 __device__ __forceinline__ unsigned warp_sum(unsigned v)
 {
@@ -326,12 +325,16 @@ __global__ void __launch_bounds__(256) len16_kernel(HuffScratch hs)
 }
 
 // Decoder table entry of every 15-bit prefix t:
-//   codeword of at most 15 bits:  symbol | L << 16                       (1 <= L <= 15)
-//   longer codewords:             kLongFlag | Lmin << 16 | (Lmax - Lmin) << 24,
-//                                 the lengths of the smallest and largest codeword
-//                                 under t (canonical codes grow in length with value)
-//   no codeword (incomplete code): 0
+//   codeword of at most 15 bits:   symbol | L << 16                         (1 <= L <= 15)
+//   longer codewords, one length L: kLongFlag | base | L << 16, where the codeword
+//                                  t r (r = its last L - 15 bits) is symbol
+//                                  sorted_sym[base + r]
+//   longer codewords, lengths Lmin..Lmax:
+//                                  kLongFlag | kMixedFlag | Lmin << 16 | (Lmax - Lmin) << 24
+//                                  (canonical codes grow in length with their value)
+//   no codeword (incomplete code):  0
 constexpr uint32_t kLongFlag = 0x80000000u;
+constexpr uint32_t kMixedFlag = 0x40000000u;
 
 __device__ __forceinline__ unsigned code_len_at(const HuffScratch &hs, unsigned long long win, int maxL)
 {
@@ -362,8 +365,17 @@ __global__ void __launch_bounds__(256) lut15_kernel(HuffScratch hs)
             const unsigned long long w1 = w0 | ((1ULL << (64 - kLenBits)) - 1);
             const unsigned lmin = code_len_at(hs, w0, maxL);
             const unsigned lmax = code_len_at(hs, w1, maxL);
-            if (lmin > (unsigned)kLenBits && lmin <= lmax)
-                e = kLongFlag | (lmin << 16) | ((lmax - lmin) << 24);
+            if (lmin > (unsigned)kLenBits && lmin < lmax) {
+                e = kLongFlag | kMixedFlag | (lmin << 16) | ((lmax - lmin) << 24);
+            } else if (lmin > (unsigned)kLenBits && lmin == lmax) {
+                // every codeword under t has length lmin: index = start + code - first
+                const unsigned long long c0 = (unsigned long long)t << (lmin - kLenBits);
+                const long long base = (long long)hs.start[lmin] + (long long)c0 - (long long)hs.first[lmin];
+                if (base >= 0 && base + (1LL << (lmin - kLenBits)) <= (long long)n)
+                    e = kLongFlag | (uint32_t)base | (lmin << 16);
+                else
+                    e = kLongFlag | kMixedFlag | (lmin << 16);
+            }
         }
         hs.lut15[t] = e;
     }
@@ -397,6 +409,9 @@ __global__ void __launch_bounds__(256) enc_count_kernel(EncodeArgs a)
     if (block_skip(&a.sc->status)) return;
     for (unsigned i = threadIdx.x; i < a.D; i += blockDim.x) slen[i] = a.len[i];
     __syncthreads();
+    // an escape adds its payload width to its codeword
+    if (a.esc && threadIdx.x == 0) slen[0] = (uint8_t)(slen[0] + a.sc->esc_w);
+    __syncthreads();
     const unsigned long long nch = (a.N + a.K - 1) / a.K;
     const unsigned long long cpb = (nch + gridDim.x - 1) / gridDim.x;
     const unsigned long long c0 = blockIdx.x * cpb, c1 = c0 + cpb < nch ? c0 + cpb : nch;
@@ -407,22 +422,27 @@ __global__ void __launch_bounds__(256) enc_count_kernel(EncodeArgs a)
         const unsigned long long end = beg + a.K < a.N ? beg + a.K : a.N;
         unsigned long long bits = 0;
         if (end - beg == a.K) {
+            // four 16-byte loads per lane in flight (K is a multiple of 128)
             const uint4 *v = reinterpret_cast<const uint4 *>(a.sym + beg);
-            for (unsigned i = lane; i < a.K / 8; i += 32) {
-                uint4 x = v[i];
-                const uint16_t *e = reinterpret_cast<const uint16_t *>(&x);
+            const unsigned nq = a.K / 8;
+            for (unsigned i0 = lane; i0 < nq; i0 += 128) {
+                uint4 x[4];
+                bool ok[4];
 #pragma unroll
-                for (int k = 0; k < 8; k++) {
-                    bits += slen[e[k]];
-                    if (a.esc && e[k] == 0) bits += esc_bits(a.esc[beg + 8ULL * i + k]);
+                for (int u = 0; u < 4; u++) {
+                    ok[u] = i0 + 32 * u < nq;
+                    if (ok[u]) x[u] = v[i0 + 32 * u];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    if (!ok[u]) continue;
+                    const uint16_t *e = reinterpret_cast<const uint16_t *>(&x[u]);
+#pragma unroll
+                    for (int k = 0; k < 8; k++) bits += slen[e[k]];
                 }
             }
         } else {
-            for (unsigned long long i = beg + lane; i < end; i += 32) {
-                uint16_t s = a.sym[i];
-                bits += slen[s];
-                if (a.esc && s == 0) bits += esc_bits(a.esc[i]);
-            }
+            for (unsigned long long i = beg + lane; i < end; i += 32) bits += slen[a.sym[i]];
         }
         bits = warp_sum64(bits);
         if (lane == 0) { a.chunk_bits[c] = bits; tb += bits; }
@@ -534,15 +554,19 @@ __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
     const bool code_sm = a.D <= (unsigned)kSmemCodes;
     unsigned long long *scode = esm;
     uint8_t *slen = reinterpret_cast<uint8_t *>(esm + (code_sm ? a.D : 0));
+    // per warp: the 32 symbols of every lane, 17 words per lane (conflict-free)
+    uint32_t *sw = reinterpret_cast<uint32_t *>(slen + ((a.D + 15) & ~15u)) + (threadIdx.x >> 5) * (32 * 17);
+    const uint16_t *ss = reinterpret_cast<const uint16_t *>(sw + (threadIdx.x & 31) * 17);
     for (unsigned i = threadIdx.x; i < a.D; i += blockDim.x) {
         slen[i] = a.len[i];
         if (code_sm) scode[i] = a.code[i];
     }
     __syncthreads();
-    const unsigned long long *codes = code_sm ? scode : a.code;
+    const unsigned long long *__restrict__ codes = code_sm ? scode : a.code;
     const unsigned long long nch = (a.N + a.K - 1) / a.K;
-    uint32_t *words = enc_words(a, nch);
-    const long long *esc = a.esc;
+    uint32_t *__restrict__ words = enc_words(a, nch);
+    const long long *__restrict__ esc = a.esc;
+    const int ew = esc ? (int)a.sc->esc_w : 0;       // escape payload width
     const unsigned lane = threadIdx.x & 31;
     const unsigned spl = a.K >> 5;
     const unsigned long long wg = blockIdx.x * (unsigned long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -554,27 +578,27 @@ __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
         if (m0 > end) m0 = end;
         if (m1 > end) m1 = end;
         unsigned long long mb = 0;
-        // full lanes of 32 symbols keep them in registers (four 16-byte loads)
-        uint32_t rs[16];
+        // full lanes of 32 symbols stage them in shared memory (four 16-byte loads)
         const bool regs = (m1 - m0 == 32) && spl == 32;
         if (regs) {
             const uint4 *v = reinterpret_cast<const uint4 *>(a.sym + m0);
+            uint4 x[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) x[q] = v[q];
+            uint32_t *dw = sw + lane * 17;
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                const uint4 x = v[q];
-                rs[4 * q] = x.x; rs[4 * q + 1] = x.y; rs[4 * q + 2] = x.z; rs[4 * q + 3] = x.w;
+                dw[4 * q] = x[q].x; dw[4 * q + 1] = x[q].y; dw[4 * q + 2] = x[q].z; dw[4 * q + 3] = x[q].w;
             }
-#pragma unroll
+#pragma unroll 4
             for (int q = 0; q < 32; q++) {
-                const unsigned sv = (rs[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
-                mb += slen[sv];
-                if (esc && sv == 0) mb += esc_bits(esc[m0 + q]);
+                const unsigned sv = ss[q];
+                mb += slen[sv] + (sv == 0 ? ew : 0);
             }
         } else {
             for (unsigned long long i = m0; i < m1; i++) {
                 const uint16_t s = a.sym[i];
-                mb += slen[s];
-                if (esc && s == 0) mb += esc_bits(esc[i]);
+                mb += slen[s] + (s == 0 ? ew : 0);
             }
         }
         unsigned long long xb = mb;
@@ -607,32 +631,40 @@ __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
                 }
             }
         };
-        auto put = [&](uint16_t s, unsigned long long i) {
-            unsigned long long cw = codes[s];
-            int L = slen[s];
-            if (esc && s == 0) {
-                // codeword, 6 bits n - 1 and the n bits of zigzag(k), in one
-                // emission when they fit 64 bits
+        // codeword (cw, L) of symbol s at stream index i, with its escape payload
+        auto put_cw = [&](unsigned long long cw, int L, uint16_t s, unsigned long long i) {
+            if (ew && s == 0) {
+                // codeword and zigzag(k) in ew bits, in one emission when they fit 64 bits
                 const unsigned long long z = zigzag(esc[i]);
-                const int n = 64 - __clzll((long long)z);
-                const unsigned long long pay = ((unsigned long long)(n - 1) << n) | z;
-                if (L + 6 + n <= 64) {
-                    cw = (cw << (6 + n)) | pay;
-                    L += 6 + n;
+                if (L + ew <= 64) {
+                    cw = (cw << ew) | z;
+                    L += ew;
                 } else {
                     emit(cw, L);
-                    emit((unsigned long long)(n - 1), 6);
                     cw = z;
-                    L = n;
+                    L = ew;
                 }
             }
             emit(cw, L);
         };
         if (regs) {
+            for (int q = 0; q < 32; q += 4) {
+                // the loads of four symbols first, then their emissions
+                uint16_t sv[4];
+                unsigned long long cv[4];
+                int lv[4];
 #pragma unroll
-            for (int q = 0; q < 32; q++) put((uint16_t)((rs[q >> 1] >> (16 * (q & 1))) & 0xFFFFu), m0 + q);
+                for (int u = 0; u < 4; u++) sv[u] = ss[q + u];
+#pragma unroll
+                for (int u = 0; u < 4; u++) { cv[u] = codes[sv[u]]; lv[u] = slen[sv[u]]; }
+#pragma unroll
+                for (int u = 0; u < 4; u++) put_cw(cv[u], lv[u], sv[u], m0 + q + u);
+            }
         } else {
-            for (unsigned long long i = m0; i < m1; i++) put(a.sym[i], i);
+            for (unsigned long long i = m0; i < m1; i++) {
+                const uint16_t sv = a.sym[i];
+                put_cw(codes[sv], slen[sv], sv, i);
+            }
         }
         const uint32_t lastw = (uint32_t)(acc >> 32);
         const bool has_last = nacc > 0;
@@ -683,7 +715,7 @@ header_kernel(HeaderArgs h, const uint8_t *len, Scalars *sc, uint8_t *out)
     if (threadIdx.x == 0) {
         for (int i = 0; i < 128; i++) hdr[i] = 0;
         hdr[0] = 'H'; hdr[1] = 'P'; hdr[2] = 'D'; hdr[3] = 'R';
-        put32(hdr + 4, 2);
+        put32(hdr + 4, 3);
         put32(hdr + 8, (uint32_t)h.dtype);
         put32(hdr + 12, (uint32_t)h.ndim);
         for (int k = 0; k < 3; k++) put64(hdr + 16 + 8 * k, h.dims[k]);
@@ -701,7 +733,7 @@ header_kernel(HeaderArgs h, const uint8_t *len, Scalars *sc, uint8_t *out)
         put64(hdr + 104, n_esc);
         sc->n_esc = n_esc;
         put64(hdr + 112, sc->total_bits);
-        put32(hdr + 120, sc->s_hi);
+        put32(hdr + 120, sc->s_hi | ((n_esc ? sc->esc_w : 0u) << 16));
         put32(hdr + 124, crc32_bytes(hdr, 124));
     }
     __syncthreads();
@@ -814,8 +846,10 @@ __global__ void __launch_bounds__(kDecThreads, 1) decode_kernel(DecodeArgs a, Hu
     __syncthreads();
     const uint16_t *symtab = sym_sm ? ssym : hs.sorted_sym;
     long long *const esc = a.esc;
+    const int ew = esc ? (int)a.esc_w : 0;     // escape payload width (1..63)
     const unsigned long long nch = (a.N + a.K - 1) / a.K;
-    for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < nch;
+    // chunks interleave over the blocks so that every SM gets a share
+    for (unsigned long long c = blockIdx.x + (unsigned long long)gridDim.x * threadIdx.x; c < nch;
          c += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long pos0 = a.chunk[c];
         const unsigned long long expect = (c + 1 < nch) ? a.chunk[c + 1] : a.total_bits;
@@ -831,10 +865,15 @@ __global__ void __launch_bounds__(kDecThreads, 1) decode_kernel(DecodeArgs a, Hu
         q.prime(pos0, hi, lo, nb);
         unsigned used = 0;
         bool bad = false;
-        // drop n <= 32 bits, then refill to at least 32 valid bits
+        // drop n <= nb bits (n <= 64), then refill to at least 32 valid bits
         auto drop = [&](unsigned n) {
-            if (n < 32) { hi = __funnelshift_l(lo, hi, n); lo <<= n; }
-            else { hi = lo; lo = 0; }
+            if (n < 32) {
+                hi = __funnelshift_l(lo, hi, n);
+                lo <<= n;
+            } else {
+                hi = n < 64 ? lo << (n - 32) : 0u;
+                lo = 0;
+            }
             nb -= (int)n;
             used += n;
             if (nb < 32) {
@@ -844,57 +883,55 @@ __global__ void __launch_bounds__(kDecThreads, 1) decode_kernel(DecodeArgs a, Hu
                 nb += 32;
             }
         };
-        auto take = [&](unsigned n) -> uint32_t {   // 1 <= n <= 32
-            const uint32_t v = hi >> (32 - n);
-            drop(n);
-            return v;
-        };
         auto step = [&](unsigned long long i) -> uint16_t {
             const uint32_t e = lut[hi >> (32 - kLenBits)];
             uint16_t sv = (uint16_t)(e & 0xFFFFu);
             unsigned L = (e >> 16) & 0x3Fu;
-            if (e >= kLongFlag || e == 0) {
-                // codeword longer than 15 bits (or no codeword: a corrupt stream)
-                if (e == 0) {
-                    bad = true;
-                    L = 1;
+            bool fetched = false;            // the codeword was read past the buffer
+            if (e & kLongFlag) {
+                unsigned long long win = ((unsigned long long)hi << 32) | lo;
+                if (!(e & kMixedFlag) && (int)L <= nb) {
+                    // one length under this prefix: symbol base + the bits after the prefix
+                    const unsigned r = (unsigned)((win << kLenBits) >> (64 - (L - kLenBits)));
+                    const unsigned idx = (e & 0xFFFFu) + r;
+                    sv = symtab[idx < nsym ? idx : 0];
                 } else {
-                    const unsigned long long win = ((unsigned long long)hi << 32) | lo;
-                    const unsigned lmin = L, lmax = L + ((e >> 24) & 0x3Fu);
+                    const unsigned lmin = L;
+                    const unsigned lmax = (e & kMixedFlag) ? L + ((e >> 24) & 0x3Fu) : L;
                     for (unsigned l = lmin; l < lmax; l++) L += (win >= slim[l]) ? 1u : 0u;
-                    unsigned long long wl = win;
                     if ((int)L > nb) {
                         // the codeword extends past the buffered bits: exact window
-                        wl = window64(a.words, a.nwords, pos0 + used);
+                        win = window64(a.words, a.nwords, pos0 + used);
                         L = lmin;
-                        for (unsigned l = lmin; l < lmax; l++) L += (wl >= slim[l]) ? 1u : 0u;
+                        for (unsigned l = lmin; l < lmax; l++) L += (win >= slim[l]) ? 1u : 0u;
+                        fetched = true;
                     }
-                    const unsigned long long off = (wl >> (64 - L)) - sfirst[L];
+                    const unsigned long long off = (win >> (64 - L)) - sfirst[L];
                     if (off >= scount[L]) bad = true;
                     const unsigned idx = sstart[L] + (unsigned)(off < scount[L] ? off : 0);
                     sv = symtab[idx < nsym ? idx : 0];
-                    if ((int)L > nb) {
-                        used += L;
-                        q.prime(pos0 + used, hi, lo, nb);
-                        L = 0;
-                    } else if (L > 32) {
-                        drop(32);
-                        L -= 32;
-                    }
                 }
+            } else if (e == 0) {
+                bad = true;               // no codeword starts here
+                L = 1;
             }
-            if (L) drop(L);
-            if (esc && sv == 0) {
-                // escape payload: 6 bits n - 1, then the n bits of zigzag(k)
-                const unsigned n = take(6) + 1;
+            if (fetched) {
+                used += L;
+                q.prime(pos0 + used, hi, lo, nb);
+            } else {
+                drop(L);
+            }
+            if (ew && sv == 0) {
+                // escape payload: zigzag(k) in ew bits
                 unsigned long long z;
-                if (n > 32) {
-                    const unsigned long long zh = take(n - 32);
-                    z = (zh << 32) | take(32);
+                if (ew <= nb) {
+                    z = ((((unsigned long long)hi) << 32) | lo) >> (64 - ew);
+                    drop((unsigned)ew);
                 } else {
-                    z = take(n);
+                    z = window64(a.words, a.nwords, pos0 + used) >> (64 - ew);
+                    used += (unsigned)ew;
+                    q.prime(pos0 + used, hi, lo, nb);
                 }
-                if (n == 64) bad = true;
                 esc[i] = unzigzag(z);
             }
             return sv;
@@ -1034,7 +1071,7 @@ cudaError_t launch_encode(const EncodeArgs &a, cudaStream_t s)
     enc_scan1_kernel<<<1, 1024, 0, s>>>(a, kEncBlocks);
     enc_scan2_kernel<<<kEncBlocks, 256, 0, s>>>(a);
     const bool code_sm = a.D <= (unsigned)kSmemCodes;
-    size_t sm = (code_sm ? 8 * (size_t)a.D : 0) + ((a.D + 15) & ~15u);
+    size_t sm = (code_sm ? 8 * (size_t)a.D : 0) + ((a.D + 15) & ~15u) + 8 * 32 * 17 * 4;
     enc_write_kernel<<<152 * 3, 256, sm, s>>>(a);
     count_launch(4);
     return cudaGetLastError();

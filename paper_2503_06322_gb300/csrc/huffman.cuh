@@ -7,8 +7,9 @@ namespace hpdr {
 constexpr int kLenBits = 15;    // decoder: code length / symbol of every 15-bit prefix
 constexpr int kMaxCodeLen = 63;
 
-// Escape payload (container format v2): after the codeword of symbol 0, 6
-// bits holding n - 1 and the n bits of zigzag(k), n = bit length (1..63).
+// Escape payload (container format v3): after the codeword of symbol 0,
+// zigzag(k) in W bits, W = the container's payload width (the largest bit
+// length of zigzag(k) over its escapes, 1..63).
 __host__ __device__ inline unsigned long long zigzag(long long k)
 {
     return k >= 0 ? 2ULL * (unsigned long long)k : 2ULL * (unsigned long long)(-(k + 1)) + 1ULL;
@@ -17,9 +18,6 @@ __host__ __device__ inline long long unzigzag(unsigned long long z)
 {
     return (z & 1ULL) ? -(long long)(z >> 1) - 1 : (long long)(z >> 1);
 }
-#ifdef __CUDACC__
-__device__ __forceinline__ unsigned esc_bits(long long k) { return 6u + 64u - (unsigned)__clzll((long long)zigzag(k)); }
-#endif
 
 // Device scratch of one codebook build (sizes for an alphabet of D symbols).
 struct HuffScratch {
@@ -66,7 +64,8 @@ struct EncodeArgs {
     const uint8_t *len;
     const unsigned long long *code;
     const long long *esc;             // null: plain symbols; else symbol 0 is the quantizer's
-                                      // escape and esc[i] its code k (payload after the codeword)
+                                      // escape and esc[i] its code k (payload after the codeword,
+                                      // in sc->esc_w bits)
     unsigned long long *chunk_bits;   // ws [nch+1] totals then offsets
     unsigned long long *bsum;         // ws [kEncBlocks] per-block sums, then offsets
     Scalars *sc;
@@ -99,6 +98,7 @@ struct DecodeArgs {
     unsigned int K;
     uint16_t *sym;
     long long *esc;                   // null: plain symbols; else receives k of every escape
+    unsigned int esc_w;               // payload width of the escapes
 };
 cudaError_t launch_decode(const DecodeArgs &a, const HuffScratch &hs, cudaStream_t s);
 cudaError_t launch_histogram(const uint16_t *sym, unsigned long long N, unsigned D,

@@ -74,6 +74,7 @@ struct Scalars {
     unsigned long long total_bits;
     unsigned long long out_bytes; // container size
     unsigned int status;          // 0 ok, else an hpdr_status magnitude
+    unsigned int esc_w;           // escape payload width: largest bit length of zigzag(k)
     unsigned int s_lo, s_hi;
     unsigned int maxbits_f32;     // max|u| as float bits (atomicMax)
     unsigned long long maxbits_f64;

@@ -79,11 +79,14 @@ __device__ __forceinline__ long long plane_base_of(const LevelGeom<T> &g, int p0
 }
 
 // an escaped code (symbol 0) keeps its k at its stream position; the encoder
-// writes it into the bitstream after the escape's codeword
-__device__ __forceinline__ void escape_store(const QuantOut &qo, long long si, long long k)
+// writes it into the bitstream after the escape's codeword, as zigzag(k) in
+// the container's payload width.  Returns the bit length of zigzag(k).
+__device__ __forceinline__ unsigned escape_store(const QuantOut &qo, long long si, long long k)
 {
     if (k >= kEscMax || k <= -kEscMax) atomicExch(&qo.sc->status, (unsigned int)DS_ARG);
     qo.esc[si] = k;
+    const unsigned long long z = k >= 0 ? 2ULL * (unsigned long long)k : 2ULL * (unsigned long long)(-(k + 1)) + 1ULL;
+    return 64u - (unsigned)__clzll((long long)z);
 }
 
 // quantize one coefficient into the symbol stream (+ block histogram / escapes)
@@ -98,7 +101,7 @@ __device__ __forceinline__ void quant_emit(const QuantOut &qo, unsigned int *hs,
         sym = (unsigned int)s;
     } else {
         sym = 0;
-        escape_store(qo, si, k);
+        atomicMax(&qo.sc->esc_w, escape_store(qo, si, k));
     }
     qo.sym[si] = (uint16_t)sym;
     if (smem_hist) atomicAdd(&hs[sym], 1u);
@@ -184,8 +187,7 @@ restrict_kernel(RestrictArgs<T> a, int seg_len)
     PlaneTaps<T> *ptaps = reinterpret_cast<PlaneTaps<T> *>(mbar + (STAGED ? NST : 0));  // [NST]
     T *W = reinterpret_cast<T *>(ptaps + NST);                       // [RR1][RR2]
     T *Jb = W + RR1 * RR2;                                           // [2][RR1][RR2] (FIELD)
-    T *R2s = Jb + (FIELD ? 2 * RR1 * RR2 : 0);                       // [RR1][TT2]
-    T *wl2s = R2s + RR1 * TT2, *wr2s = wl2s + RR2;                   // [RR2]
+    T *wl2s = Jb + (FIELD ? 2 * RR1 * RR2 : 0), *wr2s = wl2s + RR2;  // [RR2]
     T *wl1s = wr2s + RR2, *wr1s = wl1s + RR1;                        // [RR1]
     unsigned int *hs = reinterpret_cast<unsigned int *>(wr1s + RR1);
 
@@ -420,27 +422,23 @@ restrict_kernel(RestrictArgs<T> a, int seg_len)
         __syncthreads();
         // the stage of plane p0 - 1 is free: refill it with plane p0 + NST - 1
         if (STAGED && warp == 0 && p0 + NST - 1 <= hi0) issue(p0 + NST - 1);
-        // ---- C: restriction along dim 2 (taps of column jl in registers) -------
-        if (jl < n2) {
-            for (int i1 = warp; i1 < r1n; i1 += RTHREADS / 32) {
-                const T *wr = W + i1 * RR2 + c2col;
-                T sacc = (T)0;
-#pragma unroll
-                for (int o = -2; o <= 2; o++) {
-                    const int q = c2col + o;
-                    if (q >= 0 && q < r2n) sacc = fma_rn(t2[o + 2], wr[o], sacc);
-                }
-                R2s[i1 * TT2 + jl] = sacc;
-            }
-        }
-        __syncthreads();
-        // ---- D: restriction along dim 1, dim-0 taps into registers ------------
+        // ---- C + D: every warp restricts along dim 2 the five rows of w its
+        // coarse row needs, then along dim 1, and adds the dim-0 taps in registers
         if (outp) {
             T r = (T)0;
 #pragma unroll
             for (int o = -2; o <= 2; o++) {
-                const int q = c1r + o;
-                if (q >= 0 && q < r1n) r = fma_rn(t1[o + 2], R2s[q * TT2 + lane], r);
+                const int q1 = c1r + o;
+                if (q1 >= 0 && q1 < r1n) {
+                    const T *wr = W + q1 * RR2 + c2col;
+                    T sacc = (T)0;
+#pragma unroll
+                    for (int t = -2; t <= 2; t++) {
+                        const int q = c2col + t;
+                        if (q >= 0 && q < r2n) sacc = fma_rn(t2[t + 2], wr[t], sacc);
+                    }
+                    r = fma_rn(t1[o + 2], sacc, r);
+                }
             }
             PlaneTaps<T> pt;
             if (STAGED) {
@@ -508,9 +506,10 @@ struct PlaneTaps2 {
     T tm[3];   // coarse mass-matrix taps (kept planes only)
 };
 
+// as quant_emit; an escape raises ew to its payload bit length
 template <typename T>
 __device__ __forceinline__ void quant_emit_w(const QuantOut &qo, unsigned int *hs, int hlo, int hn,
-                                             long long si, T w, T rho)
+                                             long long si, T w, T rho, unsigned &ew)
 {
     long long k = quant_code(w, rho);
     long long s = k + (long long)(qo.D / 2);
@@ -519,7 +518,7 @@ __device__ __forceinline__ void quant_emit_w(const QuantOut &qo, unsigned int *h
         sym = (unsigned int)s;
     } else {
         sym = 0;
-        escape_store(qo, si, k);
+        ew = max(ew, escape_store(qo, si, k));
     }
     qo.sym[si] = (uint16_t)sym;
     const unsigned rel = sym - (unsigned)hlo;
@@ -558,9 +557,7 @@ decomp_level_kernel(RestrictArgs<T> a, int seg_len)
         (reinterpret_cast<uintptr_t>(rowoff + NST * RR1) + 15) & ~uintptr_t(15));
     PlaneTaps2<T> *ptaps = reinterpret_cast<PlaneTaps2<T> *>(mbar + NST);
     T *Jb = reinterpret_cast<T *>(ptaps + NST);          // [2][OWN1][JPITCH]
-    T *Rrow = Jb + 2 * OWN1 * JPITCH;                    // [RR1][TT2]
-    T *Mrow = Rrow + RR1 * TT2;                          // [RR1][TT2]
-    T *wl2s = Mrow + RR1 * TT2, *wr2s = wl2s + RR2;      // [RR2]
+    T *wl2s = Jb + 2 * OWN1 * JPITCH, *wr2s = wl2s + RR2;   // [RR2]
     T *wl1s = wr2s + RR2, *wr1s = wl1s + RR1;            // [RR1]
     unsigned int *hs = reinterpret_cast<unsigned int *>(wr1s + RR1);
 
@@ -604,8 +601,10 @@ decomp_level_kernel(RestrictArgs<T> a, int seg_len)
         mt1[d] = ok ? a.g.dim[1].mtap[(J1 + j1l) * 3 + d] : (T)0;
         mr1[d] = ok ? cpos_of(m1, mc1, j) - lo1 : 0;
     }
-    // this thread's owned nodes: row rr, four consecutive nodes from column 4q
-    const int rr = tid >> 4, q4 = (tid & 15) * 4;
+    // this thread's owned nodes: row rr, four consecutive nodes from column 4q;
+    // the two half-warps take rows w and w + 8, of equal parity, so that a
+    // warp's kept/new pattern (and its path through phase B) is uniform
+    const int rr = warp + 8 * ((tid >> 4) & 1), q4 = (tid & 15) * 4;
     const int p1 = o1a + rr;
     const bool rowv = p1 < o1b;
     const int i1 = p1 - lo1;
@@ -705,6 +704,7 @@ decomp_level_kernel(RestrictArgs<T> a, int seg_len)
     int jb = J0a;
     const long long cstride = (long long)mc1 * mc2;
     const long long out_col = (long long)(J1 + j1l) * mc2 + (J2 + jl);
+    unsigned ew = 0;    // largest escape payload bit length seen by this thread
 
     for (int p0 = lo0; p0 <= hi0; p0++) {
         const int s0 = (p0 - lo0) % NST;
@@ -716,6 +716,8 @@ decomp_level_kernel(RestrictArgs<T> a, int seg_len)
             for (int p = waited + 1; p <= hi0 && p < p0 + NST; p++) wait_plane(p);
             return;
         }
+        // every warp is done with plane p0 - 1: its stage takes plane p0 + NST - 1
+        if (warp == 0 && p0 + NST - 1 <= hi0) issue(p0 + NST - 1);
         const bool f0 = !kept_pos(m0, p0);
         const int pj = f0 ? p0 + 1 : p0;
         if (jdone < pj) {
@@ -756,7 +758,7 @@ decomp_level_kernel(RestrictArgs<T> a, int seg_len)
                                 if (rel < (unsigned)hn) atomicAdd(&hs[rel], 1u);
                                 else atomicAdd(&a.qo.hist[sym], 1ULL);
                             } else {
-                                quant_emit_w(a.qo, hs, hlo, hn, si, w, rho);
+                                quant_emit_w(a.qo, hs, hlo, hn, si, w, rho, ew);
                             }
                         }
                     }
@@ -766,39 +768,36 @@ decomp_level_kernel(RestrictArgs<T> a, int seg_len)
                 }
             }
         }
-        // ---- C: restriction of the staged rows along dim 2 ---------------------
-        if (colv) {
-            for (int r = warp; r < r1n; r += RTHREADS / 32) {
-                const T *vr = Vrow(s0, r);
-                T sacc = (T)0;
-#pragma unroll
-                for (int o = -2; o <= 2; o++) {
-                    const int qq = c2col + o;
-                    if (qq >= 0 && qq < r2n) sacc = fma_rn(t2[o + 2], vr[qq], sacc);
-                }
-                Rrow[r * TT2 + jl] = sacc;
-                if (!f0) {
-                    T macc = (T)0;
-#pragma unroll
-                    for (int d = 0; d < 3; d++) macc = fma_rn(mt2[d], vr[mc2col[d]], macc);
-                    Mrow[r * TT2 + jl] = macc;
-                }
-            }
-        }
-        __syncthreads();
-        if (warp == 0 && p0 + NST - 1 <= hi0) issue(p0 + NST - 1);
-        // ---- D: dim 1, then the dim-0 taps into registers ---------------------
+        // ---- C + D: every warp restricts along dim 2 the five fine rows its
+        // coarse row needs (and, on kept planes, applies the coarse mass matrix
+        // along dim 2 to the three kept rows), then along dim 1, and adds the
+        // dim-0 taps in registers
         if (outp) {
             T r = (T)0;
 #pragma unroll
             for (int o = -2; o <= 2; o++) {
                 const int qq = c1r + o;
-                if (qq >= 0 && qq < r1n) r = fma_rn(t1[o + 2], Rrow[qq * TT2 + jl], r);
+                if (qq >= 0 && qq < r1n) {
+                    const T *vr = Vrow(s0, qq);
+                    T sacc = (T)0;
+#pragma unroll
+                    for (int t = -2; t <= 2; t++) {
+                        const int q = c2col + t;
+                        if (q >= 0 && q < r2n) sacc = fma_rn(t2[t + 2], vr[q], sacc);
+                    }
+                    r = fma_rn(t1[o + 2], sacc, r);
+                }
             }
             T rc = (T)0;
             if (!f0) {
 #pragma unroll
-                for (int d = 0; d < 3; d++) rc = fma_rn(mt1[d], Mrow[mr1[d] * TT2 + jl], rc);
+                for (int d = 0; d < 3; d++) {
+                    const T *vr = Vrow(s0, mr1[d]);
+                    T macc = (T)0;
+#pragma unroll
+                    for (int e = 0; e < 3; e++) macc = fma_rn(mt2[e], vr[mc2col[e]], macc);
+                    rc = fma_rn(mt1[d], macc, rc);
+                }
             }
             const PlaneTaps2<T> pt = ptaps[s0];
             while (jb < pt.jlo && jb < J0b) {
@@ -819,6 +818,8 @@ decomp_level_kernel(RestrictArgs<T> a, int seg_len)
         }
     }
     if (hn) {
+        ew = __reduce_max_sync(0xffffffffu, ew);
+        if (lane == 0 && ew) atomicMax(&a.qo.sc->esc_w, ew);
         __syncthreads();
         for (int i = tid; i < hn; i += RTHREADS)
             if (hs[i]) atomicAdd(&a.qo.hist[hlo + i], (unsigned long long)hs[i]);
@@ -832,9 +833,45 @@ size_t decomp_smem(Sink sink, unsigned int D)
     size_t b = (size_t)NST * RR1 * row_pitch_bytes<T>() + NST * RR1 * 4 + 16 + NST * 8;
     b += NST * sizeof(PlaneTaps2<T>);
     b = (b + 15) & ~size_t(15);
-    b += (2 * OWN1 * JPITCH + 2 * RR1 * TT2 + 2 * (RR1 + RR2)) * sizeof(T) + 16;
+    b += (2 * OWN1 * JPITCH + 2 * (RR1 + RR2)) * sizeof(T) + 16;
     if (sink == Sink::QUANT) b += ((size_t)2 * std::min<unsigned>(D / 2, kHistWin) + 1) * sizeof(unsigned int);
     return b;
+}
+
+// Coarse planes per CTA (segment) for a grid of `tiles` x segments CTAs:
+// fill whole waves of the resident CTAs (per_sm per SM) while keeping the
+// dim-0 halo (two fine planes each side of a segment) small.
+int choose_segment(int mc0, long long tiles, int per_sm)
+{
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+            nsm = 152;
+    }
+    const long long slots = (long long)nsm * std::max(1, per_sm);
+    double best = -1.0;
+    int best_seg = mc0;
+    for (int gz = 1; gz <= mc0 && gz <= 512; gz++) {
+        const int seg = (mc0 + gz - 1) / gz;
+        const long long ctas = tiles * ((mc0 + seg - 1) / seg);
+        const long long waves = (ctas + slots - 1) / slots;
+        const double score = (double)ctas / (double)(waves * slots) * (2.0 * seg) / (2.0 * seg + 4.0);
+        if (score > best + 1e-9) { best = score; best_seg = seg; }
+    }
+    return best_seg;
+}
+
+template <typename K>
+int resident_ctas(K kernel, size_t smem)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, RTHREADS, smem) != cudaSuccess) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return std::max(1, n);
 }
 
 template <typename T, int SINK>
@@ -842,12 +879,6 @@ cudaError_t launch_decomp_t(const RestrictArgs<T> &a, cudaStream_t s)
 {
     const int mc0 = a.g.dim[0].mc, mc1 = a.g.dim[1].mc, mc2 = a.g.dim[2].mc;
     const int gx = (mc2 + TT2 - 1) / TT2, gy = (mc1 + TT1 - 1) / TT1;
-    const long long target = 152LL * 6;
-    long long tiles = (long long)gx * gy;
-    int seg = (int)std::max<long long>(2, (mc0 * tiles + target - 1) / target);
-    if (seg > 64) seg = 64;
-    if (seg > mc0) seg = mc0;
-    const int gz = (mc0 + seg - 1) / seg;
     size_t sm = decomp_smem<T>((Sink)SINK, SINK == (int)Sink::QUANT ? a.qo.D : 0);
     static bool attr_set = false;
     if (!attr_set) {
@@ -856,6 +887,8 @@ cudaError_t launch_decomp_t(const RestrictArgs<T> &a, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
+    const int seg = choose_segment(mc0, (long long)gx * gy, resident_ctas(decomp_level_kernel<T, SINK>, sm));
+    const int gz = (mc0 + seg - 1) / seg;
     decomp_level_kernel<T, SINK><<<dim3(gx, gy, gz), RTHREADS, sm, s>>>(a, seg);
     count_launch();
     return cudaGetLastError();
@@ -869,7 +902,7 @@ size_t restrict_smem(WSrc src, Sink sink, unsigned int D)
     else if (src == WSrc::SYMBOLS) b += (size_t)NST * RR1 * row_pitch_bytes<uint16_t>() + NST * RR1 * 4 + 16 + NST * 8;
     b += NST * sizeof(PlaneTaps<T>);
     b = (b + 15) & ~size_t(15);
-    size_t n = RR1 * RR2 * (src == WSrc::FIELD ? 3 : 1) + RR1 * TT2 + 2 * (RR1 + RR2);
+    size_t n = RR1 * RR2 * (src == WSrc::FIELD ? 3 : 1) + 2 * (RR1 + RR2);
     b += n * sizeof(T) + 16;
     if (sink == Sink::QUANT && D <= (unsigned)kHistSmemMax) b += (size_t)D * sizeof(unsigned int);
     return b;
@@ -1193,14 +1226,6 @@ cudaError_t launch_restrict_t(const RestrictArgs<T> &a, cudaStream_t s)
 {
     const int mc0 = a.g.dim[0].mc, mc1 = a.g.dim[1].mc, mc2 = a.g.dim[2].mc;
     const int gx = (mc2 + TT2 - 1) / TT2, gy = (mc1 + TT1 - 1) / TT1;
-    // enough CTAs for every SM to hold three; segments of at least two coarse
-    // planes keep the dim-0 halo (two planes each side) small
-    const long long target = 152LL * 6;
-    long long tiles = (long long)gx * gy;
-    int seg = (int)std::max<long long>(2, (mc0 * tiles + target - 1) / target);
-    if (seg > 64) seg = 64;
-    if (seg > mc0) seg = mc0;
-    const int gz = (mc0 + seg - 1) / seg;
     size_t sm = restrict_smem<T>((WSrc)SRC, (Sink)SINK, SINK == (int)Sink::QUANT ? a.qo.D : 0);
     static bool attr_set = false;
     if (!attr_set) {
@@ -1209,6 +1234,8 @@ cudaError_t launch_restrict_t(const RestrictArgs<T> &a, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
+    const int seg = choose_segment(mc0, (long long)gx * gy, resident_ctas(restrict_kernel<T, SRC, SINK>, sm));
+    const int gz = (mc0 + seg - 1) / seg;
     restrict_kernel<T, SRC, SINK><<<dim3(gx, gy, gz), RTHREADS, sm, s>>>(a, seg);
     count_launch();
     return cudaGetLastError();

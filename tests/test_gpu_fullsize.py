@@ -79,7 +79,7 @@ def test_513_codes_and_huffman_bit_exact(oracle, H, big):
     u, ud = big
     buf = H.hpdr_compress(u, 1e-3).cpu().numpy()
     h = _parse(oracle, buf)
-    sym, esc = oracle.decode(h["words"], h["chunk"], h["N"], h["K"], h["lengths"], escapes=True)
+    sym, esc = oracle.decode(h["words"], h["chunk"], h["N"], h["K"], h["lengths"], esc_width=h["esc_width"])
     coef = H.hpdr_decompose(u).cpu().numpy().astype(np.float64)
     ref_sym, ref_idx, ref_k = oracle.quantize(coef, BIG, h["q"], D=h["D"], precision=32)
     assert np.array_equal(sym, ref_sym)

@@ -65,7 +65,7 @@ def test_recompose_parity_and_identity(oracle, H, dev, shape, dtype):
 
 def _decode_container_symbols(oracle, buf):
     h = oracle.parse_header(buf)
-    sym, esc = oracle.decode(h["words"], h["chunk"], h["N"], h["K"], h["lengths"], escapes=True)
+    sym, esc = oracle.decode(h["words"], h["chunk"], h["N"], h["K"], h["lengths"], esc_width=h["esc_width"])
     return h, sym, esc
 
 

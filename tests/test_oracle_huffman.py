@@ -77,12 +77,15 @@ def test_golden_escape_payload(oracle):
         ln[int(s_)] = int(l_)
     sym = np.array([int(x) for x in spec["symbols"]], dtype=np.uint16)
     esc = np.array([int(x) for x in spec["escapes"]], dtype=np.int64)
-    words, chunk, bits = oracle.encode(sym, ln, K=2, esc_k=esc)
-    assert [int(w) for w in words] == [int(x, 16) for x in spec["words"]]
-    assert bits == int(spec["bits"][0])
-    assert [int(c) for c in chunk] == [int(x) for x in spec["chunks"]]
-    dsym, desc = oracle.decode(words, chunk, sym.size, 2, ln, escapes=True)
-    assert np.array_equal(dsym, sym) and np.array_equal(desc, esc)
+    assert oracle.escape_width(esc) == int(spec["width"][0])
+    for prefix, width in (("", None), ("width5_", 5)):
+        words, chunk, bits = oracle.encode(sym, ln, K=2, esc_k=esc, esc_width=width)
+        assert [int(w) for w in words] == [int(x, 16) for x in spec[prefix + "words"]]
+        assert bits == int(spec[prefix + "bits"][0])
+        assert [int(c) for c in chunk] == [int(x) for x in spec[prefix + "chunks"]]
+        w = int(spec["width"][0]) if width is None else width
+        dsym, desc = oracle.decode(words, chunk, sym.size, 2, ln, esc_width=w)
+        assert np.array_equal(dsym, sym) and np.array_equal(desc, esc)
     # without escapes symbol 0 is a plain symbol: 3 bits in all
     w2, c2, b2 = oracle.encode(sym, ln, K=2)
     assert b2 == 3 and [int(w) for w in w2] == [0x60000000]
@@ -96,15 +99,18 @@ def test_escape_payload_round_trip(oracle, seed):
     sym = rng.integers(0, D, N).astype(np.uint16)
     sym[rng.random(N) < 0.2] = 0
     ne = int((sym == 0).sum())
-    mags = np.concatenate([[D // 2, 2 ** 61, 2 ** 62 - 1, 1 << 31, (1 << 31) - 1],
-                           rng.integers(D // 2, 2 ** 40, max(ne - 5, 0))])[:ne]
+    mags = np.concatenate([[D // 2, 2 ** 40, (1 << 31) - 1],
+                           rng.integers(D // 2, 2 ** 20, max(ne - 3, 0))])[:ne]
+    if seed == 2:
+        mags[0] = 2 ** 62 - 1
     esc = (mags * rng.choice([-1, 1], ne)).astype(np.int64)
     ln = oracle.code_lengths(oracle.histogram(sym, D))
     words, chunk, bits = oracle.encode(sym, ln, K=128, esc_k=esc)
-    z = np.where(esc >= 0, 2 * esc.astype(object), -2 * esc.astype(object) - 1)
-    pay = sum(6 + int(x).bit_length() for x in z)
-    assert bits == int(ln[sym].astype(np.int64).sum()) + pay
-    dsym, desc = oracle.decode(words, chunk, N, 128, ln, escapes=True)
+    z = [2 * int(k) if k >= 0 else -2 * int(k) - 1 for k in esc]
+    w = max(x.bit_length() for x in z)
+    assert oracle.escape_width(esc) == w
+    assert bits == int(ln[sym].astype(np.int64).sum()) + ne * w
+    dsym, desc = oracle.decode(words, chunk, N, 128, ln, esc_width=w)
     assert np.array_equal(dsym, sym) and np.array_equal(desc, esc)
 
 
@@ -113,9 +119,11 @@ def test_escape_code_out_of_range_is_rejected(oracle):
     ln[[0, 1]] = 1
     sym = np.array([0, 1], dtype=np.uint16)
     with pytest.raises(Exception):
-        oracle.encode(sym, ln, K=2, esc_k=np.array([2 ** 62], dtype=np.int64))
+        oracle.encode(sym, ln, K=2, esc_k=np.array([2 ** 62], dtype=np.int64), esc_width=63)
     with pytest.raises(Exception):
-        oracle.encode(sym, ln, K=2, esc_k=np.array([0], dtype=np.int64))
+        oracle.encode(sym, ln, K=2, esc_k=np.array([0], dtype=np.int64), esc_width=8)
+    with pytest.raises(Exception):   # a width too small for the code
+        oracle.encode(sym, ln, K=2, esc_k=np.array([1000], dtype=np.int64), esc_width=5)
 
 
 def _heap_cost(freqs):
@@ -227,7 +235,7 @@ def test_container_round_trip_within_bound(oracle, shape, tol, mode, kind, D, dt
         u = sinusoid_field_2d().astype(dtype)
     buf = oracle.compress(u, tol, tol_kind=kind, mode=mode, D=D)
     h = oracle.parse_header(buf)
-    assert h["magic"] == b"HPDR" and h["version"] == 2 and h["dims"] == shape
+    assert h["magic"] == b"HPDR" and h["version"] == 3 and h["dims"] == shape
     assert h["crc"] == oracle.crc32(bytes(buf[:124]))
     assert h["total_bytes"] == len(buf)
     ref_norm = np.abs(u.astype(np.float64)).max() if mode == 0 else \
