@@ -335,6 +335,9 @@ __global__ void __launch_bounds__(256) len16_kernel(HuffScratch hs)
 //   no codeword (incomplete code):  0
 constexpr uint32_t kLongFlag = 0x80000000u;
 constexpr uint32_t kMixedFlag = 0x40000000u;
+// decoder copy of a short entry of the escape symbol 0 whose codeword and
+// payload (W bits) together fit 32 bits: L = codeword length + W
+constexpr uint32_t kEscFolded = 0x40000000u;
 
 __device__ __forceinline__ unsigned code_len_at(const HuffScratch &hs, unsigned long long win, int maxL)
 {
@@ -549,20 +552,27 @@ __global__ void __launch_bounds__(256) enc_scan2_kernel(EncodeArgs a)
 // at lane boundaries are merged through shuffles (full chunks) or atomics
 __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
 {
-    extern __shared__ unsigned long long esm[];
+    extern __shared__ uint32_t esm32[];
     if (block_skip(&a.sc->status)) return;
+    // codeword table: code << 8 | length for codewords of at most 24 bits; a
+    // length field of 0xFF sends the symbol to the global tables
     const bool code_sm = a.D <= (unsigned)kSmemCodes;
-    unsigned long long *scode = esm;
-    uint8_t *slen = reinterpret_cast<uint8_t *>(esm + (code_sm ? a.D : 0));
+    uint32_t *spk = esm32;
     // per warp: the 32 symbols of every lane, 17 words per lane (conflict-free)
-    uint32_t *sw = reinterpret_cast<uint32_t *>(slen + ((a.D + 15) & ~15u)) + (threadIdx.x >> 5) * (32 * 17);
+    uint32_t *sw = esm32 + (code_sm ? a.D : 0) + (threadIdx.x >> 5) * (32 * 17);
     const uint16_t *ss = reinterpret_cast<const uint16_t *>(sw + (threadIdx.x & 31) * 17);
-    for (unsigned i = threadIdx.x; i < a.D; i += blockDim.x) {
-        slen[i] = a.len[i];
-        if (code_sm) scode[i] = a.code[i];
-    }
+    if (code_sm)
+        for (unsigned i = threadIdx.x; i < a.D; i += blockDim.x) {
+            const unsigned L = a.len[i];
+            spk[i] = L <= 24 ? (uint32_t)((a.code[i] << 8) | L) : 0xFFu;
+        }
     __syncthreads();
-    const unsigned long long *__restrict__ codes = code_sm ? scode : a.code;
+    // (codeword, length) of symbol s
+    auto cw_of = [&](unsigned sv, unsigned long long &cw, int &L) {
+        const uint32_t e = code_sm ? spk[sv] : 0xFFu;
+        if ((e & 0xFFu) != 0xFFu) { cw = e >> 8; L = (int)(e & 0xFFu); }
+        else { cw = a.code[sv]; L = a.len[sv]; }
+    };
     const unsigned long long nch = (a.N + a.K - 1) / a.K;
     uint32_t *__restrict__ words = enc_words(a, nch);
     const long long *__restrict__ esc = a.esc;
@@ -593,12 +603,13 @@ __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
 #pragma unroll 4
             for (int q = 0; q < 32; q++) {
                 const unsigned sv = ss[q];
-                mb += slen[sv] + (sv == 0 ? ew : 0);
+                const uint32_t e = code_sm ? spk[sv] : 0xFFu;
+                mb += ((e & 0xFFu) != 0xFFu ? (e & 0xFFu) : a.len[sv]) + (sv == 0 ? ew : 0);
             }
         } else {
             for (unsigned long long i = m0; i < m1; i++) {
                 const uint16_t s = a.sym[i];
-                mb += slen[s] + (s == 0 ? ew : 0);
+                mb += a.len[s] + (s == 0 ? ew : 0);
             }
         }
         unsigned long long xb = mb;
@@ -656,14 +667,17 @@ __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
 #pragma unroll
                 for (int u = 0; u < 4; u++) sv[u] = ss[q + u];
 #pragma unroll
-                for (int u = 0; u < 4; u++) { cv[u] = codes[sv[u]]; lv[u] = slen[sv[u]]; }
+                for (int u = 0; u < 4; u++) cw_of(sv[u], cv[u], lv[u]);
 #pragma unroll
                 for (int u = 0; u < 4; u++) put_cw(cv[u], lv[u], sv[u], m0 + q + u);
             }
         } else {
             for (unsigned long long i = m0; i < m1; i++) {
                 const uint16_t sv = a.sym[i];
-                put_cw(codes[sv], slen[sv], sv, i);
+                unsigned long long cw;
+                int L;
+                cw_of(sv, cw, L);
+                put_cw(cw, L, sv, i);
             }
         }
         const uint32_t lastw = (uint32_t)(acc >> 32);
@@ -831,9 +845,16 @@ __global__ void __launch_bounds__(kDecThreads, 1) decode_kernel(DecodeArgs a, Hu
     const unsigned nsym = *hs.nsym;
     const bool sym_sm = nsym <= (unsigned)kDecSymSmem;
     {
-        const uint4 *src = reinterpret_cast<const uint4 *>(hs.lut15);
-        uint4 *dst = reinterpret_cast<uint4 *>(lut);
-        for (int i = threadIdx.x; i < (4 << kLenBits) / 16; i += blockDim.x) dst[i] = src[i];
+        // escape entries take their payload width into their length when both fit 32 bits
+        const unsigned ewc = a.esc ? a.esc_w : 0u;
+        for (int i = threadIdx.x; i < (1 << kLenBits); i += blockDim.x) {
+            uint32_t e = hs.lut15[i];
+            if (ewc && e && !(e & kLongFlag) && (e & 0xFFFFu) == 0) {
+                const unsigned L = (e >> 16) & 0x3Fu;
+                if (L + ewc <= 32) e = kEscFolded | ((L + ewc) << 16);
+            }
+            lut[i] = e;
+        }
     }
     for (int i = threadIdx.x; i < 64; i += blockDim.x) {
         sfirst[i] = hs.first[i];
@@ -883,8 +904,9 @@ __global__ void __launch_bounds__(kDecThreads, 1) decode_kernel(DecodeArgs a, Hu
                 nb += 32;
             }
         };
-        auto step = [&](unsigned long long i) -> uint16_t {
-            const uint32_t e = lut[hi >> (32 - kLenBits)];
+        // every other entry: longer codewords, escapes whose codeword and
+        // payload exceed 32 bits, and prefixes that start no codeword
+        auto slow = [&](unsigned long long i, uint32_t e) -> uint16_t {
             uint16_t sv = (uint16_t)(e & 0xFFFFu);
             unsigned L = (e >> 16) & 0x3Fu;
             bool fetched = false;            // the codeword was read past the buffer
@@ -934,6 +956,33 @@ __global__ void __launch_bounds__(kDecThreads, 1) decode_kernel(DecodeArgs a, Hu
                 }
                 esc[i] = unzigzag(z);
             }
+            return sv;
+        };
+        // n <= 32 bits (n <= nb), then refill to at least 32 valid bits
+        auto drop32 = [&](unsigned n) {
+            hi = n < 32 ? __funnelshift_l(lo, hi, n) : lo;
+            lo = n < 32 ? lo << n : 0u;
+            nb -= (int)n;
+            used += n;
+            if (nb < 32) {
+                const uint32_t wv = q.next();
+                hi |= wv >> nb;
+                lo = __funnelshift_rc(0u, wv, (unsigned)nb);
+                nb += 32;
+            }
+        };
+        auto step = [&](unsigned long long i) -> uint16_t {
+            const uint32_t e = lut[hi >> (32 - kLenBits)];
+            const uint16_t sv = (uint16_t)(e & 0xFFFFu);
+            const unsigned L = (e >> 16) & 0x3Fu;
+            const bool at_esc = ew && sv == 0;
+            if ((e & kLongFlag) || e == 0 || (at_esc && !(e & kEscFolded))) return slow(i, e);
+            if (at_esc) {
+                // folded escape: codeword of L - ew bits, then zigzag(k) in ew bits
+                const unsigned long long win = ((unsigned long long)hi << 32) | lo;
+                esc[i] = unzigzag((win << (L - ew)) >> (64 - ew));
+            }
+            drop32(L);
             return sv;
         };
         const unsigned long long beg = c * a.K;
@@ -1071,8 +1120,16 @@ cudaError_t launch_encode(const EncodeArgs &a, cudaStream_t s)
     enc_scan1_kernel<<<1, 1024, 0, s>>>(a, kEncBlocks);
     enc_scan2_kernel<<<kEncBlocks, 256, 0, s>>>(a);
     const bool code_sm = a.D <= (unsigned)kSmemCodes;
-    size_t sm = (code_sm ? 8 * (size_t)a.D : 0) + ((a.D + 15) & ~15u) + 8 * 32 * 17 * 4;
-    enc_write_kernel<<<152 * 3, 256, sm, s>>>(a);
+    const size_t sm = (code_sm ? 4 * (size_t)a.D : 0) + 8 * 32 * 17 * 4;
+    int per_sm = 0, nsm = 0, dev = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, enc_write_kernel, 256, sm) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 3;
+        nsm = 152;
+    }
+    enc_write_kernel<<<(unsigned)(nsm * std::max(1, per_sm)), 256, sm, s>>>(a);
     count_launch(4);
     return cudaGetLastError();
 }
