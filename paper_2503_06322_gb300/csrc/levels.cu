@@ -939,6 +939,79 @@ solve_strided_kernel(T *b, int n, long long stride, long long nlines, const T *_
     }
 }
 
+// One thread per line, 32 adjacent lines per warp (every step one coalesced
+// row), the line swept in place in global memory: the loads of the next eight
+// steps are in flight while the current eight are computed; the Thomas
+// factors sit in shared memory.
+constexpr int kSolvePre = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+solve_stream_kernel(T *b, int n, long long st, long long ostride, long long ninner, long long nlines,
+                    const T *__restrict__ sub, const T *__restrict__ cp, const T *__restrict__ inv_den)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *csub = reinterpret_cast<T *>(smem_raw), *ccp = csub + n, *cinv = ccp + n;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) { csub[t] = sub[t]; ccp[t] = cp[t]; cinv[t] = inv_den[t]; }
+    __syncthreads();
+    const long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (line >= nlines) return;
+    const long long o = line / ninner, i = line - o * ninner;
+    T *p = b + o * ostride + i;
+    constexpr int P = kSolvePre;
+    const int nfull = n / P;   // blocks of P steps
+    // forward sweep: y_t = (d_t - sub_t y_{t-1}) / den_t
+    T y = (T)0;
+    T cur[P], nxt[P];
+    if (nfull > 0) {
+#pragma unroll
+        for (int u = 0; u < P; u++) cur[u] = p[(long long)u * st];
+    }
+    for (int k = 0; k < nfull; k++) {
+        const int t0 = k * P;
+        if (k + 1 < nfull) {
+#pragma unroll
+            for (int u = 0; u < P; u++) nxt[u] = p[(long long)(t0 + P + u) * st];
+        }
+#pragma unroll
+        for (int u = 0; u < P; u++) {
+            y = mul_rn(fma_rn(-csub[t0 + u], y, cur[u]), cinv[t0 + u]);
+            p[(long long)(t0 + u) * st] = y;
+        }
+#pragma unroll
+        for (int u = 0; u < P; u++) cur[u] = nxt[u];
+    }
+    for (int t = nfull * P; t < n; t++) {
+        y = mul_rn(fma_rn(-csub[t], y, p[(long long)t * st]), cinv[t]);
+        p[(long long)t * st] = y;
+    }
+    // backward sweep: x_t = y_t - cp_t x_{t+1}, from the end
+    T x = (T)0;
+    const int ntail = n - nfull * P;
+    for (int t = n - 1; t >= n - ntail; t--) {
+        x = fma_rn(-ccp[t], x, p[(long long)t * st]);
+        p[(long long)t * st] = x;
+    }
+    if (nfull > 0) {
+#pragma unroll
+        for (int u = 0; u < P; u++) cur[u] = p[(long long)((nfull - 1) * P + u) * st];
+    }
+    for (int k = nfull - 1; k >= 0; k--) {
+        const int t0 = k * P;
+        if (k > 0) {
+#pragma unroll
+            for (int u = 0; u < P; u++) nxt[u] = p[(long long)(t0 - P + u) * st];
+        }
+#pragma unroll
+        for (int u = P - 1; u >= 0; u--) {
+            x = fma_rn(-ccp[t0 + u], x, cur[u]);
+            p[(long long)(t0 + u) * st] = x;
+        }
+#pragma unroll
+        for (int u = 0; u < P; u++) cur[u] = nxt[u];
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void cp_async_elem(T *dst_smem, const T *src)
 {
@@ -1253,6 +1326,8 @@ cudaError_t launch_restrict(WSrc src, Sink sink, const RestrictArgs<T> &a, cudaS
     return launch_restrict_t<T, 3, 0>(a, s);
 }
 
+constexpr bool kSolveStream = true;   // strided dimensions: streaming sweeps
+
 template <typename T>
 cudaError_t launch_solves(const LevelGeom<T> &g, T *b, T *vc, int sign, cudaStream_t s)
 {
@@ -1263,7 +1338,15 @@ cudaError_t launch_solves(const LevelGeom<T> &g, T *b, T *vc, int sign, cudaStre
         const DimTables<T> &d = g.dim[k];
         if (!(d.m > 1)) continue;
         int sg = (k == last) ? sign : 0;
-        if (k < 2 && sg == 0 && (size_t)d.mc * 35 * sizeof(T) <= 160 * 1024) {
+        if (k < 2 && sg == 0 && kSolveStream) {
+            // dim 0: lines (j1, j2), step c1*c2; dim 1: lines (j0, j2), step c2
+            const long long st = (k == 0) ? c1 * c2 : c2;
+            const long long outer = (k == 0) ? c1 : c0;
+            const long long ostride = (k == 0) ? c2 : c1 * c2;
+            const long long nlines = outer * c2;
+            solve_stream_kernel<T><<<(unsigned)((nlines + 255) / 256), 256, 3 * (size_t)d.mc * sizeof(T), s>>>(
+                b, d.mc, st, ostride, c2, nlines, d.sub, d.cp, d.inv_den);
+        } else if (k < 2 && sg == 0 && (size_t)d.mc * 35 * sizeof(T) <= 160 * 1024) {
             // dim 0: lines (j1, j2), step c1*c2; dim 1: lines (j0, j2), step c2
             const long long st = (k == 0) ? c1 * c2 : c2;
             const long long outer = (k == 0) ? c1 : c0;
