@@ -64,7 +64,9 @@ typedef struct hpdr_ctx hpdr_ctx;
  * with |k| < D/2 become symbols k + D/2; others are escaped (symbol 0, with
  * k written after its codeword); even, 4 <= D <= 65536; default 8192.
  * chunk K: symbols per decode chunk (the chunk table stores the bit offset of
- * every K-th symbol); multiple of 128, 128 <= K <= 32768; default 1024.
+ * every K-th symbol); multiple of 128, 128 <= K <= 32768; default (0): chosen
+ * from the field's N values, 1024 for N >= 2^27, 512 for N >= 2^26, else 256
+ * (every chunk is one sequential decode, so smaller fields take shorter ones).
  * A zero field selects the default. */
 typedef struct {
     uint32_t dict_size;

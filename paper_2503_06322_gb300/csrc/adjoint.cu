@@ -34,8 +34,18 @@ mass_prolong_kernel(const T *__restrict__ in, T *out, long long s0, long long s1
     const long long in1 = (k == 1) ? mck : s1, in2 = (k == 2) ? mck : s2;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
          idx += (long long)gridDim.x * blockDim.x) {
-        const long long i2 = idx % s2, t = idx / s2;
-        const long long i1 = t % s1, i0 = t / s1;
+        long long i0, i1, i2;
+        if (n < (1LL << 31)) {   // 32-bit divisions (64-bit ones run on the slow FP64 path)
+            const unsigned u = (unsigned)idx, t = u / (unsigned)s2;
+            i2 = u - t * (unsigned)s2;
+            i0 = t / (unsigned)s1;
+            i1 = t - (unsigned)i0 * (unsigned)s1;
+        } else {
+            const long long t = idx / s2;
+            i2 = idx - t * s2;
+            i1 = t % s1;
+            i0 = t / s1;
+        }
         const long long p = (k == 0) ? i0 : (k == 1) ? i1 : i2;
         const int j0 = efirst[p];
         T v = (T)0;
@@ -72,8 +82,18 @@ __global__ void set_kept_kernel(T *G, const T *gv, const T *R, LevelGeom<T> g)
     const long long c1 = g.dim[1].mc, c2 = g.dim[2].mc;
     const long long n = (long long)g.dim[0].mc * c1 * c2;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        const long long q2 = q % c2, t = q / c2;
-        const long long q1 = t % c1, q0 = t / c1;
+        long long q0, q1, q2;
+        if (n < (1LL << 31)) {   // 32-bit divisions
+            const unsigned u = (unsigned)q, t = u / (unsigned)c2;
+            q2 = u - t * (unsigned)c2;
+            q0 = t / (unsigned)c1;
+            q1 = t - (unsigned)q0 * (unsigned)c1;
+        } else {
+            const long long t = q / c2;
+            q2 = q - t * c2;
+            q1 = t % c1;
+            q0 = t / c1;
+        }
         const long long p0 = cpos_of(g.dim[0].m, g.dim[0].mc, (int)q0);
         const long long p1 = cpos_of(g.dim[1].m, g.dim[1].mc, (int)q1);
         const long long p2 = cpos_of(g.dim[2].m, g.dim[2].mc, (int)q2);

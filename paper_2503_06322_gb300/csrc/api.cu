@@ -55,15 +55,26 @@ hpdr_status map_device_status(unsigned st)
     }
 }
 
+// K = 0 after validation: chosen from the field size (chunk_of)
 bool valid_cfg(const hpdr_config *cfg, unsigned &D, unsigned &K)
 {
     D = cfg ? cfg->dict_size : 8192;
-    K = cfg ? cfg->chunk : 1024;
+    K = cfg ? cfg->chunk : 0;
     if (cfg && D == 0) D = 8192;
-    if (cfg && K == 0) K = 1024;
     if (D < 4 || D > 65536 || (D & 1)) return false;
-    if (K < 128 || K > 32768 || (K % 128)) return false;
+    if (K != 0 && (K < 128 || K > 32768 || (K % 128))) return false;
     return true;
+}
+
+// Symbols per decode chunk when the caller leaves it to the library: every
+// chunk is one thread's sequential decode, so smaller fields take shorter
+// chunks to keep the GPU's threads busy (about 2^17 chunks or more).
+unsigned chunk_of(unsigned K, unsigned long long N)
+{
+    if (K) return K;
+    if (N >= (1ULL << 27)) return 1024;
+    if (N >= (1ULL << 26)) return 512;
+    return 256;
 }
 
 long long total_of(int ndim, const size_t *dims)
@@ -211,11 +222,24 @@ hpdr_status compress_core(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, co
     return HPDR_OK;
 }
 
+// container size and device status of one compression, for callers that
+// do not wait for it
+__global__ void size_status_kernel(const Scalars *sc, unsigned long long *dst)
+{
+    dst[0] = sc->out_bytes;
+    dst[1] = sc->status;
+}
+
+// h_size_status == null: synchronize and return the size in *out_bytes;
+// otherwise the call is left in flight and {size, device status} are copied
+// into the pinned host pair h_size_status when the stream gets there
 template <typename T>
 hpdr_status compress_t(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, const size_t *dims,
                        double tol, int tol_kind, int mode, unsigned D, unsigned K, uint8_t *out,
-                       size_t cap, size_t *out_bytes, cudaStream_t s)
+                       size_t cap, size_t *out_bytes, cudaStream_t s,
+                       unsigned long long *h_size_status = nullptr, unsigned long long *d_pair = nullptr)
 {
+    K = chunk_of(K, (unsigned long long)P->N[P->L]);
     Ws w;
     size_t need = carve_ws(nullptr, P, sizeof(T), D, K, true, &w);
     hpdr_status st = ensure_workspace(ctx, need);
@@ -223,6 +247,13 @@ hpdr_status compress_t(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, const
     carve_ws(ctx->ws.base, P, sizeof(T), D, K, true, &w);
     st = compress_core<T>(ctx, P, u, ndim, dims, tol, tol_kind, mode, D, K, out, cap, w, s);
     if (st != HPDR_OK) return st;
+    if (h_size_status) {
+        size_status_kernel<<<1, 1, 0, s>>>(w.sc, d_pair);
+        count_launch();
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(h_size_status, d_pair, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        return HPDR_OK;
+    }
     Scalars *hsc = (Scalars *)ctx->host_pinned;
     CK(cudaMemcpyAsync(hsc, w.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -300,9 +331,41 @@ hpdr_status parse_header(const uint8_t *b, size_t avail, size_t in_bytes, Hdr *h
     return HPDR_OK;
 }
 
+// the decoder-side scalars of one container, set on the device from the
+// launch parameters (no host staging buffer, so calls need not wait)
+struct ScalarInit {
+    double q[kMaxLevels + 1];
+    int L;
+    unsigned long long n_esc, total_bits;
+};
+__global__ void init_scalars_kernel(Scalars *sc, ScalarInit si)
+{
+    unsigned char *b = reinterpret_cast<unsigned char *>(sc);
+    for (unsigned i = threadIdx.x; i < sizeof(Scalars); i += blockDim.x) b[i] = 0;
+    __syncthreads();
+    for (int l = threadIdx.x; l <= si.L; l += blockDim.x) {
+        sc->q[l] = si.q[l];
+        sc->q_f[l] = __double2float_rn(si.q[l]);
+        sc->rho_d[l] = 1.0 / si.q[l];
+        sc->rho_f[l] = __double2float_rn(1.0 / si.q[l]);
+    }
+    if (threadIdx.x == 0) {
+        sc->n_esc = si.n_esc;
+        sc->total_bits = si.total_bits;
+    }
+}
+
+// status of one decompression OR-ed into an accumulated word
+__global__ void accumulate_status_kernel(const Scalars *sc, unsigned *acc)
+{
+    if (sc->status) atomicOr(acc, sc->status);
+}
+
+// err_acc == null: synchronize and report this call's status; otherwise the
+// call is left in flight and its status OR-ed into *err_acc on the device
 template <typename T>
 hpdr_status decompress_t(hpdr_ctx *ctx, const Plan *P, const Hdr &h, const uint8_t *in, T *out,
-                         cudaStream_t s)
+                         cudaStream_t s, unsigned *err_acc = nullptr)
 {
     Ws w;
     size_t need = carve_ws(nullptr, P, sizeof(T), h.D, h.K, true, &w);
@@ -311,16 +374,17 @@ hpdr_status decompress_t(hpdr_ctx *ctx, const Plan *P, const Hdr &h, const uint8
     carve_ws(ctx->ws.base, P, sizeof(T), h.D, h.K, true, &w);
     const int L = P->L;
     Scalars *hsc = (Scalars *)ctx->host_pinned;
-    memset(hsc, 0, sizeof(Scalars));
-    for (int l = 0; l <= L; l++) {
-        hsc->q[l] = h.q[l];
-        hsc->q_f[l] = (float)h.q[l];
-        hsc->rho_d[l] = 1.0 / h.q[l];
-        hsc->rho_f[l] = (float)(1.0 / h.q[l]);
+    {
+        ScalarInit si;
+        memset(&si, 0, sizeof(si));
+        for (int l = 0; l <= L; l++) si.q[l] = h.q[l];
+        si.L = L;
+        si.n_esc = h.n_esc;
+        si.total_bits = h.bits;
+        init_scalars_kernel<<<1, 256, 0, s>>>(w.sc, si);
+        count_launch();
+        CK(cudaGetLastError());
     }
-    hsc->n_esc = h.n_esc;
-    hsc->total_bits = h.bits;
-    CK(cudaMemcpyAsync(w.sc, hsc, sizeof(Scalars), cudaMemcpyHostToDevice, s));
     HuffScratch hs;
     huff_scratch_carve(w.huff, h.D, w.sc, &hs);
     CK(cudaMemsetAsync(hs.len, 0, h.D, s));
@@ -370,10 +434,36 @@ hpdr_status decompress_t(hpdr_ctx *ctx, const Plan *P, const Hdr &h, const uint8
         }
         v = dst;
     }
+    if (err_acc) {
+        accumulate_status_kernel<<<1, 1, 0, s>>>(w.sc, err_acc);
+        count_launch();
+        CK(cudaGetLastError());
+        return HPDR_OK;
+    }
     CK(cudaMemcpyAsync(hsc, w.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (hsc->status) return map_device_status(hsc->status);
     return HPDR_OK;
+}
+
+// Decompression of a container whose header the caller already holds in
+// host memory (hdr_host, hdr_bytes): no header read-back, and with err_acc the
+// call does not wait (status OR-ed into *err_acc on the device).
+hpdr_status decompress_with_header(hpdr_ctx *ctx, const uint8_t *hdr_host, size_t hdr_bytes, const void *d_in,
+                                   size_t in_bytes, void *d_out, size_t out_capacity, cudaStream_t s,
+                                   unsigned *err_acc)
+{
+    Hdr h;
+    hpdr_status st = parse_header(hdr_host, hdr_bytes, in_bytes, &h);
+    if (st != HPDR_OK) return st;
+    if (hdr_bytes < 128 + 8ULL * (h.L + 1)) return HPDR_ERR_FORMAT;
+    const size_t esz = h.dtype == 0 ? 4 : 8;
+    if (out_capacity < h.N * esz) return HPDR_ERR_CAPACITY;
+    Plan *P;
+    st = get_plan(ctx, h.ndim, h.dims, h.dtype == 1, &P);
+    if (st != HPDR_OK) return st;
+    if (h.dtype == 0) return decompress_t<float>(ctx, P, h, (const uint8_t *)d_in, (float *)d_out, s, err_acc);
+    return decompress_t<double>(ctx, P, h, (const uint8_t *)d_in, (double *)d_out, s, err_acc);
 }
 
 template <typename T>
@@ -553,15 +643,16 @@ hpdr_status enqueue_batch(hpdr_ctx *ctx, BatchRes *r, BatchPlan *bp, const hpdr_
         for (int i : q[k]) {
             const Plan *P = bp->plans[i];
             const bool f64 = f[i].dtype == HPDR_F64;
+            const unsigned Ki = chunk_of(K, (unsigned long long)P->N[P->L]);
             Ws w;
-            carve_ws((char *)bp->ws + bp->ws_off[i], P, f64 ? 8 : 4, D, K, true, &w);
+            carve_ws((char *)bp->ws + bp->ws_off[i], P, f64 ? 8 : 4, D, Ki, true, &w);
             hpdr_status stt;
             if (f64)
                 stt = compress_core<double>(ctx, P, (const double *)f[i].d_in, f[i].ndim, f[i].dims, f[i].tol,
-                                            f[i].tol_kind, f[i].mode, D, K, d_out + bp->out_off[i], bp->bound[i], w, st);
+                                            f[i].tol_kind, f[i].mode, D, Ki, d_out + bp->out_off[i], bp->bound[i], w, st);
             else
                 stt = compress_core<float>(ctx, P, (const float *)f[i].d_in, f[i].ndim, f[i].dims, f[i].tol,
-                                           f[i].tol_kind, f[i].mode, D, K, d_out + bp->out_off[i], bp->bound[i], w, st);
+                                           f[i].tol_kind, f[i].mode, D, Ki, d_out + bp->out_off[i], bp->bound[i], w, st);
             if (stt != HPDR_OK) return stt;
             store_size_kernel<<<1, 1, 0, st>>>(w.sc, bp->sizes + 2 * i);
             count_launch();
@@ -595,6 +686,37 @@ bool is_device_ptr(const void *p)
 }
 
 }  // namespace
+
+namespace hpdr {
+hpdr_status decompress_in_flight(hpdr_ctx *ctx, const uint8_t *hdr_host, size_t hdr_bytes, const void *d_in,
+                                 size_t in_bytes, void *d_out, size_t out_capacity, cudaStream_t s,
+                                 unsigned *err_acc)
+{
+    return decompress_with_header(ctx, hdr_host, hdr_bytes, d_in, in_bytes, d_out, out_capacity, s, err_acc);
+}
+hpdr_status status_of_device(unsigned st) { return map_device_status(st); }
+hpdr_status compress_in_flight(hpdr_ctx *ctx, const void *d_in, hpdr_dtype dtype, int ndim, const size_t *dims,
+                               double tol, hpdr_tol_kind tol_kind, hpdr_mode mode, const hpdr_config *cfg,
+                               void *d_out, size_t out_capacity, unsigned long long *h_size_status,
+                               unsigned long long *d_pair, cudaStream_t s)
+{
+    unsigned D, K;
+    if (!ctx || !d_in || !d_out || !h_size_status || !d_pair || !valid_cfg(cfg, D, K)) return HPDR_ERR_ARG;
+    if ((dtype != HPDR_F32 && dtype != HPDR_F64) || (mode != HPDR_LINF && mode != HPDR_L2) ||
+        (tol_kind != HPDR_ABS && tol_kind != HPDR_REL) || !(tol > 0.0) || !std::isfinite(tol))
+        return HPDR_ERR_ARG;
+    if (((uintptr_t)d_in & 15) || ((uintptr_t)d_out & 15)) return HPDR_ERR_ARG;
+    Plan *P;
+    hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P);
+    if (st != HPDR_OK) return st;
+    size_t unused = 0;
+    if (dtype == HPDR_F32)
+        return compress_t<float>(ctx, P, (const float *)d_in, ndim, dims, tol, tol_kind, mode, D, K,
+                                 (uint8_t *)d_out, out_capacity, &unused, s, h_size_status, d_pair);
+    return compress_t<double>(ctx, P, (const double *)d_in, ndim, dims, tol, tol_kind, mode, D, K,
+                              (uint8_t *)d_out, out_capacity, &unused, s, h_size_status, d_pair);
+}
+}  // namespace hpdr
 
 extern "C" {
 
@@ -652,6 +774,7 @@ size_t hpdr_compress_bound(int ndim, const size_t *dims, hpdr_dtype dtype, const
     for (int k = 0; k < ndim; k++) if (dims[k] < 2 || dims[k] > (1u << 30)) return 0;
     int L = levels_of(ndim, dims);
     unsigned long long N = (unsigned long long)total_of(ndim, dims);
+    K = chunk_of(K, N);
     // a Huffman code is never longer in total than the fixed-length code of
     // ceil(log2 D) bits per symbol; an escape payload takes at most 32 bits
     // while |k| < 2^31
@@ -765,7 +888,7 @@ hpdr_status hpdr_huffman_encode(hpdr_ctx *ctx, const uint16_t *d_symbols, uint64
 {
     hpdr_config cfg = {D, K};
     unsigned Dv, Kv;
-    if (!ctx || !d_symbols || !d_lengths || !d_chunk_bits || !d_words || !total_bits || N == 0 ||
+    if (!ctx || !d_symbols || !d_lengths || !d_chunk_bits || !d_words || !total_bits || N == 0 || K == 0 ||
         !valid_cfg(&cfg, Dv, Kv) || ((uintptr_t)d_symbols & 15))
         return HPDR_ERR_ARG;
     DevGuard g(ctx->device);
@@ -812,7 +935,7 @@ hpdr_status hpdr_huffman_decode(hpdr_ctx *ctx, const uint32_t *d_words, uint64_t
 {
     hpdr_config cfg = {D, K};
     unsigned Dv, Kv;
-    if (!ctx || !d_words || !d_chunk_bits || !d_lengths || !d_symbols || N == 0 ||
+    if (!ctx || !d_words || !d_chunk_bits || !d_lengths || !d_symbols || N == 0 || K == 0 ||
         !valid_cfg(&cfg, Dv, Kv) || ((uintptr_t)d_symbols & 15))
         return HPDR_ERR_ARG;
     DevGuard g(ctx->device);
@@ -960,7 +1083,8 @@ hpdr_status hpdr_compress_batched(hpdr_ctx *ctx, int nfields, const hpdr_field *
             st = get_plan(ctx, f.ndim, f.dims, f.dtype == HPDR_F64, &bp->plans[i]);
             if (st != HPDR_OK) { delete bp; return st; }
             Ws w;
-            const size_t need = carve_ws(nullptr, bp->plans[i], f.dtype == HPDR_F64 ? 8 : 4, D, K, true, &w);
+            const unsigned Ki = chunk_of(K, (unsigned long long)bp->plans[i]->N[bp->plans[i]->L]);
+            const size_t need = carve_ws(nullptr, bp->plans[i], f.dtype == HPDR_F64 ? 8 : 4, D, Ki, true, &w);
             bp->ws_off[i] = wsz;
             wsz = (wsz + need + 255) & ~size_t(255);
             bp->out_off[i] = out_offsets[i];

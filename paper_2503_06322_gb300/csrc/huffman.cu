@@ -588,20 +588,23 @@ __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
         if (m0 > end) m0 = end;
         if (m1 > end) m1 = end;
         unsigned long long mb = 0;
-        // full lanes of 32 symbols stage them in shared memory (four 16-byte loads)
-        const bool regs = (m1 - m0 == 32) && spl == 32;
+        // full lanes of 8, 16 or 32 symbols stage them in shared memory (16-byte loads)
+        const bool regs = (m1 - m0 == spl) && (spl == 32 || spl == 16 || spl == 8);
         if (regs) {
             const uint4 *v = reinterpret_cast<const uint4 *>(a.sym + m0);
+            const int nq = (int)spl / 8;
             uint4 x[4];
 #pragma unroll
-            for (int q = 0; q < 4; q++) x[q] = v[q];
+            for (int q = 0; q < 4; q++) if (q < nq) x[q] = v[q];
             uint32_t *dw = sw + lane * 17;
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                dw[4 * q] = x[q].x; dw[4 * q + 1] = x[q].y; dw[4 * q + 2] = x[q].z; dw[4 * q + 3] = x[q].w;
+                if (q < nq) {
+                    dw[4 * q] = x[q].x; dw[4 * q + 1] = x[q].y; dw[4 * q + 2] = x[q].z; dw[4 * q + 3] = x[q].w;
+                }
             }
 #pragma unroll 4
-            for (int q = 0; q < 32; q++) {
+            for (int q = 0; q < (int)spl; q++) {
                 const unsigned sv = ss[q];
                 const uint32_t e = code_sm ? spk[sv] : 0xFFu;
                 mb += ((e & 0xFFu) != 0xFFu ? (e & 0xFFu) : a.len[sv]) + (sv == 0 ? ew : 0);
@@ -659,7 +662,7 @@ __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
             emit(cw, L);
         };
         if (regs) {
-            for (int q = 0; q < 32; q += 4) {
+            for (int q = 0; q < (int)spl; q += 4) {
                 // the loads of four symbols first, then their emissions
                 uint16_t sv[4];
                 unsigned long long cv[4];
@@ -682,9 +685,10 @@ __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
         }
         const uint32_t lastw = (uint32_t)(acc >> 32);
         const bool has_last = nacc > 0;
-        const bool full = (end - beg == a.K) && spl >= 32;
+        // a full chunk whose every lane holds >= 32 bits (always true with 32
+        // symbols per lane): lane i's last partial word is lane i+1's first word
+        const bool full = __all_sync(0xffffffffu, (end - beg == a.K) && mb >= 32);
         if (full) {
-            // every lane holds >= 32 bits: lane i's last partial word is lane i+1's first word
             const uint32_t prev = __shfl_up_sync(0xffffffffu, lastw, 1);
             const bool sh = (start & 31) != 0;
             if (lane > 0 && sh) firstw |= prev;

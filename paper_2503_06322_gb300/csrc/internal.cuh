@@ -193,6 +193,21 @@ namespace hpdr {
 extern unsigned long long g_launches;
 inline void count_launch(int n = 1) { g_launches += (unsigned long long)n; }
 
+// Decompression of a container whose header the caller holds in host memory:
+// no header read-back and no wait; the device status is OR-ed into *err_acc
+// (a device word).  status_of_device maps such a word to an hpdr_status.
+hpdr_status decompress_in_flight(hpdr_ctx *ctx, const uint8_t *hdr_host, size_t hdr_bytes, const void *d_in,
+                                 size_t in_bytes, void *d_out, size_t out_capacity, cudaStream_t s,
+                                 unsigned *err_acc);
+hpdr_status status_of_device(unsigned st);
+// Compression that does not wait: {container size, device status} arrive in
+// the pinned host pair h_size_status (through the device pair d_pair) when
+// the stream reaches the end of the call.
+hpdr_status compress_in_flight(hpdr_ctx *ctx, const void *d_in, hpdr_dtype dtype, int ndim, const size_t *dims,
+                               double tol, hpdr_tol_kind tol_kind, hpdr_mode mode, const hpdr_config *cfg,
+                               void *d_out, size_t out_capacity, unsigned long long *h_size_status,
+                               unsigned long long *d_pair, cudaStream_t s);
+
 // diagnostics scope: records CUDA events around a group of launches
 struct ProfScope {
     hpdr_ctx *ctx;

@@ -28,6 +28,9 @@ struct StreamRes {
     cudaEvent_t ev[8] = {};
     void *buf[4] = {nullptr, nullptr, nullptr, nullptr};
     size_t bytes[4] = {0, 0, 0, 0};
+    unsigned *err = nullptr;        // device: statuses of in-flight decompressions, OR-ed
+    unsigned long long *h_pairs = nullptr, *d_pairs = nullptr;   // per slab {size, status}
+    size_t npairs = 0;
 };
 
 // slab split along dim 0: as few slabs as the byte budget allows, of equal
@@ -50,6 +53,21 @@ void split_slabs(size_t n0, size_t plane_bytes, size_t slab_bytes, std::vector<s
     }
 }
 
+hpdr_status ensure_pairs(StreamRes *r, size_t n)
+{
+    if (r->npairs >= n) return HPDR_OK;
+    if (r->h_pairs) { cudaDeviceSynchronize(); cudaFreeHost(r->h_pairs); r->h_pairs = nullptr; }
+    if (r->d_pairs) { cudaFree(r->d_pairs); r->d_pairs = nullptr; }
+    r->npairs = 0;
+    if (cudaHostAlloc(&r->h_pairs, 2 * n * sizeof(unsigned long long), cudaHostAllocDefault) != cudaSuccess ||
+        cudaMalloc(&r->d_pairs, 2 * n * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        return HPDR_ERR_NOMEM;
+    }
+    r->npairs = n;
+    return HPDR_OK;
+}
+
 hpdr_status ensure_res(hpdr_ctx *ctx, StreamRes *&r, size_t in_bytes, size_t out_bytes)
 {
     if (!ctx->stream_res) {
@@ -58,6 +76,7 @@ hpdr_status ensure_res(hpdr_ctx *ctx, StreamRes *&r, size_t in_bytes, size_t out
             if (cudaStreamCreateWithFlags(&r->s[i], cudaStreamNonBlocking) != cudaSuccess) return HPDR_ERR_CUDA;
         for (int i = 0; i < 8; i++)
             if (cudaEventCreateWithFlags(&r->ev[i], cudaEventDisableTiming) != cudaSuccess) return HPDR_ERR_CUDA;
+        if (cudaMalloc(&r->err, sizeof(unsigned)) != cudaSuccess) { cudaGetLastError(); return HPDR_ERR_NOMEM; }
         ctx->stream_res = r;
     }
     r = (StreamRes *)ctx->stream_res;
@@ -84,6 +103,9 @@ void destroy_stream_res(hpdr_ctx *ctx)
     StreamRes *r = (StreamRes *)ctx->stream_res;
     if (!r) return;
     for (int i = 0; i < 4; i++) if (r->buf[i]) cudaFree(r->buf[i]);
+    if (r->err) cudaFree(r->err);
+    if (r->h_pairs) cudaFreeHost(r->h_pairs);
+    if (r->d_pairs) cudaFree(r->d_pairs);
     for (int i = 0; i < 8; i++) if (r->ev[i]) cudaEventDestroy(r->ev[i]);
     for (int i = 0; i < 3; i++) if (r->s[i]) cudaStreamDestroy(r->s[i]);
     delete r;
@@ -137,24 +159,18 @@ extern "C" hpdr_status hpdr_compress_host_streamed(hpdr_ctx *ctx, const void *h_
         }
         return cudaEventRecord(h2d_done[j], sH) == cudaSuccess;
     };
-    if (!h2d(0)) return HPDR_ERR_CUDA;
-    for (size_t i = 0; i < ns; i++) {
-        const int j = (int)(i & 1);
-        if (i + 1 < ns && !h2d(i + 1)) return HPDR_ERR_CUDA;
-        if (cudaStreamWaitEvent(sC, h2d_done[j], 0) != cudaSuccess) return HPDR_ERR_CUDA;
-        if (i >= 2 && cudaStreamWaitEvent(sC, d2h_done[j], 0) != cudaSuccess) return HPDR_ERR_CUDA;
-        size_t d[3] = {count[i], ndim > 1 ? dims[1] : 1, ndim > 2 ? dims[2] : 1};
-        size_t nb = 0;
-        {
-            hpdr::ProfScope ps(ctx, "s_compute", sC);
-            st = hpdr_compress(ctx, r->buf[j], dtype, ndim, d, tol, tol_kind, mode, cfg, r->buf[2 + j],
-                               r->bytes[2 + j], &nb, sC);
-        }
-        if (st != HPDR_OK) { cudaDeviceSynchronize(); return st; }
-        if (cudaEventRecord(comp_done[j], sC) != cudaSuccess) return HPDR_ERR_CUDA;
-        if (at + nb > out_capacity) { cudaDeviceSynchronize(); return HPDR_ERR_CAPACITY; }
-        off[i] = at;
-        sz[i] = nb;
+    if (ensure_pairs(r, ns) != HPDR_OK) return HPDR_ERR_NOMEM;
+    // The host enqueues the compression of slab i before it waits for slab
+    // i - 1 (to learn its container size and copy it back), so the compute
+    // stream always has the next slab queued.
+    auto finish = [&](size_t k) -> hpdr_status {
+        const int j = (int)(k & 1);
+        if (cudaEventSynchronize(comp_done[j]) != cudaSuccess) return HPDR_ERR_CUDA;
+        const unsigned long long nb = r->h_pairs[2 * k], stat = r->h_pairs[2 * k + 1];
+        if (stat) return hpdr::status_of_device((unsigned)stat);
+        if (at + nb > out_capacity) return HPDR_ERR_CAPACITY;
+        off[k] = at;
+        sz[k] = nb;
         if (cudaStreamWaitEvent(sD, comp_done[j], 0) != cudaSuccess) return HPDR_ERR_CUDA;
         {
             hpdr::ProfScope ps(ctx, "s_d2h", sD);
@@ -163,7 +179,29 @@ extern "C" hpdr_status hpdr_compress_host_streamed(hpdr_ctx *ctx, const void *h_
         }
         if (cudaEventRecord(d2h_done[j], sD) != cudaSuccess) return HPDR_ERR_CUDA;
         at = (at + nb + 15) & ~15ull;
+        return HPDR_OK;
+    };
+    if (!h2d(0)) return HPDR_ERR_CUDA;
+    for (size_t i = 0; i < ns; i++) {
+        const int j = (int)(i & 1);
+        if (i + 1 < ns && !h2d(i + 1)) return HPDR_ERR_CUDA;
+        if (cudaStreamWaitEvent(sC, h2d_done[j], 0) != cudaSuccess) return HPDR_ERR_CUDA;
+        if (i >= 2 && cudaStreamWaitEvent(sC, d2h_done[j], 0) != cudaSuccess) return HPDR_ERR_CUDA;
+        size_t d[3] = {count[i], ndim > 1 ? dims[1] : 1, ndim > 2 ? dims[2] : 1};
+        {
+            hpdr::ProfScope ps(ctx, "s_compute", sC);
+            st = hpdr::compress_in_flight(ctx, r->buf[j], dtype, ndim, d, tol, tol_kind, mode, cfg, r->buf[2 + j],
+                                          r->bytes[2 + j], r->h_pairs + 2 * i, r->d_pairs + 2 * i, sC);
+        }
+        if (st != HPDR_OK) { cudaDeviceSynchronize(); return st; }
+        if (cudaEventRecord(comp_done[j], sC) != cudaSuccess) return HPDR_ERR_CUDA;
+        if (i >= 1) {
+            st = finish(i - 1);
+            if (st != HPDR_OK) { cudaDeviceSynchronize(); return st; }
+        }
     }
+    st = finish(ns - 1);
+    if (st != HPDR_OK) { cudaDeviceSynchronize(); return st; }
     if (cudaStreamSynchronize(sD) != cudaSuccess || cudaStreamSynchronize(sH) != cudaSuccess) return HPDR_ERR_CUDA;
     memset(out, 0, table);
     memcpy(out, "HPDS", 4);
@@ -236,6 +274,9 @@ extern "C" hpdr_status hpdr_decompress_host_streamed(hpdr_ctx *ctx, const void *
         }
         return cudaEventRecord(h2d_done[j], sH) == cudaSuccess;
     };
+    // the host never waits inside the loop: every slab's header is read from
+    // the host copy of the container and the statuses are checked at the end
+    if (cudaMemsetAsync(r->err, 0, sizeof(unsigned), sC) != cudaSuccess) return HPDR_ERR_CUDA;
     if (!h2d(0)) return HPDR_ERR_CUDA;
     for (size_t i = 0; i < ns; i++) {
         const int j = (int)(i & 1);
@@ -244,7 +285,9 @@ extern "C" hpdr_status hpdr_decompress_host_streamed(hpdr_ctx *ctx, const void *
         if (i >= 2 && cudaStreamWaitEvent(sC, d2h_done[j], 0) != cudaSuccess) return HPDR_ERR_CUDA;
         {
             hpdr::ProfScope ps(ctx, "s_compute", sC);
-            st = hpdr_decompress(ctx, r->buf[j], sz[i], r->buf[2 + j], r->bytes[2 + j], sC);
+            const size_t hb = std::min<size_t>((size_t)sz[i], 128 + 8 * (hpdr::kMaxLevels + 1));
+            st = hpdr::decompress_in_flight(ctx, in + off[i], hb, r->buf[j], sz[i], r->buf[2 + j],
+                                            r->bytes[2 + j], sC, r->err);
         }
         if (st != HPDR_OK) { cudaDeviceSynchronize(); return st; }
         if (cudaEventRecord(comp_done[j], sC) != cudaSuccess) return HPDR_ERR_CUDA;
@@ -257,6 +300,11 @@ extern "C" hpdr_status hpdr_decompress_host_streamed(hpdr_ctx *ctx, const void *
         }
         if (cudaEventRecord(d2h_done[j], sD) != cudaSuccess) return HPDR_ERR_CUDA;
     }
-    if (cudaStreamSynchronize(sD) != cudaSuccess || cudaStreamSynchronize(sH) != cudaSuccess) return HPDR_ERR_CUDA;
+    if (cudaStreamSynchronize(sD) != cudaSuccess || cudaStreamSynchronize(sH) != cudaSuccess ||
+        cudaStreamSynchronize(sC) != cudaSuccess)
+        return HPDR_ERR_CUDA;
+    unsigned err = 0;
+    if (cudaMemcpy(&err, r->err, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return HPDR_ERR_CUDA;
+    if (err) return hpdr::status_of_device(err);
     return HPDR_OK;
 }

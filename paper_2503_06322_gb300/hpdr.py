@@ -132,13 +132,13 @@ def _dev_tensor(t, what):
     return t
 
 
-def hpdr_compress_bound(shape, dtype=torch.float32, dict_size=8192, chunk=1024):
+def hpdr_compress_bound(shape, dtype=torch.float32, dict_size=8192, chunk=0):
     nd, dims = _dims(shape)
     cfg = _cfg(dict_size, chunk)
     return int(lib().hpdr_compress_bound(nd, dims, _dtype_code(dtype), C.byref(cfg)))
 
 
-def hpdr_compress(u, tol, tol_kind=REL, mode=LINF, dict_size=8192, chunk=1024, out=None,
+def hpdr_compress(u, tol, tol_kind=REL, mode=LINF, dict_size=8192, chunk=0, out=None,
                   stream=None):
     """Compress a CUDA field; returns a uint8 CUDA tensor holding the container."""
     _dev_tensor(u, "u")
@@ -205,7 +205,7 @@ def hpdr_decompose_noalloc(u, out=None, stream=None):
     return out
 
 
-def streamed_bound(shape, dtype=torch.float32, slab_bytes=256 << 20, dict_size=8192, chunk=1024):
+def streamed_bound(shape, dtype=torch.float32, slab_bytes=256 << 20, dict_size=8192, chunk=0):
     """Capacity that always holds the streamed container of a field."""
     esz = 4 if dtype == torch.float32 else 8
     plane = esz
@@ -218,7 +218,7 @@ def streamed_bound(shape, dtype=torch.float32, slab_bytes=256 << 20, dict_size=8
 
 
 def hpdr_compress_host_streamed(u, tol, tol_kind=REL, mode=LINF, slab_bytes=256 << 20, dict_size=8192,
-                                chunk=1024, out=None, device=None):
+                                chunk=0, out=None, device=None):
     """Compress a CPU tensor (pinned for overlapped copies) in slabs; returns a
     CPU uint8 tensor holding the streamed container."""
     if u.is_cuda or not u.is_contiguous():
@@ -252,7 +252,7 @@ def hpdr_decompress_host_streamed(buf, out=None, device=None):
     return out
 
 
-def batched_capacity(shapes_dtypes, dict_size=8192, chunk=1024):
+def batched_capacity(shapes_dtypes, dict_size=8192, chunk=0):
     """Output bytes hpdr_compress_batched needs for these (shape, dtype) fields."""
     total = 0
     for shape, dt in shapes_dtypes:
@@ -260,7 +260,7 @@ def batched_capacity(shapes_dtypes, dict_size=8192, chunk=1024):
     return total
 
 
-def hpdr_compress_batched(fields, tols, tol_kind=REL, mode=LINF, dict_size=8192, chunk=1024, out=None,
+def hpdr_compress_batched(fields, tols, tol_kind=REL, mode=LINF, dict_size=8192, chunk=0, out=None,
                           stream=None):
     """Compress a list of CUDA fields (one graph replay; see include/hpdr.h).
     Returns (out uint8 tensor, offsets list, sizes list)."""

@@ -100,7 +100,8 @@ def test_codes_bit_exact_on_identical_inputs(oracle, H, dev, shape, tol, D, dtyp
 
 @pytest.mark.parametrize("n,D,K,spread", [(20000, 8192, 1024, 300.0), (1, 16, 128, 1.0),
                                           (777, 256, 128, 0.0), (300000, 65536, 1024, 2000.0),
-                                          (65536, 8192, 4096, 3.0), (5000, 64, 256, 40.0)])
+                                          (65536, 8192, 4096, 3.0), (5000, 64, 256, 40.0),
+                                          (100000, 8192, 512, 500.0)])
 def test_huffman_bit_exact(oracle, H, dev, n, D, K, spread):
     rng = np.random.default_rng(n)
     sym = np.clip(np.round(rng.laplace(D // 2, spread + 1e-9, size=n)), 1, D - 1).astype(np.uint16)
