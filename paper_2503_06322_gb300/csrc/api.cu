@@ -387,11 +387,9 @@ hpdr_status decompress_t(hpdr_ctx *ctx, const Plan *P, const Hdr &h, const uint8
     }
     HuffScratch hs;
     huff_scratch_carve(w.huff, h.D, w.sc, &hs);
-    CK(cudaMemsetAsync(hs.len, 0, h.D, s));
-    CK(cudaMemcpyAsync(hs.len + h.s_lo, in + h.off_len, h.s_hi - h.s_lo + 1, cudaMemcpyDeviceToDevice, s));
     {
     ProfScope ps(ctx, "d_tables", s);
-    CK(launch_decode_tables(hs.len, h.D, hs, s));
+    CK(launch_decode_tables(in + h.off_len, h.s_lo, h.s_hi, h.D, hs, s));
     }
     DecodeArgs da;
     da.words = (const uint32_t *)(in + h.off_bits);
@@ -950,8 +948,7 @@ hpdr_status hpdr_huffman_decode(hpdr_ctx *ctx, const uint32_t *d_words, uint64_t
     CK(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
     HuffScratch hs;
     huff_scratch_carve(hb, D, sc, &hs);
-    CK(cudaMemcpyAsync(hs.len, d_lengths, D, cudaMemcpyDeviceToDevice, s));
-    CK(launch_decode_tables(hs.len, D, hs, s));
+    CK(launch_decode_tables(d_lengths, 0, D - 1, D, hs, s));
     DecodeArgs da;
     da.words = d_words; da.nwords = (total_bits + 31) / 32;
     da.chunk = (const unsigned long long *)d_chunk_bits;

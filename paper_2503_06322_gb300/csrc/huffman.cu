@@ -278,25 +278,6 @@ __global__ void __launch_bounds__(1024) merge_kernel(HuffScratch hs, unsigned D)
     if (tid == 0) length_tables(hs, cnt);
 }
 
-// decoder side: per-length counts from the present (length, symbol) keys
-__global__ void __launch_bounds__(1024) length_count_kernel(HuffScratch hs)
-{
-    __shared__ unsigned cnt[kMaxCodeLen + 2];
-    const unsigned n = *hs.nsym;
-    for (unsigned L = threadIdx.x; L < kMaxCodeLen + 2; L += blockDim.x) cnt[L] = 0;
-    __syncthreads();
-    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
-        unsigned L = (unsigned)(hs.keys2[i] >> 16);
-        if (L > (unsigned)kMaxCodeLen) { atomicExch(hs.status, (unsigned)DS_FORMAT); L = kMaxCodeLen; }
-        atomicAdd(&cnt[L], 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (n == 0) atomicExch(hs.status, (unsigned)DS_FORMAT);
-        length_tables(hs, cnt);
-    }
-}
-
 // canonical codeword of every present symbol and the (length, symbol) order
 __global__ void __launch_bounds__(256) assign_kernel(HuffScratch hs)
 {
@@ -307,20 +288,6 @@ __global__ void __launch_bounds__(256) assign_kernel(HuffScratch hs)
         unsigned r = hs.rank[i];
         hs.code[s] = hs.first[L] + (r - hs.start[L]);
         hs.sorted_sym[r] = (uint16_t)s;
-    }
-}
-
-__global__ void __launch_bounds__(256) len16_kernel(HuffScratch hs)
-{
-    const unsigned n = *hs.nsym;
-    if (*hs.status) return;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const unsigned long long k = hs.keys2[i];
-        const unsigned s = (unsigned)(k & 0xFFFFu), L = (unsigned)(k >> 16);
-        if (L == 0 || L > (unsigned)kLenBits) continue;
-        const unsigned base = (unsigned)(hs.code[s] << (kLenBits - L));
-        const unsigned span = 1u << (kLenBits - L);
-        for (unsigned e = 0; e < span; e++) hs.len16[base + e] = (uint8_t)L;
     }
 }
 
@@ -356,32 +323,402 @@ __global__ void __launch_bounds__(256) lut15_kernel(HuffScratch hs)
     for (int l = kMaxCodeLen; l >= 1; l--) if (hs.count[l]) { maxL = l; break; }
     for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < (1u << kLenBits); t += gridDim.x * blockDim.x) {
         uint32_t e = 0;
-        const unsigned L = ok ? hs.len16[t] : 0u;
-        if (L) {
-            const unsigned long long off = (unsigned long long)(t >> (kLenBits - L)) - hs.first[L];
-            if (off < hs.count[L]) {
-                const unsigned idx = hs.start[L] + (unsigned)off;
-                if (idx < n) e = (uint32_t)hs.sorted_sym[idx] | (L << 16);
-            }
-        } else if (ok) {
+        if (ok && maxL) {
+            // the codeword whose left-justified range holds t's first bit string;
+            // at most 15 bits long, it is a prefix of every extension of t
             const unsigned long long w0 = (unsigned long long)t << (64 - kLenBits);
-            const unsigned long long w1 = w0 | ((1ULL << (64 - kLenBits)) - 1);
             const unsigned lmin = code_len_at(hs, w0, maxL);
-            const unsigned lmax = code_len_at(hs, w1, maxL);
-            if (lmin > (unsigned)kLenBits && lmin < lmax) {
-                e = kLongFlag | kMixedFlag | (lmin << 16) | ((lmax - lmin) << 24);
-            } else if (lmin > (unsigned)kLenBits && lmin == lmax) {
-                // every codeword under t has length lmin: index = start + code - first
-                const unsigned long long c0 = (unsigned long long)t << (lmin - kLenBits);
-                const long long base = (long long)hs.start[lmin] + (long long)c0 - (long long)hs.first[lmin];
-                if (base >= 0 && base + (1LL << (lmin - kLenBits)) <= (long long)n)
-                    e = kLongFlag | (uint32_t)base | (lmin << 16);
-                else
-                    e = kLongFlag | kMixedFlag | (lmin << 16);
+            if (lmin <= (unsigned)kLenBits) {
+                const unsigned long long off = (unsigned long long)(t >> (kLenBits - lmin)) - hs.first[lmin];
+                if (off < hs.count[lmin]) {
+                    const unsigned idx = hs.start[lmin] + (unsigned)off;
+                    if (idx < n) e = (uint32_t)hs.sorted_sym[idx] | (lmin << 16);
+                }
+            } else {
+                const unsigned long long w1 = w0 | ((1ULL << (64 - kLenBits)) - 1);
+                const unsigned lmax = code_len_at(hs, w1, maxL);
+                if (lmin < lmax) {
+                    e = kLongFlag | kMixedFlag | (lmin << 16) | ((lmax - lmin) << 24);
+                } else {
+                    // every codeword under t has length lmin: index = start + code - first
+                    const unsigned long long c0 = (unsigned long long)t << (lmin - kLenBits);
+                    const long long base = (long long)hs.start[lmin] + (long long)c0 - (long long)hs.first[lmin];
+                    if (base >= 0 && base + (1LL << (lmin - kLenBits)) <= (long long)n)
+                        e = kLongFlag | (uint32_t)base | (lmin << 16);
+                    else
+                        e = kLongFlag | kMixedFlag | (lmin << 16);
+                }
             }
         }
         hs.lut15[t] = e;
     }
+}
+
+// Canonical codewords (Sec. IV-B): the present symbols ordered by (length,
+// symbol) get consecutive codewords within each length, so a symbol's rank is
+// start[L] plus the number of smaller symbols of its length L, and its
+// codeword first[L] plus that number.  The block (1024 threads) walks the
+// alphabet in tiles of 1024 symbols: __match_any_sync groups a warp's lanes by
+// length, wc[warp][L] holds per-warp counts that are then scanned over the
+// warps of every length on top of the running totals of the earlier tiles.
+constexpr int kWcStride = 65;     // 64 lengths, padded against bank conflicts
+__device__ void canonical_assign(const uint8_t *lens, unsigned D, const unsigned *sstart,
+                                 const unsigned long long *sfirst, unsigned *wc, unsigned *run,
+                                 unsigned long long *code, uint16_t *sorted_sym)
+{
+    const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (unsigned i = threadIdx.x; i < 64; i += blockDim.x) run[i] = 0;
+    for (unsigned t0 = 0; t0 < D; t0 += 1024) {
+        for (unsigned i = threadIdx.x; i < 32 * kWcStride; i += blockDim.x) wc[i] = 0;
+        __syncthreads();
+        const unsigned s = t0 + threadIdx.x;
+        const unsigned L = s < D ? lens[s] : 0u;
+        const unsigned m = __match_any_sync(0xffffffffu, L);
+        const unsigned below = __popc(m & ((1u << lane) - 1));
+        if (below == 0) wc[w * kWcStride + L] = __popc(m);
+        __syncthreads();
+        for (unsigned Lq = w; Lq < 64; Lq += 32) {
+            const unsigned x = wc[lane * kWcStride + Lq];
+            unsigned y = x;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned z = __shfl_up_sync(0xffffffffu, y, o);
+                if ((int)lane >= o) y += z;
+            }
+            const unsigned base = run[Lq];
+            __syncwarp();
+            wc[lane * kWcStride + Lq] = base + y - x;
+            if (lane == 31) run[Lq] = base + y;
+        }
+        __syncthreads();
+        if (L) {
+            const unsigned k = wc[w * kWcStride + L] + below;
+            if (code) code[s] = sfirst[L] + k;
+            sorted_sym[sstart[L] + k] = (uint16_t)s;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One-block codebook for alphabets of at most kFusedMaxD symbols, everything
+// in shared memory: present symbols, their (frequency, symbol) order, the
+// two-queue code lengths in rounds (as merge_kernel), depths by pointer
+// jumping, canonical codewords.  Rounds that pick at most kWarpRound nodes,
+// the common case once the smallest weights are merged, run on warp 0 alone
+// without block barriers.
+constexpr unsigned kFusedMaxD = 8192;
+constexpr unsigned kWarpRound = 64;
+constexpr size_t kCodebookSmem = 16ull * kFusedMaxD            // keys + sort buffer / internal weights
+                                 + 2ull * 2 * kFusedMaxD         // parent / ancestor
+                                 + 2ull * kFusedMaxD             // depth
+                                 + kFusedMaxD                    // lengths by symbol
+                                 + 4ull * 32 * kWcStride;        // per-warp length counts
+
+// number of the first rem sorted values v(i) that are <= thr (v non-decreasing),
+// by warp ballot over the first 32 and binary search beyond
+template <typename F>
+__device__ __forceinline__ unsigned warp_count_le(F v, unsigned rem, unsigned long long thr, unsigned lane)
+{
+    const bool p = lane < rem && v(lane) <= thr;
+    const unsigned c = __popc(__ballot_sync(0xffffffffu, p));
+    if (c < 32 || rem <= 32) return c;
+    unsigned lo = 32, hi = rem;
+    while (lo < hi) { const unsigned m = (lo + hi) >> 1; if (v(m) <= thr) lo = m + 1; else hi = m; }
+    return lo;
+}
+
+// sorted ascending 8 keys in registers (odd-even transposition, 8 rounds)
+__device__ __forceinline__ void sort8(unsigned long long (&k)[8])
+{
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+#pragma unroll
+        for (int i = r & 1; i + 1 < 8; i += 2) {
+            const unsigned long long a = k[i], b = k[i + 1];
+            k[i] = a < b ? a : b;
+            k[i + 1] = a < b ? b : a;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024, 1) codebook_kernel(const unsigned long long *hist, unsigned D, HuffScratch hs)
+{
+    extern __shared__ __align__(16) unsigned char csm[];
+    unsigned long long *key = reinterpret_cast<unsigned long long *>(csm);   // [kFusedMaxD]
+    unsigned long long *aux = key + kFusedMaxD;                              // [kFusedMaxD]
+    uint16_t *par = reinterpret_cast<uint16_t *>(aux + kFusedMaxD);          // [2 kFusedMaxD]
+    uint16_t *dep = par + 2 * kFusedMaxD;                                    // [kFusedMaxD] as bytes x2
+    uint8_t *lens = reinterpret_cast<uint8_t *>(dep + kFusedMaxD);           // [kFusedMaxD]
+    unsigned *wc = reinterpret_cast<unsigned *>(lens + kFusedMaxD);          // [32 * kWcStride]
+    uint8_t *depb = reinterpret_cast<uint8_t *>(dep);                        // [2 kFusedMaxD]
+    __shared__ unsigned wcnt[32], wpre[32], cnt[64], run[64], sstart[64];
+    __shared__ unsigned long long sfirst[64];
+    __shared__ unsigned sh_n, sh_lo, sh_hi, s_ia, s_ib, s_nb, s_a, s_b;
+    __shared__ int s_done;
+    const unsigned tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const unsigned long long INF = ~0ULL;
+
+    // 1. present symbols as keys (frequency << 16) | s, in symbol order
+    if (tid == 0) { sh_n = 0; sh_lo = 0xFFFFFFFFu; sh_hi = 0; }
+    for (unsigned i = tid; i < 64; i += blockDim.x) cnt[i] = 0;
+    for (unsigned i = tid; i < D; i += blockDim.x) lens[i] = 0;
+    __syncthreads();
+    for (unsigned t0 = 0; t0 < D; t0 += 1024) {
+        const unsigned s = t0 + tid;
+        const unsigned long long f = s < D ? hist[s] : 0ULL;
+        const bool p = f != 0;
+        const unsigned ball = __ballot_sync(0xffffffffu, p);
+        if (lane == 0) wcnt[w] = __popc(ball);
+        __syncthreads();
+        if (w == 0) {
+            const unsigned v = wcnt[lane];
+            unsigned x = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+                if ((int)lane >= o) x += y;
+            }
+            wpre[lane] = x - v;
+        }
+        __syncthreads();
+        if (p) {
+            key[sh_n + wpre[w] + __popc(ball & ((1u << lane) - 1))] = (f << 16) | s;
+            atomicMin(&sh_lo, s);
+            atomicMax(&sh_hi, s);
+        }
+        __syncthreads();
+        if (tid == 0) sh_n += wpre[31] + wcnt[31];
+        __syncthreads();
+    }
+    const unsigned n = sh_n;
+    if (tid == 0) {
+        *hs.nsym = n;
+        *hs.s_lo = n ? sh_lo : 0;
+        *hs.s_hi = n ? sh_hi : 0;
+    }
+    if (n == 0) {
+        for (unsigned i = tid; i < D; i += blockDim.x) hs.len[i] = 0;
+        return;
+    }
+
+    // 2. sort the keys (unique) ascending: runs of 8 in registers, then
+    //    merge-path rounds in shared memory
+    unsigned P = 8;
+    while (P < n) P <<= 1;
+    unsigned rounds = 0;
+    for (unsigned r = 8; r < P; r <<= 1) rounds++;
+    {
+        unsigned long long *dst = (rounds & 1) ? aux : key;
+        unsigned long long k8[8];
+        const bool act = tid * 8 < P;
+        if (act) {
+#pragma unroll
+            for (int i = 0; i < 8; i++) k8[i] = (tid * 8 + i < n) ? key[tid * 8 + i] : INF;
+            sort8(k8);
+        }
+        __syncthreads();
+        if (act) {
+#pragma unroll
+            for (int i = 0; i < 8; i++) dst[tid * 8 + i] = k8[i];
+        }
+        __syncthreads();
+        unsigned long long *src = dst;
+        for (unsigned R = 8; R < P; R <<= 1) {
+            dst = (src == key) ? aux : key;
+            if (act) {
+                const unsigned o = tid * 8, pair = o / (2 * R), d = o % (2 * R);
+                const unsigned long long *A = src + pair * 2 * R, *B = A + R;
+                unsigned lo = d > R ? d - R : 0, hi = d < R ? d : R;
+                while (lo < hi) {
+                    const unsigned m = (lo + hi) >> 1;
+                    if (A[m] <= B[d - m - 1]) lo = m + 1; else hi = m;
+                }
+                unsigned i = lo, j = d - lo;
+#pragma unroll
+                for (int e = 0; e < 8; e++) {
+                    unsigned long long v;
+                    if (j >= R || (i < R && A[i] <= B[j])) { v = A[i]; i++; } else { v = B[j]; j++; }
+                    dst[o + e] = v;
+                }
+            }
+            __syncthreads();
+            src = dst;
+        }
+    }
+    // key[0, n) sorted; aux becomes the internal node weights
+    for (unsigned i = tid; i < n; i += blockDim.x) aux[i] = 0;
+    unsigned long long *intw = aux;
+    auto LW = [&](unsigned i) { return key[i] >> 16; };
+
+    // 3. two-queue merging in rounds
+    if (tid == 0) { s_ia = s_ib = s_nb = 0; s_done = 0; }
+    __syncthreads();
+    // s_done is read only between the barrier after warp 0 writes it and the
+    // next round's barriers, so every warp leaves the loop at the same barrier
+    while (n > 1) {
+        if (w == 0) {
+            unsigned ia = s_ia, ib = s_ib, nb = s_nb, a = 0, b = 0;
+            int state = 0;
+            while (true) {
+                const unsigned remA = n - ia, remB = nb - ib;
+                if (remA + remB <= 1) { state = 2; break; }
+                const unsigned long long wa = remA ? LW(ia) : INF, wb = remB ? intw[ib] : INF;
+                const unsigned long long wmin = wa < wb ? wa : wb;
+                const unsigned long long thr = wmin > (INF >> 1) ? INF : 2 * wmin;
+                a = warp_count_le([&](unsigned i) { return LW(ia + i); }, remA, thr, lane);
+                b = warp_count_le([&](unsigned i) { return intw[ib + i]; }, remB, thr, lane);
+                if (a + b < 2) {
+                    a = b = 0;
+                    for (int t = 0; t < 2; t++) {
+                        const bool la = (a < remA) && (b >= remB || LW(ia + a) <= intw[ib + b]);
+                        if (la) a++; else b++;
+                    }
+                } else if ((a + b) & 1) {
+                    if (a == 0) b--;
+                    else if (b == 0) a--;
+                    else if (intw[ib + b - 1] >= LW(ia + a - 1)) b--;
+                    else a--;
+                }
+                if (a + b > kWarpRound) { state = 1; break; }
+                for (unsigned i = lane; i < a + b; i += 32) {
+                    unsigned long long wt;
+                    unsigned q, node;
+                    if (i < a) {
+                        wt = LW(ia + i);
+                        unsigned lo = 0, hi = b;     // internal weights < wt come first
+                        while (lo < hi) { const unsigned m = (lo + hi) >> 1; if (intw[ib + m] < wt) lo = m + 1; else hi = m; }
+                        q = i + lo;
+                        node = ia + i;
+                    } else {
+                        const unsigned j = i - a;
+                        wt = intw[ib + j];
+                        unsigned lo = 0, hi = a;     // leaves <= wt come first
+                        while (lo < hi) { const unsigned m = (lo + hi) >> 1; if (LW(ia + m) <= wt) lo = m + 1; else hi = m; }
+                        q = j + lo;
+                        node = n + ib + j;
+                    }
+                    const unsigned t = nb + (q >> 1);
+                    atomicAdd(&intw[t], wt);
+                    par[node] = (uint16_t)(n + t);
+                }
+                __syncwarp();
+                ia += a; ib += b; nb += (a + b) >> 1;
+            }
+            if (lane == 0) {
+                s_ia = ia; s_ib = ib; s_nb = nb; s_a = a; s_b = b;
+                s_done = state == 2;
+            }
+        }
+        __syncthreads();
+        if (s_done) break;
+        {
+            const unsigned ia = s_ia, ib = s_ib, nb = s_nb, a = s_a, b = s_b;
+            for (unsigned i = tid; i < a + b; i += blockDim.x) {
+                unsigned long long wt;
+                unsigned q, node;
+                if (i < a) {
+                    wt = LW(ia + i);
+                    q = i + count_lt(intw + ib, b, wt);
+                    node = ia + i;
+                } else {
+                    const unsigned j = i - a;
+                    wt = intw[ib + j];
+                    unsigned lo = 0, hi = a;
+                    while (lo < hi) { const unsigned m = (lo + hi) >> 1; if (LW(ia + m) <= wt) lo = m + 1; else hi = m; }
+                    q = j + lo;
+                    node = n + ib + j;
+                }
+                const unsigned t = nb + (q >> 1);
+                atomicAdd(&intw[t], wt);
+                par[node] = (uint16_t)(n + t);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) { s_ia += s_a; s_ib += s_b; s_nb += (s_a + s_b) >> 1; }
+        __syncthreads();
+    }
+
+    // 4. depth of every node by pointer jumping (parents have larger indices)
+    const unsigned total = 2 * n - 1, root = total - 1;
+    for (unsigned i = tid; i < total; i += blockDim.x) {
+        if (i == root) par[i] = (uint16_t)root;
+        depb[i] = i == root ? 0 : 1;
+    }
+    __syncthreads();
+    for (int step = 0; step < 7; step++) {
+        uint16_t na[16];
+        uint8_t nd[16];
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            const unsigned i = tid + 1024u * k;
+            if (i < total) {
+                const unsigned a = par[i];
+                const unsigned dd = (unsigned)depb[i] + depb[a];
+                nd[k] = (uint8_t)(dd > 255 ? 255 : dd);
+                na[k] = par[a];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            const unsigned i = tid + 1024u * k;
+            if (i < total) { par[i] = na[k]; depb[i] = nd[k]; }
+        }
+        __syncthreads();
+    }
+
+    // 5. code lengths, per-length counts, canonical tables and codewords
+    for (unsigned i = tid; i < n; i += blockDim.x) {
+        unsigned L = n == 1 ? 1u : depb[i];
+        if (n > 1 && (par[i] != root || L > (unsigned)kMaxCodeLen || L == 0)) {
+            atomicExch(hs.status, (unsigned)DS_LENGTH);
+            L = kMaxCodeLen;
+        }
+        lens[(unsigned)(key[i] & 0xFFFFu)] = (uint8_t)L;
+        atomicAdd(&cnt[L], 1u);
+    }
+    __syncthreads();
+    for (unsigned i = tid; i < D; i += blockDim.x) hs.len[i] = lens[i];
+    if (tid == 0) length_tables(hs, cnt);
+    __syncthreads();
+    if (tid < 64) { sstart[tid] = hs.start[tid]; sfirst[tid] = hs.first[tid]; }
+    __syncthreads();
+    canonical_assign(lens, D, sstart, sfirst, wc, run, hs.code, hs.sorted_sym);
+}
+
+// Decoder tables from the code lengths of symbols s_lo..s_hi (every other
+// symbol of the alphabet absent), one block of 1024 threads: counts,
+// canonical tables, the (length, symbol) order of the symbols.
+__global__ void __launch_bounds__(1024, 1) dec_tables_kernel(const uint8_t *lenb, unsigned s_lo, unsigned s_hi,
+                                                             unsigned D, HuffScratch hs)
+{
+    extern __shared__ __align__(16) unsigned char tsm[];
+    unsigned *wc = reinterpret_cast<unsigned *>(tsm);                        // [32 * kWcStride]
+    uint8_t *lens = tsm + 4 * 32 * kWcStride;                                // [D]
+    __shared__ unsigned cnt[64], run[64], sstart[64], nsum;
+    __shared__ unsigned long long sfirst[64];
+    const unsigned tid = threadIdx.x;
+    for (unsigned i = tid; i < 64; i += blockDim.x) cnt[i] = 0;
+    if (tid == 0) nsum = 0;
+    __syncthreads();
+    unsigned mine = 0;
+    for (unsigned s = tid; s < D; s += blockDim.x) {
+        unsigned L = (s >= s_lo && s <= s_hi) ? lenb[s - s_lo] : 0u;
+        if (L > (unsigned)kMaxCodeLen) { atomicExch(hs.status, (unsigned)DS_FORMAT); L = 0; }
+        lens[s] = (uint8_t)L;
+        if (L) { atomicAdd(&cnt[L], 1u); mine++; }
+    }
+    mine = warp_sum(mine);
+    if ((tid & 31) == 0 && mine) atomicAdd(&nsum, mine);
+    __syncthreads();
+    if (tid == 0) {
+        *hs.nsym = nsum;
+        if (nsum == 0) atomicExch(hs.status, (unsigned)DS_FORMAT);
+        length_tables(hs, cnt);
+    }
+    __syncthreads();
+    if (tid < 64) { sstart[tid] = hs.start[tid]; sfirst[tid] = hs.first[tid]; }
+    __syncthreads();
+    canonical_assign(lens, D, sstart, sfirst, wc, run, nullptr, hs.sorted_sym);
 }
 
 // ---------------------------------------------------------------------------
@@ -1031,6 +1368,11 @@ cudaError_t set_attrs()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemKeys * 16);
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCodebookSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(dec_tables_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 4 * 32 * kWcStride + 65536);
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(enc_write_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(enc_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
@@ -1052,7 +1394,7 @@ size_t huff_scratch_bytes(unsigned int D)
     add(8 * d); add(8 * d);                            // leafw, intw
     add(4); add(8 * 64); add(4 * 64); add(4 * 64);     // nsym, first, count, start
     add(d); add(8 * d); add(2 * d); add(4u << kLenBits);
-    add(1u << kLenBits); add(8 * 64);
+    add(8 * 64);
     return b;
 }
 
@@ -1078,7 +1420,6 @@ void huff_scratch_carve(void *base, unsigned int D, Scalars *sc, HuffScratch *hs
     hs->code = (unsigned long long *)take(8 * d);
     hs->sorted_sym = (uint16_t *)take(2 * d);
     hs->lut15 = (uint32_t *)take(4u << kLenBits);
-    hs->len16 = (uint8_t *)take(1u << kLenBits);
     hs->lim = (unsigned long long *)take(8 * 64);
     hs->status = &sc->status;
     hs->s_lo = &sc->s_lo;
@@ -1090,6 +1431,11 @@ cudaError_t launch_codebook(const unsigned long long *hist, unsigned int D, cons
 {
     cudaError_t e = set_attrs();
     if (e != cudaSuccess) return e;
+    if (D <= kFusedMaxD) {
+        codebook_kernel<<<1, 1024, kCodebookSmem, s>>>(hist, D, hs);
+        count_launch();
+        return cudaGetLastError();
+    }
     compact_kernel<<<1, 1024, 0, s>>>(hist, nullptr, D, hs.keys, hs.nsym, hs.s_lo, hs.s_hi);
     rank_kernel<<<kRankBlocks, 256, kSmemKeys * 8, s>>>(hs.keys, hs.nsym, hs.sorted, nullptr);
     merge_kernel<<<1, 1024, kSmemKeys * 16, s>>>(hs, D);
@@ -1099,20 +1445,14 @@ cudaError_t launch_codebook(const unsigned long long *hist, unsigned int D, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_decode_tables(const uint8_t *len, unsigned int D, const HuffScratch &hs,
-                                 cudaStream_t s)
+cudaError_t launch_decode_tables(const uint8_t *lenb, unsigned int s_lo, unsigned int s_hi, unsigned int D,
+                                 const HuffScratch &hs, cudaStream_t s)
 {
     cudaError_t e = set_attrs();
     if (e != cudaSuccess) return e;
-    compact_kernel<<<1, 1024, 0, s>>>(nullptr, len, D, hs.keys2, hs.nsym, nullptr, nullptr);
-    length_count_kernel<<<1, 1024, 0, s>>>(hs);
-    rank_kernel<<<kRankBlocks, 256, kSmemKeys * 8, s>>>(hs.keys2, hs.nsym, nullptr, hs.rank);
-    assign_kernel<<<64, 256, 0, s>>>(hs);
-    e = cudaMemsetAsync(hs.len16, 0, 1u << kLenBits, s);
-    if (e != cudaSuccess) return e;
-    len16_kernel<<<64, 256, 0, s>>>(hs);
+    dec_tables_kernel<<<1, 1024, 4 * 32 * kWcStride + D, s>>>(lenb, s_lo, s_hi, D, hs);
     lut15_kernel<<<(1u << kLenBits) / 256, 256, 0, s>>>(hs);
-    count_launch(6);
+    count_launch(2);
     return cudaGetLastError();
 }
 

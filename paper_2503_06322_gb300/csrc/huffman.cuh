@@ -38,7 +38,6 @@ struct HuffScratch {
     unsigned long long *code;     // [D]
     uint16_t *sorted_sym;         // [D]
     uint32_t *lut15;              // [1 << kLenBits] symbol | length << 16 of a 15-bit prefix (0: longer)
-    uint8_t *len16;               // [1 << kLenBits] code length of a 15-bit prefix (0: longer)
     unsigned long long *lim;      // [64] left-justified upper limit of the codes of each length
     unsigned int *status;         // -> Scalars::status
     unsigned int *s_lo, *s_hi;    // -> Scalars
@@ -49,9 +48,10 @@ void huff_scratch_carve(void *base, unsigned int D, Scalars *sc, HuffScratch *hs
 // Codebook from a histogram hist[D] (two-queue lengths, canonical codes).
 cudaError_t launch_codebook(const unsigned long long *hist, unsigned int D, const HuffScratch &hs,
                             cudaStream_t s);
-// Canonical tables + LUT from given lengths len[D] (decoder side).
-cudaError_t launch_decode_tables(const uint8_t *len, unsigned int D, const HuffScratch &hs,
-                                 cudaStream_t s);
+// Canonical tables + LUT from the code lengths lenb[0 .. s_hi - s_lo] of the
+// symbols s_lo..s_hi (device bytes; every other symbol absent), decoder side.
+cudaError_t launch_decode_tables(const uint8_t *lenb, unsigned int s_lo, unsigned int s_hi, unsigned int D,
+                                 const HuffScratch &hs, cudaStream_t s);
 
 // Encoder.  Layout of the destination: chunk table at chunk_out, bitstream at
 // words (both device pointers, possibly inside a container whose offsets are

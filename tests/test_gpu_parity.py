@@ -101,7 +101,7 @@ def test_codes_bit_exact_on_identical_inputs(oracle, H, dev, shape, tol, D, dtyp
 @pytest.mark.parametrize("n,D,K,spread", [(20000, 8192, 1024, 300.0), (1, 16, 128, 1.0),
                                           (777, 256, 128, 0.0), (300000, 65536, 1024, 2000.0),
                                           (65536, 8192, 4096, 3.0), (5000, 64, 256, 40.0),
-                                          (100000, 8192, 512, 500.0)])
+                                          (100000, 8192, 512, 500.0), (300000, 8192, 1024, 3000.0)])
 def test_huffman_bit_exact(oracle, H, dev, n, D, K, spread):
     rng = np.random.default_rng(n)
     sym = np.clip(np.round(rng.laplace(D // 2, spread + 1e-9, size=n)), 1, D - 1).astype(np.uint16)
@@ -118,6 +118,21 @@ def test_huffman_bit_exact(oracle, H, dev, n, D, K, spread):
     ct = torch.from_numpy(chunk_ref.view(np.int64).copy()).to(dev)
     lt = torch.from_numpy(ln_ref).to(dev)
     dec = H.hpdr_huffman_decode(wt, bits_ref, ct, n, lt, D=D, K=K)
+    assert np.array_equal(dec.cpu().numpy().view(np.uint16), sym)
+
+
+@pytest.mark.parametrize("D,reps", [(8192, 3), (4096, 1), (16, 7)])
+def test_huffman_equal_frequencies(oracle, H, dev, D, reps):
+    """Every symbol equally frequent: all weights tie, so the order of the
+    leaves and the two-queue tie rule decide every pick."""
+    sym = np.tile(np.arange(D, dtype=np.uint16), reps)
+    K = 1024
+    ln_ref = oracle.code_lengths(oracle.histogram(sym, D))
+    words_ref, chunk_ref, bits_ref = oracle.encode(sym, ln_ref, K=K)
+    ln, chunk, words, bits = H.hpdr_huffman_encode(torch.from_numpy(sym.view(np.int16)).to(dev), D=D, K=K)
+    assert np.array_equal(ln.cpu().numpy(), ln_ref) and bits == bits_ref
+    assert np.array_equal(words.cpu().numpy().view(np.uint32), words_ref)
+    dec = H.hpdr_huffman_decode(words, bits, chunk, sym.size, ln, D=D, K=K)
     assert np.array_equal(dec.cpu().numpy().view(np.uint16), sym)
 
 
