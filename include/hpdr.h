@@ -223,6 +223,76 @@ hpdr_status hpdr_compress_host_streamed(hpdr_ctx *ctx, const void *h_in, hpdr_dt
 hpdr_status hpdr_decompress_host_streamed(hpdr_ctx *ctx, const void *h_in, size_t in_bytes, void *h_out,
                                           size_t out_capacity);
 
+/* Adaptive chunk sizing of the host-device pipeline (Sec. V-C, Alg. 4).
+ * Model of the pipeline (all sizes in bytes, throughputs in bytes/s):
+ *   Phi(C)   = alpha * C + beta  for C <  c_threshold
+ *            = gamma             for C >= c_threshold
+ *              compression throughput on a chunk of C bytes;
+ *   Theta(t) = t * h2d: bytes the host-to-device copy moves in t seconds.
+ * Alg. 4 sizes the next chunk so that its copy takes as long as the
+ * compression of the current one:
+ *   C_next = min(Theta(C_curr / Phi(C_curr)), C_limit, bytes left). */
+typedef struct hpdr_pipeline_model {
+    double alpha;        /* 1/s */
+    double beta;         /* bytes/s */
+    double gamma;        /* bytes/s, saturated throughput */
+    double c_threshold;  /* bytes */
+    double h2d;          /* bytes/s */
+} hpdr_pipeline_model;
+
+/* Fit of Phi from n >= 1 profiled chunks (chunk_bytes[i] > 0, throughput[i]
+ * > 0 bytes/s, any order), as Sec. V-C describes: gamma is the throughput of
+ * the largest chunk; walking to smaller chunks, a chunk belongs to the
+ * saturated range while its throughput is at least (1 - f) * gamma
+ * (0 <= f < 1); c_threshold is the smallest chunk of that range; alpha and
+ * beta are the least-squares line through the smaller chunks (one smaller
+ * chunk: the line through it and (c_threshold, gamma); none: alpha = 0,
+ * beta = gamma).  h2d is copied into the model.  Host only, no device work.
+ * Errors: HPDR_ERR_ARG. */
+hpdr_status hpdr_pipeline_fit(const double *chunk_bytes, const double *throughput, int n, double f, double h2d,
+                              hpdr_pipeline_model *model);
+
+/* Chunk plan of Alg. 4 for a field of n0 planes of plane_bytes each, cut
+ * along its first dimension: the first chunk holds c_init bytes, every next
+ * one min(Theta(C / Phi(C)), c_limit, what is left) for the previous chunk's
+ * C (c_limit 0: no limit).  Sizes are rounded down to whole planes, at least
+ * two planes per chunk, and a single plane left at the end joins the last
+ * chunk.  Writes min(count, cap) plane counts to planes[] and returns the
+ * count (0 on bad arguments: n0 < 2, plane_bytes 0, a model with gamma or
+ * h2d <= 0).  Host only, no device work. */
+size_t hpdr_pipeline_plan(const hpdr_pipeline_model *model, size_t n0, size_t plane_bytes, size_t c_init,
+                          size_t c_limit, size_t *planes, size_t cap);
+
+/* Capacity that always holds the streamed container of a field cut into
+ * n_chunks chunks of planes[i] planes (sum = dims[0]) along dimension 0.
+ * 0 on bad arguments.  Host only. */
+size_t hpdr_streamed_bound(int ndim, const size_t *dims, hpdr_dtype dtype, const hpdr_config *cfg,
+                           const size_t *planes, size_t n_chunks);
+
+/* Profiling that builds the model on the data itself (Sec. V-C fits Phi
+ * per dataset and error bound): the first planes of the host field h_in are
+ * copied to the device once (timed: h2d), then device-resident compressions
+ * of the first chunk_bytes[i] bytes (whole planes, at least two) are timed
+ * with CUDA events, reps times each after one warm-up, keeping the fastest;
+ * the pairs are fitted as hpdr_pipeline_fit with f.  Uses the context's
+ * pipeline buffers.  Synchronous.  Errors as hpdr_compress, HPDR_ERR_ARG for
+ * n < 1 or reps < 1. */
+hpdr_status hpdr_pipeline_profile(hpdr_ctx *ctx, const void *h_in, hpdr_dtype dtype, int ndim, const size_t *dims,
+                                  double tol, hpdr_tol_kind tol_kind, hpdr_mode mode, const hpdr_config *cfg,
+                                  const size_t *chunk_bytes, int n, int reps, double f,
+                                  hpdr_pipeline_model *model);
+
+/* hpdr_compress_host_streamed with the chunk plan of hpdr_pipeline_plan
+ * (model, c_init, c_limit) instead of equal slabs: Alg. 4.  The container is
+ * the same streamed format (hpdr_decompress_host_streamed reads it); each
+ * chunk's container equals hpdr_compress of the same planes.  h_out needs
+ * hpdr_streamed_bound of the plan.  Synchronous.  Errors as
+ * hpdr_compress_host_streamed. */
+hpdr_status hpdr_compress_host_adaptive(hpdr_ctx *ctx, const void *h_in, hpdr_dtype dtype, int ndim,
+                                        const size_t *dims, double tol, hpdr_tol_kind tol_kind, hpdr_mode mode,
+                                        const hpdr_config *cfg, const hpdr_pipeline_model *model, size_t c_init,
+                                        size_t c_limit, void *h_out, size_t out_capacity, size_t *out_bytes);
+
 /* Decomposition for callers that cannot allocate device memory on their call
  * path -- for example code running while a stream is captured into a CUDA
  * graph (allocation calls are not permitted in a global-mode capture), or a

@@ -1338,7 +1338,9 @@ cudaError_t launch_solves(const LevelGeom<T> &g, T *b, T *vc, int sign, cudaStre
         const DimTables<T> &d = g.dim[k];
         if (!(d.m > 1)) continue;
         int sg = (k == last) ? sign : 0;
-        if (k < 2 && sg == 0 && kSolveStream) {
+        // the streaming sweep keeps the three factor tables in shared memory
+        // (at most the default 48 KB); longer lines take the strided kernel
+        if (k < 2 && sg == 0 && kSolveStream && 3 * (size_t)d.mc * sizeof(T) <= 48 * 1024) {
             // dim 0: lines (j1, j2), step c1*c2; dim 1: lines (j0, j2), step c2
             const long long st = (k == 0) ? c1 * c2 : c2;
             const long long outer = (k == 0) ? c1 : c0;
@@ -1371,7 +1373,10 @@ cudaError_t launch_solves(const LevelGeom<T> &g, T *b, T *vc, int sign, cudaStre
             long long nlines = c0 * c1;
             int pitch = n | 1;
             size_t rowbytes = (size_t)pitch * sizeof(T);
-            int rows = (int)std::min<size_t>(64, (90 * 1024) / rowbytes);
+            // the row tile and the three factor tables share the 100 KB limit
+            const size_t tab = 3 * (size_t)n * sizeof(T);
+            const size_t budget = std::min<size_t>(90 * 1024, tab < 100 * 1024 ? 100 * 1024 - tab : 0);
+            int rows = (int)std::min<size_t>(64, budget / rowbytes);
             if (rows < 1) {
                 solve_strided_kernel<T><<<(unsigned)((nlines + 255) / 256), 256, 0, s>>>(
                     b, n, 1, nlines, d.sub, d.cp, d.inv_den, vc, sg);

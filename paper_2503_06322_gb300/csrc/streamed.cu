@@ -1,7 +1,7 @@
 // streamed.cu -- compression of host-resident fields in slabs, with host-to-
 // device copies, compression and device-to-host copies overlapped on three
-// CUDA streams (the host-device pipeline of Sec. V, Fig. 7 and Alg. 4 with a
-// fixed slab size).
+// CUDA streams (the host-device pipeline of Sec. V-B, Fig. 7 and Alg. 4),
+// with fixed slabs or with the adaptive chunk sizes of Sec. V-C.
 //
 // Slab i uses device buffers I[i%2] (input) and O[i%2] (output): two buffer
 // pairs serve three stages because slab i+2 may only enter a buffer pair
@@ -14,8 +14,11 @@
 //   0 "HPDS"   4 u32 version (1)   8 u32 number of slabs   12 u32 dtype
 //   16 u64 dims[3] (unused dims hold 1)   40 u32 ndim   44..63 zero
 //   64 per slab: u64 first plane, u64 planes, u64 byte offset, u64 bytes
-//   then the slab containers (format v1), each at a 16-byte boundary.
+//   then the slab containers (format v3), each at a 16-byte boundary.
+#include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <utility>
 #include <vector>
 #include "internal.cuh"
 
@@ -113,24 +116,15 @@ void destroy_stream_res(hpdr_ctx *ctx)
 }
 }  // namespace hpdr
 
-extern "C" hpdr_status hpdr_compress_host_streamed(hpdr_ctx *ctx, const void *h_in, hpdr_dtype dtype, int ndim,
-                                                   const size_t *dims, double tol, hpdr_tol_kind tol_kind,
-                                                   hpdr_mode mode, const hpdr_config *cfg, size_t slab_bytes,
-                                                   void *h_out, size_t out_capacity, size_t *out_bytes)
+namespace {
+
+// The pipeline over the slabs first[i] .. first[i] + count[i] - 1 (planes of
+// plane bytes along dimension 0): fixed slabs or the chunks of Alg. 4.
+hpdr_status compress_slabs(hpdr_ctx *ctx, const void *h_in, hpdr_dtype dtype, int ndim, const size_t *dims,
+                           double tol, hpdr_tol_kind tol_kind, hpdr_mode mode, const hpdr_config *cfg,
+                           const std::vector<size_t> &first, const std::vector<size_t> &count, size_t plane,
+                           void *h_out, size_t out_capacity, size_t *out_bytes)
 {
-    if (!ctx || !h_in || !h_out || !out_bytes || !dims || ndim < 1 || ndim > 3) return HPDR_ERR_ARG;
-    if (dtype != HPDR_F32 && dtype != HPDR_F64) return HPDR_ERR_ARG;
-    for (int k = 0; k < ndim; k++) if (dims[k] < 2) return HPDR_ERR_ARG;
-    int dev_prev = -1;
-    cudaGetDevice(&dev_prev);
-    if (dev_prev != ctx->device) cudaSetDevice(ctx->device);
-    struct Restore { int d, p; ~Restore() { if (d != p) cudaSetDevice(p); } } restore{ctx->device, dev_prev};
-    const size_t esz = dtype == HPDR_F64 ? 8 : 4;
-    size_t plane = esz;
-    for (int k = 1; k < ndim; k++) plane *= dims[k];
-    std::vector<size_t> first, count;
-    if (ndim == 1) { first.push_back(0); count.push_back(dims[0]); }
-    else split_slabs(dims[0], plane, slab_bytes ? slab_bytes : (size_t(256) << 20), first, count);
     const size_t ns = first.size();
     size_t maxp = 0;
     for (size_t c : count) maxp = std::max(maxp, c);
@@ -227,6 +221,30 @@ extern "C" hpdr_status hpdr_compress_host_streamed(hpdr_ctx *ctx, const void *h_
     return HPDR_OK;
 }
 
+}  // namespace
+
+extern "C" hpdr_status hpdr_compress_host_streamed(hpdr_ctx *ctx, const void *h_in, hpdr_dtype dtype, int ndim,
+                                                   const size_t *dims, double tol, hpdr_tol_kind tol_kind,
+                                                   hpdr_mode mode, const hpdr_config *cfg, size_t slab_bytes,
+                                                   void *h_out, size_t out_capacity, size_t *out_bytes)
+{
+    if (!ctx || !h_in || !h_out || !out_bytes || !dims || ndim < 1 || ndim > 3) return HPDR_ERR_ARG;
+    if (dtype != HPDR_F32 && dtype != HPDR_F64) return HPDR_ERR_ARG;
+    for (int k = 0; k < ndim; k++) if (dims[k] < 2) return HPDR_ERR_ARG;
+    int dev_prev = -1;
+    cudaGetDevice(&dev_prev);
+    if (dev_prev != ctx->device) cudaSetDevice(ctx->device);
+    struct Restore { int d, p; ~Restore() { if (d != p) cudaSetDevice(p); } } restore{ctx->device, dev_prev};
+    const size_t esz = dtype == HPDR_F64 ? 8 : 4;
+    size_t plane = esz;
+    for (int k = 1; k < ndim; k++) plane *= dims[k];
+    std::vector<size_t> first, count;
+    if (ndim == 1) { first.push_back(0); count.push_back(dims[0]); }
+    else split_slabs(dims[0], plane, slab_bytes ? slab_bytes : (size_t(256) << 20), first, count);
+    return compress_slabs(ctx, h_in, dtype, ndim, dims, tol, tol_kind, mode, cfg, first, count, plane, h_out,
+                          out_capacity, out_bytes);
+}
+
 extern "C" hpdr_status hpdr_decompress_host_streamed(hpdr_ctx *ctx, const void *h_in, size_t in_bytes, void *h_out,
                                                      size_t out_capacity)
 {
@@ -307,4 +325,231 @@ extern "C" hpdr_status hpdr_decompress_host_streamed(hpdr_ctx *ctx, const void *
     if (cudaMemcpy(&err, r->err, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return HPDR_ERR_CUDA;
     if (err) return hpdr::status_of_device(err);
     return HPDR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Adaptive chunk sizing (Sec. V-C, Alg. 4).  The chunk sizes depend on the
+// model only, so the whole plan is computed before the first copy and then
+// run by the same three-stream pipeline as the fixed slabs.
+
+namespace {
+
+// Phi(C); a fitted line may fall to zero or below for chunks smaller than
+// every profiled one, where the throughput is floored at 1e-6 gamma
+double phi(const hpdr_pipeline_model &m, double c)
+{
+    const double p = c < m.c_threshold ? m.alpha * c + m.beta : m.gamma;
+    const double lo = 1e-6 * m.gamma;
+    return p > lo ? p : lo;
+}
+
+bool model_ok(const hpdr_pipeline_model *m)
+{
+    return m && std::isfinite(m->alpha) && std::isfinite(m->beta) && std::isfinite(m->gamma) && m->gamma > 0 &&
+           std::isfinite(m->h2d) && m->h2d > 0 && std::isfinite(m->c_threshold) && m->c_threshold >= 0;
+}
+
+void plan_chunks(const hpdr_pipeline_model &m, size_t n0, size_t plane_bytes, size_t c_init, size_t c_limit,
+                 std::vector<size_t> &planes)
+{
+    const size_t lim = c_limit ? std::max<size_t>(2, c_limit / plane_bytes) : n0;
+    auto take = [&](size_t p, size_t rest) {
+        p = std::max<size_t>(2, std::min(p, lim));
+        if (p > rest) p = rest;
+        if (rest - p == 1) p++;        // no chunk of a single plane
+        return p;
+    };
+    size_t cur = take(c_init / plane_bytes, n0);
+    planes.push_back(cur);
+    size_t rest = n0 - cur;
+    while (rest > 0) {
+        const double c = (double)cur * (double)plane_bytes;
+        const double t = c / phi(m, c);                           // compression of the current chunk
+        // Theta(t) in planes, rounded down; rounding errors below a millionth of
+        // a plane do not take a plane away
+        const double np = t * m.h2d / (double)plane_bytes + 1e-6;
+        cur = take(np >= (double)n0 ? n0 : (size_t)np, rest);
+        planes.push_back(cur);
+        rest -= cur;
+    }
+}
+
+hpdr_status check_field_args(hpdr_ctx *ctx, const void *h_in, hpdr_dtype dtype, int ndim, const size_t *dims)
+{
+    if (!ctx || !h_in || !dims || ndim < 1 || ndim > 3) return HPDR_ERR_ARG;
+    if (dtype != HPDR_F32 && dtype != HPDR_F64) return HPDR_ERR_ARG;
+    for (int k = 0; k < ndim; k++) if (dims[k] < 2) return HPDR_ERR_ARG;
+    return HPDR_OK;
+}
+
+size_t plane_bytes_of(hpdr_dtype dtype, int ndim, const size_t *dims)
+{
+    size_t plane = dtype == HPDR_F64 ? 8 : 4;
+    for (int k = 1; k < ndim; k++) plane *= dims[k];
+    return plane;
+}
+
+}  // namespace
+
+extern "C" hpdr_status hpdr_pipeline_fit(const double *chunk_bytes, const double *throughput, int n, double f,
+                                         double h2d, hpdr_pipeline_model *model)
+{
+    if (!chunk_bytes || !throughput || !model || n < 1 || !(f >= 0.0 && f < 1.0) || !(h2d > 0.0) ||
+        !std::isfinite(h2d))
+        return HPDR_ERR_ARG;
+    std::vector<std::pair<double, double>> v((size_t)n);
+    for (int i = 0; i < n; i++) {
+        if (!(chunk_bytes[i] > 0.0) || !(throughput[i] > 0.0) || !std::isfinite(chunk_bytes[i]) ||
+            !std::isfinite(throughput[i]))
+            return HPDR_ERR_ARG;
+        v[(size_t)i] = {chunk_bytes[i], throughput[i]};
+    }
+    std::sort(v.begin(), v.end());
+    const double gamma = v.back().second;
+    size_t k = v.size() - 1;      // first chunk of the saturated range
+    while (k > 0 && v[k - 1].second >= (1.0 - f) * gamma) k--;
+    const double cth = v[k].first;
+    double alpha = 0.0, beta = gamma;
+    if (k >= 2) {
+        double mx = 0, my = 0;
+        for (size_t i = 0; i < k; i++) { mx += v[i].first; my += v[i].second; }
+        mx /= (double)k;
+        my /= (double)k;
+        double sxx = 0, sxy = 0;
+        for (size_t i = 0; i < k; i++) {
+            sxx += (v[i].first - mx) * (v[i].first - mx);
+            sxy += (v[i].first - mx) * (v[i].second - my);
+        }
+        alpha = sxx > 0 ? sxy / sxx : 0.0;
+        beta = my - alpha * mx;
+    } else if (k == 1) {
+        alpha = cth > v[0].first ? (gamma - v[0].second) / (cth - v[0].first) : 0.0;
+        beta = v[0].second - alpha * v[0].first;
+    }
+    model->alpha = alpha;
+    model->beta = beta;
+    model->gamma = gamma;
+    model->c_threshold = cth;
+    model->h2d = h2d;
+    return HPDR_OK;
+}
+
+extern "C" size_t hpdr_pipeline_plan(const hpdr_pipeline_model *model, size_t n0, size_t plane_bytes, size_t c_init,
+                                     size_t c_limit, size_t *planes, size_t cap)
+{
+    if (!model_ok(model) || n0 < 2 || plane_bytes == 0 || (cap && !planes)) return 0;
+    std::vector<size_t> pl;
+    plan_chunks(*model, n0, plane_bytes, c_init, c_limit, pl);
+    for (size_t i = 0; i < pl.size() && i < cap; i++) planes[i] = pl[i];
+    return pl.size();
+}
+
+extern "C" size_t hpdr_streamed_bound(int ndim, const size_t *dims, hpdr_dtype dtype, const hpdr_config *cfg,
+                                      const size_t *planes, size_t n_chunks)
+{
+    if (!dims || !planes || n_chunks == 0 || ndim < 1 || ndim > 3) return 0;
+    size_t total = (kStreamHdr + 32 * n_chunks + 15) & ~size_t(15), sum = 0;
+    for (size_t i = 0; i < n_chunks; i++) {
+        if (planes[i] < 2) return 0;
+        const size_t d[3] = {planes[i], ndim > 1 ? dims[1] : 1, ndim > 2 ? dims[2] : 1};
+        const size_t b = hpdr_compress_bound(ndim, d, dtype, cfg);
+        if (!b) return 0;
+        total += (b + 15) & ~size_t(15);
+        sum += planes[i];
+    }
+    return sum == dims[0] ? total : 0;
+}
+
+extern "C" hpdr_status hpdr_pipeline_profile(hpdr_ctx *ctx, const void *h_in, hpdr_dtype dtype, int ndim,
+                                             const size_t *dims, double tol, hpdr_tol_kind tol_kind, hpdr_mode mode,
+                                             const hpdr_config *cfg, const size_t *chunk_bytes, int n, int reps,
+                                             double f, hpdr_pipeline_model *model)
+{
+    hpdr_status st = check_field_args(ctx, h_in, dtype, ndim, dims);
+    if (st != HPDR_OK) return st;
+    if (!chunk_bytes || n < 1 || reps < 1 || !model || !(f >= 0.0 && f < 1.0)) return HPDR_ERR_ARG;
+    int dev_prev = -1;
+    cudaGetDevice(&dev_prev);
+    if (dev_prev != ctx->device) cudaSetDevice(ctx->device);
+    struct Restore { int d, p; ~Restore() { if (d != p) cudaSetDevice(p); } } restore{ctx->device, dev_prev};
+    const size_t plane = plane_bytes_of(dtype, ndim, dims), n0 = dims[0];
+    std::vector<size_t> pl((size_t)n);
+    size_t maxp = 0;
+    for (int i = 0; i < n; i++) {
+        pl[(size_t)i] = std::min(n0, std::max<size_t>(2, chunk_bytes[i] / plane));
+        maxp = std::max(maxp, pl[(size_t)i]);
+    }
+    const size_t sd[3] = {maxp, ndim > 1 ? dims[1] : 1, ndim > 2 ? dims[2] : 1};
+    const size_t bound = hpdr_compress_bound(ndim, sd, dtype, cfg);
+    if (!bound) return HPDR_ERR_ARG;
+    StreamRes *r = nullptr;
+    st = ensure_res(ctx, r, maxp * plane, bound);
+    if (st != HPDR_OK) return st;
+    if (ensure_pairs(r, 1) != HPDR_OK) return HPDR_ERR_NOMEM;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return HPDR_ERR_CUDA;
+    }
+    struct Ev { cudaEvent_t a, b; ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); } } ev{e0, e1};
+    cudaStream_t sH = r->s[0], sC = r->s[1];
+    float ms = 0.f;
+    // Theta: the largest chunk is copied in once untimed (the first touch of a
+    // host range can be several times slower than the steady state), then
+    // the fastest of three timed copies of its first 256 MiB (or less; the
+    // same bytes to the same place) gives h2d
+    if (cudaMemcpyAsync(r->buf[0], h_in, maxp * plane, cudaMemcpyHostToDevice, sH) != cudaSuccess)
+        return HPDR_ERR_CUDA;
+    const size_t tb = std::min(maxp * plane, size_t(256) << 20);
+    float best_copy = 1e30f;
+    for (int rep = 0; rep < 3; rep++) {
+        if (cudaEventRecord(e0, sH) != cudaSuccess ||
+            cudaMemcpyAsync(r->buf[0], h_in, tb, cudaMemcpyHostToDevice, sH) != cudaSuccess ||
+            cudaEventRecord(e1, sH) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+            return HPDR_ERR_CUDA;
+        best_copy = std::min(best_copy, ms);
+    }
+    const double h2d = (double)tb / (std::max(best_copy, 1e-3f) * 1e-3);
+    std::vector<double> cb((size_t)n), tp((size_t)n);
+    for (int i = 0; i < n; i++) {
+        const size_t d[3] = {pl[(size_t)i], ndim > 1 ? dims[1] : 1, ndim > 2 ? dims[2] : 1};
+        double best = 1e30;
+        for (int rep = 0; rep <= reps; rep++) {
+            if (cudaEventRecord(e0, sC) != cudaSuccess) return HPDR_ERR_CUDA;
+            st = hpdr::compress_in_flight(ctx, r->buf[0], dtype, ndim, d, tol, tol_kind, mode, cfg, r->buf[2],
+                                          r->bytes[2], r->h_pairs, r->d_pairs, sC);
+            if (st != HPDR_OK) { cudaDeviceSynchronize(); return st; }
+            if (cudaEventRecord(e1, sC) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                return HPDR_ERR_CUDA;
+            if (r->h_pairs[1]) return hpdr::status_of_device((unsigned)r->h_pairs[1]);
+            if (rep > 0) best = std::min(best, (double)ms);     // rep 0 warms up
+        }
+        cb[(size_t)i] = (double)(pl[(size_t)i] * plane);
+        tp[(size_t)i] = cb[(size_t)i] / (std::max(best, 1e-3) * 1e-3);
+    }
+    return hpdr_pipeline_fit(cb.data(), tp.data(), n, f, h2d, model);
+}
+
+extern "C" hpdr_status hpdr_compress_host_adaptive(hpdr_ctx *ctx, const void *h_in, hpdr_dtype dtype, int ndim,
+                                                   const size_t *dims, double tol, hpdr_tol_kind tol_kind,
+                                                   hpdr_mode mode, const hpdr_config *cfg,
+                                                   const hpdr_pipeline_model *model, size_t c_init, size_t c_limit,
+                                                   void *h_out, size_t out_capacity, size_t *out_bytes)
+{
+    hpdr_status st = check_field_args(ctx, h_in, dtype, ndim, dims);
+    if (st != HPDR_OK) return st;
+    if (!h_out || !out_bytes || !model_ok(model)) return HPDR_ERR_ARG;
+    int dev_prev = -1;
+    cudaGetDevice(&dev_prev);
+    if (dev_prev != ctx->device) cudaSetDevice(ctx->device);
+    struct Restore { int d, p; ~Restore() { if (d != p) cudaSetDevice(p); } } restore{ctx->device, dev_prev};
+    const size_t plane = plane_bytes_of(dtype, ndim, dims);
+    std::vector<size_t> pl, first, count;
+    plan_chunks(*model, dims[0], plane, c_init, c_limit, pl);
+    size_t at = 0;
+    for (size_t p : pl) { first.push_back(at); count.push_back(p); at += p; }
+    return compress_slabs(ctx, h_in, dtype, ndim, dims, tol, tol_kind, mode, cfg, first, count, plane, h_out,
+                          out_capacity, out_bytes);
 }

@@ -13,6 +13,7 @@ Function names follow the C ABI:
   hpdr_decompose_noalloc.
 """
 import ctypes as C
+import math
 import os
 
 import torch
@@ -35,6 +36,16 @@ class HpdrError(RuntimeError):
 
 class Config(C.Structure):
     _fields_ = [("dict_size", C.c_uint32), ("chunk", C.c_uint32)]
+
+
+class PipelineModel(C.Structure):
+    """Adaptive pipeline model (Sec. V-C): Phi(C) = alpha*C + beta below
+    c_threshold bytes, gamma above (bytes/s); Theta(t) = t * h2d bytes."""
+    _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
+                ("c_threshold", C.c_double), ("h2d", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Field(C.Structure):
@@ -76,6 +87,14 @@ def lib():
             "hpdr_compress_batched": [vp, C.c_int, C.POINTER(Field), C.POINTER(Config), vp, C.c_size_t,
                                       sz, sz, vp],
             "hpdr_batched_streams": [vp],
+            "hpdr_pipeline_fit": [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, C.c_double,
+                                  C.c_double, C.POINTER(PipelineModel)],
+            "hpdr_pipeline_profile": [vp, vp, C.c_int, C.c_int, sz, C.c_double, C.c_int, C.c_int,
+                                      C.POINTER(Config), sz, C.c_int, C.c_int, C.c_double,
+                                      C.POINTER(PipelineModel)],
+            "hpdr_compress_host_adaptive": [vp, vp, C.c_int, C.c_int, sz, C.c_double, C.c_int, C.c_int,
+                                            C.POINTER(Config), C.POINTER(PipelineModel), C.c_size_t,
+                                            C.c_size_t, vp, C.c_size_t, sz],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -83,6 +102,11 @@ def lib():
             f.restype = C.c_int
         L.hpdr_compress_bound.argtypes = [C.c_int, sz, C.c_int, C.POINTER(Config)]
         L.hpdr_compress_bound.restype = C.c_size_t
+        L.hpdr_pipeline_plan.argtypes = [C.POINTER(PipelineModel), C.c_size_t, C.c_size_t, C.c_size_t,
+                                          C.c_size_t, sz, C.c_size_t]
+        L.hpdr_pipeline_plan.restype = C.c_size_t
+        L.hpdr_streamed_bound.argtypes = [C.c_int, sz, C.c_int, C.POINTER(Config), sz, C.c_size_t]
+        L.hpdr_streamed_bound.restype = C.c_size_t
         L.hpdr_status_string.argtypes = [C.c_int]
         L.hpdr_status_string.restype = C.c_char_p
         _lib = L
@@ -233,6 +257,78 @@ def hpdr_compress_host_streamed(u, tol, tol_kind=REL, mode=LINF, slab_bytes=256 
                                              nd, dims, float(tol), int(tol_kind), int(mode), C.byref(cfg),
                                              int(slab_bytes), C.c_void_p(out.data_ptr()), out.numel(),
                                              C.byref(nb)), "hpdr_compress_host_streamed")
+    return out[:nb.value]
+
+
+def pipeline_fit(chunk_bytes, throughput, h2d, f=0.1):
+    """Fit of the throughput model Phi from profiled (chunk bytes, bytes/s)
+    pairs (Sec. V-C); host only."""
+    n = len(chunk_bytes)
+    cb = (C.c_double * n)(*[float(x) for x in chunk_bytes])
+    tp = (C.c_double * n)(*[float(x) for x in throughput])
+    m = PipelineModel()
+    _check(lib().hpdr_pipeline_fit(cb, tp, n, float(f), float(h2d), C.byref(m)), "hpdr_pipeline_fit")
+    return m
+
+
+def pipeline_plan(model, n0, plane_bytes, c_init, c_limit=0):
+    """Plane counts of the chunks of Alg. 4 for n0 planes; host only."""
+    L = lib()
+    n = L.hpdr_pipeline_plan(C.byref(model), int(n0), int(plane_bytes), int(c_init), int(c_limit), None, 0)
+    if n == 0:
+        raise HpdrError(-1, "hpdr_pipeline_plan")
+    buf = (C.c_size_t * n)()
+    L.hpdr_pipeline_plan(C.byref(model), int(n0), int(plane_bytes), int(c_init), int(c_limit), buf, n)
+    return list(buf)
+
+
+def streamed_bound_plan(shape, dtype, planes, dict_size=8192, chunk=0):
+    """Capacity that always holds the streamed container of a field cut into
+    chunks of planes[i] planes along dimension 0; host only."""
+    nd, dims = _dims(shape)
+    cfg = _cfg(dict_size, chunk)
+    pl = (C.c_size_t * len(planes))(*[int(p) for p in planes])
+    b = lib().hpdr_streamed_bound(nd, dims, _dtype_code(dtype), C.byref(cfg), pl, len(planes))
+    if b == 0:
+        raise HpdrError(-1, "hpdr_streamed_bound")
+    return b
+
+
+def pipeline_profile(u, tol, chunk_bytes, tol_kind=REL, mode=LINF, reps=3, f=0.1, dict_size=8192, chunk=0,
+                     device=None):
+    """Model of the adaptive pipeline profiled on the CPU field u itself:
+    timed host-to-device copy and device compressions of its first planes."""
+    if u.is_cuda or not u.is_contiguous():
+        raise TypeError("u must be a contiguous CPU tensor")
+    nd, dims = _dims(u.shape)
+    cfg = _cfg(dict_size, chunk)
+    cb = (C.c_size_t * len(chunk_bytes))(*[int(x) for x in chunk_bytes])
+    m = PipelineModel()
+    _check(lib().hpdr_pipeline_profile(context(device), C.c_void_p(u.data_ptr()), _dtype_code(u.dtype), nd, dims,
+                                       float(tol), int(tol_kind), int(mode), C.byref(cfg), cb, len(chunk_bytes),
+                                       int(reps), float(f), C.byref(m)), "hpdr_pipeline_profile")
+    return m
+
+
+def hpdr_compress_host_adaptive(u, tol, model, c_init=64 << 20, c_limit=1 << 30, tol_kind=REL, mode=LINF,
+                                dict_size=8192, chunk=0, out=None, device=None):
+    """Compress a CPU tensor with the adaptive chunk sizes of Alg. 4; returns a
+    CPU uint8 tensor holding the streamed container."""
+    if u.is_cuda or not u.is_contiguous():
+        raise TypeError("u must be a contiguous CPU tensor")
+    nd, dims = _dims(u.shape)
+    cfg = _cfg(dict_size, chunk)
+    if out is None:
+        plane = u.element_size() * (math.prod(int(s) for s in u.shape[1:]) if u.dim() > 1 else 1)
+        planes = pipeline_plan(model, u.shape[0], plane, c_init, c_limit)
+        out = torch.empty(streamed_bound_plan(u.shape, u.dtype, planes, dict_size, chunk), dtype=torch.uint8,
+                          pin_memory=True)
+    nb = C.c_size_t()
+    _check(lib().hpdr_compress_host_adaptive(context(device), C.c_void_p(u.data_ptr()), _dtype_code(u.dtype),
+                                             nd, dims, float(tol), int(tol_kind), int(mode), C.byref(cfg),
+                                             C.byref(model), int(c_init), int(c_limit),
+                                             C.c_void_p(out.data_ptr()), out.numel(), C.byref(nb)),
+           "hpdr_compress_host_adaptive")
     return out[:nb.value]
 
 

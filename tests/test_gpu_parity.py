@@ -72,7 +72,8 @@ def _decode_container_symbols(oracle, buf):
 @pytest.mark.parametrize("shape,tol,D", [((129, 129), 1e-3, 8192), ((33, 17, 9), 1e-2, 8192),
                                          ((70, 70, 70), 1e-4, 8192), ((65, 33), 1e-3, 64),
                                          ((100, 7, 5), 1e-3, 8192), ((1000,), 1e-3, 8192),
-                                         ((3, 2), 1e-2, 4)], ids=str)
+                                         ((3, 2), 1e-2, 4), ((50000,), 1e-3, 8192), ((9000, 3), 1e-3, 8192)],
+                         ids=str)
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 def test_codes_bit_exact_on_identical_inputs(oracle, H, dev, shape, tol, D, dtype):
     u = _field(shape, 3, dtype)
