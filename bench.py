@@ -46,6 +46,7 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-field batched leg")
     ap.add_argument("--batch-dict", type=int, default=8192, help="dictionary size of the batched leg")
     ap.add_argument("--no-stream", action="store_true", help="skip the 1025^3 host-streamed leg")
+    ap.add_argument("--no-lossless", action="store_true", help="skip the lossless (Huffman-only) leg")
     return ap.parse_args()
 
 
@@ -116,9 +117,17 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def source_hash():
+LEVEL_GROUPS = ("c_restrict_quant_L", "d_restrict_sym_L", "d_expand_L", "c_solves_L", "d_solves_L")
+
+
+def source_hash(group="c_restrict_quant_L"):
+    """SHA-256 prefix of the sources of a kernel group's translation unit: the
+    level kernels (levels.cu, levels.cuh, internal.cuh) or the Huffman kernels
+    (huffman.cu, huffman.cuh, internal.cuh)."""
+    files = (("levels.cu", "levels.cuh", "internal.cuh") if group in LEVEL_GROUPS
+             else ("huffman.cu", "huffman.cuh", "internal.cuh"))
     h = hashlib.sha256()
-    for f in ("levels.cu", "huffman.cu", "levels.cuh", "internal.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2503_06322_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -132,7 +141,7 @@ def ncu_traffic(kernel_group):
         lines = open(path).read().splitlines()
     except OSError:
         return None
-    cur = source_hash()
+    cur = source_hash(kernel_group)
     for ln in lines:
         parts = [p.strip() for p in ln.strip().strip("|").split("|")]
         if len(parts) >= 4 and parts[0] == kernel_group and parts[1] == cur:
@@ -528,6 +537,49 @@ def run_stream(args, dev):
             "fixed_256MiB": fixed, "adaptive_alg4": adaptive, "whole_field_ratio": round(fb / whole, 4)}
 
 
+def run_lossless(args, dev):
+    """The Huffman stage on its own (Alg. 2) through hpdr_lossless_compress /
+    hpdr_lossless_decompress, device-resident: 1 GiB of byte keys (rounded
+    Laplacian of scale 6 around 128, about 4.4 bits of entropy) and 256 Mi
+    16-bit keys (rounded Laplacian of scale 40, about 7.7 bits).  Throughput =
+    key bytes / time, CUDA events around five calls after one warm-up."""
+    import torch
+    from paper_2503_06322_gb300 import hpdr
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    res = {"workload": "1 GiB byte keys (Laplacian, scale 6) and 256 Mi 16-bit keys (Laplacian, scale 40), "
+                       "synthetic, device-resident; key bytes / time"}
+    for name, n, kb, scale in (("byte_keys", 1 << 30, 1, 6.0), ("keys16", 1 << 28, 2, 40.0)):
+        x = torch.empty(n, device=dev).exponential_(generator=g)
+        x.sub_(torch.empty(n, device=dev).exponential_(generator=g)).mul_(scale).round_()
+        keys = (x + 128).clamp_(0, 255).to(torch.uint8) if kb == 1 else x.clamp_(-32768, 32767).to(torch.int16)
+        del x
+        buf = torch.empty(hpdr.lossless_bound(n, kb), dtype=torch.uint8, device=dev)
+        out = torch.empty_like(keys)
+        b = hpdr.hpdr_lossless_compress(keys, out=buf)
+        hpdr.hpdr_lossless_decompress(b, out=out)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        reps = 5
+        e0.record()
+        for _ in range(reps):
+            b = hpdr.hpdr_lossless_compress(keys, out=buf)
+        e1.record()
+        for _ in range(reps):
+            hpdr.hpdr_lossless_decompress(b, out=out)
+        e2.record()
+        torch.cuda.synchronize()
+        tc, td = e0.elapsed_time(e1) / reps, e1.elapsed_time(e2) / reps
+        nbytes = n * kb
+        res[name] = {"compress_gbs": round(nbytes / (tc * 1e-3) / 1e9, 2),
+                     "decompress_gbs": round(nbytes / (td * 1e-3) / 1e9, 2),
+                     "compression_ratio": round(nbytes / b.numel(), 4),
+                     "bits_per_key": round(8.0 * b.numel() / n, 4),
+                     "round_trip_exact": bool(torch.equal(out, keys))}
+        del keys, buf, out, b
+        torch.cuda.empty_cache()
+    return res
+
+
 def cpu_sample(args, u_host_planes, steps=1):
     """The oracle (single-threaded C, FP64) on the first planes of the field."""
     import numpy as np
@@ -593,6 +645,8 @@ def main():
         out["batched"] = run_batched(args, u.device)
     if rank == 0 and not args.no_stream:
         out["host_streamed"] = run_stream(args, u.device)
+    if rank == 0 and not args.no_lossless:
+        out["lossless"] = run_lossless(args, u.device)
     if rank == 0 and world == 1 and not args.no_cpu:
         planes = min(args.cpu_planes, shape[0])
         host = u[:planes].cpu().numpy()

@@ -223,6 +223,43 @@ hpdr_status hpdr_compress_host_streamed(hpdr_ctx *ctx, const void *h_in, hpdr_dt
 hpdr_status hpdr_decompress_host_streamed(hpdr_ctx *ctx, const void *h_in, size_t in_bytes, void *h_out,
                                           size_t out_capacity);
 
+/* Lossless compression of keys: the Huffman stage of Sec. IV-B (Alg. 2:
+ * histogram, codebook, encode, serialize) on its own, for byte keys
+ * (key_bytes = 1, alphabet D = 256) or 16-bit keys (key_bytes = 2,
+ * D = 65536).  Container "HPDL" (little endian, device memory):
+ *    0 "HPDL"  4 u32 version (1)  8 u32 key_bytes  12 u32 D  16 u32 K
+ *   20 u32 0   24 u64 n  32 u64 total_bits  40 u64 chunk-table offset
+ *   48 u64 bitstream offset  56 u32 0  60 u32 CRC-32 of bytes [0, 60)
+ *   64 code length of every symbol 0..D-1 (u8, 0 = absent)
+ *   then the chunk table (u64 bit offset of every K-th key) and the
+ *   bitstream (u32 words, codewords MSB first), each at a 16-byte boundary.
+ * Codes are the canonical two-queue Huffman code of the keys' histogram
+ * (lengths at most 63), the same as hpdr_huffman_encode's. */
+
+/* Capacity that always holds the container of n keys (the code never exceeds
+ * 8 or 16 bits per key).  K: chunk size, 0 = automatic.  0 on bad
+ * arguments.  Host only. */
+size_t hpdr_lossless_bound(uint64_t n, int key_bytes, uint32_t K);
+
+/* Compresses n >= 1 keys at d_keys (device; 16-byte aligned for 16-bit keys)
+ * into d_out (device, 16-byte aligned, out_capacity bytes); *out_bytes (host)
+ * receives the container size.  K: chunk size (multiple of 128 in
+ * [128, 32768]) or 0 for automatic.  Synchronizes stream.  Errors:
+ * HPDR_ERR_ARG, HPDR_ERR_CAPACITY, HPDR_ERR_NOMEM, HPDR_ERR_CUDA. */
+hpdr_status hpdr_lossless_compress(hpdr_ctx *ctx, const void *d_keys, uint64_t n, int key_bytes, uint32_t K,
+                                   void *d_out, size_t out_capacity, size_t *out_bytes, void *stream);
+
+/* Inverse of hpdr_lossless_compress: d_in (device, in_bytes) to d_keys
+ * (device, keys_capacity bytes; 16-byte aligned for 16-bit keys).
+ * Synchronizes stream (header read and status).  Errors: HPDR_ERR_FORMAT
+ * (bad magic, version, CRC, sizes or bitstream), HPDR_ERR_CAPACITY,
+ * HPDR_ERR_ARG, HPDR_ERR_CUDA. */
+hpdr_status hpdr_lossless_decompress(hpdr_ctx *ctx, const void *d_in, size_t in_bytes, void *d_keys,
+                                     size_t keys_capacity, void *stream);
+
+/* Key width and count of an HPDL container (host or device pointer). */
+hpdr_status hpdr_lossless_inspect(const void *in, size_t in_bytes, int *key_bytes, uint64_t *n);
+
 /* Adaptive chunk sizing of the host-device pipeline (Sec. V-C, Alg. 4).
  * Model of the pipeline (all sizes in bytes, throughputs in bytes/s):
  *   Phi(C)   = alpha * C + beta  for C <  c_threshold

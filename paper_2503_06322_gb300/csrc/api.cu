@@ -683,6 +683,55 @@ bool is_device_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// ----- lossless container (HPDL) -------------------------------------------
+// byte keys travel as 16-bit symbols through the Huffman kernels
+__global__ void widen_keys_kernel(const uint8_t *in, unsigned long long n, uint16_t *out)
+{
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        out[i] = in[i];
+}
+__global__ void narrow_keys_kernel(const uint16_t *in, unsigned long long n, uint8_t *out)
+{
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        out[i] = (uint8_t)in[i];
+}
+
+constexpr unsigned kLosslessHdr = 64;
+struct LosslessHdr {
+    unsigned key_bytes, D, K;
+    unsigned long long n, bits, nch, off_chunk, off_bits, total;
+};
+void lossless_layout(LosslessHdr *h)
+{
+    h->nch = (h->n + h->K - 1) / h->K;
+    h->off_chunk = a16(kLosslessHdr + h->D);
+    h->off_bits = a16(h->off_chunk + 8 * h->nch);
+    h->total = h->off_bits + 4 * ((h->bits + 31) / 32);
+}
+void wr32(uint8_t *p, uint32_t v) { for (int i = 0; i < 4; i++) p[i] = (uint8_t)(v >> (8 * i)); }
+void wr64(uint8_t *p, uint64_t v) { for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i)); }
+uint32_t rd32l(const uint8_t *p) { uint32_t v = 0; for (int i = 0; i < 4; i++) v |= (uint32_t)p[i] << (8 * i); return v; }
+uint64_t rd64l(const uint8_t *p) { uint64_t v = 0; for (int i = 0; i < 8; i++) v |= (uint64_t)p[i] << (8 * i); return v; }
+
+hpdr_status parse_lossless(const uint8_t *b, size_t in_bytes, LosslessHdr *h)
+{
+    if (in_bytes < kLosslessHdr || memcmp(b, "HPDL", 4) != 0 || rd32l(b + 4) != 1) return HPDR_ERR_FORMAT;
+    if (crc32_host(b, 60) != rd32l(b + 60)) return HPDR_ERR_FORMAT;
+    h->key_bytes = rd32l(b + 8);
+    h->D = rd32l(b + 12);
+    h->K = rd32l(b + 16);
+    h->n = rd64l(b + 24);
+    h->bits = rd64l(b + 32);
+    if ((h->key_bytes != 1 && h->key_bytes != 2) || h->D != (h->key_bytes == 1 ? 256u : 65536u)) return HPDR_ERR_FORMAT;
+    if (h->K < 128 || h->K > 32768 || (h->K % 128) || h->n == 0 || h->n > (1ull << 40)) return HPDR_ERR_FORMAT;
+    if (h->bits > 63ull * h->n) return HPDR_ERR_FORMAT;
+    lossless_layout(h);
+    if (rd64l(b + 40) != h->off_chunk || rd64l(b + 48) != h->off_bits || h->total > in_bytes) return HPDR_ERR_FORMAT;
+    return HPDR_OK;
+}
+
 }  // namespace
 
 namespace hpdr {
@@ -924,6 +973,173 @@ hpdr_status hpdr_huffman_encode(hpdr_ctx *ctx, const uint16_t *d_symbols, uint64
     CK(cudaStreamSynchronize(s));
     if (hsc->status) return map_device_status(hsc->status);
     *total_bits = hsc->total_bits;
+    return HPDR_OK;
+}
+
+size_t hpdr_lossless_bound(uint64_t n, int key_bytes, uint32_t K)
+{
+    if (n == 0 || (key_bytes != 1 && key_bytes != 2)) return 0;
+    LosslessHdr h;
+    h.key_bytes = (unsigned)key_bytes;
+    h.D = key_bytes == 1 ? 256u : 65536u;
+    hpdr_config cfg = {h.D, K};
+    unsigned Dv, Kv;
+    if (!valid_cfg(&cfg, Dv, Kv)) return 0;
+    h.K = chunk_of(Kv, n);
+    h.n = n;
+    h.bits = n * 8ull * (unsigned)key_bytes;   // never above the fixed-length code
+    lossless_layout(&h);
+    return (size_t)h.total;
+}
+
+hpdr_status hpdr_lossless_compress(hpdr_ctx *ctx, const void *d_keys, uint64_t n, int key_bytes, uint32_t K,
+                                   void *d_out, size_t out_capacity, size_t *out_bytes, void *stream)
+{
+    if (!ctx || !d_keys || !d_out || !out_bytes || n == 0 || (key_bytes != 1 && key_bytes != 2)) return HPDR_ERR_ARG;
+    LosslessHdr h;
+    h.key_bytes = (unsigned)key_bytes;
+    h.D = key_bytes == 1 ? 256u : 65536u;
+    hpdr_config cfg = {h.D, K};
+    unsigned Dv, Kv;
+    if (!valid_cfg(&cfg, Dv, Kv) || ((uintptr_t)d_out & 15) || (key_bytes == 2 && ((uintptr_t)d_keys & 15)))
+        return HPDR_ERR_ARG;
+    h.K = chunk_of(Kv, n);
+    h.n = n;
+    h.bits = 0;
+    lossless_layout(&h);
+    if (h.off_bits > out_capacity) return HPDR_ERR_CAPACITY;
+    DevGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned D = h.D;
+    Carver c(nullptr);
+    c.take<Scalars>(1); c.take<unsigned long long>(D); c.take<unsigned long long>(h.nch + 2);
+    c.take<unsigned long long>(1024); c.take<char>(huff_scratch_bytes(D));
+    if (key_bytes == 1) c.take<uint16_t>(n + 8);
+    hpdr_status st = ensure_workspace(ctx, c.used + 256);
+    if (st != HPDR_OK) return st;
+    Carver w(ctx->ws.base);
+    Scalars *sc = w.take<Scalars>(1);
+    unsigned long long *hist = w.take<unsigned long long>(D);
+    unsigned long long *cb = w.take<unsigned long long>(h.nch + 2);
+    unsigned long long *bs = w.take<unsigned long long>(1024);
+    void *hb = w.take<char>(huff_scratch_bytes(D));
+    const uint16_t *sym = (const uint16_t *)d_keys;
+    if (key_bytes == 1) {
+        uint16_t *wide = w.take<uint16_t>(n + 8);
+        widen_keys_kernel<<<152 * 8, 256, 0, s>>>((const uint8_t *)d_keys, n, wide);
+        count_launch();
+        CK(cudaGetLastError());
+        sym = wide;
+    }
+    uint8_t *out = (uint8_t *)d_out;
+    CK(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
+    CK(cudaMemsetAsync(hist, 0, 8ULL * D, s));
+    CK(launch_histogram(sym, n, D, hist, &sc->status, s));
+    HuffScratch hs;
+    huff_scratch_carve(hb, D, sc, &hs);
+    CK(launch_codebook(hist, D, hs, s));
+    EncodeArgs ea;
+    memset(&ea, 0, sizeof(ea));
+    ea.sym = sym; ea.N = n; ea.D = D; ea.K = h.K; ea.len = hs.len; ea.code = hs.code;
+    ea.chunk_bits = cb; ea.sc = sc; ea.bsum = bs;
+    ea.chunk_out = (unsigned long long *)(out + h.off_chunk);
+    ea.words_out = (uint32_t *)(out + h.off_bits);
+    ea.words_cap = (out_capacity - h.off_bits) / 4;
+    CK(launch_encode(ea, s));
+    CK(cudaMemcpyAsync(out + kLosslessHdr, hs.len, D, cudaMemcpyDeviceToDevice, s));
+    Scalars *hsc = (Scalars *)ctx->host_pinned;
+    CK(cudaMemcpyAsync(hsc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hsc->status) return map_device_status(hsc->status);
+    h.bits = hsc->total_bits;
+    lossless_layout(&h);
+    if (h.total > out_capacity) return HPDR_ERR_CAPACITY;
+    uint8_t *hdr = (uint8_t *)ctx->host_pinned + 48 * 1024;
+    memset(hdr, 0, kLosslessHdr);
+    memcpy(hdr, "HPDL", 4);
+    wr32(hdr + 4, 1);
+    wr32(hdr + 8, h.key_bytes);
+    wr32(hdr + 12, h.D);
+    wr32(hdr + 16, h.K);
+    wr64(hdr + 24, h.n);
+    wr64(hdr + 32, h.bits);
+    wr64(hdr + 40, h.off_chunk);
+    wr64(hdr + 48, h.off_bits);
+    wr32(hdr + 60, crc32_host(hdr, 60));
+    CK(cudaMemcpyAsync(out, hdr, kLosslessHdr, cudaMemcpyHostToDevice, s));
+    // the gaps before the chunk table and the bitstream are zero
+    if (h.off_chunk > kLosslessHdr + D)
+        CK(cudaMemsetAsync(out + kLosslessHdr + D, 0, h.off_chunk - kLosslessHdr - D, s));
+    if (h.off_bits > h.off_chunk + 8 * h.nch)
+        CK(cudaMemsetAsync(out + h.off_chunk + 8 * h.nch, 0, h.off_bits - h.off_chunk - 8 * h.nch, s));
+    CK(cudaStreamSynchronize(s));
+    *out_bytes = (size_t)h.total;
+    return HPDR_OK;
+}
+
+hpdr_status hpdr_lossless_decompress(hpdr_ctx *ctx, const void *d_in, size_t in_bytes, void *d_keys,
+                                     size_t keys_capacity, void *stream)
+{
+    if (!ctx || !d_in || !d_keys || ((uintptr_t)d_in & 15)) return HPDR_ERR_ARG;
+    if (in_bytes < kLosslessHdr) return HPDR_ERR_FORMAT;
+    DevGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    uint8_t *hb = (uint8_t *)ctx->host_pinned + 48 * 1024;
+    CK(cudaMemcpyAsync(hb, d_in, kLosslessHdr, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    LosslessHdr h;
+    hpdr_status st = parse_lossless(hb, in_bytes, &h);
+    if (st != HPDR_OK) return st;
+    if (h.n * h.key_bytes > keys_capacity) return HPDR_ERR_CAPACITY;
+    if (h.key_bytes == 2 && ((uintptr_t)d_keys & 15)) return HPDR_ERR_ARG;
+    const unsigned D = h.D;
+    Carver c(nullptr);
+    c.take<Scalars>(1); c.take<char>(huff_scratch_bytes(D));
+    if (h.key_bytes == 1) c.take<uint16_t>(h.n + 8);
+    st = ensure_workspace(ctx, c.used + 256);
+    if (st != HPDR_OK) return st;
+    Carver w(ctx->ws.base);
+    Scalars *sc = w.take<Scalars>(1);
+    void *hsb = w.take<char>(huff_scratch_bytes(D));
+    uint16_t *sym = h.key_bytes == 1 ? w.take<uint16_t>(h.n + 8) : (uint16_t *)d_keys;
+    const uint8_t *in = (const uint8_t *)d_in;
+    CK(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
+    HuffScratch hs;
+    huff_scratch_carve(hsb, D, sc, &hs);
+    CK(launch_decode_tables(in + kLosslessHdr, 0, D - 1, D, hs, s));
+    DecodeArgs da;
+    da.words = (const uint32_t *)(in + h.off_bits);
+    da.nwords = (h.bits + 31) / 32;
+    da.chunk = (const unsigned long long *)(in + h.off_chunk);
+    da.N = h.n; da.K = h.K; da.sym = sym; da.total_bits = h.bits; da.esc = nullptr; da.esc_w = 0;
+    CK(launch_decode(da, hs, s));
+    if (h.key_bytes == 1) {
+        narrow_keys_kernel<<<152 * 8, 256, 0, s>>>(sym, h.n, (uint8_t *)d_keys);
+        count_launch();
+        CK(cudaGetLastError());
+    }
+    Scalars *hsc = (Scalars *)ctx->host_pinned;
+    CK(cudaMemcpyAsync(hsc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hsc->status) return map_device_status(hsc->status);
+    return HPDR_OK;
+}
+
+hpdr_status hpdr_lossless_inspect(const void *in, size_t in_bytes, int *key_bytes, uint64_t *n)
+{
+    if (!in || !key_bytes || !n) return HPDR_ERR_ARG;
+    if (in_bytes < kLosslessHdr) return HPDR_ERR_FORMAT;
+    uint8_t hb[kLosslessHdr];
+    if (is_device_ptr(in)) {
+        if (cudaMemcpy(hb, in, kLosslessHdr, cudaMemcpyDeviceToHost) != cudaSuccess) return HPDR_ERR_CUDA;
+    } else {
+        memcpy(hb, in, kLosslessHdr);
+    }
+    LosslessHdr h;
+    hpdr_status st = parse_lossless(hb, in_bytes, &h);
+    if (st != HPDR_OK) return st;
+    *key_bytes = (int)h.key_bytes;
+    *n = h.n;
     return HPDR_OK;
 }
 

@@ -1359,6 +1359,58 @@ hist_kernel(const uint16_t *sym, unsigned long long N, unsigned D, unsigned long
             if (hsm[i]) atomicAdd(&hist[i], (unsigned long long)hsm[i]);
 }
 
+// Histogram of an alphabet above 16384 symbols (up to 65536): two 16-bit
+// counters per 32-bit shared word, 128 KB.  A block counts at most 32768 keys
+// per round, so no counter carries into its neighbour, then adds the nonzero
+// counts to the global histogram and clears its words.
+constexpr int kHistWideThreads = 1024;
+constexpr unsigned kHistWideRound = 32u * kHistWideThreads;
+__global__ void __launch_bounds__(kHistWideThreads, 1)
+hist_wide_kernel(const uint16_t *sym, unsigned long long N, unsigned D, unsigned long long *hist, unsigned *status)
+{
+    extern __shared__ unsigned hw[];
+    const unsigned nw = (D + 1) / 2;
+    for (unsigned i = threadIdx.x; i < nw; i += blockDim.x) hw[i] = 0;
+    __syncthreads();
+    for (unsigned long long r0 = blockIdx.x * (unsigned long long)kHistWideRound; r0 < N;
+         r0 += (unsigned long long)gridDim.x * kHistWideRound) {
+        const unsigned long long r1 = r0 + kHistWideRound < N ? r0 + kHistWideRound : N;
+        if (r1 - r0 == kHistWideRound && ((uintptr_t)(sym + r0) & 15) == 0) {
+            // a full round: four 16-byte loads (32 keys) per thread
+            const uint4 *v = reinterpret_cast<const uint4 *>(sym + r0);
+            uint4 x[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) x[u] = v[threadIdx.x + u * kHistWideThreads];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const unsigned w4[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const unsigned s = (w4[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+                    if (s >= D) { atomicExch(status, (unsigned)DS_ARG); continue; }
+                    atomicAdd(&hw[s >> 1], (s & 1) ? 0x10000u : 1u);
+                }
+            }
+        } else {
+            for (unsigned long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+                const unsigned s = sym[i];
+                if (s >= D) { atomicExch(status, (unsigned)DS_ARG); continue; }
+                atomicAdd(&hw[s >> 1], (s & 1) ? 0x10000u : 1u);
+            }
+        }
+        __syncthreads();
+        for (unsigned i = threadIdx.x; i < nw; i += blockDim.x) {
+            const unsigned w = hw[i];
+            if (w) {
+                if (w & 0xFFFFu) atomicAdd(&hist[2 * i], (unsigned long long)(w & 0xFFFFu));
+                if (w >> 16) atomicAdd(&hist[2 * i + 1], (unsigned long long)(w >> 16));
+                hw[i] = 0;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 bool g_attr_done = false;
 cudaError_t set_attrs()
 {
@@ -1492,10 +1544,24 @@ cudaError_t launch_histogram(const uint16_t *sym, unsigned long long N, unsigned
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(hist_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536 * 2);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    hist_kernel<<<152 * 4, 256, D <= 16384 ? D * 4 : 0, s>>>(sym, N, D, hist, status);
+    if (D <= 16384) {
+        hist_kernel<<<152 * 4, 256, D * 4, s>>>(sym, N, D, hist, status);
+    } else {
+        int dev = 0, nsm = 152;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            nsm = 152;
+        }
+        const unsigned long long rounds = (N + kHistWideRound - 1) / kHistWideRound;
+        const unsigned grid = (unsigned)(rounds < (unsigned long long)nsm ? rounds : (unsigned long long)nsm);
+        hist_wide_kernel<<<grid, kHistWideThreads, ((D + 1) / 2) * 4, s>>>(sym, N, D, hist, status);
+    }
     count_launch();
     return cudaGetLastError();
 }

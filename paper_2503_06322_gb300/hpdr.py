@@ -87,6 +87,9 @@ def lib():
             "hpdr_compress_batched": [vp, C.c_int, C.POINTER(Field), C.POINTER(Config), vp, C.c_size_t,
                                       sz, sz, vp],
             "hpdr_batched_streams": [vp],
+            "hpdr_lossless_compress": [vp, vp, C.c_uint64, C.c_int, C.c_uint32, vp, C.c_size_t, sz, vp],
+            "hpdr_lossless_decompress": [vp, vp, C.c_size_t, vp, C.c_size_t, vp],
+            "hpdr_lossless_inspect": [vp, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_uint64)],
             "hpdr_pipeline_fit": [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, C.c_double,
                                   C.c_double, C.POINTER(PipelineModel)],
             "hpdr_pipeline_profile": [vp, vp, C.c_int, C.c_int, sz, C.c_double, C.c_int, C.c_int,
@@ -102,6 +105,8 @@ def lib():
             f.restype = C.c_int
         L.hpdr_compress_bound.argtypes = [C.c_int, sz, C.c_int, C.POINTER(Config)]
         L.hpdr_compress_bound.restype = C.c_size_t
+        L.hpdr_lossless_bound.argtypes = [C.c_uint64, C.c_int, C.c_uint32]
+        L.hpdr_lossless_bound.restype = C.c_size_t
         L.hpdr_pipeline_plan.argtypes = [C.POINTER(PipelineModel), C.c_size_t, C.c_size_t, C.c_size_t,
                                           C.c_size_t, sz, C.c_size_t]
         L.hpdr_pipeline_plan.restype = C.c_size_t
@@ -258,6 +263,54 @@ def hpdr_compress_host_streamed(u, tol, tol_kind=REL, mode=LINF, slab_bytes=256 
                                              int(slab_bytes), C.c_void_p(out.data_ptr()), out.numel(),
                                              C.byref(nb)), "hpdr_compress_host_streamed")
     return out[:nb.value]
+
+
+def _key_bytes(dtype):
+    if dtype == torch.uint8:
+        return 1
+    if dtype in (torch.int16, getattr(torch, "uint16", torch.int16)):
+        return 2
+    raise TypeError("keys must be uint8 (byte keys) or int16/uint16 (16-bit keys)")
+
+
+def lossless_bound(n, key_bytes, K=0):
+    """Container capacity for n keys of key_bytes bytes; host only."""
+    b = lib().hpdr_lossless_bound(int(n), int(key_bytes), int(K))
+    if b == 0:
+        raise HpdrError(-1, "hpdr_lossless_bound")
+    return b
+
+
+def hpdr_lossless_compress(keys, K=0, out=None, stream=None):
+    """Huffman-compress a CUDA tensor of byte keys (uint8) or 16-bit keys
+    (int16/uint16 bit patterns); returns the HPDL container (uint8, CUDA)."""
+    _dev_tensor(keys, "keys")
+    kb = _key_bytes(keys.dtype)
+    n = keys.numel()
+    if out is None:
+        out = torch.empty(lossless_bound(n, kb, K), dtype=torch.uint8, device=keys.device)
+    nb = C.c_size_t()
+    with torch.cuda.device(keys.device):
+        _check(lib().hpdr_lossless_compress(context(keys.device.index), C.c_void_p(keys.data_ptr()), n, kb, int(K),
+                                            C.c_void_p(out.data_ptr()), out.numel(), C.byref(nb), _stream(stream)),
+               "hpdr_lossless_compress")
+    return out[:nb.value]
+
+
+def hpdr_lossless_decompress(buf, out=None, stream=None):
+    """Inverse of hpdr_lossless_compress (CUDA tensors in and out): uint8 keys
+    or int16 bit patterns of 16-bit keys."""
+    _dev_tensor(buf, "buf")
+    kb, n = C.c_int(), C.c_uint64()
+    _check(lib().hpdr_lossless_inspect(C.c_void_p(buf.data_ptr()), buf.numel(), C.byref(kb), C.byref(n)),
+           "hpdr_lossless_inspect")
+    if out is None:
+        out = torch.empty(n.value, dtype=torch.uint8 if kb.value == 1 else torch.int16, device=buf.device)
+    with torch.cuda.device(buf.device):
+        _check(lib().hpdr_lossless_decompress(context(buf.device.index), C.c_void_p(buf.data_ptr()), buf.numel(),
+                                              C.c_void_p(out.data_ptr()), out.numel() * out.element_size(),
+                                              _stream(stream)), "hpdr_lossless_decompress")
+    return out
 
 
 def pipeline_fit(chunk_bytes, throughput, h2d, f=0.1):

@@ -92,3 +92,14 @@ def test_streamed_bound_of_a_plan(H):
     for bad in ([2, 4, 8, 5], [1, 4, 8, 7]):
         with pytest.raises(H.HpdrError):
             H.streamed_bound_plan(shape, torch.float32, bad)
+
+
+def test_lossless_bound(H):
+    # n = 1000 byte keys, automatic K = 256: 4 chunks; table at a16(64 + 256) = 320,
+    # bitstream at a16(320 + 32) = 352, at most 8 bits per key
+    assert H.lossless_bound(1000, 1) == 352 + 4 * 250
+    # 16-bit keys: a 65536-byte length table, at most 16 bits per key
+    assert H.lossless_bound(1000, 2, 128) == (64 + 65536 + 8 * 8 + 15) // 16 * 16 + 4 * 500
+    for bad in ((0, 1, 0), (10, 3, 0), (10, 1, 100)):
+        with pytest.raises(H.HpdrError):
+            H.lossless_bound(*bad)
