@@ -1314,10 +1314,19 @@ __global__ void __launch_bounds__(kDecThreads, 1) decode_kernel(DecodeArgs a, Hu
         };
         auto step = [&](unsigned long long i) -> uint16_t {
             const uint32_t e = lut[hi >> (32 - kLenBits)];
-            const uint16_t sv = (uint16_t)(e & 0xFFFFu);
+            uint16_t sv = (uint16_t)(e & 0xFFFFu);
             const unsigned L = (e >> 16) & 0x3Fu;
+            // a codeword of 16..32 bits under a prefix of one length: its
+            // symbol is symtab[base + the bits after the prefix], all within hi
+            // (nb >= 32), so it stays on this path
+            const bool longu = (e & (kLongFlag | kMixedFlag)) == kLongFlag && L <= 32;
+            if (longu) {
+                const unsigned idx = (e & 0xFFFFu) + ((hi >> (32 - L)) & ((1u << (L - kLenBits)) - 1u));
+                sv = symtab[idx < nsym ? idx : 0];
+            }
             const bool at_esc = ew && sv == 0;
-            if ((e & kLongFlag) || e == 0 || (at_esc && !(e & kEscFolded))) return slow(i, e);
+            if (((e & kLongFlag) && !longu) || e == 0 || (at_esc && (longu || !(e & kEscFolded))))
+                return slow(i, e);
             if (at_esc) {
                 // folded escape: codeword of L - ew bits, then zigzag(k) in ew bits
                 const unsigned long long win = ((unsigned long long)hi << 32) | lo;
