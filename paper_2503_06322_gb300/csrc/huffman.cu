@@ -1338,6 +1338,15 @@ __global__ void __launch_bounds__(kDecThreads, 1) decode_kernel(DecodeArgs a, Hu
         const unsigned long long beg = c * a.K;
         const unsigned long long end = beg + a.K < a.N ? beg + a.K : a.N;
         unsigned long long i = beg;
+        // eight symbols per 16-byte store (a chunk starts on a 256-byte boundary)
+        for (; i + 8 <= end; i += 8) {
+            uint4 o;
+            o.x = (uint32_t)step(i) | ((uint32_t)step(i + 1) << 16);
+            o.y = (uint32_t)step(i + 2) | ((uint32_t)step(i + 3) << 16);
+            o.z = (uint32_t)step(i + 4) | ((uint32_t)step(i + 5) << 16);
+            o.w = (uint32_t)step(i + 6) | ((uint32_t)step(i + 7) << 16);
+            *reinterpret_cast<uint4 *>(a.sym + i) = o;
+        }
         for (; i + 2 <= end; i += 2) {
             const uint32_t v0 = step(i);
             const uint32_t v1 = step(i + 1);

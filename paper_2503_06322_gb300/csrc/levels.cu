@@ -956,7 +956,10 @@ solve_stream_kernel(T *b, int n, long long st, long long ostride, long long ninn
     __syncthreads();
     const long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (line >= nlines) return;
-    const long long o = line / ninner, i = line - o * ninner;
+    long long o, i;
+    if (ninner == 1) { o = line; i = 0; }
+    else if (nlines <= 0xFFFFFFFFll) { o = (unsigned)line / (unsigned)ninner; i = line - o * ninner; }
+    else { o = line / ninner; i = line - o * ninner; }     // 64-bit division only for huge grids
     T *p = b + o * ostride + i;
     constexpr int P = kSolvePre;
     const int nfull = n / P;   // blocks of P steps
