@@ -1074,30 +1074,36 @@ solve_contig_kernel(T *b, int n, long long nlines, int rows, int pitch, const T 
     T *S = reinterpret_cast<T *>(smem_raw);
     T *csub = S + (size_t)rows * pitch, *ccp = csub + n, *cinv = ccp + n;
     for (int t = threadIdx.x; t < n; t += blockDim.x) { csub[t] = sub[t]; ccp[t] = cp[t]; cinv[t] = inv_den[t]; }
-    long long row0 = blockIdx.x * (long long)rows;
-    int nr = (int)min((long long)rows, nlines - row0);
-    const T *src = b + row0 * n;
-    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
-        int r = idx / n, t = idx - r * n;
-        cp_async_elem(&S[r * pitch + t], src + idx);
+    const long long row0 = blockIdx.x * (long long)rows;
+    const int nr = (int)min((long long)rows, nlines - row0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    // one warp per row: coalesced, no per-element division
+    for (int r = warp; r < nr; r += nwarp) {
+        const T *srow = b + (row0 + r) * n;
+        T *drow = S + r * pitch;
+        for (int t = lane; t < n; t += 32) cp_async_elem(&drow[t], srow + t);
     }
     cp_async_wait_all();
     __syncthreads();
     if ((int)threadIdx.x < nr) {
         T *p = S + threadIdx.x * pitch;
         T y = (T)0;
+#pragma unroll 8
         for (int t = 0; t < n; t++) { y = mul_rn(fma_rn(-csub[t], y, p[t]), cinv[t]); p[t] = y; }
         T x = (T)0;
+#pragma unroll 8
         for (int t = n - 1; t >= 0; t--) { x = fma_rn(-ccp[t], x, p[t]); p[t] = x; }
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
-        int r = idx / n, t = idx - r * n;
-        T z = S[r * pitch + t];
-        long long gi = row0 * n + idx;
-        if (sign == 0) b[gi] = z;
-        else if (sign > 0) vc[gi] = add_rn(vc[gi], z);
-        else vc[gi] = sub_rn(vc[gi], z);
+    for (int r = warp; r < nr; r += nwarp) {
+        const T *srow = S + r * pitch;
+        const long long g0 = (row0 + r) * n;
+        for (int t = lane; t < n; t += 32) {
+            const T z = srow[t];
+            if (sign == 0) b[g0 + t] = z;
+            else if (sign > 0) vc[g0 + t] = add_rn(vc[g0 + t], z);
+            else vc[g0 + t] = sub_rn(vc[g0 + t], z);
+        }
     }
 }
 
