@@ -168,7 +168,10 @@ hpdr_status compress_core(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, co
     qo.sym = w.sym; qo.hist = w.hist; qo.esc = w.esc;
     qo.D = D; qo.sc = w.sc;
     const T *v = u;
-    for (int l = L; l >= 1; l--) {
+    // levels 1..ls and level 0 in one CTA (0: none fits)
+    const LevelGeom<T> *geo = &geom<T>(P, 0);
+    const int ls = coarse_top<T>(P, geo);
+    for (int l = L; l > ls; l--) {
         T *vc = (T *)(((L - l) % 2 == 0) ? w.va : w.vb);
         RestrictArgs<T> a;
         memset(&a, 0, sizeof(a));
@@ -189,7 +192,14 @@ hpdr_status compress_core(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, co
         }
         v = vc;
     }
-    CK(launch_level0<T>(Sink::QUANT, v, P->N[0], nullptr, qo, s));
+    if (ls >= 1) {
+        ProfScope ps(ctx, "c_coarse", s);
+        SymIn none;
+        memset(&none, 0, sizeof(none));
+        CK(launch_coarse<T>(0, P, geo, ls, v, nullptr, qo, nullptr, none, nullptr, s));
+    } else {
+        CK(launch_level0<T>(Sink::QUANT, v, P->N[0], nullptr, qo, s));
+    }
 
     HuffScratch hs;
     huff_scratch_carve(w.huff, D, w.sc, &hs);
@@ -406,9 +416,21 @@ hpdr_status decompress_t(hpdr_ctx *ctx, const Plan *P, const Hdr &h, const uint8
     si.status = &w.sc->status;
     // level buffers: v_{l-1} in X, v_l written to Y (or to out at l = L)
     T *bufs[2] = {(T *)w.va, (T *)w.vb};
-    T *v = L == 0 ? out : bufs[0];
-    CK(launch_level0_in<T>(WSrc::SYMBOLS, nullptr, si, P->N[0], v, s));
-    for (int l = 1; l <= L; l++) {
+    const LevelGeom<T> *geo = &geom<T>(P, 0);
+    const int ls = coarse_top<T>(P, geo);
+    T *v;
+    if (ls >= 1) {
+        // levels 0..ls in one CTA, level ls written where level ls + 1 reads it
+        v = (ls == L) ? out : bufs[ls % 2];
+        ProfScope ps(ctx, "d_coarse", s);
+        QuantOut none;
+        memset(&none, 0, sizeof(none));
+        CK(launch_coarse<T>(2, P, geo, ls, nullptr, v, none, nullptr, si, nullptr, s));
+    } else {
+        v = L == 0 ? out : bufs[0];
+        CK(launch_level0_in<T>(WSrc::SYMBOLS, nullptr, si, P->N[0], v, s));
+    }
+    for (int l = ls + 1; l <= L; l++) {
         const LevelGeom<T> &g = geom<T>(P, l);
         RestrictArgs<T> a;
         memset(&a, 0, sizeof(a));
@@ -477,7 +499,9 @@ hpdr_status decompose_t(hpdr_ctx *ctx, const Plan *P, const T *u, T *coef, cudaS
     CK(cudaMemsetAsync(w.sc, 0, sizeof(Scalars), s));
     QuantOut qo;
     memset(&qo, 0, sizeof(qo));
-    for (int l = L; l >= 1; l--) {
+    const LevelGeom<T> *geo = &geom<T>(P, 0);
+    const int ls = coarse_top<T>(P, geo);
+    for (int l = L; l > ls; l--) {
         T *vc = (T *)(((L - l) % 2 == 0) ? w.va : w.vb);
         RestrictArgs<T> a;
         memset(&a, 0, sizeof(a));
@@ -492,7 +516,13 @@ hpdr_status decompose_t(hpdr_ctx *ctx, const Plan *P, const T *u, T *coef, cudaS
         CK(launch_solves<T>(a.g, (T *)w.b, vc, +1, s));
         v = vc;
     }
-    CK(launch_level0<T>(Sink::STREAM, v, P->N[0], coef, qo, s));
+    if (ls >= 1) {
+        SymIn none;
+        memset(&none, 0, sizeof(none));
+        CK(launch_coarse<T>(1, P, geo, ls, v, nullptr, qo, coef, none, nullptr, s));
+    } else {
+        CK(launch_level0<T>(Sink::STREAM, v, P->N[0], coef, qo, s));
+    }
     return HPDR_OK;
 }
 
@@ -508,9 +538,19 @@ hpdr_status recompose_t(hpdr_ctx *ctx, const Plan *P, const T *coef, T *out, cud
     SymIn si;
     memset(&si, 0, sizeof(si));
     T *bufs[2] = {(T *)w.va, (T *)w.vb};
-    T *v = L == 0 ? out : bufs[0];
-    CK(launch_level0_in<T>(WSrc::STREAM, coef, si, P->N[0], v, s));
-    for (int l = 1; l <= L; l++) {
+    const LevelGeom<T> *geo = &geom<T>(P, 0);
+    const int ls = coarse_top<T>(P, geo);
+    T *v;
+    if (ls >= 1) {
+        v = (ls == L) ? out : bufs[ls % 2];
+        QuantOut none;
+        memset(&none, 0, sizeof(none));
+        CK(launch_coarse<T>(3, P, geo, ls, nullptr, v, none, nullptr, si, coef, s));
+    } else {
+        v = L == 0 ? out : bufs[0];
+        CK(launch_level0_in<T>(WSrc::STREAM, coef, si, P->N[0], v, s));
+    }
+    for (int l = ls + 1; l <= L; l++) {
         const LevelGeom<T> &g = geom<T>(P, l);
         RestrictArgs<T> a;
         memset(&a, 0, sizeof(a));

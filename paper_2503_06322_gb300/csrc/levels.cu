@@ -1321,6 +1321,255 @@ __global__ void bins_kernel(BinArgs ba, const double *partials, int nparts, Scal
     if (!ok) atomicExch(&sc->status, (unsigned int)DS_ARG);
 }
 
+// --------------------------------------------------------------------------
+// The coarse levels in one CTA.  Every level l <= ls (the largest level whose
+// working arrays fit in shared memory) and level 0 run in a single 1024-thread
+// block out of shared memory, instead of four or five launches per level.  A
+// level of compression (Alg. 1) here:
+//   1. v_c = the kept nodes of v, compacted; w = v - P v_c on the new nodes
+//      (0 on kept ones), quantized or written to the stream;
+//   2. b = (x)_k P^T M_l w, dimension 2, then 1, then 0 (5 taps each);
+//   3. z = (x)_k M_{l-1}^{-1} b, Thomas sweeps along dimension 0, 1, then 2;
+//   4. v_{l-1} = v_c + z.
+// Recomposition runs the levels upwards: w from the stream, b and z as above,
+// v_c = v_{l-1} - z, then v = P v_c + w.  P v_c is the multilinear
+// interpolant, taken along dimension 2, then 1, then 0.
+constexpr int kCoarseThreads = 1024;
+
+template <typename T>
+struct CoarseArgs {
+    LevelGeom<T> g[kCoarseMaxLevels + 1];   // levels 1..ls
+    int ls;
+    long long N0;
+    const T *v_in;       // compression / decomposition: the level-ls grid
+    T *v_out;            // recomposition: the level-ls grid
+    QuantOut qo;         // compression
+    T *coef_out;         // decomposition
+    SymIn symin;         // decompression
+    const T *coef_in;    // recomposition
+};
+
+// element counts of the shared arrays for top level ls (host and device)
+template <typename T>
+__host__ __device__ inline void coarse_sizes(const LevelGeom<T> &g, long long &nl, long long &nc, long long &r2,
+                                             long long &r1)
+{
+    const long long m0 = g.dim[0].m, m1 = g.dim[1].m, m2 = g.dim[2].m;
+    const long long c0 = g.dim[0].mc, c1 = g.dim[1].mc, c2 = g.dim[2].mc;
+    nl = m0 * m1 * m2;
+    nc = c0 * c1 * c2;
+    r2 = m0 * m1 * c2;
+    r1 = m0 * c1 * c2;
+}
+
+// multilinear interpolant of the compact coarse array X at fine node (p0, p1, p2)
+template <typename T>
+__device__ __forceinline__ T coarse_interp(const LevelGeom<T> &g, const T *X, int p0, int p1, int p2)
+{
+    const int c1 = g.dim[1].mc, c2 = g.dim[2].mc;
+    int a[3], b[3];
+    bool nw[3];
+    const int p[3] = {p0, p1, p2};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const int m = g.dim[k].m, mc = g.dim[k].mc;
+        nw[k] = !kept_pos(m, p[k]);
+        if (nw[k]) { a[k] = cidx_of(m, mc, p[k] - 1); b[k] = cidx_of(m, mc, p[k] + 1); }
+        else { a[k] = b[k] = cidx_of(m, mc, p[k]); }
+    }
+    auto along2 = [&](int i0, int i1) -> T {
+        const T *row = X + ((long long)i0 * c1 + i1) * c2;
+        if (!nw[2]) return row[a[2]];
+        return fma_rn(g.dim[2].wr[p2], row[b[2]], mul_rn(g.dim[2].wl[p2], row[a[2]]));
+    };
+    auto along1 = [&](int i0) -> T {
+        if (!nw[1]) return along2(i0, a[1]);
+        return fma_rn(g.dim[1].wr[p1], along2(i0, b[1]), mul_rn(g.dim[1].wl[p1], along2(i0, a[1])));
+    };
+    if (!nw[0]) return along1(a[0]);
+    return fma_rn(g.dim[0].wr[p0], along1(b[0]), mul_rn(g.dim[0].wl[p0], along1(a[0])));
+}
+
+// out = in restricted along dimension k with the 5 taps of P^T M_l; in has
+// extents n[3] (n[k] = m), out the same with n[k] = mc
+template <typename T>
+__device__ void coarse_restrict(const DimTables<T> &d, int k, const int n[3], const T *in, T *out)
+{
+    int o[3] = {n[0], n[1], n[2]};
+    o[k] = d.mc;
+    const long long tot = (long long)o[0] * o[1] * o[2];
+    const long long is[3] = {(long long)n[1] * n[2], n[2], 1};
+    for (long long idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+        const int j2 = (int)(idx % o[2]);
+        const long long r = idx / o[2];
+        const int j1 = (int)(r % o[1]), j0 = (int)(r / o[1]);
+        const int jj[3] = {j0, j1, j2};
+        if (d.m <= 1) { out[idx] = in[j0 * is[0] + j1 * is[1] + j2]; continue; }
+        const int jk = jj[k];
+        const int c = cpos_of(d.m, d.mc, jk);
+        long long base = 0;
+#pragma unroll
+        for (int q = 0; q < 3; q++) if (q != k) base += jj[q] * is[q];
+        T acc = (T)0;
+#pragma unroll
+        for (int t = 0; t < 5; t++) {
+            const int pos = c - 2 + t;
+            if (pos < 0 || pos >= d.m) continue;
+            acc = fma_rn(d.tap[jk * 5 + t], in[base + pos * is[k]], acc);
+        }
+        out[idx] = acc;
+    }
+}
+
+// Thomas sweeps of (x)_k M_{l-1} on the compact coarse array B (extents c[3]), in place
+template <typename T>
+__device__ void coarse_solves(const LevelGeom<T> &g, const int c[3], T *B)
+{
+    for (int k = 0; k < 3; k++) {
+        const DimTables<T> &d = g.dim[k];
+        if (!(d.m > 1)) continue;
+        const long long st = k == 0 ? (long long)c[1] * c[2] : k == 1 ? c[2] : 1;
+        const int oa = k == 0 ? c[1] : c[0], ob = k == 2 ? c[1] : c[2];
+        for (int line = threadIdx.x; line < oa * ob; line += blockDim.x) {
+            const int u = line / ob, v = line - u * ob;
+            long long base;
+            if (k == 0) base = (long long)u * c[2] + v;
+            else if (k == 1) base = (long long)u * c[1] * c[2] + v;
+            else base = ((long long)u * c[1] + v) * c[2];
+            T *p = B + base;
+            const int n = d.mc;
+            T y = (T)0;
+            for (int t = 0; t < n; t++) { y = mul_rn(fma_rn(-d.sub[t], y, p[t * st]), d.inv_den[t]); p[t * st] = y; }
+            T x = (T)0;
+            for (int t = n - 1; t >= 0; t--) { x = fma_rn(-d.cp[t], x, p[t * st]); p[t * st] = x; }
+        }
+        __syncthreads();
+    }
+}
+
+// b = (x)_k P^T M_l W into B (R2, R1 scratch)
+template <typename T>
+__device__ void coarse_rhs(const LevelGeom<T> &g, const T *W, T *R2, T *R1, T *B)
+{
+    const int m[3] = {g.dim[0].m, g.dim[1].m, g.dim[2].m};
+    const int n2[3] = {m[0], m[1], m[2]};
+    coarse_restrict<T>(g.dim[2], 2, n2, W, R2);
+    __syncthreads();
+    const int n1[3] = {m[0], m[1], g.dim[2].mc};
+    coarse_restrict<T>(g.dim[1], 1, n1, R2, R1);
+    __syncthreads();
+    const int n0[3] = {m[0], g.dim[1].mc, g.dim[2].mc};
+    coarse_restrict<T>(g.dim[0], 0, n0, R1, B);
+    __syncthreads();
+}
+
+// MODE 0: compression (quantize), 1: decomposition (coefficient stream),
+// 2: decompression (symbols), 3: recomposition (coefficient stream)
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kCoarseThreads, 1) coarse_kernel(CoarseArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char coarse_smem[];
+    long long nl, nc, r2, r1;
+    coarse_sizes<T>(a.g[a.ls], nl, nc, r2, r1);
+    T *VA = reinterpret_cast<T *>(coarse_smem);   // [nl]
+    T *VB = VA + nl;                                // [nc]
+    T *W = VB + nc;                                 // [nl]
+    T *R2 = W + nl;                                 // [r2]
+    T *R1 = R2 + r2;                                // [r1]
+    T *B = R1 + r1;                                 // [nc]
+    T *VK = B + nc;                                 // [nc]
+    const int tid = threadIdx.x;
+    if (MODE <= 1) {
+        for (long long i = tid; i < nl; i += blockDim.x) VA[i] = a.v_in[i];
+        __syncthreads();
+        T *V = VA, *Vn = VB;
+        for (int l = a.ls; l >= 1; l--) {
+            const LevelGeom<T> &g = a.g[l];
+            const int m1 = g.dim[1].m, m2 = g.dim[2].m;
+            const int c[3] = {g.dim[0].mc, g.dim[1].mc, g.dim[2].mc};
+            const long long n = (long long)g.dim[0].m * m1 * m2, ncl = (long long)c[0] * c[1] * c[2];
+            // 1. kept nodes, compacted
+            for (long long j = tid; j < ncl; j += blockDim.x) {
+                const int j2 = (int)(j % c[2]);
+                const long long r = j / c[2];
+                const int j1 = (int)(r % c[1]), j0 = (int)(r / c[1]);
+                const long long f = ((long long)cpos_of(g.dim[0].m, c[0], j0) * m1 + cpos_of(m1, c[1], j1)) * m2 +
+                                    cpos_of(m2, c[2], j2);
+                VK[j] = V[f];
+            }
+            __syncthreads();
+            //    coefficients of the new nodes
+            const T rho = MODE == 0 ? rho_of<T>(a.qo.sc, l) : (T)0;
+            for (long long i = tid; i < n; i += blockDim.x) {
+                const int p2 = (int)(i % m2);
+                const long long r = i / m2;
+                const int p1 = (int)(r % m1), p0 = (int)(r / m1);
+                if (kept_pos(g.dim[0].m, p0) && kept_pos(m1, p1) && kept_pos(m2, p2)) { W[i] = (T)0; continue; }
+                const T w = sub_rn(V[i], coarse_interp<T>(g, VK, p0, p1, p2));
+                W[i] = w;
+                const long long si = stream_rank(g, p0, p1, p2);
+                if (MODE == 0) quant_emit(a.qo, nullptr, false, si, w, rho);
+                else a.coef_out[si] = w;
+            }
+            __syncthreads();
+            // 2.-3.
+            coarse_rhs<T>(g, W, R2, R1, B);
+            coarse_solves<T>(g, c, B);
+            // 4.
+            for (long long j = tid; j < ncl; j += blockDim.x) Vn[j] = add_rn(VK[j], B[j]);
+            __syncthreads();
+            T *t = V; V = Vn; Vn = t;
+        }
+        // level 0
+        const T rho0 = MODE == 0 ? rho_of<T>(a.qo.sc, 0) : (T)0;
+        for (long long i = tid; i < a.N0; i += blockDim.x) {
+            if (MODE == 0) quant_emit(a.qo, nullptr, false, i, V[i], rho0);
+            else a.coef_out[i] = V[i];
+        }
+    } else {
+        T *V = VA, *Vn = VB;
+        // the same ping-pong as compression, run backwards: level l's grid lands
+        // where compression read it (the top level in VA)
+        if ((a.ls & 1) == 1) { V = VB; Vn = VA; }
+        const T q0 = MODE == 2 ? q_of<T>(a.symin.sc, 0) : (T)0;
+        for (long long i = tid; i < a.N0; i += blockDim.x)
+            V[i] = MODE == 2 ? dequant_sym<T>(a.symin, a.symin.sym[i], i, q0) : a.coef_in[i];
+        __syncthreads();
+        for (int l = 1; l <= a.ls; l++) {
+            const LevelGeom<T> &g = a.g[l];
+            const int m1 = g.dim[1].m, m2 = g.dim[2].m;
+            const int c[3] = {g.dim[0].mc, g.dim[1].mc, g.dim[2].mc};
+            const long long n = (long long)g.dim[0].m * m1 * m2, ncl = (long long)c[0] * c[1] * c[2];
+            const T q = MODE == 2 ? q_of<T>(a.symin.sc, l) : (T)0;
+            for (long long i = tid; i < n; i += blockDim.x) {
+                const int p2 = (int)(i % m2);
+                const long long r = i / m2;
+                const int p1 = (int)(r % m1), p0 = (int)(r / m1);
+                if (kept_pos(g.dim[0].m, p0) && kept_pos(m1, p1) && kept_pos(m2, p2)) { W[i] = (T)0; continue; }
+                const long long si = stream_rank(g, p0, p1, p2);
+                W[i] = MODE == 2 ? dequant_sym<T>(a.symin, a.symin.sym[si], si, q) : a.coef_in[si];
+            }
+            __syncthreads();
+            coarse_rhs<T>(g, W, R2, R1, B);
+            coarse_solves<T>(g, c, B);
+            for (long long j = tid; j < ncl; j += blockDim.x) VK[j] = sub_rn(V[j], B[j]);
+            __syncthreads();
+            for (long long i = tid; i < n; i += blockDim.x) {
+                const int p2 = (int)(i % m2);
+                const long long r = i / m2;
+                const int p1 = (int)(r % m1), p0 = (int)(r / m1);
+                const bool kept = kept_pos(g.dim[0].m, p0) && kept_pos(m1, p1) && kept_pos(m2, p2);
+                Vn[i] = kept ? VK[((long long)cidx_of(g.dim[0].m, c[0], p0) * c[1] + cidx_of(m1, c[1], p1)) * c[2] +
+                                  cidx_of(m2, c[2], p2)]
+                             : add_rn(W[i], coarse_interp<T>(g, VK, p0, p1, p2));
+            }
+            __syncthreads();
+            T *t = V; V = Vn; Vn = t;
+        }
+        for (long long i = tid; i < nl; i += blockDim.x) a.v_out[i] = V[i];
+    }
+}
+
 }  // namespace
 
 int norm_parts() { return kNormBlocks; }
@@ -1486,6 +1735,56 @@ cudaError_t launch_bins(const BinArgs &ba, const double *partials, int nparts, S
     return cudaGetLastError();
 }
 
+
+template <typename T>
+size_t coarse_smem_bytes(const LevelGeom<T> &g)
+{
+    long long nl, nc, r2, r1;
+    coarse_sizes<T>(g, nl, nc, r2, r1);
+    return (size_t)(2 * nl + 3 * nc + r2 + r1) * sizeof(T);
+}
+
+template <typename T>
+int coarse_top(const Plan *P, const LevelGeom<T> *geo)
+{
+    int ls = 0;
+    for (int l = 1; l <= P->L && l <= kCoarseMaxLevels; l++)
+        if (coarse_smem_bytes<T>(geo[l]) <= kCoarseSmem) ls = l;
+        else break;
+    return ls;
+}
+
+template <typename T>
+cudaError_t launch_coarse(int mode, const Plan *P, const LevelGeom<T> *geo, int ls, const T *v_in, T *v_out,
+                          const QuantOut &qo, T *coef_out, const SymIn &symin, const T *coef_in, cudaStream_t s)
+{
+    if (ls < 1 || ls > kCoarseMaxLevels) return cudaErrorInvalidValue;
+    CoarseArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    for (int l = 1; l <= ls; l++) a.g[l] = geo[l];
+    a.ls = ls;
+    a.N0 = P->N[0];
+    a.v_in = v_in; a.v_out = v_out; a.qo = qo; a.coef_out = coef_out; a.symin = symin; a.coef_in = coef_in;
+    const size_t sm = coarse_smem_bytes<T>(geo[ls]);
+    static bool attr[4] = {false, false, false, false};
+    auto go = [&](auto kern) -> cudaError_t {
+        if (!attr[mode]) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmem);
+            if (e != cudaSuccess) return e;
+            attr[mode] = true;
+        }
+        kern<<<1, kCoarseThreads, sm, s>>>(a);
+        count_launch();
+        return cudaGetLastError();
+    };
+    switch (mode) {
+    case 0: return go(coarse_kernel<T, 0>);
+    case 1: return go(coarse_kernel<T, 1>);
+    case 2: return go(coarse_kernel<T, 2>);
+    default: return go(coarse_kernel<T, 3>);
+    }
+}
+
 #define INST(T)                                                                                   \
     template cudaError_t launch_restrict<T>(WSrc, Sink, const RestrictArgs<T> &, cudaStream_t);  \
     template cudaError_t launch_solves<T>(const LevelGeom<T> &, T *, T *, int, cudaStream_t);    \
@@ -1495,7 +1794,10 @@ cudaError_t launch_bins(const BinArgs &ba, const double *partials, int nparts, S
                                           cudaStream_t);                                         \
     template cudaError_t launch_level0_in<T>(WSrc, const T *, const SymIn &, long long, T *,      \
                                              cudaStream_t);                                      \
-    template cudaError_t launch_norm<T>(const T *, long long, double *, int, cudaStream_t);
+    template cudaError_t launch_norm<T>(const T *, long long, double *, int, cudaStream_t);      \
+    template int coarse_top<T>(const Plan *, const LevelGeom<T> *);                              \
+    template cudaError_t launch_coarse<T>(int, const Plan *, const LevelGeom<T> *, int, const T *, T *, \
+                                          const QuantOut &, T *, const SymIn &, const T *, cudaStream_t);
 INST(float)
 INST(double)
 

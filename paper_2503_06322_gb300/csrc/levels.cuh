@@ -91,6 +91,18 @@ cudaError_t launch_mass_prolong(const LevelGeom<T> &g, const T *yc, T *yf, T *tm
 
 int norm_parts();
 
+// The coarse levels in one CTA (levels.cu): levels 1..ls and level 0, with
+// ls = coarse_top(), the largest level whose shared arrays fit kCoarseSmem.
+// mode 0: compression (v_in -> symbols), 1: decomposition (v_in -> coef_out),
+// 2: decompression (symbols -> v_out), 3: recomposition (coef_in -> v_out).
+constexpr int kCoarseMaxLevels = 16;
+constexpr size_t kCoarseSmem = 200 * 1024;
+template <typename T>
+int coarse_top(const Plan *P, const LevelGeom<T> *geo);
+template <typename T>
+cudaError_t launch_coarse(int mode, const Plan *P, const LevelGeom<T> *geo, int ls, const T *v_in, T *v_out,
+                          const QuantOut &qo, T *coef_out, const SymIn &symin, const T *coef_in, cudaStream_t s);
+
 // adjoint.cu: transposes of recomposition / decomposition over all levels.
 // ga, gb, y, R hold N_{L-1} elements; t1, t2 the partial prolongations
 // (max over levels of c0*c1*m2 and c0*m1*m2 elements).

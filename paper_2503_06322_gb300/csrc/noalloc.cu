@@ -63,7 +63,10 @@ hpdr_status decompose_into(const hpdr::Plan &P, const T *u, T *coef, char *scrat
     QuantOut qo;
     memset(&qo, 0, sizeof(qo));
     const T *v = u;
-    for (int l = L; l >= 1; l--) {
+    // the same split as hpdr_decompose: levels 1..ls and level 0 in one CTA
+    const LevelGeom<T> *geo = &geom_of<T>(P, 0);
+    const int ls = coarse_top<T>(&P, geo);
+    for (int l = L; l > ls; l--) {
         T *vc = ((L - l) % 2 == 0) ? va : vb;
         RestrictArgs<T> a;
         memset(&a, 0, sizeof(a));
@@ -78,7 +81,14 @@ hpdr_status decompose_into(const hpdr::Plan &P, const T *u, T *coef, char *scrat
         if (launch_solves<T>(a.g, b, vc, +1, s) != cudaSuccess) return HPDR_ERR_CUDA;
         v = vc;
     }
-    if (launch_level0<T>(Sink::STREAM, v, P.N[0], coef, qo, s) != cudaSuccess) return HPDR_ERR_CUDA;
+    if (ls >= 1) {
+        SymIn none;
+        memset(&none, 0, sizeof(none));
+        if (launch_coarse<T>(1, &P, geo, ls, v, nullptr, qo, coef, none, nullptr, s) != cudaSuccess)
+            return HPDR_ERR_CUDA;
+    } else if (launch_level0<T>(Sink::STREAM, v, P.N[0], coef, qo, s) != cudaSuccess) {
+        return HPDR_ERR_CUDA;
+    }
     return HPDR_OK;
 }
 
