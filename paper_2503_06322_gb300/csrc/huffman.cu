@@ -1045,16 +1045,6 @@ __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
 }
 
 
-__device__ uint32_t crc32_bytes(const uint8_t *p, int n)
-{
-    uint32_t c = 0xFFFFFFFFu;
-    for (int i = 0; i < n; i++) {
-        c ^= p[i];
-        for (int b = 0; b < 8; b++) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
-    }
-    return c ^ 0xFFFFFFFFu;
-}
-
 __device__ __forceinline__ void put32(uint8_t *p, uint32_t v) { for (int i = 0; i < 4; i++) p[i] = (uint8_t)(v >> (8 * i)); }
 __device__ __forceinline__ void put64(uint8_t *p, unsigned long long v) { for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i)); }
 __device__ __forceinline__ void putd(uint8_t *p, double v) { put64(p, (unsigned long long)__double_as_longlong(v)); }
@@ -1063,12 +1053,20 @@ __global__ void __launch_bounds__(256)
 header_kernel(HeaderArgs h, const uint8_t *len, Scalars *sc, uint8_t *out)
 {
     __shared__ uint8_t hdr[128];
+    __shared__ uint32_t crct[256];
     if (block_skip(&sc->status)) return;
     const unsigned long long nch = (h.N + h.K - 1) / h.K;
     Layout lay = container_layout(h.L, sc->s_lo, sc->s_hi, nch, sc->total_bits);
     const unsigned long long n_esc = h.hist ? h.hist[0] : 0ULL;
+    // CRC-32 (reflected, polynomial 0xEDB88320) by a byte table, one entry per thread
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        uint32_t c = (uint32_t)i;
+        for (int b = 0; b < 8; b++) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
+        crct[i] = c;
+    }
+    for (int i = threadIdx.x; i < 128; i += blockDim.x) hdr[i] = 0;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 128; i++) hdr[i] = 0;
         hdr[0] = 'H'; hdr[1] = 'P'; hdr[2] = 'D'; hdr[3] = 'R';
         put32(hdr + 4, 3);
         put32(hdr + 8, (uint32_t)h.dtype);
@@ -1089,7 +1087,9 @@ header_kernel(HeaderArgs h, const uint8_t *len, Scalars *sc, uint8_t *out)
         sc->n_esc = n_esc;
         put64(hdr + 112, sc->total_bits);
         put32(hdr + 120, sc->s_hi | ((n_esc ? sc->esc_w : 0u) << 16));
-        put32(hdr + 124, crc32_bytes(hdr, 124));
+        uint32_t c = 0xFFFFFFFFu;
+        for (int i = 0; i < 124; i++) c = crct[(c ^ hdr[i]) & 0xFFu] ^ (c >> 8);
+        put32(hdr + 124, c ^ 0xFFFFFFFFu);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 128; i += blockDim.x) out[i] = hdr[i];

@@ -1292,22 +1292,24 @@ __global__ void bins_kernel(BinArgs ba, const double *partials, int nparts, Scal
         }
         __syncthreads();
     }
-    if (threadIdx.x != 0) return;
     mx = smx[0];
     ss = sss[0];
-    sc->maxabs = mx;
-    sc->sumsq = ss;
+    if (threadIdx.x == 0) {
+        sc->maxabs = mx;
+        sc->sumsq = ss;
+    }
     const int L = ba.L;
     bool ok = mx <= DBL_MAX;
     double nrm = ba.mode == 0 ? mx : sqrt(__ddiv_rn(ss, (double)ba.N));
     double tau = ba.tol_kind == 1 ? __dmul_rn(ba.tol, nrm) : ba.tol;
-    sc->tau_abs = tau;
+    if (threadIdx.x == 0) sc->tau_abs = tau;
     double tp = 0.0;
     if (ok && mx > 0.0) {
         tp = __dsub_rn(tau, __dmul_rn(__dmul_rn(__dmul_rn(32.0, (double)(L + 1)), ba.eps), mx));
         if (!(tp > 0.0)) ok = false;
     }
-    for (int l = 0; l <= L; l++) {
+    // one level per thread (two FP64 divisions each)
+    for (int l = threadIdx.x; l <= L; l += blockDim.x) {
         double q;
         if (!ok || mx == 0.0) q = 1.0;
         else if (l == 0) q = __ddiv_rn(__dmul_rn(2.0, tp), (double)(L + 1));
@@ -1318,7 +1320,7 @@ __global__ void bins_kernel(BinArgs ba, const double *partials, int nparts, Scal
         sc->rho_f[l] = __double2float_rn(r);
         sc->q_f[l] = __double2float_rn(q);
     }
-    if (!ok) atomicExch(&sc->status, (unsigned int)DS_ARG);
+    if (!ok && threadIdx.x == 0) atomicExch(&sc->status, (unsigned int)DS_ARG);
 }
 
 // --------------------------------------------------------------------------
