@@ -1345,7 +1345,9 @@ __global__ void __launch_bounds__(kDecThreads, 1) decode_kernel(DecodeArgs a, Hu
             o.y = (uint32_t)step(i + 2) | ((uint32_t)step(i + 3) << 16);
             o.z = (uint32_t)step(i + 4) | ((uint32_t)step(i + 5) << 16);
             o.w = (uint32_t)step(i + 6) | ((uint32_t)step(i + 7) << 16);
-            *reinterpret_cast<uint4 *>(a.sym + i) = o;
+            // streaming store: the symbols are written once and read by the next
+            // kernel, so they should not push the bitstream out of L2
+            __stcs(reinterpret_cast<uint4 *>(a.sym + i), o);
         }
         for (; i + 2 <= end; i += 2) {
             const uint32_t v0 = step(i);

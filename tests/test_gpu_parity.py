@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 SHAPES = [(2,), (3,), (33,), (1000,), (3, 2), (6, 5), (129, 129), (65, 33), (500, 50),
           (6, 5, 4), (9, 6, 5), (33, 17, 9), (70, 70, 70), (100, 7, 5), (65, 65, 65),
-          (17, 100, 41)]
+          (17, 100, 41), (300, 200), (100, 60, 40)]
 
 
 @pytest.fixture(scope="module")
