@@ -966,6 +966,20 @@ __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
         bool have_first = false;
         // append the low L bits of cw (L <= 64), most significant first
         auto emit = [&](unsigned long long cw, int L) {
+            if (L <= 32) {
+                // nacc < 32 here, so the codeword fits the 64-bit accumulator whole
+                acc |= cw << (64 - nacc - L);
+                nacc += L;
+                if (nacc >= 32) {
+                    const uint32_t wv = (uint32_t)(acc >> 32);
+                    if (!have_first) { firstw = wv; have_first = true; }
+                    else words[widx] = wv;
+                    widx++;
+                    acc <<= 32;
+                    nacc -= 32;
+                }
+                return;
+            }
             while (L > 0) {
                 const int take = L > 32 ? 32 : L;
                 const unsigned long long part = (cw >> (L - take)) & ((1ULL << take) - 1);
