@@ -39,6 +39,10 @@ def _L():
             "oracle_levels": [C.c_int, sz, C.POINTER(C.c_int), sz],
             "oracle_decompose": [C.c_int, sz, dp, dp],
             "oracle_recompose": [C.c_int, sz, dp, dp],
+            "oracle_decompose_c": [C.c_int, sz, dp, dp, dp],
+            "oracle_recompose_c": [C.c_int, sz, dp, dp, dp],
+            "oracle_correction_norms_c": [C.c_int, sz, dp, dp],
+            "oracle_bins_c": [C.c_int, sz, dp, C.c_double, C.c_double, C.c_double, dp],
             "oracle_recompose_adjoint": [C.c_int, sz, dp, dp],
             "oracle_decompose_adjoint": [C.c_int, sz, dp, dp],
             "oracle_correction_norms": [C.c_int, sz, dp],
@@ -54,6 +58,9 @@ def _L():
             "oracle_decode": [u32, C.c_uint64, u64, C.c_uint64, C.c_uint32, u8, C.c_uint32, u16,
                               C.c_int, i64, C.c_uint64, u64],
             "oracle_escape_bits": [C.c_int64],
+            "oracle_compress_c": [C.c_int, sz, dp, dp, C.c_int, C.c_double, C.c_int, C.c_int,
+                                  C.c_uint32, C.c_uint32, C.POINTER(C.c_uint8), C.c_uint64,
+                                  C.POINTER(C.c_uint64)],
             "oracle_compress": [C.c_int, sz, dp, C.c_int, C.c_double, C.c_int, C.c_int,
                                 C.c_uint32, C.c_uint32, u8, C.c_uint64, u64],
             "oracle_decompress": [u8, C.c_uint64, dp, C.c_uint64],
@@ -113,14 +120,38 @@ def _field_op(fn, x, shape, what):
     return out
 
 
-def decompose(u):
-    """Level-major coefficient stream (FP64) of the field u (Alg. 1)."""
+def _coords(shape, coords):
+    """Concatenated node coordinates (dimension 0 first) or None; accepts a
+    sequence of per-dimension arrays or one flat array."""
+    if coords is None:
+        return None
+    if isinstance(coords, (list, tuple)):
+        if len(coords) != len(shape) or any(len(c) != n for c, n in zip(coords, shape)):
+            raise ValueError("one coordinate array per dimension, of the dimension's length")
+        coords = np.concatenate([np.asarray(c, dtype=np.float64) for c in coords])
+    coords = np.ascontiguousarray(coords, dtype=np.float64).reshape(-1)
+    if coords.size != int(sum(shape)):
+        raise ValueError("coords must hold sum(shape) values")
+    return coords
+
+
+def decompose(u, coords=None):
+    """Level-major coefficient stream (FP64) of the field u (Alg. 1); coords:
+    node coordinates of every dimension (default: node i at coordinate i)."""
     u = np.asarray(u)
-    return _field_op(_L().oracle_decompose, u, u.shape, "decompose")
+    co = _coords(u.shape, coords)
+    if co is None:
+        return _field_op(_L().oracle_decompose, u, u.shape, "decompose")
+    return _field_op(lambda d, dims, x, o: _L().oracle_decompose_c(d, dims, _p(co, C.c_double), x, o),
+                     u, u.shape, "decompose")
 
 
-def recompose(coef, shape):
-    return _field_op(_L().oracle_recompose, coef, shape, "recompose").reshape(shape)
+def recompose(coef, shape, coords=None):
+    co = _coords(shape, coords)
+    if co is None:
+        return _field_op(_L().oracle_recompose, coef, shape, "recompose").reshape(shape)
+    return _field_op(lambda d, dims, x, o: _L().oracle_recompose_c(d, dims, _p(co, C.c_double), x, o),
+                     coef, shape, "recompose").reshape(shape)
 
 
 def recompose_adjoint(g_u):
@@ -133,20 +164,23 @@ def decompose_adjoint(g_coef, shape):
                      "decompose_adjoint").reshape(shape)
 
 
-def correction_norms(shape):
+def correction_norms(shape, coords=None):
     d, dims = _dims(shape)
     L, _ = levels(shape)
     c = np.zeros(L + 1)
-    _check(_L().oracle_correction_norms(d, dims, _p(c, C.c_double)), "correction_norms")
+    co = _coords(shape, coords)
+    _check(_L().oracle_correction_norms_c(d, dims, None if co is None else _p(co, C.c_double),
+                                          _p(c, C.c_double)), "correction_norms")
     return c
 
 
-def bins(shape, tau_abs, norm_inf, eps):
+def bins(shape, tau_abs, norm_inf, eps, coords=None):
     d, dims = _dims(shape)
     L, _ = levels(shape)
     q = np.zeros(L + 1)
-    _check(_L().oracle_bins(d, dims, float(tau_abs), float(norm_inf), float(eps),
-                            _p(q, C.c_double)), "bins")
+    co = _coords(shape, coords)
+    _check(_L().oracle_bins_c(d, dims, None if co is None else _p(co, C.c_double), float(tau_abs),
+                              float(norm_inf), float(eps), _p(q, C.c_double)), "bins")
     return q
 
 
@@ -265,8 +299,9 @@ def compress_bound(shape, D=8192, K=1024):
     return int(_L().oracle_compress_bound(d, dims, D, K))
 
 
-def compress(u, tol, tol_kind=REL, mode=LINF, D=8192, K=1024, dtype=None):
-    """Container bytes of the field u (dtype defaults to u's own: f32 or f64)."""
+def compress(u, tol, tol_kind=REL, mode=LINF, D=8192, K=1024, dtype=None, coords=None):
+    """Container bytes of the field u (dtype defaults to u's own: f32 or f64);
+    coords: node coordinates (recorded in the container)."""
     u = np.asarray(u)
     if dtype is None:
         dtype = DTYPE_F32 if u.dtype == np.float32 else DTYPE_F64
@@ -275,8 +310,10 @@ def compress(u, tol, tol_kind=REL, mode=LINF, D=8192, K=1024, dtype=None):
     cap = compress_bound(u.shape, D, K)
     out = np.zeros(cap, dtype=np.uint8)
     nb = C.c_uint64()
-    _check(_L().oracle_compress(d, dims, _p(x, C.c_double), dtype, float(tol), tol_kind, mode, D,
-                                K, _p(out, C.c_uint8), cap, C.byref(nb)), "compress")
+    co = _coords(u.shape, coords)
+    _check(_L().oracle_compress_c(d, dims, None if co is None else _p(co, C.c_double), _p(x, C.c_double),
+                                  dtype, float(tol), tol_kind, mode, D, K, _p(out, C.c_uint8), cap,
+                                  C.byref(nb)), "compress")
     return out[:nb.value].copy()
 
 
@@ -313,20 +350,24 @@ def parse_header(buf):
     f64 = lambda o: float(np.frombuffer(b[o:o + 8], dtype="<f8")[0])  # noqa: E731
     h = dict(magic=b[:4], version=u32(4), dtype=u32(8), ndim=u32(12),
              dims=tuple(u64(16 + 8 * k) for k in range(u32(12))), L=u32(40), mode=u32(44),
-             tol_kind=u32(48), D=u32(52), K=u32(56), s_lo=u32(60), tol=f64(64),
+             tol_kind=u32(48) & 0xFF, has_coords=bool(u32(48) & 0x100), D=u32(52), K=u32(56),
+             s_lo=u32(60), tol=f64(64),
              tau_abs=f64(72), norm_inf=f64(80), norm_rms=f64(88), N=u64(96),
              n_escapes=u64(104), total_bits=u64(112), s_hi=u32(120) & 0xFFFF,
              esc_width=(u32(120) >> 16) & 0xFF, crc=u32(124))
     a16 = lambda x: (x + 15) & ~15  # noqa: E731
     L = h["L"]
     off_q = 128
-    off_len = a16(off_q + 8 * (L + 1))
+    nco = sum(h["dims"]) if h["has_coords"] else 0
+    off_co = off_q + 8 * (L + 1)
+    off_len = a16(off_co + 8 * nco)
     off_chunk = a16(off_len + h["s_hi"] - h["s_lo"] + 1)
     nch = (h["N"] + h["K"] - 1) // h["K"]
     off_bits = a16(off_chunk + 8 * nch)
     nw = (h["total_bits"] + 31) // 32
     arr = np.frombuffer(b, dtype=np.uint8)
     h["q"] = arr[off_q:off_q + 8 * (L + 1)].view("<f8").copy()
+    h["coords"] = arr[off_co:off_co + 8 * nco].view("<f8").copy() if nco else None
     ln = np.zeros(h["D"], dtype=np.uint8)
     ln[h["s_lo"]:h["s_hi"] + 1] = arr[off_len:off_len + h["s_hi"] - h["s_lo"] + 1]
     h["lengths"] = ln

@@ -8,13 +8,16 @@
  * padding bytes are zero):
  *   0   "HPDR"            4  u32 version (3)     8  u32 dtype (0 f32, 1 f64)
  *   12  u32 ndim          16 u64 dims[3] (unused dims hold 1)
- *   40  u32 L             44 u32 mode (0 Linf, 1 L2)   48 u32 tol kind (0 abs, 1 rel)
+ *   40  u32 L             44 u32 mode (0 Linf, 1 L2)
+ *   48  u32 tol kind (0 abs, 1 rel) | 0x100 when the container holds node coordinates
  *   52  u32 D             56 u32 K               60 u32 s_lo
  *   64  f64 tol           72 f64 tau_abs         80 f64 max|u|    88 f64 rms(u)
  *   96  u64 N             104 u64 escapes        112 u64 bitstream bits
  *   120 u16 s_hi          122 u8 escape width W   123 u8 0
  *   124 u32 CRC-32 of bytes [0,124)
  *   128 f64 q[L+1]
+ *   with the coordinate flag: f64 node coordinates, dims[0] + ... + dims[ndim-1]
+ *                 values, dimension 0 first (directly after q, 8-byte aligned)
  *   code lengths  u8[s_hi - s_lo + 1]  (symbols s_lo..s_hi)
  *   chunk table   u64[ceil(N/K)]       (bit offset of symbol j*K)
  *   bitstream     u32[ceil(bits/32)]
@@ -58,9 +61,10 @@ uint64_t oracle_compress_bound(int d, const size_t *n, uint32_t D, uint32_t K)
 {
     int L;
     if (oracle_levels(d, n, &L, NULL) || K == 0) return 0;
-    uint64_t N = 1;
-    for (int k = 0; k < d; k++) N *= n[k];
-    uint64_t b = align16(HDR + 8 * (uint64_t)(L + 1));
+    uint64_t N = 1, nco = 0;
+    for (int k = 0; k < d; k++) { N *= n[k]; nco += n[k]; }
+    /* room for the node coordinates, present or not */
+    uint64_t b = align16(HDR + 8 * (uint64_t)(L + 1) + 8 * nco);
     b = align16(b + D);
     b = align16(b + 8 * ((N + K - 1) / K));
     /* Huffman bits <= N ceil(log2 D) (a fixed-length code is a prefix code);
@@ -74,6 +78,13 @@ uint64_t oracle_compress_bound(int d, const size_t *n, uint32_t D, uint32_t K)
 int oracle_compress(int d, const size_t *n, const double *u, int dtype, double tol, int tol_kind,
                     int mode, uint32_t D, uint32_t K, uint8_t *out, uint64_t cap,
                     uint64_t *out_bytes)
+{
+    return oracle_compress_c(d, n, NULL, u, dtype, tol, tol_kind, mode, D, K, out, cap, out_bytes);
+}
+
+int oracle_compress_c(int d, const size_t *n, const double *coords, const double *u, int dtype, double tol,
+                      int tol_kind, int mode, uint32_t D, uint32_t K, uint8_t *out, uint64_t cap,
+                      uint64_t *out_bytes)
 {
     int L;
     if (oracle_levels(d, n, &L, NULL)) return -1;
@@ -90,13 +101,13 @@ int oracle_compress(int d, const size_t *n, const double *u, int dtype, double t
     double tau_abs = (tol_kind == 1) ? tol * nrm : tol;
     double eps = (dtype == 0) ? ldexp(1.0, -24) : ldexp(1.0, -53);
     double *q = (double *)malloc((size_t)(L + 1) * sizeof(double));
-    int rc = oracle_bins(d, n, tau_abs, mx, eps, q);
+    int rc = oracle_bins_c(d, n, coords, tau_abs, mx, eps, q);
     if (rc) { free(q); return (rc == -2) ? -1 : rc; }
 
     double *coef = (double *)malloc(N * sizeof(double));
     uint16_t *sym = (uint16_t *)malloc(N * sizeof(uint16_t));
     uint64_t nout = 0;
-    oracle_decompose(d, n, u, coef);
+    if (oracle_decompose_c(d, n, coords, u, coef)) { free(q); free(coef); free(sym); return -1; }
     oracle_quantize(d, n, coef, q, 64, D, sym, &nout, NULL, NULL, 0);
     uint64_t *oidx = (uint64_t *)malloc((nout + 1) * sizeof(uint64_t));
     int64_t *ok = (int64_t *)malloc((nout + 1) * sizeof(int64_t));
@@ -113,8 +124,11 @@ int oracle_compress(int d, const size_t *n, const double *u, int dtype, double t
     for (uint32_t s = D; s-- > 0;) if (len[s]) { shi = s; break; }
 
     uint64_t nch = (N + K - 1) / K;
+    uint64_t nco = 0;
+    if (coords) for (int k = 0; k < d; k++) nco += n[k];
     uint64_t off_q = HDR;
-    uint64_t off_len = align16(off_q + 8 * (uint64_t)(L + 1));
+    uint64_t off_co = off_q + 8 * (uint64_t)(L + 1);
+    uint64_t off_len = align16(off_co + 8 * nco);
     uint64_t off_chunk = align16(off_len + (shi - slo + 1));
     uint64_t off_bits = align16(off_chunk + 8 * nch);
     uint64_t bits = 0;
@@ -143,7 +157,7 @@ int oracle_compress(int d, const size_t *n, const double *u, int dtype, double t
         for (int k = 0; k < 3; k++) put64(out + 16 + 8 * k, (k < d) ? (uint64_t)n[k] : 1);
         put32(out + 40, (uint32_t)L);
         put32(out + 44, (uint32_t)mode);
-        put32(out + 48, (uint32_t)tol_kind);
+        put32(out + 48, (uint32_t)tol_kind | (coords ? 0x100u : 0u));
         put32(out + 52, D);
         put32(out + 56, K);
         put32(out + 60, slo);
@@ -157,6 +171,7 @@ int oracle_compress(int d, const size_t *n, const double *u, int dtype, double t
         put32(out + 120, shi | ((uint32_t)ew << 16));
         put32(out + 124, oracle_crc32(out, 124));
         for (int l = 0; l <= L; l++) putf64(out + off_q + 8 * l, q[l]);
+        for (uint64_t i = 0; i < nco; i++) putf64(out + off_co + 8 * i, coords[i]);
         for (uint32_t s = slo; s <= shi; s++) out[off_len + (s - slo)] = len[s];
         for (uint64_t j = 0; j < nch; j++) put64(out + off_chunk + 8 * j, chunk[j]);
         for (uint64_t w = 0; w < nwords; w++) put32(out + off_bits + 4 * w, words[w]);
@@ -171,8 +186,8 @@ typedef struct {
     int dtype, d, L, mode, tol_kind;
     size_t n[3];
     uint32_t D, K, slo, shi, ew;
-    uint64_t N, nout, bits, nch, nwords;
-    uint64_t off_q, off_len, off_chunk, off_bits, total;
+    uint64_t N, nout, bits, nch, nwords, nco;
+    uint64_t off_q, off_co, off_len, off_chunk, off_bits, total;
 } hdr_t;
 
 static int parse(const uint8_t *in, uint64_t in_bytes, hdr_t *h)
@@ -185,7 +200,9 @@ static int parse(const uint8_t *in, uint64_t in_bytes, hdr_t *h)
     for (int k = 0; k < 3; k++) h->n[k] = (size_t)get64(in + 16 + 8 * k);
     h->L = (int)get32(in + 40);
     h->mode = (int)get32(in + 44);
-    h->tol_kind = (int)get32(in + 48);
+    const uint32_t tk = get32(in + 48);
+    if (tk & ~0x101u) return -4;
+    h->tol_kind = (int)(tk & 1u);
     h->D = get32(in + 52);
     h->K = get32(in + 56);
     h->slo = get32(in + 60);
@@ -204,8 +221,11 @@ static int parse(const uint8_t *in, uint64_t in_bytes, hdr_t *h)
     if (h->nout > N || h->ew > 63 || (h->nout && h->ew == 0)) return -4;
     h->nch = (N + h->K - 1) / h->K;
     h->nwords = (h->bits + 31) / 32;
+    h->nco = 0;
+    if (tk & 0x100u) for (int k = 0; k < h->d; k++) h->nco += h->n[k];
     h->off_q = HDR;
-    h->off_len = align16(h->off_q + 8 * (uint64_t)(L + 1));
+    h->off_co = h->off_q + 8 * (uint64_t)(L + 1);
+    h->off_len = align16(h->off_co + 8 * h->nco);
     h->off_chunk = align16(h->off_len + (h->shi - h->slo + 1));
     h->off_bits = align16(h->off_chunk + 8 * h->nch);
     h->total = h->off_bits + 4 * h->nwords;
@@ -248,7 +268,13 @@ int oracle_decompress(const uint8_t *in, uint64_t in_bytes, double *u, uint64_t 
     for (uint64_t i = 0, j = 0; rc == 0 && i < h.N; i++)
         if (sym[i] == 0) oidx[j++] = i;
     if (rc == 0) rc = oracle_dequantize(h.d, h.n, sym, q, h.D, h.nout, oidx, ok, coef);
-    if (rc == 0) rc = oracle_recompose(h.d, h.n, coef, u);
+    double *co = NULL;
+    if (rc == 0 && h.nco) {
+        co = (double *)malloc(h.nco * sizeof(double));
+        for (uint64_t i = 0; i < h.nco; i++) co[i] = getf64(in + h.off_co + 8 * i);
+    }
+    if (rc == 0) rc = oracle_recompose_c(h.d, h.n, co, coef, u) ? -4 : 0;
+    free(co);
     free(q); free(len); free(chunk); free(oidx); free(ok); free(words); free(sym); free(coef);
     return rc;
 }

@@ -4,8 +4,11 @@
  * TEST INFRASTRUCTURE ONLY (see hpdr_oracle.h).
  *
  * Readings of the paper fixed here:
- *   - The data is a piecewise multilinear function on the finest grid with
- *     unit spacing (node i at coordinate i).  One level of coarsening keeps
+ *   - The data is a piecewise multilinear function on the finest grid, node
+ *     i of a dimension at coordinate i (unit spacing) or at the coordinate
+ *     the caller gives (any strictly increasing values: MGARD's non-uniform
+ *     grids).  Weights, mass matrices and the correction use the node
+ *     coordinates of every level.  One level of coarsening keeps
  *     every other node of each dimension plus the last node, so sizes 2^j+1
  *     give uniform levels and other sizes give a short last interval.  All
  *     dimensions coarsen together; L is the smallest per-dimension count of
@@ -36,7 +39,7 @@ static int dim_levels(size_t n)
     return c;
 }
 
-int ohier_build(ohier *H, int d, const size_t *n)
+int ohier_build(ohier *H, int d, const size_t *n, const double *coords)
 {
     if (d < 1 || d > OMAXD || !n) return -1;
     memset(H, 0, sizeof(*H));
@@ -50,18 +53,23 @@ int ohier_build(ohier *H, int d, const size_t *n)
     }
     if (L > OMAXL) return -1;
     H->L = L;
+    const double *ck = coords;
     for (int k = 0; k < d; k++) {
         H->m[k][L] = n[k];
-        H->idx[k][L] = (size_t *)malloc(n[k] * sizeof(size_t));
-        if (!H->idx[k][L]) return -1;
-        for (size_t i = 0; i < n[k]; i++) H->idx[k][L][i] = i;
+        H->x[k][L] = (double *)malloc(n[k] * sizeof(double));
+        if (!H->x[k][L]) return -1;
+        for (size_t i = 0; i < n[k]; i++) {
+            H->x[k][L][i] = ck ? ck[i] : (double)i;
+            if (!isfinite(H->x[k][L][i]) || (i > 0 && !(H->x[k][L][i] > H->x[k][L][i - 1]))) return -1;
+        }
+        if (ck) ck += n[k];
         for (int l = L; l >= 1; l--) {
             size_t m = H->m[k][l];
             size_t mc = coarsen_size(m);
             H->m[k][l - 1] = mc;
-            H->idx[k][l - 1] = (size_t *)malloc(mc * sizeof(size_t));
-            if (!H->idx[k][l - 1]) return -1;
-            for (size_t j = 0; j < mc; j++) H->idx[k][l - 1][j] = H->idx[k][l][ocpos(m, mc, j)];
+            H->x[k][l - 1] = (double *)malloc(mc * sizeof(double));
+            if (!H->x[k][l - 1]) return -1;
+            for (size_t j = 0; j < mc; j++) H->x[k][l - 1][j] = H->x[k][l][ocpos(m, mc, j)];
         }
     }
     return 0;
@@ -70,7 +78,7 @@ int ohier_build(ohier *H, int d, const size_t *n)
 void ohier_free(ohier *H)
 {
     for (int k = 0; k < OMAXD; k++)
-        for (int l = 0; l <= OMAXL; l++) { free(H->idx[k][l]); H->idx[k][l] = NULL; }
+        for (int l = 0; l <= OMAXL; l++) { free(H->x[k][l]); H->x[k][l] = NULL; }
 }
 
 size_t ohier_count(const ohier *H, int l)
@@ -92,7 +100,7 @@ static size_t ocidx(size_t m, size_t p) { return (p == m - 1) ? coarsen_size(m) 
 
 /* interpolation weights of a new position p from its coarse neighbours
  * p-1 (left) and p+1 (right): piecewise-linear in the coordinates x. */
-static void interp_weights(const size_t *x, size_t p, double *wl, double *wr)
+static void interp_weights(const double *x, size_t p, double *wl, double *wr)
 {
     double a = (double)x[p - 1], b = (double)x[p + 1], c = (double)x[p];
     *wl = (b - c) / (b - a);
@@ -104,7 +112,7 @@ static void interp_weights(const size_t *x, size_t p, double *wl, double *wr)
 
 /* y = M x, the P1 mass matrix on coordinates xc[0..m-1]:
  * diagonal (h_{i-1}+h_i)/3, off-diagonal h_i/6. */
-static void mass_mul(const size_t *xc, size_t m, const double *x, double *y)
+static void mass_mul(const double *xc, size_t m, const double *x, double *y)
 {
     for (size_t i = 0; i < m; i++) {
         double hl = (i > 0) ? (double)(xc[i] - xc[i - 1]) : 0.0;
@@ -117,7 +125,7 @@ static void mass_mul(const size_t *xc, size_t m, const double *x, double *y)
 }
 
 /* Solve M z = b in place (Thomas algorithm), M the mass matrix on xc. */
-static void mass_solve(const size_t *xc, size_t m, double *b)
+static void mass_solve(const double *xc, size_t m, double *b)
 {
     double *cp = (double *)malloc(m * sizeof(double));
     double diag0 = (double)(xc[1] - xc[0]) / 3.0;
@@ -139,7 +147,7 @@ static void mass_solve(const size_t *xc, size_t m, double *b)
 /* out = P^T y for a level with coordinates xf (m nodes) and its coarsening
  * (mc nodes): every coarse node collects its own value and, from each new
  * neighbour, the interpolation weight that neighbour gives it. */
-static void prolong_T(const size_t *xf, size_t m, size_t mc, const double *y, double *out)
+static void prolong_T(const double *xf, size_t m, size_t mc, const double *y, double *out)
 {
     for (size_t j = 0; j < mc; j++) {
         size_t c = ocpos(m, mc, j);
@@ -152,7 +160,7 @@ static void prolong_T(const size_t *xf, size_t m, size_t mc, const double *y, do
 }
 
 /* out = P z: coarse values copied, new positions interpolated */
-static void prolong(const size_t *xf, size_t m, size_t mc, const double *z, double *out)
+static void prolong(const double *xf, size_t m, size_t mc, const double *z, double *out)
 {
     for (size_t p = 0; p < m; p++) {
         if (ois_coarse(m, p)) { out[p] = z[ocidx(m, p)]; continue; }
@@ -181,8 +189,8 @@ static void along_dim(const ohier *H, int l, int op, const size_t *s, int k,
     double *lin = (double *)malloc(mmax * sizeof(double));
     double *tmp = (double *)malloc(mmax * sizeof(double));
     double *lout = (double *)malloc(mmax * sizeof(double));
-    const size_t *xf = H->idx[k][l];
-    const size_t *xc = H->idx[k][l - 1];
+    const double *xf = H->x[k][l];
+    const double *xc = H->x[k][l - 1];
     size_t mf = H->m[k][l], mcn = H->m[k][l - 1];
     for (size_t o = 0; o < outer; o++) {
         for (size_t i = 0; i < inner; i++) {
@@ -287,7 +295,7 @@ static int corners(const ohier *H, int l, const size_t *p, size_t *cf, size_t *c
         size_t m = H->m[k][l];
         if (ois_coarse(m, p[k])) continue;
         double wl, wr;
-        interp_weights(H->idx[k][l], p[k], &wl, &wr);
+        interp_weights(H->x[k][l], p[k], &wl, &wr);
         for (int i = 0; i < nc; i++) {
             for (int j = 0; j < H->d; j++) pf[nc + i][j] = pf[i][j];
             pf[i][k] = p[k] - 1;
@@ -313,7 +321,7 @@ static int corners(const ohier *H, int l, const size_t *p, size_t *cf, size_t *c
 int oracle_levels(int d, const size_t *n, int *L, size_t *m_out)
 {
     ohier H;
-    if (ohier_build(&H, d, n)) { ohier_free(&H); return -1; }
+    if (ohier_build(&H, d, n, NULL)) { ohier_free(&H); return -1; }
     *L = H.L;
     if (m_out)
         for (int k = 0; k < 3; k++)
@@ -324,8 +332,13 @@ int oracle_levels(int d, const size_t *n, int *L, size_t *m_out)
 
 int oracle_decompose(int d, const size_t *n, const double *u, double *coef)
 {
+    return oracle_decompose_c(d, n, NULL, u, coef);
+}
+
+int oracle_decompose_c(int d, const size_t *n, const double *coords, const double *u, double *coef)
+{
     ohier H;
-    if (ohier_build(&H, d, n)) { ohier_free(&H); return -1; }
+    if (ohier_build(&H, d, n, coords)) { ohier_free(&H); return -1; }
     size_t N = ohier_count(&H, H.L);
     double *v = (double *)malloc(N * sizeof(double));
     memcpy(v, u, N * sizeof(double));
@@ -366,8 +379,13 @@ int oracle_decompose(int d, const size_t *n, const double *u, double *coef)
  * values, then rebuild the new nodes as coefficient plus interpolant. */
 int oracle_recompose(int d, const size_t *n, const double *coef, double *u)
 {
+    return oracle_recompose_c(d, n, NULL, coef, u);
+}
+
+int oracle_recompose_c(int d, const size_t *n, const double *coords, const double *coef, double *u)
+{
     ohier H;
-    if (ohier_build(&H, d, n)) { ohier_free(&H); return -1; }
+    if (ohier_build(&H, d, n, coords)) { ohier_free(&H); return -1; }
     size_t N0 = ohier_count(&H, 0);
     double *v = (double *)malloc(N0 * sizeof(double));
     memcpy(v, coef, N0 * sizeof(double));
@@ -414,7 +432,7 @@ int oracle_recompose(int d, const size_t *n, const double *coef, double *u)
 int oracle_recompose_adjoint(int d, const size_t *n, const double *g_u, double *g_coef)
 {
     ohier H;
-    if (ohier_build(&H, d, n)) { ohier_free(&H); return -1; }
+    if (ohier_build(&H, d, n, NULL)) { ohier_free(&H); return -1; }
     size_t N = ohier_count(&H, H.L);
     double *g = (double *)malloc(N * sizeof(double));
     memcpy(g, g_u, N * sizeof(double));
@@ -460,7 +478,7 @@ int oracle_recompose_adjoint(int d, const size_t *n, const double *g_u, double *
 int oracle_decompose_adjoint(int d, const size_t *n, const double *g_coef, double *g_u)
 {
     ohier H;
-    if (ohier_build(&H, d, n)) { ohier_free(&H); return -1; }
+    if (ohier_build(&H, d, n, NULL)) { ohier_free(&H); return -1; }
     size_t N0 = ohier_count(&H, 0);
     double *gv = (double *)malloc(N0 * sizeof(double));
     memcpy(gv, g_coef, N0 * sizeof(double));
@@ -503,8 +521,13 @@ int oracle_decompose_adjoint(int d, const size_t *n, const double *g_coef, doubl
  * infinity-norm amplification of one level's correction. */
 int oracle_correction_norms(int d, const size_t *n, double *c)
 {
+    return oracle_correction_norms_c(d, n, NULL, c);
+}
+
+int oracle_correction_norms_c(int d, const size_t *n, const double *coords, double *c)
+{
     ohier H;
-    if (ohier_build(&H, d, n)) { ohier_free(&H); return -1; }
+    if (ohier_build(&H, d, n, coords)) { ohier_free(&H); return -1; }
     c[0] = 0.0;
     for (int l = 1; l <= H.L; l++) {
         double prod = 1.0;
@@ -517,9 +540,9 @@ int oracle_correction_norms(int d, const size_t *n, double *c)
             for (size_t p = 0; p < mf; p++) {
                 memset(e, 0, mf * sizeof(double));
                 e[p] = 1.0;
-                mass_mul(H.idx[k][l], mf, e, t);
-                prolong_T(H.idx[k][l], mf, mc, t, col);
-                mass_solve(H.idx[k][l - 1], mc, col);
+                mass_mul(H.x[k][l], mf, e, t);
+                prolong_T(H.x[k][l], mf, mc, t, col);
+                mass_solve(H.x[k][l - 1], mc, col);
                 for (size_t i = 0; i < mc; i++) rows[i] += fabs(col[i]);
             }
             double mx = 0.0;
@@ -540,6 +563,12 @@ int oracle_correction_norms(int d, const size_t *n, double *c)
  * (all codes are zero and the reconstruction is exact). */
 int oracle_bins(int d, const size_t *n, double tau_abs, double norm_inf, double eps, double *q)
 {
+    return oracle_bins_c(d, n, NULL, tau_abs, norm_inf, eps, q);
+}
+
+int oracle_bins_c(int d, const size_t *n, const double *coords, double tau_abs, double norm_inf, double eps,
+                  double *q)
+{
     int L;
     if (oracle_levels(d, n, &L, NULL)) return -1;
     if (norm_inf == 0.0) {
@@ -549,7 +578,7 @@ int oracle_bins(int d, const size_t *n, double tau_abs, double norm_inf, double 
     double tp = tau_abs - 32.0 * (double)(L + 1) * eps * norm_inf;
     if (!(tp > 0.0)) return -2;
     double *c = (double *)malloc((size_t)(L + 1) * sizeof(double));
-    if (oracle_correction_norms(d, n, c)) { free(c); return -1; }
+    if (oracle_correction_norms_c(d, n, coords, c)) { free(c); return -1; }
     q[0] = 2.0 * tp / (double)(L + 1);
     for (int l = 1; l <= L; l++) q[l] = 2.0 * tp / ((double)(L + 1) * (1.0 + c[l]));
     free(c);
@@ -592,7 +621,7 @@ int oracle_quantize(int d, const size_t *n, const double *coef, const double *q,
 {
     ohier H;
     if (D < 4 || D > 65536 || (D % 2)) return -1;
-    if (ohier_build(&H, d, n)) { ohier_free(&H); return -1; }
+    if (ohier_build(&H, d, n, NULL)) { ohier_free(&H); return -1; }
     size_t Nl[OMAXL + 1];
     for (int l = 0; l <= H.L; l++) Nl[l] = ohier_count(&H, l);
     uint64_t N = Nl[H.L], no = 0;
@@ -618,7 +647,7 @@ int oracle_dequantize(int d, const size_t *n, const uint16_t *symbols, const dou
                       uint64_t n_out, const uint64_t *out_idx, const int64_t *out_k, double *coef)
 {
     ohier H;
-    if (ohier_build(&H, d, n)) { ohier_free(&H); return -1; }
+    if (ohier_build(&H, d, n, NULL)) { ohier_free(&H); return -1; }
     size_t Nl[OMAXL + 1];
     for (int l = 0; l <= H.L; l++) Nl[l] = ohier_count(&H, l);
     uint64_t N = Nl[H.L], j = 0;

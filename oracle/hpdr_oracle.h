@@ -32,6 +32,14 @@ int oracle_levels(int d, const size_t *n, int *L, size_t *m_out /* [3*(L+1)], m_
 
 /* Multilevel decomposition / recomposition and their transposes (FP64). */
 int oracle_decompose(int d, const size_t *n, const double *u, double *coef);
+/* _c variants: coords = NULL (node i at coordinate i) or the node
+ * coordinates of every dimension, n[0] + ... + n[d-1] strictly increasing
+ * values, dimension 0 first (MGARD's non-uniform grids) */
+int oracle_decompose_c(int d, const size_t *n, const double *coords, const double *u, double *coef);
+int oracle_recompose_c(int d, const size_t *n, const double *coords, const double *coef, double *u);
+int oracle_correction_norms_c(int d, const size_t *n, const double *coords, double *c);
+int oracle_bins_c(int d, const size_t *n, const double *coords, double tau_abs, double norm_inf, double eps,
+                  double *q);
 int oracle_recompose(int d, const size_t *n, const double *coef, double *u);
 int oracle_recompose_adjoint(int d, const size_t *n, const double *g_u, double *g_coef);
 int oracle_decompose_adjoint(int d, const size_t *n, const double *g_coef, double *g_u);
@@ -84,6 +92,11 @@ int oracle_decode(const uint32_t *words, uint64_t nwords, const uint64_t *chunk_
 int oracle_compress(int d, const size_t *n, const double *u, int dtype, double tol, int tol_kind,
                     int mode, uint32_t D, uint32_t K, uint8_t *out, uint64_t cap,
                     uint64_t *out_bytes);
+/* oracle_compress with node coordinates (as oracle_decompose_c); the
+ * container records them, and oracle_decompress uses them */
+int oracle_compress_c(int d, const size_t *n, const double *coords, const double *u, int dtype, double tol,
+                      int tol_kind, int mode, uint32_t D, uint32_t K, uint8_t *out, uint64_t cap,
+                      uint64_t *out_bytes);
 int oracle_decompress(const uint8_t *in, uint64_t in_bytes, double *u, uint64_t cap_elems);
 int oracle_inspect(const uint8_t *in, uint64_t in_bytes, int *dtype, int *d, uint64_t *dims);
 uint64_t oracle_compress_bound(int d, const size_t *n, uint32_t D, uint32_t K);

@@ -13,10 +13,12 @@ typedef struct {
     size_t n[OMAXD];
     int L;
     size_t m[OMAXD][OMAXL + 1];      /* node count of dim k on level l */
-    size_t *idx[OMAXD][OMAXL + 1];   /* finest-grid index (= coordinate) of each node */
+    double *x[OMAXD][OMAXL + 1];     /* coordinate of each node (finest: i, or the given ones) */
 } ohier;
 
-int ohier_build(ohier *H, int d, const size_t *n);
+/* coords: NULL (node i at coordinate i) or n[0] + ... + n[d-1] strictly
+ * increasing finite coordinates, dimension 0 first */
+int ohier_build(ohier *H, int d, const size_t *n, const double *coords);
 void ohier_free(ohier *H);
 size_t ohier_count(const ohier *H, int l);
 size_t ocpos(size_t m, size_t mc, size_t j);
