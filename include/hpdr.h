@@ -26,10 +26,19 @@
  *     for l = 1..L the nodes that are new on level l, in row-major order of
  *     their level-l grid index.  Level l therefore starts at N_{l-1}, the node
  *     count of level l-1.  Element type = dtype.
- *   - Hierarchy: node i of a dimension sits at coordinate i; one coarsening
+ *   - Hierarchy: node i of a dimension sits at coordinate i (unit spacing)
+ *     unless the *_coords entry points give node coordinates; one coarsening
  *     keeps every other node plus the last one; all dimensions coarsen
  *     together, L = the smallest per-dimension number of coarsenings that
  *     reaches two nodes.
+ *   - Node coordinates (Sec. IV-A: MGARD reduces uniform and non-uniform
+ *     grids alike): `coords` is a HOST array of dims[0] + ... + dims[ndim-1]
+ *     doubles, the coordinates of dimension 0's nodes, then dimension 1's,
+ *     and so on, each run finite and strictly increasing (else HPDR_ERR_ARG).
+ *     Interpolation weights, mass matrices, the correction solves and the
+ *     correction norms behind the bins all follow them.  The library copies
+ *     them into its plan cache (keyed by their bytes); the caller keeps
+ *     ownership.  NULL means unit spacing, identical to the plain entries.
  *   - No exception crosses the ABI.  Errors are reported by the returned
  *     status; a failing call leaves the output buffer's contents undefined.
  *   - Calls on one context must not overlap in time (one host thread at a
@@ -82,7 +91,7 @@ hpdr_status hpdr_ctx_create(hpdr_ctx **ctx, int device);
 hpdr_status hpdr_ctx_destroy(hpdr_ctx *ctx);
 
 /* Upper bound of the container size for a field, with the given config (NULL
- * = defaults): header, bins, code lengths, chunk table and ceil(log2 D) + 32
+ * = defaults): header, bins, room for node coordinates, code lengths, chunk table and ceil(log2 D) + 32
  * bits per value (a Huffman code never exceeds the fixed-length code of
  * ceil(log2 D) bits in total; an escape payload takes at most 32 bits while
  * |k| < 2^31).  Only tolerances so small that many codes reach |k| >= 2^31
@@ -111,8 +120,19 @@ hpdr_status hpdr_compress(hpdr_ctx *ctx, const void *d_in, hpdr_dtype dtype, int
                           const hpdr_config *cfg, void *d_out, size_t out_capacity,
                           size_t *out_bytes, void *stream);
 
+/* hpdr_compress on a grid with the given node coordinates (host array, see
+ * Common conventions; NULL = unit spacing, the same container as
+ * hpdr_compress).  With coordinates the container's header word at byte 48
+ * carries 0x100 and the coordinates follow the bins as doubles, so
+ * hpdr_decompress needs nothing else to invert it. */
+hpdr_status hpdr_compress_coords(hpdr_ctx *ctx, const void *d_in, hpdr_dtype dtype, int ndim,
+                                 const size_t *dims, const double *coords, double tol, hpdr_tol_kind tol_kind,
+                                 hpdr_mode mode, const hpdr_config *cfg, void *d_out, size_t out_capacity,
+                                 size_t *out_bytes, void *stream);
+
 /* Decompress a device-resident container into d_out (out_capacity bytes; the
- * field's shape and type are read from the header, see hpdr_inspect).
+ * field's shape and type are read from the header, see hpdr_inspect; node
+ * coordinates too, when the container carries them).
  * Errors: HPDR_ERR_FORMAT, HPDR_ERR_CAPACITY, HPDR_ERR_ARG, HPDR_ERR_CUDA.
  * Synchronizes `stream` once (to read the header). */
 hpdr_status hpdr_decompress(hpdr_ctx *ctx, const void *d_in, size_t in_bytes, void *d_out,
@@ -131,6 +151,15 @@ hpdr_status hpdr_decompose(hpdr_ctx *ctx, const void *d_u, void *d_coef, hpdr_dt
 /* Multilevel recomposition, the exact inverse of hpdr_decompose. */
 hpdr_status hpdr_recompose(hpdr_ctx *ctx, const void *d_coef, void *d_u, hpdr_dtype dtype,
                            int ndim, const size_t *dims, void *stream);
+
+/* hpdr_decompose / hpdr_recompose on a grid with the given node coordinates
+ * (host array, see Common conventions; NULL = unit spacing).  Errors as for
+ * the plain entries, plus HPDR_ERR_ARG for coordinates that are not finite
+ * and strictly increasing along each dimension. */
+hpdr_status hpdr_decompose_coords(hpdr_ctx *ctx, const void *d_u, void *d_coef, hpdr_dtype dtype,
+                                  int ndim, const size_t *dims, const double *coords, void *stream);
+hpdr_status hpdr_recompose_coords(hpdr_ctx *ctx, const void *d_coef, void *d_u, hpdr_dtype dtype,
+                                  int ndim, const size_t *dims, const double *coords, void *stream);
 
 /* Transpose of hpdr_recompose: maps a field-shaped gradient d_grad_u to the
  * gradient with respect to the coefficient stream (no intermediate of the

@@ -215,6 +215,7 @@ hpdr_status compress_core(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, co
     ea.chunk_bits = w.chunk_bits; ea.sc = w.sc;
     ea.bsum = w.bsum;
     ea.container = out; ea.L = L; ea.capacity = cap;
+    ea.ncoord = P->coords.size();
     {
     ProfScope ps(ctx, "c_encode", s);
     CK(launch_encode(ea, s));
@@ -228,6 +229,7 @@ hpdr_status compress_core(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, co
     h.tol_kind = tol_kind;
     for (int k = 0; k < 3; k++) h.dims[k] = k < ndim ? dims[k] : 1;
     h.D = D; h.K = K; h.tol = tol; h.N = (unsigned long long)N; h.hist = w.hist;
+    h.coords = P->coords_dev; h.ncoord = P->coords.size();
     CK(launch_header(h, hs.len, w.sc, out, s));
     return HPDR_OK;
 }
@@ -278,6 +280,7 @@ struct Hdr {
     size_t dims[3];
     unsigned D, K, s_lo, s_hi, esc_w;
     unsigned long long N, n_esc, bits, nch, nwords;
+    unsigned long long ncoord;   // node coordinates after q (0: unit spacing)
     unsigned long long off_len, off_chunk, off_bits, total;
     double q[kMaxLevels + 1];
 };
@@ -306,7 +309,9 @@ hpdr_status parse_header(const uint8_t *b, size_t avail, size_t in_bytes, Hdr *h
     for (int k = 0; k < h->ndim; k++) if (h->dims[k] < 2 || h->dims[k] > (1u << 30)) return HPDR_ERR_FORMAT;
     h->L = (int)rd32(b + 40);
     h->mode = (int)rd32(b + 44);
-    h->tol_kind = (int)rd32(b + 48);
+    const uint32_t tk = rd32(b + 48);
+    if (tk & ~0x101u) return HPDR_ERR_FORMAT;
+    h->tol_kind = (int)(tk & 1u);
     h->D = rd32(b + 52);
     h->K = rd32(b + 56);
     h->s_lo = rd32(b + 60);
@@ -327,7 +332,9 @@ hpdr_status parse_header(const uint8_t *b, size_t avail, size_t in_bytes, Hdr *h
         return HPDR_ERR_FORMAT;
     h->nch = (h->N + h->K - 1) / h->K;
     h->nwords = (h->bits + 31) / 32;
-    h->off_len = a16(128 + 8ULL * (h->L + 1));
+    h->ncoord = 0;
+    if (tk & 0x100u) for (int k = 0; k < h->ndim; k++) h->ncoord += h->dims[k];
+    h->off_len = a16(128 + 8ULL * (h->L + 1) + 8ULL * h->ncoord);
     h->off_chunk = a16(h->off_len + (h->s_hi - h->s_lo + 1));
     h->off_bits = a16(h->off_chunk + 8 * h->nch);
     h->total = h->off_bits + 4 * h->nwords;
@@ -466,6 +473,17 @@ hpdr_status decompress_t(hpdr_ctx *ctx, const Plan *P, const Hdr &h, const uint8
     return HPDR_OK;
 }
 
+// node coordinates of a container (empty with unit spacing) from a host copy
+// that holds at least its first 128 + 8 (L + 1 + ncoord) bytes
+void read_coords(const uint8_t *b, const Hdr &h, std::vector<double> &co)
+{
+    co.resize(h.ncoord);
+    for (unsigned long long i = 0; i < h.ncoord; i++) {
+        uint64_t u = rd64(b + 128 + 8 * (h.L + 1) + 8 * i);
+        memcpy(&co[i], &u, 8);
+    }
+}
+
 // Decompression of a container whose header the caller already holds in
 // host memory (hdr_host, hdr_bytes): no header read-back, and with err_acc the
 // call does not wait (status OR-ed into *err_acc on the device).
@@ -476,11 +494,13 @@ hpdr_status decompress_with_header(hpdr_ctx *ctx, const uint8_t *hdr_host, size_
     Hdr h;
     hpdr_status st = parse_header(hdr_host, hdr_bytes, in_bytes, &h);
     if (st != HPDR_OK) return st;
-    if (hdr_bytes < 128 + 8ULL * (h.L + 1)) return HPDR_ERR_FORMAT;
+    if (hdr_bytes < 128 + 8ULL * (h.L + 1 + h.ncoord)) return HPDR_ERR_FORMAT;
     const size_t esz = h.dtype == 0 ? 4 : 8;
     if (out_capacity < h.N * esz) return HPDR_ERR_CAPACITY;
+    std::vector<double> co;
+    read_coords(hdr_host, h, co);
     Plan *P;
-    st = get_plan(ctx, h.ndim, h.dims, h.dtype == 1, &P);
+    st = get_plan(ctx, h.ndim, h.dims, h.dtype == 1, &P, co.empty() ? nullptr : co.data());
     if (st != HPDR_OK) return st;
     if (h.dtype == 0) return decompress_t<float>(ctx, P, h, (const uint8_t *)d_in, (float *)d_out, s, err_acc);
     return decompress_t<double>(ctx, P, h, (const uint8_t *)d_in, (double *)d_out, s, err_acc);
@@ -867,7 +887,10 @@ size_t hpdr_compress_bound(int ndim, const size_t *dims, hpdr_dtype dtype, const
     // while |k| < 2^31
     unsigned bpsym = 1;
     while ((1ULL << bpsym) < D) bpsym++;
-    unsigned long long b = a16(128 + 8ULL * (L + 1));
+    // room for node coordinates (sum of dims doubles) whether given or not
+    unsigned long long nco = 0;
+    for (int k = 0; k < ndim; k++) nco += dims[k];
+    unsigned long long b = a16(128 + 8ULL * (L + 1) + 8 * nco);
     b = a16(b + D);
     b = a16(b + 8 * ((N + K - 1) / K));
     b += 4 * (((bpsym + 32ULL) * N + 31) / 32);
@@ -879,6 +902,15 @@ hpdr_status hpdr_compress(hpdr_ctx *ctx, const void *d_in, hpdr_dtype dtype, int
                           const hpdr_config *cfg, void *d_out, size_t out_capacity,
                           size_t *out_bytes, void *stream)
 {
+    return hpdr_compress_coords(ctx, d_in, dtype, ndim, dims, nullptr, tol, tol_kind, mode, cfg, d_out,
+                                out_capacity, out_bytes, stream);
+}
+
+hpdr_status hpdr_compress_coords(hpdr_ctx *ctx, const void *d_in, hpdr_dtype dtype, int ndim,
+                                 const size_t *dims, const double *coords, double tol, hpdr_tol_kind tol_kind,
+                                 hpdr_mode mode, const hpdr_config *cfg, void *d_out, size_t out_capacity,
+                                 size_t *out_bytes, void *stream)
+{
     unsigned D, K;
     if (!ctx || !d_in || !d_out || !out_bytes || !valid_cfg(cfg, D, K)) return HPDR_ERR_ARG;
     if ((dtype != HPDR_F32 && dtype != HPDR_F64) || (mode != HPDR_LINF && mode != HPDR_L2) ||
@@ -887,7 +919,7 @@ hpdr_status hpdr_compress(hpdr_ctx *ctx, const void *d_in, hpdr_dtype dtype, int
     if (((uintptr_t)d_in & 15) || ((uintptr_t)d_out & 15)) return HPDR_ERR_ARG;
     DevGuard g(ctx->device);
     Plan *P;
-    hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P);
+    hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P, coords);
     if (st != HPDR_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if (dtype == HPDR_F32)
@@ -934,8 +966,17 @@ hpdr_status hpdr_decompress(hpdr_ctx *ctx, const void *d_in, size_t in_bytes, vo
     if (rd < 128 + 8ULL * (h.L + 1)) return HPDR_ERR_FORMAT;
     size_t esz = h.dtype == 0 ? 4 : 8;
     if (out_capacity < h.N * esz) return HPDR_ERR_CAPACITY;
+    std::vector<double> co;
+    if (h.ncoord) {
+        // the coordinate section follows q; its size is bounded by the
+        // container size that parse_header checked
+        const size_t cb = 128 + 8 * (h.L + 1 + h.ncoord);
+        std::vector<uint8_t> full(cb);
+        CK(cudaMemcpy(full.data(), d_in, cb, cudaMemcpyDeviceToHost));
+        read_coords(full.data(), h, co);
+    }
     Plan *P;
-    st = get_plan(ctx, h.ndim, h.dims, h.dtype == 1, &P);
+    st = get_plan(ctx, h.ndim, h.dims, h.dtype == 1, &P, co.empty() ? nullptr : co.data());
     if (st != HPDR_OK) return st;
     if (h.dtype == 0) return decompress_t<float>(ctx, P, h, (const uint8_t *)d_in, (float *)d_out, s);
     return decompress_t<double>(ctx, P, h, (const uint8_t *)d_in, (double *)d_out, s);
@@ -944,11 +985,17 @@ hpdr_status hpdr_decompress(hpdr_ctx *ctx, const void *d_in, size_t in_bytes, vo
 hpdr_status hpdr_decompose(hpdr_ctx *ctx, const void *d_u, void *d_coef, hpdr_dtype dtype,
                            int ndim, const size_t *dims, void *stream)
 {
+    return hpdr_decompose_coords(ctx, d_u, d_coef, dtype, ndim, dims, nullptr, stream);
+}
+
+hpdr_status hpdr_decompose_coords(hpdr_ctx *ctx, const void *d_u, void *d_coef, hpdr_dtype dtype,
+                                  int ndim, const size_t *dims, const double *coords, void *stream)
+{
     if (!ctx || !d_u || !d_coef || (dtype != HPDR_F32 && dtype != HPDR_F64)) return HPDR_ERR_ARG;
     if ((uintptr_t)d_u & 15) return HPDR_ERR_ARG;
     DevGuard g(ctx->device);
     Plan *P;
-    hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P);
+    hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P, coords);
     if (st != HPDR_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if (dtype == HPDR_F32) return decompose_t<float>(ctx, P, (const float *)d_u, (float *)d_coef, s);
@@ -958,10 +1005,16 @@ hpdr_status hpdr_decompose(hpdr_ctx *ctx, const void *d_u, void *d_coef, hpdr_dt
 hpdr_status hpdr_recompose(hpdr_ctx *ctx, const void *d_coef, void *d_u, hpdr_dtype dtype,
                            int ndim, const size_t *dims, void *stream)
 {
+    return hpdr_recompose_coords(ctx, d_coef, d_u, dtype, ndim, dims, nullptr, stream);
+}
+
+hpdr_status hpdr_recompose_coords(hpdr_ctx *ctx, const void *d_coef, void *d_u, hpdr_dtype dtype,
+                                  int ndim, const size_t *dims, const double *coords, void *stream)
+{
     if (!ctx || !d_u || !d_coef || (dtype != HPDR_F32 && dtype != HPDR_F64)) return HPDR_ERR_ARG;
     DevGuard g(ctx->device);
     Plan *P;
-    hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P);
+    hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P, coords);
     if (st != HPDR_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if (dtype == HPDR_F32) return recompose_t<float>(ctx, P, (const float *)d_coef, (float *)d_u, s);

@@ -727,11 +727,12 @@ __global__ void __launch_bounds__(1024, 1) dec_tables_kernel(const uint8_t *lenb
 struct Layout {
     unsigned long long off_len, off_chunk, off_bits, total;
 };
-__device__ __forceinline__ Layout container_layout(int L, unsigned s_lo, unsigned s_hi,
+__device__ __forceinline__ Layout container_layout(int L, unsigned long long ncoord, unsigned s_lo, unsigned s_hi,
                                                    unsigned long long nch, unsigned long long bits)
 {
     Layout y;
-    y.off_len = a16(128 + 8ULL * (L + 1));
+    // the node coordinates (ncoord values, when the container carries them) follow q[L+1]
+    y.off_len = a16(128 + 8ULL * (L + 1) + 8ULL * ncoord);
     y.off_chunk = a16(y.off_len + (s_hi - s_lo + 1));
     y.off_bits = a16(y.off_chunk + 8 * nch);
     y.total = y.off_bits + 4 * ((bits + 31) / 32);
@@ -816,7 +817,7 @@ __global__ void __launch_bounds__(1024) enc_scan1_kernel(EncodeArgs a, int nb)
         const unsigned long long nch = (a.N + a.K - 1) / a.K;
         const unsigned long long x = sb[1023];
         if (a.container) {
-            Layout lay = container_layout(a.L, a.sc->s_lo, a.sc->s_hi, nch, x);
+            Layout lay = container_layout(a.L, a.ncoord, a.sc->s_lo, a.sc->s_hi, nch, x);
             if (lay.total > a.capacity) atomicExch(&a.sc->status, (unsigned)DS_CAPACITY);
             a.sc->out_bytes = lay.total;
         } else {
@@ -829,7 +830,7 @@ __global__ void __launch_bounds__(1024) enc_scan1_kernel(EncodeArgs a, int nb)
 __device__ __forceinline__ uint32_t *enc_words(const EncodeArgs &a, unsigned long long nch)
 {
     if (!a.container) return a.words_out;
-    Layout lay = container_layout(a.L, a.sc->s_lo, a.sc->s_hi, nch, a.sc->total_bits);
+    Layout lay = container_layout(a.L, a.ncoord, a.sc->s_lo, a.sc->s_hi, nch, a.sc->total_bits);
     return reinterpret_cast<uint32_t *>(a.container + lay.off_bits);
 }
 
@@ -845,7 +846,7 @@ __global__ void __launch_bounds__(256) enc_scan2_kernel(EncodeArgs a)
     uint32_t *words = enc_words(a, nch);
     unsigned long long *ctab = a.chunk_out;
     if (a.container) {
-        Layout lay = container_layout(a.L, a.sc->s_lo, a.sc->s_hi, nch, a.sc->total_bits);
+        Layout lay = container_layout(a.L, a.ncoord, a.sc->s_lo, a.sc->s_hi, nch, a.sc->total_bits);
         ctab = reinterpret_cast<unsigned long long *>(a.container + lay.off_chunk);
     }
     const unsigned long long total = a.sc->total_bits;
@@ -1070,7 +1071,7 @@ header_kernel(HeaderArgs h, const uint8_t *len, Scalars *sc, uint8_t *out)
     __shared__ uint32_t crct[256];
     if (block_skip(&sc->status)) return;
     const unsigned long long nch = (h.N + h.K - 1) / h.K;
-    Layout lay = container_layout(h.L, sc->s_lo, sc->s_hi, nch, sc->total_bits);
+    Layout lay = container_layout(h.L, h.ncoord, sc->s_lo, sc->s_hi, nch, sc->total_bits);
     const unsigned long long n_esc = h.hist ? h.hist[0] : 0ULL;
     // CRC-32 (reflected, polynomial 0xEDB88320) by a byte table, one entry per thread
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
@@ -1088,7 +1089,7 @@ header_kernel(HeaderArgs h, const uint8_t *len, Scalars *sc, uint8_t *out)
         for (int k = 0; k < 3; k++) put64(hdr + 16 + 8 * k, h.dims[k]);
         put32(hdr + 40, (uint32_t)h.L);
         put32(hdr + 44, (uint32_t)h.mode);
-        put32(hdr + 48, (uint32_t)h.tol_kind);
+        put32(hdr + 48, (uint32_t)h.tol_kind | (h.ncoord ? 0x100u : 0u));
         put32(hdr + 52, h.D);
         put32(hdr + 56, h.K);
         put32(hdr + 60, sc->s_lo);
@@ -1109,7 +1110,8 @@ header_kernel(HeaderArgs h, const uint8_t *len, Scalars *sc, uint8_t *out)
     for (int i = threadIdx.x; i < 128; i += blockDim.x) out[i] = hdr[i];
     const unsigned long long qend = 128 + 8ULL * (h.L + 1);
     for (int l = threadIdx.x; l <= h.L; l += blockDim.x) putd(out + 128 + 8 * l, sc->q[l]);
-    for (unsigned long long i = qend + threadIdx.x; i < lay.off_len; i += blockDim.x) out[i] = 0;
+    for (unsigned long long i = threadIdx.x; i < h.ncoord; i += blockDim.x) putd(out + qend + 8 * i, h.coords[i]);
+    for (unsigned long long i = qend + 8 * h.ncoord + threadIdx.x; i < lay.off_len; i += blockDim.x) out[i] = 0;
     const unsigned nlen = sc->s_hi - sc->s_lo + 1;
     for (unsigned i = threadIdx.x; i < nlen; i += blockDim.x) out[lay.off_len + i] = len[sc->s_lo + i];
     for (unsigned long long i = lay.off_len + nlen + threadIdx.x; i < lay.off_chunk; i += blockDim.x) out[i] = 0;

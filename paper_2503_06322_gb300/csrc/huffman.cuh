@@ -72,6 +72,7 @@ struct EncodeArgs {
     // destination
     uint8_t *container;               // if non-null: chunk table and bits go into the container
     int L;                            // levels (container layout)
+    unsigned long long ncoord;        // node coordinates the container carries (0: none)
     unsigned long long capacity;      // bytes available at container / words
     unsigned long long *chunk_out;    // (container == null) chunk table destination
     uint32_t *words_out;              // (container == null) bitstream destination
@@ -86,6 +87,8 @@ struct HeaderArgs {
     double tol;
     unsigned long long N;
     const unsigned long long *hist;   // histogram: hist[0] = escapes recorded in the header
+    const double *coords;             // node coordinates (device), ncoord values, or null
+    unsigned long long ncoord;
 };
 cudaError_t launch_header(const HeaderArgs &h, const uint8_t *len, Scalars *sc, uint8_t *container,
                           cudaStream_t s);

@@ -156,6 +156,12 @@ struct Plan {
     LevelGeom<float> gf[kMaxLevels + 1];
     LevelGeom<double> gd[kMaxLevels + 1];
     bool is_f64;
+    // node coordinates given by the caller (dims[0] + ... + dims[ndim-1]
+    // values, dimension 0 first), empty for unit spacing; coords_dev is
+    // their device copy inside the tables
+    std::vector<double> coords;
+    const double *coords_dev = nullptr;
+    size_t coords_off = 0;
 };
 
 struct Workspace {
@@ -226,10 +232,14 @@ struct PlanImage {
     std::vector<TableOff> offF, offD;   // offsets of every (level, dim) table, binary32 / binary64
 };
 // hierarchy and host image of the tables of one (shape, type)
-hpdr_status plan_image(int ndim, const size_t *dims, bool f64, Plan *P, PlanImage *img);
+// coords: null (node i at coordinate i) or the node coordinates of every
+// dimension, strictly increasing and finite, dimension 0 first
+hpdr_status plan_image(int ndim, const size_t *dims, bool f64, Plan *P, PlanImage *img,
+                       const double *coords = nullptr);
 // point the plan's tables at a device copy of img.bytes
 void bind_plan(Plan *P, const PlanImage &img, void *tables);
-hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan **out);
+hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan **out,
+                     const double *coords = nullptr);
 hpdr_status ensure_workspace(hpdr_ctx *ctx, size_t bytes);
 int levels_of(int ndim, const size_t *dims);
 

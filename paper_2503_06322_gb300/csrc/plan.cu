@@ -155,7 +155,7 @@ double corr_norm_dim(const HostTab &t)
 
 }  // namespace
 
-hpdr_status plan_image(int ndim, const size_t *dims, bool f64, Plan *P, PlanImage *img)
+hpdr_status plan_image(int ndim, const size_t *dims, bool f64, Plan *P, PlanImage *img, const double *coords)
 {
     if (ndim < 1 || ndim > 3 || !dims) return HPDR_ERR_ARG;
     for (int k = 0; k < ndim; k++)
@@ -168,13 +168,22 @@ hpdr_status plan_image(int ndim, const size_t *dims, bool f64, Plan *P, PlanImag
     int pad = 3 - ndim;
     bool active[3];
     std::vector<std::vector<double>> xs[3];  // xs[k][l] coordinates
+    P->coords.clear();
+    const double *ck = coords;
     for (int k = 0; k < 3; k++) {
         active[k] = k >= pad;
         long long n = active[k] ? (long long)dims[k - pad] : 1;
         P->n[k] = n;
         xs[k].resize(L + 1);
         xs[k][L].resize(n);
-        for (long long i = 0; i < n; i++) xs[k][L][i] = (double)i;
+        for (long long i = 0; i < n; i++) {
+            xs[k][L][i] = (active[k] && ck) ? ck[i] : (double)i;
+            if (!std::isfinite(xs[k][L][i]) || (i > 0 && !(xs[k][L][i] > xs[k][L][i - 1]))) return HPDR_ERR_ARG;
+        }
+        if (active[k] && ck) {
+            P->coords.insert(P->coords.end(), ck, ck + n);
+            ck += n;
+        }
         for (int l = L; l >= 1; l--) {
             const auto &xf = xs[k][l];
             int m = (int)xf.size();
@@ -216,6 +225,7 @@ hpdr_status plan_image(int ndim, const size_t *dims, bool f64, Plan *P, PlanImag
         }
         P->corr_norm[l] = prod;
     }
+    if (!P->coords.empty()) P->coords_off = append(P->coords.data(), P->coords.size() * sizeof(double));
     if (all.empty()) all.resize(256);
     return HPDR_OK;
 }
@@ -224,6 +234,7 @@ void bind_plan(Plan *P, const PlanImage &img, void *tables)
 {
     P->tables = tables;
     char *base = (char *)tables;
+    P->coords_dev = P->coords.empty() ? nullptr : (const double *)(base + P->coords_off);
     const int L = P->L;
     for (int l = 0; l <= L; l++) {
         P->gf[l].level = P->gd[l].level = l;
@@ -255,18 +266,35 @@ void bind_plan(Plan *P, const PlanImage &img, void *tables)
     }
 }
 
-hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan **out)
+hpdr_status get_plan(hpdr_ctx *ctx, int ndim, const size_t *dims, bool f64, Plan **out, const double *coords)
 {
     if (ndim < 1 || ndim > 3 || !dims) return HPDR_ERR_ARG;
     for (int k = 0; k < ndim; k++)
         if (dims[k] < 2 || dims[k] > (size_t)(1u << 30)) return HPDR_ERR_ARG;
     std::string key = std::to_string(ndim) + (f64 ? "d" : "f");
     for (int k = 0; k < ndim; k++) key += ":" + std::to_string(dims[k]);
+    size_t nco = 0;
+    if (coords) {
+        // plans of given coordinates are keyed by the coordinates' bytes
+        for (int k = 0; k < ndim; k++) nco += dims[k];
+        uint64_t hsh = 1469598103934665603ull;
+        const unsigned char *cb = (const unsigned char *)coords;
+        for (size_t i = 0; i < nco * sizeof(double); i++) hsh = (hsh ^ cb[i]) * 1099511628211ull;
+        key += ":c" + std::to_string(hsh);
+    }
     auto it = ctx->plans.find(key);
-    if (it != ctx->plans.end()) { *out = it->second; return HPDR_OK; }
+    if (it != ctx->plans.end()) {
+        const Plan *Q = it->second;
+        if (!coords || (Q->coords.size() == nco && memcmp(Q->coords.data(), coords, nco * sizeof(double)) == 0)) {
+            *out = it->second;
+            return HPDR_OK;
+        }
+        // a hash collision: build this plan under a longer key
+        key += ":" + std::to_string(ctx->plans.size());
+    }
     Plan *P = new Plan();
     PlanImage img;
-    hpdr_status st = plan_image(ndim, dims, f64, P, &img);
+    hpdr_status st = plan_image(ndim, dims, f64, P, &img, coords);
     if (st != HPDR_OK) { delete P; return st; }
     int dev_prev = -1;
     cudaGetDevice(&dev_prev);

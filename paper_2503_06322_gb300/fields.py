@@ -65,7 +65,7 @@ def powerlaw_field(shape, seed=1, exponent=-11.0 / 3.0, dtype=np.float32):
     nz = k2 > 0
     amp[nz] = k2[nz] ** (exponent / 4.0)          # sqrt(P(k)) = |k|^(exponent/2)
     noise = rng.standard_normal(k2.shape) + 1j * rng.standard_normal(k2.shape)
-    f = np.fft.irfftn(noise * amp, s=shape)
+    f = np.fft.irfftn(noise * amp, s=shape, axes=tuple(range(len(shape))))
     f -= f.mean()
     f /= f.std()
     return f.astype(dtype)
@@ -130,3 +130,19 @@ def front_field_torch(shape, seed=7, device="cuda"):
     x = torch.arange(shape[0], device=device, dtype=torch.float32) - (shape[0] - 1) / 2.0
     f += torch.tanh(x / 5.0).reshape([shape[0]] + [1] * (len(shape) - 1))
     return f
+
+
+def node_coords(shape, seed, kind="random"):
+    """Strictly increasing node coordinates for every dimension of a
+    non-uniform grid: "random" spacings drawn uniformly from [0.3, 2.5]
+    (ratio up to about 8 between neighbouring cells), or "stretched" nodes
+    clustered towards both ends as in a boundary-layer mesh
+    (x = sinh(4 (t - 1/2)) on t uniform in [0, 1])."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for n in shape:
+        if kind == "stretched":
+            out.append(np.sinh(4.0 * (np.linspace(0.0, 1.0, n) - 0.5)))
+        else:
+            out.append(np.cumsum(rng.uniform(0.3, 2.5, size=n)))
+    return out

@@ -15,6 +15,7 @@ Function names follow the C ABI:
 import ctypes as C
 import math
 import os
+import numpy as np
 
 import torch
 
@@ -74,6 +75,10 @@ def lib():
             "hpdr_inspect": [vp, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_int), sz],
             "hpdr_decompose": [vp, vp, vp, C.c_int, C.c_int, sz, vp],
             "hpdr_recompose": [vp, vp, vp, C.c_int, C.c_int, sz, vp],
+            "hpdr_compress_coords": [vp, vp, C.c_int, C.c_int, sz, C.POINTER(C.c_double), C.c_double, C.c_int,
+                                     C.c_int, C.POINTER(Config), vp, C.c_size_t, sz, vp],
+            "hpdr_decompose_coords": [vp, vp, vp, C.c_int, C.c_int, sz, C.POINTER(C.c_double), vp],
+            "hpdr_recompose_coords": [vp, vp, vp, C.c_int, C.c_int, sz, C.POINTER(C.c_double), vp],
             "hpdr_recompose_adjoint": [vp, vp, vp, C.c_int, C.c_int, sz, vp],
             "hpdr_decompose_adjoint": [vp, vp, vp, C.c_int, C.c_int, sz, vp],
             "hpdr_huffman_encode": [vp, vp, C.c_uint64, C.c_uint32, C.c_uint32, vp, vp, vp,
@@ -167,9 +172,29 @@ def hpdr_compress_bound(shape, dtype=torch.float32, dict_size=8192, chunk=0):
     return int(lib().hpdr_compress_bound(nd, dims, _dtype_code(dtype), C.byref(cfg)))
 
 
+def _coords(coords, shape):
+    """Node coordinates as one host double array (dimension 0's, then 1's,
+    ...), or None for unit spacing.  `coords` is one 1-D sequence per
+    dimension, of that dimension's length."""
+    if coords is None:
+        return None
+    if len(coords) != len(shape):
+        raise ValueError("coords needs one array per dimension")
+    parts = []
+    for k, c in enumerate(coords):
+        c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(-1))
+        if c.size != shape[k]:
+            raise ValueError("coords[%d] has %d entries for a dimension of %d" % (k, c.size, shape[k]))
+        parts.append(c)
+    flat = np.ascontiguousarray(np.concatenate(parts))
+    return flat, flat.ctypes.data_as(C.POINTER(C.c_double))
+
+
 def hpdr_compress(u, tol, tol_kind=REL, mode=LINF, dict_size=8192, chunk=0, out=None,
-                  stream=None):
-    """Compress a CUDA field; returns a uint8 CUDA tensor holding the container."""
+                  stream=None, coords=None):
+    """Compress a CUDA field; returns a uint8 CUDA tensor holding the
+    container.  coords: optional node coordinates, one array per dimension
+    (non-uniform grid); the container then carries them."""
     _dev_tensor(u, "u")
     nd, dims = _dims(u.shape)
     cfg = _cfg(dict_size, chunk)
@@ -177,10 +202,11 @@ def hpdr_compress(u, tol, tol_kind=REL, mode=LINF, dict_size=8192, chunk=0, out=
     if out is None:
         out = torch.empty(cap, dtype=torch.uint8, device=u.device)
     nb = C.c_size_t()
-    _check(lib().hpdr_compress(context(u.device.index), C.c_void_p(u.data_ptr()), _dtype_code(u.dtype),
-                               nd, dims, float(tol), int(tol_kind), int(mode), C.byref(cfg),
-                               C.c_void_p(out.data_ptr()), out.numel(), C.byref(nb),
-                               _stream(stream)), "hpdr_compress")
+    co = _coords(coords, tuple(u.shape))
+    _check(lib().hpdr_compress_coords(context(u.device.index), C.c_void_p(u.data_ptr()), _dtype_code(u.dtype),
+                                      nd, dims, co[1] if co else None, float(tol), int(tol_kind), int(mode),
+                                      C.byref(cfg), C.c_void_p(out.data_ptr()), out.numel(), C.byref(nb),
+                                      _stream(stream)), "hpdr_compress")
     return out[:nb.value]
 
 
@@ -212,11 +238,23 @@ def _field_call(name, src, out, shape, stream):
     return out
 
 
-def hpdr_decompose(u, out=None, stream=None):
-    """Level-major coefficient stream (1-D tensor) of the field u."""
+def _coords_call(name, src, out, shape, coords, stream):
+    nd, dims = _dims(shape)
+    co = _coords(coords, tuple(shape))
+    _check(getattr(lib(), name)(context(src.device.index), C.c_void_p(src.data_ptr()),
+                                C.c_void_p(out.data_ptr()), _dtype_code(src.dtype), nd, dims,
+                                co[1] if co else None, _stream(stream)), name)
+    return out
+
+
+def hpdr_decompose(u, out=None, stream=None, coords=None):
+    """Level-major coefficient stream (1-D tensor) of the field u (coords:
+    optional node coordinates, one array per dimension)."""
     _dev_tensor(u, "u")
     if out is None:
         out = torch.empty(u.numel(), dtype=u.dtype, device=u.device)
+    if coords is not None:
+        return _coords_call("hpdr_decompose_coords", u, out, u.shape, coords, stream)
     return _field_call("hpdr_decompose", u, out, u.shape, stream)
 
 
@@ -432,10 +470,12 @@ def hpdr_compress_batched(fields, tols, tol_kind=REL, mode=LINF, dict_size=8192,
     return out, list(offs), list(sizes)
 
 
-def hpdr_recompose(coef, shape, out=None, stream=None):
+def hpdr_recompose(coef, shape, out=None, stream=None, coords=None):
     _dev_tensor(coef, "coef")
     if out is None:
         out = torch.empty(tuple(shape), dtype=coef.dtype, device=coef.device)
+    if coords is not None:
+        return _coords_call("hpdr_recompose_coords", coef, out, shape, coords, stream)
     return _field_call("hpdr_recompose", coef, out, shape, stream)
 
 
