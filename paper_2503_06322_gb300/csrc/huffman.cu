@@ -741,6 +741,11 @@ __device__ __forceinline__ Layout container_layout(int L, unsigned long long nco
 
 constexpr int kEncBlocks = 152 * 4;
 
+// The encoder's unit of work: a warp takes r consecutive chunks (r K symbols,
+// 32 per lane) when K < 1024 divides 1024, else one chunk.  The bitstream is
+// continuous across chunks, so the grouping changes no output bit.
+__host__ __device__ inline unsigned enc_group(unsigned K) { return (K < 1024 && 1024 % K == 0) ? 1024 / K : 1; }
+
 // bits of every chunk (codewords + escape payloads); block b owns the
 // contiguous chunk range [b*cpb, (b+1)*cpb) and leaves its sum in bsum
 __global__ void __launch_bounds__(256) enc_count_kernel(EncodeArgs a)
@@ -758,6 +763,37 @@ __global__ void __launch_bounds__(256) enc_count_kernel(EncodeArgs a)
     const unsigned long long c0 = blockIdx.x * cpb, c1 = c0 + cpb < nch ? c0 + cpb : nch;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long tb = 0;
+    const unsigned r = enc_group(a.K);
+    if (r > 1) {
+        // r chunks per warp, 32 / r lanes per chunk, 32 symbols per lane
+        const unsigned lpc = 32 / r;
+        for (unsigned long long g = c0 + (unsigned long long)warp * r; g < c1; g += (blockDim.x >> 5) * r) {
+            const unsigned long long c = g + lane / lpc;
+            unsigned long long bits = 0;
+            if (c < c1) {
+                const unsigned long long beg = c * a.K + (unsigned long long)(lane % lpc) * 32;
+                const unsigned long long cend = (c + 1) * a.K < a.N ? (c + 1) * a.K : a.N;
+                if (beg + 32 <= cend) {
+                    const uint4 *v = reinterpret_cast<const uint4 *>(a.sym + beg);
+                    uint4 x[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) x[u] = v[u];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const uint16_t *e = reinterpret_cast<const uint16_t *>(&x[u]);
+#pragma unroll
+                        for (int k = 0; k < 8; k++) bits += slen[e[k]];
+                    }
+                } else {
+                    for (unsigned long long i = beg; i < cend; i++) bits += slen[a.sym[i]];
+                }
+            }
+            // sum over the lpc lanes of each chunk
+            for (unsigned o = 1; o < lpc; o <<= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
+            if (lane % lpc == 0 && c < c1) { a.chunk_bits[c] = bits; tb += bits; }
+        }
+        tb = warp_sum64(tb);
+    } else
     for (unsigned long long c = c0 + warp; c < c1; c += blockDim.x >> 5) {
         const unsigned long long beg = c * a.K;
         const unsigned long long end = beg + a.K < a.N ? beg + a.K : a.N;
@@ -868,11 +904,15 @@ __global__ void __launch_bounds__(256) enc_scan2_kernel(EncodeArgs a)
             a.chunk_bits[c] = off;
             ctab[c] = off;
             const unsigned long long cend = off + v;
-            // full chunks of K >= 1024 symbols share only their first word with the previous
-            // chunk; other chunks are written word by word with atomics: zero them
-            const bool full = (c + 1) * (unsigned long long)a.K <= a.N && a.K >= 1024;
+            // a complete group of at least 1024 symbols (one warp, 32 or more per lane)
+            // shares only its first word with the previous group and stores every
+            // other word whole; other chunks are written word by word with atomics:
+            // zero them
+            const unsigned r = enc_group(a.K);
+            const unsigned long long G = (unsigned long long)a.K * r;
+            const bool full = (c / r + 1) * G <= a.N && G >= 1024;
             if (full) {
-                words[off >> 5] = 0u;
+                if (c % r == 0) words[off >> 5] = 0u;
             } else {
                 for (unsigned long long w = off >> 5; w <= ((cend ? cend - 1 : 0) >> 5); w++) words[w] = 0u;
             }
@@ -885,9 +925,10 @@ __global__ void __launch_bounds__(256) enc_scan2_kernel(EncodeArgs a)
     if (blockIdx.x == 0 && t == 0) a.chunk_bits[nch] = total;
 }
 
-// one warp per chunk: every lane encodes K/32 consecutive symbols, assembling
-// its bits in a 64-bit register and storing whole words; the partial words
-// at lane boundaries are merged through shuffles (full chunks) or atomics
+// one warp per group of chunks (enc_group): every lane encodes 32 (K/32 when
+// K >= 1024) consecutive symbols, assembling its bits in a 64-bit register and
+// storing whole words; the partial words at lane boundaries are merged through
+// shuffles (complete groups) or atomics (the last, partial group)
 __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
 {
     extern __shared__ uint32_t esm32[];
@@ -916,12 +957,15 @@ __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
     const long long *__restrict__ esc = a.esc;
     const int ew = esc ? (int)a.sc->esc_w : 0;       // escape payload width
     const unsigned lane = threadIdx.x & 31;
-    const unsigned spl = a.K >> 5;
+    const unsigned r = enc_group(a.K);
+    const unsigned long long G = (unsigned long long)a.K * r;   // symbols per warp group
+    const unsigned long long ngr = (a.N + G - 1) / G;
+    const unsigned spl = (unsigned)(G >> 5);
     const unsigned long long wg = blockIdx.x * (unsigned long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
     const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
-    for (unsigned long long c = wg; c < nch; c += nw) {
-        const unsigned long long beg = c * a.K;
-        const unsigned long long end = beg + a.K < a.N ? beg + a.K : a.N;
+    for (unsigned long long c = wg; c < ngr; c += nw) {
+        const unsigned long long beg = c * G;
+        const unsigned long long end = beg + G < a.N ? beg + G : a.N;
         unsigned long long m0 = beg + (unsigned long long)lane * spl, m1 = m0 + spl;
         if (m0 > end) m0 = end;
         if (m1 > end) m1 = end;
@@ -958,7 +1002,7 @@ __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
             const unsigned long long yb = __shfl_up_sync(0xffffffffu, xb, o);
             if ((int)lane >= o) xb += yb;
         }
-        const unsigned long long start = a.chunk_bits[c] + xb - mb;
+        const unsigned long long start = a.chunk_bits[c * r] + xb - mb;
         unsigned long long acc = 0;
         unsigned nacc = (unsigned)(start & 31);
         unsigned long long widx = start >> 5;
@@ -1037,9 +1081,9 @@ __global__ void __launch_bounds__(256) enc_write_kernel(EncodeArgs a)
         }
         const uint32_t lastw = (uint32_t)(acc >> 32);
         const bool has_last = nacc > 0;
-        // a full chunk whose every lane holds >= 32 bits (always true with 32
+        // a full group whose every lane holds >= 32 bits (always true with 32
         // symbols per lane): lane i's last partial word is lane i+1's first word
-        const bool full = __all_sync(0xffffffffu, (end - beg == a.K) && mb >= 32);
+        const bool full = __all_sync(0xffffffffu, (end - beg == G) && mb >= 32);
         if (full) {
             const uint32_t prev = __shfl_up_sync(0xffffffffu, lastw, 1);
             const bool sh = (start & 31) != 0;

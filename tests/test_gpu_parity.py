@@ -102,7 +102,12 @@ def test_codes_bit_exact_on_identical_inputs(oracle, H, dev, shape, tol, D, dtyp
 @pytest.mark.parametrize("n,D,K,spread", [(20000, 8192, 1024, 300.0), (1, 16, 128, 1.0),
                                           (777, 256, 128, 0.0), (300000, 65536, 1024, 2000.0),
                                           (65536, 8192, 4096, 3.0), (5000, 64, 256, 40.0),
-                                          (100000, 8192, 512, 500.0), (300000, 8192, 1024, 3000.0)])
+                                          (100000, 8192, 512, 500.0), (300000, 8192, 1024, 3000.0),
+                                          # several warp groups of chunks (K < 1024 dividing 1024), ragged tails,
+                                          # a K that does not divide 1024, and a one-symbol stream
+                                          (100003, 8192, 128, 40.0), (262147, 8192, 256, 0.3),
+                                          (50001, 4096, 384, 100.0), (70001, 256, 512, 0.0),
+                                          (1048576, 8192, 256, 2.0), (33000, 8192, 512, 8000.0)])
 def test_huffman_bit_exact(oracle, H, dev, n, D, K, spread):
     rng = np.random.default_rng(n)
     sym = np.clip(np.round(rng.laplace(D // 2, spread + 1e-9, size=n)), 1, D - 1).astype(np.uint16)
@@ -137,7 +142,7 @@ def test_huffman_equal_frequencies(oracle, H, dev, D, reps):
     assert np.array_equal(dec.cpu().numpy().view(np.uint16), sym)
 
 
-@pytest.mark.parametrize("nsym,K", [(20, 1024), (35, 2048)])
+@pytest.mark.parametrize("nsym,K", [(20, 1024), (35, 2048), (35, 256), (28, 128)])
 def test_huffman_long_codewords(oracle, H, dev, nsym, K):
     """Fibonacci frequencies give codewords up to nsym - 1 bits: past the
     decoder's 15-bit table and, for 35 symbols, past 32 bits."""
