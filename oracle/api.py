@@ -11,14 +11,14 @@ from . import build as _build
 
 __all__ = [
     "levels", "decompose", "recompose", "recompose_adjoint", "decompose_adjoint",
-    "correction_norms", "bins", "quantize", "dequantize", "histogram",
+    "correction_norms", "bins", "bins_l2s", "l2s_weights", "quantize", "dequantize", "histogram",
     "code_lengths", "canonical_codes", "encode", "decode", "escape_width", "compress",
     "decompress", "inspect", "compress_bound", "crc32", "level_sizes",
-    "parse_header", "DTYPE_F32", "DTYPE_F64", "LINF", "L2", "ABS", "REL",
+    "parse_header", "DTYPE_F32", "DTYPE_F64", "LINF", "L2", "L2_STAT", "ABS", "REL",
 ]
 
 DTYPE_F32, DTYPE_F64 = 0, 1
-LINF, L2 = 0, 1
+LINF, L2, L2_STAT = 0, 1, 2
 ABS, REL = 0, 1
 
 _lib = None
@@ -43,6 +43,8 @@ def _L():
             "oracle_recompose_c": [C.c_int, sz, dp, dp, dp],
             "oracle_correction_norms_c": [C.c_int, sz, dp, dp],
             "oracle_bins_c": [C.c_int, sz, dp, C.c_double, C.c_double, C.c_double, dp],
+            "oracle_bins_l2s_c": [C.c_int, sz, dp, C.c_double, C.c_double, C.c_double, dp],
+            "oracle_l2s_weights_c": [C.c_int, sz, dp, dp, dp],
             "oracle_recompose_adjoint": [C.c_int, sz, dp, dp],
             "oracle_decompose_adjoint": [C.c_int, sz, dp, dp],
             "oracle_correction_norms": [C.c_int, sz, dp],
@@ -172,6 +174,30 @@ def correction_norms(shape, coords=None):
     _check(_L().oracle_correction_norms_c(d, dims, None if co is None else _p(co, C.c_double),
                                           _p(c, C.c_double)), "correction_norms")
     return c
+
+
+def bins_l2s(shape, tau_abs, norm_inf, eps, coords=None):
+    """Statistical L2 bins (mode 2): q_l = sqrt(12 tau'^2 T / ((L+1) S_l))."""
+    d, dims = _dims(shape)
+    L, _ = levels(shape)
+    q = np.zeros(L + 1)
+    co = _coords(shape, coords)
+    _check(_L().oracle_bins_l2s_c(d, dims, None if co is None else _p(co, C.c_double), float(tau_abs),
+                                  float(norm_inf), float(eps), _p(q, C.c_double)), "bins_l2s")
+    return q
+
+
+def l2s_weights(shape, coords=None):
+    """(S[0..L], T): the mass-matrix diagonal summed over each level's new
+    nodes (all of level 0's), and over all finest nodes."""
+    d, dims = _dims(shape)
+    L, _ = levels(shape)
+    S = np.zeros(L + 1)
+    T = np.zeros(1)
+    co = _coords(shape, coords)
+    _check(_L().oracle_l2s_weights_c(d, dims, None if co is None else _p(co, C.c_double), _p(S, C.c_double),
+                                     _p(T, C.c_double)), "l2s_weights")
+    return S, float(T[0])
 
 
 def bins(shape, tau_abs, norm_inf, eps, coords=None):

@@ -8,7 +8,7 @@
  * padding bytes are zero):
  *   0   "HPDR"            4  u32 version (3)     8  u32 dtype (0 f32, 1 f64)
  *   12  u32 ndim          16 u64 dims[3] (unused dims hold 1)
- *   40  u32 L             44 u32 mode (0 Linf, 1 L2)
+ *   40  u32 L             44 u32 mode (0 Linf, 1 L2, 2 statistical L2)
  *   48  u32 tol kind (0 abs, 1 rel) | 0x100 when the container holds node coordinates
  *   52  u32 D             56 u32 K               60 u32 s_lo
  *   64  f64 tol           72 f64 tau_abs         80 f64 max|u|    88 f64 rms(u)
@@ -27,9 +27,10 @@
  * bitstream by zigzag(k) in W bits, W the largest bit length of the
  * container's escapes (0 without escapes; see oracle_encode).
  *
- * Tolerance: REL means tol times max|u| (Linf mode) or times rms(u) (L2
- * mode); ABS means tol itself.  L2 mode uses the same bins, which bound the
- * maximum error and therefore the RMS error too.
+ * Tolerance: REL means tol times max|u| (Linf mode) or times rms(u) (both L2
+ * modes); ABS means tol itself.  L2 mode uses the same bins, which bound the
+ * maximum error and therefore the RMS error too; statistical L2 mode uses the
+ * bins of oracle_bins_l2s_c, which bound the expected RMS error.
  */
 #include <stdlib.h>
 #include <string.h>
@@ -88,7 +89,7 @@ int oracle_compress_c(int d, const size_t *n, const double *coords, const double
 {
     int L;
     if (oracle_levels(d, n, &L, NULL)) return -1;
-    if ((dtype != 0 && dtype != 1) || (mode != 0 && mode != 1) || (tol_kind != 0 && tol_kind != 1))
+    if ((dtype != 0 && dtype != 1) || mode < 0 || mode > 2 || (tol_kind != 0 && tol_kind != 1))
         return -1;
     if (D < 4 || D > 65536 || (D % 2) || K == 0 || !(tol > 0)) return -1;
     uint64_t N = 1;
@@ -101,7 +102,8 @@ int oracle_compress_c(int d, const size_t *n, const double *coords, const double
     double tau_abs = (tol_kind == 1) ? tol * nrm : tol;
     double eps = (dtype == 0) ? ldexp(1.0, -24) : ldexp(1.0, -53);
     double *q = (double *)malloc((size_t)(L + 1) * sizeof(double));
-    int rc = oracle_bins_c(d, n, coords, tau_abs, mx, eps, q);
+    int rc = (mode == 2) ? oracle_bins_l2s_c(d, n, coords, tau_abs, mx, eps, q)
+                         : oracle_bins_c(d, n, coords, tau_abs, mx, eps, q);
     if (rc) { free(q); return (rc == -2) ? -1 : rc; }
 
     double *coef = (double *)malloc(N * sizeof(double));

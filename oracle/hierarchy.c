@@ -586,6 +586,76 @@ int oracle_bins_c(int d, const size_t *n, const double *coords, double tau_abs, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Statistical L2 bins (mode 2).  The paper gives no formula for an L2 bound,
+ * so this reading is fixed here.  The level components (Q_l - Q_{l-1}) u are
+ * L2-orthogonal, so coefficient errors delta_l on the new nodes of level l
+ * reach the reconstruction as (I - Q_{l-1}) f_l with f_l = sum_i delta_i
+ * phi_i (level-l hat functions), and ||u - u~||^2 <= sum_l ||f_l||^2.  With
+ * errors independent and uniform on [-q_l/2, q_l/2], E||f_l||^2 =
+ * (q_l^2 / 12) S_l, S_l = sum over the new nodes of the mass-matrix diagonal.
+ * The budget is tau'^2 T, T = trace of the finest mass matrix (the L2 norm of
+ * a field of uncorrelated nodal errors of RMS tau'), split evenly over the
+ * L + 1 levels:  q_l = sqrt(12 tau'^2 T / ((L+1) S_l)).  tau' carries the
+ * same precision margin as the max-norm bins.  The bound is on the expected
+ * error, not on every field. */
+
+/* diagonal entry i of the 1-D P1 mass matrix on nodes x[0..m-1] */
+static double mass_diag(const double *x, size_t m, size_t i)
+{
+    double h = 0.0;
+    if (i > 0) h += x[i] - x[i - 1];
+    if (i + 1 < m) h += x[i + 1] - x[i];
+    return h / 3.0;
+}
+
+int oracle_l2s_weights_c(int d, const size_t *n, const double *coords, double *S, double *T)
+{
+    ohier H;
+    if (ohier_build(&H, d, n, coords)) { ohier_free(&H); return -1; }
+    for (int l = 0; l <= H.L; l++) {
+        /* every node of level l, row-major; new unless kept in every dimension */
+        size_t cnt = ohier_count(&H, l);
+        double sum = 0.0, all = 0.0;
+        size_t p[OMAXD] = {0};
+        for (size_t idx = 0; idx < cnt; idx++) {
+            size_t r = idx;
+            for (int k = H.d - 1; k >= 0; k--) { p[k] = r % H.m[k][l]; r /= H.m[k][l]; }
+            double w = 1.0;
+            int kept = 1;
+            for (int k = 0; k < H.d; k++) {
+                w *= mass_diag(H.x[k][l], H.m[k][l], p[k]);
+                if (!ois_coarse(H.m[k][l], p[k])) kept = 0;
+            }
+            all += w;
+            if (l == 0 || !kept) sum += w;
+        }
+        S[l] = sum;
+        if (l == H.L) *T = all;
+    }
+    ohier_free(&H);
+    return 0;
+}
+
+int oracle_bins_l2s_c(int d, const size_t *n, const double *coords, double tau_abs, double norm_inf, double eps,
+                      double *q)
+{
+    int L;
+    if (oracle_levels(d, n, &L, NULL)) return -1;
+    if (norm_inf == 0.0) {
+        for (int l = 0; l <= L; l++) q[l] = 1.0;
+        return 0;
+    }
+    double tp = tau_abs - 32.0 * (double)(L + 1) * eps * norm_inf;
+    if (!(tp > 0.0)) return -2;
+    double *S = (double *)malloc((size_t)(L + 1) * sizeof(double));
+    double T = 0.0;
+    if (oracle_l2s_weights_c(d, n, coords, S, &T)) { free(S); return -1; }
+    for (int l = 0; l <= L; l++) q[l] = sqrt(12.0 * (tp * tp) * T / ((double)(L + 1) * S[l]));
+    free(S);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Linear quantization (MapAndProcess over levels, Sec. IV-A).                 */
 
 /* level of stream index i: level l occupies [N_{l-1}, N_l) (level 0: [0, N_0)) */

@@ -40,6 +40,13 @@ int oracle_recompose_c(int d, const size_t *n, const double *coords, const doubl
 int oracle_correction_norms_c(int d, const size_t *n, const double *coords, double *c);
 int oracle_bins_c(int d, const size_t *n, const double *coords, double tau_abs, double norm_inf, double eps,
                   double *q);
+/* Statistical L2 bins (mode 2; the paper states no formula, see
+ * hierarchy.c): S[l] = sum over the nodes new on level l (every node of level
+ * 0) of the diagonal of the level-l tensor P1 mass matrix, and *T the same
+ * sum over all finest nodes; q_l = sqrt(12 tau'^2 T / ((L+1) S_l)). */
+int oracle_l2s_weights_c(int d, const size_t *n, const double *coords, double *S /* [L+1] */, double *T);
+int oracle_bins_l2s_c(int d, const size_t *n, const double *coords, double tau_abs, double norm_inf, double eps,
+                      double *q);
 int oracle_recompose(int d, const size_t *n, const double *coef, double *u);
 int oracle_recompose_adjoint(int d, const size_t *n, const double *g_u, double *g_coef);
 int oracle_decompose_adjoint(int d, const size_t *n, const double *g_coef, double *g_u);
