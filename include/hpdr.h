@@ -64,7 +64,15 @@ typedef enum {
 } hpdr_status;
 
 typedef enum { HPDR_F32 = 0, HPDR_F64 = 1 } hpdr_dtype;
-typedef enum { HPDR_LINF = 0, HPDR_L2 = 1 } hpdr_mode;      /* norm of the error bound */
+/* Norm of the error bound.  LINF: max |u - u~| <= tau.  L2: tau from the RMS
+ * of u (REL), with the max-norm bins, so max |u - u~| <= tau as well.
+ * L2_STAT: statistical L2 bins (the paper names an L2 mode without a rule):
+ * q_l = sqrt(12 tau'^2 T / ((L+1) S_l)), S_l the level-l P1 mass-matrix
+ * diagonal summed over the level's new nodes and T its sum over all finest
+ * nodes, which bounds the EXPECTED squared L2 error by tau'^2 T (errors
+ * uniform and independent; the level components are L2-orthogonal), i.e. an
+ * RMS error of about tau or less; no per-field guarantee. */
+typedef enum { HPDR_LINF = 0, HPDR_L2 = 1, HPDR_L2_STAT = 2 } hpdr_mode;
 typedef enum { HPDR_ABS = 0, HPDR_REL = 1 } hpdr_tol_kind;  /* REL: tol x norm of the input */
 
 typedef struct hpdr_ctx hpdr_ctx;
@@ -102,8 +110,10 @@ size_t hpdr_compress_bound(int ndim, const size_t *dims, hpdr_dtype dtype, const
 /* Compress a device-resident field (Alg. 1 then Alg. 2).
  *   d_in        device array, ndim/dims as above, element type dtype.
  *   tol, tol_kind, mode: the error bound.  REL: tau = tol * max|u| (LINF) or
- *               tol * rms(u) (L2); ABS: tau = tol.  The reconstruction then
- *               satisfies max|u - u~| <= tau (which also bounds the RMS error).
+ *               tol * rms(u) (L2, L2_STAT); ABS: tau = tol.  With LINF and L2
+ *               the reconstruction satisfies max|u - u~| <= tau (which also
+ *               bounds the RMS error); with L2_STAT its expected RMS error is
+ *               at most about tau (see hpdr_mode).
  *   d_out       device buffer of out_capacity bytes receiving the container
  *               (format v3: 128-byte header, bins, code lengths, chunk table,
  *               bitstream; every section 16-byte aligned).  A code k whose

@@ -608,6 +608,18 @@ static double mass_diag(const double *x, size_t m, size_t i)
     return h / 3.0;
 }
 
+/* compensated (Neumaier) running sum: the sums below run over every node of
+ * a level, and a plain recursive sum of n terms may drift by n units of
+ * roundoff; this one stays within a few */
+typedef struct { double s, c; } ksum;
+static void ksum_add(ksum *k, double x)
+{
+    double t = k->s + x;
+    if (fabs(k->s) >= fabs(x)) k->c += (k->s - t) + x;
+    else k->c += (x - t) + k->s;
+    k->s = t;
+}
+
 int oracle_l2s_weights_c(int d, const size_t *n, const double *coords, double *S, double *T)
 {
     ohier H;
@@ -615,7 +627,7 @@ int oracle_l2s_weights_c(int d, const size_t *n, const double *coords, double *S
     for (int l = 0; l <= H.L; l++) {
         /* every node of level l, row-major; new unless kept in every dimension */
         size_t cnt = ohier_count(&H, l);
-        double sum = 0.0, all = 0.0;
+        ksum sum = {0.0, 0.0}, all = {0.0, 0.0};
         size_t p[OMAXD] = {0};
         for (size_t idx = 0; idx < cnt; idx++) {
             size_t r = idx;
@@ -626,11 +638,11 @@ int oracle_l2s_weights_c(int d, const size_t *n, const double *coords, double *S
                 w *= mass_diag(H.x[k][l], H.m[k][l], p[k]);
                 if (!ois_coarse(H.m[k][l], p[k])) kept = 0;
             }
-            all += w;
-            if (l == 0 || !kept) sum += w;
+            ksum_add(&all, w);
+            if (l == 0 || !kept) ksum_add(&sum, w);
         }
-        S[l] = sum;
-        if (l == H.L) *T = all;
+        S[l] = sum.s + sum.c;
+        if (l == H.L) *T = all.s + all.c;
     }
     ohier_free(&H);
     return 0;

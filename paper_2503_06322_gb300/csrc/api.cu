@@ -138,6 +138,84 @@ template <> const LevelGeom<double> &geom<double>(const Plan *P, int l) { return
         if (_e != cudaSuccess) { return HPDR_ERR_CUDA; }         \
     } while (0)
 
+// ----- statistical L2 bins (mode 2) ----------------------------------------
+// The paper names an L2 mode without a bin rule; the rule taken here bounds
+// the expected squared L2 error.  Coefficient errors on the new nodes of
+// level l enter the reconstruction as (I - Q_{l-1}) f_l, f_l their level-l
+// piecewise-linear function; the components are L2-orthogonal across levels,
+// so E||u - u~||^2 <= sum_l (q_l^2 / 12) S_l for independent uniform errors,
+// S_l = the level-l mass-matrix diagonal summed over the level's new nodes.
+// The budget tau'^2 T (T = trace of the finest mass matrix) is split evenly:
+//     q_l = sqrt(12 tau'^2 T / ((L+1) S_l)).
+// The diagonal is a product of 1-D diagonals, so the sum over all nodes of a
+// level is a product of 1-D sums A_k and the sum over its kept nodes a
+// product of sums B_k over the kept positions: S_l = prod A_k - prod B_k
+// (S_0 = prod A_k), T = prod A_k on the finest level.
+struct L2sArgs {
+    int L;
+    double eps, T;
+    double S[kMaxLevels + 1];
+};
+
+void l2s_weights(const Plan *P, L2sArgs &a)
+{
+    const int L = P->L, pad = 3 - P->ndim;
+    double A[3][kMaxLevels + 1], B[3][kMaxLevels + 1];
+    size_t co = 0;
+    for (int k = 0; k < 3; k++) {
+        for (int l = 0; l <= L; l++) A[k][l] = B[k][l] = 1.0;
+        if (k < pad) continue;
+        const int n = (int)P->n[k];
+        std::vector<double> x(n);
+        for (int i = 0; i < n; i++) x[i] = P->coords.empty() ? (double)i : P->coords[co + i];
+        co += n;
+        auto diag = [&](int i) {
+            double h = 0.0;
+            if (i > 0) h += x[i] - x[i - 1];
+            if (i + 1 < (int)x.size()) h += x[i + 1] - x[i];
+            return h / 3.0;
+        };
+        for (int l = L; l >= 0; l--) {
+            const int m = (int)x.size(), mc = l > 0 ? P->m[k][l - 1] : 0;
+            double sa = 0.0, sb = 0.0;
+            for (int i = 0; i < m; i++) sa += diag(i);
+            for (int j = 0; j < mc; j++) sb += diag(cpos_of(m, mc, j));
+            A[k][l] = sa;
+            B[k][l] = sb;
+            if (l > 0) {
+                std::vector<double> xc(mc);
+                for (int j = 0; j < mc; j++) xc[j] = x[cpos_of(m, mc, j)];
+                x.swap(xc);
+            }
+        }
+    }
+    a.L = L;
+    for (int l = 0; l <= L; l++) {
+        const double pa = A[0][l] * A[1][l] * A[2][l];
+        a.S[l] = l == 0 ? pa : pa - B[0][l] * B[1][l] * B[2][l];
+        if (l == L) a.T = pa;
+    }
+}
+
+// runs after bins_kernel (which set the norm, tau and the status of the
+// bound) and replaces its bins; a rejected bound or a zero field keeps them
+__global__ void bins_l2s_kernel(L2sArgs a, Scalars *sc)
+{
+    if (sc->status) return;
+    const double mx = sc->maxabs;
+    if (!(mx > 0.0)) return;
+    const double tp = __dsub_rn(sc->tau_abs, __dmul_rn(__dmul_rn(__dmul_rn(32.0, (double)(a.L + 1)), a.eps), mx));
+    for (int l = threadIdx.x; l <= a.L; l += blockDim.x) {
+        const double q = __dsqrt_rn(__ddiv_rn(__dmul_rn(__dmul_rn(12.0, __dmul_rn(tp, tp)), a.T),
+                                              __dmul_rn((double)(a.L + 1), a.S[l])));
+        sc->q[l] = q;
+        const double r = __ddiv_rn(1.0, q);
+        sc->rho_d[l] = r;
+        sc->rho_f[l] = __double2float_rn(r);
+        sc->q_f[l] = __double2float_rn(q);
+    }
+}
+
 // the whole compression of one field, enqueued on s without any host wait;
 // the container size and status stay in w.sc (device)
 template <typename T>
@@ -159,10 +237,19 @@ hpdr_status compress_core(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, co
     for (int l = 0; l <= L; l++) ba.c[l] = P->corr_norm[l];
     ba.tol = tol;
     ba.tol_kind = tol_kind;
-    ba.mode = mode;
+    ba.mode = mode == 2 ? 1 : mode;   // both L2 modes take the RMS norm
     ba.eps = sizeof(T) == 4 ? ldexp(1.0, -24) : ldexp(1.0, -53);
     ba.N = N;
     CK(launch_bins(ba, w.partials, norm_parts(), w.sc, s));
+    if (mode == 2) {
+        L2sArgs la;
+        memset(&la, 0, sizeof(la));
+        l2s_weights(P, la);
+        la.eps = ba.eps;
+        bins_l2s_kernel<<<1, 32, 0, s>>>(la, w.sc);
+        count_launch();
+        CK(cudaGetLastError());
+    }
 
     QuantOut qo;
     qo.sym = w.sym; qo.hist = w.hist; qo.esc = w.esc;
@@ -809,7 +896,7 @@ hpdr_status compress_in_flight(hpdr_ctx *ctx, const void *d_in, hpdr_dtype dtype
 {
     unsigned D, K;
     if (!ctx || !d_in || !d_out || !h_size_status || !d_pair || !valid_cfg(cfg, D, K)) return HPDR_ERR_ARG;
-    if ((dtype != HPDR_F32 && dtype != HPDR_F64) || (mode != HPDR_LINF && mode != HPDR_L2) ||
+    if ((dtype != HPDR_F32 && dtype != HPDR_F64) || (mode != HPDR_LINF && mode != HPDR_L2 && mode != HPDR_L2_STAT) ||
         (tol_kind != HPDR_ABS && tol_kind != HPDR_REL) || !(tol > 0.0) || !std::isfinite(tol))
         return HPDR_ERR_ARG;
     if (((uintptr_t)d_in & 15) || ((uintptr_t)d_out & 15)) return HPDR_ERR_ARG;
@@ -913,7 +1000,7 @@ hpdr_status hpdr_compress_coords(hpdr_ctx *ctx, const void *d_in, hpdr_dtype dty
 {
     unsigned D, K;
     if (!ctx || !d_in || !d_out || !out_bytes || !valid_cfg(cfg, D, K)) return HPDR_ERR_ARG;
-    if ((dtype != HPDR_F32 && dtype != HPDR_F64) || (mode != HPDR_LINF && mode != HPDR_L2) ||
+    if ((dtype != HPDR_F32 && dtype != HPDR_F64) || (mode != HPDR_LINF && mode != HPDR_L2 && mode != HPDR_L2_STAT) ||
         (tol_kind != HPDR_ABS && tol_kind != HPDR_REL) || !(tol > 0.0) || !std::isfinite(tol))
         return HPDR_ERR_ARG;
     if (((uintptr_t)d_in & 15) || ((uintptr_t)d_out & 15)) return HPDR_ERR_ARG;
@@ -1354,7 +1441,7 @@ hpdr_status hpdr_compress_batched(hpdr_ctx *ctx, int nfields, const hpdr_field *
     for (int i = 0; i < nfields; i++) {
         const hpdr_field &f = fields[i];
         if (!f.d_in || ((uintptr_t)f.d_in & 15) || (f.dtype != HPDR_F32 && f.dtype != HPDR_F64) ||
-            (f.mode != HPDR_LINF && f.mode != HPDR_L2) || (f.tol_kind != HPDR_ABS && f.tol_kind != HPDR_REL) ||
+            (f.mode != HPDR_LINF && f.mode != HPDR_L2 && f.mode != HPDR_L2_STAT) || (f.tol_kind != HPDR_ABS && f.tol_kind != HPDR_REL) ||
             !(f.tol > 0.0) || !std::isfinite(f.tol))
             return HPDR_ERR_ARG;
         const size_t b = hpdr_compress_bound(f.ndim, f.dims, f.dtype, cfg);

@@ -23,7 +23,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhpdr.so")
 
 F32, F64 = 0, 1
-LINF, L2 = 0, 1
+LINF, L2, L2_STAT = 0, 1, 2
 ABS, REL = 0, 1
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "output buffer too small",
           -4: "malformed container", -5: "device wait timed out", -6: "device allocation failed"}

@@ -1,0 +1,106 @@
+"""Statistical L2 bins (mode 2) on the GPU against the oracle.
+
+Bins within rtol 1e-12 of the oracle's (the GPU takes the level mass sums in
+closed form, the oracle node by node); codes bit-exact when the oracle
+quantizes the GPU's coefficients with the container's bins; cross decoding
+both ways; RMS error below tau; batched and host-streamed containers equal to
+the single-field ones."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2503_06322_gb300 import hpdr
+    return hpdr
+
+
+def _field(shape, seed, dtype):
+    from paper_2503_06322_gb300 import fields
+    if len(shape) == 1:
+        return (np.random.default_rng(seed).standard_normal(shape) * 2 + 0.5).astype(dtype)
+    return fields.powerlaw_field(shape, seed=seed, dtype=dtype)
+
+
+@pytest.mark.parametrize("shape,tol,coords", [((129, 129), 1e-3, False), ((33, 17, 9), 1e-2, False),
+                                              ((70, 70, 70), 1e-3, False), ((1000,), 1e-3, False),
+                                              ((65, 65, 65), 1e-4, False), ((300, 200), 1e-3, True),
+                                              ((40, 30, 20), 1e-3, True)], ids=str)
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_bins_codes_and_cross_decoding(oracle, H, shape, tol, coords, dtype):
+    from paper_2503_06322_gb300 import fields
+    u = _field(shape, 11, dtype)
+    co = fields.node_coords(shape, 12) if coords else None
+    ut = torch.from_numpy(u).cuda()
+    buf = H.hpdr_compress(ut, tol, mode=H.L2_STAT, coords=co).cpu().numpy()
+    h = oracle.parse_header(buf)
+    assert h["mode"] == 2
+    ud = u.astype(np.float64)
+    rms = math.sqrt(float(np.mean(ud * ud)))
+    tau = tol * rms
+    eps = 2.0 ** -24 if dtype == np.float32 else 2.0 ** -53
+    q_ref = oracle.bins_l2s(shape, tau, np.abs(ud).max(), eps, coords=co)
+    # tau = tol * rms(u): for FP32 data the GPU's per-thread partial sums of
+    # squares are binary32 sums of at most 8 squares at these sizes (relative
+    # error <= 8 * 2^-24 ~ 5e-7, halved by the square root), and q is
+    # proportional to tau; FP64 partials agree to rounding
+    rtol = 2e-6 if dtype == np.float32 else 1e-12
+    assert np.allclose(h["q"], q_ref, rtol=rtol, atol=0)
+    sym, esc = oracle.decode(h["words"], h["chunk"], h["N"], h["K"], h["lengths"], esc_width=h["esc_width"])
+    coef = H.hpdr_decompose(ut, coords=co).cpu().numpy().astype(np.float64)
+    prec = 32 if dtype == np.float32 else 64
+    ref_sym, _, ref_k = oracle.quantize(coef, shape, h["q"], precision=prec)
+    assert np.array_equal(sym, ref_sym) and np.array_equal(esc, ref_k)
+    rec = H.hpdr_decompress(torch.from_numpy(buf).cuda()).cpu().numpy().astype(np.float64)
+    e_rms = math.sqrt(float(np.mean((rec - ud) ** 2)))
+    assert e_rms <= tau
+    # the oracle decodes the GPU container
+    assert math.sqrt(float(np.mean((oracle.decompress(buf) - ud) ** 2))) <= tau
+    ob = oracle.compress(u, tol, mode=oracle.L2_STAT, coords=co)
+    rec2 = H.hpdr_decompress(torch.from_numpy(ob).cuda()).cpu().numpy().astype(np.float64)
+    assert math.sqrt(float(np.mean((rec2 - ud) ** 2))) <= tau
+    # wider bins than the max-norm rule: a smaller container
+    assert buf.size < H.hpdr_compress(ut, tol, mode=H.LINF, coords=co).numel()
+
+
+def test_bench_field_rms_and_ratio(H):
+    """The 513^3 bench field class at 257^3: RMS error under tau, and the
+    ratio against the max-norm bins at the same tol."""
+    from paper_2503_06322_gb300 import fields
+    u = fields.powerlaw_field_torch((257, 257, 257), seed=1, device="cuda")
+    tol = 1e-3
+    b2 = H.hpdr_compress(u, tol, mode=H.L2_STAT)
+    rec = H.hpdr_decompress(b2)
+    tau = tol * u.double().pow(2).mean().sqrt().item()
+    e_rms = (rec.double() - u.double()).pow(2).mean().sqrt().item()
+    assert 0.05 * tau <= e_rms <= tau
+    b0 = H.hpdr_compress(u, tol, mode=H.LINF)
+    assert b2.numel() < b0.numel()
+
+
+def test_batched_and_streamed_match_single_field(H):
+    from paper_2503_06322_gb300 import fields
+    shapes = [(65, 33), (17, 9, 33), (129, 129)]
+    us = [torch.from_numpy(fields.powerlaw_field(s, seed=20 + i, dtype=np.float32)).cuda()
+          for i, s in enumerate(shapes)]
+    out, offs, sizes = H.hpdr_compress_batched(us, [1e-3] * len(us), mode=H.L2_STAT)
+    for u, o, n in zip(us, offs, sizes):
+        single = H.hpdr_compress(u, 1e-3, mode=H.L2_STAT).cpu().numpy()
+        assert np.array_equal(out[o:o + n].cpu().numpy(), single)
+    u = fields.powerlaw_field((40, 33, 33), seed=30, dtype=np.float32)
+    plane = 33 * 33 * 4
+    buf = H.hpdr_compress_host_streamed(torch.from_numpy(u).pin_memory(), 1e-3, mode=H.L2_STAT,
+                                        slab_bytes=10 * plane)
+    b = buf.numpy().tobytes()
+    ns = int.from_bytes(b[8:12], "little")
+    for i in range(ns):
+        e = 64 + 32 * i
+        first, cnt, off, size = (int.from_bytes(b[e + 8 * j:e + 8 * j + 8], "little") for j in range(4))
+        slab = np.ascontiguousarray(u[first:first + cnt])
+        single = H.hpdr_compress(torch.from_numpy(slab).cuda(), 1e-3, mode=H.L2_STAT).cpu().numpy()
+        assert np.array_equal(np.frombuffer(b[off:off + size], dtype=np.uint8), single)
