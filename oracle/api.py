@@ -14,7 +14,8 @@ __all__ = [
     "correction_norms", "bins", "bins_l2s", "l2s_weights", "quantize", "dequantize", "histogram",
     "code_lengths", "canonical_codes", "encode", "decode", "escape_width", "compress",
     "decompress", "inspect", "compress_bound", "crc32", "level_sizes",
-    "parse_header", "DTYPE_F32", "DTYPE_F64", "LINF", "L2", "L2_STAT", "ABS", "REL",
+    "parse_header", "zfp_bound", "zfp_compress", "zfp_decompress", "zfp_fwd_line", "zfp_inv_line",
+    "zfp_order", "negabinary", "from_negabinary", "zfp_encode_planes", "zfp_decode_planes", "DTYPE_F32", "DTYPE_F64", "LINF", "L2", "L2_STAT", "ABS", "REL",
 ]
 
 DTYPE_F32, DTYPE_F64 = 0, 1
@@ -75,6 +76,26 @@ def _L():
         _lib.oracle_compress_bound.argtypes = [C.c_int, sz, C.c_uint32, C.c_uint32]
         _lib.oracle_compress_bound.restype = C.c_uint64
         _lib.oracle_crc32.argtypes = [u8, C.c_uint64]
+        _lib.oracle_zfp_bound.argtypes = [C.c_int, sz, C.c_int, C.c_uint32]
+        _lib.oracle_zfp_bound.restype = C.c_uint64
+        _lib.oracle_zfp_compress.argtypes = [C.c_int, sz, dp, C.c_int, C.c_uint32, u8, C.c_uint64, u64]
+        _lib.oracle_zfp_compress.restype = C.c_int
+        _lib.oracle_zfp_decompress.argtypes = [u8, C.c_uint64, dp, C.c_uint64]
+        _lib.oracle_zfp_decompress.restype = C.c_int
+        _lib.oracle_zfp_fwd_line.argtypes = [i64, C.c_int]
+        _lib.oracle_zfp_fwd_line.restype = None
+        _lib.oracle_zfp_inv_line.argtypes = [i64, C.c_int]
+        _lib.oracle_zfp_inv_line.restype = None
+        _lib.oracle_zfp_order.argtypes = [C.c_int, C.POINTER(C.c_int)]
+        _lib.oracle_zfp_order.restype = None
+        _lib.oracle_negabinary.argtypes = [C.c_int64, C.c_int]
+        _lib.oracle_negabinary.restype = C.c_uint64
+        _lib.oracle_from_negabinary.argtypes = [C.c_uint64, C.c_int]
+        _lib.oracle_from_negabinary.restype = C.c_int64
+        _lib.oracle_zfp_encode_planes.argtypes = [u64, C.c_int, C.c_int, u32, C.c_uint64, C.c_uint64]
+        _lib.oracle_zfp_encode_planes.restype = None
+        _lib.oracle_zfp_decode_planes.argtypes = [u64, C.c_int, C.c_int, u32, C.c_uint64, C.c_uint64]
+        _lib.oracle_zfp_decode_planes.restype = None
         _lib.oracle_crc32.restype = C.c_uint32
     return _lib
 
@@ -361,6 +382,79 @@ def decompress(buf):
     _check(_L().oracle_decompress(_p(buf, C.c_uint8), buf.size, _p(u, C.c_double), n),
            "decompress")
     return u.reshape(shape)
+
+
+# ---- fixed-rate ZFP (Alg. 3) ---------------------------------------------
+
+def zfp_bound(shape, rate, dtype=DTYPE_F32):
+    d, dims = _dims(shape)
+    return int(_L().oracle_zfp_bound(d, dims, int(dtype), int(rate)))
+
+
+def zfp_compress(u, rate, dtype=None):
+    """Fixed-rate container bytes of u (dtype defaults to u's: f32 or f64)."""
+    u = np.asarray(u)
+    if dtype is None:
+        dtype = DTYPE_F32 if u.dtype == np.float32 else DTYPE_F64
+    d, dims = _dims(u.shape)
+    x = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+    cap = zfp_bound(u.shape, rate, dtype)
+    if cap == 0:
+        raise ValueError("zfp: invalid rate %r for %d dimensions" % (rate, d))
+    out = np.zeros(cap, dtype=np.uint8)
+    nb = C.c_uint64()
+    _check(_L().oracle_zfp_compress(d, dims, _p(x, C.c_double), int(dtype), int(rate), _p(out, C.c_uint8), cap,
+                                    C.byref(nb)), "zfp_compress")
+    return out[:nb.value].copy()
+
+
+def zfp_decompress(buf):
+    b = np.ascontiguousarray(np.frombuffer(bytes(buf), dtype=np.uint8))
+    d = int.from_bytes(bytes(b[12:16]), "little")
+    shape = tuple(int.from_bytes(bytes(b[16 + 8 * k:24 + 8 * k]), "little") for k in range(d))
+    u = np.empty(int(np.prod(shape)))
+    _check(_L().oracle_zfp_decompress(_p(b, C.c_uint8), b.size, _p(u, C.c_double), u.size), "zfp_decompress")
+    return u.reshape(shape)
+
+
+def zfp_fwd_line(a):
+    x = np.ascontiguousarray(a, dtype=np.int64).copy()
+    _L().oracle_zfp_fwd_line(_p(x, C.c_int64), 1)
+    return x
+
+
+def zfp_inv_line(a):
+    x = np.ascontiguousarray(a, dtype=np.int64).copy()
+    _L().oracle_zfp_inv_line(_p(x, C.c_int64), 1)
+    return x
+
+
+def zfp_order(d):
+    perm = (C.c_int * (4 ** d))()
+    _L().oracle_zfp_order(d, perm)
+    return list(perm)
+
+
+def negabinary(q, P):
+    return int(_L().oracle_negabinary(int(q), int(P)))
+
+
+def from_negabinary(u, P):
+    return int(_L().oracle_from_negabinary(int(u), int(P)))
+
+
+def zfp_encode_planes(u, P, maxbits):
+    u = np.ascontiguousarray(u, dtype=np.uint64)
+    w = np.zeros((maxbits + 31) // 32, dtype=np.uint32)
+    _L().oracle_zfp_encode_planes(_p(u, C.c_uint64), u.size, P, _p(w, C.c_uint32), 0, maxbits)
+    return w
+
+
+def zfp_decode_planes(words, B, P, maxbits):
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    u = np.zeros(B, dtype=np.uint64)
+    _L().oracle_zfp_decode_planes(_p(u, C.c_uint64), B, P, _p(w, C.c_uint32), 0, maxbits)
+    return u
 
 
 def crc32(data):

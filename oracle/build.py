@@ -7,7 +7,7 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["hierarchy.c", "huffman.c", "container.c"]
+SOURCES = ["hierarchy.c", "huffman.c", "container.c", "zfp.c"]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 

@@ -47,6 +47,21 @@ int oracle_bins_c(int d, const size_t *n, const double *coords, double tau_abs, 
 int oracle_l2s_weights_c(int d, const size_t *n, const double *coords, double *S /* [L+1] */, double *T);
 int oracle_bins_l2s_c(int d, const size_t *n, const double *coords, double tau_abs, double norm_inf, double eps,
                       double *q);
+/* Fixed-rate ZFP (Alg. 3; the reading is in zfp.c's header).  rate = bits
+ * per value (1..256); rate * 4^d must be a multiple of 32.  dtype 0 rounds the input
+ * to binary32 first.  Returns 0, -1 (arguments), -3 (capacity), -4 (format). */
+uint64_t oracle_zfp_bound(int d, const size_t *n, int dtype, uint32_t rate);
+int oracle_zfp_compress(int d, const size_t *n, const double *u, int dtype, uint32_t rate, uint8_t *out,
+                        uint64_t cap, uint64_t *out_bytes);
+int oracle_zfp_decompress(const uint8_t *in, uint64_t in_bytes, double *u, uint64_t n_cap);
+/* its steps, for the pins */
+void oracle_zfp_fwd_line(int64_t *a, int stride);
+void oracle_zfp_inv_line(int64_t *a, int stride);
+void oracle_zfp_order(int d, int *perm);
+uint64_t oracle_negabinary(int64_t q, int P);
+int64_t oracle_from_negabinary(uint64_t u, int P);
+void oracle_zfp_encode_planes(const uint64_t *u, int B, int P, uint32_t *words, uint64_t start, uint64_t end);
+void oracle_zfp_decode_planes(uint64_t *u, int B, int P, const uint32_t *words, uint64_t start, uint64_t end);
 int oracle_recompose(int d, const size_t *n, const double *coef, double *u);
 int oracle_recompose_adjoint(int d, const size_t *n, const double *g_u, double *g_coef);
 int oracle_decompose_adjoint(int d, const size_t *n, const double *g_coef, double *g_u);
