@@ -48,6 +48,7 @@ def parse_args():
     ap.add_argument("--no-stream", action="store_true", help="skip the 1025^3 host-streamed leg")
     ap.add_argument("--no-lossless", action="store_true", help="skip the lossless (Huffman-only) leg")
     ap.add_argument("--no-l2s", action="store_true", help="skip the statistical L2 mode leg")
+    ap.add_argument("--no-zfp", action="store_true", help="skip the fixed-rate ZFP leg")
     return ap.parse_args()
 
 
@@ -579,6 +580,42 @@ def run_l2s(args, u):
             "max_err_over_tau": round((rec - u).abs().max().item() / tau, 4)}
 
 
+def run_zfp(args, u):
+    """Fixed-rate ZFP (Alg. 3) on the timed field at 8 and 16 bits per value:
+    compress and decompress throughput (field bytes / time, CUDA events over
+    ten calls after three warm-ups each), ratio and RMS error over the
+    field's standard deviation."""
+    import torch
+    from paper_2503_06322_gb300 import hpdr
+    fb = u.numel() * u.element_size()
+    res = {"workload": "the timed field, fixed rate, one thread per 4^3 block"}
+    std = u.double().std().item()
+    for rate in (8, 16):
+        cap = hpdr.zfp_bound(tuple(u.shape), rate, u.dtype)
+        cbuf = torch.empty(cap, dtype=torch.uint8, device=u.device)
+        rec = torch.empty_like(u)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        for _ in range(3):
+            b = hpdr.hpdr_zfp_compress(u, rate, out=cbuf)
+            hpdr.hpdr_zfp_decompress(b, out=rec)
+        n = 10
+        e0.record()
+        for _ in range(n):
+            b = hpdr.hpdr_zfp_compress(u, rate, out=cbuf)
+        e1.record()
+        for _ in range(n):
+            hpdr.hpdr_zfp_decompress(b, out=rec)
+        e2.record()
+        torch.cuda.synchronize()
+        tc, td = e0.elapsed_time(e1) / n, e1.elapsed_time(e2) / n
+        err = (rec.double() - u.double()).pow(2).mean().sqrt().item() / std
+        res["rate_%d" % rate] = {"compress_gbs": round(fb / (tc * 1e-3) / 1e9, 2),
+                                 "decompress_gbs": round(fb / (td * 1e-3) / 1e9, 2),
+                                 "compression_ratio": round(fb / b.numel(), 4), "rms_err_over_std": float("%.4g" % err)}
+        del cbuf, rec
+    return res
+
+
 def run_lossless(args, dev):
     """The Huffman stage on its own (Alg. 2) through hpdr_lossless_compress /
     hpdr_lossless_decompress, device-resident: 1 GiB of byte keys (rounded
@@ -685,6 +722,8 @@ def main():
         out["adjoint"] = run_adjoint(args, u.device)
     if rank == 0 and not args.no_l2s:
         out["l2_stat"] = run_l2s(args, u)
+    if rank == 0 and not args.no_zfp:
+        out["zfp"] = run_zfp(args, u)
     if rank == 0 and not args.no_batched:
         out["batched"] = run_batched(args, u.device)
     if rank == 0 and not args.no_stream:

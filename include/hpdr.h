@@ -299,6 +299,38 @@ hpdr_status hpdr_lossless_decompress(hpdr_ctx *ctx, const void *d_in, size_t in_
 /* Key width and count of an HPDL container (host or device pointer). */
 hpdr_status hpdr_lossless_inspect(const void *in, size_t in_bytes, int *key_bytes, uint64_t *n);
 
+/* ---- Fixed-rate ZFP (Alg. 3, Sec. IV-C) --------------------------------
+ * A second compressor on its own path: the field is cut into blocks of 4^d
+ * values (edge-replicated at the array border), each block aligned to its
+ * largest binary exponent and made fixed point (P - 5 fraction bits, P = 32
+ * or 64), decorrelated by a two-level integer S-transform per dimension,
+ * reordered coarse to fine, mapped to negabinary, and its bit planes coded
+ * most significant first with group tests, cut at exactly rate * 4^d bits.
+ * Every block has the same size, so compression and decompression are one
+ * thread per block with no coordination and no synchronization.
+ * Container "HPDZ": a 64-byte header (version 1, dtype, ndim, dims, rate,
+ * bits per block, block count, CRC-32 of bytes [0,60)) and the blocks' 32-bit
+ * words (bits least significant first).
+ *   rate   bits per value, 1..256, with rate * 4^ndim a multiple of 32 (1-D:
+ *          multiples of 8; 2-D: even; 3-D: any).
+ * hpdr_zfp_bound: the exact container size (0 on bad arguments).
+ * hpdr_zfp_compress: d_in device array (dims >= 1, row-major), d_out 16-byte
+ *   aligned; *out_bytes = hpdr_zfp_bound(...).  Does not synchronize.
+ *   Errors: HPDR_ERR_ARG, HPDR_ERR_CAPACITY, HPDR_ERR_CUDA.  Non-finite
+ *   values are not supported (their blocks decode to unspecified values).
+ * hpdr_zfp_decompress: reads the header back (synchronizes `stream` once),
+ *   then decodes into d_out (out_capacity bytes).  Errors: HPDR_ERR_FORMAT,
+ *   HPDR_ERR_CAPACITY, HPDR_ERR_ARG, HPDR_ERR_CUDA.
+ * hpdr_zfp_inspect: dtype, ndim, dims (3 slots) and rate of a container in
+ *   host or device memory. */
+size_t hpdr_zfp_bound(int ndim, const size_t *dims, hpdr_dtype dtype, uint32_t rate);
+hpdr_status hpdr_zfp_compress(hpdr_ctx *ctx, const void *d_in, hpdr_dtype dtype, int ndim, const size_t *dims,
+                              uint32_t rate, void *d_out, size_t out_capacity, size_t *out_bytes, void *stream);
+hpdr_status hpdr_zfp_decompress(hpdr_ctx *ctx, const void *d_in, size_t in_bytes, void *d_out, size_t out_capacity,
+                                void *stream);
+hpdr_status hpdr_zfp_inspect(const void *in, size_t in_bytes, hpdr_dtype *dtype, int *ndim, size_t *dims,
+                             uint32_t *rate);
+
 /* Adaptive chunk sizing of the host-device pipeline (Sec. V-C, Alg. 4).
  * Model of the pipeline (all sizes in bytes, throughputs in bytes/s):
  *   Phi(C)   = alpha * C + beta  for C <  c_threshold

@@ -95,6 +95,10 @@ def lib():
             "hpdr_lossless_compress": [vp, vp, C.c_uint64, C.c_int, C.c_uint32, vp, C.c_size_t, sz, vp],
             "hpdr_lossless_decompress": [vp, vp, C.c_size_t, vp, C.c_size_t, vp],
             "hpdr_lossless_inspect": [vp, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_uint64)],
+            "hpdr_zfp_compress": [vp, vp, C.c_int, C.c_int, sz, C.c_uint32, vp, C.c_size_t, sz, vp],
+            "hpdr_zfp_decompress": [vp, vp, C.c_size_t, vp, C.c_size_t, vp],
+            "hpdr_zfp_inspect": [vp, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_int), sz,
+                                 C.POINTER(C.c_uint32)],
             "hpdr_pipeline_fit": [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, C.c_double,
                                   C.c_double, C.POINTER(PipelineModel)],
             "hpdr_pipeline_profile": [vp, vp, C.c_int, C.c_int, sz, C.c_double, C.c_int, C.c_int,
@@ -118,6 +122,8 @@ def lib():
         L.hpdr_streamed_bound.argtypes = [C.c_int, sz, C.c_int, C.POINTER(Config), sz, C.c_size_t]
         L.hpdr_streamed_bound.restype = C.c_size_t
         L.hpdr_status_string.argtypes = [C.c_int]
+        L.hpdr_zfp_bound.restype = C.c_size_t
+        L.hpdr_zfp_bound.argtypes = [C.c_int, sz, C.c_int, C.c_uint32]
         L.hpdr_status_string.restype = C.c_char_p
         _lib = L
     return _lib
@@ -522,4 +528,47 @@ def hpdr_huffman_decode(words, total_bits, chunk, N, lengths, D=8192, K=1024, ou
                                      int(total_bits), C.c_void_p(chunk.data_ptr()), N, D, K,
                                      C.c_void_p(lengths.data_ptr()), C.c_void_p(out.data_ptr()),
                                      _stream(stream)), "hpdr_huffman_decode")
+    return out
+
+
+# ---- fixed-rate ZFP (Alg. 3) ------------------------------------------------
+
+def zfp_bound(shape, rate, dtype=torch.float32):
+    nd, dims = _dims(shape)
+    return int(lib().hpdr_zfp_bound(nd, dims, _dtype_code(dtype), int(rate)))
+
+
+def hpdr_zfp_compress(u, rate, out=None, stream=None):
+    """Fixed-rate ZFP container (uint8 CUDA tensor) of a CUDA field; rate =
+    bits per value (rate * 4^ndim a multiple of 32)."""
+    _dev_tensor(u, "u")
+    nd, dims = _dims(u.shape)
+    cap = zfp_bound(u.shape, rate, u.dtype)
+    if cap == 0:
+        raise ValueError("invalid ZFP rate %r for %d dimensions" % (rate, nd))
+    if out is None:
+        out = torch.empty(cap, dtype=torch.uint8, device=u.device)
+    nb = C.c_size_t()
+    _check(lib().hpdr_zfp_compress(context(u.device.index), C.c_void_p(u.data_ptr()), _dtype_code(u.dtype), nd,
+                                   dims, int(rate), C.c_void_p(out.data_ptr()), out.numel(), C.byref(nb),
+                                   _stream(stream)), "hpdr_zfp_compress")
+    return out[:nb.value]
+
+
+def hpdr_zfp_inspect(buf):
+    dt, nd, r = C.c_int(), C.c_int(), C.c_uint32()
+    dims = (C.c_size_t * 3)()
+    _check(lib().hpdr_zfp_inspect(C.c_void_p(buf.data_ptr()), buf.numel(), C.byref(dt), C.byref(nd), dims,
+                                  C.byref(r)), "hpdr_zfp_inspect")
+    return (torch.float32 if dt.value == F32 else torch.float64), tuple(dims[:nd.value]), r.value
+
+
+def hpdr_zfp_decompress(buf, out=None, stream=None):
+    _dev_tensor(buf, "buf")
+    dt, shape, _ = hpdr_zfp_inspect(buf)
+    if out is None:
+        out = torch.empty(shape, dtype=dt, device=buf.device)
+    _check(lib().hpdr_zfp_decompress(context(buf.device.index), C.c_void_p(buf.data_ptr()), buf.numel(),
+                                     C.c_void_p(out.data_ptr()), out.numel() * out.element_size(),
+                                     _stream(stream)), "hpdr_zfp_decompress")
     return out
