@@ -263,6 +263,21 @@ struct BitReader {
         left -= (uint32_t)cnt;
         return cnt;
     }
+    // the next cnt bits (cnt <= min(32, left)) without consuming them
+    __device__ __forceinline__ uint32_t peek(int cnt)
+    {
+        if (nbuf < cnt) {
+            buf |= (unsigned long long)w[idx++] << nbuf;
+            nbuf += 32;
+        }
+        return (uint32_t)buf & (cnt == 32 ? 0xFFFFFFFFu : ((1u << cnt) - 1u));
+    }
+    __device__ __forceinline__ void skip(int cnt)
+    {
+        buf >>= cnt;
+        nbuf -= cnt;
+        left -= (uint32_t)cnt;
+    }
 };
 
 template <typename T, int D>
@@ -379,12 +394,23 @@ __global__ void __launch_bounds__(kZfpThreads) zfp_decode_kernel(const uint32_t 
                 uint32_t t;
                 if (br.get(1, &t) == 0) { more = false; break; }
                 if (!t) break;
-                // scan to the next 1 (a malformed stream may run out at B)
+                // scan to the next 1, up to 32 bits at a time (a malformed
+                // stream may run out at B)
                 while (n < B) {
-                    uint32_t x;
-                    if (br.get(1, &x) == 0) { more = false; break; }
-                    n++;
-                    if (x) { mask |= 1ull << (n - 1); break; }
+                    int avail = B - n < 32 ? B - n : 32;
+                    if (avail > (int)br.left) avail = (int)br.left;
+                    if (avail == 0) { more = false; break; }
+                    const uint32_t x = br.peek(avail);
+                    if (!x) {
+                        br.skip(avail);
+                        n += avail;
+                        continue;
+                    }
+                    const int j = __ffs((int)x) - 1;
+                    br.skip(j + 1);
+                    n += j + 1;
+                    mask |= 1ull << (n - 1);
+                    break;
                 }
             }
             if (mask) {
