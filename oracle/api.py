@@ -47,6 +47,8 @@ def _L():
             "oracle_bins_l2s_c": [C.c_int, sz, dp, C.c_double, C.c_double, C.c_double, dp],
             "oracle_l2s_weights_c": [C.c_int, sz, dp, dp, dp],
             "oracle_recompose_adjoint": [C.c_int, sz, dp, dp],
+            "oracle_recompose_adjoint_c": [C.c_int, sz, dp, dp, dp],
+            "oracle_decompose_adjoint_c": [C.c_int, sz, dp, dp, dp],
             "oracle_decompose_adjoint": [C.c_int, sz, dp, dp],
             "oracle_correction_norms": [C.c_int, sz, dp],
             "oracle_bins": [C.c_int, sz, C.c_double, C.c_double, C.c_double, dp],
@@ -177,14 +179,21 @@ def recompose(coef, shape, coords=None):
                      coef, shape, "recompose").reshape(shape)
 
 
-def recompose_adjoint(g_u):
+def recompose_adjoint(g_u, coords=None):
     g_u = np.asarray(g_u)
-    return _field_op(_L().oracle_recompose_adjoint, g_u, g_u.shape, "recompose_adjoint")
+    co = _coords(g_u.shape, coords)
+    if co is None:
+        return _field_op(_L().oracle_recompose_adjoint, g_u, g_u.shape, "recompose_adjoint")
+    return _field_op(lambda d, dims, x, o: _L().oracle_recompose_adjoint_c(d, dims, _p(co, C.c_double), x, o),
+                     g_u, g_u.shape, "recompose_adjoint")
 
 
-def decompose_adjoint(g_coef, shape):
-    return _field_op(_L().oracle_decompose_adjoint, g_coef, shape,
-                     "decompose_adjoint").reshape(shape)
+def decompose_adjoint(g_coef, shape, coords=None):
+    co = _coords(shape, coords)
+    if co is None:
+        return _field_op(_L().oracle_decompose_adjoint, g_coef, shape, "decompose_adjoint").reshape(shape)
+    return _field_op(lambda d, dims, x, o: _L().oracle_decompose_adjoint_c(d, dims, _p(co, C.c_double), x, o),
+                     g_coef, shape, "decompose_adjoint").reshape(shape)
 
 
 def correction_norms(shape, coords=None):

@@ -431,8 +431,13 @@ int oracle_recompose_c(int d, const size_t *n, const double *coords, const doubl
  *   g_{v_{l-1}} = P^T g_l,   g_{c_l} = g_l|new - S^T P^T g_l. */
 int oracle_recompose_adjoint(int d, const size_t *n, const double *g_u, double *g_coef)
 {
+    return oracle_recompose_adjoint_c(d, n, NULL, g_u, g_coef);
+}
+
+int oracle_recompose_adjoint_c(int d, const size_t *n, const double *coords, const double *g_u, double *g_coef)
+{
     ohier H;
-    if (ohier_build(&H, d, n, NULL)) { ohier_free(&H); return -1; }
+    if (ohier_build(&H, d, n, coords)) { ohier_free(&H); return -1; }
     size_t N = ohier_count(&H, H.L);
     double *g = (double *)malloc(N * sizeof(double));
     memcpy(g, g_u, N * sizeof(double));
@@ -477,8 +482,13 @@ int oracle_recompose_adjoint(int d, const size_t *n, const double *g_u, double *
  *   g_{v_l} = E_new h + E_kept (g_{v_{l-1}} - P^T E_new h). */
 int oracle_decompose_adjoint(int d, const size_t *n, const double *g_coef, double *g_u)
 {
+    return oracle_decompose_adjoint_c(d, n, NULL, g_coef, g_u);
+}
+
+int oracle_decompose_adjoint_c(int d, const size_t *n, const double *coords, const double *g_coef, double *g_u)
+{
     ohier H;
-    if (ohier_build(&H, d, n, NULL)) { ohier_free(&H); return -1; }
+    if (ohier_build(&H, d, n, coords)) { ohier_free(&H); return -1; }
     size_t N0 = ohier_count(&H, 0);
     double *gv = (double *)malloc(N0 * sizeof(double));
     memcpy(gv, g_coef, N0 * sizeof(double));

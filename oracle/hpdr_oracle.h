@@ -38,6 +38,8 @@ int oracle_decompose(int d, const size_t *n, const double *u, double *coef);
 int oracle_decompose_c(int d, const size_t *n, const double *coords, const double *u, double *coef);
 int oracle_recompose_c(int d, const size_t *n, const double *coords, const double *coef, double *u);
 int oracle_correction_norms_c(int d, const size_t *n, const double *coords, double *c);
+int oracle_recompose_adjoint_c(int d, const size_t *n, const double *coords, const double *g_u, double *g_coef);
+int oracle_decompose_adjoint_c(int d, const size_t *n, const double *coords, const double *g_coef, double *g_u);
 int oracle_bins_c(int d, const size_t *n, const double *coords, double tau_abs, double norm_inf, double eps,
                   double *q);
 /* Statistical L2 bins (mode 2; the paper states no formula, see

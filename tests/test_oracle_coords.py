@@ -142,3 +142,28 @@ def test_rejects_bad_coordinates():
         oracle.decompose(u, coords=[np.arange(5.0), np.array([0.0, 1.0, np.nan, 2.0])])
     with pytest.raises(ValueError):
         oracle.decompose(u, coords=[np.arange(5.0)])
+
+
+@pytest.mark.parametrize("shape", [(9,), (7, 6), (5, 4, 6), (17, 9)], ids=str)
+def test_adjoints_with_coordinates(shape):
+    """The transposes on a non-uniform grid: dot-product identities against
+    the coordinate recomposition and decomposition, and the explicit
+    transpose of the recomposition matrix on small grids."""
+    rng = np.random.default_rng(len(shape) * 7 + shape[0])
+    co = _rand_coords(rng, shape)
+    N = int(np.prod(shape))
+    c, g = rng.standard_normal(N), rng.standard_normal(shape)
+    lhs = float(np.sum(oracle.recompose(c, shape, coords=co) * g))
+    rhs = float(np.dot(c, oracle.recompose_adjoint(g, coords=co)))
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+    u, gc = rng.standard_normal(shape), rng.standard_normal(N)
+    lhs = float(np.dot(oracle.decompose(u, coords=co), gc))
+    rhs = float(np.sum(u * oracle.decompose_adjoint(gc, shape, coords=co)))
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+    if N <= 200:
+        R = np.stack([oracle.recompose(np.eye(N)[i], shape, coords=co).reshape(-1) for i in range(N)], axis=1)
+        Rt = np.stack([oracle.recompose_adjoint(np.eye(N)[i].reshape(shape), coords=co) for i in range(N)], axis=1)
+        assert np.allclose(Rt, R.T, atol=1e-12)
+    # unit spacing given explicitly is the plain transpose
+    unit = [np.arange(n, dtype=float) for n in shape]
+    assert np.allclose(oracle.recompose_adjoint(g, coords=unit), oracle.recompose_adjoint(g), atol=1e-13)
