@@ -182,6 +182,14 @@ hpdr_status hpdr_recompose_adjoint(hpdr_ctx *ctx, const void *d_grad_u, void *d_
 hpdr_status hpdr_decompose_adjoint(hpdr_ctx *ctx, const void *d_grad_coef, void *d_grad_u,
                                    hpdr_dtype dtype, int ndim, const size_t *dims, void *stream);
 
+/* The two transposes on a grid with the given node coordinates (host array,
+ * see Common conventions; NULL = unit spacing): the transposes of
+ * hpdr_recompose_coords and hpdr_decompose_coords on the same grid. */
+hpdr_status hpdr_recompose_adjoint_coords(hpdr_ctx *ctx, const void *d_grad_u, void *d_grad_coef, hpdr_dtype dtype,
+                                          int ndim, const size_t *dims, const double *coords, void *stream);
+hpdr_status hpdr_decompose_adjoint_coords(hpdr_ctx *ctx, const void *d_grad_coef, void *d_grad_u, hpdr_dtype dtype,
+                                          int ndim, const size_t *dims, const double *coords, void *stream);
+
 /* Huffman stage alone (Alg. 2) on a device array of N uint16 symbols < D:
  * histogram, code lengths (two-queue rule, leaves sorted by (frequency,
  * symbol)), canonical codewords, encoding.  Outputs (device): d_lengths[D]

@@ -1360,10 +1360,16 @@ hpdr_status hpdr_huffman_decode(hpdr_ctx *ctx, const uint32_t *d_words, uint64_t
 hpdr_status hpdr_recompose_adjoint(hpdr_ctx *ctx, const void *d_grad_u, void *d_grad_coef,
                                    hpdr_dtype dtype, int ndim, const size_t *dims, void *stream)
 {
+    return hpdr_recompose_adjoint_coords(ctx, d_grad_u, d_grad_coef, dtype, ndim, dims, nullptr, stream);
+}
+
+hpdr_status hpdr_recompose_adjoint_coords(hpdr_ctx *ctx, const void *d_grad_u, void *d_grad_coef, hpdr_dtype dtype,
+                                          int ndim, const size_t *dims, const double *coords, void *stream)
+{
     if (!ctx || !d_grad_u || !d_grad_coef || (dtype != HPDR_F32 && dtype != HPDR_F64)) return HPDR_ERR_ARG;
     DevGuard g(ctx->device);
     Plan *P;
-    hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P);
+    hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P, coords);
     if (st != HPDR_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if (dtype == HPDR_F32)
@@ -1374,10 +1380,16 @@ hpdr_status hpdr_recompose_adjoint(hpdr_ctx *ctx, const void *d_grad_u, void *d_
 hpdr_status hpdr_decompose_adjoint(hpdr_ctx *ctx, const void *d_grad_coef, void *d_grad_u,
                                    hpdr_dtype dtype, int ndim, const size_t *dims, void *stream)
 {
+    return hpdr_decompose_adjoint_coords(ctx, d_grad_coef, d_grad_u, dtype, ndim, dims, nullptr, stream);
+}
+
+hpdr_status hpdr_decompose_adjoint_coords(hpdr_ctx *ctx, const void *d_grad_coef, void *d_grad_u, hpdr_dtype dtype,
+                                          int ndim, const size_t *dims, const double *coords, void *stream)
+{
     if (!ctx || !d_grad_u || !d_grad_coef || (dtype != HPDR_F32 && dtype != HPDR_F64)) return HPDR_ERR_ARG;
     DevGuard g(ctx->device);
     Plan *P;
-    hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P);
+    hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P, coords);
     if (st != HPDR_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if (dtype == HPDR_F32)

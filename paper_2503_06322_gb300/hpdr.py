@@ -79,6 +79,8 @@ def lib():
                                      C.c_int, C.POINTER(Config), vp, C.c_size_t, sz, vp],
             "hpdr_decompose_coords": [vp, vp, vp, C.c_int, C.c_int, sz, C.POINTER(C.c_double), vp],
             "hpdr_recompose_coords": [vp, vp, vp, C.c_int, C.c_int, sz, C.POINTER(C.c_double), vp],
+            "hpdr_recompose_adjoint_coords": [vp, vp, vp, C.c_int, C.c_int, sz, C.POINTER(C.c_double), vp],
+            "hpdr_decompose_adjoint_coords": [vp, vp, vp, C.c_int, C.c_int, sz, C.POINTER(C.c_double), vp],
             "hpdr_recompose_adjoint": [vp, vp, vp, C.c_int, C.c_int, sz, vp],
             "hpdr_decompose_adjoint": [vp, vp, vp, C.c_int, C.c_int, sz, vp],
             "hpdr_huffman_encode": [vp, vp, C.c_uint64, C.c_uint32, C.c_uint32, vp, vp, vp,
@@ -485,17 +487,21 @@ def hpdr_recompose(coef, shape, out=None, stream=None, coords=None):
     return _field_call("hpdr_recompose", coef, out, shape, stream)
 
 
-def hpdr_recompose_adjoint(grad_u, out=None, stream=None):
+def hpdr_recompose_adjoint(grad_u, out=None, stream=None, coords=None):
     _dev_tensor(grad_u, "grad_u")
     if out is None:
         out = torch.empty(grad_u.numel(), dtype=grad_u.dtype, device=grad_u.device)
+    if coords is not None:
+        return _coords_call("hpdr_recompose_adjoint_coords", grad_u, out, grad_u.shape, coords, stream)
     return _field_call("hpdr_recompose_adjoint", grad_u, out, grad_u.shape, stream)
 
 
-def hpdr_decompose_adjoint(grad_coef, shape, out=None, stream=None):
+def hpdr_decompose_adjoint(grad_coef, shape, out=None, stream=None, coords=None):
     _dev_tensor(grad_coef, "grad_coef")
     if out is None:
         out = torch.empty(tuple(shape), dtype=grad_coef.dtype, device=grad_coef.device)
+    if coords is not None:
+        return _coords_call("hpdr_decompose_adjoint_coords", grad_coef, out, shape, coords, stream)
     return _field_call("hpdr_decompose_adjoint", grad_coef, out, shape, stream)
 
 

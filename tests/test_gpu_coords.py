@@ -134,3 +134,21 @@ def test_bad_coordinates_are_rejected(H):
             H.hpdr_compress(u, 1e-3, coords=co)
     with pytest.raises(ValueError):
         H.hpdr_decompose(u, coords=[np.arange(5.0)])
+
+
+@pytest.mark.parametrize("shape", [(33,), (65, 33), (17, 9, 33), (40, 30, 20)], ids=str)
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_adjoints_parity(oracle, H, shape, dtype):
+    """Both transposes on a non-uniform grid against the oracle's."""
+    from paper_2503_06322_gb300 import fields
+    co = fields.node_coords(shape, 31)
+    rng = np.random.default_rng(32)
+    g = rng.standard_normal(shape).astype(dtype)
+    got = H.hpdr_recompose_adjoint(torch.from_numpy(g).cuda(), coords=co).cpu().numpy().astype(np.float64)
+    ref = oracle.recompose_adjoint(g.astype(np.float64), coords=co)
+    tol = 1e-5 if dtype == np.float32 else 1e-12
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+    gc = rng.standard_normal(int(np.prod(shape))).astype(dtype)
+    got = H.hpdr_decompose_adjoint(torch.from_numpy(gc).cuda(), shape, coords=co).cpu().numpy().astype(np.float64)
+    ref = oracle.decompose_adjoint(gc.astype(np.float64), shape, coords=co)
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
