@@ -106,6 +106,14 @@ def _p(a, ct):
     return a.ctypes.data_as(C.POINTER(ct))
 
 
+def _zdims(shape):
+    """dims of a fixed-rate ZFP field: 1..3 sizes, each >= 1"""
+    d = len(shape)
+    if not 1 <= d <= 3 or any(int(s) < 1 for s in shape):
+        raise ValueError("dims must be 1..3 sizes, each >= 1: %r" % (shape,))
+    return d, (C.c_size_t * 3)(*[int(s) for s in shape] + [1] * (3 - d))
+
+
 def _dims(shape):
     d = len(shape)
     if not 1 <= d <= 3 or any(int(s) < 2 for s in shape):
@@ -396,7 +404,7 @@ def decompress(buf):
 # ---- fixed-rate ZFP (Alg. 3) ---------------------------------------------
 
 def zfp_bound(shape, rate, dtype=DTYPE_F32):
-    d, dims = _dims(shape)
+    d, dims = _zdims(shape)
     return int(_L().oracle_zfp_bound(d, dims, int(dtype), int(rate)))
 
 
@@ -405,7 +413,7 @@ def zfp_compress(u, rate, dtype=None):
     u = np.asarray(u)
     if dtype is None:
         dtype = DTYPE_F32 if u.dtype == np.float32 else DTYPE_F64
-    d, dims = _dims(u.shape)
+    d, dims = _zdims(u.shape)
     x = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
     cap = zfp_bound(u.shape, rate, dtype)
     if cap == 0:

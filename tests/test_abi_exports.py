@@ -56,3 +56,23 @@ def test_host_only_entries(lib):
     assert 128 + 65 ** 3 * 13 // 8 <= b32 <= b64 < 64 * 65 ** 3
     bad = (C.c_size_t * 3)(65, 1, 65)
     assert lib.hpdr_compress_bound(3, bad, 0, None) == 0
+
+
+def test_zfp_bound_matches_the_oracle(lib):
+    """The fixed-rate container size is exact and host-only: it must equal the
+    oracle's for every dimension count, type and rate, and both must reject
+    the same rates (rate * 4^d not a multiple of 32, or out of 1..256)."""
+    import oracle
+    lib.hpdr_zfp_bound.restype = C.c_size_t
+    lib.hpdr_zfp_bound.argtypes = [C.c_int, C.POINTER(C.c_size_t), C.c_int, C.c_uint32]
+    for shape in [(1,), (7,), (1000,), (5, 9), (65, 33), (1, 1, 1), (33, 17, 9), (513, 513, 513)]:
+        dims = (C.c_size_t * 3)(*(list(shape) + [1] * (3 - len(shape))))
+        for dtype in (0, 1):
+            for rate in (1, 2, 3, 4, 7, 8, 12, 16, 64, 136, 256, 257, 0):
+                got = lib.hpdr_zfp_bound(len(shape), dims, dtype, rate)
+                assert got == oracle.zfp_bound(shape, rate, dtype), (shape, dtype, rate)
+                if got:
+                    nb = 1
+                    for s in shape:
+                        nb *= (s + 3) // 4
+                    assert got == 64 + nb * rate * 4 ** len(shape) // 8
