@@ -326,8 +326,9 @@ hpdr_status hpdr_lossless_inspect(const void *in, size_t in_bytes, int *key_byte
  *   aligned; *out_bytes = hpdr_zfp_bound(...).  Does not synchronize.
  *   Errors: HPDR_ERR_ARG, HPDR_ERR_CAPACITY, HPDR_ERR_CUDA.  Non-finite
  *   values are not supported (their blocks decode to unspecified values).
- * hpdr_zfp_decompress: reads the header back (synchronizes `stream` once),
- *   then decodes into d_out (out_capacity bytes).  Errors: HPDR_ERR_FORMAT,
+ * hpdr_zfp_decompress: d_in (16-byte aligned) holds in_bytes of a container;
+ *   reads the header back (synchronizes `stream` once), then decodes into
+ *   d_out (out_capacity bytes, aligned to the element size).  Errors: HPDR_ERR_FORMAT,
  *   HPDR_ERR_CAPACITY, HPDR_ERR_ARG, HPDR_ERR_CUDA.
  * hpdr_zfp_inspect: dtype, ndim, dims (3 slots) and rate of a container in
  *   host or device memory. */
