@@ -8,8 +8,9 @@
 // block held in registers (all loops over the 4^d values unrolled) and its
 // bits written straight to its own words.
 //
-// The details the paper leaves open are read as follows (the byte format is
-// the one the header below documents):
+// The details the paper leaves open are read as follows (the container, a
+// 64-byte header and the block words, is documented with hpdr_zfp_compress
+// in include/hpdr.h):
 //   blocks      row-major over ceil(n_k / 4) blocks per dimension, values in
 //               a block row-major (last index fastest); positions past the
 //               array edge repeat the last in-range value of their dimension,
@@ -34,7 +35,6 @@
 //               bits from n up to and including the next 1); the block stops
 //               where its budget ends, the rest of its bits zero.  Bits fill
 //               32-bit words least significant first.
-#include <climits>
 #include <cstdint>
 #include <cstring>
 #include <cmath>
