@@ -40,7 +40,7 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-to-host leg")
-    ap.add_argument("--cpu-planes", type=int, default=65,
+    ap.add_argument("--cpu-planes", type=int, default=257,
                     help="planes of the field in the CPU-baseline sample")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the 257^3 adjoint leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-field batched leg")
