@@ -411,22 +411,25 @@ hpdr_status hpdr_compress_host_adaptive(hpdr_ctx *ctx, const void *h_in, hpdr_dt
                                         size_t c_limit, void *h_out, size_t out_capacity, size_t *out_bytes);
 
 /* Decomposition for callers that cannot allocate device memory on their call
- * path -- for example code running while a stream is captured into a CUDA
- * graph (allocation calls are not permitted in a global-mode capture), or a
- * service that reserves all device memory at start-up.  The paper has no
- * counterpart: this is a variant of hpdr_decompose that takes no context and
- * calls no cudaMalloc, cudaFree or other allocating routine.  Its plan tables
- * and level buffers live in one fixed 16 MiB device array inside the library
- * (every GPU that loads the library holds it until the process exits).
+ * path -- for example a service that hands all device memory to its own pool
+ * at start-up (a later cudaMalloc fails or is forbidden), or a latency-bound
+ * loop that cannot pay for cudaMalloc/cudaFree, which may synchronize the
+ * device.  The paper has no counterpart: this is a variant of hpdr_decompose
+ * that takes no context and calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Its plan tables and level buffers live in one fixed
+ * 16 MiB device array inside the library (every GPU that loads the library
+ * holds it until the process exits).
  *   d_u, d_coef, dtype, ndim, dims, stream: as for hpdr_decompose, on the
  *   current device; d_u 16-byte aligned.
  * Limit: the tables plus three arrays of the first coarse level (N_{L-1}
  * elements each) must fit in 16 MiB -- FP32 fields up to about 213^3 nodes;
  * larger fields return HPDR_ERR_CAPACITY before any work is queued.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Every
- * call shares the one array and overwrites it: calls that overlap on the GPU
- * (on different streams, or from several host threads) race. */
+ * device current); make that first call before any stream capture.  The
+ * tables are copied from a host image that the library keeps, per dtype and
+ * shape, until the process exits.  Every call shares the one array and
+ * overwrites it: calls that overlap on the GPU (on different streams, or
+ * from several host threads) race. */
 hpdr_status hpdr_decompose_noalloc(const void *d_u, void *d_coef, hpdr_dtype dtype, int ndim,
                                    const size_t *dims, void *stream);
 

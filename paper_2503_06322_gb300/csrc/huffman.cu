@@ -1491,10 +1491,9 @@ hist_wide_kernel(const uint16_t *sym, unsigned long long N, unsigned D, unsigned
     }
 }
 
-bool g_attr_done = false;
-cudaError_t set_attrs()
+PerDeviceOnce g_attr_done;
+cudaError_t set_attrs_now()
 {
-    if (g_attr_done) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kSmemKeys * 8);
     if (e == cudaSuccess)
@@ -1510,9 +1509,9 @@ cudaError_t set_attrs()
         e = cudaFuncSetAttribute(enc_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e == cudaSuccess) g_attr_done = true;
     return e;
 }
+cudaError_t set_attrs() { return once_per_device(g_attr_done, set_attrs_now); }
 
 }  // namespace
 
@@ -1621,14 +1620,14 @@ cudaError_t launch_header(const HeaderArgs &h, const uint8_t *len, Scalars *sc, 
 cudaError_t launch_histogram(const uint16_t *sym, unsigned long long N, unsigned D,
                              unsigned long long *hist, unsigned *status, cudaStream_t s)
 {
-    static bool attr = false;
-    if (!attr) {
+    static PerDeviceOnce attr;
+    cudaError_t ea = once_per_device(attr, [] {
         cudaError_t e = cudaFuncSetAttribute(hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(hist_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536 * 2);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+        return e;
+    });
+    if (ea != cudaSuccess) return ea;
     if (D <= 16384) {
         hist_kernel<<<152 * 4, 256, D * 4, s>>>(sym, N, D, hist, status);
     } else {

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <atomic>
 #include <vector>
 #include <map>
 #include <string>
@@ -247,6 +248,34 @@ int levels_of(int ndim, const size_t *dims);
 void destroy_stream_res(hpdr_ctx *ctx);
 
 inline hpdr_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HPDR_OK : HPDR_ERR_CUDA; }
+
+inline int current_device()
+{
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess) { cudaGetLastError(); d = 0; }
+    return d;
+}
+
+// A set-up step that must run once on every device the process uses (a
+// kernel attribute such as its dynamic shared-memory limit belongs to one
+// device's context).  Devices 0..63 keep a bit each; higher ordinals run the
+// step on every call.  Thread-safe: a step may run twice when two threads race
+// on its first call, which is harmless for idempotent steps.
+struct PerDeviceOnce {
+    std::atomic<unsigned long long> done{0};
+};
+template <typename F>
+cudaError_t once_per_device(PerDeviceOnce &o, F step)
+{
+    const int dev = current_device();
+    const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (o.done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    const cudaError_t e = step();
+    if (e == cudaSuccess && bit) o.done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+// Number of SMs of the current device (cached per device).
+int sm_count();
 
 }  // namespace hpdr
 

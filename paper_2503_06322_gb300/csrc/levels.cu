@@ -324,12 +324,18 @@ restrict_kernel(RestrictArgs<T> a, int seg_len)
         bool ok = true;
         if (STAGED) {
             const int need = min(p0 + 1, hi0);
-            while (waited < need) { waited++; ok = ok && wait_plane(waited); }
+            while (ok && waited < need) {
+                if (wait_plane(waited + 1)) waited++;
+                else ok = false;
+            }
         }
         if (__syncthreads_or(!ok)) {
-            // give up: wait (bounded) for the copies still in flight, then leave
+            // give up: wait (bounded) for every plane issued so far that this
+            // thread has not seen complete, the one that timed out included,
+            // so that no bulk copy still targets shared memory, then leave
             if (tid == 0) atomicExch(a.status, (unsigned)DS_TIMEOUT);
-            for (int p = waited + 1; p <= hi0 && p < p0 + NST; p++) wait_plane(p);
+            const int last_issued = min(hi0, p0 + NST - 2);
+            for (int p = waited + 1; p <= last_issued; p++) wait_plane(p);
             return;
         }
         const bool f0 = !kept_pos(m0, p0);
@@ -710,10 +716,15 @@ decomp_level_kernel(RestrictArgs<T> a, int seg_len)
         const int s0 = (p0 - lo0) % NST;
         bool ok = true;
         const int need = min(p0 + 1, hi0);
-        while (waited < need) { waited++; ok = ok && wait_plane(waited); }
+        while (ok && waited < need) {
+            if (wait_plane(waited + 1)) waited++;
+            else ok = false;
+        }
         if (__syncthreads_or(!ok)) {
+            // drain every issued plane not seen complete (see restrict_kernel)
             if (tid == 0) atomicExch(a.status, (unsigned)DS_TIMEOUT);
-            for (int p = waited + 1; p <= hi0 && p < p0 + NST; p++) wait_plane(p);
+            const int last_issued = min(hi0, p0 + NST - 2);
+            for (int p = waited + 1; p <= last_issued; p++) wait_plane(p);
             return;
         }
         // every warp is done with plane p0 - 1: its stage takes plane p0 + NST - 1
@@ -843,13 +854,7 @@ size_t decomp_smem(Sink sink, unsigned int D)
 // dim-0 halo (two fine planes each side of a segment) small.
 int choose_segment(int mc0, long long tiles, int per_sm)
 {
-    static int nsm = 0;
-    if (!nsm) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
-            nsm = 152;
-    }
+    const int nsm = sm_count();
     const long long slots = (long long)nsm * std::max(1, per_sm);
     double best = -1.0;
     int best_seg = mc0;
@@ -880,13 +885,12 @@ cudaError_t launch_decomp_t(const RestrictArgs<T> &a, cudaStream_t s)
     const int mc0 = a.g.dim[0].mc, mc1 = a.g.dim[1].mc, mc2 = a.g.dim[2].mc;
     const int gx = (mc2 + TT2 - 1) / TT2, gy = (mc1 + TT1 - 1) / TT1;
     size_t sm = decomp_smem<T>((Sink)SINK, SINK == (int)Sink::QUANT ? a.qo.D : 0);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(decomp_level_kernel<T, SINK>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static PerDeviceOnce attr;
+    cudaError_t e = once_per_device(attr, [] {
+        return cudaFuncSetAttribute(decomp_level_kernel<T, SINK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    160 * 1024);
+    });
+    if (e != cudaSuccess) return e;
     const int seg = choose_segment(mc0, (long long)gx * gy, resident_ctas(decomp_level_kernel<T, SINK>, sm));
     const int gz = (mc0 + seg - 1) / seg;
     decomp_level_kernel<T, SINK><<<dim3(gx, gy, gz), RTHREADS, sm, s>>>(a, seg);
@@ -1582,13 +1586,12 @@ cudaError_t launch_restrict_t(const RestrictArgs<T> &a, cudaStream_t s)
     const int mc0 = a.g.dim[0].mc, mc1 = a.g.dim[1].mc, mc2 = a.g.dim[2].mc;
     const int gx = (mc2 + TT2 - 1) / TT2, gy = (mc1 + TT1 - 1) / TT1;
     size_t sm = restrict_smem<T>((WSrc)SRC, (Sink)SINK, SINK == (int)Sink::QUANT ? a.qo.D : 0);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(restrict_kernel<T, SRC, SINK>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static PerDeviceOnce attr;
+    cudaError_t e = once_per_device(attr, [] {
+        return cudaFuncSetAttribute(restrict_kernel<T, SRC, SINK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    160 * 1024);
+    });
+    if (e != cudaSuccess) return e;
     const int seg = choose_segment(mc0, (long long)gx * gy, resident_ctas(restrict_kernel<T, SRC, SINK>, sm));
     const int gz = (mc0 + seg - 1) / seg;
     restrict_kernel<T, SRC, SINK><<<dim3(gx, gy, gz), RTHREADS, sm, s>>>(a, seg);
@@ -1636,11 +1639,12 @@ cudaError_t launch_solves(const LevelGeom<T> &g, T *b, T *vc, int sign, cudaStre
             const long long outer = (k == 0) ? c1 : c0;
             const long long ostride = (k == 0) ? c2 : c1 * c2;
             const int ninner = (int)c2;
-            static bool attr = false;
-            if (!attr) {
-                cudaFuncSetAttribute(solve_tile_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 164 * 1024);
-                attr = true;
-            }
+            static PerDeviceOnce attr;
+            cudaError_t ea = once_per_device(attr, [] {
+                return cudaFuncSetAttribute(solve_tile_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            164 * 1024);
+            });
+            if (ea != cudaSuccess) return ea;
             const long long grid = outer * ((ninner + 31) / 32);
             solve_tile_kernel<T><<<(unsigned)grid, 128, (size_t)d.mc * 35 * sizeof(T), s>>>(
                 b, d.mc, st, ostride, ninner, d.sub, d.cp, d.inv_den);
@@ -1663,11 +1667,12 @@ cudaError_t launch_solves(const LevelGeom<T> &g, T *b, T *vc, int sign, cudaStre
                 solve_strided_kernel<T><<<(unsigned)((nlines + 255) / 256), 256, 0, s>>>(
                     b, n, 1, nlines, d.sub, d.cp, d.inv_den, vc, sg);
             } else {
-                static bool attr = false;
-                if (!attr) {
-                    cudaFuncSetAttribute(solve_contig_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-                    attr = true;
-                }
+                static PerDeviceOnce attr;
+                cudaError_t ea = once_per_device(attr, [] {
+                    return cudaFuncSetAttribute(solve_contig_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                100 * 1024);
+                });
+                if (ea != cudaSuccess) return ea;
                 solve_contig_kernel<T><<<(unsigned)((nlines + rows - 1) / rows), 256,
                                          rows * rowbytes + 3 * (size_t)n * sizeof(T), s>>>(
                     b, n, nlines, rows, pitch, d.sub, d.cp, d.inv_den, vc, sg);
@@ -1768,13 +1773,12 @@ cudaError_t launch_coarse(int mode, const Plan *P, const LevelGeom<T> *geo, int 
     a.N0 = P->N[0];
     a.v_in = v_in; a.v_out = v_out; a.qo = qo; a.coef_out = coef_out; a.symin = symin; a.coef_in = coef_in;
     const size_t sm = coarse_smem_bytes<T>(geo[ls]);
-    static bool attr[4] = {false, false, false, false};
+    static PerDeviceOnce attr[4];
     auto go = [&](auto kern) -> cudaError_t {
-        if (!attr[mode]) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmem);
-            if (e != cudaSuccess) return e;
-            attr[mode] = true;
-        }
+        cudaError_t e = once_per_device(attr[mode], [&] {
+            return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmem);
+        });
+        if (e != cudaSuccess) return e;
         kern<<<1, kCoarseThreads, sm, s>>>(a);
         count_launch();
         return cudaGetLastError();

@@ -1,14 +1,18 @@
 // noalloc.cu -- multilevel decomposition without any device allocation.
 //
-// Some callers cannot allocate device memory on their call path: code that
-// runs while a stream is being captured into a CUDA graph (allocation calls
-// are not permitted during a global-mode capture), and services that reserve
-// all device memory at start-up and forbid allocations afterwards.  For them
+// Some callers cannot allocate device memory on their call path: services
+// that hand all device memory to their own pool at start-up (a later
+// cudaMalloc would fail, or is forbidden by the service's rules), and
+// latency-critical loops that cannot afford cudaMalloc/cudaFree, which may
+// synchronize the device and take unbounded time.  For them
 // hpdr_decompose_noalloc runs the same kernels as hpdr_decompose, with the
 // plan tables and the level buffers placed in one fixed file-scope device
 // array instead of a context workspace.
 #include <cstring>
+#include <map>
+#include <memory>
 #include <mutex>
+#include <string>
 #include "internal.cuh"
 #include "levels.cuh"
 
@@ -39,6 +43,33 @@ hpdr_status scratch_address(int dev, void **out)
 }
 
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Host images of the plan tables, one per (dtype, shape), kept until the
+// process exits.  The tables reach the device by an asynchronous copy from
+// this image, so the image must outlive every copy queued from it; a copy
+// from pageable memory may still read its source after the call returns.
+struct CachedPlan {
+    hpdr::Plan P;
+    hpdr::PlanImage img;
+};
+std::map<std::string, std::unique_ptr<CachedPlan>> g_plan_cache;
+std::mutex g_plan_mutex;
+
+hpdr_status cached_plan(int ndim, const size_t *dims, bool f64, const CachedPlan **out)
+{
+    std::string key = f64 ? "d" : "f";
+    for (int k = 0; k < ndim && k < 3; k++) key += ":" + std::to_string(dims[k]);
+    std::lock_guard<std::mutex> lk(g_plan_mutex);
+    auto it = g_plan_cache.find(key);
+    if (it == g_plan_cache.end()) {
+        std::unique_ptr<CachedPlan> c(new CachedPlan());
+        const hpdr_status st = hpdr::plan_image(ndim, dims, f64, &c->P, &c->img);
+        if (st != HPDR_OK) return st;
+        it = g_plan_cache.emplace(key, std::move(c)).first;
+    }
+    *out = it->second.get();
+    return HPDR_OK;
+}
 
 template <typename T> const hpdr::LevelGeom<T> &geom_of(const hpdr::Plan &P, int l);
 template <> const hpdr::LevelGeom<float> &geom_of<float>(const hpdr::Plan &P, int l) { return P.gf[l]; }
@@ -105,17 +136,18 @@ extern "C" hpdr_status hpdr_decompose_noalloc(const void *d_u, void *d_coef, hpd
     void *scratch = nullptr;
     hpdr_status st = scratch_address(dev, &scratch);
     if (st != HPDR_OK) return st;
-    Plan P;
-    PlanImage img;
     const bool f64 = dtype == HPDR_F64;
-    st = plan_image(ndim, dims, f64, &P, &img);
+    const CachedPlan *cp = nullptr;
+    st = cached_plan(ndim, dims, f64, &cp);
     if (st != HPDR_OK) return st;
+    const PlanImage &img = cp->img;
+    Plan P = cp->P;
     const size_t esz = f64 ? 8 : 4;
     const size_t n1 = (size_t)(P.L >= 1 ? P.N[P.L - 1] : 1);
     const size_t need = up256(img.bytes.size()) + up256(sizeof(Scalars)) + 3 * up256(n1 * esz);
     if (need > kScratchBytes) return HPDR_ERR_CAPACITY;
     cudaStream_t s = (cudaStream_t)stream;
-    // pageable source: the call returns once the bytes are staged, so the host image may go
+    // the source is the cached image, alive until exit
     if (cudaMemcpyAsync(scratch, img.bytes.data(), img.bytes.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return HPDR_ERR_CUDA;
     bind_plan(&P, img, scratch);

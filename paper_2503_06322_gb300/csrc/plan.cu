@@ -17,6 +17,23 @@
 
 namespace hpdr {
 
+int sm_count()
+{
+    static std::atomic<int> cache[64];
+    const int dev = current_device();
+    if (dev >= 0 && dev < 64) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = 152;
+    }
+    if (dev >= 0 && dev < 64) cache[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
+
 static int coarsen(int m) { return (m % 2) ? (m + 1) / 2 : m / 2 + 1; }
 
 int levels_of(int ndim, const size_t *dims)

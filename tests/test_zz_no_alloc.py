@@ -1,9 +1,12 @@
 """The allocation-free decomposition entry point.
 
-Some callers cannot allocate device memory on their call path (a stream being
-captured into a CUDA graph, services that reserve all memory at start-up);
+Some callers cannot allocate device memory on their call path: services that
+hand all device memory to their own pool at start-up, and latency-bound loops
+that cannot pay for cudaMalloc/cudaFree (which may synchronize the device).
 hpdr_decompose_noalloc serves them from a fixed device array inside the
-library.  This file is collected last so that, if it fails, a run stopping at
+library.  Its output is checked against hpdr_decompose (the entry point that
+allocates) and against the FP64 oracle, on two calls in a row, because the
+array keeps the previous call's contents.  This file is collected last so that, if it fails, a run stopping at
 the first failure has already run every other test.
 """
 import ctypes as C
@@ -27,7 +30,7 @@ def _call(lib, u, out):
 
 @pytest.mark.parametrize("shape", [(65, 65, 65), (129, 129), (100, 7, 5), (1000,)], ids=str)
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
-def test_noalloc_matches_decompose_twice(shape, dtype):
+def test_noalloc_matches_decompose_twice(oracle, shape, dtype):
     from paper_2503_06322_gb300 import fields, hpdr
     lib = hpdr.lib()
     dev = torch.device("cuda:0")
@@ -38,12 +41,32 @@ def test_noalloc_matches_decompose_twice(shape, dtype):
         u = fields.powerlaw_field(shape, seed=9, dtype=np_dtype)
     ut = torch.from_numpy(u).to(dev)
     ref = hpdr.hpdr_decompose(ut)
+    oref = oracle.decompose(u.astype(np.float64))
     tol = 1e-5 if dtype == torch.float32 else 1e-12
     for _ in range(2):                       # the array keeps the last call's contents
         out = torch.full_like(ref, float("nan"))
         assert _call(lib, ut, out) == 0
         assert torch.isfinite(out).all()
         assert (out - ref).abs().max().item() <= tol * ref.abs().max().item()
+        got = out.cpu().numpy().astype(np.float64)
+        assert np.abs(got - oref).max() <= tol * np.abs(oref).max()
+
+
+def test_noalloc_alternating_shapes(oracle):
+    """Calls of two shapes in turn: each call stages its own tables."""
+    from paper_2503_06322_gb300 import fields, hpdr
+    lib = hpdr.lib()
+    dev = torch.device("cuda:0")
+    cases = []
+    for shape in [(33, 17, 9), (65, 65)]:
+        u = fields.powerlaw_field(shape, seed=4, dtype=np.float32)
+        cases.append((torch.from_numpy(u).to(dev), oracle.decompose(u.astype(np.float64))))
+    for _ in range(2):
+        for ut, oref in cases:
+            out = torch.full((ut.numel(),), float("nan"), device=dev)
+            assert _call(lib, ut, out) == 0
+            got = out.cpu().numpy().astype(np.float64)
+            assert np.abs(got - oref).max() <= 1e-5 * np.abs(oref).max()
 
 
 def test_noalloc_rejects_fields_beyond_its_array():
