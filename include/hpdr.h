@@ -445,6 +445,18 @@ hpdr_status hpdr_profile_enable(hpdr_ctx *ctx, int on);
 int hpdr_profile_read(hpdr_ctx *ctx, const char **names, double *ms, long long *count, int cap);
 unsigned long long hpdr_launch_count(void);
 
+/* Failure detection (test support; not part of the reduction).  The plane
+ * pipelines of the level kernels wait on mbarriers for their bulk copies;
+ * every such wait gives up after a number of polls, the kernel records
+ * DS_TIMEOUT, waits (with its own, long bound) for the copies it has in
+ * flight and returns, and the call returns HPDR_ERR_TIMEOUT.  This sets the
+ * number of polls for every later launch in the process (polls >= 0; a
+ * negative value only reads it) and returns the previous value.  The
+ * default, 2^20, is never reached by a healthy GPU; 0 makes the first wait
+ * give up at once, which is how the tests make a wait run out without
+ * stalling the GPU.  Not thread-safe against concurrent launches. */
+int hpdr_debug_set_wait_limit(int polls);
+
 /* Static description of a status code. */
 const char *hpdr_status_string(hpdr_status status);
 

@@ -12,8 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhpdr.so")
-SOURCES = ["plan.cu", "levels.cu", "huffman.cu", "adjoint.cu", "api.cu", "streamed.cu", "noalloc.cu", "zfp.cu"]
-HEADERS = ["internal.cuh", "levels.cuh", "huffman.cuh"]
+SOURCES = ["plan.cu", "levels.cu", "decomp.cu", "huffman.cu", "adjoint.cu", "api.cu", "streamed.cu", "noalloc.cu", "zfp.cu"]
+HEADERS = ["internal.cuh", "levels.cuh", "levels_dev.cuh", "huffman.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-Wall"]

@@ -1437,6 +1437,13 @@ int hpdr_profile_read(hpdr_ctx *ctx, const char **names, double *ms, long long *
 
 unsigned long long hpdr_launch_count(void) { return g_launches; }
 
+int hpdr_debug_set_wait_limit(int polls)
+{
+    const int prev = g_wait_limit;
+    if (polls >= 0) g_wait_limit = polls;
+    return prev;
+}
+
 hpdr_status hpdr_compress_batched(hpdr_ctx *ctx, int nfields, const hpdr_field *fields, const hpdr_config *cfg,
                                   void *d_out, size_t out_capacity, size_t *out_offsets, size_t *out_sizes,
                                   void *stream)

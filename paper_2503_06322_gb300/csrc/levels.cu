@@ -17,7 +17,7 @@
 // in a fixed order.
 #include <cfloat>
 #include <type_traits>
-#include "levels.cuh"
+#include "levels_dev.cuh"
 
 namespace hpdr {
 namespace {
@@ -27,107 +27,6 @@ constexpr int RR1 = 2 * TT1 + 4, RR2 = 2 * TT2 + 4;  // largest fine region
 constexpr int RTHREADS = 256;
 constexpr int kHistSmemMax = 16384;
 constexpr int kNormBlocks = 152 * 8;
-
-template <typename T>
-__device__ __forceinline__ long long quant_code(T x, T rho)
-{
-    // k = sign(x) floor(|x| rho + 1/2), every operation rounded in T
-    T ax = x < (T)0 ? -x : x;
-    T y = mul_rn(ax, rho);
-    T t = add_rn(y, (T)0.5);
-    long long k = (t < (T)1073741824) ? (long long)(int)floor(t) : (long long)floor(t);
-    return x < (T)0 ? -k : k;
-}
-
-template <typename T> __device__ __forceinline__ T rho_of(const Scalars *sc, int l);
-template <> __device__ __forceinline__ float rho_of<float>(const Scalars *sc, int l) { return sc->rho_f[l]; }
-template <> __device__ __forceinline__ double rho_of<double>(const Scalars *sc, int l) { return sc->rho_d[l]; }
-template <typename T> __device__ __forceinline__ T q_of(const Scalars *sc, int l);
-template <> __device__ __forceinline__ float q_of<float>(const Scalars *sc, int l) { return sc->q_f[l]; }
-template <> __device__ __forceinline__ double q_of<double>(const Scalars *sc, int l) { return sc->q[l]; }
-
-template <typename T>
-__device__ __forceinline__ long long stream_rank(const LevelGeom<T> &g, int p0, int p1, int p2)
-{
-    const long long m1 = g.dim[1].m, m2 = g.dim[2].m;
-    const long long mc1 = g.dim[1].mc, mc2 = g.dim[2].mc;
-    long long flat = ((long long)p0 * m1 + p1) * m2 + p2;
-    long long cr = (long long)kept_before(p0) * mc1 * mc2;
-    if (kept_pos(g.dim[0].m, p0)) {
-        cr += (long long)kept_before(p1) * mc2;
-        if (kept_pos((int)m1, p1)) cr += kept_before(p2);
-    }
-    return g.Nprev + flat - cr;
-}
-
-// Stream index of the new nodes of row (p0, p1) of level l:
-//   every node new (p0 or p1 new):        base + p2
-//   p0 and p1 kept (only odd p2 new):     base + (p2 - 1) / 2
-template <typename T>
-__device__ __forceinline__ long long row_base(const LevelGeom<T> &g, long long plane_base, bool k0,
-                                              int p1)
-{
-    const long long m2 = g.dim[2].m, mc2 = g.dim[2].mc;
-    return plane_base + (long long)p1 * m2 - (k0 ? (long long)kept_before(p1) * mc2 : 0LL);
-}
-template <typename T>
-__device__ __forceinline__ long long plane_base_of(const LevelGeom<T> &g, int p0)
-{
-    const long long m1 = g.dim[1].m, m2 = g.dim[2].m;
-    const long long mc1 = g.dim[1].mc, mc2 = g.dim[2].mc;
-    return g.Nprev + (long long)p0 * m1 * m2 - (long long)kept_before(p0) * mc1 * mc2;
-}
-
-// an escaped code (symbol 0) keeps its k at its stream position; the encoder
-// writes it into the bitstream after the escape's codeword, as zigzag(k) in
-// the container's payload width.  Returns the bit length of zigzag(k).
-__device__ __forceinline__ unsigned escape_store(const QuantOut &qo, long long si, long long k)
-{
-    if (k >= kEscMax || k <= -kEscMax) atomicExch(&qo.sc->status, (unsigned int)DS_ARG);
-    qo.esc[si] = k;
-    const unsigned long long z = k >= 0 ? 2ULL * (unsigned long long)k : 2ULL * (unsigned long long)(-(k + 1)) + 1ULL;
-    return 64u - (unsigned)__clzll((long long)z);
-}
-
-// quantize one coefficient into the symbol stream (+ block histogram / escapes)
-template <typename T>
-__device__ __forceinline__ void quant_emit(const QuantOut &qo, unsigned int *hs, bool smem_hist,
-                                           long long si, T w, T rho)
-{
-    long long k = quant_code(w, rho);
-    long long s = k + (long long)(qo.D / 2);
-    unsigned int sym;
-    if (s >= 1 && s <= (long long)qo.D - 1) {
-        sym = (unsigned int)s;
-    } else {
-        sym = 0;
-        atomicMax(&qo.sc->esc_w, escape_store(qo, si, k));
-    }
-    qo.sym[si] = (uint16_t)sym;
-    if (smem_hist) atomicAdd(&hs[sym], 1u);
-    else atomicAdd(&qo.hist[sym], 1ULL);
-}
-
-template <typename T>
-__device__ __forceinline__ T dequant_sym(const SymIn &si_, unsigned s, long long idx, T q)
-{
-    if (s != 0) return mul_rn((T)((int)s - (int)(si_.D / 2)), q);
-    return mul_rn((T)si_.esc[idx], q);
-}
-
-template <typename T>
-__device__ __forceinline__ T dequant(const SymIn &si_, long long idx, int level)
-{
-    return dequant_sym<T>(si_, si_.sym[idx], idx, q_of<T>(si_.sc, level));
-}
-
-template <typename T>
-__device__ __forceinline__ int first_coarse_at_or_after(const DimTables<T> &d, int p)
-{
-    // smallest coarse j with cpos(j) >= p
-    int j = p <= 0 ? 0 : (p + 1) >> 1;
-    return j < d.mc ? j : d.mc - 1;
-}
 
 constexpr int NST = 4;   // planes in flight per CTA
 
@@ -489,413 +388,6 @@ restrict_kernel(RestrictArgs<T> a, int seg_len)
         for (int i = tid; i < (int)a.qo.D; i += RTHREADS)
             if (hs[i]) atomicAdd(&a.qo.hist[i], (unsigned long long)hs[i]);
     }
-}
-
-// ---------------------------------------------------------------------------
-// Decomposition of one level from a level-l field (Alg. 1: lerp, quantization
-// of the new-node coefficients, mass_trans).  The coarse right-hand side uses
-// the Galerkin identity P^T M_l P = M_{l-1} of nested piecewise-linear spaces:
-//     b = P^T M_l (v - P v_c) = ((x)_k P^T M_l) v - ((x)_k M_{l-1}) v_c,
-// so the restriction reads the staged level-l values directly and the
-// coefficients w = v - lerp(v) are formed only on the nodes the CTA owns
-// (each thread: four consecutive nodes of one row).
-
-constexpr int OWN1 = 2 * TT1, OWN2 = 2 * TT2;   // owned fine region of a tile
-constexpr int JPITCH = OWN2 + 4;
-constexpr int kHistWin = 4096;                  // shared-memory histogram: D/2 +- kHistWin,
-                                                // plus one slot for the escape symbol 0
-
-template <typename T>
-struct PlaneTaps2 {
-    int jlo;
-    T tr[3];   // restriction taps of plane p for coarse jlo..jlo+2
-    T tm[3];   // coarse mass-matrix taps (kept planes only)
-};
-
-// as quant_emit; an escape raises ew to its payload bit length
-template <typename T>
-__device__ __forceinline__ void quant_emit_w(const QuantOut &qo, unsigned int *hs, int hlo, int hn,
-                                             long long si, T w, T rho, unsigned &ew)
-{
-    long long k = quant_code(w, rho);
-    long long s = k + (long long)(qo.D / 2);
-    unsigned int sym;
-    if (s >= 1 && s <= (long long)qo.D - 1) {
-        sym = (unsigned int)s;
-    } else {
-        sym = 0;
-        ew = max(ew, escape_store(qo, si, k));
-    }
-    qo.sym[si] = (uint16_t)sym;
-    const unsigned rel = sym - (unsigned)hlo;
-    if (rel < (unsigned)hn) atomicAdd(&hs[rel], 1u);
-    else if (sym == 0) atomicAdd(&hs[hn], 1u);
-    else atomicAdd(&qo.hist[sym], 1ULL);
-}
-
-template <typename T, int SINK>
-__global__ void __launch_bounds__(RTHREADS, 3)
-decomp_level_kernel(RestrictArgs<T> a, int seg_len)
-{
-    constexpr int PB = row_pitch_bytes<T>();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int m0 = a.g.dim[0].m, m1 = a.g.dim[1].m, m2 = a.g.dim[2].m;
-    const int mc0 = a.g.dim[0].mc, mc1 = a.g.dim[1].mc, mc2 = a.g.dim[2].mc;
-    const int J2 = blockIdx.x * TT2, J1 = blockIdx.y * TT1;
-    const int J0a = blockIdx.z * seg_len;
-    const int J0b = min(J0a + seg_len, mc0);
-    if (J0a >= J0b) return;
-    const int n2 = min(TT2, mc2 - J2), n1 = min(TT1, mc1 - J1);
-    const int lo2 = max(0, cpos_of(m2, mc2, J2) - 2) & ~1;
-    const int hi2 = min(m2 - 1, cpos_of(m2, mc2, J2 + n2 - 1) + 2);
-    const int lo1 = max(0, cpos_of(m1, mc1, J1) - 2) & ~1;
-    const int hi1 = min(m1 - 1, cpos_of(m1, mc1, J1 + n1 - 1) + 2);
-    const int lo0 = max(0, cpos_of(m0, mc0, J0a) - 2) & ~1;
-    const int hi0 = min(m0 - 1, cpos_of(m0, mc0, J0b - 1) + 2);
-    const int r1n = hi1 - lo1 + 1, r2n = hi2 - lo2 + 1;
-    const int o2a = cpos_of(m2, mc2, J2), o2b = (J2 + n2 < mc2) ? cpos_of(m2, mc2, J2 + n2) : m2;
-    const int o1a = cpos_of(m1, mc1, J1), o1b = (J1 + n1 < mc1) ? cpos_of(m1, mc1, J1 + n1) : m1;
-    const int o0a = cpos_of(m0, mc0, J0a), o0b = (J0b < mc0) ? cpos_of(m0, mc0, J0b) : m0;
-
-    unsigned char *stage_base = smem_raw;
-    int *rowoff = reinterpret_cast<int *>(smem_raw + NST * RR1 * PB);
-    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(
-        (reinterpret_cast<uintptr_t>(rowoff + NST * RR1) + 15) & ~uintptr_t(15));
-    PlaneTaps2<T> *ptaps = reinterpret_cast<PlaneTaps2<T> *>(mbar + NST);
-    T *Jb = reinterpret_cast<T *>(ptaps + NST);          // [2][OWN1][JPITCH]
-    T *wl2s = Jb + 2 * OWN1 * JPITCH, *wr2s = wl2s + RR2;   // [RR2]
-    T *wl1s = wr2s + RR2, *wr1s = wl1s + RR1;            // [RR1]
-    unsigned int *hs = reinterpret_cast<unsigned int *>(wr1s + RR1);
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int hhalf = SINK == (int)Sink::QUANT ? min((int)a.qo.D / 2, kHistWin) : 0;
-    const int hlo = (int)(a.qo.D / 2) - hhalf, hn = 2 * hhalf;
-    for (int i = tid; i < r2n; i += RTHREADS) { wl2s[i] = a.g.dim[2].wl[lo2 + i]; wr2s[i] = a.g.dim[2].wr[lo2 + i]; }
-    for (int i = tid; i < r1n; i += RTHREADS) { wl1s[i] = a.g.dim[1].wl[lo1 + i]; wr1s[i] = a.g.dim[1].wr[lo1 + i]; }
-    if (hn) for (int i = tid; i <= hn; i += RTHREADS) hs[i] = 0u;
-    if (tid == 0) {
-        for (int i = 0; i < NST; i++) mbar_init(&mbar[i], 1);
-        mbar_fence_init();
-    }
-    // taps of this thread's dim-2 column (restriction and coarse mass matrix)
-    const int jl = lane;
-    const bool colv = jl < n2;
-    T t2[5], mt2[3];
-    int mc2col[3];
-    const int c2col = colv ? cpos_of(m2, mc2, J2 + jl) - lo2 : 0;
-#pragma unroll
-    for (int o = 0; o < 5; o++) t2[o] = colv ? a.g.dim[2].tap[(J2 + jl) * 5 + o] : (T)0;
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        const int j = J2 + jl + d - 1;
-        const bool ok = colv && j >= 0 && j < mc2;
-        mt2[d] = ok ? a.g.dim[2].mtap[(J2 + jl) * 3 + d] : (T)0;
-        mc2col[d] = ok ? cpos_of(m2, mc2, j) - lo2 : 0;
-    }
-    // taps of this thread's output row (phase D)
-    const int j1l = warp;
-    const bool outp = j1l < n1 && colv;
-    T t1[5], mt1[3];
-    int mr1[3];
-    const int c1r = outp ? cpos_of(m1, mc1, J1 + j1l) - lo1 : 0;
-#pragma unroll
-    for (int o = 0; o < 5; o++) t1[o] = outp ? a.g.dim[1].tap[(J1 + j1l) * 5 + o] : (T)0;
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        const int j = J1 + j1l + d - 1;
-        const bool ok = outp && j >= 0 && j < mc1;
-        mt1[d] = ok ? a.g.dim[1].mtap[(J1 + j1l) * 3 + d] : (T)0;
-        mr1[d] = ok ? cpos_of(m1, mc1, j) - lo1 : 0;
-    }
-    // this thread's owned nodes: row rr, four consecutive nodes from column 4q;
-    // the two half-warps take rows w and w + 8, of equal parity, so that a
-    // warp's kept/new pattern (and its path through phase B) is uniform
-    const int rr = warp + 8 * ((tid >> 4) & 1), q4 = (tid & 15) * 4;
-    const int p1 = o1a + rr;
-    const bool rowv = p1 < o1b;
-    const int i1 = p1 - lo1;
-    const bool f1 = rowv && !kept_pos(m1, p1);
-    // the four owned columns: valid ones and new ones (bit e = column p2b + e)
-    const int p2b = o2a + q4, i2b = p2b - lo2;
-    unsigned vmask = 0, nmask = 0;
-#pragma unroll
-    for (int e = 0; e < 4; e++) {
-        if (p2b + e < o2b) vmask |= 1u << e;
-        if (!kept_pos(m2, p2b + e)) nmask |= 1u << e;
-    }
-    T rho = (T)0;
-    if (SINK == (int)Sink::QUANT) rho = rho_of<T>(a.qo.sc, a.g.level);
-    const T halfD = (T)(a.qo.D / 2);
-    __syncthreads();
-
-    auto issue = [&](int p) {
-        const int slot = (p - lo0) % NST;
-        unsigned char *dst0 = stage_base + slot * RR1 * PB;
-        uint32_t bytes = 0;
-        const unsigned char *src = nullptr;
-        if (lane < r1n) {
-            const T *row = a.v + ((long long)p * m1 + lo1 + lane) * m2 + lo2;
-            const uintptr_t g0 = reinterpret_cast<uintptr_t>(row);
-            const uintptr_t g1 = g0 + (uintptr_t)r2n * sizeof(T);
-            const uintptr_t s0 = g0 & ~uintptr_t(15);
-            uintptr_t s1 = (g1 + 15) & ~uintptr_t(15);
-            const uintptr_t lim = reinterpret_cast<uintptr_t>(a.src_end) & ~uintptr_t(15);
-            bool tail = false;
-            if (s1 > lim) { tail = true; s1 = lim; }
-            bytes = s1 > s0 ? (uint32_t)(s1 - s0) : 0u;
-            src = reinterpret_cast<const unsigned char *>(s0);
-            rowoff[slot * RR1 + lane] = (int)((g0 - s0) / sizeof(T));
-            if (tail) {
-                const uintptr_t t0 = s1 > g0 ? s1 : g0;
-                for (uintptr_t b = t0; b < g1; b += sizeof(T))
-                    *reinterpret_cast<T *>(dst0 + lane * PB + (b - s0)) = *reinterpret_cast<const T *>(b);
-            }
-        }
-        if (lane == 0) {
-            PlaneTaps2<T> pt;
-            int jlo = first_coarse_at_or_after(a.g.dim[0], p - 2);
-            if (jlo < J0a) jlo = J0a;
-            pt.jlo = jlo;
-            const bool k0 = kept_pos(m0, p);
-            const int jc = k0 ? cidx_of(m0, mc0, p) : -10;
-#pragma unroll
-            for (int i = 0; i < 3; i++) {
-                const int j = jlo + i;
-                const int o = p - cpos_of(m0, mc0, j);
-                const bool inj = j < J0b;
-                pt.tr[i] = (inj && o >= -2 && o <= 2) ? a.g.dim[0].tap[j * 5 + o + 2] : (T)0;
-                const int d = jc - j;
-                pt.tm[i] = (inj && d >= -1 && d <= 1) ? a.g.dim[0].mtap[j * 3 + d + 1] : (T)0;
-            }
-            ptaps[slot] = pt;
-        }
-        uint32_t tot = bytes;
-        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-        if (lane == 0) mbar_arrive_expect_tx(&mbar[slot], tot);
-        __syncwarp();
-        if (lane < r1n && bytes) bulk_g2s(dst0 + lane * PB, src, bytes, &mbar[slot]);
-    };
-    auto wait_plane = [&](int p) -> bool {
-        const int r = p - lo0;
-        return mbar_wait_bounded(&mbar[r % NST], (uint32_t)((r / NST) & 1), kWaitPolls);
-    };
-    auto Vrow = [&](int slot, int r) -> const T * {
-        return reinterpret_cast<const T *>(stage_base + (slot * RR1 + r) * PB) + rowoff[slot * RR1 + r];
-    };
-    // J = I_1 I_2 v of kept plane p on the owned region
-    auto form_J = [&](int p) {
-        if (!rowv) return;
-        const int vs = (p - lo0) % NST;
-        T *J = Jb + (cidx_of(m0, mc0, p) & 1) * OWN1 * JPITCH + rr * JPITCH + q4;
-        const T *r0 = Vrow(vs, i1);
-        const T *rm = f1 ? Vrow(vs, i1 - 1) : r0;
-        const T *rp = f1 ? Vrow(vs, i1 + 1) : r0;
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-            const int p2 = o2a + q4 + e;
-            if (p2 >= o2b) break;
-            const int i2 = p2 - lo2;
-            const bool f2 = !kept_pos(m2, p2);
-            auto I2 = [&](const T *row) -> T {
-                return f2 ? fma_rn(wr2s[i2], row[i2 + 1], mul_rn(wl2s[i2], row[i2 - 1])) : row[i2];
-            };
-            J[e] = f1 ? fma_rn(wr1s[i1], I2(rp), mul_rn(wl1s[i1], I2(rm))) : I2(r0);
-        }
-    };
-
-    if (warp == 0)
-        for (int p = lo0; p <= hi0 && p < lo0 + NST - 1; p++) issue(p);
-    int waited = lo0 - 1, jdone = lo0 - 1;
-    T acc0 = 0, acc1 = 0, acc2 = 0;
-    int jb = J0a;
-    const long long cstride = (long long)mc1 * mc2;
-    const long long out_col = (long long)(J1 + j1l) * mc2 + (J2 + jl);
-    unsigned ew = 0;    // largest escape payload bit length seen by this thread
-
-    for (int p0 = lo0; p0 <= hi0; p0++) {
-        const int s0 = (p0 - lo0) % NST;
-        bool ok = true;
-        const int need = min(p0 + 1, hi0);
-        while (ok && waited < need) {
-            if (wait_plane(waited + 1)) waited++;
-            else ok = false;
-        }
-        if (__syncthreads_or(!ok)) {
-            // drain every issued plane not seen complete (see restrict_kernel)
-            if (tid == 0) atomicExch(a.status, (unsigned)DS_TIMEOUT);
-            const int last_issued = min(hi0, p0 + NST - 2);
-            for (int p = waited + 1; p <= last_issued; p++) wait_plane(p);
-            return;
-        }
-        // every warp is done with plane p0 - 1: its stage takes plane p0 + NST - 1
-        if (warp == 0 && p0 + NST - 1 <= hi0) issue(p0 + NST - 1);
-        const bool f0 = !kept_pos(m0, p0);
-        const int pj = f0 ? p0 + 1 : p0;
-        if (jdone < pj) {
-            form_J(pj);
-            jdone = pj;
-            __syncthreads();
-        }
-        // ---- B: coefficients of the owned nodes -----------------------------
-        if (rowv && p0 >= o0a && p0 < o0b) {
-            const T *Jm = Jb + (cidx_of(m0, mc0, f0 ? p0 - 1 : p0) & 1) * OWN1 * JPITCH + rr * JPITCH + q4;
-            const T *Jp = Jb + (cidx_of(m0, mc0, f0 ? p0 + 1 : p0) & 1) * OWN1 * JPITCH + rr * JPITCH + q4;
-            const T wl0 = f0 ? a.g.dim[0].wl[p0] : (T)0, wr0 = f0 ? a.g.dim[0].wr[p0] : (T)0;
-            const T *vr = Vrow(s0, i1) + i2b;
-            const bool rownew = f0 || f1;
-            const unsigned emask = vmask & (rownew ? 0xFu : nmask);   // nodes with a coefficient
-            const long long rb = row_base(a.g, plane_base_of(a.g, p0), !f0, p1);
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                if (!((vmask >> e) & 1u)) continue;
-                const T v = vr[e];
-                if ((emask >> e) & 1u) {
-                    const T lerp = f0 ? fma_rn(wr0, Jp[e], mul_rn(wl0, Jm[e])) : Jm[e];
-                    const T w = sub_rn(v, lerp);
-                    if (SINK != (int)Sink::NONE) {
-                        const int p2 = p2b + e;
-                        const long long si = rb + (rownew ? p2 : (p2 - 1) >> 1);
-                        if (SINK == (int)Sink::STREAM) {
-                            a.coef_out[si] = w;
-                        } else {
-                            // k = sign(w) floor(|w| rho + 1/2), every operation rounded in T;
-                            // symbols D/2 + k for |k| < D/2, escapes otherwise
-                            const T kf = floor(add_rn(mul_rn(w < (T)0 ? -w : w, rho), (T)0.5));
-                            if (kf < halfD) {
-                                const int ki = (int)kf;
-                                const unsigned sym = (unsigned)((int)(a.qo.D / 2) + (w < (T)0 ? -ki : ki));
-                                a.qo.sym[si] = (uint16_t)sym;
-                                const unsigned rel = sym - (unsigned)hlo;
-                                if (rel < (unsigned)hn) atomicAdd(&hs[rel], 1u);
-                                else atomicAdd(&a.qo.hist[sym], 1ULL);
-                            } else {
-                                quant_emit_w(a.qo, hs, hlo, hn, si, w, rho, ew);
-                            }
-                        }
-                    }
-                } else if (a.vc) {
-                    a.vc[(long long)cidx_of(m0, mc0, p0) * cstride +
-                         (long long)cidx_of(m1, mc1, p1) * mc2 + cidx_of(m2, mc2, p2b + e)] = v;
-                }
-            }
-        }
-        // ---- C + D: every warp restricts along dim 2 the five fine rows its
-        // coarse row needs (and, on kept planes, applies the coarse mass matrix
-        // along dim 2 to the three kept rows), then along dim 1, and adds the
-        // dim-0 taps in registers
-        if (outp) {
-            T r = (T)0;
-#pragma unroll
-            for (int o = -2; o <= 2; o++) {
-                const int qq = c1r + o;
-                if (qq >= 0 && qq < r1n) {
-                    const T *vr = Vrow(s0, qq);
-                    T sacc = (T)0;
-#pragma unroll
-                    for (int t = -2; t <= 2; t++) {
-                        const int q = c2col + t;
-                        if (q >= 0 && q < r2n) sacc = fma_rn(t2[t + 2], vr[q], sacc);
-                    }
-                    r = fma_rn(t1[o + 2], sacc, r);
-                }
-            }
-            T rc = (T)0;
-            if (!f0) {
-#pragma unroll
-                for (int d = 0; d < 3; d++) {
-                    const T *vr = Vrow(s0, mr1[d]);
-                    T macc = (T)0;
-#pragma unroll
-                    for (int e = 0; e < 3; e++) macc = fma_rn(mt2[e], vr[mc2col[e]], macc);
-                    rc = fma_rn(mt1[d], macc, rc);
-                }
-            }
-            const PlaneTaps2<T> pt = ptaps[s0];
-            while (jb < pt.jlo && jb < J0b) {
-                a.b[(long long)jb * cstride + out_col] = acc0;
-                acc0 = acc1; acc1 = acc2; acc2 = (T)0;
-                jb++;
-            }
-            acc0 = fma_rn(-pt.tm[0], rc, fma_rn(pt.tr[0], r, acc0));
-            acc1 = fma_rn(-pt.tm[1], rc, fma_rn(pt.tr[1], r, acc1));
-            acc2 = fma_rn(-pt.tm[2], rc, fma_rn(pt.tr[2], r, acc2));
-        }
-    }
-    if (outp) {
-        while (jb < J0b) {
-            a.b[(long long)jb * cstride + out_col] = acc0;
-            acc0 = acc1; acc1 = acc2; acc2 = (T)0;
-            jb++;
-        }
-    }
-    if (hn) {
-        ew = __reduce_max_sync(0xffffffffu, ew);
-        if (lane == 0 && ew) atomicMax(&a.qo.sc->esc_w, ew);
-        __syncthreads();
-        for (int i = tid; i < hn; i += RTHREADS)
-            if (hs[i]) atomicAdd(&a.qo.hist[hlo + i], (unsigned long long)hs[i]);
-        if (tid == 0 && hs[hn]) atomicAdd(&a.qo.hist[0], (unsigned long long)hs[hn]);
-    }
-}
-
-template <typename T>
-size_t decomp_smem(Sink sink, unsigned int D)
-{
-    size_t b = (size_t)NST * RR1 * row_pitch_bytes<T>() + NST * RR1 * 4 + 16 + NST * 8;
-    b += NST * sizeof(PlaneTaps2<T>);
-    b = (b + 15) & ~size_t(15);
-    b += (2 * OWN1 * JPITCH + 2 * (RR1 + RR2)) * sizeof(T) + 16;
-    if (sink == Sink::QUANT) b += ((size_t)2 * std::min<unsigned>(D / 2, kHistWin) + 1) * sizeof(unsigned int);
-    return b;
-}
-
-// Coarse planes per CTA (segment) for a grid of `tiles` x segments CTAs:
-// fill whole waves of the resident CTAs (per_sm per SM) while keeping the
-// dim-0 halo (two fine planes each side of a segment) small.
-int choose_segment(int mc0, long long tiles, int per_sm)
-{
-    const int nsm = sm_count();
-    const long long slots = (long long)nsm * std::max(1, per_sm);
-    double best = -1.0;
-    int best_seg = mc0;
-    for (int gz = 1; gz <= mc0 && gz <= 512; gz++) {
-        const int seg = (mc0 + gz - 1) / gz;
-        const long long ctas = tiles * ((mc0 + seg - 1) / seg);
-        const long long waves = (ctas + slots - 1) / slots;
-        const double score = (double)ctas / (double)(waves * slots) * (2.0 * seg) / (2.0 * seg + 4.0);
-        if (score > best + 1e-9) { best = score; best_seg = seg; }
-    }
-    return best_seg;
-}
-
-template <typename K>
-int resident_ctas(K kernel, size_t smem)
-{
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, RTHREADS, smem) != cudaSuccess) {
-        cudaGetLastError();
-        n = 1;
-    }
-    return std::max(1, n);
-}
-
-template <typename T, int SINK>
-cudaError_t launch_decomp_t(const RestrictArgs<T> &a, cudaStream_t s)
-{
-    const int mc0 = a.g.dim[0].mc, mc1 = a.g.dim[1].mc, mc2 = a.g.dim[2].mc;
-    const int gx = (mc2 + TT2 - 1) / TT2, gy = (mc1 + TT1 - 1) / TT1;
-    size_t sm = decomp_smem<T>((Sink)SINK, SINK == (int)Sink::QUANT ? a.qo.D : 0);
-    static PerDeviceOnce attr;
-    cudaError_t e = once_per_device(attr, [] {
-        return cudaFuncSetAttribute(decomp_level_kernel<T, SINK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    160 * 1024);
-    });
-    if (e != cudaSuccess) return e;
-    const int seg = choose_segment(mc0, (long long)gx * gy, resident_ctas(decomp_level_kernel<T, SINK>, sm));
-    const int gz = (mc0 + seg - 1) / seg;
-    decomp_level_kernel<T, SINK><<<dim3(gx, gy, gz), RTHREADS, sm, s>>>(a, seg);
-    count_launch();
-    return cudaGetLastError();
 }
 
 template <typename T>
@@ -1580,6 +1072,26 @@ __global__ void __launch_bounds__(kCoarseThreads, 1) coarse_kernel(CoarseArgs<T>
 
 int norm_parts() { return kNormBlocks; }
 
+// Coarse planes per CTA (segment) for a grid of `tiles` x segments CTAs:
+// fill whole waves of the resident CTAs (per_sm per SM) while keeping the
+// dim-0 halo (two fine planes each side of a segment) small.
+int choose_segment(int mc0, long long tiles, int per_sm)
+{
+    const int nsm = sm_count();
+    const long long slots = (long long)nsm * std::max(1, per_sm);
+    double best = -1.0;
+    int best_seg = mc0;
+    for (int gz = 1; gz <= mc0 && gz <= 512; gz++) {
+        const int seg = (mc0 + gz - 1) / gz;
+        const long long ctas = tiles * ((mc0 + seg - 1) / seg);
+        const long long waves = (ctas + slots - 1) / slots;
+        const double score = (double)ctas / (double)(waves * slots) * (2.0 * seg) / (2.0 * seg + 4.0);
+        if (score > best + 1e-9) { best = score; best_seg = seg; }
+    }
+    return best_seg;
+}
+
+
 template <typename T, int SRC, int SINK>
 cudaError_t launch_restrict_t(const RestrictArgs<T> &a, cudaStream_t s)
 {
@@ -1592,7 +1104,7 @@ cudaError_t launch_restrict_t(const RestrictArgs<T> &a, cudaStream_t s)
                                     160 * 1024);
     });
     if (e != cudaSuccess) return e;
-    const int seg = choose_segment(mc0, (long long)gx * gy, resident_ctas(restrict_kernel<T, SRC, SINK>, sm));
+    const int seg = choose_segment(mc0, (long long)gx * gy, resident_ctas(restrict_kernel<T, SRC, SINK>, RTHREADS, sm));
     const int gz = (mc0 + seg - 1) / seg;
     restrict_kernel<T, SRC, SINK><<<dim3(gx, gy, gz), RTHREADS, sm, s>>>(a, seg);
     count_launch();
@@ -1603,11 +1115,9 @@ cudaError_t launch_restrict_t(const RestrictArgs<T> &a, cudaStream_t s)
 template <typename T>
 cudaError_t launch_restrict(WSrc src, Sink sink, const RestrictArgs<T> &a, cudaStream_t s)
 {
-    if (src == WSrc::FIELD && sink == Sink::QUANT) return launch_decomp_t<T, 2>(a, s);
-    if (src == WSrc::FIELD && sink == Sink::STREAM) return launch_decomp_t<T, 1>(a, s);
-    if (src == WSrc::FIELD) return launch_decomp_t<T, 0>(a, s);
+    if (src == WSrc::FIELD) return launch_decomp<T>(sink, a, s);
     if (src == WSrc::STREAM) return launch_restrict_t<T, 1, 0>(a, s);
-    if (src == WSrc::SYMBOLS) return launch_restrict_t<T, 2, 0>(a, s);
+    if (src == WSrc::SYMBOLS) return launch_restrict_symbols<T>(a, s);
     return launch_restrict_t<T, 3, 0>(a, s);
 }
 

@@ -44,10 +44,24 @@ struct RestrictArgs {
     int dense_new_only;  // DENSE: 1 = use only the new nodes (E_new^T of the input)
     const void *src_end; // one past the last byte of the staged source (FIELD: v, SYMBOLS: sym)
     unsigned int *status;  // device status word (timeouts)
+    int wait_limit;      // polls of a pipeline wait before it gives up (0: use the library's limit)
 };
 
 template <typename T>
 cudaError_t launch_restrict(WSrc src, Sink sink, const RestrictArgs<T> &a, cudaStream_t s);
+
+// decomp.cu: the level kernel of decomposition and compression (FIELD
+// source; Sink::QUANT or Sink::STREAM) and the restriction of decompression
+// (SYMBOLS source), warp-specialised plane pipelines.
+template <typename T>
+cudaError_t launch_decomp(Sink sink, const RestrictArgs<T> &a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_restrict_symbols(const RestrictArgs<T> &a, cudaStream_t s);
+
+// Polls of a bounded pipeline wait before the kernel gives up with
+// DS_TIMEOUT (set through hpdr_debug_set_wait_limit; default kWaitPolls).
+// The drain of copies in flight after a give-up always uses kWaitPolls.
+extern int g_wait_limit;
 
 // Solve (x)_k M_{l-1} along every active dimension of the coarse array b, in
 // place; the last solve optionally adds (sign=+1) or subtracts (sign=-1) the

@@ -10,7 +10,7 @@ Function names follow the C ABI:
   hpdr_compress, hpdr_decompress, hpdr_inspect, hpdr_compress_bound,
   hpdr_decompose, hpdr_recompose, hpdr_recompose_adjoint,
   hpdr_decompose_adjoint, hpdr_huffman_encode, hpdr_huffman_decode,
-  hpdr_decompose_noalloc.
+  hpdr_decompose_noalloc, hpdr_debug_set_wait_limit.
 """
 import ctypes as C
 import math
@@ -124,6 +124,8 @@ def lib():
         L.hpdr_streamed_bound.argtypes = [C.c_int, sz, C.c_int, C.POINTER(Config), sz, C.c_size_t]
         L.hpdr_streamed_bound.restype = C.c_size_t
         L.hpdr_status_string.argtypes = [C.c_int]
+        L.hpdr_debug_set_wait_limit.argtypes = [C.c_int]
+        L.hpdr_debug_set_wait_limit.restype = C.c_int
         L.hpdr_zfp_bound.restype = C.c_size_t
         L.hpdr_zfp_bound.argtypes = [C.c_int, sz, C.c_int, C.c_uint32]
         L.hpdr_status_string.restype = C.c_char_p
