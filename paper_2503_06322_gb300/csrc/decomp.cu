@@ -89,10 +89,20 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-// a bounded wait that the whole warp agrees on
+// A bounded wait that the whole warp agrees on.  Each poll suspends the warp
+// for up to kSleepNs (it resumes as soon as the phase completes), so waiting
+// costs no issue slots; `limit` polls bound the wait (kWaitPolls polls of
+// 2 us: about two seconds).
+constexpr uint32_t kSleepNs = 2000;
+__device__ __forceinline__ bool wait_sleep_bounded(unsigned long long *bar, uint32_t parity, int limit)
+{
+    for (int i = 0; i < limit; i++)
+        if (mbar_try_wait_sleep(bar, parity, kSleepNs)) return true;
+    return false;
+}
 __device__ __forceinline__ bool warp_wait(unsigned long long *bar, uint32_t parity, int limit)
 {
-    const bool ok = mbar_wait_bounded(bar, parity, limit);
+    const bool ok = wait_sleep_bounded(bar, parity, limit);
     return __all_sync(0xffffffffu, ok);
 }
 __device__ __forceinline__ void named_sync(int id, int nthreads)
@@ -372,6 +382,10 @@ decomp_kernel(RestrictArgs<T> a, int seg_len)
 
     if (warp == DCW) {
         // ---------------- producer ----------------
+        // the dim-0 taps of the next plane are loaded while this plane's
+        // copies are issued, so their latency overlaps the ring's wait
+        PlaneInfo<T> pnext;
+        if (lane == 0) pnext = plane_info(g, tg, tg.lo0);
         int k = 0;
         for (int p = tg.lo0; p <= tg.hi0; p++, k++) {
             const int slot = k % NST;
@@ -406,7 +420,7 @@ decomp_kernel(RestrictArgs<T> a, int seg_len)
                     }
                 }
             }
-            if (lane == 0) pinfo[slot] = plane_info(g, tg, p);
+            if (lane == 0) pinfo[slot] = pnext;
             for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
             __syncwarp();
             if (lane == 0) mbar_arrive_expect_tx(&full[slot], bytes);
@@ -414,10 +428,11 @@ decomp_kernel(RestrictArgs<T> a, int seg_len)
 #pragma unroll
             for (int h = 0; h < 2; h++)
                 if (nb[h]) bulk_g2s(dst0 + (lane + 32 * h) * PB, src[h], nb[h], &full[slot]);
+            if (lane == 0 && p < tg.hi0) pnext = plane_info(g, tg, p + 1);
         }
         // every copy still in flight lands before the CTA may exit
         for (int kk = max(0, k - NST); kk < k; kk++)
-            mbar_wait_bounded(&full[kk % NST], (uint32_t)((kk / NST) & 1), kWaitPolls);
+            wait_sleep_bounded(&full[kk % NST], (uint32_t)((kk / NST) & 1), kWaitPolls);
         return;
     }
 
@@ -736,6 +751,8 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
 
     if (warp == DCW) {
         // ---------------- producer: symbol rows of each plane ----------------
+        PlaneInfo<T> pnext;
+        if (lane == 0) pnext = plane_info(g, tg, tg.lo0);
         int k = 0;
         for (int p = tg.lo0; p <= tg.hi0; p++, k++) {
             const int slot = k % NST;
@@ -770,16 +787,17 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
                         *reinterpret_cast<uint16_t *>(dst0 + lane * PB + (b - s0)) = *reinterpret_cast<const uint16_t *>(b);
                 }
             }
-            if (lane == 0) pinfo[slot] = plane_info(g, tg, p);
+            if (lane == 0) pinfo[slot] = pnext;
             uint32_t bytes = nb;
             for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
             __syncwarp();
             if (lane == 0) mbar_arrive_expect_tx(&full[slot], bytes);
             __syncwarp();
             if (nb) bulk_g2s(dst0 + lane * PB, src, nb, &full[slot]);
+            if (lane == 0 && p < tg.hi0) pnext = plane_info(g, tg, p + 1);
         }
         for (int kk = max(0, k - NST); kk < k; kk++)
-            mbar_wait_bounded(&full[kk % NST], (uint32_t)((kk / NST) & 1), kWaitPolls);
+            wait_sleep_bounded(&full[kk % NST], (uint32_t)((kk / NST) & 1), kWaitPolls);
         return;
     }
 
@@ -802,6 +820,9 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
     for (int p0 = tg.lo0; p0 <= tg.hi0; p0++, k++, slot = (slot + 1 == NST) ? 0 : slot + 1, buf ^= 1) {
         const bool ok = warp_wait(&full[slot], (uint32_t)((k / NST) & 1), limit);
         T *W = W0 + (size_t)buf * (S::wtile_bytes / sizeof(T)) + 2 * kWPitch + 4;
+        // the plane's dim-0 taps belong to the stage: read them before handing it back
+        PlaneInfo<T> pi;
+        if (ok) pi = pinfo[slot];
         if (ok) {
             // ---- dequantize the region of plane p0 into W, four nodes per item
             const bool k0 = kept_pos(m0, p0);
@@ -843,7 +864,6 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
         if (named_sync_or(1, DCW * 32, !ok)) { failed = true; break; }
         if (tid == 0) mbar_arrive(&empty[slot]);
         if (wr.va) {
-            const PlaneInfo<T> pi = pinfo[slot];
             const uint32_t wb = smem_u32(W) - (2 * kWPitch + 4) * (uint32_t)sizeof(T);
             T ra, rb;
             restrict_plane<T>(wr, lc.t2, [&](int i) {
@@ -892,8 +912,9 @@ cudaError_t launch_decomp(Sink sink, const RestrictArgs<T> &a0, cudaStream_t s)
     const int gx = (mc2 + DT2 - 1) / DT2, gy = (mc1 + DT1 - 1) / DT1;
     const int hn = sink == Sink::QUANT ? 2 * (int)std::min<unsigned>(a.qo.D / 2, kHistWin) : 0;
     const size_t sm = DecompSmem<T>::bytes(hn);
-    auto go = [&](auto kern) -> cudaError_t {
-        static PerDeviceOnce attr;
+    // one set-up flag per kernel (both instantiations share a function type)
+    static PerDeviceOnce attr_quant, attr_stream;
+    auto go = [&](auto kern, PerDeviceOnce &attr) -> cudaError_t {
         cudaError_t e = once_per_device(attr, [&] {
             return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         });
@@ -904,8 +925,8 @@ cudaError_t launch_decomp(Sink sink, const RestrictArgs<T> &a0, cudaStream_t s)
         count_launch();
         return cudaGetLastError();
     };
-    if (sink == Sink::QUANT) return go(decomp_kernel<T, (int)Sink::QUANT>);
-    return go(decomp_kernel<T, (int)Sink::STREAM>);
+    if (sink == Sink::QUANT) return go(decomp_kernel<T, (int)Sink::QUANT>, attr_quant);
+    return go(decomp_kernel<T, (int)Sink::STREAM>, attr_stream);
 }
 
 template <typename T>

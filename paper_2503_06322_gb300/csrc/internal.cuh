@@ -125,6 +125,21 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t 
         : "memory");
     return ok != 0;
 }
+// As mbar_try_wait, but a thread whose phase is not complete is suspended in
+// hardware until the phase completes or about `ns` nanoseconds pass, so a
+// waiting warp issues no instructions.
+__device__ __forceinline__ bool mbar_try_wait_sleep(unsigned long long *bar, uint32_t parity, uint32_t ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
 // Waits for the phase with the given parity; gives up after `limit` polls.
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t parity, int limit)
 {

@@ -167,9 +167,12 @@ def test_huffman_long_codewords(oracle, H, dev, nsym, K):
     assert np.array_equal(dec.cpu().numpy().view(np.uint16), sym)
 
 
+# (129, 129, 129) and (300, 65, 65) give the level kernels segments of more
+# planes than their ring of stages holds, so every stage is reused
 @pytest.mark.parametrize("shape,tol,kind,mode", [((129, 129), 1e-3, 1, 0), ((65, 65, 65), 1e-2, 1, 0),
                                                  ((65, 65, 65), 1e-4, 1, 0), ((40, 30, 20), 1e-3, 1, 1),
-                                                 ((500, 50), 0.01, 0, 0), ((2,), 1e-3, 1, 0)],
+                                                 ((500, 50), 0.01, 0, 0), ((2,), 1e-3, 1, 0),
+                                                 ((129, 129, 129), 1e-3, 1, 0), ((300, 65, 65), 1e-3, 1, 0)],
                          ids=str)
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 def test_round_trips_within_bound(oracle, H, dev, shape, tol, kind, mode, dtype):
