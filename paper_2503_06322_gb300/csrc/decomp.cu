@@ -279,35 +279,19 @@ __device__ __forceinline__ void lane_cols(const LevelGeom<T> &g, const TileGeom 
     }
 }
 
-template <typename T>
-__device__ __forceinline__ T ld_s(uint32_t addr)
-{
-    T v;
-    if constexpr (sizeof(T) == 4) {
-        float f;
-        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(f) : "r"(addr) : "memory");
-        v = f;
-    } else {
-        double d;
-        asm volatile("ld.shared.f64 %0, [%1];" : "=d"(d) : "r"(addr) : "memory");
-        v = d;
-    }
-    return v;
-}
-
 // dim-2 then dim-1 restriction of one staged plane for the warp's two
-// outputs; row(i) is the shared address of local row i at the lane's window
-// start (column Ca - 2)
+// outputs; row(i) points at local row i in shared memory, at the lane's
+// window start (column Ca - 2)
 template <typename T, typename RowAddr>
 __device__ __forceinline__ void restrict_plane(const WarpRows<T> &w, const T t2[5], RowAddr row, T &ra, T &rb)
 {
     T s[7];
 #pragma unroll
     for (int i = 0; i < 7; i++) {
-        const uint32_t a = row(i);
+        const T *a = row(i);
         T acc = (T)0;
 #pragma unroll
-        for (int o = 0; o < 5; o++) acc = fma_rn(t2[o], ld_s<T>(a + o * (uint32_t)sizeof(T)), acc);
+        for (int o = 0; o < 5; o++) acc = fma_rn(t2[o], a[o], acc);
         s[i] = acc;
     }
     T x = (T)0, y = (T)0;
@@ -354,7 +338,7 @@ decomp_kernel(RestrictArgs<T> a, int seg_len)
     unsigned long long *empty = reinterpret_cast<unsigned long long *>(smem_raw + S::off_empty);
     PlaneInfo<T> *pinfo = reinterpret_cast<PlaneInfo<T> *>(smem_raw + S::off_info);
     unsigned int *hs = reinterpret_cast<unsigned int *>(smem_raw + S::off_hist);
-    const uint32_t stage0 = smem_u32(smem_raw + S::off_stage);
+    const unsigned char *stage_p = smem_raw + S::off_stage;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int hhalf = QUANT ? min((int)a.qo.D / 2, kHistWin) : 0;
     const int hlo = (int)(a.qo.D / 2) - hhalf, hn = 2 * hhalf;
@@ -464,12 +448,13 @@ decomp_kernel(RestrictArgs<T> a, int seg_len)
         const uint32_t bel = (uint32_t)(reinterpret_cast<uintptr_t>(a.v) / sizeof(T)) + (uint32_t)tg.lo2;
         const uint32_t m1m2 = (uint32_t)m1 * (uint32_t)m2;
         constexpr uint32_t VM = 16 / sizeof(T) - 1;
-        const uint32_t lanecol = (uint32_t)(lc.ca - 2) * (uint32_t)sizeof(T);
-        // shared address of local row i of stage `slot` (plane p) at column Ca - 2
-        auto rowaddr = [&](int slot, int p, int i) -> uint32_t {
+        const int lanecol = lc.ca - 2;
+        // local row i of stage `slot` (plane p), at column Ca - 2: the row's
+        // data starts at its copy's alignment offset inside the staged row
+        auto rowaddr = [&](int slot, int p, int i) -> const T * {
             const uint32_t off = (bel + (uint32_t)p * m1m2 + wr.rm0 + (uint32_t)(i * m2)) & VM;
-            return stage0 + (uint32_t)slot * (uint32_t)S::stage_bytes + (uint32_t)(wr.rl0 + i) * PB +
-                   off * (uint32_t)sizeof(T) + lanecol;
+            return reinterpret_cast<const T *>(stage_p + slot * (int)S::stage_bytes + (wr.rl0 + i) * PB) +
+                   (int)off + lanecol;
         };
         Interp<T> Jp;   // interpolant of the last kept plane at the owned nodes
 #pragma unroll
@@ -478,12 +463,12 @@ decomp_kernel(RestrictArgs<T> a, int seg_len)
         // J = I_1 I_2 v of the kept plane staged in `slot` (plane p), at the owned nodes
         auto form_J = [&](int slot, int p) -> Interp<T> {
             Interp<T> J;
-            const uint32_t aA = rowaddr(slot, p, 2) + 2 * sizeof(T);
-            const uint32_t aB = rowaddr(slot, p, 2 + wr.offb) + 2 * sizeof(T);
-            const uint32_t aC = rowaddr(slot, p, 4 + wr.offb) + 2 * sizeof(T);
-            const T A0 = ld_s<T>(aA), A2 = ld_s<T>(aA + 2 * sizeof(T));
-            const T B0 = ld_s<T>(aB), B2 = ld_s<T>(aB + 2 * sizeof(T));
-            const T C0 = ld_s<T>(aC), C2 = ld_s<T>(aC + 2 * sizeof(T));
+            const T *aA = rowaddr(slot, p, 2) + 2;
+            const T *aB = rowaddr(slot, p, 2 + wr.offb) + 2;
+            const T *aC = rowaddr(slot, p, 4 + wr.offb) + 2;
+            const T A0 = aA[0], A2 = aA[2];
+            const T B0 = aB[0], B2 = aB[2];
+            const T C0 = aC[0], C2 = aC[2];
             const T IA = fma_rn(lc.wr2, A2, mul_rn(lc.wl2, A0));
             const T IB = fma_rn(lc.wr2, B2, mul_rn(lc.wl2, B0));
             const T IC = fma_rn(lc.wr2, C2, mul_rn(lc.wl2, C0));
@@ -548,10 +533,10 @@ decomp_kernel(RestrictArgs<T> a, int seg_len)
                 for (int i = 0; i < 7; i++) {
                     sm[i] = (T)0;
                     if ((mrows >> i) & 1u) {
-                        const uint32_t ad = rowaddr(slot, p0, i);
+                        const T *ad = rowaddr(slot, p0, i);
                         T m = (T)0;
 #pragma unroll
-                        for (int o = 0; o < 5; o++) m = fma_rn(lc.m2t[o], ld_s<T>(ad + o * (uint32_t)sizeof(T)), m);
+                        for (int o = 0; o < 5; o++) m = fma_rn(lc.m2t[o], ad[o], m);
                         sm[i] = m;
                     }
                 }
@@ -597,27 +582,27 @@ decomp_kernel(RestrictArgs<T> a, int seg_len)
                 const long long pb = plane_base_of(g, p0);
                 if (k0) {
                     if (jv != p0) { Jp = form_J(slot, p0); jv = p0; }
-                    const uint32_t a2 = rowaddr(slot, p0, 2) + 2 * sizeof(T);
-                    const uint32_t a3 = rowaddr(slot, p0, 3) + 2 * sizeof(T);
-                    const uint32_t a4 = rowaddr(slot, p0, 2 + wr.offb) + 2 * sizeof(T);
-                    const uint32_t a5 = rowaddr(slot, p0, 3 + wr.offb) + 2 * sizeof(T);
+                    const T *a2 = rowaddr(slot, p0, 2) + 2;
+                    const T *a3 = rowaddr(slot, p0, 3) + 2;
+                    const T *a4 = rowaddr(slot, p0, 2 + wr.offb) + 2;
+                    const T *a5 = rowaddr(slot, p0, 3 + wr.offb) + 2;
                     const int j0 = cidx_of(m0, mc0, p0);
                     const int cko = (Cb - 1) >> 1;   // kept rows: only odd columns are new
                     if (lc.colv) {
                         // kept row Ra: Ca is a coarse node, Ca + 1 a new one
-                        if (a.vc) a.vc[(long long)j0 * cstride + out_a] = ld_s<T>(a2);
-                        if (lc.has_b) emit(pb, kro(0) + cko, sub_rn(ld_s<T>(a2 + sizeof(T)), Jp.v[0][1]));
+                        if (a.vc) a.vc[(long long)j0 * cstride + out_a] = a2[0];
+                        if (lc.has_b) emit(pb, kro(0) + cko, sub_rn(a2[1], Jp.v[0][1]));
                         if (s1) {
-                            emit(pb, kro(1) + lc.Ca, sub_rn(ld_s<T>(a3), Jp.v[1][0]));
-                            if (lc.has_b) emit(pb, kro(1) + Cb, sub_rn(ld_s<T>(a3 + sizeof(T)), Jp.v[1][1]));
+                            emit(pb, kro(1) + lc.Ca, sub_rn(a3[0], Jp.v[1][0]));
+                            if (lc.has_b) emit(pb, kro(1) + Cb, sub_rn(a3[1], Jp.v[1][1]));
                         }
                         if (wr.vb) {
-                            if (a.vc) a.vc[(long long)j0 * cstride + out_b] = ld_s<T>(a4);
-                            if (lc.has_b) emit(pb, kro(2) + cko, sub_rn(ld_s<T>(a4 + sizeof(T)), Jp.v[2][1]));
+                            if (a.vc) a.vc[(long long)j0 * cstride + out_b] = a4[0];
+                            if (lc.has_b) emit(pb, kro(2) + cko, sub_rn(a4[1], Jp.v[2][1]));
                         }
                         if (s3) {
-                            emit(pb, kro(3) + lc.Ca, sub_rn(ld_s<T>(a5), Jp.v[3][0]));
-                            if (lc.has_b) emit(pb, kro(3) + Cb, sub_rn(ld_s<T>(a5 + sizeof(T)), Jp.v[3][1]));
+                            emit(pb, kro(3) + lc.Ca, sub_rn(a5[0], Jp.v[3][0]));
+                            if (lc.has_b) emit(pb, kro(3) + Cb, sub_rn(a5[1], Jp.v[3][1]));
                         }
                     }
                 } else {
@@ -625,25 +610,25 @@ decomp_kernel(RestrictArgs<T> a, int seg_len)
                     const int nslot = (slot + 1 == NST) ? 0 : slot + 1;
                     if (!warp_wait(&full[nslot], (uint32_t)(((k + 1) / NST) & 1), limit)) { ok = false; break; }
                     const Interp<T> Jn = form_J(nslot, p0 + 1);
-                    const uint32_t a2 = rowaddr(slot, p0, 2) + 2 * sizeof(T);
-                    const uint32_t a3 = rowaddr(slot, p0, 3) + 2 * sizeof(T);
-                    const uint32_t a4 = rowaddr(slot, p0, 2 + wr.offb) + 2 * sizeof(T);
-                    const uint32_t a5 = rowaddr(slot, p0, 3 + wr.offb) + 2 * sizeof(T);
+                    const T *a2 = rowaddr(slot, p0, 2) + 2;
+                    const T *a3 = rowaddr(slot, p0, 3) + 2;
+                    const T *a4 = rowaddr(slot, p0, 2 + wr.offb) + 2;
+                    const T *a5 = rowaddr(slot, p0, 3 + wr.offb) + 2;
                     auto lerp0 = [&](int sl, int c) { return fma_rn(pi.wr, Jn.v[sl][c], mul_rn(pi.wl, Jp.v[sl][c])); };
                     if (lc.colv) {
-                        emit(pb, nro(0) + lc.Ca, sub_rn(ld_s<T>(a2), lerp0(0, 0)));
-                        if (lc.has_b) emit(pb, nro(0) + Cb, sub_rn(ld_s<T>(a2 + sizeof(T)), lerp0(0, 1)));
+                        emit(pb, nro(0) + lc.Ca, sub_rn(a2[0], lerp0(0, 0)));
+                        if (lc.has_b) emit(pb, nro(0) + Cb, sub_rn(a2[1], lerp0(0, 1)));
                         if (s1) {
-                            emit(pb, nro(1) + lc.Ca, sub_rn(ld_s<T>(a3), lerp0(1, 0)));
-                            if (lc.has_b) emit(pb, nro(1) + Cb, sub_rn(ld_s<T>(a3 + sizeof(T)), lerp0(1, 1)));
+                            emit(pb, nro(1) + lc.Ca, sub_rn(a3[0], lerp0(1, 0)));
+                            if (lc.has_b) emit(pb, nro(1) + Cb, sub_rn(a3[1], lerp0(1, 1)));
                         }
                         if (wr.vb) {
-                            emit(pb, nro(2) + lc.Ca, sub_rn(ld_s<T>(a4), lerp0(2, 0)));
-                            if (lc.has_b) emit(pb, nro(2) + Cb, sub_rn(ld_s<T>(a4 + sizeof(T)), lerp0(2, 1)));
+                            emit(pb, nro(2) + lc.Ca, sub_rn(a4[0], lerp0(2, 0)));
+                            if (lc.has_b) emit(pb, nro(2) + Cb, sub_rn(a4[1], lerp0(2, 1)));
                         }
                         if (s3) {
-                            emit(pb, nro(3) + lc.Ca, sub_rn(ld_s<T>(a5), lerp0(3, 0)));
-                            if (lc.has_b) emit(pb, nro(3) + Cb, sub_rn(ld_s<T>(a5 + sizeof(T)), lerp0(3, 1)));
+                            emit(pb, nro(3) + lc.Ca, sub_rn(a5[0], lerp0(3, 0)));
+                            if (lc.has_b) emit(pb, nro(3) + Cb, sub_rn(a5[1], lerp0(3, 1)));
                         }
                     }
                     Jp = Jn;
@@ -807,8 +792,7 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
     LaneCols<T> lc;
     lane_cols(g, tg, lane, false, lc);
     const T q = q_of<T>(si_.sc, g.level);
-    const uint32_t w0 = smem_u32(W0);
-    const uint32_t lanecol = (uint32_t)(lc.ca - 2 + 4) * (uint32_t)sizeof(T);
+    const int lanecol = lc.ca - 2;
     const long long cstride = (long long)mc1 * mc2;
     const long long out_a = (long long)wr.j1a * mc2 + lc.j2, out_b = (long long)wr.j1b * mc2 + lc.j2;
     T acc[2][3];
@@ -864,11 +848,9 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
         if (named_sync_or(1, DCW * 32, !ok)) { failed = true; break; }
         if (tid == 0) mbar_arrive(&empty[slot]);
         if (wr.va) {
-            const uint32_t wb = smem_u32(W) - (2 * kWPitch + 4) * (uint32_t)sizeof(T);
             T ra, rb;
-            restrict_plane<T>(wr, lc.t2, [&](int i) {
-                return wb + (uint32_t)(wr.rl0 + i + 2) * (uint32_t)(kWPitch * sizeof(T)) + lanecol;
-            }, ra, rb);
+            restrict_plane<T>(wr, lc.t2, [&](int i) -> const T * { return W + (wr.rl0 + i) * kWPitch + lanecol; },
+                              ra, rb);
             while (jb < pi.jlo && jb < tg.J0b) {
                 if (lc.colv) {
                     a.b[(long long)jb * cstride + out_a] = acc[0][0];

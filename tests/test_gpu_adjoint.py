@@ -74,6 +74,41 @@ def test_mse_gradient_matches_finite_differences():
             assert abs(fd - grad[i].item()) <= 1e-6 * abs(grad).max().item() + 1e-12
 
 
+def test_mse_gradient_finite_differences_257():
+    """Config of the differentiation workload: 257^3 coefficients of a
+    power-law field (seed 4), target seed 5, loss = mean((R(c) - t)^2),
+    central differences with step 1e-3 at 64 random coordinates (seed 6),
+    in FP64.  The loss is quadratic, so the central difference equals the
+    gradient up to rounding; it is summed as the mean of the per-element
+    differences, so the mean over 1.7e7 elements does not swamp the
+    ~1e-7 gradients.  The FP64 adjoint must match to 1e-8 of max|grad|,
+    the FP32 adjoint to 1e-4."""
+    from paper_2503_06322_gb300 import autograd, fields, hpdr
+    shape = (257, 257, 257)
+    t = torch.from_numpy(fields.powerlaw_field(shape, seed=5, dtype=np.float64)).cuda()
+    u0 = torch.from_numpy(fields.powerlaw_field(shape, seed=4, dtype=np.float64)).cuda()
+    grads = {}
+    for dt in (torch.float64, torch.float32):
+        c = hpdr.hpdr_decompose(u0.to(dt)).requires_grad_(True)
+        loss = ((autograd.recompose(c, shape) - t.to(dt)) ** 2).mean()
+        loss.backward()
+        grads[dt] = c.grad.detach().double()
+    c = hpdr.hpdr_decompose(u0)
+    rng = np.random.default_rng(6)
+    idx = rng.choice(c.numel(), size=64, replace=False)
+    h = 1e-3
+    gmax = grads[torch.float64].abs().max().item()
+    with torch.no_grad():
+        for i in idx:
+            cp = c.clone(); cp[i] += h
+            cm = c.clone(); cm[i] -= h
+            rp = hpdr.hpdr_recompose(cp, shape) - t
+            rm = hpdr.hpdr_recompose(cm, shape) - t
+            fd = ((rp * rp - rm * rm).mean() / (2 * h)).item()
+            assert abs(fd - grads[torch.float64][i].item()) <= 1e-8 * gmax
+            assert abs(fd - grads[torch.float32][i].item()) <= 1e-4 * gmax
+
+
 def test_fp32_backward_close_to_fp64():
     from paper_2503_06322_gb300 import autograd, fields, hpdr
     shape = (129, 129, 129)

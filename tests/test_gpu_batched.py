@@ -32,3 +32,26 @@ def test_batched_matches_plain_and_replays(oracle):
     h = out[offs[3]:offs[3] + sizes[3]].cpu().numpy()
     u3 = us[3].cpu().numpy().astype(np.float64)
     assert np.abs(oracle.decompress(h) - u3).max() <= tols[3] * np.abs(u3).max()
+
+
+def test_batched_full_draw_matches_plain():
+    """The batching workload's own draw: 256 fields (seed 3), 2-D or 3-D,
+    dims log-uniform in [17, 513], bounds from {1e-2, 1e-3, 1e-4}.  Large
+    fields take the level kernels' multi-tile, multi-segment paths; every
+    container must equal the plain API's, byte for byte, and decompress
+    within its bound."""
+    from paper_2503_06322_gb300 import fields, hpdr
+    draw = fields.batch_shapes(count=256, seed=3)
+    assert max(max(s) for s, _ in draw) >= 400
+    us = [fields.powerlaw_field_torch(s, seed=1000 + i, device=torch.device("cuda:0")) for i, (s, _) in enumerate(draw)]
+    tols = [t for _, t in draw]
+    out, offs, sizes = hpdr.hpdr_compress_batched(us, tols)
+    for i, (u, tol) in enumerate(zip(us, tols)):
+        plain = hpdr.hpdr_compress(u, tol)
+        assert sizes[i] == plain.numel(), i
+        got = out[offs[i]:offs[i] + sizes[i]]
+        assert torch.equal(got, plain), i
+        if max(u.shape) >= 257:
+            rec = hpdr.hpdr_decompress(got.clone())
+            un = u.double()
+            assert (rec.double() - un).abs().max().item() <= tol * un.abs().max().item(), i

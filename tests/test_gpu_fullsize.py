@@ -111,3 +111,33 @@ def test_500x500x100_fp64_round_trip(oracle, H, f64field, tol):
     orec = oracle.decompress(bnp)
     assert np.abs(orec - ud).max() <= tau
     assert np.abs(orec - rec).max() <= 1e-12 * np.abs(ud).max()
+
+
+def test_513_codes_against_fp64_decision_at_1e4(oracle, H, big):
+    """The codes of the container against the FP64 decision on the GPU's own
+    coefficients (the kernels decide in binary32, reading R5): they agree
+    everywhere except at bin-boundary ties, at most 1e-5 of the elements,
+    and every disagreement is a neighbouring code with |x|/q within a few
+    binary32 ulps of a half-integer."""
+    u, ud = big
+    buf = H.hpdr_compress(u, 1e-4).cpu().numpy()
+    h = _parse(oracle, buf)
+    sym, esc = oracle.decode(h["words"], h["chunk"], h["N"], h["K"], h["lengths"], esc_width=h["esc_width"])
+    half = h["D"] // 2
+    k_gpu = sym.astype(np.int64) - half
+    k_gpu[sym == 0] = esc
+    del sym, esc
+    coef = H.hpdr_decompose(u).cpu().numpy().astype(np.float64)
+    ref_sym, ref_idx, ref_k = oracle.quantize(coef, BIG, h["q"], D=h["D"], precision=64)
+    k_ref = ref_sym.astype(np.int64) - half
+    k_ref[ref_idx] = ref_k
+    del ref_sym
+    bad = np.flatnonzero(k_gpu != k_ref)
+    assert bad.size <= 1e-5 * coef.size, bad.size
+    if bad.size:
+        sizes = np.asarray(oracle.level_sizes(BIG))
+        lev = np.searchsorted(sizes, bad, side="right")
+        q = np.asarray(h["q"])[lev]
+        t = np.abs(coef[bad]) / q
+        assert np.all(np.abs(k_gpu[bad] - k_ref[bad]) == 1)
+        assert np.all(np.abs(t - (np.floor(t) + 0.5)) <= 4 * 2.0 ** -24 * np.maximum(t, 1.0))
