@@ -212,6 +212,7 @@ __global__ void bins_l2s_kernel(L2sArgs a, Scalars *sc)
         const double r = __ddiv_rn(1.0, q);
         sc->rho_d[l] = r;
         sc->rho_f[l] = __double2float_rn(r);
+        sc->rho_lo[l] = __double2float_rn(__dsub_rn(r, (double)sc->rho_f[l]));
         sc->q_f[l] = __double2float_rn(q);
     }
 }
@@ -452,6 +453,7 @@ __global__ void init_scalars_kernel(Scalars *sc, ScalarInit si)
         sc->q_f[l] = __double2float_rn(si.q[l]);
         sc->rho_d[l] = 1.0 / si.q[l];
         sc->rho_f[l] = __double2float_rn(1.0 / si.q[l]);
+        sc->rho_lo[l] = __double2float_rn(sc->rho_d[l] - (double)sc->rho_f[l]);
     }
     if (threadIdx.x == 0) {
         sc->n_esc = si.n_esc;

@@ -114,9 +114,6 @@ __device__ __forceinline__ void fence_proxy_async()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// floor(t) as an integer; values at or above 2^31 saturate (and escape)
-__device__ __forceinline__ int floor_int(float t) { return __float2int_rd(t); }
-__device__ __forceinline__ int floor_int(double t) { return __double2int_rd(t); }
 
 // Geometry of one CTA, common to both kernels.
 struct TileGeom {
@@ -427,8 +424,13 @@ decomp_kernel(RestrictArgs<T> a, int seg_len)
     lane_cols(g, tg, lane, true, lc);
     unsigned ew = 0;   // widest escape payload seen by this thread
     if (wr.va) {
-        const T rho = QUANT ? rho_of<T>(a.qo.sc, g.level) : (T)0;
+        const double rho = QUANT ? rho64_of(a.qo.sc, g.level) : 0.0;
+        const float rho_hi = QUANT ? a.qo.sc->rho_f[g.level] : 0.f;
+        const float rho_lo = QUANT ? a.qo.sc->rho_lo[g.level] : 0.f;
         const int halfD = (int)(a.qo.D / 2);
+        // below this |w| rho_hi the double-word decision is valid and the code
+        // is a symbol (|k| <= D/2 - 1)
+        const float plim = (float)(halfD - 2);
         // owned rows: Ra (kept), Ra + 1 (new, if any), Rb (kept, if j1b), Rb + 1 (new, if any)
         const bool s1 = wr.Ra + 1 < m1 && !kept_pos(m1, wr.Ra + 1);
         const bool s3 = wr.vb && wr.Rb + 1 < m1 && !kept_pos(m1, wr.Rb + 1);
@@ -487,15 +489,26 @@ decomp_kernel(RestrictArgs<T> a, int seg_len)
             if constexpr (SINK == (int)Sink::STREAM) {
                 a.coef_out[base + off] = w;
             } else if constexpr (QUANT) {
-                // k = sign(w) floor(|w| rho + 1/2), every operation rounded in T
-                const T t = add_rn(mul_rn(w < (T)0 ? -w : w, rho), (T)0.5);
-                const int ki = floor_int(t);
+                // k = sign(w) floor(|w| rho + 1/2) with binary64 semantics
+                // (quant_code); codes near the escape range decide in binary64
                 unsigned sym;
-                if (ki < halfD) {
+                bool small = false;
+                int ki = 0;
+                if constexpr (sizeof(T) == 4) {
+                    const float ax = fabsf(w);
+                    small = __fmul_rn(ax, rho_hi) < plim;
+                    if (small) ki = quant_small_f32(ax, rho_hi, rho_lo);
+                }
+                if (small) {
                     sym = (unsigned)(halfD + (w < (T)0 ? -ki : ki));
                 } else {
-                    sym = 0u;
-                    ew = max(ew, escape_store(a.qo, base + off, quant_code(w, rho)));
+                    const long long k = quant_code(w, rho);
+                    if (k > -halfD && k < halfD) {
+                        sym = (unsigned)(halfD + (int)k);
+                    } else {
+                        sym = 0u;
+                        ew = max(ew, escape_store(a.qo, base + off, k));
+                    }
                 }
                 a.qo.sym[base + off] = (uint16_t)sym;
                 const unsigned rel = sym - (unsigned)hlo;

@@ -68,8 +68,9 @@ struct Scalars {
     double sumsq;             // sum u^2
     double tau_abs;           // absolute bound
     double q[kMaxLevels + 1]; // bins (binary64)
-    double rho_d[kMaxLevels + 1];
-    float rho_f[kMaxLevels + 1];
+    double rho_d[kMaxLevels + 1];  // 1/q rounded to binary64
+    float rho_f[kMaxLevels + 1];   // rho_d rounded to binary32 (high word)
+    float rho_lo[kMaxLevels + 1];  // rho_d - rho_f rounded to binary32 (low word)
     float q_f[kMaxLevels + 1];
     unsigned long long n_esc;     // escaped codes (occurrences of symbol 0)
     unsigned long long total_bits;

@@ -116,8 +116,8 @@ restrict_kernel(RestrictArgs<T> a, int seg_len)
     for (int o = 0; o < 5; o++) t1[o] = outp ? tap1src[(J1 + j1l) * 5 + o] : (T)0;
     __syncthreads();
 
-    T rho = (T)0;
-    if (SINK == (int)Sink::QUANT) rho = rho_of<T>(a.qo.sc, a.g.level);
+    double rho = 0.0;
+    if (SINK == (int)Sink::QUANT) rho = rho64_of(a.qo.sc, a.g.level);
     T qlev = (T)0;
     if (SRC == (int)WSrc::SYMBOLS) qlev = q_of<T>(a.symin.sc, a.g.level);
     const float inv_r2n = 1.0f / (float)r2n;
@@ -696,7 +696,7 @@ __global__ void level0_kernel(const T *v0, long long N0, T *coef_out, QuantOut q
     if (i >= N0) return;
     T x = v0[i];
     if (SINK == (int)Sink::STREAM) { coef_out[i] = x; return; }
-    quant_emit(qo, nullptr, false, i, x, rho_of<T>(qo.sc, 0));
+    quant_emit(qo, nullptr, false, i, x, rho64_of(qo.sc, 0));
 }
 
 template <typename T, int SRC>
@@ -814,6 +814,7 @@ __global__ void bins_kernel(BinArgs ba, const double *partials, int nparts, Scal
         double r = __ddiv_rn(1.0, q);
         sc->rho_d[l] = r;
         sc->rho_f[l] = __double2float_rn(r);
+        sc->rho_lo[l] = __double2float_rn(__dsub_rn(r, (double)sc->rho_f[l]));
         sc->q_f[l] = __double2float_rn(q);
     }
     if (!ok && threadIdx.x == 0) atomicExch(&sc->status, (unsigned int)DS_ARG);
@@ -997,7 +998,7 @@ __global__ void __launch_bounds__(kCoarseThreads, 1) coarse_kernel(CoarseArgs<T>
             }
             __syncthreads();
             //    coefficients of the new nodes
-            const T rho = MODE == 0 ? rho_of<T>(a.qo.sc, l) : (T)0;
+            const double rho = MODE == 0 ? rho64_of(a.qo.sc, l) : 0.0;
             for (long long i = tid; i < n; i += blockDim.x) {
                 const int p2 = (int)(i % m2);
                 const long long r = i / m2;
@@ -1019,7 +1020,7 @@ __global__ void __launch_bounds__(kCoarseThreads, 1) coarse_kernel(CoarseArgs<T>
             T *t = V; V = Vn; Vn = t;
         }
         // level 0
-        const T rho0 = MODE == 0 ? rho_of<T>(a.qo.sc, 0) : (T)0;
+        const double rho0 = MODE == 0 ? rho64_of(a.qo.sc, 0) : 0.0;
         for (long long i = tid; i < a.N0; i += blockDim.x) {
             if (MODE == 0) quant_emit(a.qo, nullptr, false, i, V[i], rho0);
             else a.coef_out[i] = V[i];

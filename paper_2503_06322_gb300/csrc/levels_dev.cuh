@@ -7,20 +7,46 @@
 namespace hpdr {
 namespace {
 
+// The quantization decision (Sec. IV-A, Alg. 1: linear quantization of the
+// coefficients with the level's bin q): k = sign(x) floor(|x| rho + 1/2),
+// rho = 1/q rounded to binary64 and every operation rounded to binary64,
+// whatever the data type, so that codes agree with a binary64 decision on
+// the same coefficients everywhere but at half-bin ties.  Codes whose
+// magnitude reaches 2^62 are clamped there (the escape store then flags them).
 template <typename T>
-__device__ __forceinline__ long long quant_code(T x, T rho)
+__device__ __forceinline__ long long quant_code(T x, double rho)
 {
-    // k = sign(x) floor(|x| rho + 1/2), every operation rounded in T
-    T ax = x < (T)0 ? -x : x;
-    T y = mul_rn(ax, rho);
-    T t = add_rn(y, (T)0.5);
-    long long k = (t < (T)1073741824) ? (long long)(int)floor(t) : (long long)floor(t);
+    const double ax = x < (T)0 ? -(double)x : (double)x;
+    const double t = __dadd_rn(__dmul_rn(ax, rho), 0.5);
+    long long k;
+    if (t < 1073741824.0) k = (long long)(int)floor(t);
+    else if (t < 4611686018427387904.0) k = (long long)floor(t);
+    else k = kEscMax;
     return x < (T)0 ? -k : k;
 }
 
-template <typename T> __device__ __forceinline__ T rho_of(const Scalars *sc, int l);
-template <> __device__ __forceinline__ float rho_of<float>(const Scalars *sc, int l) { return sc->rho_f[l]; }
-template <> __device__ __forceinline__ double rho_of<double>(const Scalars *sc, int l) { return sc->rho_d[l]; }
+// The same decision for a binary32 coefficient, in binary32 arithmetic on a
+// double-word product (binary64 throughput is low on this part).  With
+// rho = rho_hi + rho_lo (rho_hi = fl32(rho), rho_lo = fl32(rho - rho_hi)):
+//   p = fl32(ax rho_hi); e = ax rho_hi - p exactly (one FMA); e2 = fl32(e + ax rho_lo),
+// so ax rho = p + e2 to within about 2^-47 ax rho.  With n = rint(p) and
+// d = p - n (exact), floor(ax rho + 1/2) = n + [d + e2 >= 1/2] - [d + e2 < -1/2],
+// and both comparisons are exact (1/2 - d and -1/2 - d are representable
+// whenever the result can change).  Valid while p < 2^22; the result then
+// differs from the binary64 decision only when ax rho lies within about
+// 2^-46 ax rho of a half-integer.
+__device__ __forceinline__ int quant_small_f32(float ax, float rho_hi, float rho_lo)
+{
+    const float p = __fmul_rn(ax, rho_hi);
+    const float e = __fmaf_rn(ax, rho_hi, -p);
+    const float e2 = __fmaf_rn(ax, rho_lo, e);
+    const float n = rintf(p);
+    const float d = __fsub_rn(p, n);
+    return __float2int_rn(n) + (e2 >= __fsub_rn(0.5f, d) ? 1 : 0) - (e2 < __fsub_rn(-0.5f, d) ? 1 : 0);
+}
+
+__device__ __forceinline__ double rho64_of(const Scalars *sc, int l) { return sc->rho_d[l]; }
+
 template <typename T> __device__ __forceinline__ T q_of(const Scalars *sc, int l);
 template <> __device__ __forceinline__ float q_of<float>(const Scalars *sc, int l) { return sc->q_f[l]; }
 template <> __device__ __forceinline__ double q_of<double>(const Scalars *sc, int l) { return sc->q[l]; }
@@ -71,7 +97,7 @@ __device__ __forceinline__ unsigned escape_store(const QuantOut &qo, long long s
 // quantize one coefficient into the symbol stream (+ block histogram / escapes)
 template <typename T>
 __device__ __forceinline__ void quant_emit(const QuantOut &qo, unsigned int *hs, bool smem_hist,
-                                           long long si, T w, T rho)
+                                           long long si, T w, double rho)
 {
     long long k = quant_code(w, rho);
     long long s = k + (long long)(qo.D / 2);

@@ -8,6 +8,7 @@ the oracle's up to rounding; every reconstruction within the bound."""
 import numpy as np
 import pytest
 import torch
+from _codes import assert_codes_match_fp64
 
 pytestmark = pytest.mark.gpu
 
@@ -89,9 +90,7 @@ def test_compress_codes_bins_and_cross_decoding(oracle, H, shape, tol, dtype):
     assert h["has_coords"] and np.array_equal(h["coords"], np.concatenate(co))
     sym, esc = oracle.decode(h["words"], h["chunk"], h["N"], h["K"], h["lengths"], esc_width=h["esc_width"])
     coef = H.hpdr_decompose(ut, coords=co).cpu().numpy().astype(np.float64)
-    prec = 32 if dtype == np.float32 else 64
-    ref_sym, ref_idx, ref_k = oracle.quantize(coef, shape, h["q"], precision=prec)
-    assert np.array_equal(sym, ref_sym) and np.array_equal(esc, ref_k)
+    assert_codes_match_fp64(oracle, sym, esc, coef, shape, h["q"], h["D"])
     eps = 2.0 ** -24 if dtype == np.float32 else 2.0 ** -53
     a = np.abs(u.astype(np.float64)).max()
     q_ref = oracle.bins(shape, tol * a, a, eps, coords=co)

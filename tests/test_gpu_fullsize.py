@@ -7,7 +7,9 @@
 What the oracle can finish in tens of seconds is compared in full:
   * decomposition coefficients, every element (1e-5 x max|coef| for FP32,
     1e-12 for FP64);
-  * quantization codes on identical inputs and the whole Huffman part of the
+  * quantization codes on identical inputs against the oracle's binary64
+    decision (equal except at half-bin ties, at most 1e-5 of the elements; at
+    1e-3 and at the tightest bound, 1e-4) and the whole Huffman part of the
     container, bit-exact (513^3 at 1e-3, the benchmark's bound);
   * cross decoding: the oracle's FP64 reconstruction of the GPU container
     against the GPU's own reconstruction;
@@ -16,6 +18,7 @@ What the oracle can finish in tens of seconds is compared in full:
 import numpy as np
 import pytest
 import torch
+from _codes import assert_codes_match_fp64
 
 pytestmark = pytest.mark.gpu
 
@@ -81,11 +84,9 @@ def test_513_codes_and_huffman_bit_exact(oracle, H, big):
     h = _parse(oracle, buf)
     sym, esc = oracle.decode(h["words"], h["chunk"], h["N"], h["K"], h["lengths"], esc_width=h["esc_width"])
     coef = H.hpdr_decompose(u).cpu().numpy().astype(np.float64)
-    ref_sym, ref_idx, ref_k = oracle.quantize(coef, BIG, h["q"], D=h["D"], precision=32)
-    assert np.array_equal(sym, ref_sym)
-    assert np.array_equal(np.flatnonzero(sym == 0), ref_idx) and np.array_equal(esc, ref_k)
-    ln = oracle.code_lengths(oracle.histogram(ref_sym, h["D"]))
-    words, chunk, bits = oracle.encode(ref_sym, ln, K=h["K"], esc_k=ref_k)
+    assert_codes_match_fp64(oracle, sym, esc, coef, BIG, h["q"], h["D"])
+    ln = oracle.code_lengths(oracle.histogram(sym, h["D"]))
+    words, chunk, bits = oracle.encode(sym, ln, K=h["K"], esc_k=esc)
     assert np.array_equal(h["lengths"], ln)
     assert h["total_bits"] == bits and np.array_equal(h["chunk"], chunk)
     assert np.array_equal(h["words"], words)
@@ -114,30 +115,14 @@ def test_500x500x100_fp64_round_trip(oracle, H, f64field, tol):
 
 
 def test_513_codes_against_fp64_decision_at_1e4(oracle, H, big):
-    """The codes of the container against the FP64 decision on the GPU's own
-    coefficients (the kernels decide in binary32, reading R5): they agree
-    everywhere except at bin-boundary ties, at most 1e-5 of the elements,
-    and every disagreement is a neighbouring code with |x|/q within a few
-    binary32 ulps of a half-integer."""
+    """At the tightest bound (codes in the thousands) the codes of the
+    container still agree with the binary64 decision on the GPU's own
+    coefficients everywhere but at half-bin ties (at most 1e-5 of the
+    elements).  A binary32 decision fails this: at this bound it disagreed
+    on 4.6e-4 of the elements."""
     u, ud = big
     buf = H.hpdr_compress(u, 1e-4).cpu().numpy()
     h = _parse(oracle, buf)
     sym, esc = oracle.decode(h["words"], h["chunk"], h["N"], h["K"], h["lengths"], esc_width=h["esc_width"])
-    half = h["D"] // 2
-    k_gpu = sym.astype(np.int64) - half
-    k_gpu[sym == 0] = esc
-    del sym, esc
     coef = H.hpdr_decompose(u).cpu().numpy().astype(np.float64)
-    ref_sym, ref_idx, ref_k = oracle.quantize(coef, BIG, h["q"], D=h["D"], precision=64)
-    k_ref = ref_sym.astype(np.int64) - half
-    k_ref[ref_idx] = ref_k
-    del ref_sym
-    bad = np.flatnonzero(k_gpu != k_ref)
-    assert bad.size <= 1e-5 * coef.size, bad.size
-    if bad.size:
-        sizes = np.asarray(oracle.level_sizes(BIG))
-        lev = np.searchsorted(sizes, bad, side="right")
-        q = np.asarray(h["q"])[lev]
-        t = np.abs(coef[bad]) / q
-        assert np.all(np.abs(k_gpu[bad] - k_ref[bad]) == 1)
-        assert np.all(np.abs(t - (np.floor(t) + 0.5)) <= 4 * 2.0 ** -24 * np.maximum(t, 1.0))
+    assert_codes_match_fp64(oracle, sym, esc, coef, BIG, h["q"], h["D"])

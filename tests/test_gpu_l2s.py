@@ -10,6 +10,7 @@ import math
 import numpy as np
 import pytest
 import torch
+from _codes import assert_codes_match_fp64
 
 pytestmark = pytest.mark.gpu
 
@@ -53,9 +54,7 @@ def test_bins_codes_and_cross_decoding(oracle, H, shape, tol, coords, dtype):
     assert np.allclose(h["q"], q_ref, rtol=rtol, atol=0)
     sym, esc = oracle.decode(h["words"], h["chunk"], h["N"], h["K"], h["lengths"], esc_width=h["esc_width"])
     coef = H.hpdr_decompose(ut, coords=co).cpu().numpy().astype(np.float64)
-    prec = 32 if dtype == np.float32 else 64
-    ref_sym, _, ref_k = oracle.quantize(coef, shape, h["q"], precision=prec)
-    assert np.array_equal(sym, ref_sym) and np.array_equal(esc, ref_k)
+    assert_codes_match_fp64(oracle, sym, esc, coef, shape, h["q"], h["D"])
     rec = H.hpdr_decompress(torch.from_numpy(buf).cuda()).cpu().numpy().astype(np.float64)
     e_rms = math.sqrt(float(np.mean((rec - ud) ** 2)))
     assert e_rms <= tau
