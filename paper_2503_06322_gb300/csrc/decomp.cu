@@ -428,9 +428,7 @@ decomp_kernel(RestrictArgs<T> a, int seg_len)
         const float rho_hi = QUANT ? a.qo.sc->rho_f[g.level] : 0.f;
         const float rho_lo = QUANT ? a.qo.sc->rho_lo[g.level] : 0.f;
         const int halfD = (int)(a.qo.D / 2);
-        // below this |w| rho_hi the double-word decision is valid and the code
-        // is a symbol (|k| <= D/2 - 1)
-        const float plim = (float)(halfD - 2);
+
         // owned rows: Ra (kept), Ra + 1 (new, if any), Rb (kept, if j1b), Rb + 1 (new, if any)
         const bool s1 = wr.Ra + 1 < m1 && !kept_pos(m1, wr.Ra + 1);
         const bool s3 = wr.vb && wr.Rb + 1 < m1 && !kept_pos(m1, wr.Rb + 1);
@@ -491,16 +489,20 @@ decomp_kernel(RestrictArgs<T> a, int seg_len)
             } else if constexpr (QUANT) {
                 // k = sign(w) floor(|w| rho + 1/2) with binary64 semantics
                 // (quant_code); codes near the escape range decide in binary64
+                // (binary32 coefficients: the double-word decision, valid for
+                // every code below 2^22, in 32-bit integers; escapes widen)
                 unsigned sym;
-                bool small = false;
-                int ki = 0;
                 if constexpr (sizeof(T) == 4) {
                     const float ax = fabsf(w);
-                    small = __fmul_rn(ax, rho_hi) < plim;
-                    if (small) ki = quant_small_f32(ax, rho_hi, rho_lo);
-                }
-                if (small) {
-                    sym = (unsigned)(halfD + (w < (T)0 ? -ki : ki));
+                    const bool dw = __fmul_rn(ax, rho_hi) < kSmallQuant;
+                    const int ki = dw ? quant_small_f32(ax, rho_hi, rho_lo) : halfD;
+                    if (ki < halfD) {
+                        sym = (unsigned)(halfD + (w < (T)0 ? -ki : ki));
+                    } else {
+                        const long long k = dw ? (w < (T)0 ? -(long long)ki : (long long)ki) : quant_code(w, rho);
+                        sym = 0u;
+                        ew = max(ew, escape_store(a.qo, base + off, k));
+                    }
                 } else {
                     const long long k = quant_code(w, rho);
                     if (k > -halfD && k < halfD) {
@@ -895,6 +897,110 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
     }
 }
 
+// ---------------------------------------------------------------------------
+// expand_kernel: recomposition of one level (the inverse of Alg. 1's lerp):
+// kept nodes take the corrected coarse grid v_c, new nodes the coefficient
+// plus the multilinear interpolant of v_c.  Warp w of a CTA owns coarse row
+// j1 = J1 + w, lane l coarse column j2 = J2 + l; the CTA marches along the
+// coarse planes of its segment.  For every coarse plane j0 the lane forms the
+// interpolant J = I_1 I_2 v_c at its 2 x 2 fine nodes (rows Ra, Ra + 1,
+// columns Ca, Ca + 1) once, and writes the kept fine plane of j0 and the new
+// fine plane between j0 - 1 and j0 (lerp of the two J's).  The neighbouring
+// column's coarse value comes from the next lane.  Every load is coalesced;
+// no shared memory, no barriers.
+
+constexpr int XW = 8;                  // warps (coarse rows) per CTA
+constexpr int XTHREADS = XW * 32;
+
+template <typename T, int SRC>
+__global__ void __launch_bounds__(XTHREADS)
+expand_kernel(LevelGeom<T> g, const T *__restrict__ vc, const T *__restrict__ coef_in, SymIn symin,
+              T *__restrict__ out, int seg_len)
+{
+    const int m0 = g.dim[0].m, m1 = g.dim[1].m, m2 = g.dim[2].m;
+    const int mc0 = g.dim[0].mc, mc1 = g.dim[1].mc, mc2 = g.dim[2].mc;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j2 = blockIdx.x * 32 + lane, j1 = blockIdx.y * XW + warp;
+    const int J0a = blockIdx.z * seg_len, J0b = min(J0a + seg_len, mc0);
+    if (J0a >= J0b || blockIdx.y * XW >= mc1) return;
+    const bool rowv = j1 < mc1;                // warp-uniform
+    const bool colv = rowv && j2 < mc2;
+    const int jc2 = min(j2, mc2 - 1), jr1 = min(j1, mc1 - 1);
+    const int Ca = cpos_of(m2, mc2, jc2), Ra = cpos_of(m1, mc1, jr1);
+    const bool hb = colv && Ca + 1 < m2 && !kept_pos(m2, Ca + 1);     // new column after Ca
+    const bool hr = rowv && Ra + 1 < m1 && !kept_pos(m1, Ra + 1);     // new row after Ra
+    const T wl2 = hb ? g.dim[2].wl[Ca + 1] : (T)0, wr2 = hb ? g.dim[2].wr[Ca + 1] : (T)0;
+    const T wl1 = hr ? g.dim[1].wl[Ra + 1] : (T)0, wr1 = hr ? g.dim[1].wr[Ra + 1] : (T)0;
+    const T q = SRC == (int)WSrc::SYMBOLS ? q_of<T>(symin.sc, g.level) : (T)0;
+    const int halfD = (int)(symin.D / 2);
+    const long long cplane = (long long)mc1 * mc2;
+    // coarse column offsets of this lane and of the next column (lane 31 loads its own)
+    const int c0 = jc2, c1 = min(jc2 + 1, mc2 - 1);
+    const int r0 = jr1, r1 = min(jr1 + 1, mc1 - 1);
+    // stream offsets inside a fine plane of the rows Ra (kept) and Ra + 1
+    const int nro0 = Ra * m2, nro1 = (Ra + 1) * m2;
+    const int kro0 = Ra * m2 - kept_before(Ra) * mc2, kro1 = (Ra + 1) * m2 - kept_before(Ra + 1) * mc2;
+    auto coef = [&](long long si) -> T {
+        if constexpr (SRC == (int)WSrc::STREAM) {
+            return coef_in[si];
+        } else {
+            const unsigned s = symin.sym[si];
+            return s != 0u ? mul_rn((T)((int)s - halfD), q) : mul_rn((T)symin.esc[si], q);
+        }
+    };
+    struct J4 { T v00, v01, v10, v11; };
+    auto interp = [&](int j0) -> J4 {
+        const T *pl = vc + (long long)j0 * cplane;
+        const T a00 = pl[(long long)r0 * mc2 + c0];
+        const T a10 = pl[(long long)r1 * mc2 + c0];
+        T a01 = __shfl_down_sync(0xffffffffu, a00, 1);
+        T a11 = __shfl_down_sync(0xffffffffu, a10, 1);
+        if (lane == 31) { a01 = pl[(long long)r0 * mc2 + c1]; a11 = pl[(long long)r1 * mc2 + c1]; }
+        J4 J;
+        J.v00 = a00;
+        J.v01 = fma_rn(wr2, a01, mul_rn(wl2, a00));
+        J.v10 = fma_rn(wr1, a10, mul_rn(wl1, a00));
+        J.v11 = fma_rn(wr1, fma_rn(wr2, a11, mul_rn(wl2, a10)), mul_rn(wl1, J.v01));
+        return J;
+    };
+    J4 Jp = {(T)0, (T)0, (T)0, (T)0};
+    const int jend = min(J0b, mc0 - 1);     // the new plane after the segment's last kept plane needs J(J0b)
+    for (int j0 = J0a; j0 <= jend; j0++) {
+        if (!rowv) break;
+        const J4 J = interp(j0);
+        const int P0 = cpos_of(m0, mc0, j0);
+        if (j0 > J0a) {
+            // the new fine plane between coarse planes j0 - 1 and j0, if any
+            const int Pn = cpos_of(m0, mc0, j0 - 1) + 1;
+            if (Pn < P0 && colv) {
+                const T wl0 = g.dim[0].wl[Pn], wr0 = g.dim[0].wr[Pn];
+                const long long pb = plane_base_of(g, Pn);
+                T *orow = out + ((long long)Pn * m1 + Ra) * m2;
+                orow[Ca] = add_rn(coef(pb + nro0 + Ca), fma_rn(wr0, J.v00, mul_rn(wl0, Jp.v00)));
+                if (hb) orow[Ca + 1] = add_rn(coef(pb + nro0 + Ca + 1), fma_rn(wr0, J.v01, mul_rn(wl0, Jp.v01)));
+                if (hr) {
+                    orow += m2;
+                    orow[Ca] = add_rn(coef(pb + nro1 + Ca), fma_rn(wr0, J.v10, mul_rn(wl0, Jp.v10)));
+                    if (hb) orow[Ca + 1] = add_rn(coef(pb + nro1 + Ca + 1), fma_rn(wr0, J.v11, mul_rn(wl0, Jp.v11)));
+                }
+            }
+        }
+        if (j0 < J0b && colv) {
+            // the kept fine plane of coarse plane j0
+            const long long pb = plane_base_of(g, P0);
+            T *orow = out + ((long long)P0 * m1 + Ra) * m2;
+            orow[Ca] = J.v00;
+            if (hb) orow[Ca + 1] = add_rn(coef(pb + kro0 + (Ca >> 1)), J.v01);
+            if (hr) {
+                orow += m2;
+                orow[Ca] = add_rn(coef(pb + kro1 + Ca), J.v10);
+                if (hb) orow[Ca + 1] = add_rn(coef(pb + kro1 + Ca + 1), J.v11);
+            }
+        }
+        Jp = J;
+    }
+}
+
 }  // namespace
 
 template <typename T>
@@ -944,9 +1050,32 @@ cudaError_t launch_restrict_symbols(const RestrictArgs<T> &a0, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_expand_planes(WSrc src, const LevelGeom<T> &g, const T *vc, const T *coef_in,
+                                 const SymIn &symin, T *out, cudaStream_t s)
+{
+    const int mc0 = g.dim[0].mc, mc1 = g.dim[1].mc, mc2 = g.dim[2].mc;
+    const int gx = (mc2 + 31) / 32, gy = (mc1 + XW - 1) / XW;
+    const bool stream = src == WSrc::STREAM;
+    const int per_sm = stream ? resident_ctas(expand_kernel<T, (int)WSrc::STREAM>, XTHREADS, 0)
+                              : resident_ctas(expand_kernel<T, (int)WSrc::SYMBOLS>, XTHREADS, 0);
+    const int seg = choose_segment(mc0, (long long)gx * gy, per_sm);
+    const int gz = (mc0 + seg - 1) / seg;
+    if (stream)
+        expand_kernel<T, (int)WSrc::STREAM><<<dim3(gx, gy, gz), XTHREADS, 0, s>>>(g, vc, coef_in, symin, out, seg);
+    else
+        expand_kernel<T, (int)WSrc::SYMBOLS><<<dim3(gx, gy, gz), XTHREADS, 0, s>>>(g, vc, coef_in, symin, out, seg);
+    count_launch();
+    return cudaGetLastError();
+}
+
 template cudaError_t launch_decomp<float>(Sink, const RestrictArgs<float> &, cudaStream_t);
 template cudaError_t launch_decomp<double>(Sink, const RestrictArgs<double> &, cudaStream_t);
 template cudaError_t launch_restrict_symbols<float>(const RestrictArgs<float> &, cudaStream_t);
 template cudaError_t launch_restrict_symbols<double>(const RestrictArgs<double> &, cudaStream_t);
+template cudaError_t launch_expand_planes<float>(WSrc, const LevelGeom<float> &, const float *, const float *,
+                                                 const SymIn &, float *, cudaStream_t);
+template cudaError_t launch_expand_planes<double>(WSrc, const LevelGeom<double> &, const double *, const double *,
+                                                  const SymIn &, double *, cudaStream_t);
 
 }  // namespace hpdr

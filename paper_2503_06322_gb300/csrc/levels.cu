@@ -604,91 +604,6 @@ solve_contig_kernel(T *b, int n, long long nlines, int rows, int pitch, const T 
 }
 
 // --------------------------------------------------------------------------
-// Recomposition of one level: kept nodes from the corrected coarse grid, new
-// nodes = coefficient + multilinear interpolant (inverse of Alg. 1 lerp).
-
-template <typename T, int SRC>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4)
-expand_kernel(LevelGeom<T> g, const T *__restrict__ vc, const T *coef_in, SymIn symin, T *out, int tpr_log2)
-{
-    // A group of tpr = 2^tpr_log2 threads per output row (p0, p1), 256 / tpr
-    // rows per block.  Thread t of a group owns the coarse columns j = t,
-    // t + tpr, ... below mc2 - 1: it interpolates the corrected coarse grid
-    // along dims 0 and 1 at column j (V_j), writes the kept position 2j and
-    // the new position 2j + 1 after it, which interpolates V_j and V_{j+1}
-    // (from the next lane); the owner of column mc2 - 2 also writes the last
-    // kept position m2 - 1, which holds V_{mc2-1}.
-    const int m0 = g.dim[0].m, m1 = g.dim[1].m, m2 = g.dim[2].m;
-    const int mc0 = g.dim[0].mc, mc1 = g.dim[1].mc, mc2 = g.dim[2].mc;
-    const int tpr = 1 << tpr_log2;
-    const int tr = (int)(threadIdx.x & (unsigned)(tpr - 1));
-    const unsigned long long row =
-        (unsigned long long)blockIdx.x * (blockDim.x >> tpr_log2) + (threadIdx.x >> tpr_log2);
-    const unsigned long long nrows = (unsigned long long)m0 * (unsigned long long)m1;
-    const bool rvalid = row < nrows;
-    const unsigned long long rr = rvalid ? row : 0ull;
-    int p0, p1;
-    if (nrows <= 0xFFFFFFFFull) {           // 32-bit division (64-bit division is slow here)
-        p0 = (int)((unsigned)rr / (unsigned)m1);
-        p1 = (int)((unsigned)rr - (unsigned)p0 * (unsigned)m1);
-    } else {
-        p0 = (int)(rr / (unsigned long long)m1);
-        p1 = (int)(rr - (unsigned long long)p0 * (unsigned long long)m1);
-    }
-    const bool f0 = !kept_pos(m0, p0), f1 = !kept_pos(m1, p1);
-    int a0, b0, a1, b1;
-    T wl0 = 0, wr0 = 0, wl1 = 0, wr1 = 0;
-    if (f0) { a0 = cidx_of(m0, mc0, p0 - 1); b0 = cidx_of(m0, mc0, p0 + 1); wl0 = g.dim[0].wl[p0]; wr0 = g.dim[0].wr[p0]; }
-    else { a0 = b0 = cidx_of(m0, mc0, p0); }
-    if (f1) { a1 = cidx_of(m1, mc1, p1 - 1); b1 = cidx_of(m1, mc1, p1 + 1); wl1 = g.dim[1].wl[p1]; wr1 = g.dim[1].wr[p1]; }
-    else { a1 = b1 = cidx_of(m1, mc1, p1); }
-    const T *raa = vc + ((long long)a0 * mc1 + a1) * mc2;
-    const T *rab = vc + ((long long)a0 * mc1 + b1) * mc2;
-    const T *rba = vc + ((long long)b0 * mc1 + a1) * mc2;
-    const T *rbb = vc + ((long long)b0 * mc1 + b1) * mc2;
-    const bool rownew = f0 || f1;
-    const long long rb = row_base(g, plane_base_of(g, p0), !f0, p1);
-    const T q = (SRC == (int)WSrc::SYMBOLS) ? q_of<T>(symin.sc, g.level) : (T)0;
-    auto V = [&](int t) -> T {
-        T va = raa[t];
-        if (f1) va = fma_rn(wr1, rab[t], mul_rn(wl1, va));
-        if (!f0) return va;
-        T vb = rba[t];
-        if (f1) vb = fma_rn(wr1, rbb[t], mul_rn(wl1, vb));
-        return fma_rn(wr0, vb, mul_rn(wl0, va));
-    };
-    auto coef = [&](long long si) -> T {
-        if (SRC == (int)WSrc::STREAM) return coef_in[si];
-        return dequant_sym<T>(symin, symin.sym[si], si, q);
-    };
-    T *orow = out + (long long)rr * m2;
-    const int lane = threadIdx.x & 31;
-    const bool nb_lane = lane != 31 && tr + 1 < tpr;     // the next lane holds column j + 1
-    const int np = mc2 - 1;
-    for (int j0 = 0; j0 < np; j0 += tpr) {
-        const int j = j0 + tr;
-        const bool act = rvalid && j < np;
-        const T vt = act ? V(j) : (T)0;
-        T vn = __shfl_down_sync(0xffffffffu, vt, 1);
-        if (act) {
-            if (!nb_lane || j + 1 >= np) vn = V(j + 1);
-            const int pk = 2 * j;
-            orow[pk] = rownew ? add_rn(coef(rb + pk), vt) : vt;
-            const int pf = pk + 1;                         // odd positions are new, but the last
-            if (pf != m2 - 1) {
-                const T lerp = fma_rn(g.dim[2].wr[pf], vn, mul_rn(g.dim[2].wl[pf], vt));
-                const long long si = rb + (rownew ? pf : (pf - 1) >> 1);
-                orow[pf] = add_rn(coef(si), lerp);
-            }
-            if (j + 1 == np) {
-                const int pl = m2 - 1;
-                orow[pl] = rownew ? add_rn(coef(rb + pl), vn) : vn;
-            }
-        }
-    }
-}
-
-// --------------------------------------------------------------------------
 template <typename T, int SINK>
 __global__ void level0_kernel(const T *v0, long long N0, T *coef_out, QuantOut qo)
 {
@@ -1200,19 +1115,7 @@ template <typename T>
 cudaError_t launch_expand(WSrc src, const LevelGeom<T> &g, const T *vc, const T *coef_in,
                           const SymIn &symin, T *out, cudaStream_t s)
 {
-    const long long rows = (long long)g.dim[0].m * g.dim[1].m;
-    // threads per output row: enough for about four coarse-column pairs each
-    const int pairs = g.dim[2].mc - 1;
-    int tl = 5;
-    while (tl < 8 && (4 << tl) < pairs) tl++;
-    const long long grid = (rows + (256 >> tl) - 1) / (256 >> tl);
-    if (grid > 0x7FFFFFFFll) return cudaErrorInvalidConfiguration;
-    if (src == WSrc::STREAM)
-        expand_kernel<T, 1><<<(unsigned)grid, 256, 0, s>>>(g, vc, coef_in, symin, out, tl);
-    else
-        expand_kernel<T, 2><<<(unsigned)grid, 256, 0, s>>>(g, vc, coef_in, symin, out, tl);
-    count_launch();
-    return cudaGetLastError();
+    return launch_expand_planes<T>(src, g, vc, coef_in, symin, out, s);
 }
 
 template <typename T>

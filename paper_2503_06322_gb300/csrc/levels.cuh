@@ -57,6 +57,9 @@ template <typename T>
 cudaError_t launch_decomp(Sink sink, const RestrictArgs<T> &a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_restrict_symbols(const RestrictArgs<T> &a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_expand_planes(WSrc src, const LevelGeom<T> &g, const T *vc, const T *coef_in,
+                                 const SymIn &symin, T *out, cudaStream_t s);
 
 // Polls of a bounded pipeline wait before the kernel gives up with
 // DS_TIMEOUT (set through hpdr_debug_set_wait_limit; default kWaitPolls).

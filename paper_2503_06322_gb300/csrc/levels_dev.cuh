@@ -32,9 +32,11 @@ __device__ __forceinline__ long long quant_code(T x, double rho)
 // so ax rho = p + e2 to within about 2^-47 ax rho.  With n = rint(p) and
 // d = p - n (exact), floor(ax rho + 1/2) = n + [d + e2 >= 1/2] - [d + e2 < -1/2],
 // and both comparisons are exact (1/2 - d and -1/2 - d are representable
-// whenever the result can change).  Valid while p < 2^22; the result then
+// whenever the result can change).  Valid while p < kSmallQuant = 2^22 (then
+// ulp(p) <= 1/4, |d + e2| < 3/4, and n is an exact integer); the result
 // differs from the binary64 decision only when ax rho lies within about
 // 2^-46 ax rho of a half-integer.
+constexpr float kSmallQuant = 4194304.0f;
 __device__ __forceinline__ int quant_small_f32(float ax, float rho_hi, float rho_lo)
 {
     const float p = __fmul_rn(ax, rho_hi);
