@@ -426,8 +426,8 @@ decomp_kernel(RestrictArgs<T> a, int seg_len)
     if (wr.va) {
         const double rho = QUANT ? rho64_of(a.qo.sc, g.level) : 0.0;
         const float rho_hi = QUANT ? a.qo.sc->rho_f[g.level] : 0.f;
-        const float rho_lo = QUANT ? a.qo.sc->rho_lo[g.level] : 0.f;
         const int halfD = (int)(a.qo.D / 2);
+        const float kmaxf = (float)halfD;   // codes the filter may settle: |k| < D/2
 
         // owned rows: Ra (kept), Ra + 1 (new, if any), Rb (kept, if j1b), Rb + 1 (new, if any)
         const bool s1 = wr.Ra + 1 < m1 && !kept_pos(m1, wr.Ra + 1);
@@ -493,15 +493,17 @@ decomp_kernel(RestrictArgs<T> a, int seg_len)
                 // every code below 2^22, in 32-bit integers; escapes widen)
                 unsigned sym;
                 if constexpr (sizeof(T) == 4) {
-                    const float ax = fabsf(w);
-                    const bool dw = __fmul_rn(ax, rho_hi) < kSmallQuant;
-                    const int ki = dw ? quant_small_f32(ax, rho_hi, rho_lo) : halfD;
-                    if (ki < halfD) {
+                    const int ki = quant_filter_f32(fabsf(w), rho_hi, kmaxf);
+                    if (ki >= 0) {
                         sym = (unsigned)(halfD + (w < (T)0 ? -ki : ki));
                     } else {
-                        const long long k = dw ? (w < (T)0 ? -(long long)ki : (long long)ki) : quant_code(w, rho);
-                        sym = 0u;
-                        ew = max(ew, escape_store(a.qo, base + off, k));
+                        const long long k = quant_settle_f32(w, rho_hi, a.qo.sc->rho_lo[g.level], rho);
+                        if (k > -halfD && k < halfD) {
+                            sym = (unsigned)(halfD + (int)k);
+                        } else {
+                            sym = 0u;
+                            ew = max(ew, escape_store(a.qo, base + off, k));
+                        }
                     }
                 } else {
                     const long long k = quant_code(w, rho);
@@ -940,61 +942,105 @@ expand_kernel(LevelGeom<T> g, const T *__restrict__ vc, const T *__restrict__ co
     // stream offsets inside a fine plane of the rows Ra (kept) and Ra + 1
     const int nro0 = Ra * m2, nro1 = (Ra + 1) * m2;
     const int kro0 = Ra * m2 - kept_before(Ra) * mc2, kro1 = (Ra + 1) * m2 - kept_before(Ra + 1) * mc2;
-    auto coef = [&](long long si) -> T {
+    // the raw inputs of one coarse plane j0: its coarse values and the
+    // coefficient words of the new fine plane before it (x) and of its kept
+    // fine plane (k); loaded one plane ahead of their use
+    using W = typename std::conditional<SRC == (int)WSrc::SYMBOLS, unsigned, T>::type;
+    struct Raw {
+        T a00, a10, a01, a11;
+        W x00, x01, x10, x11, k01, k10, k11;
+        long long pbx, pbk;
+    };
+    const int jend = min(J0b, mc0 - 1);     // the new plane after the segment's last kept plane needs J(J0b)
+    auto word = [&](long long si) -> W {
+        if constexpr (SRC == (int)WSrc::STREAM) return coef_in[si];
+        else return symin.sym[si];
+    };
+    auto value = [&](W wv, long long si) -> T {
         if constexpr (SRC == (int)WSrc::STREAM) {
-            return coef_in[si];
+            return wv;
         } else {
-            const unsigned s = symin.sym[si];
-            return s != 0u ? mul_rn((T)((int)s - halfD), q) : mul_rn((T)symin.esc[si], q);
+            return wv != 0u ? mul_rn((T)((int)wv - halfD), q) : mul_rn((T)symin.esc[si], q);
         }
     };
-    struct J4 { T v00, v01, v10, v11; };
-    auto interp = [&](int j0) -> J4 {
+    auto load = [&](int j0) -> Raw {
+        Raw r;
         const T *pl = vc + (long long)j0 * cplane;
-        const T a00 = pl[(long long)r0 * mc2 + c0];
-        const T a10 = pl[(long long)r1 * mc2 + c0];
-        T a01 = __shfl_down_sync(0xffffffffu, a00, 1);
-        T a11 = __shfl_down_sync(0xffffffffu, a10, 1);
-        if (lane == 31) { a01 = pl[(long long)r0 * mc2 + c1]; a11 = pl[(long long)r1 * mc2 + c1]; }
-        J4 J;
-        J.v00 = a00;
-        J.v01 = fma_rn(wr2, a01, mul_rn(wl2, a00));
-        J.v10 = fma_rn(wr1, a10, mul_rn(wl1, a00));
-        J.v11 = fma_rn(wr1, fma_rn(wr2, a11, mul_rn(wl2, a10)), mul_rn(wl1, J.v01));
-        return J;
-    };
-    J4 Jp = {(T)0, (T)0, (T)0, (T)0};
-    const int jend = min(J0b, mc0 - 1);     // the new plane after the segment's last kept plane needs J(J0b)
-    for (int j0 = J0a; j0 <= jend; j0++) {
-        if (!rowv) break;
-        const J4 J = interp(j0);
+        r.a00 = pl[(long long)r0 * mc2 + c0];
+        r.a10 = pl[(long long)r1 * mc2 + c0];
+        r.a01 = r.a11 = (T)0;
+        if (lane == 31) { r.a01 = pl[(long long)r0 * mc2 + c1]; r.a11 = pl[(long long)r1 * mc2 + c1]; }
+        const W z = (W)0;
+        r.x00 = r.x01 = r.x10 = r.x11 = r.k01 = r.k10 = r.k11 = z;
+        r.pbx = r.pbk = 0;
         const int P0 = cpos_of(m0, mc0, j0);
-        if (j0 > J0a) {
+        if (j0 > J0a && colv) {
+            const int Pn = cpos_of(m0, mc0, j0 - 1) + 1;
+            if (Pn < P0) {
+                const long long pb = plane_base_of(g, Pn);
+                r.pbx = pb;
+                r.x00 = word(pb + nro0 + Ca);
+                if (hb) r.x01 = word(pb + nro0 + Ca + 1);
+                if (hr) {
+                    r.x10 = word(pb + nro1 + Ca);
+                    if (hb) r.x11 = word(pb + nro1 + Ca + 1);
+                }
+            }
+        }
+        if (j0 < J0b && colv) {
+            const long long pb = plane_base_of(g, P0);
+            r.pbk = pb;
+            if (hb) r.k01 = word(pb + kro0 + (Ca >> 1));
+            if (hr) {
+                r.k10 = word(pb + kro1 + Ca);
+                if (hb) r.k11 = word(pb + kro1 + Ca + 1);
+            }
+        }
+        return r;
+    };
+    struct J4 { T v00, v01, v10, v11; };
+    J4 Jp = {(T)0, (T)0, (T)0, (T)0};
+    if (!rowv) return;
+    Raw nx = load(J0a);
+    for (int j0 = J0a; j0 <= jend; j0++) {
+        const Raw r = nx;
+        if (j0 < jend) nx = load(j0 + 1);
+        // J = I_1 I_2 v_c at the lane's 2 x 2 fine nodes; the next column from the next lane
+        T a01 = __shfl_down_sync(0xffffffffu, r.a00, 1);
+        T a11 = __shfl_down_sync(0xffffffffu, r.a10, 1);
+        if (lane == 31) { a01 = r.a01; a11 = r.a11; }
+        J4 J;
+        J.v00 = r.a00;
+        J.v01 = fma_rn(wr2, a01, mul_rn(wl2, r.a00));
+        J.v10 = fma_rn(wr1, r.a10, mul_rn(wl1, r.a00));
+        J.v11 = fma_rn(wr1, fma_rn(wr2, a11, mul_rn(wl2, r.a10)), mul_rn(wl1, J.v01));
+        const int P0 = cpos_of(m0, mc0, j0);
+        if (j0 > J0a && colv) {
             // the new fine plane between coarse planes j0 - 1 and j0, if any
             const int Pn = cpos_of(m0, mc0, j0 - 1) + 1;
-            if (Pn < P0 && colv) {
+            if (Pn < P0) {
                 const T wl0 = g.dim[0].wl[Pn], wr0 = g.dim[0].wr[Pn];
-                const long long pb = plane_base_of(g, Pn);
+                const long long pb = r.pbx;
                 T *orow = out + ((long long)Pn * m1 + Ra) * m2;
-                orow[Ca] = add_rn(coef(pb + nro0 + Ca), fma_rn(wr0, J.v00, mul_rn(wl0, Jp.v00)));
-                if (hb) orow[Ca + 1] = add_rn(coef(pb + nro0 + Ca + 1), fma_rn(wr0, J.v01, mul_rn(wl0, Jp.v01)));
+                orow[Ca] = add_rn(value(r.x00, pb + nro0 + Ca), fma_rn(wr0, J.v00, mul_rn(wl0, Jp.v00)));
+                if (hb) orow[Ca + 1] = add_rn(value(r.x01, pb + nro0 + Ca + 1), fma_rn(wr0, J.v01, mul_rn(wl0, Jp.v01)));
                 if (hr) {
                     orow += m2;
-                    orow[Ca] = add_rn(coef(pb + nro1 + Ca), fma_rn(wr0, J.v10, mul_rn(wl0, Jp.v10)));
-                    if (hb) orow[Ca + 1] = add_rn(coef(pb + nro1 + Ca + 1), fma_rn(wr0, J.v11, mul_rn(wl0, Jp.v11)));
+                    orow[Ca] = add_rn(value(r.x10, pb + nro1 + Ca), fma_rn(wr0, J.v10, mul_rn(wl0, Jp.v10)));
+                    if (hb) orow[Ca + 1] = add_rn(value(r.x11, pb + nro1 + Ca + 1), fma_rn(wr0, J.v11, mul_rn(wl0, Jp.v11)));
                 }
             }
         }
         if (j0 < J0b && colv) {
             // the kept fine plane of coarse plane j0
-            const long long pb = plane_base_of(g, P0);
+            const long long pb = r.pbk;
             T *orow = out + ((long long)P0 * m1 + Ra) * m2;
             orow[Ca] = J.v00;
-            if (hb) orow[Ca + 1] = add_rn(coef(pb + kro0 + (Ca >> 1)), J.v01);
+            if (hb) orow[Ca + 1] = add_rn(value(r.k01, pb + kro0 + (Ca >> 1)), J.v01);
             if (hr) {
                 orow += m2;
-                orow[Ca] = add_rn(coef(pb + kro1 + Ca), J.v10);
-                if (hb) orow[Ca + 1] = add_rn(coef(pb + kro1 + Ca + 1), J.v11);
+                orow[Ca] = add_rn(value(r.k10, pb + kro1 + Ca), J.v10);
+                if (hb) orow[Ca + 1] = add_rn(value(r.k11, pb + kro1 + Ca + 1), J.v11);
             }
         }
         Jp = J;
