@@ -427,7 +427,7 @@ decomp_kernel(RestrictArgs<T> a, int seg_len)
         const double rho = QUANT ? rho64_of(a.qo.sc, g.level) : 0.0;
         const float rho_hi = QUANT ? a.qo.sc->rho_f[g.level] : 0.f;
         const int halfD = (int)(a.qo.D / 2);
-        const float kmaxf = (float)halfD;   // codes the filter may settle: |k| < D/2
+        const float rho_lo = QUANT ? a.qo.sc->rho_lo[g.level] : 0.f;
 
         // owned rows: Ra (kept), Ra + 1 (new, if any), Rb (kept, if j1b), Rb + 1 (new, if any)
         const bool s1 = wr.Ra + 1 < m1 && !kept_pos(m1, wr.Ra + 1);
@@ -493,17 +493,15 @@ decomp_kernel(RestrictArgs<T> a, int seg_len)
                 // every code below 2^22, in 32-bit integers; escapes widen)
                 unsigned sym;
                 if constexpr (sizeof(T) == 4) {
-                    const int ki = quant_filter_f32(fabsf(w), rho_hi, kmaxf);
-                    if (ki >= 0) {
+                    const float ax = fabsf(w);
+                    int ki;
+                    if (__fmul_rn(ax, rho_hi) < kSmallQuant) ki = quant_small_f32(ax, rho_hi, rho_lo);
+                    else ki = halfD;   // a code of 2^22 or more: an escape, decided below
+                    if (ki < halfD) {
                         sym = (unsigned)(halfD + (w < (T)0 ? -ki : ki));
                     } else {
-                        const long long k = quant_settle_f32(w, rho_hi, a.qo.sc->rho_lo[g.level], rho);
-                        if (k > -halfD && k < halfD) {
-                            sym = (unsigned)(halfD + (int)k);
-                        } else {
-                            sym = 0u;
-                            ew = max(ew, escape_store(a.qo, base + off, k));
-                        }
+                        sym = 0u;
+                        ew = max(ew, escape_f32(a.qo, base + off, w, rho_hi, rho_lo, rho));
                     }
                 } else {
                     const long long k = quant_code(w, rho);
@@ -698,7 +696,18 @@ struct RsymSmem {
     static constexpr size_t off_full = off_stage + NST * stage_bytes;
     static constexpr size_t off_empty = off_full + NST * 8;
     static constexpr size_t off_info = off_empty + NST * 8;
-    static constexpr size_t bytes = (off_info + NST * sizeof(PlaneInfo<T>) + 15) & ~size_t(15);
+    static constexpr size_t off_rows = (off_info + NST * sizeof(PlaneInfo<T>) + 15) & ~size_t(15);
+    static constexpr size_t bytes = off_rows + (size_t)NST * DR1 * 16;
+};
+
+// where a staged symbol row of a plane sits in the stream, written by the
+// producer beside the row: the stream index of its first node (for escapes),
+// the offset of its first symbol inside the staged copy, and whether the row
+// holds every node (1) or only the new nodes of a kept row (0)
+struct SymRow {
+    long long rb;
+    int off;
+    int rownew;
 };
 
 __device__ __forceinline__ bool named_sync_or(int id, int nthreads, bool pred)
@@ -732,6 +741,7 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
     unsigned long long *empty = reinterpret_cast<unsigned long long *>(smem_raw + S::off_empty);
     PlaneInfo<T> *pinfo = reinterpret_cast<PlaneInfo<T> *>(smem_raw + S::off_info);
     T *W0 = reinterpret_cast<T *>(smem_raw + S::off_w);
+    SymRow *rowinfo = reinterpret_cast<SymRow *>(smem_raw + S::off_rows);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int limit = a.wait_limit;
     const SymIn &si_ = a.symin;
@@ -774,6 +784,11 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
                 const long long first = rownew ? rb + tg.lo2 : rb + (tg.lo2 >> 1);
                 const int cnt = rownew ? tg.r2n : ((tg.hi2 - tg.lo2) >> 1);
                 const uintptr_t g0 = reinterpret_cast<uintptr_t>(si_.sym + first);
+                SymRow sr_;
+                sr_.rb = rb;
+                sr_.off = (int)((g0 & 15) >> 1);
+                sr_.rownew = rownew ? 1 : 0;
+                rowinfo[slot * DR1 + lane] = sr_;
                 const uintptr_t g1 = g0 + (uintptr_t)cnt * 2;
                 const uintptr_t s0 = g0 & ~uintptr_t(15);
                 uintptr_t s1 = (g1 + 15) & ~uintptr_t(15);
@@ -826,28 +841,26 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
         if (ok) pi = pinfo[slot];
         if (ok) {
             // ---- dequantize the region of plane p0 into W, four nodes per item
-            const bool k0 = kept_pos(m0, p0);
-            const long long pb = plane_base_of(g, p0);
             const unsigned char *st = smem_raw + S::off_stage + slot * S::stage_bytes;
+            const SymRow *ri = rowinfo + slot * DR1;
+            const int nq = (tg.r2n + 3) >> 2;
             for (int u = tid; u < tg.r1n * NQ; u += DCW * 32) {
-                const int i1 = u / NQ, i2b = (u - i1 * NQ) * 4;
-                const int p1 = tg.lo1 + i1;
-                const bool rownew = !k0 || !kept_pos(m1, p1);
-                const uintptr_t rowg = reinterpret_cast<uintptr_t>(
-                    si_.sym + (rownew ? row_base(g, pb, k0, p1) + tg.lo2 : row_base(g, pb, k0, p1) + (tg.lo2 >> 1)));
-                const uint16_t *sr = reinterpret_cast<const uint16_t *>(st + i1 * PB) + ((rowg & 15) >> 1);
+                const int i1 = u / NQ, qd = u - i1 * NQ, i2b = qd * 4;
+                if (qd >= nq) continue;
+                const SymRow r = ri[i1];
+                const uint16_t *sr = reinterpret_cast<const uint16_t *>(st + i1 * PB) + r.off;
                 T wv[4];
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
                     const int i2 = i2b + e, p2 = tg.lo2 + i2;
                     wv[e] = (T)0;
-                    if (i2 < tg.r2n && (rownew || !kept_pos(m2, p2))) {
-                        const int sx = rownew ? i2 : (i2 - 1) >> 1;
+                    if (i2 < tg.r2n && (r.rownew || !kept_pos(m2, p2))) {
+                        const int sx = r.rownew ? i2 : (i2 - 1) >> 1;
                         const unsigned sv = sr[sx];
                         if (sv != 0u) {
                             wv[e] = mul_rn((T)((int)sv - (int)(si_.D / 2)), q);
                         } else {
-                            const long long idx = row_base(g, pb, k0, p1) + (rownew ? p2 : (p2 - 1) >> 1);
+                            const long long idx = r.rb + (r.rownew ? p2 : (p2 - 1) >> 1);
                             wv[e] = mul_rn((T)si_.esc[idx], q);
                         }
                     }

@@ -49,32 +49,6 @@ __device__ __forceinline__ int quant_small_f32(float ax, float rho_hi, float rho
 
 __device__ __forceinline__ double rho64_of(const Scalars *sc, int l) { return sc->rho_d[l]; }
 
-// A binary32 filter in front of that decision.  With rho_f = fl32(rho),
-// p = fl32(ax rho_f) and t = fl32(p + 1/2), |t - (ax rho + 1/2)| <= 2^-22 (ax rho + 1),
-// so whenever the fraction of t is at least 2^-21 (t + 1) away from 0 and from 1,
-// floor(t) is the binary64 decision.  Returns that code (>= 0), or -1 when
-// the filter cannot settle it (a value near a half-bin boundary, a code of
-// kmax or more, a non-finite value).
-__device__ __forceinline__ int quant_filter_f32(float ax, float rho_f, float kmax)
-{
-    const float t = __fadd_rn(__fmul_rn(ax, rho_f), 0.5f);
-    const float kf = floorf(t);
-    const float f = __fsub_rn(t, kf);
-    const float band = __fmaf_rn(t, 0x1p-21f, 0x1p-21f);
-    return (f >= band && f <= __fsub_rn(1.0f, band) && kf < kmax) ? __float2int_rz(kf) : -1;
-}
-
-// The code of a binary32 coefficient that the filter left open: the
-// double-word decision below 2^22, binary64 above.
-__device__ __noinline__ long long quant_settle_f32(float w, float rho_f, float rho_lo, double rho)
-{
-    const float ax = fabsf(w);
-    if (__fmul_rn(ax, rho_f) < kSmallQuant) {
-        const int ki = quant_small_f32(ax, rho_f, rho_lo);
-        return w < 0.0f ? -(long long)ki : (long long)ki;
-    }
-    return quant_code(w, rho);
-}
 
 template <typename T> __device__ __forceinline__ T q_of(const Scalars *sc, int l);
 template <> __device__ __forceinline__ float q_of<float>(const Scalars *sc, int l) { return sc->q_f[l]; }
@@ -121,6 +95,23 @@ __device__ __forceinline__ unsigned escape_store(const QuantOut &qo, long long s
     qo.esc[si] = k;
     const unsigned long long z = k >= 0 ? 2ULL * (unsigned long long)k : 2ULL * (unsigned long long)(-(k + 1)) + 1ULL;
     return 64u - (unsigned)__clzll((long long)z);
+}
+
+// An escape of a binary32 coefficient (|k| >= D/2): its exact code (the
+// double-word decision below 2^22, binary64 above) stored at its stream
+// position; returns the payload bit length.  Out of line: escapes are rare.
+__device__ __noinline__ unsigned escape_f32(const QuantOut &qo, long long si, float w, float rho_f, float rho_lo,
+                                            double rho)
+{
+    const float ax = fabsf(w);
+    long long k;
+    if (__fmul_rn(ax, rho_f) < kSmallQuant) {
+        const int ki = quant_small_f32(ax, rho_f, rho_lo);
+        k = w < 0.0f ? -(long long)ki : (long long)ki;
+    } else {
+        k = quant_code(w, rho);
+    }
+    return escape_store(qo, si, k);
 }
 
 // quantize one coefficient into the symbol stream (+ block histogram / escapes)
