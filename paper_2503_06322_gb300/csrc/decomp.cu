@@ -692,13 +692,23 @@ struct RsymSmem {
     static constexpr int WROWS = DR1 + 6;     // zero rows around the region: two before, up to four after
     static constexpr size_t wtile_bytes = (size_t)WROWS * kWPitch * sizeof(T);
     static constexpr size_t off_w = 0;
-    static constexpr size_t off_stage = off_w + 2 * wtile_bytes;
+    static constexpr size_t off_stage = off_w + 3 * wtile_bytes;   // three dequantized tiles
     static constexpr size_t off_full = off_stage + NST * stage_bytes;
     static constexpr size_t off_empty = off_full + NST * 8;
     static constexpr size_t off_info = off_empty + NST * 8;
     static constexpr size_t off_rows = (off_info + NST * sizeof(PlaneInfo<T>) + 15) & ~size_t(15);
-    static constexpr size_t bytes = off_rows + (size_t)NST * DR1 * 16;
+    static constexpr int EPITCH = DR2;           // escaped codes of a plane: [DR1][DR2] int64
+    static constexpr size_t off_esc = off_rows + (size_t)NST * DR1 * 16;
+    static constexpr size_t bytes = off_esc + 2 * (size_t)DR1 * EPITCH * 8;
 };
+
+// an asynchronous 8-byte global -> shared copy (its own completion group per thread)
+__device__ __forceinline__ void cp_async8(void *dst_smem, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // where a staged symbol row of a plane sits in the stream, written by the
 // producer beside the row: the stream index of its first node (for escapes),
@@ -731,6 +741,7 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
     using S = RsymSmem<T>;
     constexpr int NST = S::NST, PB = S::PB;
     constexpr int NQ = (DR2 + 3) / 4;   // quads of four nodes per region row
+    constexpr int kDqItems = (DR1 * NQ + DCW * 32 - 1) / (DCW * 32);   // quads per thread and plane
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const LevelGeom<T> &g = a.g;
     const TileGeom tg = tile_geom(g, seg_len);
@@ -832,56 +843,112 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
     for (int u = 0; u < 2; u++) acc[u][0] = acc[u][1] = acc[u][2] = (T)0;
     int jb = tg.J0a;
     bool failed = false;
-    int k = 0, slot = 0, buf = 0;
-    for (int p0 = tg.lo0; p0 <= tg.hi0; p0++, k++, slot = (slot + 1 == NST) ? 0 : slot + 1, buf ^= 1) {
-        const bool ok = warp_wait(&full[slot], (uint32_t)((k / NST) & 1), limit);
-        T *W = W0 + (size_t)buf * (S::wtile_bytes / sizeof(T)) + 2 * kWPitch + 4;
-        // the plane's dim-0 taps belong to the stage: read them before handing it back
-        PlaneInfo<T> pi;
-        if (ok) pi = pinfo[slot];
-        if (ok) {
-            // ---- dequantize the region of plane p0 into W, four nodes per item
-            const unsigned char *st = smem_raw + S::off_stage + slot * S::stage_bytes;
-            const SymRow *ri = rowinfo + slot * DR1;
-            const int nq = (tg.r2n + 3) >> 2;
-            for (int u = tid; u < tg.r1n * NQ; u += DCW * 32) {
-                const int i1 = u / NQ, qd = u - i1 * NQ, i2b = qd * 4;
-                if (qd >= nq) continue;
-                const SymRow r = ri[i1];
-                const uint16_t *sr = reinterpret_cast<const uint16_t *>(st + i1 * PB) + r.off;
-                T wv[4];
+    const int nplanes = tg.hi0 - tg.lo0 + 1;
+    const int nq = (tg.r2n + 3) >> 2;
+    auto tile = [&](int kk) -> T * { return W0 + (size_t)(kk % 3) * (S::wtile_bytes / sizeof(T)) + 2 * kWPitch + 4; };
+    // The dequantized tile of plane kk is filled one iteration before its
+    // restriction: the values of its symbols now; its escaped codes travel
+    // from global memory into a shared escape tile by asynchronous copies and
+    // enter the tile on the next iteration, so their latency hides behind a
+    // plane of work (a register destination would serialize the warp on
+    // every escape it meets).
+    struct Taps {
+        int jlo;
+        T tr[3];
+    };
+    long long *esc_tile0 = reinterpret_cast<long long *>(smem_raw + S::off_esc);
+    // returns the mask of this thread's escaped nodes (bit 4 it + e)
+    auto fill = [&](int kk, T *Wt) -> unsigned {
+        const int sl = kk % NST;
+        const unsigned char *st = smem_raw + S::off_stage + sl * S::stage_bytes;
+        const SymRow *ri = rowinfo + sl * DR1;
+        long long *et = esc_tile0 + (size_t)(kk & 1) * DR1 * S::EPITCH;
+        unsigned escm = 0;
 #pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    const int i2 = i2b + e, p2 = tg.lo2 + i2;
-                    wv[e] = (T)0;
-                    if (i2 < tg.r2n && (r.rownew || !kept_pos(m2, p2))) {
-                        const int sx = r.rownew ? i2 : (i2 - 1) >> 1;
-                        const unsigned sv = sr[sx];
-                        if (sv != 0u) {
-                            wv[e] = mul_rn((T)((int)sv - (int)(si_.D / 2)), q);
-                        } else {
-                            const long long idx = r.rb + (r.rownew ? p2 : (p2 - 1) >> 1);
-                            wv[e] = mul_rn((T)si_.esc[idx], q);
-                        }
+        for (int it = 0; it < kDqItems; it++) {
+            const int u = tid + it * DCW * 32;
+            const int i1 = u / NQ, qd = u - i1 * NQ, i2b = qd * 4;
+            if (!(u < tg.r1n * NQ && qd < nq)) continue;
+            const SymRow r = ri[i1];
+            const uint16_t *sr = reinterpret_cast<const uint16_t *>(st + i1 * PB) + r.off;
+            T wv[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int i2 = i2b + e, p2 = tg.lo2 + i2;
+                wv[e] = (T)0;
+                if (i2 < tg.r2n && (r.rownew || !kept_pos(m2, p2))) {
+                    const int sx = r.rownew ? i2 : (i2 - 1) >> 1;
+                    const unsigned sv = sr[sx];
+                    if (sv != 0u) {
+                        wv[e] = mul_rn((T)((int)sv - (int)(si_.D / 2)), q);
+                    } else {
+                        cp_async8(et + i1 * S::EPITCH + i2, si_.esc + r.rb + (r.rownew ? p2 : (p2 - 1) >> 1));
+                        escm |= 1u << (4 * it + e);
                     }
                 }
-                T *wd = W + i1 * kWPitch + i2b;
-                if constexpr (sizeof(T) == 4) {
-                    *reinterpret_cast<float4 *>(wd) = make_float4(wv[0], wv[1], wv[2], wv[3]);
-                } else {
-                    reinterpret_cast<double2 *>(wd)[0] = make_double2(wv[0], wv[1]);
-                    reinterpret_cast<double2 *>(wd)[1] = make_double2(wv[2], wv[3]);
-                }
+            }
+            T *wd = Wt + i1 * kWPitch + i2b;
+            if constexpr (sizeof(T) == 4) {
+                *reinterpret_cast<float4 *>(wd) = make_float4(wv[0], wv[1], wv[2], wv[3]);
+            } else {
+                reinterpret_cast<double2 *>(wd)[0] = make_double2(wv[0], wv[1]);
+                reinterpret_cast<double2 *>(wd)[1] = make_double2(wv[2], wv[3]);
             }
         }
-        // the tile is complete, the stage read, and every consumer knows whether a wait ran out
+        cp_async_commit();
+        return escm;
+    };
+    // the escaped codes of plane kk (this thread's, copied one iteration ago) into its tile
+    auto patch = [&](int kk, T *Wt, unsigned escm) {
+        if (!escm) return;
+        const long long *et = esc_tile0 + (size_t)(kk & 1) * DR1 * S::EPITCH;
+#pragma unroll
+        for (int it = 0; it < kDqItems; it++) {
+            const int u = tid + it * DCW * 32;
+            const int i1 = u / NQ, i2b = (u - i1 * NQ) * 4;
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                if ((escm >> (4 * it + e)) & 1u)
+                    Wt[i1 * kWPitch + i2b + e] = mul_rn((T)et[i1 * S::EPITCH + i2b + e], q);
+        }
+    };
+    auto taps_of = [&](int kk) -> Taps {
+        const PlaneInfo<T> &pi = pinfo[kk % NST];
+        Taps t;
+        t.jlo = pi.jlo;
+        t.tr[0] = pi.tr[0]; t.tr[1] = pi.tr[1]; t.tr[2] = pi.tr[2];
+        return t;
+    };
+    unsigned ec = 0;
+    Taps tc;
+    tc.jlo = 0; tc.tr[0] = tc.tr[1] = tc.tr[2] = (T)0;
+    {
+        const bool ok = warp_wait(&full[0], 0u, limit);
+        if (ok) { tc = taps_of(0); ec = fill(0, tile(0)); }
+        if (named_sync_or(1, DCW * 32, !ok)) failed = true;
+        else if (tid == 0) mbar_arrive(&empty[0]);
+    }
+    for (int k = 0; k < nplanes && !failed; k++) {
+        // this plane's escaped codes (copied one iteration ago) have landed
+        cp_async_wait0();
+        T *W = tile(k);
+        patch(k, W, ec);
+        // the next plane: symbols into its tile, its escaped codes in flight
+        unsigned en = 0;
+        Taps tn = tc;
+        bool ok = true;
+        if (k + 1 < nplanes) {
+            ok = warp_wait(&full[(k + 1) % NST], (uint32_t)(((k + 1) / NST) & 1), limit);
+            if (ok) { tn = taps_of(k + 1); en = fill(k + 1, tile(k + 1)); }
+        }
+        // tile k complete, stage k + 1 read, and every consumer knows whether a wait ran out
         if (named_sync_or(1, DCW * 32, !ok)) { failed = true; break; }
-        if (tid == 0) mbar_arrive(&empty[slot]);
+        if (tid == 0 && k + 1 < nplanes) mbar_arrive(&empty[(k + 1) % NST]);
         if (wr.va) {
             T ra, rb;
             restrict_plane<T>(wr, lc.t2, [&](int i) -> const T * { return W + (wr.rl0 + i) * kWPitch + lanecol; },
                               ra, rb);
-            while (jb < pi.jlo && jb < tg.J0b) {
+            while (jb < tc.jlo && jb < tg.J0b) {
                 if (lc.colv) {
                     a.b[(long long)jb * cstride + out_a] = acc[0][0];
                     if (wr.vb) a.b[(long long)jb * cstride + out_b] = acc[1][0];
@@ -892,10 +959,12 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
             }
 #pragma unroll
             for (int i = 0; i < 3; i++) {
-                acc[0][i] = fma_rn(pi.tr[i], ra, acc[0][i]);
-                acc[1][i] = fma_rn(pi.tr[i], rb, acc[1][i]);
+                acc[0][i] = fma_rn(tc.tr[i], ra, acc[0][i]);
+                acc[1][i] = fma_rn(tc.tr[i], rb, acc[1][i]);
             }
         }
+        ec = en;
+        tc = tn;
     }
     if (failed) {
         if (tid == 0) atomicExch(a.status, (unsigned)DS_TIMEOUT);
@@ -969,13 +1038,6 @@ expand_kernel(LevelGeom<T> g, const T *__restrict__ vc, const T *__restrict__ co
         if constexpr (SRC == (int)WSrc::STREAM) return coef_in[si];
         else return symin.sym[si];
     };
-    auto value = [&](W wv, long long si) -> T {
-        if constexpr (SRC == (int)WSrc::STREAM) {
-            return wv;
-        } else {
-            return wv != 0u ? mul_rn((T)((int)wv - halfD), q) : mul_rn((T)symin.esc[si], q);
-        }
-    };
     auto load = [&](int j0) -> Raw {
         Raw r;
         const T *pl = vc + (long long)j0 * cplane;
@@ -985,7 +1047,8 @@ expand_kernel(LevelGeom<T> g, const T *__restrict__ vc, const T *__restrict__ co
         if (lane == 31) { r.a01 = pl[(long long)r0 * mc2 + c1]; r.a11 = pl[(long long)r1 * mc2 + c1]; }
         const W z = (W)0;
         r.x00 = r.x01 = r.x10 = r.x11 = r.k01 = r.k10 = r.k11 = z;
-        r.pbx = r.pbk = 0;
+        r.pbx = 0;    // no new plane before j0 (a new plane never starts the stream)
+        r.pbk = -1;   // no kept plane of j0 in this segment
         const int P0 = cpos_of(m0, mc0, j0);
         if (j0 > J0a && colv) {
             const int Pn = cpos_of(m0, mc0, j0 - 1) + 1;
@@ -1014,10 +1077,50 @@ expand_kernel(LevelGeom<T> g, const T *__restrict__ vc, const T *__restrict__ co
     struct J4 { T v00, v01, v10, v11; };
     J4 Jp = {(T)0, (T)0, (T)0, (T)0};
     if (!rowv) return;
-    Raw nx = load(J0a);
-    for (int j0 = J0a; j0 <= jend; j0++) {
-        const Raw r = nx;
-        if (j0 < jend) nx = load(j0 + 1);
+    // Escaped codes (symbol 0) travel into shared slots by asynchronous
+    // copies, one plane ahead of their use; with a register destination a
+    // warp would wait on every node at which any lane escapes.
+    extern __shared__ __align__(16) unsigned char xsm[];
+    long long *eslot = reinterpret_cast<long long *>(xsm) + threadIdx.x * 7;   // [2][XTHREADS][7]
+    bool pend = false;   // escapes of the current plane in flight
+    auto issue_esc = [&](const Raw &r, int b) -> bool {
+        if constexpr (SRC == (int)WSrc::SYMBOLS) {
+            const bool any = (r.x00 == 0u && colv && r.pbx) || (r.x01 == 0u && hb && r.pbx) ||
+                             (r.x10 == 0u && hr && r.pbx) || (r.x11 == 0u && hr && hb && r.pbx) ||
+                             (r.k01 == 0u && hb && r.pbk >= 0) || (r.k10 == 0u && hr && r.pbk >= 0) ||
+                             (r.k11 == 0u && hr && hb && r.pbk >= 0);
+            if (!__any_sync(0xffffffffu, any)) return false;
+            long long *e = eslot + (size_t)b * XTHREADS * 7;
+            if (r.x00 == 0u && colv && r.pbx) cp_async8(e + 0, symin.esc + r.pbx + nro0 + Ca);
+            if (r.x01 == 0u && hb && r.pbx) cp_async8(e + 1, symin.esc + r.pbx + nro0 + Ca + 1);
+            if (r.x10 == 0u && hr && r.pbx) cp_async8(e + 2, symin.esc + r.pbx + nro1 + Ca);
+            if (r.x11 == 0u && hr && hb && r.pbx) cp_async8(e + 3, symin.esc + r.pbx + nro1 + Ca + 1);
+            if (r.k01 == 0u && hb && r.pbk >= 0) cp_async8(e + 4, symin.esc + r.pbk + kro0 + (Ca >> 1));
+            if (r.k10 == 0u && hr && r.pbk >= 0) cp_async8(e + 5, symin.esc + r.pbk + kro1 + Ca);
+            if (r.k11 == 0u && hr && hb && r.pbk >= 0) cp_async8(e + 6, symin.esc + r.pbk + kro1 + Ca + 1);
+            cp_async_commit();
+            return true;
+        }
+        return false;
+    };
+    // value of coefficient word w (slot j of buffer b holds its code when w is an escape)
+    auto val = [&](W wv, int b, int j) -> T {
+        if constexpr (SRC == (int)WSrc::STREAM) {
+            return wv;
+        } else {
+            return wv != 0u ? mul_rn((T)((int)wv - halfD), q) : mul_rn((T)eslot[(size_t)b * XTHREADS * 7 + j], q);
+        }
+    };
+    auto step = [&](int j0, Raw &cur, const Raw &nxt, int b) {
+        // this plane's escapes were issued a step ago; the next plane's words
+        // arrived a step ago: its escapes go in flight
+        const bool pn = j0 + 1 <= jend && issue_esc(nxt, b ^ 1);
+        if (pend) {
+            if (pn) asm volatile("cp.async.wait_group 1;" ::: "memory");
+            else asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        pend = pn;
+        const Raw &r = cur;
         // J = I_1 I_2 v_c at the lane's 2 x 2 fine nodes; the next column from the next lane
         T a01 = __shfl_down_sync(0xffffffffu, r.a00, 1);
         T a11 = __shfl_down_sync(0xffffffffu, r.a10, 1);
@@ -1033,32 +1136,43 @@ expand_kernel(LevelGeom<T> g, const T *__restrict__ vc, const T *__restrict__ co
             const int Pn = cpos_of(m0, mc0, j0 - 1) + 1;
             if (Pn < P0) {
                 const T wl0 = g.dim[0].wl[Pn], wr0 = g.dim[0].wr[Pn];
-                const long long pb = r.pbx;
                 T *orow = out + ((long long)Pn * m1 + Ra) * m2;
-                orow[Ca] = add_rn(value(r.x00, pb + nro0 + Ca), fma_rn(wr0, J.v00, mul_rn(wl0, Jp.v00)));
-                if (hb) orow[Ca + 1] = add_rn(value(r.x01, pb + nro0 + Ca + 1), fma_rn(wr0, J.v01, mul_rn(wl0, Jp.v01)));
+                orow[Ca] = add_rn(val(r.x00, b, 0), fma_rn(wr0, J.v00, mul_rn(wl0, Jp.v00)));
+                if (hb) orow[Ca + 1] = add_rn(val(r.x01, b, 1), fma_rn(wr0, J.v01, mul_rn(wl0, Jp.v01)));
                 if (hr) {
                     orow += m2;
-                    orow[Ca] = add_rn(value(r.x10, pb + nro1 + Ca), fma_rn(wr0, J.v10, mul_rn(wl0, Jp.v10)));
-                    if (hb) orow[Ca + 1] = add_rn(value(r.x11, pb + nro1 + Ca + 1), fma_rn(wr0, J.v11, mul_rn(wl0, Jp.v11)));
+                    orow[Ca] = add_rn(val(r.x10, b, 2), fma_rn(wr0, J.v10, mul_rn(wl0, Jp.v10)));
+                    if (hb) orow[Ca + 1] = add_rn(val(r.x11, b, 3), fma_rn(wr0, J.v11, mul_rn(wl0, Jp.v11)));
                 }
             }
         }
         if (j0 < J0b && colv) {
             // the kept fine plane of coarse plane j0
-            const long long pb = r.pbk;
             T *orow = out + ((long long)P0 * m1 + Ra) * m2;
             orow[Ca] = J.v00;
-            if (hb) orow[Ca + 1] = add_rn(value(r.k01, pb + kro0 + (Ca >> 1)), J.v01);
+            if (hb) orow[Ca + 1] = add_rn(val(r.k01, b, 4), J.v01);
             if (hr) {
                 orow += m2;
-                orow[Ca] = add_rn(value(r.k10, pb + kro1 + Ca), J.v10);
-                if (hb) orow[Ca + 1] = add_rn(value(r.k11, pb + kro1 + Ca + 1), J.v11);
+                orow[Ca] = add_rn(val(r.k10, b, 5), J.v10);
+                if (hb) orow[Ca + 1] = add_rn(val(r.k11, b, 6), J.v11);
             }
         }
         Jp = J;
+        // this plane's registers take the plane after next
+        if (j0 + 2 <= jend) cur = load(j0 + 2);
+    };
+    Raw A = load(J0a);
+    Raw B;
+    if (J0a + 1 <= jend) B = load(J0a + 1);
+    pend = issue_esc(A, 0);
+    for (int j0 = J0a; j0 <= jend; j0 += 2) {
+        step(j0, A, B, 0);
+        if (j0 + 1 > jend) break;
+        step(j0 + 1, B, A, 1);
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
+
 
 }  // namespace
 
@@ -1116,14 +1230,15 @@ cudaError_t launch_expand_planes(WSrc src, const LevelGeom<T> &g, const T *vc, c
     const int mc0 = g.dim[0].mc, mc1 = g.dim[1].mc, mc2 = g.dim[2].mc;
     const int gx = (mc2 + 31) / 32, gy = (mc1 + XW - 1) / XW;
     const bool stream = src == WSrc::STREAM;
+    const size_t sm = stream ? 0 : (size_t)2 * XTHREADS * 7 * sizeof(long long);   // escape slots
     const int per_sm = stream ? resident_ctas(expand_kernel<T, (int)WSrc::STREAM>, XTHREADS, 0)
-                              : resident_ctas(expand_kernel<T, (int)WSrc::SYMBOLS>, XTHREADS, 0);
+                              : resident_ctas(expand_kernel<T, (int)WSrc::SYMBOLS>, XTHREADS, sm);
     const int seg = choose_segment(mc0, (long long)gx * gy, per_sm);
     const int gz = (mc0 + seg - 1) / seg;
     if (stream)
         expand_kernel<T, (int)WSrc::STREAM><<<dim3(gx, gy, gz), XTHREADS, 0, s>>>(g, vc, coef_in, symin, out, seg);
     else
-        expand_kernel<T, (int)WSrc::SYMBOLS><<<dim3(gx, gy, gz), XTHREADS, 0, s>>>(g, vc, coef_in, symin, out, seg);
+        expand_kernel<T, (int)WSrc::SYMBOLS><<<dim3(gx, gy, gz), XTHREADS, sm, s>>>(g, vc, coef_in, symin, out, seg);
     count_launch();
     return cudaGetLastError();
 }
