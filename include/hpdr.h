@@ -148,6 +148,33 @@ hpdr_status hpdr_compress_coords(hpdr_ctx *ctx, const void *d_in, hpdr_dtype dty
 hpdr_status hpdr_decompress(hpdr_ctx *ctx, const void *d_in, size_t in_bytes, void *d_out,
                             size_t out_capacity, void *stream);
 
+/* Compression and decompression that never wait on the host, so that a
+ * caller can queue many of them back to back (the paper's host-device
+ * execution model keeps the device fed, Sec. V-A).  Both return once
+ * everything is queued on `stream`; errors found on the host (arguments,
+ * allocation) are returned as usual, errors found on the device only through
+ * d_result, a device array written when the stream reaches the end of the
+ * call: 0 means success, otherwise a device status code that
+ * hpdr_device_status maps to an hpdr_status.  A call may synchronize the
+ * device once, when its context's workspace has to grow.
+ *
+ * hpdr_compress_async: as hpdr_compress (unit spacing); d_result holds two
+ *   uint64 values, {container bytes, device status}, 8-byte aligned.
+ * hpdr_decompress_async: the container at d_in (in_capacity readable bytes)
+ *   is decoded with its header parsed on the device.  The caller passes the
+ *   dtype, ndim, dims and cfg the container was compressed with; a header that
+ *   disagrees with them, fails its CRC, or carries node coordinates gives the
+ *   FORMAT status and leaves d_out undefined.  d_result: one uint64 (status).
+ *   out_capacity must hold the field (HPDR_ERR_CAPACITY otherwise). */
+hpdr_status hpdr_compress_async(hpdr_ctx *ctx, const void *d_in, hpdr_dtype dtype, int ndim, const size_t *dims,
+                                double tol, hpdr_tol_kind tol_kind, hpdr_mode mode, const hpdr_config *cfg,
+                                void *d_out, size_t out_capacity, uint64_t *d_result, void *stream);
+hpdr_status hpdr_decompress_async(hpdr_ctx *ctx, const void *d_in, size_t in_capacity, hpdr_dtype dtype, int ndim,
+                                  const size_t *dims, const hpdr_config *cfg, void *d_out, size_t out_capacity,
+                                  uint64_t *d_result, void *stream);
+/* The hpdr_status of a device status code (d_result of the calls above). */
+hpdr_status hpdr_device_status(uint64_t code);
+
 /* Read the shape and type of a container held in host or device memory
  * (detected).  dims receives ndim entries (3 slots must be provided). */
 hpdr_status hpdr_inspect(const void *in, size_t in_bytes, hpdr_dtype *dtype, int *ndim,

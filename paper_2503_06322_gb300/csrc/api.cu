@@ -96,6 +96,7 @@ struct Ws {
     unsigned long long *chunk_bits;
     unsigned long long *bsum;
     void *huff;
+    DevHdr *dh;   // a container header parsed on the device
 };
 
 size_t carve_ws(void *base, const Plan *P, size_t esz, unsigned D, unsigned K, bool need_sym, Ws *w)
@@ -115,6 +116,7 @@ size_t carve_ws(void *base, const Plan *P, size_t esz, unsigned D, unsigned K, b
     w->chunk_bits = c.take<unsigned long long>(nch + 2);
     w->bsum = c.take<unsigned long long>(1024);
     w->huff = c.take<char>(huff_scratch_bytes(D));
+    w->dh = c.take<DevHdr>(1);
     return c.used + 256;
 }
 
@@ -469,6 +471,60 @@ __global__ void accumulate_status_kernel(const Scalars *sc, unsigned *acc)
 
 // err_acc == null: synchronize and report this call's status; otherwise the
 // call is left in flight and its status OR-ed into *err_acc on the device
+// the levels of one decompression, after its symbols are decoded (Sec. IV-A:
+// the inverse of Alg. 1 -- dequantization, mass_trans, tridiag and the
+// correction, then the interpolation up to the next level)
+template <typename T>
+hpdr_status decompress_levels(hpdr_ctx *ctx, const Plan *P, unsigned D, unsigned long long N, const Ws &w, T *out,
+                              cudaStream_t s)
+{
+    const int L = P->L;
+    SymIn si;
+    si.sym = w.sym; si.D = D; si.sc = w.sc; si.esc = w.esc;
+    si.status = &w.sc->status;
+    // level buffers: v_{l-1} in X, v_l written to Y (or to out at l = L)
+    T *bufs[2] = {(T *)w.va, (T *)w.vb};
+    const LevelGeom<T> *geo = &geom<T>(P, 0);
+    const int ls = coarse_top<T>(P, geo);
+    T *v;
+    if (ls >= 1) {
+        // levels 0..ls in one CTA, level ls written where level ls + 1 reads it
+        v = (ls == L) ? out : bufs[ls % 2];
+        ProfScope ps(ctx, "d_coarse", s);
+        QuantOut none;
+        memset(&none, 0, sizeof(none));
+        CK(launch_coarse<T>(2, P, geo, ls, nullptr, v, none, nullptr, si, nullptr, s));
+    } else {
+        v = L == 0 ? out : bufs[0];
+        CK(launch_level0_in<T>(WSrc::SYMBOLS, nullptr, si, P->N[0], v, s));
+    }
+    for (int l = ls + 1; l <= L; l++) {
+        const LevelGeom<T> &g = geom<T>(P, l);
+        RestrictArgs<T> a;
+        memset(&a, 0, sizeof(a));
+        a.g = g;
+        a.symin = si;
+        a.src_end = w.sym + N + 8;
+        a.status = &w.sc->status;
+        a.b = (T *)w.b;
+        {
+        ProfScope ps(ctx, l == L ? "d_restrict_sym_L" : kLevelName[2][l], s);
+        CK(launch_restrict<T>(WSrc::SYMBOLS, Sink::NONE, a, s));
+        }
+        {
+        ProfScope ps(ctx, l == L ? "d_solves_L" : kLevelName[3][l], s);
+        CK(launch_solves<T>(g, (T *)w.b, v, -1, s));
+        }
+        T *dst = (l == L) ? out : bufs[l % 2];
+        {
+        ProfScope ps(ctx, l == L ? "d_expand_L" : kLevelName[4][l], s);
+        CK(launch_expand<T>(WSrc::SYMBOLS, g, v, nullptr, si, dst, s));
+        }
+        v = dst;
+    }
+    return HPDR_OK;
+}
+
 template <typename T>
 hpdr_status decompress_t(hpdr_ctx *ctx, const Plan *P, const Hdr &h, const uint8_t *in, T *out,
                          cudaStream_t s, unsigned *err_acc = nullptr)
@@ -507,49 +563,8 @@ hpdr_status decompress_t(hpdr_ctx *ctx, const Plan *P, const Hdr &h, const uint8
     ProfScope ps(ctx, "d_decode", s);
     CK(launch_decode(da, hs, s));
     }
-    SymIn si;
-    si.sym = w.sym; si.D = h.D; si.sc = w.sc; si.esc = w.esc;
-    si.status = &w.sc->status;
-    // level buffers: v_{l-1} in X, v_l written to Y (or to out at l = L)
-    T *bufs[2] = {(T *)w.va, (T *)w.vb};
-    const LevelGeom<T> *geo = &geom<T>(P, 0);
-    const int ls = coarse_top<T>(P, geo);
-    T *v;
-    if (ls >= 1) {
-        // levels 0..ls in one CTA, level ls written where level ls + 1 reads it
-        v = (ls == L) ? out : bufs[ls % 2];
-        ProfScope ps(ctx, "d_coarse", s);
-        QuantOut none;
-        memset(&none, 0, sizeof(none));
-        CK(launch_coarse<T>(2, P, geo, ls, nullptr, v, none, nullptr, si, nullptr, s));
-    } else {
-        v = L == 0 ? out : bufs[0];
-        CK(launch_level0_in<T>(WSrc::SYMBOLS, nullptr, si, P->N[0], v, s));
-    }
-    for (int l = ls + 1; l <= L; l++) {
-        const LevelGeom<T> &g = geom<T>(P, l);
-        RestrictArgs<T> a;
-        memset(&a, 0, sizeof(a));
-        a.g = g;
-        a.symin = si;
-        a.src_end = w.sym + h.N + 8;
-        a.status = &w.sc->status;
-        a.b = (T *)w.b;
-        {
-        ProfScope ps(ctx, l == L ? "d_restrict_sym_L" : kLevelName[2][l], s);
-        CK(launch_restrict<T>(WSrc::SYMBOLS, Sink::NONE, a, s));
-        }
-        {
-        ProfScope ps(ctx, l == L ? "d_solves_L" : kLevelName[3][l], s);
-        CK(launch_solves<T>(g, (T *)w.b, v, -1, s));
-        }
-        T *dst = (l == L) ? out : bufs[l % 2];
-        {
-        ProfScope ps(ctx, l == L ? "d_expand_L" : kLevelName[4][l], s);
-        CK(launch_expand<T>(WSrc::SYMBOLS, g, v, nullptr, si, dst, s));
-        }
-        v = dst;
-    }
+    st = decompress_levels<T>(ctx, P, h.D, h.N, w, out, s);
+    if (st != HPDR_OK) return st;
     if (err_acc) {
         accumulate_status_kernel<<<1, 1, 0, s>>>(w.sc, err_acc);
         count_launch();
@@ -559,6 +574,140 @@ hpdr_status decompress_t(hpdr_ctx *ctx, const Plan *P, const Hdr &h, const uint8
     CK(cudaMemcpyAsync(hsc, w.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (hsc->status) return map_device_status(hsc->status);
+    return HPDR_OK;
+}
+
+// ----- container header parsed on the device ---------------------------------
+// The checks of parse_header, plus agreement with the shape, type and
+// dictionary the caller expects; a failure sets DS_FORMAT, and every later
+// kernel of the decompression skips or computes on stale (in-bounds) data.
+struct HdrExpect {
+    int dtype, ndim, L;
+    unsigned long long dims[3], N;
+    unsigned D, K;
+};
+
+__device__ uint32_t crc32_dev(const uint8_t *p, int n)
+{
+    uint32_t c = 0xFFFFFFFFu;
+    for (int i = 0; i < n; i++) {
+        c ^= p[i];
+        for (int b = 0; b < 8; b++) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
+    }
+    return c ^ 0xFFFFFFFFu;
+}
+__device__ uint32_t rd32d(const uint8_t *p) { uint32_t v = 0; for (int i = 0; i < 4; i++) v |= (uint32_t)p[i] << (8 * i); return v; }
+__device__ uint64_t rd64d(const uint8_t *p) { uint64_t v = 0; for (int i = 0; i < 8; i++) v |= (uint64_t)p[i] << (8 * i); return v; }
+__device__ unsigned long long a16d(unsigned long long x) { return (x + 15) & ~15ULL; }
+
+__global__ void hdr_parse_kernel(const uint8_t *b, unsigned long long in_bytes, HdrExpect ex, DevHdr *dh, Scalars *sc)
+{
+    unsigned char *z = reinterpret_cast<unsigned char *>(sc);
+    for (unsigned i = threadIdx.x; i < sizeof(Scalars); i += blockDim.x) z[i] = 0;
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool g = in_bytes >= 128;
+        if (g) g = b[0] == 'H' && b[1] == 'P' && b[2] == 'D' && b[3] == 'R' && rd32d(b + 4) == 3u;
+        if (g) g = crc32_dev(b, 124) == rd32d(b + 124);
+        DevHdr h;
+        h.pad = 0;
+        if (g) {
+            g = (int)rd32d(b + 8) == ex.dtype && (int)rd32d(b + 12) == ex.ndim && (int)rd32d(b + 40) == ex.L &&
+                rd32d(b + 48) <= 1u && rd32d(b + 52) == ex.D && rd32d(b + 56) == ex.K && rd64d(b + 96) == ex.N;
+            for (int k = 0; k < 3; k++) g = g && rd64d(b + 16 + 8 * k) == ex.dims[k];
+        }
+        if (g) {
+            h.s_lo = rd32d(b + 60);
+            h.n_esc = rd64d(b + 104);
+            h.total_bits = rd64d(b + 112);
+            const uint32_t w120 = rd32d(b + 120);
+            h.s_hi = w120 & 0xFFFFu;
+            h.esc_w = (w120 >> 16) & 0xFFu;
+            g = (w120 >> 24) == 0u && h.s_hi < ex.D && h.s_lo <= h.s_hi && h.n_esc <= ex.N && h.esc_w <= 63u &&
+                ((h.n_esc > 0) == (h.esc_w > 0)) && h.total_bits >= ex.N &&
+                h.total_bits <= 63ULL * ex.N + (unsigned long long)h.esc_w * h.n_esc;
+        }
+        if (g) {
+            const unsigned long long nch = (ex.N + ex.K - 1) / ex.K;
+            h.nwords = (h.total_bits + 31) / 32;
+            h.off_len = a16d(128 + 8ULL * (ex.L + 1));
+            h.off_chunk = a16d(h.off_len + (h.s_hi - h.s_lo + 1));
+            h.off_bits = a16d(h.off_chunk + 8 * nch);
+            g = h.off_bits + 4 * h.nwords <= in_bytes;
+        }
+        if (g)
+            for (int l = 0; l <= ex.L; l++) {
+                const double q = __longlong_as_double((long long)rd64d(b + 128 + 8 * l));
+                if (!(q > 0.0) || !isfinite(q)) g = false;
+            }
+        if (g) {
+            *dh = h;
+            sc->n_esc = h.n_esc;
+            sc->total_bits = h.total_bits;
+        } else {
+            sc->status = (unsigned)DS_FORMAT;
+        }
+        ok = g ? 1 : 0;
+    }
+    __syncthreads();
+    if (!ok) return;
+    for (int l = threadIdx.x; l <= ex.L; l += blockDim.x) {
+        const double q = __longlong_as_double((long long)rd64d(b + 128 + 8 * l));
+        sc->q[l] = q;
+        sc->q_f[l] = __double2float_rn(q);
+        sc->rho_d[l] = 1.0 / q;
+        sc->rho_f[l] = __double2float_rn(1.0 / q);
+        sc->rho_lo[l] = __double2float_rn(sc->rho_d[l] - (double)sc->rho_f[l]);
+    }
+}
+
+// {status} of one call into a device word
+__global__ void status_out_kernel(const Scalars *sc, unsigned long long *dst) { dst[0] = sc->status; }
+
+// decompression whose header is read on the device: no host wait
+template <typename T>
+hpdr_status decompress_dev(hpdr_ctx *ctx, const Plan *P, int dtype, int ndim, const size_t *dims, unsigned D,
+                           unsigned K, const uint8_t *in, size_t in_bytes, T *out, unsigned long long *d_result,
+                           cudaStream_t s)
+{
+    K = chunk_of(K, (unsigned long long)P->N[P->L]);
+    Ws w;
+    size_t need = carve_ws(nullptr, P, sizeof(T), D, K, true, &w);
+    hpdr_status st = ensure_workspace(ctx, need);
+    if (st != HPDR_OK) return st;
+    carve_ws(ctx->ws.base, P, sizeof(T), D, K, true, &w);
+    HdrExpect ex;
+    memset(&ex, 0, sizeof(ex));
+    ex.dtype = dtype;
+    ex.ndim = ndim;
+    ex.L = P->L;
+    for (int k = 0; k < 3; k++) ex.dims[k] = k < ndim ? dims[k] : 1;
+    ex.N = (unsigned long long)P->N[P->L];
+    ex.D = D;
+    ex.K = K;
+    hdr_parse_kernel<<<1, 256, 0, s>>>(in, in_bytes, ex, w.dh, w.sc);
+    count_launch();
+    CK(cudaGetLastError());
+    HuffScratch hs;
+    huff_scratch_carve(w.huff, D, w.sc, &hs);
+    {
+    ProfScope ps(ctx, "d_tables", s);
+    CK(launch_decode_tables_dev(in, w.dh, D, hs, s));
+    }
+    DecodeArgs da;
+    da.words = nullptr; da.nwords = 0; da.chunk = nullptr; da.total_bits = 0; da.esc_w = 0;
+    da.N = ex.N; da.K = K; da.sym = w.sym; da.esc = w.esc;
+    da.base = in; da.dh = w.dh;
+    {
+    ProfScope ps(ctx, "d_decode", s);
+    CK(launch_decode(da, hs, s));
+    }
+    st = decompress_levels<T>(ctx, P, D, ex.N, w, out, s);
+    if (st != HPDR_OK) return st;
+    status_out_kernel<<<1, 1, 0, s>>>(w.sc, d_result);
+    count_launch();
+    CK(cudaGetLastError());
     return HPDR_OK;
 }
 
@@ -1069,6 +1218,64 @@ hpdr_status hpdr_decompress(hpdr_ctx *ctx, const void *d_in, size_t in_bytes, vo
     if (st != HPDR_OK) return st;
     if (h.dtype == 0) return decompress_t<float>(ctx, P, h, (const uint8_t *)d_in, (float *)d_out, s);
     return decompress_t<double>(ctx, P, h, (const uint8_t *)d_in, (double *)d_out, s);
+}
+
+hpdr_status hpdr_compress_async(hpdr_ctx *ctx, const void *d_in, hpdr_dtype dtype, int ndim, const size_t *dims,
+                                double tol, hpdr_tol_kind tol_kind, hpdr_mode mode, const hpdr_config *cfg,
+                                void *d_out, size_t out_capacity, uint64_t *d_result, void *stream)
+{
+    unsigned D, K;
+    if (!ctx || !d_in || !d_out || !d_result || !dims || !valid_cfg(cfg, D, K)) return HPDR_ERR_ARG;
+    if ((dtype != HPDR_F32 && dtype != HPDR_F64) || (mode != HPDR_LINF && mode != HPDR_L2 && mode != HPDR_L2_STAT) ||
+        (tol_kind != HPDR_ABS && tol_kind != HPDR_REL) || !(tol > 0.0) || !std::isfinite(tol))
+        return HPDR_ERR_ARG;
+    if (((uintptr_t)d_in & 15) || ((uintptr_t)d_out & 15) || ((uintptr_t)d_result & 7)) return HPDR_ERR_ARG;
+    DevGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Plan *P;
+    hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P);
+    if (st != HPDR_OK) return st;
+    K = chunk_of(K, (unsigned long long)P->N[P->L]);
+    Ws w;
+    size_t need = carve_ws(nullptr, P, dtype == HPDR_F64 ? 8 : 4, D, K, true, &w);
+    st = ensure_workspace(ctx, need);
+    if (st != HPDR_OK) return st;
+    carve_ws(ctx->ws.base, P, dtype == HPDR_F64 ? 8 : 4, D, K, true, &w);
+    if (dtype == HPDR_F32)
+        st = compress_core<float>(ctx, P, (const float *)d_in, ndim, dims, tol, tol_kind, mode, D, K,
+                                  (uint8_t *)d_out, out_capacity, w, s);
+    else
+        st = compress_core<double>(ctx, P, (const double *)d_in, ndim, dims, tol, tol_kind, mode, D, K,
+                                   (uint8_t *)d_out, out_capacity, w, s);
+    if (st != HPDR_OK) return st;
+    size_status_kernel<<<1, 1, 0, s>>>(w.sc, (unsigned long long *)d_result);
+    count_launch();
+    CK(cudaGetLastError());
+    return HPDR_OK;
+}
+
+hpdr_status hpdr_device_status(uint64_t code) { return map_device_status((unsigned)code); }
+
+hpdr_status hpdr_decompress_async(hpdr_ctx *ctx, const void *d_in, size_t in_capacity, hpdr_dtype dtype, int ndim,
+                                  const size_t *dims, const hpdr_config *cfg, void *d_out, size_t out_capacity,
+                                  uint64_t *d_result, void *stream)
+{
+    unsigned D, K;
+    if (!ctx || !d_in || !d_out || !d_result || !dims || !valid_cfg(cfg, D, K)) return HPDR_ERR_ARG;
+    if ((dtype != HPDR_F32 && dtype != HPDR_F64) || ((uintptr_t)d_in & 15) || ((uintptr_t)d_result & 7))
+        return HPDR_ERR_ARG;
+    DevGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Plan *P;
+    hpdr_status st = get_plan(ctx, ndim, dims, dtype == HPDR_F64, &P);
+    if (st != HPDR_OK) return st;
+    const size_t esz = dtype == HPDR_F64 ? 8 : 4;
+    if (out_capacity < (size_t)P->N[P->L] * esz) return HPDR_ERR_CAPACITY;
+    if (dtype == HPDR_F32)
+        return decompress_dev<float>(ctx, P, 0, ndim, dims, D, K, (const uint8_t *)d_in, in_capacity, (float *)d_out,
+                                     (unsigned long long *)d_result, s);
+    return decompress_dev<double>(ctx, P, 1, ndim, dims, D, K, (const uint8_t *)d_in, in_capacity, (double *)d_out,
+                                  (unsigned long long *)d_result, s);
 }
 
 hpdr_status hpdr_decompose(hpdr_ctx *ctx, const void *d_u, void *d_coef, hpdr_dtype dtype,

@@ -689,8 +689,16 @@ __global__ void __launch_bounds__(1024, 1) codebook_kernel(const unsigned long l
 // symbol of the alphabet absent), one block of 1024 threads: counts,
 // canonical tables, the (length, symbol) order of the symbols.
 __global__ void __launch_bounds__(1024, 1) dec_tables_kernel(const uint8_t *lenb, unsigned s_lo, unsigned s_hi,
-                                                             unsigned D, HuffScratch hs)
+                                                             unsigned D, HuffScratch hs, const uint8_t *base,
+                                                             const DevHdr *dh)
 {
+    if (dh) {
+        // a header parsed on the device (and rejected there: nothing to build)
+        if (block_skip(hs.status)) return;
+        lenb = base + dh->off_len;
+        s_lo = dh->s_lo;
+        s_hi = dh->s_hi;
+    }
     extern __shared__ __align__(16) unsigned char tsm[];
     unsigned *wc = reinterpret_cast<unsigned *>(tsm);                        // [32 * kWcStride]
     uint8_t *lens = tsm + 4 * 32 * kWcStride;                                // [D]
@@ -1233,8 +1241,19 @@ __device__ __forceinline__ unsigned long long window64(const uint32_t *w, unsign
     return sh ? (hi << sh) | (ldw(w, i + 2, n) >> (32 - sh)) : hi;
 }
 
-__global__ void __launch_bounds__(kDecThreads, 1) decode_kernel(DecodeArgs a, HuffScratch hs)
+__global__ void __launch_bounds__(kDecThreads, 1) decode_kernel(DecodeArgs a_in, HuffScratch hs)
 {
+    DecodeArgs a = a_in;
+    if (a.dh) {
+        if (block_skip(hs.status)) return;
+        const DevHdr h = *a.dh;
+        a.words = reinterpret_cast<const uint32_t *>(a.base + h.off_bits);
+        a.nwords = h.nwords;
+        a.chunk = reinterpret_cast<const unsigned long long *>(a.base + h.off_chunk);
+        a.total_bits = h.total_bits;
+        a.esc_w = h.esc_w;
+        if (h.esc_w == 0) a.esc = nullptr;
+    }
     extern __shared__ __align__(16) unsigned char dsm[];
     uint32_t *lut = reinterpret_cast<uint32_t *>(dsm);                                      // [1 << kLenBits]
     unsigned long long *sfirst = reinterpret_cast<unsigned long long *>(dsm + (4u << kLenBits));  // [64]
@@ -1581,7 +1600,18 @@ cudaError_t launch_decode_tables(const uint8_t *lenb, unsigned int s_lo, unsigne
 {
     cudaError_t e = set_attrs();
     if (e != cudaSuccess) return e;
-    dec_tables_kernel<<<1, 1024, 4 * 32 * kWcStride + D, s>>>(lenb, s_lo, s_hi, D, hs);
+    dec_tables_kernel<<<1, 1024, 4 * 32 * kWcStride + D, s>>>(lenb, s_lo, s_hi, D, hs, nullptr, nullptr);
+    lut15_kernel<<<(1u << kLenBits) / 256, 256, 0, s>>>(hs);
+    count_launch(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decode_tables_dev(const uint8_t *base, const DevHdr *dh, unsigned int D, const HuffScratch &hs,
+                                     cudaStream_t s)
+{
+    cudaError_t e = set_attrs();
+    if (e != cudaSuccess) return e;
+    dec_tables_kernel<<<1, 1024, 4 * 32 * kWcStride + D, s>>>(nullptr, 0u, 0u, D, hs, base, dh);
     lut15_kernel<<<(1u << kLenBits) / 256, 256, 0, s>>>(hs);
     count_launch(2);
     return cudaGetLastError();

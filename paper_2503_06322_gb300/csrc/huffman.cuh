@@ -42,6 +42,14 @@ struct HuffScratch {
     unsigned int *status;         // -> Scalars::status
     unsigned int *s_lo, *s_hi;    // -> Scalars
 };
+// The header fields that locate a container's sections, parsed on the device
+// (a decompression that does not read the header back to the host).
+struct DevHdr {
+    unsigned long long off_len, off_chunk, off_bits;   // byte offsets of the sections
+    unsigned long long nwords, total_bits, n_esc;
+    unsigned int s_lo, s_hi, esc_w, pad;
+};
+
 size_t huff_scratch_bytes(unsigned int D);
 void huff_scratch_carve(void *base, unsigned int D, Scalars *sc, HuffScratch *hs);
 
@@ -52,6 +60,9 @@ cudaError_t launch_codebook(const unsigned long long *hist, unsigned int D, cons
 // symbols s_lo..s_hi (device bytes; every other symbol absent), decoder side.
 cudaError_t launch_decode_tables(const uint8_t *lenb, unsigned int s_lo, unsigned int s_hi, unsigned int D,
                                  const HuffScratch &hs, cudaStream_t s);
+// the same with the length table located through a device-parsed header
+cudaError_t launch_decode_tables_dev(const uint8_t *base, const DevHdr *dh, unsigned int D, const HuffScratch &hs,
+                                     cudaStream_t s);
 
 // Encoder.  Layout of the destination: chunk table at chunk_out, bitstream at
 // words (both device pointers, possibly inside a container whose offsets are
@@ -102,6 +113,10 @@ struct DecodeArgs {
     uint16_t *sym;
     long long *esc;                   // null: plain symbols; else receives k of every escape
     unsigned int esc_w;               // payload width of the escapes
+    // non-null: words, nwords, chunk, total_bits and esc_w come from this
+    // device-parsed header of the container at base (esc_w 0: no escapes)
+    const uint8_t *base = nullptr;
+    const DevHdr *dh = nullptr;
 };
 cudaError_t launch_decode(const DecodeArgs &a, const HuffScratch &hs, cudaStream_t s);
 cudaError_t launch_histogram(const uint16_t *sym, unsigned long long N, unsigned D,

@@ -88,6 +88,11 @@ def lib():
             "hpdr_huffman_decode": [vp, vp, C.c_uint64, vp, C.c_uint64, C.c_uint32, C.c_uint32,
                                     vp, vp, vp],
             "hpdr_decompose_noalloc": [vp, vp, C.c_int, C.c_int, sz, vp],
+            "hpdr_compress_async": [vp, vp, C.c_int, C.c_int, sz, C.c_double, C.c_int, C.c_int,
+                                    C.POINTER(Config), vp, C.c_size_t, vp, vp],
+            "hpdr_decompress_async": [vp, vp, C.c_size_t, C.c_int, C.c_int, sz, C.POINTER(Config), vp,
+                                      C.c_size_t, vp, vp],
+            "hpdr_device_status": [C.c_uint64],
             "hpdr_compress_host_streamed": [vp, vp, C.c_int, C.c_int, sz, C.c_double, C.c_int, C.c_int,
                                             C.POINTER(Config), C.c_size_t, vp, C.c_size_t, sz],
             "hpdr_decompress_host_streamed": [vp, vp, C.c_size_t, vp, C.c_size_t],
@@ -218,6 +223,38 @@ def hpdr_compress(u, tol, tol_kind=REL, mode=LINF, dict_size=8192, chunk=0, out=
                                       C.byref(cfg), C.c_void_p(out.data_ptr()), out.numel(), C.byref(nb),
                                       _stream(stream)), "hpdr_compress")
     return out[:nb.value]
+
+
+def hpdr_compress_async(u, tol, out, result, tol_kind=REL, mode=LINF, dict_size=8192, chunk=0, stream=None):
+    """Queue a compression without any host wait: `out` (uint8 CUDA tensor of
+    at least hpdr_compress_bound bytes) receives the container, `result` (int64
+    CUDA tensor of 2) receives {container bytes, device status} when the stream
+    gets there."""
+    _dev_tensor(u, "u")
+    nd, dims = _dims(u.shape)
+    cfg = _cfg(dict_size, chunk)
+    _check(lib().hpdr_compress_async(context(u.device.index), C.c_void_p(u.data_ptr()), _dtype_code(u.dtype), nd, dims,
+                                     float(tol), int(tol_kind), int(mode), C.byref(cfg), C.c_void_p(out.data_ptr()),
+                                     out.numel(), C.c_void_p(result.data_ptr()), _stream(stream)),
+           "hpdr_compress_async")
+
+
+def hpdr_decompress_async(buf, out, result, dict_size=8192, chunk=0, stream=None):
+    """Queue a decompression whose header is parsed on the device: `out` has
+    the field's shape and type (they must match the container), `result`
+    (int64 CUDA tensor of 1) receives the device status."""
+    _dev_tensor(buf, "buf")
+    nd, dims = _dims(out.shape)
+    cfg = _cfg(dict_size, chunk)
+    _check(lib().hpdr_decompress_async(context(buf.device.index), C.c_void_p(buf.data_ptr()), buf.numel(),
+                                       _dtype_code(out.dtype), nd, dims, C.byref(cfg), C.c_void_p(out.data_ptr()),
+                                       out.numel() * out.element_size(), C.c_void_p(result.data_ptr()),
+                                       _stream(stream)), "hpdr_decompress_async")
+
+
+def device_status(code):
+    """hpdr_status of a device status code (0: ok)."""
+    return lib().hpdr_device_status(int(code))
 
 
 def hpdr_inspect(buf):
