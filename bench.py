@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--no-l2s", action="store_true", help="skip the statistical L2 mode leg")
     ap.add_argument("--no-zfp", action="store_true", help="skip the fixed-rate ZFP leg")
     ap.add_argument("--no-coords", action="store_true", help="skip the non-uniform grid leg")
+    ap.add_argument("--no-bounds", action="store_true",
+                    help="skip the legs at the other bounds (1e-2, 1e-4) and the 500x500x100 FP64 field")
     return ap.parse_args()
 
 
@@ -570,6 +572,56 @@ def run_stream(args, dev):
             "fixed_256MiB": fixed, "adaptive_alg4": adaptive, "whole_field_ratio": round(fb / whole, 4)}
 
 
+def run_bounds(args, u):
+    """The scale workload's other measured points: the timed field at relative
+    Linf 1e-2 and 1e-4, and a 500 x 500 x 100 FP64 power-law field (seed 2) at
+    1e-3; compress + decompress through the asynchronous calls."""
+    import numpy as np
+    import torch
+    from paper_2503_06322_gb300 import fields, hpdr
+    dev = u.device
+
+    def leg(x, tol, steps=10):
+        cap = hpdr.hpdr_compress_bound(tuple(x.shape), x.dtype)
+        cbuf = torch.empty(cap, dtype=torch.uint8, device=dev)
+        rec = torch.empty_like(x)
+        rc = torch.zeros((steps + 3, 2), dtype=torch.int64, device=dev)
+        rd = torch.zeros((steps + 3, 1), dtype=torch.int64, device=dev)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        for i in range(3):
+            hpdr.hpdr_compress_async(x, tol, cbuf, rc[i])
+            hpdr.hpdr_decompress_async(cbuf, rec, rd[i])
+        tc = td = 0.0
+        for i in range(steps):
+            e[0].record()
+            hpdr.hpdr_compress_async(x, tol, cbuf, rc[3 + i])
+            e[1].record()
+            hpdr.hpdr_decompress_async(cbuf, rec, rd[3 + i])
+            e[2].record()
+            torch.cuda.synchronize()
+            tc += e[0].elapsed_time(e[1])
+            td += e[1].elapsed_time(e[2])
+        if int((rc[:, 1] != 0).sum()) or int((rd[:, 0] != 0).sum()):
+            return {"error": "device status"}
+        nb = x.numel() * x.element_size()
+        tau = tol * x.abs().max().item()
+        return {"compress_gbs": round(nb / (tc / steps * 1e-3) / 1e9, 2),
+                "decompress_gbs": round(nb / (td / steps * 1e-3) / 1e9, 2),
+                "gbs": round(2 * nb / ((tc + td) / steps * 1e-3) / 1e9, 2),
+                "compression_ratio": round(nb / int(rc[3, 0]), 4),
+                "max_err_over_tau": round((rec - x).abs().max().item() / tau, 4)}
+
+    res = {"workload": "the timed field at relative Linf 1e-2 and 1e-4; 500x500x100 FP64 power-law field (seed 2) "
+                       "at 1e-3; compress + decompress, device-resident"}
+    for tol in (1e-2, 1e-4):
+        res["tol_%g" % tol] = leg(u, tol)
+    f64 = torch.from_numpy(fields.powerlaw_field((500, 500, 100), seed=2, dtype=np.float64)).to(dev)
+    res["fp64_500x500x100"] = leg(f64, 1e-3)
+    del f64
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_l2s(args, u):
     """The timed workload in statistical L2 mode (bins bounding the expected
     RMS error by tau = tol * rms(u)) beside the max-norm bins of the headline:
@@ -852,6 +904,11 @@ def main():
     del cbuf
     if rank == 0 and not args.no_adjoint:
         out["adjoint"] = run_adjoint(args, u.device)
+    if rank == 0 and not args.no_bounds:
+        try:
+            out["bounds"] = run_bounds(args, u)
+        except Exception as exc:       # a side leg never stops the headline line
+            out["bounds"] = {"error": "%s: %s" % (type(exc).__name__, exc)}
     if rank == 0 and not args.no_l2s:
         out["l2_stat"] = run_l2s(args, u)
     if rank == 0 and not args.no_zfp:
