@@ -39,6 +39,8 @@ def parse_args():
     ap.add_argument("--shape", default="513,513,513")
     ap.add_argument("--tol", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--dtype", choices=["f32", "f64"], default="f32",
+                    help="element type of the timed field (f64 for profiling the FP64 path)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-to-host leg")
     ap.add_argument("--cpu-planes", type=int, default=257,
@@ -56,9 +58,9 @@ def parse_args():
     return ap.parse_args()
 
 
-def workload_name(shape, tol):
-    return "%s FP32 power-law field (|k|^-11/3), rel Linf %g, compress+decompress" % (
-        "x".join(str(s) for s in shape), tol)
+def workload_name(shape, tol, dtype="f32"):
+    return "%s %s power-law field (|k|^-11/3), rel Linf %g, compress+decompress" % (
+        "x".join(str(s) for s in shape), "FP64" if dtype == "f64" else "FP32", tol)
 
 
 # ---------------------------------------------------------------------------
@@ -128,9 +130,9 @@ LEVEL_GROUPS = ("c_restrict_quant_L", "d_restrict_sym_L", "d_expand_L", "c_solve
 
 def source_hash(group="c_restrict_quant_L"):
     """SHA-256 prefix of the sources of a kernel group's translation unit: the
-    level kernels (levels.cu, levels.cuh, internal.cuh) or the Huffman kernels
+    level kernels (levels.cu, decomp.cu, levels.cuh, levels_dev.cuh, internal.cuh) or the Huffman kernels
     (huffman.cu, huffman.cuh, internal.cuh)."""
-    files = (("levels.cu", "levels.cuh", "internal.cuh") if group in LEVEL_GROUPS
+    files = (("levels.cu", "decomp.cu", "levels.cuh", "levels_dev.cuh", "internal.cuh") if group in LEVEL_GROUPS
              else ("huffman.cu", "huffman.cuh", "internal.cuh"))
     h = hashlib.sha256()
     for f in files:
@@ -182,7 +184,8 @@ def run_ours(args, rank, world, local):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     shape = tuple(int(x) for x in args.shape.split(","))
-    u = fields.powerlaw_field_torch(shape, seed=args.seed + rank, device=dev)
+    u = fields.powerlaw_field_torch(shape, seed=args.seed + rank, device=dev,
+                                    dtype=torch.float64 if args.dtype == "f64" else torch.float32)
     nbytes = u.numel() * u.element_size()
     L = hpdr.lib()
     ctx = hpdr.context(local)
@@ -289,7 +292,7 @@ def run_ours(args, rank, world, local):
     best = max((g for g in single if g in groups), key=lambda g: groups[g][0])
     ms_b, cnt_b = groups[best]
     avg_s = ms_b / cnt_b * 1e-3
-    alg = algorithmic_bytes(best, 4, NL, NL1, bits, nch)
+    alg = algorithmic_bytes(best, u.element_size(), NL, NL1, bits, nch)
     peak, peak_kind = measured_peak()
     achieved = alg / avg_s / 1e9
     traffic = ncu_traffic(best)
@@ -303,11 +306,11 @@ def run_ours(args, rank, world, local):
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
         "data": "synthetic (seeded power-law Gaussian random field generated on the device)",
-        "config": {"workload": workload_name(shape, args.tol), "shape": list(shape),
+        "config": {"workload": workload_name(shape, args.tol, args.dtype), "shape": list(shape),
                    "tol": args.tol, "tol_kind": "rel", "mode": "Linf", "dict_size": 8192,
-                   "chunk": kchunk, "l2": "inputs larger than L2 (540 MB field, 129 MB L2)",
+                   "chunk": kchunk, "l2": "inputs larger than L2 (%d MB field, 129 MB L2)" % (nbytes // 10**6),
                    "parallelism": "replicas x%d" % world},
         "compress_gbs": round(nbytes / (tc / nsep * 1e-3) / 1e9, 2),
         "decompress_gbs": round(nbytes / (td / nsep * 1e-3) / 1e9, 2),

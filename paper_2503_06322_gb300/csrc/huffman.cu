@@ -291,67 +291,151 @@ __global__ void __launch_bounds__(256) assign_kernel(HuffScratch hs)
     }
 }
 
-// Decoder table entry of every 15-bit prefix t:
-//   codeword of at most 15 bits:   symbol | L << 16                         (1 <= L <= 15)
-//   longer codewords, one length L: kLongFlag | base | L << 16, where the codeword
-//                                  t r (r = its last L - 15 bits) is symbol
-//                                  sorted_sym[base + r]
-//   longer codewords, lengths Lmin..Lmax:
-//                                  kLongFlag | kMixedFlag | Lmin << 16 | (Lmax - Lmin) << 24
-//                                  (canonical codes grow in length with their value)
+// Decoder table entry of every 13-bit prefix t (P = kLutBits):
+//   codeword of at most P bits:     symbol | L << 16                        (1 <= L <= P)
+//   longer codewords, Lmax <= P + kSubMax, within the second-level budget:
+//                                   kSubFlag | off | (Lmax - P) << 16; the next
+//                                   Lmax - P bits r select lut_sub[off + r], an
+//                                   entry symbol | L << 16 (0: no codeword)
+//   other longer codewords:         kLongFlag | Lmin << 16 | (Lmax - Lmin) << 24
+//                                   (canonical codes grow in length with their value)
 //   no codeword (incomplete code):  0
 constexpr uint32_t kLongFlag = 0x80000000u;
-constexpr uint32_t kMixedFlag = 0x40000000u;
-// decoder copy of a short entry of the escape symbol 0 whose codeword and
-// payload (W bits) together fit 32 bits: L = codeword length + W
+constexpr uint32_t kSubFlag = 0x20000000u;
+// decoder copy of an entry of the escape symbol 0 whose codeword and payload
+// (W bits) together fit 32 bits: L = codeword length + W
 constexpr uint32_t kEscFolded = 0x40000000u;
 
-__device__ __forceinline__ unsigned code_len_at(const HuffScratch &hs, unsigned long long win, int maxL)
+// canonical length tables staged in shared memory
+struct LenTabs {
+    unsigned long long first[64], lim[64];
+    unsigned start[64], count[64];
+};
+
+// length of the canonical codeword at the top of the left-aligned window,
+// known to lie in [lo, hi]: the first length l in [lo, hi) whose limit lim[l]
+// the window stays below, else hi (the limits do not decrease with l, so a
+// binary search finds it)
+__device__ __forceinline__ unsigned code_len_in(const LenTabs &t, unsigned long long win, unsigned lo, unsigned hi)
 {
-    // length of the canonical codeword at the top of the left-aligned window:
-    // one more than the number of shorter lengths whose limit win reaches
-    unsigned L = 1;
-    for (int l = 1; l < maxL; l++) L += (win >= hs.lim[l]) ? 1u : 0u;
-    return L;
+    while (lo < hi) {
+        const unsigned m = (lo + hi) >> 1;
+        if (win >= t.lim[m]) lo = m + 1; else hi = m;
+    }
+    return lo;
 }
 
-__global__ void __launch_bounds__(256) lut15_kernel(HuffScratch hs)
+// symbol | L << 16 of the codeword of length L at the top of the window (0: none)
+__device__ __forceinline__ uint32_t leaf_of(const LenTabs &t, const uint16_t *sorted_sym, unsigned n,
+                                            unsigned long long win, unsigned L)
 {
+    const unsigned long long off = (win >> (64 - L)) - t.first[L];
+    if (off >= t.count[L]) return 0u;
+    const unsigned idx = t.start[L] + (unsigned)off;
+    return idx < n ? ((uint32_t)sorted_sym[idx] | (L << 16)) : 0u;
+}
+
+// One block of 1024 threads, eight consecutive prefixes each.  The
+// second-level tables are laid out in prefix order by a block scan of their
+// sizes; prefixes past the budget keep long entries.  The sorted symbols are
+// staged in shared memory when there are at most kLutSyms of them.
+constexpr int kLutThreads = 1024;
+constexpr unsigned kLutPer = (1u << kLutBits) / kLutThreads;
+constexpr unsigned kLutSyms = 16384;
+constexpr size_t kLutSmem = (4u << kLutBits) + 2 * kLutSyms;
+__global__ void __launch_bounds__(kLutThreads, 1) lut_kernel(HuffScratch hs)
+{
+    __shared__ LenTabs T;
+    __shared__ unsigned wsum[kLutThreads / 32];
+    __shared__ unsigned total;
+    extern __shared__ __align__(16) unsigned char lsm[];
+    uint32_t *ent = reinterpret_cast<uint32_t *>(lsm);                         // [1 << kLutBits]
+    uint16_t *ssym = reinterpret_cast<uint16_t *>(ent + (1u << kLutBits));      // [kLutSyms]
+    const unsigned tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < 64) {
+        T.first[tid] = hs.first[tid];
+        T.lim[tid] = hs.lim[tid];
+        T.start[tid] = hs.start[tid];
+        T.count[tid] = hs.count[tid];
+    }
     const unsigned n = *hs.nsym;
+    const uint16_t *sorted = n <= kLutSyms ? ssym : hs.sorted_sym;
+    if (n <= kLutSyms)
+        for (unsigned i = tid; i < n; i += kLutThreads) ssym[i] = hs.sorted_sym[i];
+    __syncthreads();
     const bool ok = *hs.status == 0;
-    int maxL = 0;
-    for (int l = kMaxCodeLen; l >= 1; l--) if (hs.count[l]) { maxL = l; break; }
-    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < (1u << kLenBits); t += gridDim.x * blockDim.x) {
+    unsigned maxL = 0;
+    for (int l = kMaxCodeLen; l >= 1; l--) if (T.count[l]) { maxL = (unsigned)l; break; }
+    const bool any = ok && maxL;
+    const unsigned t0 = tid * kLutPer;
+    constexpr unsigned long long kTail = (1ULL << (64 - kLutBits)) - 1;
+    unsigned mine = 0;
+    unsigned char sbs[kLutPer];
+#pragma unroll
+    for (unsigned j = 0; j < kLutPer; j++) {
+        const unsigned t = t0 + j;
         uint32_t e = 0;
-        if (ok && maxL) {
+        sbs[j] = 0;
+        if (any) {
             // the codeword whose left-justified range holds t's first bit string;
-            // at most 15 bits long, it is a prefix of every extension of t
-            const unsigned long long w0 = (unsigned long long)t << (64 - kLenBits);
-            const unsigned lmin = code_len_at(hs, w0, maxL);
-            if (lmin <= (unsigned)kLenBits) {
-                const unsigned long long off = (unsigned long long)(t >> (kLenBits - lmin)) - hs.first[lmin];
-                if (off < hs.count[lmin]) {
-                    const unsigned idx = hs.start[lmin] + (unsigned)off;
-                    if (idx < n) e = (uint32_t)hs.sorted_sym[idx] | (lmin << 16);
-                }
+            // at most P bits long, it is a prefix of every extension of t
+            const unsigned long long w0 = (unsigned long long)t << (64 - kLutBits);
+            const unsigned lmin = code_len_in(T, w0, 1, maxL);
+            if (lmin <= (unsigned)kLutBits) {
+                e = leaf_of(T, sorted, n, w0, lmin);
             } else {
-                const unsigned long long w1 = w0 | ((1ULL << (64 - kLenBits)) - 1);
-                const unsigned lmax = code_len_at(hs, w1, maxL);
-                if (lmin < lmax) {
-                    e = kLongFlag | kMixedFlag | (lmin << 16) | ((lmax - lmin) << 24);
-                } else {
-                    // every codeword under t has length lmin: index = start + code - first
-                    const unsigned long long c0 = (unsigned long long)t << (lmin - kLenBits);
-                    const long long base = (long long)hs.start[lmin] + (long long)c0 - (long long)hs.first[lmin];
-                    if (base >= 0 && base + (1LL << (lmin - kLenBits)) <= (long long)n)
-                        e = kLongFlag | (uint32_t)base | (lmin << 16);
-                    else
-                        e = kLongFlag | kMixedFlag | (lmin << 16);
+                const unsigned lmax = code_len_in(T, w0 | kTail, lmin, maxL);
+                e = kLongFlag | (lmin << 16) | ((lmax - lmin) << 24);
+                if (lmax <= (unsigned)(kLutBits + kSubMax)) {
+                    sbs[j] = (unsigned char)(lmax - kLutBits);
+                    mine += 1u << (lmax - kLutBits);
                 }
             }
         }
-        hs.lut15[t] = e;
+        ent[t] = e;
     }
+    // exclusive scan of the second-level sizes over the block
+    unsigned incl = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (unsigned)o) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned v = wsum[lane];
+        unsigned x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= (unsigned)o) x += y;
+        }
+        wsum[lane] = x - v;
+        if (lane == 31) total = x < kSubCap ? x : kSubCap;
+    }
+    __syncthreads();
+    unsigned off = wsum[warp] + incl - mine;
+#pragma unroll
+    for (unsigned j = 0; j < kLutPer; j++) {
+        if (!sbs[j]) continue;
+        const unsigned sz = 1u << sbs[j];
+        if (off + sz <= kSubCap) ent[t0 + j] = kSubFlag | off | ((unsigned)sbs[j] << 16);
+        off += sz;
+    }
+    __syncthreads();
+    for (unsigned t = tid; t < (1u << kLutBits); t += kLutThreads) hs.lut1[t] = ent[t];
+    // second-level entries: a warp per prefix, a lane per suffix
+    for (unsigned t = warp; t < (1u << kLutBits); t += kLutThreads / 32) {
+        const uint32_t e = ent[t];
+        if ((e & (kLongFlag | kSubFlag)) != kSubFlag) continue;
+        const unsigned sb = (e >> 16) & 0xFu, base = e & 0xFFFFu;
+        const unsigned long long w0 = (unsigned long long)t << (64 - kLutBits);
+        const unsigned lo = code_len_in(T, w0, 1, maxL);
+        for (unsigned r = lane; r < (1u << sb); r += 32) {
+            const unsigned long long w = w0 | ((unsigned long long)r << (64 - kLutBits - sb));
+            hs.lut_sub[base + r] = leaf_of(T, sorted, n, w, code_len_in(T, w, lo, kLutBits + sb));
+        }
+    }
+    if (tid == 0) *hs.nsub = any ? total : 0u;
 }
 
 // Canonical codewords (Sec. IV-B): the present symbols ordered by (length,
@@ -1171,8 +1255,22 @@ header_kernel(HeaderArgs h, const uint8_t *len, Scalars *sc, uint8_t *out)
 }
 
 // ---------------------------------------------------------------------------
-// Decoder: one thread per chunk, canonical decode with a 12-bit table and a
-// per-length fallback for longer codewords.
+// Decoder: one thread per chunk, canonical decode with a two-level table and
+// a per-length fallback for the longest codewords.
+//
+// A thread decodes its chunk of K symbols.  It keeps the next bits of the
+// chunk MSB-aligned in two 32-bit registers hi:lo (nb valid bits, at least 32
+// before every read) and refills them a word at a time from a queue of two
+// prefetched 16-byte blocks.  A codeword of at most 13 bits is one load from
+// the first-level table of every 13-bit prefix; one of up to 23 bits is a
+// second load from the table its prefix names, indexed by the bits after the
+// prefix; either gives symbol and length, with no search.  Every other case
+// (longer codewords, prefixes past the second-level budget, escape payloads
+// that do not fit the 32-bit window, invalid codes) leaves the loop for an
+// out-of-line routine that reads its window from global memory, after which
+// the queue restarts at the new position.
+constexpr int kDecThreads = 1024;
+constexpr size_t kDecSmem = (4u << kLutBits) + 4 * kSubCap + sizeof(LenTabs);
 
 __device__ __forceinline__ uint32_t ldw(const uint32_t *w, unsigned long long i, unsigned long long n)
 {
@@ -1188,20 +1286,6 @@ __device__ __forceinline__ uint4 ld4(const uint32_t *w, unsigned long long i, un
     v.x = ldw(w, i, n); v.y = ldw(w, i + 1, n); v.z = ldw(w, i + 2, n); v.w = ldw(w, i + 3, n);
     return v;
 }
-
-// Decoder: one thread per chunk of K symbols.  The thread keeps the next bits
-// of its chunk MSB-aligned in two 32-bit registers hi:lo (nb valid bits, at
-// least 32 before every read) and refills them a word at a time from a queue
-// of two prefetched 16-byte blocks.  The 2^15-entry table of every 15-bit
-// prefix gives symbol and length of a codeword of at most 15 bits in one
-// shared-memory load; for longer codewords it gives the range of lengths
-// under the prefix, and the length is the lower end plus the number of
-// length limits the window reaches in that range (canonical codes); the
-// symbol is then sorted_sym[start[L] + code - first[L]].  A codeword longer
-// than the buffered bits (only possible above 32 bits) re-reads its window
-// from global memory.  Escape payloads (container streams) follow symbol 0.
-constexpr int kDecSymSmem = 16384;
-constexpr int kDecThreads = 1024;
 
 struct BitQueue {
     const uint32_t *w;
@@ -1241,6 +1325,45 @@ __device__ __forceinline__ unsigned long long window64(const uint32_t *w, unsign
     return sh ? (hi << sh) | (ldw(w, i + 2, n) >> (32 - sh)) : hi;
 }
 
+struct SlowOut {
+    unsigned long long pos;
+    uint32_t sv, bad;
+};
+
+// A step the table loop does not take: the entry e at pos is a long entry,
+// invalid, or an escape whose payload does not fit the 32-bit window.
+__device__ __noinline__ SlowOut decode_slow(uint32_t e, unsigned long long pos, const uint32_t *words,
+                                            unsigned long long nwords, const LenTabs *T, const uint16_t *symtab,
+                                            unsigned nsym, int ew, long long *esc_i)
+{
+    SlowOut o;
+    o.bad = 0;
+    const unsigned long long win = window64(words, nwords, pos);
+    uint32_t sv = e & 0xFFFFu;
+    unsigned L = (e >> 16) & 0x3Fu;
+    if (e & kLongFlag) {
+        const unsigned lmin = L, lmax = L + ((e >> 24) & 0x3Fu);
+        L = code_len_in(*T, win, lmin, lmax);
+        const unsigned long long off = (win >> (64 - L)) - T->first[L];
+        if (off >= T->count[L]) o.bad = 1;
+        const unsigned idx = T->start[L] + (unsigned)(off < T->count[L] ? off : 0);
+        sv = symtab[idx < nsym ? idx : 0];
+    } else if (e == 0) {
+        o.bad = 1;               // no codeword starts here
+        L = 1;
+    }
+    pos += L;
+    if (ew && sv == 0) {
+        // escape payload: zigzag(k) in ew bits
+        const unsigned long long z = window64(words, nwords, pos) >> (64 - ew);
+        pos += (unsigned)ew;
+        *esc_i = unzigzag(z);
+    }
+    o.pos = pos;
+    o.sv = sv;
+    return o;
+}
+
 __global__ void __launch_bounds__(kDecThreads, 1) decode_kernel(DecodeArgs a_in, HuffScratch hs)
 {
     DecodeArgs a = a_in;
@@ -1255,37 +1378,33 @@ __global__ void __launch_bounds__(kDecThreads, 1) decode_kernel(DecodeArgs a_in,
         if (h.esc_w == 0) a.esc = nullptr;
     }
     extern __shared__ __align__(16) unsigned char dsm[];
-    uint32_t *lut = reinterpret_cast<uint32_t *>(dsm);                                      // [1 << kLenBits]
-    unsigned long long *sfirst = reinterpret_cast<unsigned long long *>(dsm + (4u << kLenBits));  // [64]
-    unsigned long long *slim = sfirst + 64;                                                  // [64]
-    unsigned *sstart = reinterpret_cast<unsigned *>(slim + 64);                              // [64]
-    unsigned *scount = sstart + 64;                                                          // [64]
-    uint16_t *ssym = reinterpret_cast<uint16_t *>(scount + 64);                              // [kDecSymSmem]
+    uint32_t *lut = reinterpret_cast<uint32_t *>(dsm);                       // [1 << kLutBits]
+    uint32_t *sub = lut + (1u << kLutBits);                                   // [kSubCap]
+    LenTabs *T = reinterpret_cast<LenTabs *>(sub + kSubCap);
     if (block_skip(hs.status)) return;
     const unsigned nsym = *hs.nsym;
-    const bool sym_sm = nsym <= (unsigned)kDecSymSmem;
+    const unsigned nsub = *hs.nsub < kSubCap ? *hs.nsub : kSubCap;
     {
         // escape entries take their payload width into their length when both fit 32 bits
         const unsigned ewc = a.esc ? a.esc_w : 0u;
-        for (int i = threadIdx.x; i < (1 << kLenBits); i += blockDim.x) {
-            uint32_t e = hs.lut15[i];
-            if (ewc && e && !(e & kLongFlag) && (e & 0xFFFFu) == 0) {
+        auto fold = [&](uint32_t e) -> uint32_t {
+            if (ewc && e && !(e & (kLongFlag | kSubFlag)) && (e & 0xFFFFu) == 0) {
                 const unsigned L = (e >> 16) & 0x3Fu;
                 if (L + ewc <= 32) e = kEscFolded | ((L + ewc) << 16);
             }
-            lut[i] = e;
-        }
+            return e;
+        };
+        for (int i = threadIdx.x; i < (1 << kLutBits); i += blockDim.x) lut[i] = fold(hs.lut1[i]);
+        for (unsigned i = threadIdx.x; i < nsub; i += blockDim.x) sub[i] = fold(hs.lut_sub[i]);
     }
-    for (int i = threadIdx.x; i < 64; i += blockDim.x) {
-        sfirst[i] = hs.first[i];
-        slim[i] = hs.lim[i];
-        sstart[i] = hs.start[i];
-        scount[i] = hs.count[i];
+    if (threadIdx.x < 64) {
+        T->first[threadIdx.x] = hs.first[threadIdx.x];
+        T->lim[threadIdx.x] = hs.lim[threadIdx.x];
+        T->start[threadIdx.x] = hs.start[threadIdx.x];
+        T->count[threadIdx.x] = hs.count[threadIdx.x];
     }
-    if (sym_sm)
-        for (unsigned i = threadIdx.x; i < nsym; i += blockDim.x) ssym[i] = hs.sorted_sym[i];
     __syncthreads();
-    const uint16_t *symtab = sym_sm ? ssym : hs.sorted_sym;
+    const uint16_t *symtab = hs.sorted_sym;
     long long *const esc = a.esc;
     const int ew = esc ? (int)a.esc_w : 0;     // escape payload width (1..63)
     const unsigned long long nch = (a.N + a.K - 1) / a.K;
@@ -1304,120 +1423,44 @@ __global__ void __launch_bounds__(kDecThreads, 1) decode_kernel(DecodeArgs a_in,
         uint32_t hi, lo;
         int nb;
         q.prime(pos0, hi, lo, nb);
-        unsigned used = 0;
+        unsigned long long used = 0;
         bool bad = false;
-        // drop n <= nb bits (n <= 64), then refill to at least 32 valid bits
-        auto drop = [&](unsigned n) {
-            if (n < 32) {
-                hi = __funnelshift_l(lo, hi, n);
-                lo <<= n;
-            } else {
-                hi = n < 64 ? lo << (n - 32) : 0u;
-                lo = 0;
-            }
-            nb -= (int)n;
-            used += n;
-            if (nb < 32) {
-                const uint32_t wv = q.next();
-                hi |= wv >> nb;
-                lo = __funnelshift_rc(0u, wv, (unsigned)nb);
-                nb += 32;
-            }
-        };
-        // every other entry: longer codewords, escapes whose codeword and
-        // payload exceed 32 bits, and prefixes that start no codeword
-        auto slow = [&](unsigned long long i, uint32_t e) -> uint16_t {
-            uint16_t sv = (uint16_t)(e & 0xFFFFu);
-            unsigned L = (e >> 16) & 0x3Fu;
-            bool fetched = false;            // the codeword was read past the buffer
-            if (e & kLongFlag) {
-                unsigned long long win = ((unsigned long long)hi << 32) | lo;
-                if (!(e & kMixedFlag) && (int)L <= nb) {
-                    // one length under this prefix: symbol base + the bits after the prefix
-                    const unsigned r = (unsigned)((win << kLenBits) >> (64 - (L - kLenBits)));
-                    const unsigned idx = (e & 0xFFFFu) + r;
-                    sv = symtab[idx < nsym ? idx : 0];
-                } else {
-                    const unsigned lmin = L;
-                    const unsigned lmax = (e & kMixedFlag) ? L + ((e >> 24) & 0x3Fu) : L;
-                    for (unsigned l = lmin; l < lmax; l++) L += (win >= slim[l]) ? 1u : 0u;
-                    if ((int)L > nb) {
-                        // the codeword extends past the buffered bits: exact window
-                        win = window64(a.words, a.nwords, pos0 + used);
-                        L = lmin;
-                        for (unsigned l = lmin; l < lmax; l++) L += (win >= slim[l]) ? 1u : 0u;
-                        fetched = true;
-                    }
-                    const unsigned long long off = (win >> (64 - L)) - sfirst[L];
-                    if (off >= scount[L]) bad = true;
-                    const unsigned idx = sstart[L] + (unsigned)(off < scount[L] ? off : 0);
-                    sv = symtab[idx < nsym ? idx : 0];
-                }
-            } else if (e == 0) {
-                bad = true;               // no codeword starts here
-                L = 1;
-            }
-            if (fetched) {
-                used += L;
-                q.prime(pos0 + used, hi, lo, nb);
-            } else {
-                drop(L);
-            }
-            if (ew && sv == 0) {
-                // escape payload: zigzag(k) in ew bits
-                unsigned long long z;
-                if (ew <= nb) {
-                    z = ((((unsigned long long)hi) << 32) | lo) >> (64 - ew);
-                    drop((unsigned)ew);
-                } else {
-                    z = window64(a.words, a.nwords, pos0 + used) >> (64 - ew);
-                    used += (unsigned)ew;
-                    q.prime(pos0 + used, hi, lo, nb);
-                }
-                esc[i] = unzigzag(z);
-            }
-            return sv;
-        };
-        // n <= 32 bits (n <= nb), then refill to at least 32 valid bits
-        auto drop32 = [&](unsigned n) {
-            hi = n < 32 ? __funnelshift_l(lo, hi, n) : lo;
-            lo = n < 32 ? lo << n : 0u;
-            nb -= (int)n;
-            used += n;
-            if (nb < 32) {
-                const uint32_t wv = q.next();
-                hi |= wv >> nb;
-                lo = __funnelshift_rc(0u, wv, (unsigned)nb);
-                nb += 32;
-            }
-        };
         auto step = [&](unsigned long long i) -> uint16_t {
-            const uint32_t e = lut[hi >> (32 - kLenBits)];
-            uint16_t sv = (uint16_t)(e & 0xFFFFu);
+            uint32_t e = lut[hi >> (32 - kLutBits)];
+            // a codeword of up to 23 bits: its second-level entry, indexed by
+            // the bits after the prefix (all within hi, nb >= 32)
+            if ((e & (kLongFlag | kSubFlag)) == kSubFlag)
+                e = sub[(e & 0xFFFFu) + ((hi << kLutBits) >> (32 - ((e >> 16) & 0xFu)))];
+            const uint32_t sv = e & 0xFFFFu;
             const unsigned L = (e >> 16) & 0x3Fu;
-            // a codeword of 16..32 bits under a prefix of one length: its
-            // symbol is symtab[base + the bits after the prefix], all within hi
-            // (nb >= 32), so it stays on this path
-            const bool longu = (e & (kLongFlag | kMixedFlag)) == kLongFlag && L <= 32;
-            if (longu) {
-                const unsigned idx = (e & 0xFFFFu) + ((hi >> (32 - L)) & ((1u << (L - kLenBits)) - 1u));
-                sv = symtab[idx < nsym ? idx : 0];
-            }
             const bool at_esc = ew && sv == 0;
-            if (((e & kLongFlag) && !longu) || e == 0 || (at_esc && (longu || !(e & kEscFolded))))
-                return slow(i, e);
-            if (at_esc) {
-                // folded escape: codeword of L - ew bits, then zigzag(k) in ew bits
-                const unsigned long long win = ((unsigned long long)hi << 32) | lo;
-                esc[i] = unzigzag((win << (L - ew)) >> (64 - ew));
+            if ((e & kLongFlag) || e == 0 || (at_esc && !(e & kEscFolded))) {
+                const SlowOut o = decode_slow(e, pos0 + used, a.words, a.nwords, T, symtab, nsym, ew,
+                                              esc ? esc + i : nullptr);
+                bad |= o.bad != 0;
+                used = o.pos - pos0;
+                q.prime(o.pos, hi, lo, nb);
+                return (uint16_t)o.sv;
             }
-            drop32(L);
-            return sv;
+            // folded escape: codeword of L - ew bits, then zigzag(k) in ew bits
+            if (at_esc) esc[i] = unzigzag((unsigned long long)((hi << (L - ew)) >> (32 - ew)));
+            // drop L <= 32 bits, then refill to at least 32 valid bits
+            hi = L < 32 ? __funnelshift_l(lo, hi, L) : lo;
+            lo = L < 32 ? lo << L : 0u;
+            nb -= (int)L;
+            used += L;
+            if (nb < 32) {
+                const uint32_t wv = q.next();
+                hi |= wv >> nb;
+                lo = __funnelshift_rc(0u, wv, (unsigned)nb);
+                nb += 32;
+            }
+            return (uint16_t)sv;
         };
         const unsigned long long beg = c * a.K;
         const unsigned long long end = beg + a.K < a.N ? beg + a.K : a.N;
         unsigned long long i = beg;
-        // eight symbols per 16-byte store (a chunk starts on a 256-byte boundary)
+        // eight symbols per 16-byte store (K is a multiple of 128)
         for (; i + 8 <= end; i += 8) {
             uint4 o;
             o.x = (uint32_t)step(i) | ((uint32_t)step(i + 1) << 16);
@@ -1428,12 +1471,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) decode_kernel(DecodeArgs a_in,
             // kernel, so they should not push the bitstream out of L2
             __stcs(reinterpret_cast<uint4 *>(a.sym + i), o);
         }
-        for (; i + 2 <= end; i += 2) {
-            const uint32_t v0 = step(i);
-            const uint32_t v1 = step(i + 1);
-            *reinterpret_cast<uint32_t *>(a.sym + i) = v0 | (v1 << 16);
-        }
-        if (i < end) a.sym[i] = step(i);
+        for (; i < end; i++) a.sym[i] = step(i);
         if (bad || pos0 + used != expect) atomicExch(hs.status, (unsigned)DS_FORMAT);
     }
 }
@@ -1527,7 +1565,9 @@ cudaError_t set_attrs_now()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(enc_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        e = cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(lut_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLutSmem);
     return e;
 }
 cudaError_t set_attrs() { return once_per_device(g_attr_done, set_attrs_now); }
@@ -1543,8 +1583,9 @@ size_t huff_scratch_bytes(unsigned int D)
     add(4 * 2 * d); add(4 * 4 * d); add(4 * 4 * d);    // parent, anc, dep
     add(8 * d); add(8 * d);                            // leafw, intw
     add(4); add(8 * 64); add(4 * 64); add(4 * 64);     // nsym, first, count, start
-    add(d); add(8 * d); add(2 * d); add(4u << kLenBits);
+    add(d); add(8 * d); add(2 * d); add(4u << kLutBits);
     add(8 * 64);
+    add(4 * kSubCap); add(4);
     return b;
 }
 
@@ -1569,8 +1610,10 @@ void huff_scratch_carve(void *base, unsigned int D, Scalars *sc, HuffScratch *hs
     hs->len = (uint8_t *)take(d);
     hs->code = (unsigned long long *)take(8 * d);
     hs->sorted_sym = (uint16_t *)take(2 * d);
-    hs->lut15 = (uint32_t *)take(4u << kLenBits);
+    hs->lut1 = (uint32_t *)take(4u << kLutBits);
     hs->lim = (unsigned long long *)take(8 * 64);
+    hs->lut_sub = (uint32_t *)take(4 * kSubCap);
+    hs->nsub = (unsigned *)take(4);
     hs->status = &sc->status;
     hs->s_lo = &sc->s_lo;
     hs->s_hi = &sc->s_hi;
@@ -1601,7 +1644,7 @@ cudaError_t launch_decode_tables(const uint8_t *lenb, unsigned int s_lo, unsigne
     cudaError_t e = set_attrs();
     if (e != cudaSuccess) return e;
     dec_tables_kernel<<<1, 1024, 4 * 32 * kWcStride + D, s>>>(lenb, s_lo, s_hi, D, hs, nullptr, nullptr);
-    lut15_kernel<<<(1u << kLenBits) / 256, 256, 0, s>>>(hs);
+    lut_kernel<<<1, kLutThreads, kLutSmem, s>>>(hs);
     count_launch(2);
     return cudaGetLastError();
 }
@@ -1612,7 +1655,7 @@ cudaError_t launch_decode_tables_dev(const uint8_t *base, const DevHdr *dh, unsi
     cudaError_t e = set_attrs();
     if (e != cudaSuccess) return e;
     dec_tables_kernel<<<1, 1024, 4 * 32 * kWcStride + D, s>>>(nullptr, 0u, 0u, D, hs, base, dh);
-    lut15_kernel<<<(1u << kLenBits) / 256, 256, 0, s>>>(hs);
+    lut_kernel<<<1, kLutThreads, kLutSmem, s>>>(hs);
     count_launch(2);
     return cudaGetLastError();
 }
@@ -1679,8 +1722,7 @@ cudaError_t launch_decode(const DecodeArgs &a, const HuffScratch &hs, cudaStream
 {
     cudaError_t e = set_attrs();
     if (e != cudaSuccess) return e;
-    const size_t sm = (4u << kLenBits) + 64 * 8 * 2 + 64 * 4 * 2 + kDecSymSmem * 2;
-    decode_kernel<<<152, kDecThreads, sm, s>>>(a, hs);
+    decode_kernel<<<sm_count(), kDecThreads, kDecSmem, s>>>(a, hs);
     count_launch();
     return cudaGetLastError();
 }

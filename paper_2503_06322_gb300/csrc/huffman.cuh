@@ -4,7 +4,9 @@
 
 namespace hpdr {
 
-constexpr int kLenBits = 15;    // decoder: code length / symbol of every 15-bit prefix
+constexpr int kLutBits = 13;    // decoder: first-level table of every 13-bit prefix
+constexpr int kSubMax = 10;     // decoder: second-level index bits (codewords of up to 23 bits)
+constexpr unsigned kSubCap = 12288;   // decoder: second-level entries (48 KB of shared memory)
 constexpr int kMaxCodeLen = 63;
 
 // Escape payload (container format v3): after the codeword of symbol 0,
@@ -37,7 +39,9 @@ struct HuffScratch {
     uint8_t *len;                 // [D]
     unsigned long long *code;     // [D]
     uint16_t *sorted_sym;         // [D]
-    uint32_t *lut15;              // [1 << kLenBits] symbol | length << 16 of a 15-bit prefix (0: longer)
+    uint32_t *lut1;               // [1 << kLutBits] first-level decoder table of every 13-bit prefix
+    uint32_t *lut_sub;            // [kSubCap] second-level entries of longer codewords
+    unsigned int *nsub;           // [1] second-level entries in use
     unsigned long long *lim;      // [64] left-justified upper limit of the codes of each length
     unsigned int *status;         // -> Scalars::status
     unsigned int *s_lo, *s_hi;    // -> Scalars

@@ -436,10 +436,10 @@ solve_strided_kernel(T *b, int n, long long stride, long long nlines, const T *_
 }
 
 // One thread per line, 32 adjacent lines per warp (every step one coalesced
-// row), the line swept in place in global memory: the loads of the next eight
-// steps are in flight while the current eight are computed; the Thomas
+// row), the line swept in place in global memory: the loads of the next sixteen
+// steps are in flight while the current sixteen are computed; the Thomas
 // factors sit in shared memory.
-constexpr int kSolvePre = 8;
+constexpr int kSolvePre = 16;
 
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -591,14 +591,37 @@ solve_contig_kernel(T *b, int n, long long nlines, int rows, int pitch, const T 
         for (int t = n - 1; t >= 0; t--) { x = fma_rn(-ccp[t], x, p[t]); p[t] = x; }
     }
     __syncthreads();
-    for (int r = warp; r < nr; r += nwarp) {
-        const T *srow = S + r * pitch;
-        const long long g0 = (row0 + r) * n;
-        for (int t = lane; t < n; t += 32) {
-            const T z = srow[t];
-            if (sign == 0) b[g0 + t] = z;
-            else if (sign > 0) vc[g0 + t] = add_rn(vc[g0 + t], z);
-            else vc[g0 + t] = sub_rn(vc[g0 + t], z);
+    if (sign == 0) {
+        for (int r = warp; r < nr; r += nwarp) {
+            const T *srow = S + r * pitch;
+            const long long g0 = (row0 + r) * n;
+            for (int t = lane; t < n; t += 32) b[g0 + t] = srow[t];
+        }
+        return;
+    }
+    // the read-modify-write of vc: a warp's elements j (row warp + nwarp (j / nk),
+    // column lane + 32 (j mod nk)) in batches of U, every load of a batch
+    // issued before its stores, so U loads per lane are in flight
+    const int nk = (n + 31) / 32;
+    const int rows_w = nr > warp ? (nr - warp + nwarp - 1) / nwarp : 0;
+    const int nj = rows_w * nk;
+    constexpr int U = sizeof(T) == 4 ? 12 : 8;
+    for (int j0 = 0; j0 < nj; j0 += U) {
+        T old[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int j = j0 + u, q = j / nk, t = lane + 32 * (j - q * nk);
+            old[u] = (j < nj && t < n) ? vc[(row0 + warp + (long long)q * nwarp) * n + t] : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int j = j0 + u, q = j / nk, t = lane + 32 * (j - q * nk);
+            if (j < nj && t < n) {
+                const int r = warp + q * nwarp;
+                const T z = S[r * pitch + t];
+                const long long g = (row0 + r) * n + t;
+                vc[g] = sign > 0 ? add_rn(old[u], z) : sub_rn(old[u], z);
+            }
         }
     }
 }
