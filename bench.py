@@ -130,10 +130,16 @@ LEVEL_GROUPS = ("c_restrict_quant_L", "d_restrict_sym_L", "d_expand_L", "c_solve
 
 def source_hash(group="c_restrict_quant_L"):
     """SHA-256 prefix of the sources of a kernel group's translation unit: the
-    level kernels (levels.cu, decomp.cu, levels.cuh, levels_dev.cuh, internal.cuh) or the Huffman kernels
-    (huffman.cu, huffman.cuh, internal.cuh)."""
-    files = (("levels.cu", "decomp.cu", "levels.cuh", "levels_dev.cuh", "internal.cuh") if group in LEVEL_GROUPS
-             else ("huffman.cu", "huffman.cuh", "internal.cuh"))
+    plane-streaming level kernels (decomp.cu, levels_dev.cuh, levels.cuh,
+    internal.cuh), the solves (levels.cu, levels_dev.cuh, levels.cuh,
+    internal.cuh) or the Huffman kernels (huffman.cu, huffman.cuh,
+    internal.cuh)."""
+    if group in ("c_solves_L", "d_solves_L"):
+        files = ("levels.cu", "levels_dev.cuh", "levels.cuh", "internal.cuh")
+    elif group in LEVEL_GROUPS:
+        files = ("decomp.cu", "levels_dev.cuh", "levels.cuh", "internal.cuh")
+    else:
+        files = ("huffman.cu", "huffman.cuh", "internal.cuh")
     h = hashlib.sha256()
     for f in files:
         with open(os.path.join(ROOT, "paper_2503_06322_gb300", "csrc", f), "rb") as fh:

@@ -262,14 +262,20 @@ typedef struct {
  *                  d_out + out_offsets[i] (256-byte aligned slots of
  *                  hpdr_compress_bound bytes); out_offsets[nfields] = bytes used;
  *   out_sizes      host [nfields]: container sizes.
- * The context keeps one workspace per field of a cached batch.  Synchronous
+ * A captured graph holds the buffers it was captured with, so a batch over
+ * other buffers (inputs or d_out) is captured anew.  The context keeps the
+ * four most recently used batches (each with one workspace per field);
+ * capturing a fifth destroys the least recently used one.  Synchronous
  * (waits for the replay).  Errors as hpdr_compress. */
 hpdr_status hpdr_compress_batched(hpdr_ctx *ctx, int nfields, const hpdr_field *fields, const hpdr_config *cfg,
                                   void *d_out, size_t out_capacity, size_t *out_offsets, size_t *out_sizes,
                                   void *stream);
 
-/* Stream count the autotuner chose for the last cached batch (0: none). */
+/* Stream count the autotuner chose for the most recently replayed batch
+ * (0: none). */
 int hpdr_batched_streams(hpdr_ctx *ctx);
+/* Number of captured batches the context holds (at most four). */
+int hpdr_batched_cached(hpdr_ctx *ctx);
 
 /* Compression of a host-resident field in slabs along its first dimension
  * (the host-device pipeline of Sec. V: Fig. 7 and Alg. 4 with a fixed slab

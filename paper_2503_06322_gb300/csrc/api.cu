@@ -877,7 +877,20 @@ struct BatchPlan {
     cudaGraphExec_t exec = nullptr;
     int streams = 0;
     double tuned_ms = 0.0;
+    unsigned long long last_use = 0;   // call counter of the last replay (least recently used goes first)
 };
+
+// Captured batches kept per context: a graph holds the pointers it was
+// captured with, so a batch over other buffers is another entry; beyond this
+// many the least recently used entry is destroyed (graph, workspace, sizes).
+constexpr size_t kMaxBatchPlans = 4;
+void free_batch_plan(BatchPlan *bp)
+{
+    if (bp->exec) cudaGraphExecDestroy(bp->exec);
+    cudaFree(bp->ws);
+    cudaFree(bp->sizes);
+    delete bp;
+}
 
 struct BatchRes {
     cudaStream_t origin = nullptr;
@@ -885,6 +898,7 @@ struct BatchRes {
     cudaEvent_t fork = nullptr;
     std::vector<cudaEvent_t> join;
     std::map<std::string, BatchPlan *> plans;
+    unsigned long long calls = 0;
 };
 
 hpdr_status batch_res(hpdr_ctx *ctx, BatchRes *&r, int nworkers)
@@ -1092,12 +1106,7 @@ hpdr_status hpdr_ctx_destroy(hpdr_ctx *ctx)
     destroy_stream_res(ctx);
     if (ctx->batch_res) {
         BatchRes *r = (BatchRes *)ctx->batch_res;
-        for (auto &kv : r->plans) {
-            if (kv.second->exec) cudaGraphExecDestroy(kv.second->exec);
-            cudaFree(kv.second->ws);
-            cudaFree(kv.second->sizes);
-            delete kv.second;
-        }
+        for (auto &kv : r->plans) free_batch_plan(kv.second);
         for (auto st : r->workers) cudaStreamDestroy(st);
         for (auto ev : r->join) cudaEventDestroy(ev);
         if (r->fork) cudaEventDestroy(r->fork);
@@ -1754,14 +1763,20 @@ hpdr_status hpdr_compress_batched(hpdr_ctx *ctx, int nfields, const hpdr_field *
         cudaEventDestroy(t1);
         ctx->prof_on = prof;
         if (st != HPDR_OK) {
-            if (bp->exec) cudaGraphExecDestroy(bp->exec);
-            cudaFree(bp->ws);
-            cudaFree(bp->sizes);
-            delete bp;
+            free_batch_plan(bp);
             return st;
+        }
+        // every earlier replay has completed (each call waits for its sizes)
+        while (r->plans.size() >= kMaxBatchPlans) {
+            auto lru = r->plans.begin();
+            for (auto jt = r->plans.begin(); jt != r->plans.end(); ++jt)
+                if (jt->second->last_use < lru->second->last_use) lru = jt;
+            free_batch_plan(lru->second);
+            r->plans.erase(lru);
         }
         r->plans[key] = bp;
     }
+    bp->last_use = ++r->calls;
     // replay: the caller's stream orders the graph before and after
     cudaEvent_t ev = r->fork;
     CK(cudaEventRecord(ev, user));
@@ -1787,9 +1802,18 @@ int hpdr_batched_streams(hpdr_ctx *ctx)
 {
     if (!ctx || !ctx->batch_res) return 0;
     BatchRes *r = (BatchRes *)ctx->batch_res;
+    // the stream count of the most recently replayed batch
     int s = 0;
-    for (auto &kv : r->plans) s = kv.second->streams;
+    unsigned long long last = 0;
+    for (auto &kv : r->plans)
+        if (kv.second->last_use >= last) { last = kv.second->last_use; s = kv.second->streams; }
     return s;
+}
+
+int hpdr_batched_cached(hpdr_ctx *ctx)
+{
+    if (!ctx || !ctx->batch_res) return 0;
+    return (int)((BatchRes *)ctx->batch_res)->plans.size();
 }
 
 const char *hpdr_status_string(hpdr_status st)

@@ -99,6 +99,7 @@ def lib():
             "hpdr_compress_batched": [vp, C.c_int, C.POINTER(Field), C.POINTER(Config), vp, C.c_size_t,
                                       sz, sz, vp],
             "hpdr_batched_streams": [vp],
+            "hpdr_batched_cached": [vp],
             "hpdr_lossless_compress": [vp, vp, C.c_uint64, C.c_int, C.c_uint32, vp, C.c_size_t, sz, vp],
             "hpdr_lossless_decompress": [vp, vp, C.c_size_t, vp, C.c_size_t, vp],
             "hpdr_lossless_inspect": [vp, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_uint64)],

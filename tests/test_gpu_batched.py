@@ -55,3 +55,31 @@ def test_batched_full_draw_matches_plain():
             rec = hpdr.hpdr_decompress(got.clone())
             un = u.double()
             assert (rec.double() - un).abs().max().item() <= tol * un.abs().max().item(), i
+
+
+def test_batched_cache_is_bounded():
+    """A captured batch holds its buffers, so every new output buffer is a new
+    capture; the context keeps the four most recently used ones and frees the
+    rest (workspace, sizes, graph), and results stay byte-identical."""
+    from paper_2503_06322_gb300 import fields, hpdr
+    lib = hpdr.lib()
+    us = [torch.from_numpy(fields.powerlaw_field((33 + 8 * i, 40, 17), seed=300 + i)).cuda() for i in range(5)]
+    tols = [1e-3] * len(us)
+    ref, offs_ref, sizes_ref = hpdr.hpdr_compress_batched(us, tols)
+    outs = [torch.zeros_like(ref) for _ in range(7)]      # seven distinct output buffers
+    free_at = []
+    for out in outs:
+        got, offs, sizes = hpdr.hpdr_compress_batched(us, tols, out=out)
+        assert sizes == sizes_ref and offs == offs_ref
+        for i in range(len(us)):
+            assert torch.equal(got[offs[i]:offs[i] + sizes[i]], ref[offs_ref[i]:offs_ref[i] + sizes_ref[i]])
+        assert 1 <= lib.hpdr_batched_cached(hpdr.context()) <= 4
+        torch.cuda.synchronize()
+        free_at.append(torch.cuda.mem_get_info()[0])
+    # once four batches are held, each new capture frees as much as it takes
+    assert abs(free_at[-1] - free_at[3]) < (16 << 20)
+    # a buffer whose batch was evicted is captured again and still agrees
+    got, offs, sizes = hpdr.hpdr_compress_batched(us, tols, out=outs[0])
+    assert sizes == sizes_ref
+    for i in range(len(us)):
+        assert torch.equal(got[offs[i]:offs[i] + sizes[i]], ref[offs_ref[i]:offs_ref[i] + sizes_ref[i]])
