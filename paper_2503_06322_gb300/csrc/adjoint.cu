@@ -24,53 +24,75 @@ enum { MP_PLAIN = 0, MP_RT_FINAL = 1, MP_DT_FINAL = 2 };
 // Final modes (k = 0, output on the level-l grid):
 //   MP_RT_FINAL: stream[rank(p)] = gsrc[p] - value   at the new nodes
 //   MP_DT_FINAL: out[p] = coef[rank(p)] + value       at the new nodes
+// One warp per output row (i0, i1), lanes along i2: the row's dimension-0
+// and dimension-1 indices, the taps of a dimension-0 or -1 pass and, in the
+// final modes, whether the row holds only new nodes and where its new nodes
+// start in the stream are computed once per row; every load and store is
+// coalesced along i2 (the kept rows of a kept plane write every other stream
+// slot: only odd i2 are new there).
+constexpr int kMpWarps = 8;
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(32 * kMpWarps)
 mass_prolong_kernel(const T *__restrict__ in, T *out, long long s0, long long s1, long long s2, int k,
                     int mck, const T *__restrict__ etap, const int *__restrict__ efirst, LevelGeom<T> g,
                     const T *gsrc, T *stream, const T *coef)
 {
-    const long long n = s0 * s1 * s2;
+    const long long rows = s0 * s1;
     const long long in1 = (k == 1) ? mck : s1, in2 = (k == 2) ? mck : s2;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
-         idx += (long long)gridDim.x * blockDim.x) {
-        long long i0, i1, i2;
-        if (n < (1LL << 31)) {   // 32-bit divisions (64-bit ones run on the slow FP64 path)
-            const unsigned u = (unsigned)idx, t = u / (unsigned)s2;
-            i2 = u - t * (unsigned)s2;
-            i0 = t / (unsigned)s1;
-            i1 = t - (unsigned)i0 * (unsigned)s1;
-        } else {
-            const long long t = idx / s2;
-            i2 = idx - t * s2;
-            i1 = t % s1;
-            i0 = t / s1;
-        }
-        const long long p = (k == 0) ? i0 : (k == 1) ? i1 : i2;
-        const int j0 = efirst[p];
-        T v = (T)0;
+    const int lane = threadIdx.x & 31;
+    for (long long row = blockIdx.x * (long long)kMpWarps + (threadIdx.x >> 5); row < rows;
+         row += (long long)gridDim.x * kMpWarps) {
+        const long long i0 = row / s1, i1 = row - i0 * s1;
+        // dimension-0 or -1 pass: the row's taps
+        int rj0 = 0;
+        T rt[3] = {(T)0, (T)0, (T)0};
+        if (k != 2) {
+            const long long pr = (k == 0) ? i0 : i1;
+            rj0 = efirst[pr];
 #pragma unroll
-        for (int i = 0; i < 3; i++) {
-            const int j = j0 + i;
-            if (j < mck) {
-                const long long a0 = (k == 0) ? j : i0, a1 = (k == 1) ? j : i1, a2 = (k == 2) ? j : i2;
-                v = fma_rn(etap[p * 3 + i], in[(a0 * in1 + a1) * in2 + a2], v);
-            }
+            for (int i = 0; i < 3; i++) rt[i] = etap[pr * 3 + i];
         }
-        if (MODE == MP_PLAIN) {
-            out[idx] = v;
-        } else {
-            const int p0 = (int)i0, p1 = (int)i1, p2 = (int)i2;
-            const bool isnew = !kept_pos(g.dim[0].m, p0) || !kept_pos(g.dim[1].m, p1) || !kept_pos(g.dim[2].m, p2);
-            if (!isnew) continue;
+        bool rownew = true;
+        long long sbase = 0;
+        if (MODE != MP_PLAIN) {
+            const int p0 = (int)i0, p1 = (int)i1;
+            const bool k0 = kept_pos(g.dim[0].m, p0), k1 = kept_pos(g.dim[1].m, p1);
+            rownew = !k0 || !k1;
             long long cr = (long long)kept_before(p0) * g.dim[1].mc * g.dim[2].mc;
-            if (kept_pos(g.dim[0].m, p0)) {
-                cr += (long long)kept_before(p1) * g.dim[2].mc;
-                if (kept_pos(g.dim[1].m, p1)) cr += kept_before(p2);
+            if (k0) cr += (long long)kept_before(p1) * g.dim[2].mc;
+            sbase = g.Nprev + row * s2 - cr;
+        }
+        for (long long i2 = lane; i2 < s2; i2 += 32) {
+            const long long idx = row * s2 + i2;
+            int j0;
+            T tp[3];
+            if (k == 2) {
+                j0 = efirst[i2];
+#pragma unroll
+                for (int i = 0; i < 3; i++) tp[i] = etap[i2 * 3 + i];
+            } else {
+                j0 = rj0;
+#pragma unroll
+                for (int i = 0; i < 3; i++) tp[i] = rt[i];
             }
-            const long long si = g.Nprev + idx - cr;
-            if (MODE == MP_RT_FINAL) stream[si] = sub_rn(gsrc[idx], v);
-            else out[idx] = add_rn(coef[si], v);
+            T v = (T)0;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                const int j = j0 + i;
+                if (j < mck) {
+                    const long long a0 = (k == 0) ? j : i0, a1 = (k == 1) ? j : i1, a2 = (k == 2) ? j : i2;
+                    v = fma_rn(tp[i], in[(a0 * in1 + a1) * in2 + a2], v);
+                }
+            }
+            if (MODE == MP_PLAIN) {
+                out[idx] = v;
+            } else {
+                const int p2 = (int)i2;
+                if (!rownew && kept_pos(g.dim[2].m, p2)) continue;
+                const long long si = sbase + i2 - (rownew ? 0 : kept_before(p2));
+                if (MODE == MP_RT_FINAL) stream[si] = sub_rn(gsrc[idx], v);
+                else out[idx] = add_rn(coef[si], v);
+            }
         }
     }
 }
@@ -109,6 +131,8 @@ __global__ void copy_kernel(T *dst, const T *src, long long n)
 }
 
 unsigned grid_for(long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16); }
+// rows of kMpWarps warps per block, capped at 16 blocks per SM
+unsigned grid_rows(long long rows) { return (unsigned)std::min<long long>((rows + kMpWarps - 1) / kMpWarps, 152LL * 16); }
 
 // y_f = (x)_k M_l P_k y, the last dimension-0 pass in a final mode
 template <typename T, int MODE>
@@ -118,17 +142,15 @@ cudaError_t mass_prolong_all(const LevelGeom<T> &g, const T *y, T *t1, T *t2, T 
     const long long m0 = g.dim[0].m, m1 = g.dim[1].m, m2 = g.dim[2].m;
     const long long c0 = g.dim[0].mc, c1 = g.dim[1].mc;
     // dim 2: c0 x c1 x c2 -> c0 x c1 x m2
-    long long n = c0 * c1 * m2;
-    mass_prolong_kernel<T, MP_PLAIN><<<grid_for(n), 256, 0, s>>>(y, t1, c0, c1, m2, 2, g.dim[2].mc, g.dim[2].etap,
-                                                                g.dim[2].efirst, g, nullptr, nullptr, nullptr);
+    constexpr int B = 32 * kMpWarps;
+    mass_prolong_kernel<T, MP_PLAIN><<<grid_rows(c0 * c1), B, 0, s>>>(y, t1, c0, c1, m2, 2, g.dim[2].mc, g.dim[2].etap,
+                                                                     g.dim[2].efirst, g, nullptr, nullptr, nullptr);
     // dim 1: -> c0 x m1 x m2
-    n = c0 * m1 * m2;
-    mass_prolong_kernel<T, MP_PLAIN><<<grid_for(n), 256, 0, s>>>(t1, t2, c0, m1, m2, 1, g.dim[1].mc, g.dim[1].etap,
-                                                                g.dim[1].efirst, g, nullptr, nullptr, nullptr);
+    mass_prolong_kernel<T, MP_PLAIN><<<grid_rows(c0 * m1), B, 0, s>>>(t1, t2, c0, m1, m2, 1, g.dim[1].mc, g.dim[1].etap,
+                                                                     g.dim[1].efirst, g, nullptr, nullptr, nullptr);
     // dim 0: -> m0 x m1 x m2, final
-    n = m0 * m1 * m2;
-    mass_prolong_kernel<T, MODE><<<grid_for(n), 256, 0, s>>>(t2, out, m0, m1, m2, 0, g.dim[0].mc, g.dim[0].etap,
-                                                            g.dim[0].efirst, g, gsrc, stream, coef);
+    mass_prolong_kernel<T, MODE><<<grid_rows(m0 * m1), B, 0, s>>>(t2, out, m0, m1, m2, 0, g.dim[0].mc, g.dim[0].etap,
+                                                                 g.dim[0].efirst, g, gsrc, stream, coef);
     count_launch(3);
     return cudaGetLastError();
 }

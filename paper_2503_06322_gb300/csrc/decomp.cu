@@ -7,8 +7,11 @@
 //                  symbol store; or a coefficient store), the coarse copy v_c
 //                  and the coarse right-hand side of the correction
 //                  (mass_trans);
-//   rsym_kernel    the restriction of decompression: the dequantized symbols
-//                  of one level through the same mass_trans.
+//   rsym_kernel    the restriction of the inverse direction: the dequantized
+//                  symbols of one level through the same mass_trans
+//                  (decompression), a level of a coefficient stream
+//                  (recomposition), or a dense level grid, all or only its
+//                  new nodes, through P^T M_l or P^T (the adjoints).
 //
 // Both are warp-specialised plane pipelines.  A CTA owns a tile of 14 x 32
 // coarse nodes in dims (1, 2) and a segment of coarse planes of dim 0.  One
@@ -148,8 +151,9 @@ __device__ __forceinline__ TileGeom tile_geom(const LevelGeom<T> &g, int seg_len
 }
 
 template <typename T>
-__device__ __forceinline__ PlaneInfo<T> plane_info(const LevelGeom<T> &g, const TileGeom &tg, int p)
+__device__ __forceinline__ PlaneInfo<T> plane_info(const LevelGeom<T> &g, const TileGeom &tg, int p, bool ptap = false)
 {
+    const T *tap0 = ptap ? g.dim[0].ptap : g.dim[0].tap;
     const int m0 = g.dim[0].m, mc0 = g.dim[0].mc;
     PlaneInfo<T> pi;
     int jlo = first_coarse_at_or_after(g.dim[0], p - 2);
@@ -163,7 +167,7 @@ __device__ __forceinline__ PlaneInfo<T> plane_info(const LevelGeom<T> &g, const 
         const int j = jlo + i;
         const int o = p - cpos_of(m0, mc0, j);
         const bool inj = j < tg.J0b;
-        pi.tr[i] = (inj && o >= -2 && o <= 2) ? g.dim[0].tap[j * 5 + o + 2] : (T)0;
+        pi.tr[i] = (inj && o >= -2 && o <= 2) ? tap0[j * 5 + o + 2] : (T)0;
         const int d = jc - j;
         pi.tm[i] = (inj && d >= -1 && d <= 1) ? g.dim[0].mtap[j * 3 + d + 1] : (T)0;
     }
@@ -189,7 +193,7 @@ struct WarpRows {
 
 template <typename T>
 __device__ __forceinline__ void warp_rows(const LevelGeom<T> &g, const TileGeom &tg, int c, bool use_mass,
-                                          WarpRows<T> &w)
+                                          WarpRows<T> &w, bool ptap = false)
 {
     const int m1 = g.dim[1].m, mc1 = g.dim[1].mc, m2 = g.dim[2].m;
     w.j1a = tg.J1 + 2 * c;
@@ -202,7 +206,7 @@ __device__ __forceinline__ void warp_rows(const LevelGeom<T> &g, const TileGeom 
     w.offb = w.Rb - w.Ra;
     w.rl0 = w.Ra - 2 - tg.lo1;
     w.rm0 = (uint32_t)(w.Ra - 2) * (uint32_t)m2;
-    const T *tap = g.dim[1].tap, *mtap = g.dim[1].mtap;
+    const T *tap = ptap ? g.dim[1].ptap : g.dim[1].tap, *mtap = g.dim[1].mtap;
 #pragma unroll
     for (int o = 0; o < 5; o++) {
         w.t1a[o] = w.va ? tap[ja * 5 + o] : (T)0;
@@ -246,8 +250,9 @@ struct LaneCols {
 
 template <typename T>
 __device__ __forceinline__ void lane_cols(const LevelGeom<T> &g, const TileGeom &tg, int lane, bool use_mass,
-                                          LaneCols<T> &l)
+                                          LaneCols<T> &l, bool ptap = false)
 {
+    const T *tap2 = ptap ? g.dim[2].ptap : g.dim[2].tap;
     const int m2 = g.dim[2].m, mc2 = g.dim[2].mc;
     l.j2 = tg.J2 + lane;
     l.colv = lane < tg.n2;
@@ -259,7 +264,7 @@ __device__ __forceinline__ void lane_cols(const LevelGeom<T> &g, const TileGeom 
     l.wr2 = l.has_b ? g.dim[2].wr[l.Ca + 1] : (T)0;
 #pragma unroll
     for (int o = 0; o < 5; o++) {
-        l.t2[o] = l.colv ? g.dim[2].tap[j * 5 + o] : (T)0;
+        l.t2[o] = l.colv ? tap2[j * 5 + o] : (T)0;
         l.m2t[o] = (T)0;
     }
     if (use_mass) {
@@ -675,19 +680,26 @@ decomp_kernel(RestrictArgs<T> a, int seg_len)
 }
 
 // ---------------------------------------------------------------------------
-// rsym_kernel: b = ((x)_k P^T M_l) w, w = dequantized symbols of level l on
-// its new nodes and 0 on the kept ones (the inverse of Alg. 1 applies the
-// same mass_trans to the decoded coefficients).  The producer stages each
-// plane's symbol rows (a row of a kept plane that is kept in dim 1 holds
-// only its odd positions in the stream); the consumers dequantize the region
-// together into one of two shared tiles W, meet at one named barrier per
-// plane (which also carries their vote on a wait that ran out), hand the
+// rsym_kernel: b = ((x)_k R) w with R = P^T M_l (or P^T: use_ptap), where w
+// is, by source,
+//   SYMBOLS  the dequantized symbols of level l on its new nodes, 0 on the
+//            kept ones (the inverse of Alg. 1 applies the same mass_trans to
+//            the decoded coefficients);
+//   STREAM   level l of a coefficient stream, laid out like the symbols;
+//   DENSE    a level-l grid, every node or (dense_new_only) its new nodes.
+// The producer stages each plane's rows (a row of a stream's kept plane that
+// is kept in dim 1 holds only its odd positions); the consumers expand the
+// region together into one of the shared tiles W, meet at one named barrier
+// per plane (which also carries their vote on a wait that ran out), hand the
 // stage back, and restrict W as decomp_kernel restricts v.
 
-template <typename T>
+template <typename T, int SRC>
 struct RsymSmem {
+    // staged element: symbols (SYMBOLS) or values (STREAM, DENSE)
+    using E = typename std::conditional<SRC == (int)WSrc::SYMBOLS, uint16_t, T>::type;
+    static constexpr bool ESC = SRC == (int)WSrc::SYMBOLS;
     static constexpr int NST = rsym_stages<T>();
-    static constexpr int PB = stage_pitch<uint16_t>();
+    static constexpr int PB = stage_pitch<E>();
     static constexpr size_t stage_bytes = (size_t)DR1 * PB;
     static constexpr int WROWS = DR1 + 6;     // zero rows around the region: two before, up to four after
     static constexpr size_t wtile_bytes = (size_t)WROWS * kWPitch * sizeof(T);
@@ -699,7 +711,7 @@ struct RsymSmem {
     static constexpr size_t off_rows = (off_info + NST * sizeof(PlaneInfo<T>) + 15) & ~size_t(15);
     static constexpr int EPITCH = DR2;           // escaped codes of a plane: [DR1][DR2] int64
     static constexpr size_t off_esc = off_rows + (size_t)NST * DR1 * 16;
-    static constexpr size_t bytes = off_esc + 2 * (size_t)DR1 * EPITCH * 8;
+    static constexpr size_t bytes = off_esc + (ESC ? 2 * (size_t)DR1 * EPITCH * 8 : 0);
 };
 
 // an asynchronous 8-byte global -> shared copy (its own completion group per thread)
@@ -710,14 +722,15 @@ __device__ __forceinline__ void cp_async8(void *dst_smem, const void *src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// where a staged symbol row of a plane sits in the stream, written by the
-// producer beside the row: the stream index of its first node (for escapes),
-// the offset of its first symbol inside the staged copy, and whether the row
-// holds every node (1) or only the new nodes of a kept row (0)
+// where a staged row of a plane sits in its source, written by the producer
+// beside the row: the stream index of its first node (for escapes), the
+// offset of its first element inside the staged copy, whether the row holds
+// every node (1: a new row of the stream, or any row of a dense grid) or only
+// the new nodes of a kept row (0), and whether every node of the row is new
 struct SymRow {
     long long rb;
     int off;
-    int rownew;
+    short rownew, allnew;
 };
 
 __device__ __forceinline__ bool named_sync_or(int id, int nthreads, bool pred)
@@ -734,11 +747,14 @@ __device__ __forceinline__ bool named_sync_or(int id, int nthreads, bool pred)
     return r != 0;
 }
 
-template <typename T>
+template <typename T, int SRC>
 __global__ void __launch_bounds__(DTHREADS, 2)
 rsym_kernel(RestrictArgs<T> a, int seg_len)
 {
-    using S = RsymSmem<T>;
+    using S = RsymSmem<T, SRC>;
+    using E = typename S::E;
+    constexpr bool SYM = SRC == (int)WSrc::SYMBOLS, DENSE = SRC == (int)WSrc::DENSE;
+    const bool ptap = a.use_ptap != 0;
     constexpr int NST = S::NST, PB = S::PB;
     constexpr int NQ = (DR2 + 3) / 4;   // quads of four nodes per region row
     constexpr int kDqItems = (DR1 * NQ + DCW * 32 - 1) / (DCW * 32);   // quads per thread and plane
@@ -775,7 +791,7 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
     if (warp == DCW) {
         // ---------------- producer: symbol rows of each plane ----------------
         PlaneInfo<T> pnext;
-        if (lane == 0) pnext = plane_info(g, tg, tg.lo0);
+        if (lane == 0) pnext = plane_info(g, tg, tg.lo0, ptap);
         int k = 0;
         for (int p = tg.lo0; p <= tg.hi0; p++, k++) {
             const int slot = k % NST;
@@ -785,22 +801,27 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
             }
             unsigned char *dst0 = smem_raw + S::off_stage + slot * S::stage_bytes;
             const bool k0 = kept_pos(m0, p);
-            const long long pb = plane_base_of(g, p);
+            const long long pb = DENSE ? 0 : plane_base_of(g, p);
             uint32_t nb = 0;
             const unsigned char *src = nullptr;
             if (lane < tg.r1n) {
                 const int p1 = tg.lo1 + lane;
-                const bool rownew = !k0 || !kept_pos(m1, p1);
-                const long long rb = row_base(g, pb, k0, p1);
+                const bool allnew = !k0 || !kept_pos(m1, p1);
+                // stream sources hold the new nodes only; a dense grid holds every node
+                const bool rownew = DENSE || allnew;
+                const long long rb = DENSE ? ((long long)p * m1 + p1) * m2 : row_base(g, pb, k0, p1);
                 const long long first = rownew ? rb + tg.lo2 : rb + (tg.lo2 >> 1);
                 const int cnt = rownew ? tg.r2n : ((tg.hi2 - tg.lo2) >> 1);
-                const uintptr_t g0 = reinterpret_cast<uintptr_t>(si_.sym + first);
+                const E *base = SYM ? reinterpret_cast<const E *>(si_.sym)
+                                    : reinterpret_cast<const E *>(DENSE ? a.v : a.coef_in);
+                const uintptr_t g0 = reinterpret_cast<uintptr_t>(base + first);
                 SymRow sr_;
                 sr_.rb = rb;
-                sr_.off = (int)((g0 & 15) >> 1);
+                sr_.off = (int)((g0 & 15) / sizeof(E));
                 sr_.rownew = rownew ? 1 : 0;
+                sr_.allnew = allnew ? 1 : 0;
                 rowinfo[slot * DR1 + lane] = sr_;
-                const uintptr_t g1 = g0 + (uintptr_t)cnt * 2;
+                const uintptr_t g1 = g0 + (uintptr_t)cnt * sizeof(E);
                 const uintptr_t s0 = g0 & ~uintptr_t(15);
                 uintptr_t s1 = (g1 + 15) & ~uintptr_t(15);
                 const uintptr_t lim = reinterpret_cast<uintptr_t>(a.src_end) & ~uintptr_t(15);
@@ -811,8 +832,8 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
                 src = reinterpret_cast<const unsigned char *>(s0);
                 if (tail) {
                     const uintptr_t t0 = s1 > g0 ? s1 : g0;
-                    for (uintptr_t b = t0; b < g1; b += 2)
-                        *reinterpret_cast<uint16_t *>(dst0 + lane * PB + (b - s0)) = *reinterpret_cast<const uint16_t *>(b);
+                    for (uintptr_t b = t0; b < g1; b += sizeof(E))
+                        *reinterpret_cast<E *>(dst0 + lane * PB + (b - s0)) = *reinterpret_cast<const E *>(b);
                 }
             }
             if (lane == 0) pinfo[slot] = pnext;
@@ -822,7 +843,7 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
             if (lane == 0) mbar_arrive_expect_tx(&full[slot], bytes);
             __syncwarp();
             if (nb) bulk_g2s(dst0 + lane * PB, src, nb, &full[slot]);
-            if (lane == 0 && p < tg.hi0) pnext = plane_info(g, tg, p + 1);
+            if (lane == 0 && p < tg.hi0) pnext = plane_info(g, tg, p + 1, ptap);
         }
         for (int kk = max(0, k - NST); kk < k; kk++)
             wait_sleep_bounded(&full[kk % NST], (uint32_t)((kk / NST) & 1), kWaitPolls);
@@ -831,10 +852,11 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
 
     // ---------------- consumers ----------------
     WarpRows<T> wr;
-    warp_rows(g, tg, warp, false, wr);
+    warp_rows(g, tg, warp, false, wr, ptap);
     LaneCols<T> lc;
-    lane_cols(g, tg, lane, false, lc);
-    const T q = q_of<T>(si_.sc, g.level);
+    lane_cols(g, tg, lane, false, lc, ptap);
+    const T q = SYM ? q_of<T>(si_.sc, g.level) : (T)0;
+    const bool new_only = a.dense_new_only != 0;
     const int lanecol = lc.ca - 2;
     const long long cstride = (long long)mc1 * mc2;
     const long long out_a = (long long)wr.j1a * mc2 + lc.j2, out_b = (long long)wr.j1b * mc2 + lc.j2;
@@ -870,20 +892,27 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
             const int i1 = u / NQ, qd = u - i1 * NQ, i2b = qd * 4;
             if (!(u < tg.r1n * NQ && qd < nq)) continue;
             const SymRow r = ri[i1];
-            const uint16_t *sr = reinterpret_cast<const uint16_t *>(st + i1 * PB) + r.off;
+            const E *sr = reinterpret_cast<const E *>(st + i1 * PB) + r.off;
             T wv[4];
 #pragma unroll
             for (int e = 0; e < 4; e++) {
                 const int i2 = i2b + e, p2 = tg.lo2 + i2;
                 wv[e] = (T)0;
-                if (i2 < tg.r2n && (r.rownew || !kept_pos(m2, p2))) {
+                if constexpr (DENSE) {
+                    // every node of a dense grid, or only its new nodes
+                    if (i2 < tg.r2n && (!new_only || r.allnew || !kept_pos(m2, p2))) wv[e] = (T)sr[i2];
+                } else if (i2 < tg.r2n && (r.rownew || !kept_pos(m2, p2))) {
                     const int sx = r.rownew ? i2 : (i2 - 1) >> 1;
-                    const unsigned sv = sr[sx];
-                    if (sv != 0u) {
-                        wv[e] = mul_rn((T)((int)sv - (int)(si_.D / 2)), q);
+                    if constexpr (SYM) {
+                        const unsigned sv = sr[sx];
+                        if (sv != 0u) {
+                            wv[e] = mul_rn((T)((int)sv - (int)(si_.D / 2)), q);
+                        } else {
+                            cp_async8(et + i1 * S::EPITCH + i2, si_.esc + r.rb + (r.rownew ? p2 : (p2 - 1) >> 1));
+                            escm |= 1u << (4 * it + e);
+                        }
                     } else {
-                        cp_async8(et + i1 * S::EPITCH + i2, si_.esc + r.rb + (r.rownew ? p2 : (p2 - 1) >> 1));
-                        escm |= 1u << (4 * it + e);
+                        wv[e] = (T)sr[sx];
                     }
                 }
             }
@@ -900,7 +929,7 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
     };
     // the escaped codes of plane kk (this thread's, copied one iteration ago) into its tile
     auto patch = [&](int kk, T *Wt, unsigned escm) {
-        if (!escm) return;
+        if (!SYM || !escm) return;
         const long long *et = esc_tile0 + (size_t)(kk & 1) * DR1 * S::EPITCH;
 #pragma unroll
         for (int it = 0; it < kDqItems; it++) {
@@ -1206,21 +1235,37 @@ cudaError_t launch_decomp(Sink sink, const RestrictArgs<T> &a0, cudaStream_t s)
 template <typename T>
 cudaError_t launch_restrict_symbols(const RestrictArgs<T> &a0, cudaStream_t s)
 {
+    return launch_restrict_planes<T>(WSrc::SYMBOLS, a0, s);
+}
+
+template <typename T>
+cudaError_t launch_restrict_planes(WSrc src, const RestrictArgs<T> &a0, cudaStream_t s)
+{
     RestrictArgs<T> a = a0;
     a.wait_limit = g_wait_limit;
     const int mc0 = a.g.dim[0].mc, mc1 = a.g.dim[1].mc, mc2 = a.g.dim[2].mc;
+    const long long nl = (long long)a.g.dim[0].m * a.g.dim[1].m * a.g.dim[2].m;
+    // the end of the staged source: the level's stream (new nodes) or its dense grid
+    if (src == WSrc::STREAM) a.src_end = a.coef_in + a.g.Nprev + (nl - (long long)mc0 * mc1 * mc2);
+    if (src == WSrc::DENSE) a.src_end = a.v + nl;
     const int gx = (mc2 + DT2 - 1) / DT2, gy = (mc1 + DT1 - 1) / DT1;
-    const size_t sm = RsymSmem<T>::bytes;
-    static PerDeviceOnce attr;
-    cudaError_t e = once_per_device(attr, [] {
-        return cudaFuncSetAttribute(rsym_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    });
-    if (e != cudaSuccess) return e;
-    const int seg = choose_segment(mc0, (long long)gx * gy, resident_ctas(rsym_kernel<T>, DTHREADS, sm));
-    const int gz = (mc0 + seg - 1) / seg;
-    rsym_kernel<T><<<dim3(gx, gy, gz), DTHREADS, sm, s>>>(a, seg);
-    count_launch();
-    return cudaGetLastError();
+    auto go = [&](auto kern, size_t sm, PerDeviceOnce &attr) -> cudaError_t {
+        cudaError_t e = once_per_device(attr, [&] {
+            return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        });
+        if (e != cudaSuccess) return e;
+        const int seg = choose_segment(mc0, (long long)gx * gy, resident_ctas(kern, DTHREADS, sm));
+        const int gz = (mc0 + seg - 1) / seg;
+        kern<<<dim3(gx, gy, gz), DTHREADS, sm, s>>>(a, seg);
+        count_launch();
+        return cudaGetLastError();
+    };
+    static PerDeviceOnce attr_sym, attr_stream, attr_dense;
+    if (src == WSrc::STREAM)
+        return go(rsym_kernel<T, (int)WSrc::STREAM>, RsymSmem<T, (int)WSrc::STREAM>::bytes, attr_stream);
+    if (src == WSrc::DENSE)
+        return go(rsym_kernel<T, (int)WSrc::DENSE>, RsymSmem<T, (int)WSrc::DENSE>::bytes, attr_dense);
+    return go(rsym_kernel<T, (int)WSrc::SYMBOLS>, RsymSmem<T, (int)WSrc::SYMBOLS>::bytes, attr_sym);
 }
 
 template <typename T>
@@ -1247,6 +1292,8 @@ template cudaError_t launch_decomp<float>(Sink, const RestrictArgs<float> &, cud
 template cudaError_t launch_decomp<double>(Sink, const RestrictArgs<double> &, cudaStream_t);
 template cudaError_t launch_restrict_symbols<float>(const RestrictArgs<float> &, cudaStream_t);
 template cudaError_t launch_restrict_symbols<double>(const RestrictArgs<double> &, cudaStream_t);
+template cudaError_t launch_restrict_planes<float>(WSrc, const RestrictArgs<float> &, cudaStream_t);
+template cudaError_t launch_restrict_planes<double>(WSrc, const RestrictArgs<double> &, cudaStream_t);
 template cudaError_t launch_expand_planes<float>(WSrc, const LevelGeom<float> &, const float *, const float *,
                                                  const SymIn &, float *, cudaStream_t);
 template cudaError_t launch_expand_planes<double>(WSrc, const LevelGeom<double> &, const double *, const double *,

@@ -1,20 +1,12 @@
-// levels.cu -- per-level kernels of the multilevel decomposition (Sec. IV-A,
-// Alg. 1) and of its inverse, for sm_103a.
-//
-// restrict_kernel is the bandwidth-critical one.  One CTA owns an 8 x 32 tile
-// of coarse nodes in dims (1, 2) and streams a segment of dim 0 plane by plane
-// (2.5-D blocking).  For each fine plane it
-//   A. stages the level-l values of the tile region (with a 2-node halo) in
-//      shared memory, three planes deep;
-//   B. forms w, the new-node coefficients mc_l = v - lerp(v) (Alg. 1 lerp),
-//      and, on the nodes it owns, hands them to a sink: quantization with the
-//      level's bin + block histogram + symbol store (compression, Alg. 1
-//      MapAndProcess and Alg. 2 histogram), or a coefficient store;
-//   C./D. applies the restriction P^T M_l (Alg. 1 mass_trans) along dim 2
-//      and dim 1 in shared memory and accumulates the dim-0 taps in registers,
-//      so that only the coarse result b (1/8 of the level) is written.
-// The result does not depend on the tiling: every coarse value sums its taps
-// in a fixed order.
+// levels.cu -- per-level pieces of the multilevel decomposition (Sec. IV-A,
+// Alg. 1) and of its inverse that are not the plane-streaming level kernels
+// (those are in decomp.cu), for sm_103a:
+//   * the Thomas solves of the coarse mass matrix along each dimension;
+//   * level 0 (quantized or stored as it is) and its inverse;
+//   * the norms of the field and the level bins;
+//   * coarse_kernel: every level whose arrays fit one CTA's shared memory,
+//     and level 0, in a single launch;
+//   * the dispatch of restriction requests to the plane pipelines.
 #include <cfloat>
 #include <type_traits>
 #include "levels_dev.cuh"
@@ -22,387 +14,7 @@
 namespace hpdr {
 namespace {
 
-constexpr int TT1 = 8, TT2 = 32;                  // coarse tile (dims 1, 2)
-constexpr int RR1 = 2 * TT1 + 4, RR2 = 2 * TT2 + 4;  // largest fine region
-constexpr int RTHREADS = 256;
-constexpr int kHistSmemMax = 16384;
 constexpr int kNormBlocks = 152 * 8;
-
-constexpr int NST = 4;   // planes in flight per CTA
-
-template <typename E>
-__host__ __device__ constexpr int row_pitch_bytes() { return ((RR2 * (int)sizeof(E) + 32) + 15) & ~15; }
-
-// Per-plane dim-0 restriction info: the first coarse index whose five-tap
-// window contains the plane, and the taps of the three candidates.
-template <typename T>
-struct PlaneTaps {
-    int jlo;
-    T t[3];
-};
-
-// The planes the restriction streams through come from global memory by
-// bulk asynchronous row copies (one per region row, 16-byte aligned around
-// the row), completed on one mbarrier per stage.  E = element type of the
-// staged rows (T for FIELD, uint16_t for SYMBOLS).
-//
-// FIELD source: the multilinear interpolant is applied separably.  For every
-// kept plane the CTA forms J = I_1 I_2 v (interpolation along dims 2 and 1 of
-// that plane) once; the new-node coefficients are then
-//     kept plane:  w = v - J(p0)                       (new nodes only)
-//     new plane:   w = v - (wl0 J(p0-1) + wr0 J(p0+1)).
-template <typename T, int SRC, int SINK>
-__global__ void __launch_bounds__(RTHREADS, 3)
-restrict_kernel(RestrictArgs<T> a, int seg_len)
-{
-    typedef typename std::conditional<SRC == (int)WSrc::SYMBOLS, uint16_t, T>::type E;
-    constexpr bool STAGED = (SRC == (int)WSrc::FIELD || SRC == (int)WSrc::SYMBOLS);
-    constexpr bool FIELD = (SRC == (int)WSrc::FIELD);
-    constexpr int PB = row_pitch_bytes<E>();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int m0 = a.g.dim[0].m, m1 = a.g.dim[1].m, m2 = a.g.dim[2].m;
-    const int mc0 = a.g.dim[0].mc, mc1 = a.g.dim[1].mc, mc2 = a.g.dim[2].mc;
-    const int J2 = blockIdx.x * TT2, J1 = blockIdx.y * TT1;
-    const int J0a = blockIdx.z * seg_len;
-    const int J0b = min(J0a + seg_len, mc0);
-    if (J0a >= J0b) return;
-    const int n2 = min(TT2, mc2 - J2), n1 = min(TT1, mc1 - J1);
-    const int lo2 = max(0, cpos_of(m2, mc2, J2) - 2) & ~1;
-    const int hi2 = min(m2 - 1, cpos_of(m2, mc2, J2 + n2 - 1) + 2);
-    const int lo1 = max(0, cpos_of(m1, mc1, J1) - 2) & ~1;
-    const int hi1 = min(m1 - 1, cpos_of(m1, mc1, J1 + n1 - 1) + 2);
-    const int lo0 = max(0, cpos_of(m0, mc0, J0a) - 2) & ~1;
-    const int hi0 = min(m0 - 1, cpos_of(m0, mc0, J0b - 1) + 2);
-    const int r1n = hi1 - lo1 + 1, r2n = hi2 - lo2 + 1;
-    const int o2a = cpos_of(m2, mc2, J2), o2b = (J2 + n2 < mc2) ? cpos_of(m2, mc2, J2 + n2) : m2;
-    const int o1a = cpos_of(m1, mc1, J1), o1b = (J1 + n1 < mc1) ? cpos_of(m1, mc1, J1 + n1) : m1;
-    const int o0a = cpos_of(m0, mc0, J0a), o0b = (J0b < mc0) ? cpos_of(m0, mc0, J0b) : m0;
-
-    // shared memory layout
-    unsigned char *stage_base = smem_raw;
-    int *rowoff = reinterpret_cast<int *>(smem_raw + (STAGED ? NST * RR1 * PB : 0));
-    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(
-        (reinterpret_cast<uintptr_t>(rowoff + (STAGED ? NST * RR1 : 0)) + 15) & ~uintptr_t(15));
-    PlaneTaps<T> *ptaps = reinterpret_cast<PlaneTaps<T> *>(mbar + (STAGED ? NST : 0));  // [NST]
-    T *W = reinterpret_cast<T *>(ptaps + NST);                       // [RR1][RR2]
-    T *Jb = W + RR1 * RR2;                                           // [2][RR1][RR2] (FIELD)
-    T *wl2s = Jb + (FIELD ? 2 * RR1 * RR2 : 0), *wr2s = wl2s + RR2;  // [RR2]
-    T *wl1s = wr2s + RR2, *wr1s = wl1s + RR1;                        // [RR1]
-    unsigned int *hs = reinterpret_cast<unsigned int *>(wr1s + RR1);
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool smem_hist = (SINK == (int)Sink::QUANT) && a.qo.D <= (unsigned)kHistSmemMax;
-    const T *tap2src = a.use_ptap ? a.g.dim[2].ptap : a.g.dim[2].tap;
-    const T *tap1src = a.use_ptap ? a.g.dim[1].ptap : a.g.dim[1].tap;
-    const T *tap0src = a.use_ptap ? a.g.dim[0].ptap : a.g.dim[0].tap;
-    for (int i = tid; i < r2n; i += RTHREADS) { wl2s[i] = a.g.dim[2].wl[lo2 + i]; wr2s[i] = a.g.dim[2].wr[lo2 + i]; }
-    for (int i = tid; i < r1n; i += RTHREADS) { wl1s[i] = a.g.dim[1].wl[lo1 + i]; wr1s[i] = a.g.dim[1].wr[lo1 + i]; }
-    if (smem_hist)
-        for (int i = tid; i < (int)a.qo.D; i += RTHREADS) hs[i] = 0u;
-    if (STAGED && tid == 0) {
-        for (int i = 0; i < NST; i++) mbar_init(&mbar[i], 1);
-        mbar_fence_init();
-    }
-    // restriction taps of this thread's dim-2 column (phase C) and output (phase D)
-    const int jl = lane;                    // dim-2 coarse column in the tile
-    T t2[5], t1[5];
-    const int c2col = jl < n2 ? cpos_of(m2, mc2, J2 + jl) - lo2 : 0;
-#pragma unroll
-    for (int o = 0; o < 5; o++) t2[o] = jl < n2 ? tap2src[(J2 + jl) * 5 + o] : (T)0;
-    const int j1l = warp;
-    const bool outp = j1l < n1 && lane < n2;
-    const int c1r = outp ? cpos_of(m1, mc1, J1 + j1l) - lo1 : 0;
-#pragma unroll
-    for (int o = 0; o < 5; o++) t1[o] = outp ? tap1src[(J1 + j1l) * 5 + o] : (T)0;
-    __syncthreads();
-
-    double rho = 0.0;
-    if (SINK == (int)Sink::QUANT) rho = rho64_of(a.qo.sc, a.g.level);
-    T qlev = (T)0;
-    if (SRC == (int)WSrc::SYMBOLS) qlev = q_of<T>(a.symin.sc, a.g.level);
-    const float inv_r2n = 1.0f / (float)r2n;
-
-    // ---- producer: warp 0 issues the row copies of plane p ------------------
-    auto issue = [&](int p) {
-        const int slot = (p - lo0) % NST;
-        unsigned char *dst0 = stage_base + slot * RR1 * PB;
-        const bool k0 = kept_pos(m0, p);
-        const long long pb = (SRC == (int)WSrc::SYMBOLS) ? plane_base_of(a.g, p) : 0;
-        uint32_t bytes = 0;
-        const unsigned char *src = nullptr;
-        if (lane < r1n) {
-            const int p1 = lo1 + lane;
-            uintptr_t g0, g1;   // byte range [g0, g1) of the row's data
-            if (FIELD) {
-                const T *row = a.v + ((long long)p * m1 + p1) * m2 + lo2;
-                g0 = reinterpret_cast<uintptr_t>(row);
-                g1 = g0 + (uintptr_t)r2n * sizeof(T);
-            } else {
-                const bool rownew = !k0 || !kept_pos(m1, p1);
-                const long long rb = row_base(a.g, pb, k0, p1);
-                const long long first = rownew ? rb + lo2 : rb + (lo2 >> 1);
-                const int cnt = rownew ? r2n : ((hi2 - lo2) >> 1);
-                g0 = reinterpret_cast<uintptr_t>(a.symin.sym + first);
-                g1 = g0 + (uintptr_t)cnt * 2;
-            }
-            const uintptr_t s0 = g0 & ~uintptr_t(15);
-            uintptr_t s1 = (g1 + 15) & ~uintptr_t(15);
-            const uintptr_t lim = reinterpret_cast<uintptr_t>(a.src_end) & ~uintptr_t(15);
-            uint32_t tail = 0;
-            if (s1 > lim) { tail = 1; s1 = lim; }
-            if (g1 <= g0) { s1 = s0; tail = 0; }
-            bytes = s1 > s0 ? (uint32_t)(s1 - s0) : 0u;
-            src = reinterpret_cast<const unsigned char *>(s0);
-            rowoff[slot * RR1 + lane] = (int)((g0 - s0) / sizeof(E));
-            // the last bytes of the buffer (past its last 16-byte boundary) are read with plain loads
-            if (tail) {
-                const uintptr_t t0 = s1 > g0 ? s1 : g0;
-                for (uintptr_t b = t0; b < g1; b += sizeof(E))
-                    *reinterpret_cast<E *>(dst0 + lane * PB + (b - s0)) = *reinterpret_cast<const E *>(b);
-            }
-        }
-        if (lane == 0) {
-            // dim-0 restriction taps of plane p (zero where p is outside a window or the segment)
-            PlaneTaps<T> pt;
-            int jlo = first_coarse_at_or_after(a.g.dim[0], p - 2);
-            if (jlo < J0a) jlo = J0a;
-            pt.jlo = jlo;
-#pragma unroll
-            for (int i = 0; i < 3; i++) {
-                const int j = jlo + i;
-                const int o = p - cpos_of(m0, mc0, j);
-                pt.t[i] = (j < J0b && o >= -2 && o <= 2) ? tap0src[j * 5 + o + 2] : (T)0;
-            }
-            ptaps[slot] = pt;
-        }
-        uint32_t tot = bytes;
-        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-        if (lane == 0) mbar_arrive_expect_tx(&mbar[slot], tot);
-        __syncwarp();
-        if (lane < r1n && bytes) bulk_g2s(dst0 + lane * PB, src, bytes, &mbar[slot]);
-    };
-    auto wait_plane = [&](int p) -> bool {
-        const int r = p - lo0;
-        return mbar_wait_bounded(&mbar[r % NST], (uint32_t)((r / NST) & 1), kWaitPolls);
-    };
-    auto Vrow = [&](int slot, int i1) -> const E * {
-        return reinterpret_cast<const E *>(stage_base + (slot * RR1 + i1) * PB) + rowoff[slot * RR1 + i1];
-    };
-
-    if (STAGED && warp == 0)
-        for (int p = lo0; p <= hi0 && p < lo0 + NST - 1; p++) issue(p);
-    int waited = lo0 - 1;   // planes up to here are complete
-    int jdone = lo0 - 1;    // last plane whose J is formed
-
-    T acc0 = 0, acc1 = 0, acc2 = 0;
-    int jb = J0a;
-    const long long out_col = (long long)(J1 + j1l) * mc2 + (J2 + lane);
-    const long long cstride = (long long)mc1 * mc2;
-    const int nreg = r1n * r2n;
-
-    // J = I_1 I_2 v on the region of kept plane p (slot of its coarse index parity)
-    auto form_J = [&](int p) {
-      if constexpr (FIELD) {
-        const int vs = (p - lo0) % NST;
-        T *J = Jb + (cidx_of(m0, mc0, p) & 1) * RR1 * RR2;
-        for (int idx = tid; idx < nreg; idx += RTHREADS) {
-            const int i1 = __float2int_rz(((float)idx + 0.5f) * inv_r2n);
-            const int i2 = idx - i1 * r2n;
-            const bool f1 = !kept_pos(m1, lo1 + i1), f2 = !kept_pos(m2, lo2 + i2);
-            auto I2 = [&](int r) -> T {
-                const T *row = Vrow(vs, r);
-                return f2 ? fma_rn(wr2s[i2], row[i2 + 1], mul_rn(wl2s[i2], row[i2 - 1])) : row[i2];
-            };
-            J[i1 * RR2 + i2] = f1 ? fma_rn(wr1s[i1], I2(i1 + 1), mul_rn(wl1s[i1], I2(i1 - 1))) : I2(i1);
-        }
-      }
-    };
-
-    for (int p0 = lo0; p0 <= hi0; p0++) {
-        const int s0 = (p0 - lo0) % NST;
-        bool ok = true;
-        if (STAGED) {
-            const int need = min(p0 + 1, hi0);
-            while (ok && waited < need) {
-                if (wait_plane(waited + 1)) waited++;
-                else ok = false;
-            }
-        }
-        if (__syncthreads_or(!ok)) {
-            // give up: wait (bounded) for every plane issued so far that this
-            // thread has not seen complete, the one that timed out included,
-            // so that no bulk copy still targets shared memory, then leave
-            if (tid == 0) atomicExch(a.status, (unsigned)DS_TIMEOUT);
-            const int last_issued = min(hi0, p0 + NST - 2);
-            for (int p = waited + 1; p <= last_issued; p++) wait_plane(p);
-            return;
-        }
-        const bool f0 = !kept_pos(m0, p0);
-        if constexpr (FIELD) {
-            const int pj = f0 ? p0 + 1 : p0;     // kept plane whose J this plane needs next
-            if (jdone < pj) {
-                form_J(pj);
-                jdone = pj;
-                __syncthreads();
-            }
-        }
-        // ---- B: w on the region ---------------------------------------------
-        const bool own0 = p0 >= o0a && p0 < o0b;
-        const long long pbase = plane_base_of(a.g, p0);
-        T wl0 = (T)0, wr0 = (T)0;
-        const T *Jm = Jb, *Jp = Jb;
-        if constexpr (FIELD) {
-            if (f0) {
-                wl0 = a.g.dim[0].wl[p0];
-                wr0 = a.g.dim[0].wr[p0];
-                Jm = Jb + (cidx_of(m0, mc0, p0 - 1) & 1) * RR1 * RR2;
-                Jp = Jb + (cidx_of(m0, mc0, p0 + 1) & 1) * RR1 * RR2;
-            } else {
-                Jm = Jb + (cidx_of(m0, mc0, p0) & 1) * RR1 * RR2;
-            }
-        }
-        if constexpr (SRC == (int)WSrc::SYMBOLS) {
-            // four consecutive nodes of one region row per thread, one vector store
-            constexpr int NQ = RR2 / 4;
-            for (int u = tid; u < r1n * NQ; u += RTHREADS) {
-                const int i1 = u / NQ, i2b = (u - i1 * NQ) * 4;
-                const int p1 = lo1 + i1;
-                const bool f1 = !kept_pos(m1, p1);
-                const bool rownew = f0 || f1;
-                const E *sr = Vrow(s0, i1);
-                const long long rb = row_base(a.g, pbase, !f0, p1);
-                T wv[4];
-#pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    const int i2 = i2b + e, p2 = lo2 + i2;
-                    wv[e] = (T)0;
-                    if (i2 < r2n && (rownew || !kept_pos(m2, p2))) {
-                        const int si2 = rownew ? i2 : (i2 - 1) >> 1;
-                        wv[e] = dequant_sym<T>(a.symin, sr[si2], rb + (rownew ? p2 : (p2 - 1) >> 1), qlev);
-                    }
-                }
-                T *wd = W + i1 * RR2 + i2b;
-                if constexpr (sizeof(T) == 4) {
-                    *reinterpret_cast<float4 *>(wd) = make_float4(wv[0], wv[1], wv[2], wv[3]);
-                } else {
-                    reinterpret_cast<double2 *>(wd)[0] = make_double2(wv[0], wv[1]);
-                    reinterpret_cast<double2 *>(wd)[1] = make_double2(wv[2], wv[3]);
-                }
-            }
-        } else
-        for (int idx = tid; idx < nreg; idx += RTHREADS) {
-            const int i1 = __float2int_rz(((float)idx + 0.5f) * inv_r2n);
-            const int i2 = idx - i1 * r2n;
-            const int p1 = lo1 + i1, p2 = lo2 + i2;
-            const bool f1 = !kept_pos(m1, p1);
-            const bool f2 = !kept_pos(m2, p2);
-            const bool isnew = f0 || f1 || f2;
-            T w = (T)0;
-            if constexpr (FIELD) {
-                if (isnew) {
-                    const int q = i1 * RR2 + i2;
-                    const T lerp = f0 ? fma_rn(wr0, Jp[q], mul_rn(wl0, Jm[q])) : Jm[q];
-                    w = sub_rn(Vrow(s0, i1)[i2], lerp);
-                    if (SINK != (int)Sink::NONE && own0 && p1 >= o1a && p1 < o1b && p2 >= o2a && p2 < o2b) {
-                        const bool rownew = f0 || f1;
-                        const long long si = row_base(a.g, pbase, !f0, p1) + (rownew ? p2 : (p2 - 1) >> 1);
-                        if (SINK == (int)Sink::STREAM) a.coef_out[si] = w;
-                        else quant_emit(a.qo, hs, smem_hist, si, w, rho);
-                    }
-                }
-            } else if constexpr (SRC == (int)WSrc::SYMBOLS) {
-                if (isnew) {
-                    const bool rownew = f0 || f1;
-                    const unsigned sv = Vrow(s0, i1)[rownew ? i2 : (i2 - 1) >> 1];
-                    const long long si = row_base(a.g, pbase, !f0, p1) + (rownew ? p2 : (p2 - 1) >> 1);
-                    w = dequant_sym<T>(a.symin, sv, si, qlev);
-                }
-            } else if constexpr (SRC == (int)WSrc::STREAM) {
-                if (isnew) w = a.coef_in[stream_rank(a.g, p0, p1, p2)];
-            } else {  // DENSE
-                if (isnew || !a.dense_new_only) w = a.v[((long long)p0 * m1 + p1) * m2 + p2];
-            }
-            W[i1 * RR2 + i2] = w;
-        }
-        __syncthreads();
-        // the stage of plane p0 - 1 is free: refill it with plane p0 + NST - 1
-        if (STAGED && warp == 0 && p0 + NST - 1 <= hi0) issue(p0 + NST - 1);
-        // ---- C + D: every warp restricts along dim 2 the five rows of w its
-        // coarse row needs, then along dim 1, and adds the dim-0 taps in registers
-        if (outp) {
-            T r = (T)0;
-#pragma unroll
-            for (int o = -2; o <= 2; o++) {
-                const int q1 = c1r + o;
-                if (q1 >= 0 && q1 < r1n) {
-                    const T *wr = W + q1 * RR2 + c2col;
-                    T sacc = (T)0;
-#pragma unroll
-                    for (int t = -2; t <= 2; t++) {
-                        const int q = c2col + t;
-                        if (q >= 0 && q < r2n) sacc = fma_rn(t2[t + 2], wr[t], sacc);
-                    }
-                    r = fma_rn(t1[o + 2], sacc, r);
-                }
-            }
-            PlaneTaps<T> pt;
-            if (STAGED) {
-                pt = ptaps[s0];
-            } else {
-                int jlo = first_coarse_at_or_after(a.g.dim[0], p0 - 2);
-                if (jlo < J0a) jlo = J0a;
-                pt.jlo = jlo;
-#pragma unroll
-                for (int i = 0; i < 3; i++) {
-                    const int j = jlo + i;
-                    const int o = p0 - cpos_of(m0, mc0, j);
-                    pt.t[i] = (j < J0b && o >= -2 && o <= 2) ? tap0src[j * 5 + o + 2] : (T)0;
-                }
-            }
-            while (jb < pt.jlo && jb < J0b) {
-                a.b[(long long)jb * cstride + out_col] = acc0;
-                acc0 = acc1; acc1 = acc2; acc2 = (T)0;
-                jb++;
-            }
-            acc0 = fma_rn(pt.t[0], r, acc0);
-            acc1 = fma_rn(pt.t[1], r, acc1);
-            acc2 = fma_rn(pt.t[2], r, acc2);
-            if constexpr (FIELD && SINK != (int)Sink::NONE) {
-                if (a.vc && !f0) {
-                    const int j0 = cidx_of(m0, mc0, p0);
-                    if (j0 >= J0a && j0 < J0b)
-                        a.vc[(long long)j0 * cstride + out_col] = Vrow(s0, c1r)[c2col];
-                }
-            }
-        }
-    }
-    if (outp) {
-        while (jb < J0b) {
-            a.b[(long long)jb * cstride + out_col] = acc0;
-            acc0 = acc1; acc1 = acc2; acc2 = (T)0;
-            jb++;
-        }
-    }
-    if (smem_hist) {
-        __syncthreads();
-        for (int i = tid; i < (int)a.qo.D; i += RTHREADS)
-            if (hs[i]) atomicAdd(&a.qo.hist[i], (unsigned long long)hs[i]);
-    }
-}
-
-template <typename T>
-size_t restrict_smem(WSrc src, Sink sink, unsigned int D)
-{
-    size_t b = 0;
-    if (src == WSrc::FIELD) b += (size_t)NST * RR1 * row_pitch_bytes<T>() + NST * RR1 * 4 + 16 + NST * 8;
-    else if (src == WSrc::SYMBOLS) b += (size_t)NST * RR1 * row_pitch_bytes<uint16_t>() + NST * RR1 * 4 + 16 + NST * 8;
-    b += NST * sizeof(PlaneTaps<T>);
-    b = (b + 15) & ~size_t(15);
-    size_t n = RR1 * RR2 * (src == WSrc::FIELD ? 3 : 1) + 2 * (RR1 + RR2);
-    b += n * sizeof(T) + 16;
-    if (sink == Sink::QUANT && D <= (unsigned)kHistSmemMax) b += (size_t)D * sizeof(unsigned int);
-    return b;
-}
 
 // --------------------------------------------------------------------------
 // Thomas solves of the coarse mass matrix along one dimension (Alg. 1
@@ -1031,33 +643,14 @@ int choose_segment(int mc0, long long tiles, int per_sm)
 }
 
 
-template <typename T, int SRC, int SINK>
-cudaError_t launch_restrict_t(const RestrictArgs<T> &a, cudaStream_t s)
-{
-    const int mc0 = a.g.dim[0].mc, mc1 = a.g.dim[1].mc, mc2 = a.g.dim[2].mc;
-    const int gx = (mc2 + TT2 - 1) / TT2, gy = (mc1 + TT1 - 1) / TT1;
-    size_t sm = restrict_smem<T>((WSrc)SRC, (Sink)SINK, SINK == (int)Sink::QUANT ? a.qo.D : 0);
-    static PerDeviceOnce attr;
-    cudaError_t e = once_per_device(attr, [] {
-        return cudaFuncSetAttribute(restrict_kernel<T, SRC, SINK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    160 * 1024);
-    });
-    if (e != cudaSuccess) return e;
-    const int seg = choose_segment(mc0, (long long)gx * gy, resident_ctas(restrict_kernel<T, SRC, SINK>, RTHREADS, sm));
-    const int gz = (mc0 + seg - 1) / seg;
-    restrict_kernel<T, SRC, SINK><<<dim3(gx, gy, gz), RTHREADS, sm, s>>>(a, seg);
-    count_launch();
-    return cudaGetLastError();
-}
-
-
 template <typename T>
 cudaError_t launch_restrict(WSrc src, Sink sink, const RestrictArgs<T> &a, cudaStream_t s)
 {
+    // the field source (compression, decomposition) and the decompression-side
+    // sources (symbols, a coefficient stream, a dense level grid) run in the
+    // warp-specialised plane pipelines of decomp.cu
     if (src == WSrc::FIELD) return launch_decomp<T>(sink, a, s);
-    if (src == WSrc::STREAM) return launch_restrict_t<T, 1, 0>(a, s);
-    if (src == WSrc::SYMBOLS) return launch_restrict_symbols<T>(a, s);
-    return launch_restrict_t<T, 3, 0>(a, s);
+    return launch_restrict_planes<T>(src, a, s);
 }
 
 constexpr bool kSolveStream = true;   // strided dimensions: streaming sweeps

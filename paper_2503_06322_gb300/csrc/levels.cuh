@@ -57,6 +57,10 @@ template <typename T>
 cudaError_t launch_decomp(Sink sink, const RestrictArgs<T> &a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_restrict_symbols(const RestrictArgs<T> &a, cudaStream_t s);
+// the same plane pipeline over any decompression-side source: SYMBOLS,
+// STREAM (a coefficient stream) or DENSE (a level-l grid, all or new nodes)
+template <typename T>
+cudaError_t launch_restrict_planes(WSrc src, const RestrictArgs<T> &a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_expand_planes(WSrc src, const LevelGeom<T> &g, const T *vc, const T *coef_in,
                                  const SymIn &symin, T *out, cudaStream_t s);
