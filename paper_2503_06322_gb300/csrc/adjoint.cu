@@ -33,9 +33,9 @@ enum { MP_PLAIN = 0, MP_RT_FINAL = 1, MP_DT_FINAL = 2 };
 constexpr int kMpWarps = 8;
 template <typename T, int MODE>
 __global__ void __launch_bounds__(32 * kMpWarps)
-mass_prolong_kernel(const T *__restrict__ in, T *out, long long s0, long long s1, long long s2, int k,
+mass_prolong_kernel(const T *__restrict__ in, T *__restrict__ out, long long s0, long long s1, long long s2, int k,
                     int mck, const T *__restrict__ etap, const int *__restrict__ efirst, LevelGeom<T> g,
-                    const T *gsrc, T *stream, const T *coef)
+                    const T *__restrict__ gsrc, T *__restrict__ stream, const T *__restrict__ coef)
 {
     const long long rows = s0 * s1;
     const long long in1 = (k == 1) ? mck : s1, in2 = (k == 2) ? mck : s2;
@@ -62,6 +62,8 @@ mass_prolong_kernel(const T *__restrict__ in, T *out, long long s0, long long s1
             if (k0) cr += (long long)kept_before(p1) * g.dim[2].mc;
             sbase = g.Nprev + row * s2 - cr;
         }
+        // four columns per lane in flight (the buffers do not alias)
+#pragma unroll 4
         for (long long i2 = lane; i2 < s2; i2 += 32) {
             const long long idx = row * s2 + i2;
             int j0;
