@@ -219,15 +219,48 @@ __global__ void bins_l2s_kernel(L2sArgs a, Scalars *sc)
     }
 }
 
-// the whole compression of one field, enqueued on s without any host wait;
-// the container size and status stay in w.sc (device)
+// the container header's fields of one compression
+template <typename T>
+HeaderArgs header_args(const Plan *P, int ndim, const size_t *dims, double tol, int tol_kind, int mode, unsigned D,
+                       unsigned K, const Ws &w)
+{
+    HeaderArgs h;
+    memset(&h, 0, sizeof(h));
+    h.dtype = sizeof(T) == 4 ? 0 : 1;
+    h.ndim = ndim;
+    h.L = P->L;
+    h.mode = mode;
+    h.tol_kind = tol_kind;
+    for (int k = 0; k < 3; k++) h.dims[k] = k < ndim ? dims[k] : 1;
+    h.D = D; h.K = K; h.tol = tol; h.N = (unsigned long long)P->N[P->L]; h.hist = w.hist;
+    h.coords = P->coords_dev; h.ncoord = P->coords.size();
+    return h;
+}
+
+// the phases of one compression; the batched path runs each phase for all
+// of its fields before the next (the single-block phases as one launch)
+enum : int { kPhLevels = 1, kPhCoarse = 2, kPhCodebook = 4, kPhEncode = 8, kPhHeader = 16, kPhAll = 31 };
+
+// the whole compression of one field (or the selected phases of it),
+// enqueued on s without any host wait; the container size and status stay
+// in w.sc (device)
 template <typename T>
 hpdr_status compress_core(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, const size_t *dims, double tol,
                           int tol_kind, int mode, unsigned D, unsigned K, uint8_t *out, size_t cap, const Ws &w,
-                          cudaStream_t s)
+                          cudaStream_t s, int phases = kPhAll)
 {
     const int L = P->L;
     const long long N = P->N[L];
+    QuantOut qo;
+    qo.sym = w.sym; qo.hist = w.hist; qo.esc = w.esc;
+    qo.D = D; qo.sc = w.sc;
+    const LevelGeom<T> *geo = &geom<T>(P, 0);
+    const int ls = coarse_top<T>(P, geo);
+    // the level-ls grid the coarse levels start from
+    const T *vtop = (ls >= L) ? u : (const T *)(((L - ls - 1) % 2 == 0) ? w.va : w.vb);
+    HuffScratch hs;
+    huff_scratch_carve(w.huff, D, w.sc, &hs);
+    if (phases & kPhLevels) {
     CK(cudaMemsetAsync(w.sc, 0, sizeof(Scalars), s));
     CK(cudaMemsetAsync(w.hist, 0, sizeof(unsigned long long) * D, s));
     {
@@ -254,13 +287,7 @@ hpdr_status compress_core(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, co
         CK(cudaGetLastError());
     }
 
-    QuantOut qo;
-    qo.sym = w.sym; qo.hist = w.hist; qo.esc = w.esc;
-    qo.D = D; qo.sc = w.sc;
     const T *v = u;
-    // levels 1..ls and level 0 in one CTA (0: none fits)
-    const LevelGeom<T> *geo = &geom<T>(P, 0);
-    const int ls = coarse_top<T>(P, geo);
     for (int l = L; l > ls; l--) {
         T *vc = (T *)(((L - l) % 2 == 0) ? w.va : w.vb);
         RestrictArgs<T> a;
@@ -282,21 +309,23 @@ hpdr_status compress_core(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, co
         }
         v = vc;
     }
-    if (ls >= 1) {
-        ProfScope ps(ctx, "c_coarse", s);
-        SymIn none;
-        memset(&none, 0, sizeof(none));
-        CK(launch_coarse<T>(0, P, geo, ls, v, nullptr, qo, nullptr, none, nullptr, s));
-    } else {
-        CK(launch_level0<T>(Sink::QUANT, v, P->N[0], nullptr, qo, s));
     }
-
-    HuffScratch hs;
-    huff_scratch_carve(w.huff, D, w.sc, &hs);
-    {
-    ProfScope ps(ctx, "c_codebook", s);
-    CK(launch_codebook(w.hist, D, hs, s));
+    // levels 1..ls and level 0 in one CTA (ls = 0: none fits; level 0 alone)
+    if (phases & kPhCoarse) {
+        if (ls >= 1) {
+            ProfScope ps(ctx, "c_coarse", s);
+            SymIn none;
+            memset(&none, 0, sizeof(none));
+            CK(launch_coarse<T>(0, P, geo, ls, vtop, nullptr, qo, nullptr, none, nullptr, s));
+        } else {
+            CK(launch_level0<T>(Sink::QUANT, vtop, P->N[0], nullptr, qo, s));
+        }
     }
+    if (phases & kPhCodebook) {
+        ProfScope ps(ctx, "c_codebook", s);
+        CK(launch_codebook(w.hist, D, hs, s));
+    }
+    if (!(phases & (kPhEncode | kPhHeader))) return HPDR_OK;
     EncodeArgs ea;
     memset(&ea, 0, sizeof(ea));
     ea.sym = w.sym; ea.N = (unsigned long long)N; ea.D = D; ea.K = K;
@@ -306,20 +335,12 @@ hpdr_status compress_core(hpdr_ctx *ctx, const Plan *P, const T *u, int ndim, co
     ea.bsum = w.bsum;
     ea.container = out; ea.L = L; ea.capacity = cap;
     ea.ncoord = P->coords.size();
-    {
-    ProfScope ps(ctx, "c_encode", s);
-    CK(launch_encode(ea, s));
+    if (phases & kPhEncode) {
+        ProfScope ps(ctx, "c_encode", s);
+        CK(launch_encode(ea, s));
     }
-    HeaderArgs h;
-    memset(&h, 0, sizeof(h));
-    h.dtype = sizeof(T) == 4 ? 0 : 1;
-    h.ndim = ndim;
-    h.L = L;
-    h.mode = mode;
-    h.tol_kind = tol_kind;
-    for (int k = 0; k < 3; k++) h.dims[k] = k < ndim ? dims[k] : 1;
-    h.D = D; h.K = K; h.tol = tol; h.N = (unsigned long long)N; h.hist = w.hist;
-    h.coords = P->coords_dev; h.ncoord = P->coords.size();
+    if (!(phases & kPhHeader)) return HPDR_OK;
+    const HeaderArgs h = header_args<T>(P, ndim, dims, tol, tol_kind, mode, D, K, w);
     CK(launch_header(h, hs.len, w.sc, out, s));
     return HPDR_OK;
 }
@@ -861,11 +882,6 @@ hpdr_status adjoint_t(hpdr_ctx *ctx, const Plan *P, const T *in, T *out, bool re
 }
 
 // ---- batched compression ------------------------------------------------
-__global__ void store_size_kernel(const Scalars *sc, unsigned long long *dst)
-{
-    dst[0] = sc->out_bytes;
-    dst[1] = sc->status;
-}
 
 struct BatchPlan {
     int nfields = 0;
@@ -878,6 +894,15 @@ struct BatchPlan {
     int streams = 0;
     double tuned_ms = 0.0;
     unsigned long long last_use = 0;   // call counter of the last replay (least recently used goes first)
+    // device job arrays of the single-block phases (one block per field)
+    void *jobs = nullptr;
+    CoarseArgs<float> *coarse32 = nullptr;
+    CoarseArgs<double> *coarse64 = nullptr;
+    int n32 = 0, n64 = 0;
+    size_t sm32 = 0, sm64 = 0;
+    std::vector<int> coarse_ls;          // per field: coarse_top (0: level 0 alone, in its field's phase)
+    CodebookJob *codebooks = nullptr;    // [nfields]
+    HeaderJob *headers = nullptr;        // [nfields]
 };
 
 // Captured batches kept per context: a graph holds the pointers it was
@@ -887,6 +912,7 @@ constexpr size_t kMaxBatchPlans = 4;
 void free_batch_plan(BatchPlan *bp)
 {
     if (bp->exec) cudaGraphExecDestroy(bp->exec);
+    cudaFree(bp->jobs);
     cudaFree(bp->ws);
     cudaFree(bp->sizes);
     delete bp;
@@ -942,37 +968,155 @@ std::vector<std::vector<int>> schedule(const hpdr_field *f, int n, int K)
     return q;
 }
 
-hpdr_status enqueue_batch(hpdr_ctx *ctx, BatchRes *r, BatchPlan *bp, const hpdr_field *f, unsigned D, unsigned K,
-                          uint8_t *d_out, int nstreams)
+// the field's workspace inside the batch's workspace
+Ws batch_ws(const BatchPlan *bp, const hpdr_field *f, int i, unsigned D, unsigned K)
 {
-    if (cudaEventRecord(r->fork, r->origin) != cudaSuccess) return HPDR_ERR_CUDA;
-    std::vector<std::vector<int>> q = schedule(f, bp->nfields, nstreams);
-    for (int k = 0; k < nstreams; k++) {
-        cudaStream_t st = r->workers[k];
-        if (cudaStreamWaitEvent(st, r->fork, 0) != cudaSuccess) return HPDR_ERR_CUDA;
-        for (int i : q[k]) {
-            const Plan *P = bp->plans[i];
-            const bool f64 = f[i].dtype == HPDR_F64;
-            const unsigned Ki = chunk_of(K, (unsigned long long)P->N[P->L]);
-            Ws w;
-            carve_ws((char *)bp->ws + bp->ws_off[i], P, f64 ? 8 : 4, D, Ki, true, &w);
-            hpdr_status stt;
-            if (f64)
-                stt = compress_core<double>(ctx, P, (const double *)f[i].d_in, f[i].ndim, f[i].dims, f[i].tol,
-                                            f[i].tol_kind, f[i].mode, D, Ki, d_out + bp->out_off[i], bp->bound[i], w, st);
-            else
-                stt = compress_core<float>(ctx, P, (const float *)f[i].d_in, f[i].ndim, f[i].dims, f[i].tol,
-                                           f[i].tol_kind, f[i].mode, D, Ki, d_out + bp->out_off[i], bp->bound[i], w, st);
-            if (stt != HPDR_OK) return stt;
-            store_size_kernel<<<1, 1, 0, st>>>(w.sc, bp->sizes + 2 * i);
-            count_launch();
-        }
-        if (cudaEventRecord(r->join[k], st) != cudaSuccess) return HPDR_ERR_CUDA;
-        if (cudaStreamWaitEvent(r->origin, r->join[k], 0) != cudaSuccess) return HPDR_ERR_CUDA;
+    const Plan *P = bp->plans[i];
+    const unsigned Ki = chunk_of(K, (unsigned long long)P->N[P->L]);
+    Ws w;
+    carve_ws((char *)bp->ws + bp->ws_off[i], P, f[i].dtype == HPDR_F64 ? 8 : 4, D, Ki, true, &w);
+    return w;
+}
+
+// the job arrays of the single-block phases, built once per batch plan
+template <typename T>
+void batch_field_jobs(const BatchPlan *bp, const hpdr_field *f, int i, unsigned D, unsigned K, uint8_t *d_out,
+                      std::vector<CoarseArgs<T>> &coarse, size_t &smem, int &ls, CodebookJob &cb, HeaderJob &hj)
+{
+    const Plan *P = bp->plans[i];
+    const unsigned Ki = chunk_of(K, (unsigned long long)P->N[P->L]);
+    const Ws w = batch_ws(bp, f, i, D, K);
+    const int L = P->L;
+    const LevelGeom<T> *geo = &geom<T>(P, 0);
+    ls = coarse_top<T>(P, geo);
+    QuantOut qo;
+    qo.sym = w.sym; qo.hist = w.hist; qo.esc = w.esc;
+    qo.D = D; qo.sc = w.sc;
+    HuffScratch hs;
+    huff_scratch_carve(w.huff, D, w.sc, &hs);
+    if (ls >= 1) {
+        const T *vtop = (ls >= L) ? (const T *)f[i].d_in : (const T *)(((L - ls - 1) % 2 == 0) ? w.va : w.vb);
+        SymIn none;
+        memset(&none, 0, sizeof(none));
+        size_t sm = 0;
+        coarse.push_back(coarse_args<T>(P, geo, ls, vtop, nullptr, qo, nullptr, none, nullptr, &sm));
+        smem = std::max(smem, sm);
+    }
+    cb.hist = w.hist;
+    cb.D = D;
+    cb.hs = hs;
+    hj.h = header_args<T>(P, f[i].ndim, f[i].dims, f[i].tol, f[i].tol_kind, f[i].mode, D, Ki, w);
+    hj.len = hs.len;
+    hj.sc = w.sc;
+    hj.out = d_out + bp->out_off[i];
+    hj.size_status = bp->sizes + 2 * i;
+}
+
+hpdr_status build_batch_jobs(BatchPlan *bp, const hpdr_field *f, unsigned D, unsigned K, uint8_t *d_out)
+{
+    const int n = bp->nfields;
+    std::vector<CoarseArgs<float>> c32;
+    std::vector<CoarseArgs<double>> c64;
+    std::vector<CodebookJob> cb(n);
+    std::vector<HeaderJob> hj(n);
+    bp->coarse_ls.assign(n, 0);
+    for (int i = 0; i < n; i++) {
+        if (f[i].dtype == HPDR_F64)
+            batch_field_jobs<double>(bp, f, i, D, K, d_out, c64, bp->sm64, bp->coarse_ls[i], cb[i], hj[i]);
+        else
+            batch_field_jobs<float>(bp, f, i, D, K, d_out, c32, bp->sm32, bp->coarse_ls[i], cb[i], hj[i]);
+    }
+    bp->n32 = (int)c32.size();
+    bp->n64 = (int)c64.size();
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t b32 = al(sizeof(CoarseArgs<float>) * c32.size()), b64 = al(sizeof(CoarseArgs<double>) * c64.size());
+    const size_t bcb = al(sizeof(CodebookJob) * n), bhj = al(sizeof(HeaderJob) * n);
+    if (cudaMalloc(&bp->jobs, b32 + b64 + bcb + bhj) != cudaSuccess) { cudaGetLastError(); return HPDR_ERR_NOMEM; }
+    char *p = (char *)bp->jobs;
+    bp->coarse32 = (CoarseArgs<float> *)p;
+    bp->coarse64 = (CoarseArgs<double> *)(p + b32);
+    bp->codebooks = (CodebookJob *)(p + b32 + b64);
+    bp->headers = (HeaderJob *)(p + b32 + b64 + bcb);
+    // pageable sources: synchronous copies, done before any capture
+    if ((c32.size() && cudaMemcpy(bp->coarse32, c32.data(), sizeof(CoarseArgs<float>) * c32.size(),
+                                  cudaMemcpyHostToDevice) != cudaSuccess) ||
+        (c64.size() && cudaMemcpy(bp->coarse64, c64.data(), sizeof(CoarseArgs<double>) * c64.size(),
+                                  cudaMemcpyHostToDevice) != cudaSuccess) ||
+        cudaMemcpy(bp->codebooks, cb.data(), sizeof(CodebookJob) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(bp->headers, hj.data(), sizeof(HeaderJob) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return HPDR_ERR_CUDA;
     }
     return HPDR_OK;
 }
 
+// The batch in four phases, each over all fields: (A) per field on the K
+// worker streams, norm, bins and the large levels (and level 0 when no level
+// fits one CTA); (B) on the origin stream, the coarse levels of every field
+// in one launch per element type, then every field's codebook in one launch;
+// (C) per field on the workers, the encoder; (D) every header and every
+// {bytes, status} pair in one launch.  Each field meets the same kernels in
+// the same order as hpdr_compress, so its container is byte-identical.
+hpdr_status enqueue_batch(hpdr_ctx *ctx, BatchRes *r, BatchPlan *bp, const hpdr_field *f, unsigned D, unsigned K,
+                          uint8_t *d_out, int nstreams)
+{
+    std::vector<std::vector<int>> q = schedule(f, bp->nfields, nstreams);
+    auto fork = [&]() -> bool {
+        if (cudaEventRecord(r->fork, r->origin) != cudaSuccess) return false;
+        for (int k = 0; k < nstreams; k++)
+            if (cudaStreamWaitEvent(r->workers[k], r->fork, 0) != cudaSuccess) return false;
+        return true;
+    };
+    auto join = [&]() -> bool {
+        for (int k = 0; k < nstreams; k++) {
+            if (cudaEventRecord(r->join[k], r->workers[k]) != cudaSuccess) return false;
+            if (cudaStreamWaitEvent(r->origin, r->join[k], 0) != cudaSuccess) return false;
+        }
+        return true;
+    };
+    auto field = [&](int i, int phases, cudaStream_t st) -> hpdr_status {
+        const Plan *P = bp->plans[i];
+        const unsigned Ki = chunk_of(K, (unsigned long long)P->N[P->L]);
+        const Ws w = batch_ws(bp, f, i, D, K);
+        if (f[i].dtype == HPDR_F64)
+            return compress_core<double>(ctx, P, (const double *)f[i].d_in, f[i].ndim, f[i].dims, f[i].tol,
+                                         f[i].tol_kind, f[i].mode, D, Ki, d_out + bp->out_off[i], bp->bound[i], w,
+                                         st, phases);
+        return compress_core<float>(ctx, P, (const float *)f[i].d_in, f[i].ndim, f[i].dims, f[i].tol,
+                                    f[i].tol_kind, f[i].mode, D, Ki, d_out + bp->out_off[i], bp->bound[i], w, st,
+                                    phases);
+    };
+    // (A)
+    if (!fork()) return HPDR_ERR_CUDA;
+    for (int k = 0; k < nstreams; k++)
+        for (int i : q[k]) {
+            const hpdr_status st = field(i, kPhLevels | (bp->coarse_ls[i] < 1 ? kPhCoarse : 0), r->workers[k]);
+            if (st != HPDR_OK) return st;
+        }
+    if (!join()) return HPDR_ERR_CUDA;
+    // (B)
+    CK(launch_coarse_batch<float>(0, bp->coarse32, bp->n32, bp->sm32, r->origin));
+    CK(launch_coarse_batch<double>(0, bp->coarse64, bp->n64, bp->sm64, r->origin));
+    if (codebook_fused(D)) {
+        CK(launch_codebook_batch(bp->codebooks, bp->nfields, r->origin));
+    } else {
+        for (int i = 0; i < bp->nfields; i++) {
+            const hpdr_status st = field(i, kPhCodebook, r->origin);
+            if (st != HPDR_OK) return st;
+        }
+    }
+    // (C)
+    if (!fork()) return HPDR_ERR_CUDA;
+    for (int k = 0; k < nstreams; k++)
+        for (int i : q[k]) {
+            const hpdr_status st = field(i, kPhEncode, r->workers[k]);
+            if (st != HPDR_OK) return st;
+        }
+    if (!join()) return HPDR_ERR_CUDA;
+    // (D)
+    CK(launch_header_batch(bp->headers, bp->nfields, r->origin));
+    return HPDR_OK;
+}
 hpdr_status capture_batch(hpdr_ctx *ctx, BatchRes *r, BatchPlan *bp, const hpdr_field *f, unsigned D, unsigned K,
                           uint8_t *d_out, int nstreams, cudaGraphExec_t *exec)
 {
@@ -1723,9 +1867,13 @@ hpdr_status hpdr_compress_batched(hpdr_ctx *ctx, int nfields, const hpdr_field *
         bp->ws_total = wsz;
         if (cudaMalloc(&bp->ws, wsz) != cudaSuccess || cudaMalloc(&bp->sizes, 16ull * nfields) != cudaSuccess) {
             cudaGetLastError();
-            cudaFree(bp->ws);
-            delete bp;
+            free_batch_plan(bp);
             return HPDR_ERR_NOMEM;
+        }
+        st = build_batch_jobs(bp, fields, D, K, (uint8_t *)d_out);
+        if (st != HPDR_OK) {
+            free_batch_plan(bp);
+            return st;
         }
         // one eager run (sets kernel attributes, warms the plans), then the
         // autotuner: capture the batch for every stream count and keep the fastest replay
@@ -1786,11 +1934,9 @@ hpdr_status hpdr_compress_batched(hpdr_ctx *ctx, int nfields, const hpdr_field *
         CK(cudaGraphLaunch(bp->exec, r->origin));
     }
     count_launch();
-    unsigned long long *hs = (unsigned long long *)ctx->host_pinned;
     std::vector<unsigned long long> sizes(2 * (size_t)nfields);
     CK(cudaMemcpyAsync(sizes.data(), bp->sizes, 16ull * nfields, cudaMemcpyDeviceToHost, r->origin));
     CK(cudaStreamSynchronize(r->origin));
-    (void)hs;
     for (int i = 0; i < nfields; i++) {
         if (sizes[2 * i + 1]) return map_device_status((unsigned)sizes[2 * i + 1]);
         out_sizes[i] = (size_t)sizes[2 * i];

@@ -126,7 +126,7 @@ __device__ unsigned count_lt(const unsigned long long *a, unsigned n, unsigned l
     return lo;
 }
 
-__device__ void length_tables(HuffScratch &hs, unsigned *cnt)
+__device__ void length_tables(const HuffScratch &hs, unsigned *cnt)
 {
     // first canonical code and start index of every length
     unsigned long long c = 0;
@@ -525,7 +525,7 @@ __device__ __forceinline__ void sort8(unsigned long long (&k)[8])
     }
 }
 
-__global__ void __launch_bounds__(1024, 1) codebook_kernel(const unsigned long long *hist, unsigned D, HuffScratch hs)
+__device__ __forceinline__ void codebook_body(const unsigned long long *hist, unsigned D, const HuffScratch &hs)
 {
     extern __shared__ __align__(16) unsigned char csm[];
     unsigned long long *key = reinterpret_cast<unsigned long long *>(csm);   // [kFusedMaxD]
@@ -767,6 +767,18 @@ __global__ void __launch_bounds__(1024, 1) codebook_kernel(const unsigned long l
     if (tid < 64) { sstart[tid] = hs.start[tid]; sfirst[tid] = hs.first[tid]; }
     __syncthreads();
     canonical_assign(lens, D, sstart, sfirst, wc, run, hs.code, hs.sorted_sym);
+}
+
+__global__ void __launch_bounds__(1024, 1) codebook_kernel(const unsigned long long *hist, unsigned D, HuffScratch hs)
+{
+    codebook_body(hist, D, hs);
+}
+
+// one codebook per block: the codebooks of a batch of fields in one launch
+__global__ void __launch_bounds__(1024, 1) codebook_batch_kernel(const CodebookJob *jobs)
+{
+    const CodebookJob j = jobs[blockIdx.x];
+    codebook_body(j.hist, j.D, j.hs);
 }
 
 // Decoder tables from the code lengths of symbols s_lo..s_hi (every other
@@ -1200,8 +1212,7 @@ __device__ __forceinline__ void put32(uint8_t *p, uint32_t v) { for (int i = 0; 
 __device__ __forceinline__ void put64(uint8_t *p, unsigned long long v) { for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i)); }
 __device__ __forceinline__ void putd(uint8_t *p, double v) { put64(p, (unsigned long long)__double_as_longlong(v)); }
 
-__global__ void __launch_bounds__(256)
-header_kernel(HeaderArgs h, const uint8_t *len, Scalars *sc, uint8_t *out)
+__device__ __forceinline__ void header_body(const HeaderArgs &h, const uint8_t *len, Scalars *sc, uint8_t *out)
 {
     __shared__ uint8_t hdr[128];
     __shared__ uint32_t crct[256];
@@ -1252,6 +1263,24 @@ header_kernel(HeaderArgs h, const uint8_t *len, Scalars *sc, uint8_t *out)
     for (unsigned i = threadIdx.x; i < nlen; i += blockDim.x) out[lay.off_len + i] = len[sc->s_lo + i];
     for (unsigned long long i = lay.off_len + nlen + threadIdx.x; i < lay.off_chunk; i += blockDim.x) out[i] = 0;
     for (unsigned long long i = lay.off_chunk + 8 * nch + threadIdx.x; i < lay.off_bits; i += blockDim.x) out[i] = 0;
+}
+
+__global__ void __launch_bounds__(256)
+header_kernel(HeaderArgs h, const uint8_t *len, Scalars *sc, uint8_t *out)
+{
+    header_body(h, len, sc, out);
+}
+
+// one container header per block, then the field's {bytes, status} pair
+__global__ void __launch_bounds__(256) header_batch_kernel(const HeaderJob *jobs)
+{
+    const HeaderJob &j = jobs[blockIdx.x];
+    header_body(j.h, j.len, j.sc, j.out);
+    __syncthreads();
+    if (threadIdx.x == 0 && j.size_status) {
+        j.size_status[0] = j.sc->out_bytes;
+        j.size_status[1] = j.sc->status;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1558,6 +1587,9 @@ cudaError_t set_attrs_now()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCodebookSmem);
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(codebook_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kCodebookSmem);
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(dec_tables_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  4 * 32 * kWcStride + 65536);
     if (e == cudaSuccess)
@@ -1686,6 +1718,26 @@ cudaError_t launch_header(const HeaderArgs &h, const uint8_t *len, Scalars *sc, 
                           cudaStream_t s)
 {
     header_kernel<<<1, 256, 0, s>>>(h, len, sc, container);
+    count_launch();
+    return cudaGetLastError();
+}
+
+bool codebook_fused(unsigned int D) { return D <= kFusedMaxD; }
+
+cudaError_t launch_codebook_batch(const CodebookJob *jobs, int n, cudaStream_t s)
+{
+    cudaError_t e = set_attrs();
+    if (e != cudaSuccess) return e;
+    if (n < 1) return cudaSuccess;
+    codebook_batch_kernel<<<n, 1024, kCodebookSmem, s>>>(jobs);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_header_batch(const HeaderJob *jobs, int n, cudaStream_t s)
+{
+    if (n < 1) return cudaSuccess;
+    header_batch_kernel<<<n, 256, 0, s>>>(jobs);
     count_launch();
     return cudaGetLastError();
 }

@@ -108,6 +108,26 @@ struct HeaderArgs {
 cudaError_t launch_header(const HeaderArgs &h, const uint8_t *len, Scalars *sc, uint8_t *container,
                           cudaStream_t s);
 
+// Batched forms for many fields at once (one block per field, the same
+// device code as the single-field launches, so the same bytes).
+struct CodebookJob {
+    const unsigned long long *hist;
+    unsigned int D;
+    HuffScratch hs;
+};
+struct HeaderJob {
+    HeaderArgs h;
+    const uint8_t *len;
+    Scalars *sc;
+    uint8_t *out;
+    unsigned long long *size_status;   // [2]: container bytes and device status (may be null)
+};
+// whether launch_codebook builds an alphabet of D symbols in one block
+// (launch_codebook_batch takes only such alphabets)
+bool codebook_fused(unsigned int D);
+cudaError_t launch_codebook_batch(const CodebookJob *jobs, int n, cudaStream_t s);   // jobs: device [n]
+cudaError_t launch_header_batch(const HeaderJob *jobs, int n, cudaStream_t s);       // jobs: device [n]
+
 struct DecodeArgs {
     const uint32_t *words;
     unsigned long long nwords;

@@ -385,18 +385,6 @@ __global__ void bins_kernel(BinArgs ba, const double *partials, int nparts, Scal
 // interpolant, taken along dimension 2, then 1, then 0.
 constexpr int kCoarseThreads = 1024;
 
-template <typename T>
-struct CoarseArgs {
-    LevelGeom<T> g[kCoarseMaxLevels + 1];   // levels 1..ls
-    int ls;
-    long long N0;
-    const T *v_in;       // compression / decomposition: the level-ls grid
-    T *v_out;            // recomposition: the level-ls grid
-    QuantOut qo;         // compression
-    T *coef_out;         // decomposition
-    SymIn symin;         // decompression
-    const T *coef_in;    // recomposition
-};
 
 // element counts of the shared arrays for top level ls (host and device)
 template <typename T>
@@ -515,7 +503,7 @@ __device__ void coarse_rhs(const LevelGeom<T> &g, const T *W, T *R2, T *R1, T *B
 // MODE 0: compression (quantize), 1: decomposition (coefficient stream),
 // 2: decompression (symbols), 3: recomposition (coefficient stream)
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kCoarseThreads, 1) coarse_kernel(CoarseArgs<T> a)
+__device__ __forceinline__ void coarse_body(const CoarseArgs<T> &a)
 {
     extern __shared__ __align__(16) unsigned char coarse_smem[];
     long long nl, nc, r2, r1;
@@ -617,6 +605,19 @@ __global__ void __launch_bounds__(kCoarseThreads, 1) coarse_kernel(CoarseArgs<T>
         }
         for (long long i = tid; i < nl; i += blockDim.x) a.v_out[i] = V[i];
     }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kCoarseThreads, 1) coarse_kernel(CoarseArgs<T> a)
+{
+    coarse_body<T, MODE>(a);
+}
+
+// one field per block
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kCoarseThreads, 1) coarse_batch_kernel(const CoarseArgs<T> *jobs)
+{
+    coarse_body<T, MODE>(jobs[blockIdx.x]);
 }
 
 }  // namespace
@@ -792,17 +793,48 @@ int coarse_top(const Plan *P, const LevelGeom<T> *geo)
 }
 
 template <typename T>
+CoarseArgs<T> coarse_args(const Plan *P, const LevelGeom<T> *geo, int ls, const T *v_in, T *v_out,
+                          const QuantOut &qo, T *coef_out, const SymIn &symin, const T *coef_in, size_t *smem)
+{
+    CoarseArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    for (int l = 1; l <= ls && l <= kCoarseMaxLevels; l++) a.g[l] = geo[l];
+    a.ls = ls;
+    a.N0 = P->N[0];
+    a.v_in = v_in; a.v_out = v_out; a.qo = qo; a.coef_out = coef_out; a.symin = symin; a.coef_in = coef_in;
+    if (smem) *smem = ls >= 1 && ls <= kCoarseMaxLevels ? coarse_smem_bytes<T>(geo[ls]) : 0;
+    return a;
+}
+
+template <typename T>
+cudaError_t launch_coarse_batch(int mode, const CoarseArgs<T> *jobs, int n, size_t smem, cudaStream_t s)
+{
+    if (n < 1) return cudaSuccess;
+    static PerDeviceOnce attr[4];
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t e = once_per_device(attr[mode & 3], [&] {
+            return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmem);
+        });
+        if (e != cudaSuccess) return e;
+        kern<<<n, kCoarseThreads, smem, s>>>(jobs);
+        count_launch();
+        return cudaGetLastError();
+    };
+    switch (mode) {
+    case 0: return go(coarse_batch_kernel<T, 0>);
+    case 1: return go(coarse_batch_kernel<T, 1>);
+    case 2: return go(coarse_batch_kernel<T, 2>);
+    default: return go(coarse_batch_kernel<T, 3>);
+    }
+}
+
+template <typename T>
 cudaError_t launch_coarse(int mode, const Plan *P, const LevelGeom<T> *geo, int ls, const T *v_in, T *v_out,
                           const QuantOut &qo, T *coef_out, const SymIn &symin, const T *coef_in, cudaStream_t s)
 {
     if (ls < 1 || ls > kCoarseMaxLevels) return cudaErrorInvalidValue;
-    CoarseArgs<T> a;
-    memset(&a, 0, sizeof(a));
-    for (int l = 1; l <= ls; l++) a.g[l] = geo[l];
-    a.ls = ls;
-    a.N0 = P->N[0];
-    a.v_in = v_in; a.v_out = v_out; a.qo = qo; a.coef_out = coef_out; a.symin = symin; a.coef_in = coef_in;
-    const size_t sm = coarse_smem_bytes<T>(geo[ls]);
+    size_t sm = 0;
+    const CoarseArgs<T> a = coarse_args<T>(P, geo, ls, v_in, v_out, qo, coef_out, symin, coef_in, &sm);
     static PerDeviceOnce attr[4];
     auto go = [&](auto kern) -> cudaError_t {
         cudaError_t e = once_per_device(attr[mode], [&] {
@@ -833,7 +865,10 @@ cudaError_t launch_coarse(int mode, const Plan *P, const LevelGeom<T> *geo, int 
     template cudaError_t launch_norm<T>(const T *, long long, double *, int, cudaStream_t);      \
     template int coarse_top<T>(const Plan *, const LevelGeom<T> *);                              \
     template cudaError_t launch_coarse<T>(int, const Plan *, const LevelGeom<T> *, int, const T *, T *, \
-                                          const QuantOut &, T *, const SymIn &, const T *, cudaStream_t);
+                                          const QuantOut &, T *, const SymIn &, const T *, cudaStream_t); \
+    template CoarseArgs<T> coarse_args<T>(const Plan *, const LevelGeom<T> *, int, const T *, T *,         \
+                                          const QuantOut &, T *, const SymIn &, const T *, size_t *);      \
+    template cudaError_t launch_coarse_batch<T>(int, const CoarseArgs<T> *, int, size_t, cudaStream_t);
 INST(float)
 INST(double)
 

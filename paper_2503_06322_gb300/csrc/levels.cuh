@@ -121,8 +121,28 @@ constexpr size_t kCoarseSmem = 200 * 1024;
 template <typename T>
 int coarse_top(const Plan *P, const LevelGeom<T> *geo);
 template <typename T>
+struct CoarseArgs {
+    LevelGeom<T> g[kCoarseMaxLevels + 1];   // levels 1..ls
+    int ls;
+    long long N0;
+    const T *v_in;       // compression / decomposition: the level-ls grid
+    T *v_out;            // recomposition: the level-ls grid
+    QuantOut qo;         // compression
+    T *coef_out;         // decomposition
+    SymIn symin;         // decompression
+    const T *coef_in;    // recomposition
+};
+template <typename T>
 cudaError_t launch_coarse(int mode, const Plan *P, const LevelGeom<T> *geo, int ls, const T *v_in, T *v_out,
                           const QuantOut &qo, T *coef_out, const SymIn &symin, const T *coef_in, cudaStream_t s);
+// the arguments of that launch (host), and its dynamic shared memory
+template <typename T>
+CoarseArgs<T> coarse_args(const Plan *P, const LevelGeom<T> *geo, int ls, const T *v_in, T *v_out,
+                          const QuantOut &qo, T *coef_out, const SymIn &symin, const T *coef_in, size_t *smem);
+// the coarse levels of n fields in one launch (one block per field; jobs:
+// device [n]; smem: the largest of the fields' shared-memory sizes)
+template <typename T>
+cudaError_t launch_coarse_batch(int mode, const CoarseArgs<T> *jobs, int n, size_t smem, cudaStream_t s);
 
 // adjoint.cu: transposes of recomposition / decomposition over all levels.
 // ga, gb, y, R hold N_{L-1} elements; t1, t2 the partial prolongations
