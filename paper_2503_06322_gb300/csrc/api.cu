@@ -579,7 +579,7 @@ hpdr_status decompress_t(hpdr_ctx *ctx, const Plan *P, const Hdr &h, const uint8
     da.nwords = h.nwords;
     da.chunk = (const unsigned long long *)(in + h.off_chunk);
     da.N = h.N; da.total_bits = h.bits; da.K = h.K; da.sym = w.sym;
-    da.esc = h.esc_w ? w.esc : nullptr; da.esc_w = h.esc_w;
+    da.esc = h.esc_w ? w.esc : nullptr; da.esc_w = h.esc_w; da.n_esc = h.n_esc;
     {
     ProfScope ps(ctx, "d_decode", s);
     CK(launch_decode(da, hs, s));

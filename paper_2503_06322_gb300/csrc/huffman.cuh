@@ -137,6 +137,7 @@ struct DecodeArgs {
     uint16_t *sym;
     long long *esc;                   // null: plain symbols; else receives k of every escape
     unsigned int esc_w;               // payload width of the escapes
+    unsigned long long n_esc = 0;     // escapes in the stream (selects the escape stores)
     // non-null: words, nwords, chunk, total_bits and esc_w come from this
     // device-parsed header of the container at base (esc_w 0: no escapes)
     const uint8_t *base = nullptr;
