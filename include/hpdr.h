@@ -250,12 +250,16 @@ typedef struct {
 } hpdr_field;
 
 /* Compress many fields of uneven shapes (each with its own bound) in one
- * replay of a CUDA graph.  The first call with a given batch (fields,
- * pointers, config) captures every field's whole compression into one graph,
- * forked over K worker streams (fields assigned largest first to the least-
- * loaded stream); an autotuner captures K = 1, 2, 4, 8, 16, times one replay
- * of each and keeps the fastest.  Later calls with the same batch only
- * replay it (one graph launch, one wait).  Each field's container is
+ * replay of a CUDA graph (Sec. III-A's Map&Process over many fields).  The
+ * first call with a given batch (fields, pointers, config) captures every
+ * field's whole compression into one graph, in four phases over all fields:
+ * the norms, bins and large levels of each field forked over K worker
+ * streams (fields assigned largest first to the least-loaded stream); the
+ * coarse levels of every field in one launch and every codebook in one
+ * launch; each field's encoder on the workers; every header (with its size
+ * and status) in one launch.  An autotuner captures K = 1, 2, 4, 8, 16, times
+ * one replay of each and keeps the fastest.  Later calls with the same batch
+ * only replay it (one graph launch, one wait).  Each field's container is
  * byte-identical to hpdr_compress on that field.
  *   d_out          device buffer of out_capacity bytes;
  *   out_offsets    host [nfields+1]: field i's container starts at
