@@ -83,3 +83,27 @@ def test_batched_cache_is_bounded():
     assert sizes == sizes_ref
     for i in range(len(us)):
         assert torch.equal(got[offs[i]:offs[i] + sizes[i]], ref[offs_ref[i]:offs_ref[i] + sizes_ref[i]])
+
+
+def test_batched_large_alphabet_and_mixed_types():
+    """An alphabet above the one-block codebook's limit (D = 16384) takes the
+    per-field codebook in the batch's codebook phase; FP32 and FP64 fields
+    whose coarse levels run in one launch per element type; a field too small
+    for any coarse level (level 0 alone).  Every container equals the plain
+    API's with the same dictionary."""
+    from paper_2503_06322_gb300 import fields, hpdr
+    shapes = [((70, 33, 40), np.float32), ((65, 65, 65), np.float64), ((300, 200), np.float32),
+              ((3, 3), np.float32), ((129, 17), np.float64), ((2,), np.float32)]
+    us = []
+    for i, (sh, dt) in enumerate(shapes):
+        if len(sh) == 1:
+            us.append(torch.from_numpy(np.random.default_rng(i).standard_normal(sh).astype(dt)).cuda())
+        else:
+            us.append(torch.from_numpy(fields.powerlaw_field(sh, seed=400 + i, dtype=dt)).cuda())
+    tols = [1e-3, 1e-4, 1e-2, 1e-3, 1e-3, 1e-3]
+    for D in (16384, 8192):
+        out, offs, sizes = hpdr.hpdr_compress_batched(us, tols, dict_size=D)
+        for i, (u, tol) in enumerate(zip(us, tols)):
+            plain = hpdr.hpdr_compress(u, tol, dict_size=D)
+            assert sizes[i] == plain.numel(), (D, i)
+            assert torch.equal(out[offs[i]:offs[i] + sizes[i]], plain), (D, i)
