@@ -953,15 +953,22 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
     tc.jlo = 0; tc.tr[0] = tc.tr[1] = tc.tr[2] = (T)0;
     {
         const bool ok = warp_wait(&full[0], 0u, limit);
-        if (ok) { tc = taps_of(0); ec = fill(0, tile(0)); }
+        if (ok) {
+            tc = taps_of(0);
+            ec = fill(0, tile(0));
+            cp_async_wait0();
+            patch(0, tile(0), ec);
+        }
         if (named_sync_or(1, DCW * 32, !ok)) failed = true;
         else if (tid == 0) mbar_arrive(&empty[0]);
     }
+    // Each iteration fills the next plane's tile, restricts this plane's
+    // (complete since the last barrier), then completes the next tile with its
+    // escaped codes and meets the other consumers once: a warp reaches the
+    // barrier with both pieces of work done, so the waits absorb the spread of
+    // their sum rather than of the fill alone.
     for (int k = 0; k < nplanes && !failed; k++) {
-        // this plane's escaped codes (copied one iteration ago) have landed
-        cp_async_wait0();
         T *W = tile(k);
-        patch(k, W, ec);
         // the next plane: symbols into its tile, its escaped codes in flight
         unsigned en = 0;
         Taps tn = tc;
@@ -970,9 +977,6 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
             ok = warp_wait(&full[(k + 1) % NST], (uint32_t)(((k + 1) / NST) & 1), limit);
             if (ok) { tn = taps_of(k + 1); en = fill(k + 1, tile(k + 1)); }
         }
-        // tile k complete, stage k + 1 read, and every consumer knows whether a wait ran out
-        if (named_sync_or(1, DCW * 32, !ok)) { failed = true; break; }
-        if (tid == 0 && k + 1 < nplanes) mbar_arrive(&empty[(k + 1) % NST]);
         if (wr.va) {
             T ra, rb;
             restrict_plane<T>(wr, lc.t2, [&](int i) -> const T * { return W + (wr.rl0 + i) * kWPitch + lanecol; },
@@ -992,7 +996,14 @@ rsym_kernel(RestrictArgs<T> a, int seg_len)
                 acc[1][i] = fma_rn(tc.tr[i], rb, acc[1][i]);
             }
         }
-        ec = en;
+        if (k + 1 < nplanes) {
+            // the next plane's escaped codes (copied during the restriction) into its tile
+            cp_async_wait0();
+            if (ok) patch(k + 1, tile(k + 1), en);
+            // next tile complete, stage k + 1 read, and every consumer knows whether a wait ran out
+            if (named_sync_or(1, DCW * 32, !ok)) { failed = true; break; }
+            if (tid == 0) mbar_arrive(&empty[(k + 1) % NST]);
+        }
         tc = tn;
     }
     if (failed) {
