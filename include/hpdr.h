@@ -176,7 +176,11 @@ hpdr_status hpdr_decompress_async(hpdr_ctx *ctx, const void *d_in, size_t in_cap
 hpdr_status hpdr_device_status(uint64_t code);
 
 /* Read the shape and type of a container held in host or device memory
- * (detected).  dims receives ndim entries (3 slots must be provided). */
+ * (detected).  dims receives ndim entries (3 slots must be provided).  The
+ * header gets the checks of hpdr_decompress (magic, version, CRC-32, field
+ * ranges, positive finite bin widths, sections inside in_bytes); a container
+ * that fails one gives HPDR_ERR_FORMAT.  No kernel runs: the header of a
+ * device buffer is read with one blocking copy, that of a host buffer in place. */
 hpdr_status hpdr_inspect(const void *in, size_t in_bytes, hpdr_dtype *dtype, int *ndim,
                          size_t *dims);
 

@@ -480,7 +480,7 @@ def crc32(data):
 
 
 def parse_header(buf):
-    """Header fields and section views of a v1 container (plain byte reads)."""
+    """Header fields and section views of a version-3 container (plain byte reads)."""
     b = bytes(buf)
     u32 = lambda o: int.from_bytes(b[o:o + 4], "little")  # noqa: E731
     u64 = lambda o: int.from_bytes(b[o:o + 8], "little")  # noqa: E731

@@ -1323,16 +1323,19 @@ hpdr_status hpdr_compress_coords(hpdr_ctx *ctx, const void *d_in, hpdr_dtype dty
 hpdr_status hpdr_inspect(const void *in, size_t in_bytes, hpdr_dtype *dtype, int *ndim, size_t *dims)
 {
     if (!in || !dtype || !ndim || !dims) return HPDR_ERR_ARG;
-    uint8_t hb[128];
+    // the fixed header and the bin widths q[0..L]: the checks of hpdr_decompress
+    uint8_t hb[128 + 8 * (kMaxLevels + 1)];
     if (in_bytes < 128) return HPDR_ERR_FORMAT;
+    const size_t rd = in_bytes < sizeof(hb) ? in_bytes : sizeof(hb);
     if (is_device_ptr(in)) {
-        if (cudaMemcpy(hb, in, 128, cudaMemcpyDeviceToHost) != cudaSuccess) return HPDR_ERR_CUDA;
+        if (cudaMemcpy(hb, in, rd, cudaMemcpyDeviceToHost) != cudaSuccess) return HPDR_ERR_CUDA;
     } else {
-        memcpy(hb, in, 128);
+        memcpy(hb, in, rd);
     }
     Hdr h;
-    hpdr_status st = parse_header(hb, 128, in_bytes, &h);
+    hpdr_status st = parse_header(hb, rd, in_bytes, &h);
     if (st != HPDR_OK) return st;
+    if (rd < 128 + 8ULL * (h.L + 1)) return HPDR_ERR_FORMAT;
     *dtype = (hpdr_dtype)h.dtype;
     *ndim = h.ndim;
     for (int k = 0; k < 3; k++) dims[k] = k < h.ndim ? h.dims[k] : 1;
