@@ -182,6 +182,37 @@ def _dev_tensor(t, what):
     return t
 
 
+def _dev_buf(t, what, device, dtype=None, numel=0):
+    """A tensor the library reads or writes whole: contiguous, on `device`, of
+    `dtype` (element size checked when dtype is an int) and at least `numel`
+    elements.  Several C entries are given no size for it (the element count
+    follows from the shape), so a smaller tensor would be read or written
+    past its end by the kernels: the check is made here, before the call."""
+    _dev_tensor(t, what)
+    if t.device != device:
+        raise ValueError("%s is on %s, the call runs on %s" % (what, t.device, device))
+    if isinstance(dtype, int):
+        if t.element_size() != dtype:
+            raise TypeError("%s must have %d-byte elements, got %s" % (what, dtype, t.dtype))
+    elif dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (what, dtype, t.dtype))
+    if t.numel() < numel:
+        raise ValueError("%s holds %d elements, %d are needed" % (what, t.numel(), numel))
+    return t
+
+
+def _host_buf(t, what):
+    """A host tensor the library copies from or into (pinned memory lets the
+    copies overlap the kernels; pageable memory works, with staged copies)."""
+    if not (isinstance(t, torch.Tensor) and not t.is_cuda and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous CPU tensor" % what)
+    return t
+
+
+def _numel(shape):
+    return math.prod(int(x) for x in shape)
+
+
 def hpdr_compress_bound(shape, dtype=torch.float32, dict_size=8192, chunk=0):
     nd, dims = _dims(shape)
     cfg = _cfg(dict_size, chunk)
@@ -214,9 +245,10 @@ def hpdr_compress(u, tol, tol_kind=REL, mode=LINF, dict_size=8192, chunk=0, out=
     _dev_tensor(u, "u")
     nd, dims = _dims(u.shape)
     cfg = _cfg(dict_size, chunk)
-    cap = hpdr_compress_bound(u.shape, u.dtype, dict_size, chunk)
     if out is None:
-        out = torch.empty(cap, dtype=torch.uint8, device=u.device)
+        out = torch.empty(hpdr_compress_bound(u.shape, u.dtype, dict_size, chunk), dtype=torch.uint8,
+                          device=u.device)
+    _dev_buf(out, "out", u.device, torch.uint8)
     nb = C.c_size_t()
     co = _coords(coords, tuple(u.shape))
     _check(lib().hpdr_compress_coords(context(u.device.index), C.c_void_p(u.data_ptr()), _dtype_code(u.dtype),
@@ -232,6 +264,8 @@ def hpdr_compress_async(u, tol, out, result, tol_kind=REL, mode=LINF, dict_size=
     CUDA tensor of 2) receives {container bytes, device status} when the stream
     gets there."""
     _dev_tensor(u, "u")
+    _dev_buf(out, "out", u.device, torch.uint8)
+    _dev_buf(result, "result", u.device, 8, 2)
     nd, dims = _dims(u.shape)
     cfg = _cfg(dict_size, chunk)
     _check(lib().hpdr_compress_async(context(u.device.index), C.c_void_p(u.data_ptr()), _dtype_code(u.dtype), nd, dims,
@@ -245,6 +279,8 @@ def hpdr_decompress_async(buf, out, result, dict_size=8192, chunk=0, stream=None
     the field's shape and type (they must match the container), `result`
     (int64 CUDA tensor of 1) receives the device status."""
     _dev_tensor(buf, "buf")
+    _dev_buf(out, "out", buf.device)
+    _dev_buf(result, "result", buf.device, 8, 1)
     nd, dims = _dims(out.shape)
     cfg = _cfg(dict_size, chunk)
     _check(lib().hpdr_decompress_async(context(buf.device.index), C.c_void_p(buf.data_ptr()), buf.numel(),
@@ -272,6 +308,7 @@ def hpdr_decompress(buf, out=None, stream=None):
     dt, shape = hpdr_inspect(buf)
     if out is None:
         out = torch.empty(shape, dtype=dt, device=buf.device)
+    _dev_buf(out, "out", buf.device, dt, _numel(shape))
     _check(lib().hpdr_decompress(context(buf.device.index), C.c_void_p(buf.data_ptr()), buf.numel(),
                                  C.c_void_p(out.data_ptr()), out.numel() * out.element_size(),
                                  _stream(stream)), "hpdr_decompress")
@@ -301,6 +338,7 @@ def hpdr_decompose(u, out=None, stream=None, coords=None):
     _dev_tensor(u, "u")
     if out is None:
         out = torch.empty(u.numel(), dtype=u.dtype, device=u.device)
+    _dev_buf(out, "out", u.device, u.dtype, u.numel())
     if coords is not None:
         return _coords_call("hpdr_decompose_coords", u, out, u.shape, coords, stream)
     return _field_call("hpdr_decompose", u, out, u.shape, stream)
@@ -312,6 +350,7 @@ def hpdr_decompose_noalloc(u, out=None, stream=None):
     _dev_tensor(u, "u")
     if out is None:
         out = torch.empty(u.numel(), dtype=u.dtype, device=u.device)
+    _dev_buf(out, "out", u.device, u.dtype, u.numel())
     nd, dims = _dims(u.shape)
     with torch.cuda.device(u.device):
         _check(lib().hpdr_decompose_noalloc(C.c_void_p(u.data_ptr()), C.c_void_p(out.data_ptr()),
@@ -343,6 +382,7 @@ def hpdr_compress_host_streamed(u, tol, tol_kind=REL, mode=LINF, slab_bytes=256 
     if out is None:
         out = torch.empty(streamed_bound(u.shape, u.dtype, slab_bytes, dict_size, chunk), dtype=torch.uint8,
                           pin_memory=True)
+    _host_buf(out, "out")
     nb = C.c_size_t()
     _check(lib().hpdr_compress_host_streamed(context(device), C.c_void_p(u.data_ptr()), _dtype_code(u.dtype),
                                              nd, dims, float(tol), int(tol_kind), int(mode), C.byref(cfg),
@@ -375,6 +415,7 @@ def hpdr_lossless_compress(keys, K=0, out=None, stream=None):
     n = keys.numel()
     if out is None:
         out = torch.empty(lossless_bound(n, kb, K), dtype=torch.uint8, device=keys.device)
+    _dev_buf(out, "out", keys.device, torch.uint8)
     nb = C.c_size_t()
     with torch.cuda.device(keys.device):
         _check(lib().hpdr_lossless_compress(context(keys.device.index), C.c_void_p(keys.data_ptr()), n, kb, int(K),
@@ -392,6 +433,7 @@ def hpdr_lossless_decompress(buf, out=None, stream=None):
            "hpdr_lossless_inspect")
     if out is None:
         out = torch.empty(n.value, dtype=torch.uint8 if kb.value == 1 else torch.int16, device=buf.device)
+    _dev_buf(out, "out", buf.device)
     with torch.cuda.device(buf.device):
         _check(lib().hpdr_lossless_decompress(context(buf.device.index), C.c_void_p(buf.data_ptr()), buf.numel(),
                                               C.c_void_p(out.data_ptr()), out.numel() * out.element_size(),
@@ -462,6 +504,7 @@ def hpdr_compress_host_adaptive(u, tol, model, c_init=64 << 20, c_limit=1 << 30,
         planes = pipeline_plan(model, u.shape[0], plane, c_init, c_limit)
         out = torch.empty(streamed_bound_plan(u.shape, u.dtype, planes, dict_size, chunk), dtype=torch.uint8,
                           pin_memory=True)
+    _host_buf(out, "out")
     nb = C.c_size_t()
     _check(lib().hpdr_compress_host_adaptive(context(device), C.c_void_p(u.data_ptr()), _dtype_code(u.dtype),
                                              nd, dims, float(tol), int(tol_kind), int(mode), C.byref(cfg),
@@ -473,6 +516,9 @@ def hpdr_compress_host_adaptive(u, tol, model, c_init=64 << 20, c_limit=1 << 30,
 
 def hpdr_decompress_host_streamed(buf, out=None, device=None):
     """Inverse of hpdr_compress_host_streamed (CPU tensors in and out)."""
+    _host_buf(buf, "buf")
+    if buf.numel() < 64:
+        raise HpdrError(-4, "hpdr_decompress_host_streamed")
     b = bytes(buf[:64].numpy().tobytes())
     ns = int.from_bytes(b[8:12], "little")
     dt = torch.float32 if int.from_bytes(b[12:16], "little") == 0 else torch.float64
@@ -480,6 +526,7 @@ def hpdr_decompress_host_streamed(buf, out=None, device=None):
     shape = tuple(int.from_bytes(b[16 + 8 * k:24 + 8 * k], "little") for k in range(nd))
     if out is None:
         out = torch.empty(shape, dtype=dt, pin_memory=True)
+    _host_buf(out, "out")
     _check(lib().hpdr_decompress_host_streamed(context(device), C.c_void_p(buf.data_ptr()), buf.numel(),
                                                C.c_void_p(out.data_ptr()), out.numel() * out.element_size()),
            "hpdr_decompress_host_streamed")
@@ -506,9 +553,15 @@ def hpdr_compress_batched(fields, tols, tol_kind=REL, mode=LINF, dict_size=8192,
         nd, dims = _dims(u.shape)
         arr[i] = Field(C.c_void_p(u.data_ptr()), _dtype_code(u.dtype), nd, dims, float(tol), int(tol_kind),
                        int(mode))
+    if n == 0:
+        raise ValueError("hpdr_compress_batched needs at least one field")
+    for u in fields:
+        if u.device != fields[0].device:
+            raise ValueError("every field of a batch must be on one device")
     if out is None:
         out = torch.empty(batched_capacity([(u.shape, u.dtype) for u in fields], dict_size, chunk),
                           dtype=torch.uint8, device=fields[0].device)
+    _dev_buf(out, "out", fields[0].device, torch.uint8)
     cfg = _cfg(dict_size, chunk)
     offs = (C.c_size_t * (n + 1))()
     sizes = (C.c_size_t * n)()
@@ -520,8 +573,12 @@ def hpdr_compress_batched(fields, tols, tol_kind=REL, mode=LINF, dict_size=8192,
 
 def hpdr_recompose(coef, shape, out=None, stream=None, coords=None):
     _dev_tensor(coef, "coef")
+    if coef.numel() != _numel(shape):
+        raise ValueError("coef holds %d coefficients, the shape %s has %d nodes" % (coef.numel(), tuple(shape),
+                                                                                   _numel(shape)))
     if out is None:
         out = torch.empty(tuple(shape), dtype=coef.dtype, device=coef.device)
+    _dev_buf(out, "out", coef.device, coef.dtype, coef.numel())
     if coords is not None:
         return _coords_call("hpdr_recompose_coords", coef, out, shape, coords, stream)
     return _field_call("hpdr_recompose", coef, out, shape, stream)
@@ -531,6 +588,7 @@ def hpdr_recompose_adjoint(grad_u, out=None, stream=None, coords=None):
     _dev_tensor(grad_u, "grad_u")
     if out is None:
         out = torch.empty(grad_u.numel(), dtype=grad_u.dtype, device=grad_u.device)
+    _dev_buf(out, "out", grad_u.device, grad_u.dtype, grad_u.numel())
     if coords is not None:
         return _coords_call("hpdr_recompose_adjoint_coords", grad_u, out, grad_u.shape, coords, stream)
     return _field_call("hpdr_recompose_adjoint", grad_u, out, grad_u.shape, stream)
@@ -538,8 +596,12 @@ def hpdr_recompose_adjoint(grad_u, out=None, stream=None, coords=None):
 
 def hpdr_decompose_adjoint(grad_coef, shape, out=None, stream=None, coords=None):
     _dev_tensor(grad_coef, "grad_coef")
+    if grad_coef.numel() != _numel(shape):
+        raise ValueError("grad_coef holds %d values, the shape %s has %d nodes" % (grad_coef.numel(), tuple(shape),
+                                                                                  _numel(shape)))
     if out is None:
         out = torch.empty(tuple(shape), dtype=grad_coef.dtype, device=grad_coef.device)
+    _dev_buf(out, "out", grad_coef.device, grad_coef.dtype, grad_coef.numel())
     if coords is not None:
         return _coords_call("hpdr_decompose_adjoint_coords", grad_coef, out, shape, coords, stream)
     return _field_call("hpdr_decompose_adjoint", grad_coef, out, shape, stream)
@@ -551,6 +613,7 @@ def hpdr_huffman_encode(symbols, D=8192, K=1024, stream=None):
     Returns (lengths uint8[D], chunk table int64[ceil(N/K)], words int32[...],
     total_bits)."""
     _dev_tensor(symbols, "symbols")
+    _dev_buf(symbols, "symbols", symbols.device, 2)
     N = symbols.numel()
     dev = symbols.device
     lengths = torch.empty(D, dtype=torch.uint8, device=dev)
@@ -567,9 +630,15 @@ def hpdr_huffman_encode(symbols, D=8192, K=1024, stream=None):
 
 def hpdr_huffman_decode(words, total_bits, chunk, N, lengths, D=8192, K=1024, out=None,
                         stream=None):
+    _dev_tensor(words, "words")
     dev = words.device
+    N, K, D = int(N), int(K), int(D)
+    _dev_buf(words, "words", dev, 4, (int(total_bits) + 31) // 32)
+    _dev_buf(chunk, "chunk", dev, 8, (N + K - 1) // K)
+    _dev_buf(lengths, "lengths", dev, torch.uint8, D)
     if out is None:
         out = torch.empty(N, dtype=torch.int16, device=dev)
+    _dev_buf(out, "out", dev, 2, N)
     _check(lib().hpdr_huffman_decode(context(dev.index), C.c_void_p(words.data_ptr()),
                                      int(total_bits), C.c_void_p(chunk.data_ptr()), N, D, K,
                                      C.c_void_p(lengths.data_ptr()), C.c_void_p(out.data_ptr()),
@@ -594,6 +663,7 @@ def hpdr_zfp_compress(u, rate, out=None, stream=None):
         raise ValueError("invalid ZFP rate %r for %d dimensions" % (rate, nd))
     if out is None:
         out = torch.empty(cap, dtype=torch.uint8, device=u.device)
+    _dev_buf(out, "out", u.device, torch.uint8)
     nb = C.c_size_t()
     _check(lib().hpdr_zfp_compress(context(u.device.index), C.c_void_p(u.data_ptr()), _dtype_code(u.dtype), nd,
                                    dims, int(rate), C.c_void_p(out.data_ptr()), out.numel(), C.byref(nb),
@@ -614,6 +684,7 @@ def hpdr_zfp_decompress(buf, out=None, stream=None):
     dt, shape, _ = hpdr_zfp_inspect(buf)
     if out is None:
         out = torch.empty(shape, dtype=dt, device=buf.device)
+    _dev_buf(out, "out", buf.device, dt)
     _check(lib().hpdr_zfp_decompress(context(buf.device.index), C.c_void_p(buf.data_ptr()), buf.numel(),
                                      C.c_void_p(out.data_ptr()), out.numel() * out.element_size(),
                                      _stream(stream)), "hpdr_zfp_decompress")
